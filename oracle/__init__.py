@@ -1,0 +1,275 @@
+"""ctypes wrapper around the plain-C oracle (``oracle/lsq_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the slow, obviously correct CPU
+statement of randomized-preconditioned normal equations (Garrison & Ipsen,
+arXiv 2603.16644, Alg. 1 and Eqs. e_pne / e_hpne).  Only the tests, the
+package smoke check and the benchmark's CPU-baseline leg may import it; the
+CUDA library never does, and the two share no code.
+
+All matrices are numpy float64 arrays in Fortran (column-major) order.
+"""
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import build as _build
+
+FP8_E4M3, BF16, FP16, FP32, FP64, AUTO = 0, 1, 2, 3, 4, 5
+GAUSSIAN, SPARSE_SIGN = 0, 1
+PREC_NAMES = {FP8_E4M3: "fp8_e4m3", BF16: "bf16", FP16: "fp16", FP32: "fp32", FP64: "fp64", AUTO: "auto"}
+
+_lib = None
+
+_d = C.POINTER(C.c_double)
+_i32 = C.POINTER(C.c_int32)
+_i8 = C.POINTER(C.c_int8)
+_u32 = C.POINTER(C.c_uint32)
+_i64 = C.c_int64
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        sig = {
+            "lsqo_round": (C.c_double, [C.c_double, C.c_int]),
+            "lsqo_round_array": (None, [_d, _i64, C.c_int, _d]),
+            "lsqo_philox4x32_10": (None, [_u32, _u32, _u32]),
+            "lsqo_sparse_sign_column": (C.c_int, [C.c_uint64, _i64, _i64, C.c_int, _i32, _i8]),
+            "lsqo_sparse_sign_indices": (C.c_int, [C.c_uint64, _i64, _i64, C.c_int, _i32, _i8]),
+            "lsqo_gaussian_entry": (C.c_double, [C.c_uint64, _i64, _i64]),
+            "lsqo_gaussian_operator": (None, [C.c_uint64, _i64, _i64, C.c_int, _d]),
+            "lsqo_colexp": (None, [_d, _i64, _i64, _i64, C.c_int, _i32]),
+            "lsqo_quantize": (None, [_d, _i64, _i64, _i64, C.c_int, _i32, _d]),
+            "lsqo_sketch": (C.c_int, [_d, _i64, _i64, _i64, C.c_int, _i64, C.c_int, C.c_uint64, C.c_int, _d, _i32]),
+            "lsqo_qr_r": (C.c_int, [_d, _i64, _i64, _i64, C.c_int, _d]),
+            "lsqo_unscale_r": (None, [_d, _i64, _i64, _i32]),
+            "lsqo_trsm_right_upper": (C.c_int, [_d, _i64, _i64, _i64, _d, _i64, _d]),
+            "lsqo_gram": (None, [_d, _d, _i64, _i64, _i64, _i64, _d, _d, _d]),
+            "lsqo_cholesky": (C.c_int, [_d, _i64, _i64]),
+            "lsqo_lu": (C.c_int, [_d, _i64, _i64, _i32]),
+            "lsqo_solve_lower": (None, [_d, _i64, _i64, C.c_int, _d]),
+            "lsqo_solve_lower_t": (None, [_d, _i64, _i64, _d]),
+            "lsqo_solve_upper": (None, [_d, _i64, _i64, _d]),
+            "lsqo_lu_solve": (None, [_d, _i64, _i64, _i32, _d]),
+            "lsqo_lstsq_qr": (C.c_int, [_d, _i64, _i64, _i64, _d, _d]),
+            "lsqo_precision_from_kappa0": (C.c_int, [C.c_double]),
+            "lsqo_condest": (C.c_int, [_d, _i64, _i64, _i64, _d, _i32, _d, _d]),
+            "lsqo_solve": (C.c_int, [_d, _i64, _i64, _i64, _d, C.c_int, C.c_int, _i64, C.c_int, C.c_uint64,
+                                     C.c_int, C.c_int, C.c_int, _d, _d, _d, _i32]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _p(a, ct=C.c_double):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def _f64(a):
+    return np.asfortranarray(np.asarray(a, dtype=np.float64))
+
+
+# --- rounding ---------------------------------------------------------------
+def round_to(x, prec):
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    y = np.empty_like(x)
+    lib().lsqo_round_array(_p(x), x.size, prec, _p(y))
+    return y
+
+
+# --- random streams ---------------------------------------------------------
+def philox4x32_10(ctr, key):
+    c = np.asarray(ctr, dtype=np.uint32).copy()
+    k = np.asarray(key, dtype=np.uint32).copy()
+    out = np.zeros(4, dtype=np.uint32)
+    lib().lsqo_philox4x32_10(_p(c, C.c_uint32), _p(k, C.c_uint32), _p(out, C.c_uint32))
+    return out
+
+
+def sparse_sign_indices(seed, m, s, zeta):
+    """Row indices (m, zeta) int32 and signs (m, zeta) int8 of every column of Omega."""
+    idx = np.zeros((m, zeta), dtype=np.int32)
+    sgn = np.zeros((m, zeta), dtype=np.int8)
+    rc = lib().lsqo_sparse_sign_indices(C.c_uint64(seed), m, s, zeta, _p(idx, C.c_int32), _p(sgn, C.c_int8))
+    if rc:
+        raise ValueError(f"sparse_sign_indices rc={rc}")
+    return idx, sgn
+
+
+def gaussian_entry(seed, i, j):
+    return lib().lsqo_gaussian_entry(C.c_uint64(seed), i, j)
+
+
+def gaussian_operator(seed, s, m, prec=FP64):
+    Om = np.zeros((s, m), dtype=np.float64, order="F")
+    lib().lsqo_gaussian_operator(C.c_uint64(seed), s, m, prec, _p(Om))
+    return Om
+
+
+# --- method steps -----------------------------------------------------------
+def colexp(A, prec):
+    A = _f64(A)
+    m, n = A.shape
+    e = np.zeros(n, dtype=np.int32)
+    lib().lsqo_colexp(_p(A), m, n, m, prec, _p(e, C.c_int32))
+    return e
+
+
+def quantize(A, prec, e):
+    A = _f64(A)
+    m, n = A.shape
+    e = np.ascontiguousarray(e, dtype=np.int32)
+    out = np.zeros((m, n), dtype=np.float64, order="F")
+    lib().lsqo_quantize(_p(A), m, n, m, prec, _p(e, C.c_int32), _p(out))
+    return out
+
+
+def sketch(A, kind, s, zeta, seed, prec):
+    """Returns (A_s (s, n) float64 holding FP32 values unless prec==FP64, colexp)."""
+    A = _f64(A)
+    m, n = A.shape
+    As = np.zeros((s, n), dtype=np.float64, order="F")
+    e = np.zeros(n, dtype=np.int32)
+    rc = lib().lsqo_sketch(_p(A), m, n, m, kind, s, zeta, C.c_uint64(seed), prec, _p(As), _p(e, C.c_int32))
+    if rc:
+        raise ValueError(f"sketch rc={rc}")
+    return As, e
+
+
+def qr_r(As, prec):
+    As = _f64(As)
+    s, n = As.shape
+    R = np.zeros((n, n), dtype=np.float64, order="F")
+    rc = lib().lsqo_qr_r(_p(As), s, n, s, prec, _p(R))
+    if rc:
+        raise ValueError(f"qr_r rc={rc}")
+    return R
+
+
+def unscale_r(R, e):
+    R = _f64(R).copy(order="F")
+    n = R.shape[0]
+    e = np.ascontiguousarray(e, dtype=np.int32)
+    lib().lsqo_unscale_r(_p(R), n, n, _p(e, C.c_int32))
+    return R
+
+
+def trsm_right_upper(A, R):
+    A = _f64(A)
+    R = _f64(R)
+    m, n = A.shape
+    Ap = np.zeros((m, n), dtype=np.float64, order="F")
+    lib().lsqo_trsm_right_upper(_p(A), m, n, m, _p(R), n, _p(Ap))
+    return Ap
+
+
+def gram(X, Y, b=None):
+    X = _f64(X)
+    Y = _f64(Y)
+    m, n = X.shape
+    G = np.zeros((n, n), dtype=np.float64, order="F")
+    c = np.zeros(n, dtype=np.float64)
+    bb = _f64(b) if b is not None else None
+    lib().lsqo_gram(_p(X), _p(Y), m, n, m, m, _p(bb) if bb is not None else None, _p(G),
+                    _p(c) if bb is not None else None)
+    return G, (c if bb is not None else None)
+
+
+def cholesky(G):
+    L = _f64(G).copy(order="F")
+    n = L.shape[0]
+    info = lib().lsqo_cholesky(_p(L), n, n)
+    return L, info
+
+
+def lu(H):
+    LU = _f64(H).copy(order="F")
+    n = LU.shape[0]
+    piv = np.zeros(n, dtype=np.int32)
+    info = lib().lsqo_lu(_p(LU), n, n, _p(piv, C.c_int32))
+    return LU, piv, info
+
+
+def solve_lower(L, y, unit=False):
+    L = _f64(L)
+    y = np.array(y, dtype=np.float64)
+    lib().lsqo_solve_lower(_p(L), L.shape[0], L.shape[0], int(unit), _p(y))
+    return y
+
+
+def solve_lower_t(L, y):
+    L = _f64(L)
+    y = np.array(y, dtype=np.float64)
+    lib().lsqo_solve_lower_t(_p(L), L.shape[0], L.shape[0], _p(y))
+    return y
+
+
+def solve_upper(U, y):
+    U = _f64(U)
+    y = np.array(y, dtype=np.float64)
+    lib().lsqo_solve_upper(_p(U), U.shape[0], U.shape[0], _p(y))
+    return y
+
+
+def lu_solve(LU, piv, y):
+    LU = _f64(LU)
+    y = np.array(y, dtype=np.float64)
+    piv = np.ascontiguousarray(piv, dtype=np.int32)
+    lib().lsqo_lu_solve(_p(LU), LU.shape[0], LU.shape[0], _p(piv, C.c_int32), _p(y))
+    return y
+
+
+def lstsq_qr(A, b):
+    """Reference least-squares solution by FP64 Householder QR (not the method)."""
+    A = _f64(A)
+    m, n = A.shape
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n, dtype=np.float64)
+    rc = lib().lsqo_lstsq_qr(_p(A), m, n, m, _p(b), _p(x))
+    if rc:
+        raise ValueError("lstsq_qr: bad shape")
+    return x
+
+
+def precision_from_kappa0(k0):
+    return lib().lsqo_precision_from_kappa0(float(k0))
+
+
+def condest(A):
+    """Returns (kappa0, chosen precision, ||G||_1, gamma, cholesky info)."""
+    A = _f64(A)
+    m, n = A.shape
+    k0 = C.c_double()
+    ch = C.c_int32()
+    nr = C.c_double()
+    ga = C.c_double()
+    info = lib().lsqo_condest(_p(A), m, n, m, C.byref(k0), C.byref(ch), C.byref(nr), C.byref(ga))
+    return k0.value, ch.value, nr.value, ga.value, info
+
+
+def solve(A, b, *, hpne=False, kind=SPARSE_SIGN, s=None, zeta=8, seed=0, sketch_prec=FP32,
+          qr_prec=FP32, refine_steps=0):
+    """Alg. 1 end to end.  Returns dict(x, Rs, info, kappa0, prec)."""
+    A = _f64(A)
+    m, n = A.shape
+    s = 2 * n if s is None else s
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n, dtype=np.float64)
+    Rs = np.zeros((n, n), dtype=np.float64, order="F")
+    k0 = C.c_double()
+    pr = C.c_int32()
+    info = lib().lsqo_solve(_p(A), m, n, m, _p(b), int(hpne), kind, s, zeta, C.c_uint64(seed),
+                            sketch_prec, qr_prec, refine_steps, _p(x), _p(Rs), C.byref(k0), C.byref(pr))
+    return {"x": x, "Rs": Rs, "info": info, "kappa0": k0.value, "prec": pr.value}
+
+
+def kappa(M):
+    s = np.linalg.svd(np.asarray(M), compute_uv=False)
+    return float(s[0] / s[-1]) if s[-1] > 0 else math.inf

@@ -1,0 +1,789 @@
+/*
+ * Plain, slow CPU oracle for randomized-preconditioned normal equations
+ * (Garrison & Ipsen, "Perturbation Analysis for Preconditioned Normal
+ * Equations in Mixed Precision", arXiv 2603.16644).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may include, link,
+ * load or call this file; only the tests, the package smoke check and the
+ * benchmark's CPU-baseline leg do.  It shares no code, header, table or
+ * constant generator with the CUDA library.
+ *
+ * Conventions
+ *   - Matrices are column-major: entry (i, j) of an m-by-n matrix with
+ *     leading dimension ld sits at [i + j*ld].
+ *   - Everything is FP64 unless a step of the method fixes a lower
+ *     precision; lower precision is emulated by explicit round-to-nearest-
+ *     even (RNE) conversions and, for FP32 arithmetic, by C `float`
+ *     operations.  Build with -ffp-contract=off so that no multiply-add is
+ *     fused behind our back: every product and sum below is rounded once.
+ *   - Loops run in plain index order; there is no blocking, fusion or
+ *     reordering, so each function can be checked against its source by eye.
+ *
+ * Precision codes: 0 FP8-e4m3 (OCP "fn", saturating), 1 BF16, 2 FP16,
+ * 3 FP32, 4 FP64, 5 AUTO (choose by the condition estimate).
+ * Sketch kinds: 0 Gaussian, 1 sparse sign.
+ *
+ * Pins (checked by the CPU-only tests against the mathematics, never
+ * against the CUDA path): rounding exhaustively against the IEEE/OCP format
+ * definitions; Philox against the published known-answer vectors; the
+ * sparse-sign stream against its distinctness/uniformity invariants; the
+ * Householder least-squares solve against exact rational arithmetic and
+ * generated problems with known solutions; QR against the Cholesky factor of
+ * the sketch Gram matrix; PNE/HPNE against exact solutions for any
+ * nonsingular R_s and against the error bounds Eq. (eq41)/(eq32); the
+ * condition estimate against the exact inverse 1-norm (it is a lower bound)
+ * and the kappa^2 inequality of Sec. 6.1.  Parity unpinned: the Gaussian
+ * entry values beyond their moments (Box-Muller through libm).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { O_FP8 = 0, O_BF16 = 1, O_FP16 = 2, O_FP32 = 3, O_FP64 = 4, O_AUTO = 5 };
+enum { O_GAUSSIAN = 0, O_SPARSE_SIGN = 1 };
+
+#define IDX(i, j, ld) ((size_t)(i) + (size_t)(j) * (size_t)(ld))
+
+/* ------------------------------------------------------------------------
+ * Rounding FP64 -> lower precision, one rounding, RNE, subnormals kept.
+ * A format is (p significand bits incl. the implicit one, minimum normal
+ * exponent emin, largest finite value, saturate-or-overflow).
+ * ---------------------------------------------------------------------- */
+static double rne_format(double x, int p, int emin, double maxfin, int sat)
+{
+    if (isnan(x) || x == 0.0) return x;
+    if (isinf(x)) return sat ? copysign(maxfin, x) : x;
+    double a = fabs(x);
+    int E;
+    frexp(a, &E);            /* a = f * 2^E with f in [0.5, 1) */
+    int e = E - 1;           /* floor(log2(a)) */
+    if (e < emin) e = emin;  /* subnormal range: fixed quantum */
+    int q = e - (p - 1);     /* exponent of one unit in the last place */
+    double r = rint(ldexp(a, -q)); /* exact scaling, then RNE to integer */
+    double y = ldexp(r, q);
+    if (y > maxfin) y = sat ? maxfin : INFINITY;
+    return copysign(y, x);
+}
+
+double lsqo_round(double x, int prec)
+{
+    switch (prec) {
+    case O_FP8:  return rne_format(x, 4, -6, 448.0, 1);
+    case O_BF16: return rne_format(x, 8, -126, 0x1.fep127, 0);
+    case O_FP16: return rne_format(x, 11, -14, 65504.0, 0);
+    case O_FP32: return rne_format(x, 24, -126, 0x1.fffffep127, 0);
+    default:     return x;
+    }
+}
+
+void lsqo_round_array(const double* x, int64_t len, int prec, double* y)
+{
+    for (int64_t i = 0; i < len; ++i) y[i] = lsqo_round(x[i], prec);
+}
+
+/* ------------------------------------------------------------------------
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel random
+ * numbers: as easy as 1, 2, 3"): ten rounds of two 32x32->64 multiplies
+ * with the published multipliers, key bumped by the published Weyl
+ * constants between rounds.
+ * ---------------------------------------------------------------------- */
+void lsqo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ------------------------------------------------------------------------
+ * Sketch operators (Alg. 1 takes a random d-by-m sketch; the sparse-sign
+ * and Gaussian families stand in for the paper's SRFT of Eq. (e_sketch)).
+ *
+ * Sparse sign, column j of Omega (s-by-m): zeta DISTINCT rows in [0, s),
+ * drawn in order from the Philox stream key = seed, counter =
+ * (block k, j_lo, j_hi, 0), words consumed w0..w3 per block; each word is
+ * mapped to [0, s) by Lemire's multiply-shift with rejection of the low
+ * product below (2^32 - s) mod s, and duplicates are rejected.  Sign of the
+ * t-th accepted row: bit t of word 0 of counter (0, j_lo, j_hi, 1), 1 = -1.
+ * ---------------------------------------------------------------------- */
+int lsqo_sparse_sign_column(uint64_t seed, int64_t j, int64_t s, int zeta,
+                            int32_t* idx, int8_t* sgn)
+{
+    if (s <= 0 || s > 0x7fffffff || zeta <= 0 || zeta > 32 || zeta > s) return -1;
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t su = (uint32_t)s;
+    uint32_t thresh = (uint32_t)(0u - su) % su;
+    int got = 0;
+    for (uint32_t k = 0; got < zeta; ++k) {
+        if (k > (1u << 20)) return -2;
+        uint32_t ctr[4] = { k, (uint32_t)j, (uint32_t)((uint64_t)j >> 32), 0u };
+        uint32_t w[4];
+        lsqo_philox4x32_10(ctr, key, w);
+        for (int t = 0; t < 4 && got < zeta; ++t) {
+            uint64_t prod = (uint64_t)w[t] * (uint64_t)su;
+            if ((uint32_t)prod < thresh) continue;
+            int32_t cand = (int32_t)(prod >> 32);
+            int dup = 0;
+            for (int q = 0; q < got; ++q) dup |= (idx[q] == cand);
+            if (!dup) idx[got++] = cand;
+        }
+    }
+    uint32_t ctr[4] = { 0u, (uint32_t)j, (uint32_t)((uint64_t)j >> 32), 1u };
+    uint32_t w[4];
+    lsqo_philox4x32_10(ctr, key, w);
+    for (int t = 0; t < zeta; ++t) sgn[t] = ((w[0] >> t) & 1u) ? (int8_t)-1 : (int8_t)1;
+    return 0;
+}
+
+int lsqo_sparse_sign_indices(uint64_t seed, int64_t m, int64_t s, int zeta,
+                             int32_t* idx /* m*zeta */, int8_t* sgn /* m*zeta */)
+{
+    for (int64_t j = 0; j < m; ++j) {
+        int rc = lsqo_sparse_sign_column(seed, j, s, zeta, idx + j * zeta, sgn + j * zeta);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+/* Gaussian entry Omega(i, j): counter (i, j_lo, j_hi, 2); two 53-bit
+ * uniforms u1 in (0, 1], u2 in [0, 1); Box-Muller z = sqrt(-2 ln u1) *
+ * cos(2 pi u2) (Box & Muller 1958).  Unscaled N(0, 1) entries. */
+double lsqo_gaussian_entry(uint64_t seed, int64_t i, int64_t j)
+{
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t ctr[4] = { (uint32_t)i, (uint32_t)j, (uint32_t)((uint64_t)j >> 32), 2u };
+    uint32_t w[4];
+    lsqo_philox4x32_10(ctr, key, w);
+    uint64_t a = (uint64_t)(w[0] >> 5), b = (uint64_t)(w[1] >> 6);
+    double u1 = ((double)(a * 67108864ull + b) + 1.0) * 0x1p-53;
+    a = (uint64_t)(w[2] >> 5); b = (uint64_t)(w[3] >> 6);
+    double u2 = (double)(a * 67108864ull + b) * 0x1p-53;
+    double rad = sqrt(-2.0 * log(u1));
+    double th = 6.283185307179586 * u2;
+    return rad * cos(th);
+}
+
+void lsqo_gaussian_operator(uint64_t seed, int64_t s, int64_t m, int prec, double* Om /* s-by-m, ld s */)
+{
+    for (int64_t j = 0; j < m; ++j)
+        for (int64_t i = 0; i < s; ++i)
+            Om[IDX(i, j, s)] = lsqo_round(lsqo_gaussian_entry(seed, i, j), prec);
+}
+
+/* ------------------------------------------------------------------------
+ * Per-column power-of-two scaling before rounding A to the sketch precision
+ * u_p (Alg. 1 computes the sketch in u_p).  Column j is multiplied by
+ * 2^e_j so that max_i |a_ij| * 2^e_j lies in [2^(t-1), 2^t) with t = 8 for
+ * FP8-e4m3, 15 for FP16, 0 for BF16 and FP32; FP64 is not scaled.
+ * ---------------------------------------------------------------------- */
+static int scale_target(int prec)
+{
+    switch (prec) { case O_FP8: return 8; case O_FP16: return 15; default: return 0; }
+}
+
+void lsqo_colexp(const double* A, int64_t m, int64_t n, int64_t lda, int prec, int32_t* colexp)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        double mx = 0.0;
+        for (int64_t i = 0; i < m; ++i) { double v = fabs(A[IDX(i, j, lda)]); if (v > mx) mx = v; }
+        if (prec == O_FP64 || mx == 0.0 || !isfinite(mx)) { colexp[j] = 0; continue; }
+        int E;
+        frexp(mx, &E);
+        colexp[j] = scale_target(prec) - E;
+    }
+}
+
+/* Ahat = round_p(A * 2^E), m-by-n, ld m. */
+void lsqo_quantize(const double* A, int64_t m, int64_t n, int64_t lda, int prec,
+                   const int32_t* colexp, double* Ahat)
+{
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < m; ++i)
+            Ahat[IDX(i, j, m)] = lsqo_round(ldexp(A[IDX(i, j, lda)], colexp[j]), prec);
+}
+
+/* ------------------------------------------------------------------------
+ * Sketch A_s = Omega_hat * Ahat (Alg. 1, "Sketch A_s = Omega A" in u_p).
+ * Products of two values in FP8/BF16/FP16 are exact in FP32; accumulation
+ * is FP32 RNE in ascending column index j of Omega (FP64 when prec = FP64).
+ * As is s-by-n, ld s, holding FP32-representable values unless FP64.
+ * ---------------------------------------------------------------------- */
+int lsqo_sketch(const double* A, int64_t m, int64_t n, int64_t lda, int kind, int64_t s,
+                int zeta, uint64_t seed, int prec, double* As, int32_t* colexp)
+{
+    if (prec < O_FP8 || prec > O_FP64 || s <= 0 || m <= 0 || n <= 0) return -1;
+    double* Ahat = (double*)malloc(sizeof(double) * (size_t)m * (size_t)n);
+    if (!Ahat) return -3;
+    lsqo_colexp(A, m, n, lda, prec, colexp);
+    lsqo_quantize(A, m, n, lda, prec, colexp, Ahat);
+    int rc = 0;
+    if (kind == O_SPARSE_SIGN) {
+        int32_t idx[32];
+        int8_t sgn[32];
+        if (prec == O_FP64) {
+            for (size_t q = 0; q < (size_t)s * (size_t)n; ++q) As[q] = 0.0;
+            for (int64_t j = 0; j < m && !rc; ++j) {
+                rc = lsqo_sparse_sign_column(seed, j, s, zeta, idx, sgn);
+                for (int t = 0; t < zeta && !rc; ++t)
+                    for (int64_t c = 0; c < n; ++c)
+                        As[IDX(idx[t], c, s)] += (double)sgn[t] * Ahat[IDX(j, c, m)];
+            }
+        } else {
+            float* acc = (float*)calloc((size_t)s * (size_t)n, sizeof(float));
+            if (!acc) { free(Ahat); return -3; }
+            for (int64_t j = 0; j < m && !rc; ++j) {
+                rc = lsqo_sparse_sign_column(seed, j, s, zeta, idx, sgn);
+                for (int t = 0; t < zeta && !rc; ++t)
+                    for (int64_t c = 0; c < n; ++c) {
+                        float term = (float)((double)sgn[t] * Ahat[IDX(j, c, m)]);
+                        acc[IDX(idx[t], c, s)] = acc[IDX(idx[t], c, s)] + term;
+                    }
+            }
+            for (size_t q = 0; q < (size_t)s * (size_t)n; ++q) As[q] = (double)acc[q];
+            free(acc);
+        }
+    } else if (kind == O_GAUSSIAN) {
+        double* om = (double*)malloc(sizeof(double) * (size_t)m);
+        if (!om) { free(Ahat); return -3; }
+        for (int64_t i = 0; i < s; ++i) {
+            for (int64_t j = 0; j < m; ++j) om[j] = lsqo_round(lsqo_gaussian_entry(seed, i, j), prec);
+            for (int64_t c = 0; c < n; ++c) {
+                if (prec == O_FP64) {
+                    double acc = 0.0;
+                    for (int64_t j = 0; j < m; ++j) acc += om[j] * Ahat[IDX(j, c, m)];
+                    As[IDX(i, c, s)] = acc;
+                } else {
+                    float acc = 0.0f;
+                    for (int64_t j = 0; j < m; ++j) {
+                        float prod = (float)om[j] * (float)Ahat[IDX(j, c, m)];
+                        acc = acc + prod;
+                    }
+                    As[IDX(i, c, s)] = (double)acc;
+                }
+            }
+        }
+        free(om);
+    } else {
+        rc = -1;
+    }
+    free(Ahat);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------
+ * Householder vector (Golub & Van Loan, Matrix Computations, 4th ed.,
+ * Alg. 5.1.1, with the sigma = 0, x1 < 0 case mapping x to |x1| e1): for x
+ * of length len, returns beta and v with v[0] = 1 such that
+ * (I - beta v v^T) x = ||x|| e1.  Two versions: FP64 and FP32 arithmetic.
+ * ---------------------------------------------------------------------- */
+static double house64(const double* x, int64_t len, double* v, double* mu_out)
+{
+    double sigma = 0.0;
+    for (int64_t i = 1; i < len; ++i) sigma += x[i] * x[i];
+    v[0] = 1.0;
+    for (int64_t i = 1; i < len; ++i) v[i] = x[i];
+    double x1 = x[0];
+    if (sigma == 0.0) {
+        *mu_out = fabs(x1);
+        return x1 >= 0.0 ? 0.0 : 2.0;
+    }
+    double mu = sqrt(x1 * x1 + sigma);
+    double v1 = (x1 <= 0.0) ? x1 - mu : -sigma / (x1 + mu);
+    double beta = 2.0 * v1 * v1 / (sigma + v1 * v1);
+    for (int64_t i = 1; i < len; ++i) v[i] = v[i] / v1;
+    *mu_out = mu;
+    return beta;
+}
+
+static float house32(const float* x, int64_t len, float* v, float* mu_out)
+{
+    float sigma = 0.0f;
+    for (int64_t i = 1; i < len; ++i) sigma = sigma + x[i] * x[i];
+    v[0] = 1.0f;
+    for (int64_t i = 1; i < len; ++i) v[i] = x[i];
+    float x1 = x[0];
+    if (sigma == 0.0f) {
+        *mu_out = fabsf(x1);
+        return x1 >= 0.0f ? 0.0f : 2.0f;
+    }
+    float mu = sqrtf(x1 * x1 + sigma);
+    float v1 = (x1 <= 0.0f) ? x1 - mu : -sigma / (x1 + mu);
+    float beta = 2.0f * v1 * v1 / (sigma + v1 * v1);
+    for (int64_t i = 1; i < len; ++i) v[i] = v[i] / v1;
+    *mu_out = mu;
+    return beta;
+}
+
+/* Thin QR of the sketch, R only (Alg. 1, "Thin QR factorization A_s =
+ * Q_s R_s"), by unblocked Householder QR (Golub & Van Loan Alg. 5.2.1) in
+ * FP32 (prec = FP32) or FP64 arithmetic.  The reflector of column k maps it
+ * to (||x||, 0, ...), so diag(R) >= 0.  R is n-by-n upper, ld n, zero below
+ * the diagonal.  Returns 0, or -1 on bad arguments. */
+int lsqo_qr_r(const double* As, int64_t s, int64_t n, int64_t ldas, int prec, double* R)
+{
+    if (s < n || n <= 0) return -1;
+    if (prec == O_FP64) {
+        double* W = (double*)malloc(sizeof(double) * (size_t)s * (size_t)n);
+        double* v = (double*)malloc(sizeof(double) * (size_t)s);
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = 0; i < s; ++i) W[IDX(i, j, s)] = As[IDX(i, j, ldas)];
+        for (int64_t k = 0; k < n; ++k) {
+            double mu;
+            double beta = house64(&W[IDX(k, k, s)], s - k, v, &mu);
+            W[IDX(k, k, s)] = mu;
+            for (int64_t i = k + 1; i < s; ++i) W[IDX(i, k, s)] = 0.0;
+            for (int64_t c = k + 1; c < n; ++c) {
+                double w = 0.0;
+                for (int64_t i = k; i < s; ++i) w += v[i - k] * W[IDX(i, c, s)];
+                double t = beta * w;
+                for (int64_t i = k; i < s; ++i) W[IDX(i, c, s)] = W[IDX(i, c, s)] - t * v[i - k];
+            }
+        }
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = 0; i < n; ++i) R[IDX(i, j, n)] = (i <= j) ? W[IDX(i, j, s)] : 0.0;
+        free(W); free(v);
+    } else {
+        float* W = (float*)malloc(sizeof(float) * (size_t)s * (size_t)n);
+        float* v = (float*)malloc(sizeof(float) * (size_t)s);
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = 0; i < s; ++i) W[IDX(i, j, s)] = (float)As[IDX(i, j, ldas)];
+        for (int64_t k = 0; k < n; ++k) {
+            float mu;
+            float beta = house32(&W[IDX(k, k, s)], s - k, v, &mu);
+            W[IDX(k, k, s)] = mu;
+            for (int64_t i = k + 1; i < s; ++i) W[IDX(i, k, s)] = 0.0f;
+            for (int64_t c = k + 1; c < n; ++c) {
+                float w = 0.0f;
+                for (int64_t i = k; i < s; ++i) w = w + v[i - k] * W[IDX(i, c, s)];
+                float t = beta * w;
+                for (int64_t i = k; i < s; ++i) W[IDX(i, c, s)] = W[IDX(i, c, s)] - t * v[i - k];
+            }
+        }
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = 0; i < n; ++i) R[IDX(i, j, n)] = (i <= j) ? (double)W[IDX(i, j, s)] : 0.0;
+        free(W); free(v);
+    }
+    return 0;
+}
+
+/* R_s = R_tilde * 2^(-E): undo the column scaling of the sketch exactly,
+ * after promotion to FP64 (Alg. 1, "Promote R_s to double precision"). */
+void lsqo_unscale_r(double* R, int64_t n, int64_t ldr, const int32_t* colexp)
+{
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i <= j; ++i) R[IDX(i, j, ldr)] = ldexp(R[IDX(i, j, ldr)], -colexp[j]);
+}
+
+/* ------------------------------------------------------------------------
+ * FP64 steps of Alg. 1.
+ * ---------------------------------------------------------------------- */
+
+/* A_p = A R^{-1} (Alg. 1, "Solve A_p = A R_s^{-1}"): for every row a of A,
+ * solve y R = a by forward substitution over the columns of R. */
+int lsqo_trsm_right_upper(const double* A, int64_t m, int64_t n, int64_t lda,
+                          const double* R, int64_t ldr, double* Ap /* ld m */)
+{
+    double* y = (double*)malloc(sizeof(double) * (size_t)n);
+    for (int64_t i = 0; i < m; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            double t = A[IDX(i, j, lda)];
+            for (int64_t k = 0; k < j; ++k) t = t - y[k] * R[IDX(k, j, ldr)];
+            y[j] = t / R[IDX(j, j, ldr)];
+        }
+        for (int64_t j = 0; j < n; ++j) Ap[IDX(i, j, m)] = y[j];
+    }
+    free(y);
+    return 0;
+}
+
+/* C = X^T Y (n-by-n) and c = X^T b, dot products over the m rows in index
+ * order.  PNE: X = Y = A_p (Eq. e_pne).  HPNE: X = A_p, Y = A (Eq. e_hpne). */
+void lsqo_gram(const double* X, const double* Y, int64_t m, int64_t n, int64_t ldx, int64_t ldy,
+               const double* b, double* C /* ld n */, double* c)
+{
+    for (int64_t q = 0; q < n; ++q)
+        for (int64_t p = 0; p < n; ++p) {
+            double acc = 0.0;
+            for (int64_t i = 0; i < m; ++i) acc += X[IDX(i, p, ldx)] * Y[IDX(i, q, ldy)];
+            C[IDX(p, q, n)] = acc;
+        }
+    if (b && c)
+        for (int64_t p = 0; p < n; ++p) {
+            double acc = 0.0;
+            for (int64_t i = 0; i < m; ++i) acc += X[IDX(i, p, ldx)] * b[i];
+            c[p] = acc;
+        }
+}
+
+/* Cholesky G = L L^T (Golub & Van Loan Alg. 4.2.1, column form), lower
+ * triangle of G overwritten by L, strict upper zeroed.  Returns 0, or k > 0
+ * when the k-th pivot (1-based) is not positive or not finite. */
+int lsqo_cholesky(double* G, int64_t n, int64_t ld)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        double d = G[IDX(j, j, ld)];
+        for (int64_t k = 0; k < j; ++k) d = d - G[IDX(j, k, ld)] * G[IDX(j, k, ld)];
+        if (!(d > 0.0) || !isfinite(d)) return (int)(j + 1);
+        double ljj = sqrt(d);
+        G[IDX(j, j, ld)] = ljj;
+        for (int64_t i = j + 1; i < n; ++i) {
+            double t = G[IDX(i, j, ld)];
+            for (int64_t k = 0; k < j; ++k) t = t - G[IDX(i, k, ld)] * G[IDX(j, k, ld)];
+            G[IDX(i, j, ld)] = t / ljj;
+        }
+    }
+    for (int64_t j = 1; j < n; ++j)
+        for (int64_t i = 0; i < j; ++i) G[IDX(i, j, ld)] = 0.0;
+    return 0;
+}
+
+/* LU with partial pivoting, P H = L U (Golub & Van Loan Alg. 3.4.1): at
+ * step k the pivot is the FIRST row i >= k of largest |h_ik|; rows are
+ * swapped in full.  piv[k] = the row swapped with k.  Unit lower L below
+ * the diagonal, U on and above.  Returns 0 or k > 0 for a zero pivot. */
+int lsqo_lu(double* H, int64_t n, int64_t ld, int32_t* piv)
+{
+    int info = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t p = k;
+        double best = fabs(H[IDX(k, k, ld)]);
+        for (int64_t i = k + 1; i < n; ++i) {
+            double v = fabs(H[IDX(i, k, ld)]);
+            if (v > best) { best = v; p = i; }
+        }
+        piv[k] = (int32_t)p;
+        if (p != k)
+            for (int64_t j = 0; j < n; ++j) {
+                double t = H[IDX(k, j, ld)]; H[IDX(k, j, ld)] = H[IDX(p, j, ld)]; H[IDX(p, j, ld)] = t;
+            }
+        double d = H[IDX(k, k, ld)];
+        if (d == 0.0 || !isfinite(d)) { if (!info) info = (int)(k + 1); continue; }
+        for (int64_t i = k + 1; i < n; ++i) H[IDX(i, k, ld)] = H[IDX(i, k, ld)] / d;
+        for (int64_t j = k + 1; j < n; ++j)
+            for (int64_t i = k + 1; i < n; ++i)
+                H[IDX(i, j, ld)] = H[IDX(i, j, ld)] - H[IDX(i, k, ld)] * H[IDX(k, j, ld)];
+    }
+    return info;
+}
+
+/* Triangular solves on a vector, in place.
+ * lower: L y = c (forward), unit diagonal if unit != 0.
+ * lower_t: L^T y = c (backward).
+ * upper: U y = c (backward). */
+void lsqo_solve_lower(const double* L, int64_t n, int64_t ld, int unit, double* y)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double t = y[i];
+        for (int64_t k = 0; k < i; ++k) t = t - L[IDX(i, k, ld)] * y[k];
+        y[i] = unit ? t : t / L[IDX(i, i, ld)];
+    }
+}
+
+void lsqo_solve_lower_t(const double* L, int64_t n, int64_t ld, double* y)
+{
+    for (int64_t i = n - 1; i >= 0; --i) {
+        double t = y[i];
+        for (int64_t k = i + 1; k < n; ++k) t = t - L[IDX(k, i, ld)] * y[k];
+        y[i] = t / L[IDX(i, i, ld)];
+    }
+}
+
+void lsqo_solve_upper(const double* U, int64_t n, int64_t ld, double* y)
+{
+    for (int64_t i = n - 1; i >= 0; --i) {
+        double t = y[i];
+        for (int64_t k = i + 1; k < n; ++k) t = t - U[IDX(i, k, ld)] * y[k];
+        y[i] = t / U[IDX(i, i, ld)];
+    }
+}
+
+/* P H x = L U x = P c: apply the row swaps to c, then the two solves. */
+void lsqo_lu_solve(const double* LU, int64_t n, int64_t ld, const int32_t* piv, double* y)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t p = piv[k];
+        if (p != k) { double t = y[k]; y[k] = y[p]; y[p] = t; }
+    }
+    lsqo_solve_lower(LU, n, ld, 1, y);
+    lsqo_solve_upper(LU, n, ld, y);
+}
+
+/* ------------------------------------------------------------------------
+ * Reference least-squares solution (not the method): Householder QR of A in
+ * FP64 (Golub & Van Loan Alg. 5.2.1 / Sec. 5.3.3), Q^T b by applying the
+ * reflectors, then R x = (Q^T b)(1:n).  Returns 0 or -1.
+ * ---------------------------------------------------------------------- */
+int lsqo_lstsq_qr(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, double* x)
+{
+    if (m < n || n <= 0) return -1;
+    double* W = (double*)malloc(sizeof(double) * (size_t)m * (size_t)n);
+    double* v = (double*)malloc(sizeof(double) * (size_t)m);
+    double* qb = (double*)malloc(sizeof(double) * (size_t)m);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < m; ++i) W[IDX(i, j, m)] = A[IDX(i, j, lda)];
+    for (int64_t i = 0; i < m; ++i) qb[i] = b[i];
+    for (int64_t k = 0; k < n; ++k) {
+        double mu;
+        double beta = house64(&W[IDX(k, k, m)], m - k, v, &mu);
+        W[IDX(k, k, m)] = mu;
+        for (int64_t i = k + 1; i < m; ++i) W[IDX(i, k, m)] = 0.0;
+        for (int64_t c = k + 1; c < n; ++c) {
+            double w = 0.0;
+            for (int64_t i = k; i < m; ++i) w += v[i - k] * W[IDX(i, c, m)];
+            double t = beta * w;
+            for (int64_t i = k; i < m; ++i) W[IDX(i, c, m)] = W[IDX(i, c, m)] - t * v[i - k];
+        }
+        double w = 0.0;
+        for (int64_t i = k; i < m; ++i) w += v[i - k] * qb[i];
+        double t = beta * w;
+        for (int64_t i = k; i < m; ++i) qb[i] = qb[i] - t * v[i - k];
+    }
+    for (int64_t i = 0; i < n; ++i) x[i] = qb[i];
+    lsqo_solve_upper(W, n, m, x);
+    free(W); free(v); free(qb);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Low-precision condition estimate (Sec. 6.1 and Alg. 1, first line).
+ * In FP32: G = fl32(A^T A) with each product rounded then summed in row
+ * order; ||G||_1; Cholesky of G; and Hager's 1-norm estimate of
+ * ||G^{-1}||_1 (Hager 1984, with Higham's 1988 stopping test and
+ * alternating-sign extra vector), at most 5 iterations, each application of
+ * G^{-1} by the two Cholesky solves.  Then, in FP64 from those FP32 values,
+ * kappa0 = 0.5 * log10(n * ||G||_1 * gamma), because
+ * kappa(A)^2 = kappa(A^T A) <= n ||A^T A||_1 ||(A^T A)^{-1}||_1.
+ * A Cholesky breakdown or a non-finite value is the "overflow" case and
+ * returns kappa0 = +inf.  The precision table (reading of Sec. 6.1 extended
+ * to the two 8-bit-class formats):
+ *   kappa0 < 2 FP8, < 3 BF16, < 4 FP16, <= 8 FP32, otherwise FP64.
+ * ---------------------------------------------------------------------- */
+static int chol32(float* G, int64_t n)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        float d = G[IDX(j, j, n)];
+        for (int64_t k = 0; k < j; ++k) d = d - G[IDX(j, k, n)] * G[IDX(j, k, n)];
+        if (!(d > 0.0f) || !isfinite(d)) return (int)(j + 1);
+        float ljj = sqrtf(d);
+        G[IDX(j, j, n)] = ljj;
+        for (int64_t i = j + 1; i < n; ++i) {
+            float t = G[IDX(i, j, n)];
+            for (int64_t k = 0; k < j; ++k) t = t - G[IDX(i, k, n)] * G[IDX(j, k, n)];
+            G[IDX(i, j, n)] = t / ljj;
+        }
+    }
+    return 0;
+}
+
+/* y <- G^{-1} y with G = L L^T, L lower in the FP32 array. */
+static void chol32_solve(const float* L, int64_t n, float* y)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        float t = y[i];
+        for (int64_t k = 0; k < i; ++k) t = t - L[IDX(i, k, n)] * y[k];
+        y[i] = t / L[IDX(i, i, n)];
+    }
+    for (int64_t i = n - 1; i >= 0; --i) {
+        float t = y[i];
+        for (int64_t k = i + 1; k < n; ++k) t = t - L[IDX(k, i, n)] * y[k];
+        y[i] = t / L[IDX(i, i, n)];
+    }
+}
+
+static float norm1_32(const float* y, int64_t n)
+{
+    float s = 0.0f;
+    for (int64_t i = 0; i < n; ++i) s = s + fabsf(y[i]);
+    return s;
+}
+
+int lsqo_precision_from_kappa0(double kappa0)
+{
+    if (!(kappa0 == kappa0) || isinf(kappa0)) return O_FP64;
+    if (kappa0 < 2.0) return O_FP8;
+    if (kappa0 < 3.0) return O_BF16;
+    if (kappa0 < 4.0) return O_FP16;
+    if (kappa0 <= 8.0) return O_FP32;
+    return O_FP64;
+}
+
+/* Hager/Higham estimate of ||G^{-1}||_1 using the FP32 Cholesky factor L.
+ * G^{-1} is symmetric, so the transpose products reuse the same solve. */
+static float hager_inv_norm1(const float* L, int64_t n, int maxit)
+{
+    float* x = (float*)malloc(sizeof(float) * (size_t)n);
+    float* y = (float*)malloc(sizeof(float) * (size_t)n);
+    float* xi = (float*)malloc(sizeof(float) * (size_t)n);
+    float* z = (float*)malloc(sizeof(float) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) x[i] = 1.0f / (float)n;
+    for (int64_t i = 0; i < n; ++i) y[i] = x[i];
+    chol32_solve(L, n, y);
+    float est = norm1_32(y, n);
+    for (int64_t i = 0; i < n; ++i) xi[i] = (y[i] >= 0.0f) ? 1.0f : -1.0f;
+    for (int64_t i = 0; i < n; ++i) z[i] = xi[i];
+    chol32_solve(L, n, z);
+    int64_t jlast = -1;
+    for (int it = 1; it < maxit; ++it) {
+        /* j = first index of max |z_i|; stop when ||z||_inf <= z^T x. */
+        int64_t j = 0;
+        float zmax = fabsf(z[0]);
+        for (int64_t i = 1; i < n; ++i) if (fabsf(z[i]) > zmax) { zmax = fabsf(z[i]); j = i; }
+        float ztx = 0.0f;
+        for (int64_t i = 0; i < n; ++i) ztx = ztx + z[i] * x[i];
+        if (zmax <= ztx || j == jlast) break;
+        jlast = j;
+        for (int64_t i = 0; i < n; ++i) x[i] = 0.0f;
+        x[j] = 1.0f;
+        for (int64_t i = 0; i < n; ++i) y[i] = x[i];
+        chol32_solve(L, n, y);
+        float est_new = norm1_32(y, n);
+        int same = 1;
+        for (int64_t i = 0; i < n; ++i) same &= (((y[i] >= 0.0f) ? 1.0f : -1.0f) == xi[i]);
+        if (same || est_new <= est) { if (est_new > est) est = est_new; break; }
+        est = est_new;
+        for (int64_t i = 0; i < n; ++i) xi[i] = (y[i] >= 0.0f) ? 1.0f : -1.0f;
+        for (int64_t i = 0; i < n; ++i) z[i] = xi[i];
+        chol32_solve(L, n, z);
+    }
+    /* Higham's extra vector x_i = (-1)^i (1 + i/(n-1)), estimate 2||y||_1/(3n). */
+    for (int64_t i = 0; i < n; ++i) {
+        float mag = (n > 1) ? 1.0f + (float)i / (float)(n - 1) : 1.0f;
+        y[i] = (i % 2 == 0) ? mag : -mag;
+    }
+    chol32_solve(L, n, y);
+    float alt = 2.0f * norm1_32(y, n) / (3.0f * (float)n);
+    if (alt > est) est = alt;
+    free(x); free(y); free(xi); free(z);
+    return est;
+}
+
+int lsqo_condest(const double* A, int64_t m, int64_t n, int64_t lda,
+                 double* kappa0, int32_t* chosen, double* norm1_out, double* gamma_out)
+{
+    float* G = (float*)malloc(sizeof(float) * (size_t)n * (size_t)n);
+    for (int64_t q = 0; q < n; ++q)
+        for (int64_t p = q; p < n; ++p) {
+            float acc = 0.0f;
+            for (int64_t i = 0; i < m; ++i) {
+                float prod = (float)A[IDX(i, p, lda)] * (float)A[IDX(i, q, lda)];
+                acc = acc + prod;
+            }
+            G[IDX(p, q, n)] = acc;
+            G[IDX(q, p, n)] = acc;
+        }
+    float nrm = 0.0f;
+    for (int64_t q = 0; q < n; ++q) {
+        float cs = 0.0f;
+        for (int64_t p = 0; p < n; ++p) cs = cs + fabsf(G[IDX(p, q, n)]);
+        if (cs > nrm) nrm = cs;
+    }
+    double k0;
+    float gam = 0.0f;
+    int info = chol32(G, n);
+    if (info != 0 || !isfinite(nrm)) {
+        k0 = INFINITY;
+    } else {
+        gam = hager_inv_norm1(G, n, 5);
+        double prod = (double)n * (double)nrm * (double)gam;
+        k0 = (isfinite(prod) && prod > 0.0) ? 0.5 * log10(prod) : INFINITY;
+    }
+    if (kappa0) *kappa0 = k0;
+    if (chosen) *chosen = lsqo_precision_from_kappa0(k0);
+    if (norm1_out) *norm1_out = (double)nrm;
+    if (gamma_out) *gamma_out = (double)gam;
+    free(G);
+    return info;
+}
+
+/* ------------------------------------------------------------------------
+ * Alg. 1 end to end: PNE (Eq. e_pne) or HPNE (Eq. e_hpne) with a randomized
+ * preconditioner computed in precision u_p, then optionally one FP64
+ * residual-refinement step (not part of the paper's algorithm):
+ *   r = b - A x;  g = A_p^T r;
+ *   PNE:  (A_p^T A_p) z = g, delta = R_s^{-1} z;   HPNE: (A_p^T A) delta = g;
+ *   x = x + delta.
+ * Returns 0, k > 0 for a factorization breakdown at pivot k, -1 for bad
+ * arguments.  Rs_out (n-by-n, may be NULL) receives R_s; kappa0_out and
+ * prec_out (may be NULL) the estimate and the precision used.
+ * ---------------------------------------------------------------------- */
+int lsqo_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+               int hpne, int kind, int64_t s, int zeta, uint64_t seed,
+               int sketch_prec, int qr_prec, int refine_steps,
+               double* x, double* Rs_out, double* kappa0_out, int32_t* prec_out)
+{
+    if (m <= 0 || n <= 0 || s < n || m < s) return -1;
+    double k0 = NAN;
+    int prec = sketch_prec;
+    if (prec == O_AUTO) {
+        int32_t ch;
+        lsqo_condest(A, m, n, lda, &k0, &ch, NULL, NULL);
+        prec = ch;
+    }
+    if (prec < O_FP8 || prec > O_FP64) return -1;
+    int qp = (prec == O_FP64) ? O_FP64 : qr_prec;
+    if (qp != O_FP32 && qp != O_FP64) qp = O_FP32;
+    if (kappa0_out) *kappa0_out = k0;
+    if (prec_out) *prec_out = prec;
+
+    size_t mn = (size_t)m * (size_t)n, nn = (size_t)n * (size_t)n;
+    double* As = (double*)malloc(sizeof(double) * (size_t)s * (size_t)n);
+    int32_t* ce = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    double* R = (double*)malloc(sizeof(double) * nn);
+    double* Ap = (double*)malloc(sizeof(double) * mn);
+    double* G = (double*)malloc(sizeof(double) * nn);
+    double* c = (double*)malloc(sizeof(double) * (size_t)n);
+    double* r = (double*)malloc(sizeof(double) * (size_t)m);
+    int32_t* piv = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int rc = lsqo_sketch(A, m, n, lda, kind, s, zeta, seed, prec, As, ce);
+    if (!rc) rc = lsqo_qr_r(As, s, n, s, qp, R);
+    int info = 0;
+    if (!rc) {
+        lsqo_unscale_r(R, n, n, ce);
+        if (Rs_out) memcpy(Rs_out, R, sizeof(double) * nn);
+        lsqo_trsm_right_upper(A, m, n, lda, R, n, Ap);
+        if (hpne) lsqo_gram(Ap, A, m, n, m, lda, b, G, c);
+        else      lsqo_gram(Ap, Ap, m, n, m, m, b, G, c);
+        info = hpne ? lsqo_lu(G, n, n, piv) : lsqo_cholesky(G, n, n);
+        if (!info) {
+            for (int64_t i = 0; i < n; ++i) x[i] = c[i];
+            if (hpne) {
+                lsqo_lu_solve(G, n, n, piv, x);
+            } else {
+                lsqo_solve_lower(G, n, n, 0, x);
+                lsqo_solve_lower_t(G, n, n, x);
+                lsqo_solve_upper(R, n, n, x);
+            }
+            for (int step = 0; step < refine_steps; ++step) {
+                for (int64_t i = 0; i < m; ++i) {
+                    double t = b[i];
+                    for (int64_t j = 0; j < n; ++j) t = t - A[IDX(i, j, lda)] * x[j];
+                    r[i] = t;
+                }
+                for (int64_t p = 0; p < n; ++p) {
+                    double acc = 0.0;
+                    for (int64_t i = 0; i < m; ++i) acc += Ap[IDX(i, p, m)] * r[i];
+                    c[p] = acc;
+                }
+                if (hpne) {
+                    lsqo_lu_solve(G, n, n, piv, c);
+                } else {
+                    lsqo_solve_lower(G, n, n, 0, c);
+                    lsqo_solve_lower_t(G, n, n, c);
+                    lsqo_solve_upper(R, n, n, c);
+                }
+                for (int64_t j = 0; j < n; ++j) x[j] = x[j] + c[j];
+            }
+        }
+    }
+    free(As); free(ce); free(R); free(Ap); free(G); free(c); free(r); free(piv);
+    return rc ? -1 : info;
+}
