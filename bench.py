@@ -1,0 +1,365 @@
+"""Throughput benchmark: least-squares solves per second of the mixed-precision
+randomized-preconditioned normal equations (Alg. 1 of Garrison & Ipsen,
+arXiv 2603.16644; PNE Eq. e_pne) on one GB300, next to this library's
+all-FP64 PNE and HPNE on the same inputs.
+
+Workload (tall-skinny): A is 65536 x 1024 FP64, A = U diag(sigma) V^T with
+kappa in {1e2, 1e6, 1e10} and relative residual in {0, 1e-8, 1e-3} (9 seeded
+synthetic problems resident in HBM, solved in turn); sparse-sign sketch with
+s = 4n rows and 8 nonzeros per column, BF16 sketch, FP32 QR, FP64 TRSM /
+Gram / Cholesky / solves, one FP64 refinement step.  Every A (512 MiB) is
+larger than L2, so no flush is needed between steps.
+
+One JSON line on rank 0.  --impl reference times the CPU oracle instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+M, N, S, ZETA = 65536, 1024, 4096, 8
+KAPPAS = [1e2, 1e6, 1e10]
+RHOS = [0.0, 1e-8, 1e-3]
+WORKLOAD = "tall_skinny_65536x1024_sparse_sign_s4096_z8_bf16_fp32qr_refine1"
+METRIC = "LS solves/s (mixed-precision PNE, 65536x1024)"
+FP64_PEAK_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA cores), nominal dense rate
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=18)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--fp64-steps", type=int, default=6, help="steps of the all-FP64 PNE comparison")
+    p.add_argument("--hpne-steps", type=int, default=6)
+    p.add_argument("--e2e-steps", type=int, default=6)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-rows", type=int, default=4096, help="rows of the oracle sample")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, pw, reasons = [], None, [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+                pw.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "samples": len(sm),
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- inputs
+def make_inputs(dev):
+    import torch
+
+    import problems as P
+
+    probs = []
+    for i, kap in enumerate(KAPPAS):
+        for j, rho in enumerate(RHOS):
+            A, b, x_star, sigma, V = P.make_problem_torch(M, N, kap, rho, P.seed_for(1, 3 * i + j), device=dev)
+            probs.append({"A": A, "b": b, "x_star": x_star, "kappa": kap, "rho": rho, "seed": P.seed_for(1, 3 * i + j)})
+            del sigma, V
+    torch.cuda.synchronize()
+    return probs
+
+
+def opts_for(lsq, prec, seed):
+    qr = lsq.FP64 if prec == lsq.FP64 else lsq.FP32
+    return lsq.make_opts(kind=lsq.SPARSE_SIGN, s=S, zeta=ZETA, seed=seed, sketch_prec=prec, qr_prec=qr,
+                         refine_steps=1)
+
+
+def run_steps(lsq, probs, steps, prec, hpne, ws, xs, infos, start=0):
+    for k in range(steps):
+        p = probs[(start + k) % len(probs)]
+        lsq.solve(p["A"], p["b"], hpne=hpne, opts=opts_for(lsq, prec, p["seed"]), ws=ws, x=xs[(start + k) % len(probs)],
+                  info=infos[(start + k) % len(probs)])
+
+
+def timed(lsq, torch, probs, steps, warmup, prec, hpne, ws, xs, infos, dist=None):
+    run_steps(lsq, probs, warmup, prec, hpne, ws, xs, infos)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    run_steps(lsq, probs, steps, prec, hpne, ws, xs, infos, start=warmup)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    return e0.elapsed_time(e1) / 1000.0
+
+
+def probe_fp64(lsq, torch):
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks = sms * 8
+    scratch = torch.zeros(blocks, dtype=torch.float64, device="cuda")
+    iters = 4096
+    lsq.probe_fp64_fma(iters, blocks, scratch)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    lsq.probe_fp64_fma(iters, blocks, scratch)
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1000.0
+    return blocks * 256 * iters * 16 / sec / 1e12
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(rows):
+    """The oracle's Alg. 1 (PNE, same n, s, zeta and precisions, one refinement
+    step) on a `rows`-row slice of the workload shape, timed as it stands.
+    The steps whose cost is independent of m (QR of the s x n sketch,
+    Cholesky, solves) are timed once more on their own; the rest is
+    proportional to m and is scaled to the full 65536 rows.  Returns
+    (seconds for one full solve, raw CPU seconds spent)."""
+    import oracle as O
+
+    rng = np.random.default_rng(2603)
+    A = np.asfortranarray(rng.standard_normal((rows, N)))
+    b = rng.standard_normal(rows)
+    t0 = time.perf_counter()
+    O.solve(A, b, kind=O.SPARSE_SIGN, s=S, zeta=ZETA, seed=1, sketch_prec=O.BF16, qr_prec=O.FP32, refine_steps=1)
+    t_total = time.perf_counter() - t0
+    As, e = O.sketch(A, O.SPARSE_SIGN, S, ZETA, 1, O.BF16)
+    X = rng.standard_normal((2 * N, N))
+    G = X.T @ X
+    t0 = time.perf_counter()
+    O.qr_r(As, O.FP32)
+    L, _ = O.cholesky(G)
+    O.solve_lower_t(L, O.solve_lower(L, np.ones(N)))
+    t_fixed = time.perf_counter() - t0
+    full = max(t_total - t_fixed, 0.0) * (M / rows) + t_fixed
+    return full, t_total + t_fixed
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    steps_t = []
+    for _ in range(args.warmup):
+        oracle_sample(args.cpu_rows)
+    for _ in range(args.steps):
+        full, raw = oracle_sample(args.cpu_rows)
+        steps_t.append(full)
+    sec = sum(steps_t)
+    value = args.steps / sec
+    sample = (f"oracle PNE (Alg. 1, refine 1) on a {args.cpu_rows}x{N} slice (s={S}, zeta={ZETA}, BF16 sketch, "
+              f"FP32 QR); m-proportional part scaled by {M // args.cpu_rows}, QR/Cholesky/solves once")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "m": M, "n": N, "s": S},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    import paper_2603_16644_gb300 as lsq
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    probs = make_inputs(dev)
+    ws_size = max(lsq.workspace_size(lsq.OP_PNE, M, N, opts_for(lsq, p, 0)) for p in (lsq.BF16, lsq.FP64))
+    ws_size = max(ws_size, lsq.workspace_size(lsq.OP_HPNE, M, N, opts_for(lsq, lsq.BF16, 0)))
+    ws = torch.empty(ws_size, dtype=torch.uint8, device=dev)
+    xs = [torch.empty(N, dtype=torch.float64, device=dev) for _ in probs]
+    infos = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in probs]
+
+    # ---- headline: mixed-precision PNE
+    clocks = ClockSampler(local)
+    run_steps(lsq, probs, args.warmup, lsq.BF16, False, ws, xs, infos)
+    torch.cuda.synchronize()
+    lsq.profile(True)
+    n_launch0 = lsq.launch_count()
+    clocks.start()
+    sec = timed(lsq, torch, probs, args.steps, 0, lsq.BF16, False, ws, xs, infos, dist)
+    clk = clocks.stop()
+    n_launch = lsq.launch_count() - n_launch0
+    stages = lsq.profile_collect()
+    lsq.profile(False)
+    if dist is not None:
+        t = torch.tensor([sec], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec = float(t.item())
+    value = world * args.steps / sec
+
+    # accuracy of the timed solves (not timed)
+    errs = {}
+    for k, p in enumerate(probs):
+        x = xs[k].cpu().numpy()
+        errs[f"k{p['kappa']:.0e}_r{p['rho']:.0e}"] = {
+            "rel_err_vs_xstar": float(np.linalg.norm(x - p["x_star"].cpu().numpy()) / np.linalg.norm(x)),
+            "info": int(infos[k].item())}
+
+    # ---- comparisons: all-FP64 PNE and mixed HPNE, same inputs
+    sec64 = timed(lsq, torch, probs, args.fp64_steps, 1, lsq.FP64, False, ws, xs, infos, dist)
+    touched = sorted({k % len(probs) for k in range(1 + args.fp64_steps)})
+    err64 = {f"k{probs[k]['kappa']:.0e}_r{probs[k]['rho']:.0e}": float(
+        np.linalg.norm(xs[k].cpu().numpy() - probs[k]["x_star"].cpu().numpy()) / np.linalg.norm(xs[k].cpu().numpy()))
+        for k in touched}
+    sech = timed(lsq, torch, probs, args.hpne_steps, 1, lsq.BF16, True, ws, xs, infos, dist)
+
+    # ---- end to end through the C ABI on host buffers
+    Ah = [p["A"].t().contiguous().cpu().pin_memory() for p in probs[:3]]
+    bh = [p["b"].cpu().pin_memory() for p in probs[:3]]
+    wsh = torch.empty(lsq.workspace_size(lsq.OP_PNE_HOST, M, N, opts_for(lsq, lsq.BF16, 0)), dtype=torch.uint8,
+                      device=dev)
+    xh = torch.empty(N, dtype=torch.float64).pin_memory()
+    for k in range(2):
+        lsq.solve_host(Ah[k % 3].t(), bh[k % 3], opts=opts_for(lsq, lsq.BF16, probs[k % 3]["seed"]), ws=wsh, x_host=xh)
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(args.e2e_steps):
+        lsq.solve_host(Ah[k % 3].t(), bh[k % 3], opts=opts_for(lsq, lsq.BF16, probs[k % 3]["seed"]), ws=wsh,
+                       x_host=xh)
+    e2e_sec = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_sec], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_sec = float(t.item())
+    e2e_value = world * args.e2e_steps / e2e_sec
+
+    # ---- roofline of the dominant kernel (FP64, CUDA cores)
+    fp64_probe = probe_fp64(lsq, torch)
+    trsm_ms = stages["trsm"][0] / max(1, stages["trsm"][1])
+    gram_ms = stages["gram"][0] / max(1, stages["gram"][1])
+    dom = "trsm" if trsm_ms >= gram_ms else "gram"
+    dom_ms = max(trsm_ms, gram_ms)
+    flops = float(M) * N * N  # TRSM: m n^2; symmetric Gram: m n^2 (+ 2mn for A_p^T b)
+    if dom == "gram":
+        flops += 2.0 * M * N
+    achieved = flops / (dom_ms / 1000.0) / 1e12
+    peak = FP64_PEAK_NOMINAL_TFLOPS
+    roofline = {"bound": "alu", "kernel": "k_trsm_right_upper" if dom == "trsm" else "k_gemm_kmajor<f64> (SYRK)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (CUDA cores; no FP64 entry in the measured peaks)",
+                "fp64_fma_probe_tflops": fp64_probe, "frac_of_probe": achieved / fp64_probe}
+
+    result = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            full, raw = oracle_sample(args.cpu_rows)
+            cpu = {"value": 1.0 / full, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                   "sample": (f"oracle PNE steps on a {args.cpu_rows}x{N} slice (same s, zeta, precisions), "
+                              f"{raw:.1f} s of CPU work; row-proportional steps scaled by {M // args.cpu_rows}, "
+                              f"QR/Cholesky/solves counted once")}
+        per_stage = {k: round(v[0] / max(1, v[1]), 3) for k, v in stages.items() if v[1]}
+        result = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * sec / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded A = U diag(sigma) V^T, known x_*)",
+            "config": {"workload": WORKLOAD, "m": M, "n": N, "s": S, "zeta": ZETA, "sketch": "sparse_sign",
+                       "sketch_prec": "bf16", "qr_prec": "fp32", "refine_steps": 1, "kappas": KAPPAS, "rhos": RHOS,
+                       "l2": "inputs larger than L2 (512 MiB A per step, 9 problems in turn)"},
+            "clocks": clk, "gpu_launches": n_launch,
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * M * N + 8 * M,
+                    "d2h_bytes_per_step": 8 * N + 4},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "stage_ms_per_solve": per_stage,
+            "fp64_pne": {"value": world * args.fp64_steps / sec64, "unit": "solves/s",
+                         "speedup_mixed_over_fp64": value / (world * args.fp64_steps / sec64),
+                         "rel_err_vs_xstar": err64},
+            "hpne": {"value": world * args.hpne_steps / sech, "unit": "solves/s"},
+            "accuracy": errs,
+        }
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,246 @@
+/*
+ * liblsq — randomized-preconditioned normal equations on NVIDIA GB300.
+ *
+ * The method is that of Garrison & Ipsen, "Perturbation Analysis for
+ * Preconditioned Normal Equations in Mixed Precision" (arXiv 2603.16644):
+ * for A (m x n, rank n) and b, Alg. 1
+ *   1. estimates kappa0 ~ log10 kappa(A) in single precision (Sec. 6.1) and
+ *      picks the preconditioner precision u_p;
+ *   2. sketches A_s = Omega A in u_p and takes the thin QR A_s = Q_s R_s;
+ *   3. promotes R_s to FP64 and forms A_p = A R_s^{-1} in FP64;
+ *   4. solves PNE  (A_p^T A_p y = A_p^T b, R_s x = y;   Eq. e_pne)  or
+ *             HPNE (A_p^T A x = A_p^T b;                 Eq. e_hpne).
+ * This library adds, as options: Gaussian and sparse-sign sketches (the
+ * paper uses a subsampled Fourier transform, Eq. e_sketch), FP8-e4m3 and
+ * BF16 sketch precisions with per-column power-of-two scaling, and one FP64
+ * residual-refinement step.
+ *
+ * Conventions for every call
+ *   - Matrices are column-major FP64: entry (i, j) at A[i + j*lda], lda >= m.
+ *   - Pointers are DEVICE pointers unless the name ends in _host.  The caller
+ *     owns every buffer; inputs (const) are never modified.  The library
+ *     never allocates device memory: scratch comes from the caller's
+ *     workspace `ws` of at least lsq_workspace_size(...) bytes (256-byte
+ *     aligned base recommended; the library aligns internally).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All work is
+ *     enqueued asynchronously on it, except where a call documents a
+ *     host synchronisation.
+ *   - Errors: the return value reports argument and launch errors.
+ *     Conditions found on the device are written to the device int32 `info`
+ *     (LAPACK style): 0 success, k > 0 breakdown (non-positive Cholesky
+ *     pivot or zero LU pivot) at the k-th pivot, -1 non-finite value,
+ *     -2 timeout.  Nothing throws across this interface.
+ *   - Precondition: rank(A) = n and n <= s <= m (Sec. 1).  Rank deficiency
+ *     shows up as a breakdown in info, not as undefined behaviour.
+ */
+#ifndef LSQ_H_
+#define LSQ_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LSQ_OK = 0,
+    LSQ_ERR_ARG = 1,        /* invalid argument (sizes, precision, null pointer) */
+    LSQ_ERR_BREAKDOWN = 2,  /* reserved for synchronous callers: see info */
+    LSQ_ERR_NONFINITE = 3,
+    LSQ_ERR_TIMEOUT = 4,
+    LSQ_ERR_CUDA = 5,       /* a CUDA launch or copy failed */
+    LSQ_ERR_NOMEM = 6       /* workspace smaller than lsq_workspace_size() */
+} lsq_status;
+
+/* Precisions.  For the sketch, u_p of Alg. 1; AUTO runs the condition
+ * estimate (lsq_condest) and applies the precision table below. */
+typedef enum {
+    LSQ_FP8_E4M3 = 0,  /* OCP FP8 e4m3 ("fn": no infinities, saturating) */
+    LSQ_BF16 = 1,
+    LSQ_FP16 = 2,      /* the paper's "half precision" */
+    LSQ_FP32 = 3,      /* "single precision" */
+    LSQ_FP64 = 4,      /* "double precision" */
+    LSQ_AUTO = 5
+} lsq_prec;
+
+typedef enum {
+    LSQ_GAUSSIAN = 0,     /* Omega_ij ~ N(0, 1), unscaled */
+    LSQ_SPARSE_SIGN = 1   /* zeta distinct +-1 entries per column of Omega */
+} lsq_sketch_kind;
+
+typedef enum {
+    LSQ_OP_SKETCH = 0,
+    LSQ_OP_PRECOND_QR = 1,
+    LSQ_OP_CONDEST = 2,
+    LSQ_OP_PNE = 3,
+    LSQ_OP_HPNE = 4,
+    LSQ_OP_TRSM_GRAM = 5,
+    LSQ_OP_FACTOR_SOLVE = 6,
+    LSQ_OP_PNE_HOST = 7,
+    LSQ_OP_HPNE_HOST = 8
+} lsq_op;
+
+/* Solver options (fixed-width fields; zero-initialise unused ones).
+ *   kind          lsq_sketch_kind
+ *   zeta          nonzeros per column of a sparse-sign Omega (1..32, <= s)
+ *   s             sketch rows d of Omega (n <= s <= m; the paper uses 3n)
+ *   seed          key of the Philox4x32-10 stream that draws Omega
+ *   sketch_prec   u_p for the sketch (lsq_prec, AUTO allowed)
+ *   qr_prec       arithmetic of the sketch QR: LSQ_FP32 or LSQ_FP64; forced
+ *                 to FP64 when the sketch precision is FP64
+ *   refine_steps  0 or 1 FP64 refinement steps (not in the paper)      */
+typedef struct {
+    int32_t kind;
+    int32_t zeta;
+    int64_t s;
+    uint64_t seed;
+    int32_t sketch_prec;
+    int32_t qr_prec;
+    int32_t refine_steps;
+    int32_t reserved;
+} lsq_opts;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int32_t lsq_version(void);
+
+/* Human-readable status name; static storage. */
+const char* lsq_status_string(int32_t status);
+
+/* Bytes of workspace the operation `op` (lsq_op) needs for an m x n problem
+ * with the given options (opts may be NULL for ops that take none).
+ * Returns 0 for invalid arguments. */
+size_t lsq_workspace_size(int32_t op, int64_t m, int64_t n, const lsq_opts* opts);
+
+/* Precision chosen by the table of Sec. 6.1 for an estimate kappa0
+ * (reading extended to the 8-bit formats): kappa0 < 2 FP8-e4m3, < 3 BF16,
+ * < 4 FP16 (the paper's half), <= 8 FP32, otherwise or non-finite FP64. */
+int32_t lsq_precision_from_kappa0(double kappa0);
+
+/* Sketch operator, for inspection and tests (Alg. 1 input Omega).
+ * Sparse sign: idx[j*zeta + t] (int32, row of the t-th nonzero of column j,
+ * distinct within a column, in draw order) and sgn[j*zeta + t] (+1/-1) for
+ * j < m.  Draw rule: Philox4x32-10 with key = seed and counter
+ * (k, j_lo, j_hi, 0), words in order, Lemire multiply-shift with rejection,
+ * duplicates rejected; sign of the t-th row = bit t of word 0 of counter
+ * (0, j_lo, j_hi, 1), set = -1. */
+lsq_status lsq_sparse_sign_operator(uint64_t seed, int64_t m, int64_t s, int32_t zeta,
+                                    int32_t* idx, int8_t* sgn, void* stream);
+
+/* Gaussian operator rounded to `prec`, returned as FP64 values in Om
+ * (s x m column-major, ld s).  Entry (i, j): counter (i, j_lo, j_hi, 2),
+ * u1 = (53-bit integer + 1) 2^-53 from words 0-1, u2 = 53-bit integer 2^-53
+ * from words 2-3, z = sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller). */
+lsq_status lsq_gaussian_operator(uint64_t seed, int64_t s, int64_t m, int32_t prec,
+                                 double* Om, void* stream);
+
+/* Sketch A_s = Omega (A 2^E) in precision opts->sketch_prec (Alg. 1,
+ * "Sketch A_s = Omega A" in u_p).  Column j of A is scaled by 2^colexp[j]
+ * before rounding to u_p so that its largest magnitude lies in
+ * [2^(t-1), 2^t), t = 8 (FP8), 15 (FP16), 0 (BF16, FP32); FP64 is unscaled.
+ * Products accumulate in FP32 (FP64 when u_p = FP64).  As (s x n,
+ * column-major, ld ldas >= s) is float* for FP8/BF16/FP16/FP32 and double*
+ * for FP64.  colexp: n int32 (device).  Sparse-sign sums run in ascending
+ * column index of Omega.  AUTO is not accepted here.  info (device int32,
+ * may be NULL) receives -3 if a row of a sparse-sign Omega holds more
+ * nonzeros than the deterministic row sort supports, -2 if the index draw
+ * did not terminate. */
+lsq_status lsq_sketch(const double* A, int64_t m, int64_t n, int64_t lda, const lsq_opts* opts,
+                      void* As, int64_t ldas, int32_t* colexp, int32_t* info, void* ws,
+                      size_t ws_bytes, void* stream);
+
+/* Preconditioner (Alg. 1, "Thin QR factorization A_s = Q_s R_s", then
+ * "Promote R_s"): Householder QR of A_s (s x n; float* if as_prec = LSQ_FP32,
+ * double* if LSQ_FP64) in qr_prec arithmetic (FP32 or FP64), R with positive
+ * diagonal, promoted to FP64 and unscaled, R_s[:, j] = R[:, j] 2^-colexp[j]
+ * (colexp may be NULL = no scaling).  Rs: n x n FP64, ld ldr >= n; only the
+ * upper triangle is written.  info: device int32. */
+lsq_status lsq_precond_qr(const void* As, int64_t s, int64_t n, int64_t ldas, int32_t as_prec,
+                          int32_t qr_prec, const int32_t* colexp, double* Rs, int64_t ldr,
+                          int32_t* info, void* ws, size_t ws_bytes, void* stream);
+
+/* Low-precision condition estimate (Sec. 6.1; Alg. 1 first line): in FP32,
+ * G = A^T A, ||G||_1, Cholesky of G and Hager's estimate gamma of
+ * ||G^{-1}||_1 (at most 5 iterations, Higham's extra vector), then
+ * kappa0 = 0.5 log10(n ||G||_1 gamma) in FP64; a breakdown or non-finite
+ * value gives kappa0 = +inf.  kappa0 (double) and chosen (int32, lsq_prec by
+ * lsq_precision_from_kappa0) are device pointers. */
+lsq_status lsq_condest(const double* A, int64_t m, int64_t n, int64_t lda, double* kappa0,
+                       int32_t* chosen, void* ws, size_t ws_bytes, void* stream);
+
+/* FP64 preconditioning and Gram formation (Alg. 1, "Solve A_p = A R_s^{-1}",
+ * and the left-hand sides of Eqs. e_pne / e_hpne):
+ *   Ap = A Rs^{-1} (m x n, ld ldap >= m; forward substitution by blocks);
+ *   hpne = 0: G = Ap^T Ap (full symmetric n x n written);
+ *   hpne = 1: G = Ap^T A;
+ *   c = Ap^T b (n).   G: ld ldg >= n. */
+lsq_status lsq_trsm_gram(const double* A, int64_t m, int64_t n, int64_t lda, const double* Rs,
+                         int64_t ldr, const double* b, int32_t hpne, double* Ap, int64_t ldap,
+                         double* G, int64_t ldg, double* c, void* ws, size_t ws_bytes,
+                         void* stream);
+
+/* Factor and solve (Eqs. e_pne / e_hpne, right-hand parts), in FP64:
+ *   hpne = 0: Cholesky G = L L^T, L L^T y = c, then Rs x = y (Rs may be
+ *             NULL: x = y);
+ *   hpne = 1: LU with partial pivoting (first largest pivot) P G = L U,
+ *             L U x = P c.
+ * G is overwritten by the factors (lower L for Cholesky; L\U for LU).
+ * piv: n int32 (device, may be NULL for hpne = 0).  info: device int32. */
+lsq_status lsq_factor_solve(int32_t hpne, double* G, int64_t n, int64_t ldg, const double* c,
+                            const double* Rs, int64_t ldr, double* x, int32_t* piv, int32_t* info,
+                            void* ws, size_t ws_bytes, void* stream);
+
+/* Whole method (Alg. 1) with PNE (Eq. e_pne): x (n), Rs_out (n x n, ld n;
+ * may be NULL), info (device int32), optional one-step FP64 refinement
+ *   r = b - A x, g = A_p^T r, (A_p^T A_p) z = g, x += R_s^{-1} z.
+ * With sketch_prec = AUTO the call runs lsq_condest and reads the chosen
+ * precision back to the host (one stream synchronisation); the workspace is
+ * then sized for the widest case (as for FP64). */
+lsq_status lsq_pne_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                         const lsq_opts* opts, double* x, double* Rs_out, int32_t* info,
+                         void* ws, size_t ws_bytes, void* stream);
+
+/* Same with HPNE (Eq. e_hpne): A_p^T A x = A_p^T b by LU with partial
+ * pivoting; refinement r = b - A x, (A_p^T A) d = A_p^T r, x += d. */
+lsq_status lsq_hpne_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                          const lsq_opts* opts, double* x, double* Rs_out, int32_t* info,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* End-to-end variants on HOST buffers (pinned memory recommended): copy
+ * A_host (ld lda) and b_host into the workspace, solve, copy x back to
+ * x_host and info back to info_host; returns after a stream synchronisation.
+ * Workspace: lsq_workspace_size(LSQ_OP_PNE_HOST / LSQ_OP_HPNE_HOST, ...). */
+lsq_status lsq_pne_solve_host(const double* A_host, int64_t m, int64_t n, int64_t lda,
+                              const double* b_host, const lsq_opts* opts, double* x_host,
+                              int32_t* info_host, void* ws, size_t ws_bytes, void* stream);
+lsq_status lsq_hpne_solve_host(const double* A_host, int64_t m, int64_t n, int64_t lda,
+                               const double* b_host, const lsq_opts* opts, double* x_host,
+                               int32_t* info_host, void* ws, size_t ws_bytes, void* stream);
+
+/* ---- Instrumentation (no counterpart in the paper) --------------------- */
+
+/* Number of kernel launches this library has issued since it was loaded. */
+int64_t lsq_launch_count(void);
+
+/* Stage timing.  lsq_profile(1) clears the records and starts recording a
+ * CUDA event pair around each step of Alg. 1 inside the solve calls (stage
+ * indices: 0 condition estimate, 1 sketch, 2 QR, 3 TRSM A R_s^{-1},
+ * 4 Gram + right-hand side, 5 factorization, 6 solves, 7 refinement);
+ * lsq_profile(0) stops.  lsq_profile_collect waits for the recorded events,
+ * writes the summed milliseconds and the number of records per stage
+ * (arrays of at least 8), and clears the records.  Host-side state, not
+ * thread safe across concurrent solves on different streams. */
+int32_t lsq_profile(int32_t enable);
+int32_t lsq_profile_collect(double* ms_by_stage, int32_t* count_by_stage, int32_t nstages);
+
+/* FP64 FMA throughput probe: `blocks` CTAs of 256 threads, each thread
+ * 8 independent FMA chains of `iters` steps (16 * iters flops per thread).
+ * scratch: device double[blocks], written only to keep the chains live.
+ * The caller times the launch to obtain the device's FP64 FMA rate. */
+int32_t lsq_probe_fp64_fma(int64_t iters, int32_t blocks, double* scratch, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSQ_H_ */

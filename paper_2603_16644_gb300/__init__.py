@@ -1,0 +1,302 @@
+"""Python binding of liblsq: randomized-preconditioned normal equations on
+GB300 (Garrison & Ipsen, arXiv 2603.16644, Alg. 1; PNE Eq. e_pne, HPNE
+Eq. e_hpne).
+
+Argument marshalling only: every step of the method runs in the CUDA
+kernels of ``liblsq.so`` behind the C ABI of ``include/lsq.h``.  PyTorch
+supplies device memory and the current stream.  There is no CPU fallback:
+importing works without a GPU, but every call needs CUDA tensors and the
+built library, and raises otherwise.
+
+Matrices are column-major FP64: an (m, n) tensor with stride (1, lda), lda >= m,
+e.g. ``colmajor(A)``.
+"""
+import ctypes as C
+import os
+
+import torch
+
+__all__ = [
+    "FP8_E4M3", "BF16", "FP16", "FP32", "FP64", "AUTO", "GAUSSIAN", "SPARSE_SIGN",
+    "Opts", "lib", "colmajor", "workspace", "sketch", "precond_qr", "condest", "trsm_gram",
+    "factor_solve", "pne", "hpne", "solve", "solve_host", "sparse_sign_operator",
+    "gaussian_operator", "precision_from_kappa0", "status_string", "LsqError",
+]
+
+FP8_E4M3, BF16, FP16, FP32, FP64, AUTO = 0, 1, 2, 3, 4, 5
+GAUSSIAN, SPARSE_SIGN = 0, 1
+OP_SKETCH, OP_PRECOND_QR, OP_CONDEST, OP_PNE, OP_HPNE, OP_TRSM_GRAM, OP_FACTOR_SOLVE, OP_PNE_HOST, OP_HPNE_HOST = range(9)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblsq.so")
+_lib = None
+
+
+class LsqError(RuntimeError):
+    pass
+
+
+class Opts(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("zeta", C.c_int32), ("s", C.c_int64), ("seed", C.c_uint64),
+                ("sketch_prec", C.c_int32), ("qr_prec", C.c_int32), ("refine_steps", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+_vp, _i64, _sz = C.c_void_p, C.c_int64, C.c_size_t
+
+
+def lib():
+    """Load liblsq.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise LsqError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        sig = {
+            "lsq_version": (C.c_int32, []),
+            "lsq_status_string": (C.c_char_p, [C.c_int32]),
+            "lsq_workspace_size": (_sz, [C.c_int32, _i64, _i64, C.POINTER(Opts)]),
+            "lsq_precision_from_kappa0": (C.c_int32, [C.c_double]),
+            "lsq_sparse_sign_operator": (C.c_int32, [C.c_uint64, _i64, _i64, C.c_int32, _vp, _vp, _vp]),
+            "lsq_gaussian_operator": (C.c_int32, [C.c_uint64, _i64, _i64, C.c_int32, _vp, _vp]),
+            "lsq_sketch": (C.c_int32, [_vp, _i64, _i64, _i64, C.POINTER(Opts), _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
+            "lsq_precond_qr": (C.c_int32, [_vp, _i64, _i64, _i64, C.c_int32, C.c_int32, _vp, _vp, _i64, _vp, _vp,
+                                           _sz, _vp]),
+            "lsq_condest": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _sz, _vp]),
+            "lsq_trsm_gram": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, C.c_int32, _vp, _i64, _vp, _i64,
+                                          _vp, _vp, _sz, _vp]),
+            "lsq_factor_solve": (C.c_int32, [C.c_int32, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _sz,
+                                             _vp]),
+            "lsq_pne_solve": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, C.POINTER(Opts), _vp, _vp, _vp, _vp, _sz, _vp]),
+            "lsq_hpne_solve": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, C.POINTER(Opts), _vp, _vp, _vp, _vp, _sz,
+                                           _vp]),
+            "lsq_pne_solve_host": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, C.POINTER(Opts), _vp, _vp, _vp, _sz,
+                                               _vp]),
+            "lsq_hpne_solve_host": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, C.POINTER(Opts), _vp, _vp, _vp, _sz,
+                                                _vp]),
+            "lsq_launch_count": (C.c_int64, []),
+            "lsq_profile": (C.c_int32, [C.c_int32]),
+            "lsq_profile_collect": (C.c_int32, [C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_int32]),
+            "lsq_probe_fp64_fma": (C.c_int32, [_i64, C.c_int32, _vp, _vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+STAGES = ["condest", "sketch", "qr", "trsm", "gram", "factor", "solve", "refine"]
+
+
+def launch_count() -> int:
+    """Kernel launches issued by liblsq since it was loaded."""
+    return int(lib().lsq_launch_count())
+
+
+def profile(enable: bool) -> None:
+    """Start (clearing old records) or stop per-stage CUDA-event timing."""
+    lib().lsq_profile(int(enable))
+
+
+def profile_collect() -> dict:
+    """{stage: (total ms, records)} since the last collect; waits for the events."""
+    ms = (C.c_double * 8)()
+    cnt = (C.c_int32 * 8)()
+    _check(lib().lsq_profile_collect(ms, cnt, 8), "lsq_profile_collect")
+    return {name: (ms[i], cnt[i]) for i, name in enumerate(STAGES)}
+
+
+def probe_fp64_fma(iters: int, blocks: int, scratch: torch.Tensor) -> None:
+    _check(lib().lsq_probe_fp64_fma(iters, blocks, _ptr(scratch), _stream()), "lsq_probe_fp64_fma")
+
+
+def status_string(rc: int) -> str:
+    return lib().lsq_status_string(rc).decode()
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise LsqError(f"{what} failed: {status_string(rc)} ({rc})")
+
+
+def _stream(device=None):
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise LsqError("liblsq needs CUDA tensors (no CPU fallback)")
+
+
+def colmajor(A: torch.Tensor, ld: int = None) -> torch.Tensor:
+    """Column-major FP64 copy of A (shape (m, n), stride (1, ld))."""
+    m, n = A.shape
+    ld = m if ld is None else ld
+    out = torch.empty((n, ld), dtype=torch.float64, device=A.device).t()[:m]
+    out.copy_(A)
+    return out
+
+
+def _ld(A):
+    m, n = A.shape
+    if A.dtype != torch.float64:
+        raise LsqError("A must be float64")
+    if n == 1:
+        return m
+    if A.stride(0) != 1 or A.stride(1) < m:
+        raise LsqError("A must be column-major: stride (1, lda) with lda >= m (see colmajor())")
+    return A.stride(1)
+
+
+def make_opts(*, kind=SPARSE_SIGN, s=None, n=None, zeta=8, seed=0, sketch_prec=FP32, qr_prec=FP32, refine_steps=0):
+    if s is None:
+        s = 2 * n
+    return Opts(kind=kind, zeta=zeta, s=s, seed=seed, sketch_prec=sketch_prec, qr_prec=qr_prec,
+                refine_steps=refine_steps, reserved=0)
+
+
+def workspace_size(op, m, n, opts=None) -> int:
+    return int(lib().lsq_workspace_size(op, m, n, C.byref(opts) if opts is not None else None))
+
+
+def workspace(op, m, n, opts=None, device=None) -> torch.Tensor:
+    nbytes = workspace_size(op, m, n, opts)
+    if nbytes == 0:
+        raise LsqError("invalid arguments for the workspace query")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def precision_from_kappa0(k0: float) -> int:
+    return int(lib().lsq_precision_from_kappa0(float(k0)))
+
+
+def sparse_sign_operator(seed, m, s, zeta, device="cuda"):
+    idx = torch.empty((m, zeta), dtype=torch.int32, device=device)
+    sgn = torch.empty((m, zeta), dtype=torch.int8, device=device)
+    _check(lib().lsq_sparse_sign_operator(seed, m, s, zeta, _ptr(idx), _ptr(sgn), _stream()), "lsq_sparse_sign_operator")
+    return idx, sgn
+
+
+def gaussian_operator(seed, s, m, prec=FP64, device="cuda"):
+    Om = torch.empty((m, s), dtype=torch.float64, device=device).t()
+    _check(lib().lsq_gaussian_operator(seed, s, m, prec, _ptr(Om), _stream()), "lsq_gaussian_operator")
+    return Om
+
+
+def sketch(A, opts: Opts, ws=None):
+    """A_s (s x n, float32 unless FP64; column-major), colexp (n int32), info."""
+    _need_cuda(A)
+    m, n = A.shape
+    lda = _ld(A)
+    s = opts.s
+    dt = torch.float64 if opts.sketch_prec == FP64 else torch.float32
+    As = torch.empty((n, s), dtype=dt, device=A.device).t()
+    colexp = torch.empty(n, dtype=torch.int32, device=A.device)
+    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    ws = workspace(OP_SKETCH, m, n, opts, A.device) if ws is None else ws
+    _check(lib().lsq_sketch(_ptr(A), m, n, lda, C.byref(opts), _ptr(As), s, _ptr(colexp), _ptr(info), _ptr(ws),
+                            ws.numel(), _stream()), "lsq_sketch")
+    return As, colexp, info
+
+
+def precond_qr(As, colexp=None, qr_prec=FP32, ws=None):
+    """R_s (n x n FP64, upper; strict lower zero), info."""
+    _need_cuda(As)
+    s, n = As.shape
+    as_prec = FP64 if As.dtype == torch.float64 else FP32
+    if As.stride(0) != 1:
+        raise LsqError("As must be column-major")
+    Rs = torch.zeros((n, n), dtype=torch.float64, device=As.device).t()
+    info = torch.zeros(1, dtype=torch.int32, device=As.device)
+    ws = workspace(OP_PRECOND_QR, s, n, None, As.device) if ws is None else ws
+    _check(lib().lsq_precond_qr(_ptr(As), s, n, As.stride(1) if n > 1 else s, as_prec, qr_prec, _ptr(colexp), _ptr(Rs),
+                                n, _ptr(info), _ptr(ws), ws.numel(), _stream()), "lsq_precond_qr")
+    return Rs, info
+
+
+def condest(A, ws=None):
+    """(kappa0 (1 float64), chosen precision (1 int32)) on the device."""
+    _need_cuda(A)
+    m, n = A.shape
+    lda = _ld(A)
+    k0 = torch.empty(1, dtype=torch.float64, device=A.device)
+    ch = torch.empty(1, dtype=torch.int32, device=A.device)
+    ws = workspace(OP_CONDEST, m, n, None, A.device) if ws is None else ws
+    _check(lib().lsq_condest(_ptr(A), m, n, lda, _ptr(k0), _ptr(ch), _ptr(ws), ws.numel(), _stream()), "lsq_condest")
+    return k0, ch
+
+
+def trsm_gram(A, Rs, b, hpne=False, ws=None):
+    """A_p = A R_s^{-1}, G = A_p^T A_p (or A_p^T A), c = A_p^T b."""
+    _need_cuda(A, Rs, b)
+    m, n = A.shape
+    lda = _ld(A)
+    Ap = torch.empty((n, m), dtype=torch.float64, device=A.device).t()
+    G = torch.empty((n, n), dtype=torch.float64, device=A.device).t()
+    c = torch.empty(n, dtype=torch.float64, device=A.device)
+    ws = workspace(OP_TRSM_GRAM, m, n, None, A.device) if ws is None else ws
+    _check(lib().lsq_trsm_gram(_ptr(A), m, n, lda, _ptr(Rs), _ld(Rs), _ptr(b), int(hpne), _ptr(Ap), m, _ptr(G), n,
+                               _ptr(c), _ptr(ws), ws.numel(), _stream()), "lsq_trsm_gram")
+    return Ap, G, c
+
+
+def factor_solve(G, c, Rs=None, hpne=False):
+    """Factor G in place (Cholesky or LU-PP) and solve; returns (x, factors, piv, info)."""
+    _need_cuda(G, c, Rs)
+    n = G.shape[0]
+    F = colmajor(G)
+    x = torch.empty(n, dtype=torch.float64, device=G.device)
+    piv = torch.zeros(n, dtype=torch.int32, device=G.device)
+    info = torch.zeros(1, dtype=torch.int32, device=G.device)
+    _check(lib().lsq_factor_solve(int(hpne), _ptr(F), n, n, _ptr(c), _ptr(Rs), _ld(Rs) if Rs is not None else n,
+                                  _ptr(x), _ptr(piv), _ptr(info), None, 0, _stream()), "lsq_factor_solve")
+    return x, F, piv, info
+
+
+def solve(A, b, *, hpne=False, opts: Opts = None, ws=None, Rs_out=None, x=None, info=None, **kw):
+    """Alg. 1 end to end (PNE or HPNE).  Returns (x, info) device tensors."""
+    _need_cuda(A, b)
+    m, n = A.shape
+    lda = _ld(A)
+    opts = opts or make_opts(n=n, **kw)
+    op = OP_HPNE if hpne else OP_PNE
+    ws = workspace(op, m, n, opts, A.device) if ws is None else ws
+    x = torch.empty(n, dtype=torch.float64, device=A.device) if x is None else x
+    info = torch.zeros(1, dtype=torch.int32, device=A.device) if info is None else info
+    fn = lib().lsq_hpne_solve if hpne else lib().lsq_pne_solve
+    _check(fn(_ptr(A), m, n, lda, _ptr(b), C.byref(opts), _ptr(x), _ptr(Rs_out), _ptr(info), _ptr(ws), ws.numel(),
+              _stream()), "lsq_hpne_solve" if hpne else "lsq_pne_solve")
+    return x, info
+
+
+def pne(A, b, **kw):
+    return solve(A, b, hpne=False, **kw)
+
+
+def hpne(A, b, **kw):
+    return solve(A, b, hpne=True, **kw)
+
+
+def solve_host(A_host, b_host, *, hpne=False, opts: Opts = None, ws=None, x_host=None, **kw):
+    """End to end on HOST tensors (pinned recommended): copies in, solves,
+    copies x back; returns (x_host, info)."""
+    m, n = A_host.shape
+    if A_host.is_cuda or b_host.is_cuda:
+        raise LsqError("solve_host takes host tensors")
+    lda = _ld(A_host)
+    opts = opts or make_opts(n=n, **kw)
+    op = OP_HPNE_HOST if hpne else OP_PNE_HOST
+    ws = workspace(op, m, n, opts) if ws is None else ws
+    x_host = torch.empty(n, dtype=torch.float64, pin_memory=A_host.is_pinned()) if x_host is None else x_host
+    info = C.c_int32(0)
+    fn = lib().lsq_hpne_solve_host if hpne else lib().lsq_pne_solve_host
+    _check(fn(_ptr(A_host), m, n, lda, _ptr(b_host), C.byref(opts), _ptr(x_host), C.cast(C.pointer(info), C.c_void_p),
+              _ptr(ws), ws.numel(), _stream()), "lsq_solve_host")
+    return x_host, info.value

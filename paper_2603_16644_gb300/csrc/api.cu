@@ -1,0 +1,537 @@
+// C-ABI entry points of liblsq (declared in include/lsq.h): argument checks,
+// workspace layout and the sequence of kernels that implements Alg. 1.
+#include "common.cuh"
+#include "kernels.cuh"
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+using namespace lsq;
+
+namespace lsq {
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Pool of event pairs, one pair per (solve, stage) while profiling is on.
+struct StageProf {
+    std::mutex mu;
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t next = 0;
+    struct Rec { int stage; size_t ev_begin, ev_end; };
+    std::vector<Rec> recs;
+    size_t open_begin[ST_COUNT] = {};
+    bool open[ST_COUNT] = {};
+};
+static StageProf g_prof;
+
+static size_t prof_event() {
+    if (g_prof.next >= g_prof.pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return (size_t)-1;
+        g_prof.pool.push_back(e);
+    }
+    return g_prof.next++;
+}
+
+void stage_mark(int stage, bool begin, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (!g_prof.on) return;
+    size_t e = prof_event();
+    if (e == (size_t)-1) return;
+    cudaEventRecord(g_prof.pool[e], st);
+    if (begin) {
+        g_prof.open_begin[stage] = e;
+        g_prof.open[stage] = true;
+    } else if (g_prof.open[stage]) {
+        g_prof.recs.push_back({stage, g_prof.open_begin[stage], e});
+        g_prof.open[stage] = false;
+    }
+}
+
+}  // namespace lsq
+
+namespace {
+
+inline cudaStream_t S(void* p) { return reinterpret_cast<cudaStream_t>(p); }
+
+bool valid_sketch_prec(int p) { return p >= LSQ_FP8_E4M3 && p <= LSQ_FP64; }
+
+lsq_status check_opts(const lsq_opts* o, int64_t m, int64_t n, bool allow_auto) {
+    if (!o) return LSQ_ERR_ARG;
+    if (o->kind != LSQ_GAUSSIAN && o->kind != LSQ_SPARSE_SIGN) return LSQ_ERR_ARG;
+    if (o->s < n || o->s > m || o->s > 0x7fffffff) return LSQ_ERR_ARG;
+    if (o->kind == LSQ_SPARSE_SIGN && (o->zeta < 1 || o->zeta > 32 || o->zeta > o->s)) return LSQ_ERR_ARG;
+    if (!valid_sketch_prec(o->sketch_prec) && !(allow_auto && o->sketch_prec == LSQ_AUTO)) return LSQ_ERR_ARG;
+    if (o->qr_prec != LSQ_FP32 && o->qr_prec != LSQ_FP64) return LSQ_ERR_ARG;
+    if (o->refine_steps < 0 || o->refine_steps > 1) return LSQ_ERR_ARG;
+    return LSQ_OK;
+}
+
+// Byte offsets of every piece of scratch, from one routine so that the size
+// query and the solver agree.
+struct Off {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        size_t o = off;
+        off = align_up(off + std::max<size_t>(bytes, 1), 256);
+        return o;
+    }
+};
+
+struct SketchLayout {
+    size_t colmax, colexp, ahat, idx, sgn, counts, rowptr, cursor, col, maxcount, err, om, gemm, total;
+    int64_t ldq, ldo;
+};
+
+SketchLayout sketch_layout(int64_t m, int64_t n, int64_t s, int kind, int zeta, int prec, int sms) {
+    SketchLayout L{};
+    Off o;
+    int es = prec_bytes(prec);
+    L.ldq = align_up((size_t)m, 16);
+    L.ldo = L.ldq;
+    L.colmax = o.take(sizeof(unsigned long long) * n);
+    L.colexp = o.take(sizeof(int32_t) * n);
+    L.err = o.take(sizeof(int32_t));
+    if (kind == LSQ_SPARSE_SIGN) {
+        L.ahat = o.take((size_t)m * n * es);
+        L.idx = o.take(sizeof(int32_t) * (size_t)m * zeta);
+        L.sgn = o.take((size_t)m * zeta);
+        L.counts = o.take(sizeof(int32_t) * (size_t)s);
+        L.rowptr = o.take(sizeof(int32_t) * (size_t)(s + 1));
+        L.cursor = o.take(sizeof(int32_t) * (size_t)s);
+        L.col = o.take(sizeof(uint32_t) * (size_t)m * zeta);
+        L.maxcount = o.take(sizeof(int32_t));
+    } else {
+        L.ahat = o.take((size_t)L.ldq * n * es);
+        L.om = o.take((size_t)L.ldo * s * es);
+        GemmPlan gp = plan_gemm_kmajor(s, n, m, false, prec == LSQ_FP64 ? LSQ_FP64 : LSQ_FP32, sms);
+        L.gemm = o.take(gemm_kmajor_ws_bytes(gp));
+    }
+    L.total = o.off;
+    return L;
+}
+
+struct SolveLayout {
+    SketchLayout sk;
+    size_t sk_base, as_, rs, qr, ap, g, c, x, r, gv, piv, gemm, gemv, cond, k0, ch, err, total;
+    size_t qr_bytes, cond_bytes;
+};
+
+SolveLayout solve_layout(int64_t m, int64_t n, const lsq_opts* o, int prec, bool hpne, int sms) {
+    SolveLayout L{};
+    Off q;
+    L.sk = sketch_layout(m, n, o->s, o->kind, o->zeta, prec, sms);
+    L.sk_base = q.take(L.sk.total);
+    int as_es = prec == LSQ_FP64 ? 8 : 4;
+    L.as_ = q.take((size_t)o->s * n * as_es);
+    L.rs = q.take(sizeof(double) * (size_t)n * n);
+    int qp = prec == LSQ_FP64 ? LSQ_FP64 : o->qr_prec;
+    L.qr_bytes = qr_ws_bytes(o->s, n, qp);
+    L.qr = q.take(L.qr_bytes);
+    L.ap = q.take(sizeof(double) * (size_t)m * n);
+    L.g = q.take(sizeof(double) * (size_t)n * n);
+    L.c = q.take(sizeof(double) * n);
+    L.x = q.take(sizeof(double) * n);
+    L.r = q.take(sizeof(double) * m);
+    L.gv = q.take(sizeof(double) * n);
+    L.piv = q.take(sizeof(int32_t) * n);
+    GemmPlan gp = plan_gemm_kmajor(n, n, m, !hpne, LSQ_FP64, sms);
+    L.gemm = q.take(gemm_kmajor_ws_bytes(gp));
+    L.gemv = q.take(gemv_t_ws_bytes(m, n));
+    L.cond_bytes = condest_ws_bytes(m, n, sms);
+    L.cond = q.take(L.cond_bytes);
+    L.k0 = q.take(sizeof(double));
+    L.ch = q.take(sizeof(int32_t));
+    L.err = q.take(sizeof(int32_t));
+    L.total = q.off + 256;
+    return L;
+}
+
+char* aligned(void* ws) { return (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255); }
+
+__global__ void k_merge_err(const int32_t* __restrict__ err, int32_t* __restrict__ info) {
+    if (*err != 0) atomicCAS(info, 0, *err);
+}
+
+lsq_status run_sketch(const double* A, int64_t m, int64_t n, int64_t lda, const lsq_opts* o, int prec, void* As,
+                      int64_t ldas, int32_t* colexp_out, char* base, const SketchLayout& L, int32_t* err,
+                      cudaStream_t st) {
+    unsigned long long* colmax = (unsigned long long*)(base + L.colmax);
+    int32_t* colexp = colexp_out ? colexp_out : (int32_t*)(base + L.colexp);
+    lsq_status r = launch_colexp(A, m, n, lda, prec, colmax, colexp, st);
+    if (r != LSQ_OK) return r;
+    if (o->kind == LSQ_SPARSE_SIGN) {
+        int32_t* idx = (int32_t*)(base + L.idx);
+        int8_t* sgn = (int8_t*)(base + L.sgn);
+        if ((r = launch_sparse_gen(o->seed, m, o->s, o->zeta, idx, sgn, err, st)) != LSQ_OK) return r;
+        if ((r = launch_sparse_csr(idx, sgn, m, o->s, o->zeta, (int32_t*)(base + L.counts), (int32_t*)(base + L.rowptr),
+                                   (int32_t*)(base + L.cursor), (uint32_t*)(base + L.col),
+                                   (int32_t*)(base + L.maxcount), err, st)) != LSQ_OK)
+            return r;
+        if ((r = launch_quantize_rm(A, m, n, lda, colexp, prec, base + L.ahat, st)) != LSQ_OK) return r;
+        return launch_sparse_gather((int32_t*)(base + L.rowptr), (uint32_t*)(base + L.col), base + L.ahat, prec,
+                                    o->s, n, As, ldas, st);
+    }
+    if ((r = launch_gauss_gen(o->seed, o->s, m, prec, base + L.om, L.ldo, st)) != LSQ_OK) return r;
+    if ((r = launch_quantize_cm(A, m, n, lda, colexp, prec, base + L.ahat, L.ldq, st)) != LSQ_OK) return r;
+    GemmPlan gp = plan_gemm_kmajor(o->s, n, m, false, prec == LSQ_FP64 ? LSQ_FP64 : LSQ_FP32, device_sm_count());
+    return launch_gemm_kmajor(gp, base + L.om, prec, L.ldo, base + L.ahat, prec, L.ldq, As, ldas, base + L.gemm, st);
+}
+
+// Solve with the factors already in G (and piv / Rs): PNE: L L^T y = v, x = Rs^{-1} y;
+// HPNE: P, unit L, U.
+lsq_status solve_factored(bool hpne, const double* G, int64_t n, int64_t ldg, const int32_t* piv, const double* Rs,
+                          int64_t ldr, double* v, const int32_t* info, cudaStream_t st) {
+    lsq_status r;
+    if (hpne) {
+        if ((r = launch_apply_piv(piv, n, v, info, st)) != LSQ_OK) return r;
+        if ((r = launch_trsv<double>(TRSV_UNIT_LOWER, G, n, ldg, v, info, st)) != LSQ_OK) return r;
+        return launch_trsv<double>(TRSV_UPPER, G, n, ldg, v, info, st);
+    }
+    if ((r = launch_trsv<double>(TRSV_LOWER, G, n, ldg, v, info, st)) != LSQ_OK) return r;
+    if ((r = launch_trsv<double>(TRSV_LOWER_T, G, n, ldg, v, info, st)) != LSQ_OK) return r;
+    if (Rs) return launch_trsv<double>(TRSV_UPPER, Rs, n, ldr, v, info, st);
+    return LSQ_OK;
+}
+
+lsq_status trsm_gram(const double* A, int64_t m, int64_t n, int64_t lda, const double* Rs, int64_t ldr,
+                     const double* b, bool hpne, double* Ap, int64_t ldap, double* G, int64_t ldg, double* c,
+                     void* gemm_ws, double* gemv_ws, int64_t gemv_cap, int sms, cudaStream_t st) {
+    stage_mark(ST_TRSM, true, st);
+    lsq_status r = launch_trsm_right_upper(A, m, n, lda, Rs, ldr, Ap, ldap, st);
+    if (r != LSQ_OK) return r;
+    stage_mark(ST_TRSM, false, st);
+    stage_mark(ST_GRAM, true, st);
+    GemmPlan gp = plan_gemm_kmajor(n, n, m, !hpne, LSQ_FP64, sms);
+    if (hpne)
+        r = launch_gemm_kmajor(gp, Ap, LSQ_FP64, ldap, A, LSQ_FP64, lda, G, ldg, gemm_ws, st);
+    else
+        r = launch_gemm_kmajor(gp, Ap, LSQ_FP64, ldap, Ap, LSQ_FP64, ldap, G, ldg, gemm_ws, st);
+    if (r != LSQ_OK) return r;
+    r = launch_gemv_t(Ap, m, n, ldap, b, c, gemv_ws, gemv_cap, st);
+    stage_mark(ST_GRAM, false, st);
+    return r;
+}
+
+lsq_status solve_impl(bool hpne, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                      const lsq_opts* o, double* x, double* Rs_out, int32_t* info, void* ws, size_t ws_bytes,
+                      cudaStream_t st) {
+    if (!A || !b || !x || !info || m <= 0 || n <= 0 || lda < m) return LSQ_ERR_ARG;
+    lsq_status r = check_opts(o, m, n, true);
+    if (r != LSQ_OK) return r;
+    int sms = device_sm_count();
+    // Layout with the widest sketch precision when AUTO, so one workspace
+    // serves whatever precision the estimate picks.
+    int prec_for_layout = o->sketch_prec == LSQ_AUTO ? LSQ_FP64 : o->sketch_prec;
+    SolveLayout L = solve_layout(m, n, o, prec_for_layout, hpne, sms);
+    if (!ws || L.total > ws_bytes) return LSQ_ERR_NOMEM;
+    char* base = aligned(ws);
+    int32_t* err = (int32_t*)(base + L.err);
+    LSQ_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
+    LSQ_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+    int prec = o->sketch_prec;
+    if (prec == LSQ_AUTO) {
+        double* k0 = (double*)(base + L.k0);
+        int32_t* ch = (int32_t*)(base + L.ch);
+        stage_mark(ST_CONDEST, true, st);
+        if ((r = launch_condest(A, m, n, lda, k0, ch, base + L.cond, L.cond_bytes, sms, st)) != LSQ_OK) return r;
+        stage_mark(ST_CONDEST, false, st);
+        int32_t host_ch = LSQ_FP64;
+        LSQ_CUDA_TRY(cudaMemcpyAsync(&host_ch, ch, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        LSQ_CUDA_TRY(cudaStreamSynchronize(st));
+        prec = host_ch;
+        if (!valid_sketch_prec(prec)) prec = LSQ_FP64;
+    }
+    int qp = prec == LSQ_FP64 ? LSQ_FP64 : o->qr_prec;
+    SketchLayout SK = sketch_layout(m, n, o->s, o->kind, o->zeta, prec, sms);
+    char* skb = base + L.sk_base;
+    void* As = base + L.as_;
+    int64_t s = o->s;
+    double* Rs = (double*)(base + L.rs);
+    double* Ap = (double*)(base + L.ap);
+    double* G = (double*)(base + L.g);
+    double* c = (double*)(base + L.c);
+    double* r_ = (double*)(base + L.r);
+    double* gv = (double*)(base + L.gv);
+    int32_t* piv = (int32_t*)(base + L.piv);
+    int32_t* colexp = (int32_t*)(skb + SK.colexp);
+    stage_mark(ST_SKETCH, true, st);
+    if ((r = run_sketch(A, m, n, lda, o, prec, As, s, colexp, skb, SK, err, st)) != LSQ_OK) return r;
+    stage_mark(ST_SKETCH, false, st);
+    stage_mark(ST_QR, true, st);
+    if ((r = launch_precond_qr(As, s, n, s, prec == LSQ_FP64 ? LSQ_FP64 : LSQ_FP32, qp, colexp, Rs, n, info,
+                               base + L.qr, L.qr_bytes, st)) != LSQ_OK)
+        return r;
+    stage_mark(ST_QR, false, st);
+    if ((r = trsm_gram(A, m, n, lda, Rs, n, b, hpne, Ap, m, G, n, c, base + L.gemm, (double*)(base + L.gemv),
+                       (int64_t)(gemv_t_ws_bytes(m, n) / sizeof(double)), sms, st)) != LSQ_OK)
+        return r;
+    stage_mark(ST_FACTOR, true, st);
+    if (hpne)
+        r = launch_lu(G, n, n, piv, info, st);
+    else
+        r = launch_cholesky<double>(G, n, n, info, st);
+    if (r != LSQ_OK) return r;
+    stage_mark(ST_FACTOR, false, st);
+    stage_mark(ST_SOLVE, true, st);
+    LSQ_CUDA_TRY(cudaMemcpyAsync(x, c, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    if ((r = solve_factored(hpne, G, n, n, piv, Rs, n, x, info, st)) != LSQ_OK) return r;
+    stage_mark(ST_SOLVE, false, st);
+    if (o->refine_steps > 0) stage_mark(ST_REFINE, true, st);
+    for (int step = 0; step < o->refine_steps; ++step) {
+        if ((r = launch_residual(A, m, n, lda, x, b, r_, st)) != LSQ_OK) return r;
+        if ((r = launch_gemv_t(Ap, m, n, m, r_, gv, (double*)(base + L.gemv),
+                               (int64_t)(gemv_t_ws_bytes(m, n) / sizeof(double)), st)) != LSQ_OK)
+            return r;
+        if ((r = solve_factored(hpne, G, n, n, piv, Rs, n, gv, info, st)) != LSQ_OK) return r;
+        if ((r = launch_axpy1(x, gv, n, st)) != LSQ_OK) return r;
+    }
+    if (o->refine_steps > 0) stage_mark(ST_REFINE, false, st);
+    if (Rs_out) LSQ_CUDA_TRY(cudaMemcpyAsync(Rs_out, Rs, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, st));
+    k_merge_err<<<1, 1, 0, st>>>(err, info);
+    LSQ_LAUNCH_CHECK();
+    return LSQ_OK;
+}
+
+struct HostLayout {
+    size_t a, b, x, info, solve, total;
+};
+
+HostLayout host_layout(int64_t m, int64_t n, const lsq_opts* o, bool hpne, int sms) {
+    HostLayout H{};
+    Off q;
+    H.a = q.take(sizeof(double) * (size_t)m * n);
+    H.b = q.take(sizeof(double) * m);
+    H.x = q.take(sizeof(double) * n);
+    H.info = q.take(sizeof(int32_t));
+    int p = o->sketch_prec == LSQ_AUTO ? LSQ_FP64 : o->sketch_prec;
+    H.solve = q.take(solve_layout(m, n, o, p, hpne, sms).total);
+    H.total = q.off + 256;
+    return H;
+}
+
+lsq_status solve_host_impl(bool hpne, const double* A_host, int64_t m, int64_t n, int64_t lda, const double* b_host,
+                           const lsq_opts* o, double* x_host, int32_t* info_host, void* ws, size_t ws_bytes,
+                           cudaStream_t st) {
+    if (!A_host || !b_host || !x_host || !info_host || m <= 0 || n <= 0 || lda < m) return LSQ_ERR_ARG;
+    lsq_status r = check_opts(o, m, n, true);
+    if (r != LSQ_OK) return r;
+    int sms = device_sm_count();
+    HostLayout H = host_layout(m, n, o, hpne, sms);
+    if (!ws || H.total > ws_bytes) return LSQ_ERR_NOMEM;
+    char* base = aligned(ws);
+    double* A = (double*)(base + H.a);
+    double* b = (double*)(base + H.b);
+    double* x = (double*)(base + H.x);
+    int32_t* info = (int32_t*)(base + H.info);
+    if (lda == m) {
+        LSQ_CUDA_TRY(cudaMemcpyAsync(A, A_host, sizeof(double) * (size_t)m * n, cudaMemcpyHostToDevice, st));
+    } else {
+        LSQ_CUDA_TRY(cudaMemcpy2DAsync(A, sizeof(double) * m, A_host, sizeof(double) * lda, sizeof(double) * m, n,
+                                       cudaMemcpyHostToDevice, st));
+    }
+    LSQ_CUDA_TRY(cudaMemcpyAsync(b, b_host, sizeof(double) * m, cudaMemcpyHostToDevice, st));
+    size_t solve_cap = ws_bytes - (size_t)((base + H.solve) - (char*)ws);
+    r = solve_impl(hpne, A, m, n, m, b, o, x, nullptr, info, base + H.solve, solve_cap, st);
+    if (r != LSQ_OK) return r;
+    LSQ_CUDA_TRY(cudaMemcpyAsync(x_host, x, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    LSQ_CUDA_TRY(cudaMemcpyAsync(info_host, info, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    LSQ_CUDA_TRY(cudaStreamSynchronize(st));
+    return LSQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t lsq_version(void) { return 100; }
+
+int64_t lsq_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int32_t lsq_profile(int32_t enable) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.on = enable != 0;
+    g_prof.next = 0;
+    g_prof.recs.clear();
+    for (int i = 0; i < ST_COUNT; ++i) g_prof.open[i] = false;
+    return LSQ_OK;
+}
+
+int32_t lsq_profile_collect(double* ms_by_stage, int32_t* count_by_stage, int32_t nstages) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (!ms_by_stage || !count_by_stage || nstages < ST_COUNT) return LSQ_ERR_ARG;
+    for (int i = 0; i < nstages; ++i) { ms_by_stage[i] = 0.0; count_by_stage[i] = 0; }
+    for (auto& rec : g_prof.recs) {
+        if (cudaEventSynchronize(g_prof.pool[rec.ev_end]) != cudaSuccess) return LSQ_ERR_CUDA;
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, g_prof.pool[rec.ev_begin], g_prof.pool[rec.ev_end]) != cudaSuccess)
+            return LSQ_ERR_CUDA;
+        ms_by_stage[rec.stage] += ms;
+        count_by_stage[rec.stage] += 1;
+    }
+    g_prof.recs.clear();
+    g_prof.next = 0;
+    return LSQ_OK;
+}
+
+const char* lsq_status_string(int32_t s) {
+    switch (s) {
+    case LSQ_OK: return "LSQ_OK";
+    case LSQ_ERR_ARG: return "LSQ_ERR_ARG";
+    case LSQ_ERR_BREAKDOWN: return "LSQ_ERR_BREAKDOWN";
+    case LSQ_ERR_NONFINITE: return "LSQ_ERR_NONFINITE";
+    case LSQ_ERR_TIMEOUT: return "LSQ_ERR_TIMEOUT";
+    case LSQ_ERR_CUDA: return "LSQ_ERR_CUDA";
+    case LSQ_ERR_NOMEM: return "LSQ_ERR_NOMEM";
+    default: return "LSQ_UNKNOWN";
+    }
+}
+
+int32_t lsq_precision_from_kappa0(double k0) {
+    if (!(k0 == k0) || k0 > 1.0e308) return LSQ_FP64;
+    if (k0 < 2.0) return LSQ_FP8_E4M3;
+    if (k0 < 3.0) return LSQ_BF16;
+    if (k0 < 4.0) return LSQ_FP16;
+    if (k0 <= 8.0) return LSQ_FP32;
+    return LSQ_FP64;
+}
+
+size_t lsq_workspace_size(int32_t op, int64_t m, int64_t n, const lsq_opts* o) {
+    if (m <= 0 || n <= 0) return 0;
+    int sms = device_sm_count();
+    switch (op) {
+    case LSQ_OP_SKETCH:
+        if (check_opts(o, m, n, false) != LSQ_OK) return 0;
+        return sketch_layout(m, n, o->s, o->kind, o->zeta, o->sketch_prec, sms).total + 256;
+    case LSQ_OP_PRECOND_QR:  // m is s here
+        return qr_ws_bytes(m, n, LSQ_FP64) + 256;
+    case LSQ_OP_CONDEST:
+        return condest_ws_bytes(m, n, sms) + 256;
+    case LSQ_OP_PNE:
+    case LSQ_OP_HPNE: {
+        if (check_opts(o, m, n, true) != LSQ_OK) return 0;
+        int p = o->sketch_prec == LSQ_AUTO ? LSQ_FP64 : o->sketch_prec;
+        return solve_layout(m, n, o, p, op == LSQ_OP_HPNE, sms).total + 256;
+    }
+    case LSQ_OP_TRSM_GRAM: {
+        GemmPlan gp = plan_gemm_kmajor(n, n, m, false, LSQ_FP64, sms);
+        GemmPlan gs = plan_gemm_kmajor(n, n, m, true, LSQ_FP64, sms);
+        return std::max(gemm_kmajor_ws_bytes(gp), gemm_kmajor_ws_bytes(gs)) + gemv_t_ws_bytes(m, n) + 1024;
+    }
+    case LSQ_OP_FACTOR_SOLVE:
+        return 256;
+    case LSQ_OP_PNE_HOST:
+    case LSQ_OP_HPNE_HOST:
+        if (check_opts(o, m, n, true) != LSQ_OK) return 0;
+        return host_layout(m, n, o, op == LSQ_OP_HPNE_HOST, sms).total + 256;
+    default:
+        return 0;
+    }
+}
+
+lsq_status lsq_sparse_sign_operator(uint64_t seed, int64_t m, int64_t s, int32_t zeta, int32_t* idx, int8_t* sgn,
+                                    void* stream) {
+    if (m <= 0 || s <= 0 || s > 0x7fffffff || zeta < 1 || zeta > 32 || zeta > s || !idx || !sgn) return LSQ_ERR_ARG;
+    return launch_sparse_gen(seed, m, s, zeta, idx, sgn, nullptr, S(stream));
+}
+
+lsq_status lsq_gaussian_operator(uint64_t seed, int64_t s, int64_t m, int32_t prec, double* Om, void* stream) {
+    if (m <= 0 || s <= 0 || !Om || !valid_sketch_prec(prec)) return LSQ_ERR_ARG;
+    return launch_gauss_inspect(seed, s, m, prec, Om, S(stream));
+}
+
+lsq_status lsq_sketch(const double* A, int64_t m, int64_t n, int64_t lda, const lsq_opts* o, void* As, int64_t ldas,
+                      int32_t* colexp, int32_t* info, void* ws, size_t ws_bytes, void* stream) {
+    if (!A || !As || m <= 0 || n <= 0 || lda < m) return LSQ_ERR_ARG;
+    lsq_status r = check_opts(o, m, n, false);
+    if (r != LSQ_OK) return r;
+    if (ldas < o->s) return LSQ_ERR_ARG;
+    int sms = device_sm_count();
+    SketchLayout L = sketch_layout(m, n, o->s, o->kind, o->zeta, o->sketch_prec, sms);
+    if (!ws || L.total + 256 > ws_bytes) return LSQ_ERR_NOMEM;
+    char* base = aligned(ws);
+    int32_t* err = (int32_t*)(base + L.err);
+    LSQ_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), S(stream)));
+    if (info) LSQ_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), S(stream)));
+    r = run_sketch(A, m, n, lda, o, o->sketch_prec, As, ldas, colexp, base, L, err, S(stream));
+    if (r != LSQ_OK) return r;
+    if (info) {
+        k_merge_err<<<1, 1, 0, S(stream)>>>(err, info);
+        LSQ_LAUNCH_CHECK();
+    }
+    return LSQ_OK;
+}
+
+lsq_status lsq_precond_qr(const void* As, int64_t s, int64_t n, int64_t ldas, int32_t as_prec, int32_t qr_prec,
+                          const int32_t* colexp, double* Rs, int64_t ldr, int32_t* info, void* ws, size_t ws_bytes,
+                          void* stream) {
+    if (!As || !Rs || n <= 0 || s < n || ldas < s || ldr < n) return LSQ_ERR_ARG;
+    if ((as_prec != LSQ_FP32 && as_prec != LSQ_FP64) || (qr_prec != LSQ_FP32 && qr_prec != LSQ_FP64)) return LSQ_ERR_ARG;
+    if (info) LSQ_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), S(stream)));
+    return launch_precond_qr(As, s, n, ldas, as_prec, qr_prec, colexp, Rs, ldr, info, ws, ws_bytes, S(stream));
+}
+
+lsq_status lsq_condest(const double* A, int64_t m, int64_t n, int64_t lda, double* kappa0, int32_t* chosen, void* ws,
+                       size_t ws_bytes, void* stream) {
+    if (!A || !kappa0 || !chosen || m <= 0 || n <= 0 || lda < m) return LSQ_ERR_ARG;
+    return launch_condest(A, m, n, lda, kappa0, chosen, ws, ws_bytes, device_sm_count(), S(stream));
+}
+
+lsq_status lsq_trsm_gram(const double* A, int64_t m, int64_t n, int64_t lda, const double* Rs, int64_t ldr,
+                         const double* b, int32_t hpne, double* Ap, int64_t ldap, double* G, int64_t ldg, double* c,
+                         void* ws, size_t ws_bytes, void* stream) {
+    if (!A || !Rs || !b || !Ap || !G || !c || m <= 0 || n <= 0 || lda < m || ldr < n || ldap < m || ldg < n)
+        return LSQ_ERR_ARG;
+    int sms = device_sm_count();
+    size_t need = lsq_workspace_size(LSQ_OP_TRSM_GRAM, m, n, nullptr);
+    if (!ws || ws_bytes < need) return LSQ_ERR_NOMEM;
+    char* base = aligned(ws);
+    size_t gemv_bytes = gemv_t_ws_bytes(m, n);
+    double* gemv_ws = (double*)base;
+    char* gemm_ws = base + align_up(gemv_bytes, 256);
+    return trsm_gram(A, m, n, lda, Rs, ldr, b, hpne != 0, Ap, ldap, G, ldg, c, gemm_ws, gemv_ws,
+                     (int64_t)(gemv_bytes / sizeof(double)), sms, S(stream));
+}
+
+lsq_status lsq_factor_solve(int32_t hpne, double* G, int64_t n, int64_t ldg, const double* c, const double* Rs,
+                            int64_t ldr, double* x, int32_t* piv, int32_t* info, void* ws, size_t ws_bytes,
+                            void* stream) {
+    (void)ws;
+    (void)ws_bytes;
+    if (!G || !c || !x || !info || n <= 0 || ldg < n || (hpne && !piv) || (Rs && ldr < n)) return LSQ_ERR_ARG;
+    cudaStream_t st = S(stream);
+    LSQ_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
+    lsq_status r = hpne ? launch_lu(G, n, ldg, piv, info, st) : launch_cholesky<double>(G, n, ldg, info, st);
+    if (r != LSQ_OK) return r;
+    LSQ_CUDA_TRY(cudaMemcpyAsync(x, c, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    return solve_factored(hpne != 0, G, n, ldg, piv, Rs, ldr, x, info, st);
+}
+
+lsq_status lsq_pne_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, const lsq_opts* opts,
+                         double* x, double* Rs_out, int32_t* info, void* ws, size_t ws_bytes, void* stream) {
+    return solve_impl(false, A, m, n, lda, b, opts, x, Rs_out, info, ws, ws_bytes, S(stream));
+}
+
+lsq_status lsq_hpne_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, const lsq_opts* opts,
+                          double* x, double* Rs_out, int32_t* info, void* ws, size_t ws_bytes, void* stream) {
+    return solve_impl(true, A, m, n, lda, b, opts, x, Rs_out, info, ws, ws_bytes, S(stream));
+}
+
+lsq_status lsq_pne_solve_host(const double* A_host, int64_t m, int64_t n, int64_t lda, const double* b_host,
+                              const lsq_opts* opts, double* x_host, int32_t* info_host, void* ws, size_t ws_bytes,
+                              void* stream) {
+    return solve_host_impl(false, A_host, m, n, lda, b_host, opts, x_host, info_host, ws, ws_bytes, S(stream));
+}
+
+lsq_status lsq_hpne_solve_host(const double* A_host, int64_t m, int64_t n, int64_t lda, const double* b_host,
+                               const lsq_opts* opts, double* x_host, int32_t* info_host, void* ws, size_t ws_bytes,
+                               void* stream) {
+    return solve_host_impl(true, A_host, m, n, lda, b_host, opts, x_host, info_host, ws, ws_bytes, S(stream));
+}
+
+}  // extern "C"

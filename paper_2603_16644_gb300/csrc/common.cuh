@@ -1,0 +1,170 @@
+// Shared device helpers for liblsq: error handling, Philox4x32-10, exact
+// FP64 -> low-precision rounding, workspace carving.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/lsq.h"
+
+namespace lsq {
+
+#define LSQ_CUDA_TRY(expr)                                  \
+    do {                                                    \
+        cudaError_t e__ = (expr);                           \
+        if (e__ != cudaSuccess) return LSQ_ERR_CUDA;        \
+    } while (0)
+
+// Every kernel launch goes through this check; it also counts launches
+// (lsq_launch_count) so callers can verify what ran.
+void note_launch();
+#define LSQ_LAUNCH_CHECK()                 \
+    do {                                   \
+        ::lsq::note_launch();              \
+        LSQ_CUDA_TRY(cudaGetLastError());  \
+    } while (0)
+
+// Stage timing (lsq_profile): events recorded around the steps of Alg. 1.
+enum Stage { ST_CONDEST = 0, ST_SKETCH, ST_QR, ST_TRSM, ST_GRAM, ST_FACTOR, ST_SOLVE, ST_REFINE, ST_COUNT };
+void stage_mark(int stage, bool begin, cudaStream_t st);
+
+static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Bump allocator over the caller's workspace (256-byte aligned pieces).
+struct Carver {
+    char* base;
+    size_t cap;
+    size_t off;
+    bool ok;
+    Carver(void* p, size_t c) : base((char*)p), cap(c), off(0), ok(true) {}
+    template <class T>
+    T* take(size_t count) {
+        size_t o = align_up(off, 256);
+        size_t bytes = align_up(count * sizeof(T), 256);
+        off = o + bytes;
+        if (off > cap || base == nullptr) { ok = false; return nullptr; }
+        return (T*)(base + o);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10, Salmon et al. SC'11 (multipliers 0xD2511F53, 0xCD9E8D57;
+// key increments 0x9E3779B9, 0xBB67AE85).
+// ---------------------------------------------------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        U4 n;
+        n.x = hi1 ^ c.y ^ k0;
+        n.y = lo1;
+        n.z = hi0 ^ c.w ^ k1;
+        n.w = lo0;
+        c = n;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t word_of(const U4& v, int t) {
+    return t == 0 ? v.x : (t == 1 ? v.y : (t == 2 ? v.z : v.w));
+}
+
+// ---------------------------------------------------------------------------
+// Exact round-to-nearest-even of an FP64 value to a format with p significand
+// bits and minimum normal exponent emin (subnormals kept), done on the integer
+// significand so there is exactly one rounding.  Returns the rounded value as
+// a double (exactly representable in the target format).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double rne_sig(double x, int p, int emin, double maxfin, bool sat) {
+    if (x == 0.0 || isnan(x)) return x;
+    if (isinf(x)) return sat ? copysign(maxfin, x) : x;
+    unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    unsigned long long sign = bits & 0x8000000000000000ull;
+    int bexp = (int)((bits >> 52) & 0x7ff);
+    if (bexp == 0) return __longlong_as_double((long long)sign);  // FP64 subnormal: far below every target
+    int E = bexp - 1023;
+    unsigned long long mant = (bits & 0x000fffffffffffffull) | 0x0010000000000000ull;  // 53 bits
+    int e = E < emin ? emin : E;
+    int drop = (53 - p) + (e - E);  // low significand bits that do not fit
+    unsigned long long keep;
+    if (drop >= 64) {
+        keep = 0;
+    } else if (drop > 54) {
+        keep = 0;  // below half of the smallest step
+    } else {
+        keep = mant >> drop;
+        unsigned long long rem = mant & ((1ull << drop) - 1ull);
+        unsigned long long half = 1ull << (drop - 1);
+        if (rem > half || (rem == half && (keep & 1ull))) keep += 1ull;
+    }
+    // value = keep * 2^(e - p + 1), exact
+    double y = ldexp((double)keep, e - p + 1);
+    if (y > maxfin) y = sat ? maxfin : __longlong_as_double(0x7ff0000000000000ll);
+    return sign ? -y : y;
+}
+
+__device__ __forceinline__ double round_to_prec(double x, int prec) {
+    switch (prec) {
+    case LSQ_FP8_E4M3: return rne_sig(x, 4, -6, 448.0, true);
+    case LSQ_BF16: return rne_sig(x, 8, -126, 3.3895313892515355e38, false);
+    case LSQ_FP16: return rne_sig(x, 11, -14, 65504.0, false);
+    case LSQ_FP32: return (double)__double2float_rn(x);
+    default: return x;
+    }
+}
+
+// Storage size in bytes of one element of a sketch precision.
+static inline int prec_bytes(int prec) {
+    switch (prec) {
+    case LSQ_FP8_E4M3: return 1;
+    case LSQ_BF16: case LSQ_FP16: return 2;
+    case LSQ_FP32: return 4;
+    default: return 8;
+    }
+}
+
+// Store an exactly-representable value in the packed format.
+__device__ __forceinline__ void store_prec(void* base, size_t i, double v, int prec) {
+    switch (prec) {
+    case LSQ_FP8_E4M3: {
+        __nv_fp8_storage_t s = __nv_cvt_double_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+        ((__nv_fp8_storage_t*)base)[i] = s;
+        break;
+    }
+    case LSQ_BF16: ((__nv_bfloat16*)base)[i] = __double2bfloat16(v); break;
+    case LSQ_FP16: ((__half*)base)[i] = __double2half(v); break;
+    case LSQ_FP32: ((float*)base)[i] = (float)v; break;
+    default: ((double*)base)[i] = v; break;
+    }
+}
+
+__device__ __forceinline__ float load_prec_f(const void* base, size_t i, int prec) {
+    switch (prec) {
+    case LSQ_FP8_E4M3: {
+        __half_raw h = __nv_cvt_fp8_to_halfraw(((const __nv_fp8_storage_t*)base)[i], __NV_E4M3);
+        return __half2float(__half(h));
+    }
+    case LSQ_BF16: return __bfloat162float(((const __nv_bfloat16*)base)[i]);
+    case LSQ_FP16: return __half2float(((const __half*)base)[i]);
+    case LSQ_FP32: return ((const float*)base)[i];
+    default: return (float)((const double*)base)[i];
+    }
+}
+
+// Device-side status word written by kernels that detect a failure.
+// info > 0: breakdown at that (1-based) pivot; -1 non-finite; -2 timeout.
+__device__ __forceinline__ void set_info_once(int32_t* info, int32_t v) {
+    if (info) atomicCAS(info, 0, v);
+}
+
+}  // namespace lsq

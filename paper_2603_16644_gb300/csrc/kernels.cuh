@@ -1,0 +1,98 @@
+// Internal launcher declarations shared by the translation units of liblsq.
+#pragma once
+#include "common.cuh"
+
+namespace lsq {
+
+__device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Conversion of a stored element to the accumulation type (exact for every
+// stored format into float; double -> float rounds to nearest even).
+template <typename TS, typename TACC>
+__device__ __forceinline__ TACC to_acc(TS v);
+template <> __device__ __forceinline__ float to_acc<__nv_fp8_storage_t, float>(__nv_fp8_storage_t v) {
+    return __half2float(__half(__nv_cvt_fp8_to_halfraw(v, __NV_E4M3)));
+}
+template <> __device__ __forceinline__ float to_acc<__nv_bfloat16, float>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ float to_acc<__half, float>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float to_acc<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_acc<double, float>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ double to_acc<double, double>(double v) { return v; }
+template <> __device__ __forceinline__ double to_acc<float, double>(float v) { return (double)v; }
+
+// ---- sketch.cu --------------------------------------------------------------
+lsq_status launch_sparse_gen(uint64_t seed, int64_t m, int64_t s, int zeta, int32_t* idx, int8_t* sgn, int32_t* err,
+                             cudaStream_t st);
+int sort_cap_for(int64_t m, int64_t s, int zeta);
+lsq_status launch_sparse_csr(const int32_t* idx, const int8_t* sgn, int64_t m, int64_t s, int zeta, int32_t* counts,
+                             int32_t* rowptr, int32_t* cursor, uint32_t* col, int32_t* maxcount, int32_t* err,
+                             cudaStream_t st);
+lsq_status launch_colexp(const double* A, int64_t m, int64_t n, int64_t lda, int prec, unsigned long long* colmax,
+                         int32_t* colexp, cudaStream_t st);
+lsq_status launch_quantize_rm(const double* A, int64_t m, int64_t n, int64_t lda, const int32_t* colexp, int prec,
+                              void* out, cudaStream_t st);
+lsq_status launch_quantize_cm(const double* A, int64_t m, int64_t n, int64_t lda, const int32_t* colexp, int prec,
+                              void* out, int64_t ldq, cudaStream_t st);
+lsq_status launch_sparse_gather(const int32_t* rowptr, const uint32_t* col, const void* Ahat, int prec, int64_t s,
+                                int64_t n, void* As, int64_t ldas, cudaStream_t st);
+lsq_status launch_gauss_gen(uint64_t seed, int64_t s, int64_t m, int prec, void* Om, int64_t ldo, cudaStream_t st);
+lsq_status launch_gauss_inspect(uint64_t seed, int64_t s, int64_t m, int prec, double* Om, cudaStream_t st);
+
+// ---- gemm.cu: dense contractions on CUDA cores ------------------------------
+// C (M x N, column-major, ldc) = sum_k X[i*ldx + k] * Y[j*ldy + k]  (both
+// operands K-contiguous), split over K into `splits` partial products reduced
+// in a fixed order.  sym: only tiles i >= j are computed and C is mirrored.
+// xprec/yprec: storage precision of X/Y (lsq_prec); acc: LSQ_FP32 or LSQ_FP64.
+struct GemmPlan {
+    int64_t M, N, K;
+    int splits;
+    int64_t kchunk;
+    bool sym;
+    int acc;
+};
+GemmPlan plan_gemm_kmajor(int64_t M, int64_t N, int64_t K, bool sym, int acc, int num_sms);
+size_t gemm_kmajor_ws_bytes(const GemmPlan& p);
+lsq_status launch_gemm_kmajor(const GemmPlan& p, const void* X, int xprec, int64_t ldx, const void* Y, int yprec,
+                              int64_t ldy, void* C, int64_t ldc, void* ws, cudaStream_t st);
+
+// FP64 right triangular solve Ap = A R^{-1} (R upper, n x n).
+lsq_status launch_trsm_right_upper(const double* A, int64_t m, int64_t n, int64_t lda, const double* R, int64_t ldr,
+                                   double* Ap, int64_t ldap, cudaStream_t st);
+
+// c = X^T v over m rows (X column-major ldx), deterministic.
+lsq_status launch_gemv_t(const double* X, int64_t m, int64_t n, int64_t ldx, const double* v, double* c,
+                         double* partial, int64_t max_partial, cudaStream_t st);
+size_t gemv_t_ws_bytes(int64_t m, int64_t n);
+// r = b - A x over m rows.
+lsq_status launch_residual(const double* A, int64_t m, int64_t n, int64_t lda, const double* x, const double* b,
+                           double* r, cudaStream_t st);
+// x += d
+lsq_status launch_axpy1(double* x, const double* d, int64_t n, cudaStream_t st);
+
+// ---- factor.cu: n x n factorizations and triangular solves ------------------
+template <typename T>
+lsq_status launch_cholesky(T* G, int64_t n, int64_t ld, int32_t* info, cudaStream_t st);
+lsq_status launch_lu(double* H, int64_t n, int64_t ld, int32_t* piv, int32_t* info, cudaStream_t st);
+enum TrsvKind { TRSV_LOWER = 0, TRSV_LOWER_T = 1, TRSV_UPPER = 2, TRSV_UNIT_LOWER = 3 };
+template <typename T>
+lsq_status launch_trsv(int kind, const T* M, int64_t n, int64_t ld, T* y, const int32_t* info, cudaStream_t st);
+lsq_status launch_apply_piv(const int32_t* piv, int64_t n, double* y, const int32_t* info, cudaStream_t st);
+
+template <typename T>
+lsq_status rank_update_ext(T* C, int64_t ldc, const T* P, int64_t psi, int64_t psk, const T* Q, int64_t qsj,
+                           int64_t qsk, int64_t M, int64_t N, int K, bool lower, const int32_t* info, cudaStream_t st);
+
+// ---- qr.cu -------------------------------------------------------------------
+size_t qr_ws_bytes(int64_t s, int64_t n, int prec);
+lsq_status launch_precond_qr(const void* As, int64_t s, int64_t n, int64_t ldas, int as_prec, int qr_prec,
+                             const int32_t* colexp, double* Rs, int64_t ldr, int32_t* info, void* ws, size_t ws_bytes,
+                             cudaStream_t st);
+
+// ---- condest.cu --------------------------------------------------------------
+size_t condest_ws_bytes(int64_t m, int64_t n, int num_sms);
+lsq_status launch_condest(const double* A, int64_t m, int64_t n, int64_t lda, double* kappa0, int32_t* chosen,
+                          void* ws, size_t ws_bytes, int num_sms, cudaStream_t st);
+
+int device_sm_count();
+
+}  // namespace lsq

@@ -1,0 +1,285 @@
+// Preconditioner of Alg. 1: thin QR of the sketch A_s (s x n) in FP32 or
+// FP64 arithmetic, R only, then promotion to FP64 and removal of the
+// column scaling.  Blocked Householder QR with the compact WY form
+// (Schreiber & Van Loan 1989):
+//   panel of QNB columns in one CTA (Householder vectors as in Golub & Van
+//   Loan Alg. 5.1.1, which maps x to +||x|| e1, so diag(R) >= 0), the
+//   triangular factor T of  H_1...H_nb = I - V T V^T, and the trailing update
+//   C <- (I - V T^T V^T) C as two contractions (W = V^T C, C -= V (T^T W)).
+#include "common.cuh"
+#include "kernels.cuh"
+
+#include <algorithm>
+
+namespace lsq {
+
+constexpr int QNB = 32;        // panel width
+constexpr int QPT = 512;       // panel threads
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red /* >= 32 */) {
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    T t = (T)0;
+    for (int w = 0; w < nw; ++w) t += red[w];  // same order in every thread
+    return t;
+}
+
+// Factor panel columns [k0, k0+nb) of W (s x n, ld), store v below the
+// diagonal (v_j = 1 implicit), R on and above, beta[j]; then build T (nb x
+// nb upper, ld QNB) and the explicit V (rows k0..s-1, ld ldv).
+template <typename T>
+__global__ void __launch_bounds__(QPT) k_qr_panel(T* __restrict__ W, int64_t ld, int64_t s, int64_t k0, int nb,
+                                                  T* __restrict__ beta, T* __restrict__ Tm, T* __restrict__ V,
+                                                  int64_t ldv) {
+    __shared__ T red[32];
+    __shared__ T wred[QPT / 32][QNB];
+    __shared__ T wcol[QNB];
+    __shared__ T sh_v1, sh_beta;
+    __shared__ int sh_scale;
+    __shared__ T Ys[QNB][QNB + 1];
+    __shared__ T Vs[32][QNB + 1];
+    __shared__ T Ts[QNB][QNB + 1];
+    int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int jj = 0; jj < nb; ++jj) {
+        int64_t j = k0 + jj;
+        T* colj = W + j * ld;
+        T sp = (T)0;
+        for (int64_t i = j + 1 + tid; i < s; i += QPT) sp = fma(colj[i], colj[i], sp);
+        T sigma = block_sum<T>(sp, red);
+        if (tid == 0) {
+            T x1 = colj[j];
+            T mu, b, v1 = (T)1;
+            int scale = 0;
+            if (sigma == (T)0) {
+                mu = fabs(x1);
+                b = x1 >= (T)0 ? (T)0 : (T)2;
+            } else {
+                mu = sqrt(x1 * x1 + sigma);
+                v1 = x1 <= (T)0 ? x1 - mu : -sigma / (x1 + mu);
+                b = (T)2 * v1 * v1 / (sigma + v1 * v1);
+                scale = 1;
+            }
+            colj[j] = mu;
+            beta[j] = b;
+            sh_v1 = v1;
+            sh_beta = b;
+            sh_scale = scale;
+        }
+        __syncthreads();
+        T v1 = sh_v1, b = sh_beta;
+        if (sh_scale)
+            for (int64_t i = j + 1 + tid; i < s; i += QPT) colj[i] = colj[i] / v1;
+        __syncthreads();
+        int rem = nb - jj - 1;
+        if (rem > 0 && b != (T)0) {
+            T acc[QNB];
+#pragma unroll
+            for (int c = 0; c < QNB; ++c) acc[c] = (T)0;
+            // w_c = W[j][c] + sum_{i>j} v_i W[i][c]
+            for (int64_t i = j + tid; i < s; i += QPT) {
+                T vi = (i == j) ? (T)1 : colj[i];
+#pragma unroll
+                for (int c = 0; c < QNB; ++c)
+                    if (c < rem) acc[c] = fma(vi, W[i + (j + 1 + c) * ld], acc[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < QNB; ++c) {
+                T v = acc[c];
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                if (lane == 0) wred[warp][c] = v;
+            }
+            __syncthreads();
+            if (tid < rem) {
+                T t = (T)0;
+                for (int w = 0; w < QPT / 32; ++w) t += wred[w][tid];
+                wcol[tid] = b * t;
+            }
+            __syncthreads();
+            for (int64_t i = j + tid; i < s; i += QPT) {
+                T vi = (i == j) ? (T)1 : colj[i];
+                for (int c = 0; c < rem; ++c) {
+                    T* p = &W[i + (j + 1 + c) * ld];
+                    *p = fma(-wcol[c], vi, *p);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // Y = V^T V over rows k0..s-1 (explicit zeros above, ones on the diagonal)
+    int p = tid >> 5, q = lane;  // 16 x 32 threads cover Y in two passes
+    T y0 = (T)0, y1 = (T)0;
+    for (int64_t r0 = k0; r0 < s; r0 += 32) {
+        for (int e = tid; e < 32 * QNB; e += QPT) {
+            int rr = e % 32, cc = e / 32;
+            int64_t i = r0 + rr;
+            T v = (T)0;
+            if (cc < nb && i < s) {
+                int64_t diag = k0 + cc;
+                v = i < diag ? (T)0 : (i == diag ? (T)1 : W[i + diag * ld]);
+            }
+            Vs[rr][cc] = v;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int rr = 0; rr < 32; ++rr) {
+            y0 = fma(Vs[rr][p], Vs[rr][q], y0);
+            y1 = fma(Vs[rr][p + 16], Vs[rr][q], y1);
+        }
+        // explicit V for the trailing contractions
+        for (int e = tid; e < 32 * QNB; e += QPT) {
+            int rr = e % 32, cc = e / 32;
+            int64_t i = r0 + rr;
+            if (i < s) V[(i - k0) + cc * ldv] = Vs[rr][cc];
+        }
+        __syncthreads();
+    }
+    Ys[p][q] = y0;
+    Ys[p + 16][q] = y1;
+    __syncthreads();
+    // T: T[j][j] = beta_j, T[0:j, j] = -beta_j T[0:j, 0:j] Y[0:j, j]
+    if (warp == 0) {
+        for (int c = 0; c < QNB; ++c) Ts[lane][c] = (T)0;
+        __syncwarp();
+        for (int jj = 0; jj < nb; ++jj) {
+            T bj = beta[k0 + jj];
+            T t = (T)0;
+            if (lane < jj)
+                for (int qq = lane; qq < jj; ++qq) t = fma(Ts[lane][qq], Ys[qq][jj], t);
+            __syncwarp();
+            if (lane < jj) Ts[lane][jj] = -bj * t;
+            if (lane == jj) Ts[jj][jj] = bj;
+            __syncwarp();
+        }
+        for (int c = 0; c < QNB; ++c) Tm[lane + c * QNB] = Ts[lane][c];
+    }
+}
+
+// W2 = T^T Wp  (nb x nt), T upper (ld QNB), Wp (nb x nt, ld nb).
+template <typename T>
+__global__ void k_qr_tw(const T* __restrict__ Tm, const T* __restrict__ Wp, int nb, int64_t nt, T* __restrict__ W2) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nb * nt) return;
+    int p = (int)(q % nb);
+    int64_t c = q / nb;
+    T t = (T)0;
+    for (int k = 0; k <= p; ++k) t = fma(Tm[k + p * QNB], Wp[k + c * nb], t);
+    W2[p + c * nb] = t;
+}
+
+template <typename TI, typename T>
+__global__ void k_qr_load(const TI* __restrict__ As, int64_t s, int64_t n, int64_t ldas, T* __restrict__ W) {
+    int64_t total = s * n;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q % s, j = q / s;
+        W[q] = (T)As[i + j * ldas];
+    }
+}
+
+template <typename T>
+__global__ void k_qr_extract(const T* __restrict__ W, int64_t ld, int64_t n, const int32_t* __restrict__ colexp,
+                             double* __restrict__ Rs, int64_t ldr) {
+    int64_t total = n * n;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q % n, j = q / n;
+        if (i <= j) {
+            double v = (double)W[i + j * ld];
+            Rs[i + j * ldr] = colexp ? ldexp(v, -colexp[j]) : v;
+        }
+    }
+}
+
+__global__ void k_check_diag(const double* __restrict__ Rs, int64_t n, int64_t ldr, int32_t* __restrict__ info) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double d = Rs[j + j * ldr];
+    if (!(d > 0.0) || !isfinite(d)) set_info_once(info, (int32_t)(j + 1));
+}
+
+struct QrLayout {
+    size_t w, beta, tm, v, wp, w2, gemm;
+    size_t total;
+};
+
+static QrLayout qr_layout(int64_t s, int64_t n, int es, int num_sms) {
+    QrLayout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    L.w = take((size_t)s * n * es);
+    L.beta = take((size_t)n * es);
+    L.tm = take((size_t)QNB * QNB * es);
+    L.v = take((size_t)s * QNB * es);
+    L.wp = take((size_t)QNB * n * es);
+    L.w2 = take((size_t)QNB * n * es);
+    (void)num_sms;
+    L.gemm = take((size_t)64 * QNB * n * es + 256);  // at most 64 split partials of nb x nt
+    L.total = off;
+    return L;
+}
+
+size_t qr_ws_bytes(int64_t s, int64_t n, int prec) {
+    int es = prec == LSQ_FP64 ? 8 : 4;
+    return qr_layout(s, n, es, device_sm_count()).total + 256;
+}
+
+template <typename T>
+static lsq_status qr_run(const void* As, int64_t s, int64_t n, int64_t ldas, int as_prec, const int32_t* colexp,
+                         double* Rs, int64_t ldr, int32_t* info, void* ws, size_t ws_bytes, cudaStream_t st) {
+    int es = sizeof(T);
+    int sms = device_sm_count();
+    QrLayout L = qr_layout(s, n, es, sms);
+    char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    if (!ws || L.total + ((char*)base - (char*)ws) > ws_bytes) return LSQ_ERR_NOMEM;
+    T* W = (T*)(base + L.w);
+    T* beta = (T*)(base + L.beta);
+    T* Tm = (T*)(base + L.tm);
+    T* V = (T*)(base + L.v);
+    T* Wp = (T*)(base + L.wp);
+    T* W2 = (T*)(base + L.w2);
+    void* gws = base + L.gemm;
+    unsigned g = (unsigned)std::min<int64_t>(ceil_div(s * n, 256), 8192);
+    if (as_prec == LSQ_FP64)
+        k_qr_load<double, T><<<g, 256, 0, st>>>((const double*)As, s, n, ldas, W);
+    else
+        k_qr_load<float, T><<<g, 256, 0, st>>>((const float*)As, s, n, ldas, W);
+    LSQ_LAUNCH_CHECK();
+    int accp = sizeof(T) == 8 ? LSQ_FP64 : LSQ_FP32;
+    for (int64_t k0 = 0; k0 < n; k0 += QNB) {
+        int nb = (int)std::min<int64_t>(QNB, n - k0);
+        int64_t rows = s - k0;
+        k_qr_panel<T><<<1, QPT, 0, st>>>(W, s, s, k0, nb, beta, Tm, V, rows);
+        LSQ_LAUNCH_CHECK();
+        int64_t nt = n - k0 - nb;
+        if (nt <= 0) continue;
+        T* C = W + k0 + (k0 + nb) * s;
+        // Wp = V^T C   (nb x nt; K = rows)
+        GemmPlan gp = plan_gemm_kmajor(nb, nt, rows, false, accp, sms);
+        lsq_status r = launch_gemm_kmajor(gp, V, sizeof(T) == 8 ? LSQ_FP64 : LSQ_FP32, rows, C,
+                                          sizeof(T) == 8 ? LSQ_FP64 : LSQ_FP32, s, Wp, nb, gws, st);
+        if (r != LSQ_OK) return r;
+        k_qr_tw<T><<<(unsigned)ceil_div(nb * nt, 256), 256, 0, st>>>(Tm, Wp, nb, nt, W2);
+        LSQ_LAUNCH_CHECK();
+        // C -= V W2:  P(i,p) = V[i + p rows],  Q(c,p) = W2[p + c nb]
+        r = rank_update_ext<T>(C, s, V, 1, rows, W2, nb, 1, rows, nt, nb, false, nullptr, st);
+        if (r != LSQ_OK) return r;
+    }
+    k_qr_extract<T><<<(unsigned)std::min<int64_t>(ceil_div(n * n, 256), 4096), 256, 0, st>>>(W, s, n, colexp, Rs, ldr);
+    LSQ_LAUNCH_CHECK();
+    if (info) {
+        k_check_diag<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(Rs, n, ldr, info);
+        LSQ_LAUNCH_CHECK();
+    }
+    return LSQ_OK;
+}
+
+lsq_status launch_precond_qr(const void* As, int64_t s, int64_t n, int64_t ldas, int as_prec, int qr_prec,
+                             const int32_t* colexp, double* Rs, int64_t ldr, int32_t* info, void* ws, size_t ws_bytes,
+                             cudaStream_t st) {
+    if (qr_prec == LSQ_FP64) return qr_run<double>(As, s, n, ldas, as_prec, colexp, Rs, ldr, info, ws, ws_bytes, st);
+    return qr_run<float>(As, s, n, ldas, as_prec, colexp, Rs, ldr, info, ws, ws_bytes, st);
+}
+
+}  // namespace lsq

@@ -1,0 +1,376 @@
+// Sketch step of Alg. 1 ("Sketch A_s = Omega A" in precision u_p):
+//   - sparse-sign operator generation (Philox4x32-10 + Lemire rejection),
+//   - deterministic CSR transpose of Omega (rows of Omega in ascending j),
+//   - per-column power-of-two scaling and rounding of A to u_p,
+//   - sparse-sign gather A_s[i,:] = sum_j Omega_ij Ahat[j,:] (FP32 or FP64
+//     accumulation in ascending j: bit-identical to a sequential sum),
+//   - Gaussian operator generation (Box-Muller in FP64, rounded to u_p).
+// The Gaussian product itself is a dense contraction (gemm.cu / sketch_tc.cu).
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace lsq {
+
+// ---------------------------------------------------------------------------
+// Sparse-sign operator: one thread per column j of Omega.
+// ---------------------------------------------------------------------------
+__global__ void k_sparse_gen(uint64_t seed, int64_t m, uint32_t s, int zeta, int32_t* __restrict__ idx,
+                             int8_t* __restrict__ sgn, int32_t* __restrict__ err) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    uint32_t thresh = (0u - s) % s;
+    int32_t got_idx[32];
+    int got = 0;
+    for (uint32_t blk = 0; got < zeta; ++blk) {
+        if (blk > (1u << 20)) { set_info_once(err, -2); return; }
+        U4 w = philox(U4{blk, (uint32_t)j, (uint32_t)((uint64_t)j >> 32), 0u}, k0, k1);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (got >= zeta) break;
+            uint64_t prod = (uint64_t)word_of(w, t) * (uint64_t)s;
+            if ((uint32_t)prod < thresh) continue;
+            int32_t cand = (int32_t)(prod >> 32);
+            bool dup = false;
+            for (int q = 0; q < got; ++q) dup |= (got_idx[q] == cand);
+            if (!dup) got_idx[got++] = cand;
+        }
+    }
+    U4 ws = philox(U4{0u, (uint32_t)j, (uint32_t)((uint64_t)j >> 32), 1u}, k0, k1);
+    for (int t = 0; t < zeta; ++t) {
+        idx[j * zeta + t] = got_idx[t];
+        sgn[j * zeta + t] = ((ws.x >> t) & 1u) ? (int8_t)-1 : (int8_t)1;
+    }
+}
+
+__global__ void k_count_rows(const int32_t* __restrict__ idx, int64_t nnz, int32_t* __restrict__ counts) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nnz) atomicAdd(&counts[idx[q]], 1);
+}
+
+// Exclusive scan of s counts -> rowptr[0..s]; one block of 1024 threads.
+__global__ void k_scan_rows(const int32_t* __restrict__ counts, int64_t s, int32_t* __restrict__ rowptr,
+                            int32_t* __restrict__ cursor, int32_t* __restrict__ maxcount) {
+    __shared__ int32_t part[1024];
+    __shared__ int32_t pmax[1024];
+    int tid = threadIdx.x;
+    int64_t per = ceil_div_dev(s, 1024);
+    int64_t lo = tid * per, hi = min(s, lo + per);
+    int32_t sum = 0, mx = 0;
+    for (int64_t i = lo; i < hi; ++i) { sum += counts[i]; mx = max(mx, counts[i]); }
+    part[tid] = sum;
+    pmax[tid] = mx;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        int32_t v = tid >= off ? part[tid - off] : 0;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    for (int off = 512; off > 0; off >>= 1) {
+        if (tid < off) pmax[tid] = max(pmax[tid], pmax[tid + off]);
+        __syncthreads();
+    }
+    int32_t run = part[tid] - sum;
+    for (int64_t i = lo; i < hi; ++i) { rowptr[i] = run; cursor[i] = run; run += counts[i]; }
+    if (tid == 1023) rowptr[s] = part[1023];
+    if (tid == 0) *maxcount = pmax[0];
+}
+
+// Scatter (j | sign bit) into row segments; order inside a segment is fixed
+// afterwards by k_sort_rows.
+__global__ void k_fill_rows(const int32_t* __restrict__ idx, const int8_t* __restrict__ sgn, int64_t m, int zeta,
+                            int32_t* __restrict__ cursor, uint32_t* __restrict__ col) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= m * zeta) return;
+    int64_t j = q / zeta;
+    int32_t r = idx[q];
+    int32_t pos = atomicAdd(&cursor[r], 1);
+    col[pos] = (uint32_t)j | (sgn[q] < 0 ? 0x80000000u : 0u);
+}
+
+// Sort each row segment by column index j (bitonic sort in shared memory).
+// Dynamic shared memory holds `cap` uint32 entries (cap a power of two).
+__global__ void k_sort_rows(const int32_t* __restrict__ rowptr, uint32_t* __restrict__ col, int cap,
+                            int32_t* __restrict__ err) {
+    extern __shared__ uint32_t seg[];
+    int64_t r = blockIdx.x;
+    int32_t lo = rowptr[r], hi = rowptr[r + 1];
+    int len = hi - lo;
+    if (len > cap) {
+        if (threadIdx.x == 0) set_info_once(err, -3);
+        return;
+    }
+    int pw = 1;
+    while (pw < len) pw <<= 1;
+    for (int i = threadIdx.x; i < pw; i += blockDim.x) seg[i] = i < len ? col[lo + i] : 0xffffffffu;
+    __syncthreads();
+    for (int k = 2; k <= pw; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int i = threadIdx.x; i < pw; i += blockDim.x) {
+                int p = i ^ jj;
+                if (p > i) {
+                    uint32_t a = seg[i], b = seg[p];
+                    uint32_t ka = a == 0xffffffffu ? a : (a & 0x7fffffffu);
+                    uint32_t kb = b == 0xffffffffu ? b : (b & 0x7fffffffu);
+                    bool up = (i & k) == 0;
+                    if ((ka > kb) == up) { seg[i] = b; seg[p] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < len; i += blockDim.x) col[lo + i] = seg[i];
+}
+
+// ---------------------------------------------------------------------------
+// Column scaling: colmax over rows (atomicMax on the bit pattern of a
+// non-negative double, which orders like the value), then the exponent.
+// ---------------------------------------------------------------------------
+__global__ void k_colmax(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda, int64_t rows_per_block,
+                         unsigned long long* __restrict__ colmax) {
+    int64_t c = blockIdx.y;
+    int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+    int64_t r1 = min(m, r0 + rows_per_block);
+    double mx = 0.0;
+    const double* col = A + c * lda;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) mx = fmax(mx, fabs(col[i]));
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    __shared__ double wmax[32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+        if (threadIdx.x == 0) atomicMax(&colmax[c], (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+__global__ void k_colexp(const unsigned long long* __restrict__ colmax, int64_t n, int prec, int32_t* __restrict__ e) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    double mx = __longlong_as_double((long long)colmax[c]);
+    int t = prec == LSQ_FP8_E4M3 ? 8 : (prec == LSQ_FP16 ? 15 : 0);
+    if (prec == LSQ_FP64 || mx == 0.0 || !isfinite(mx)) { e[c] = 0; return; }
+    int E;
+    frexp(mx, &E);
+    e[c] = t - E;
+}
+
+// Ahat in ROW-major order (n contiguous per row j), for the sparse gather.
+// 32x32 tiles through shared memory so both the read of column-major A and
+// the write are coalesced.
+__global__ void k_quantize_rm(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda,
+                              const int32_t* __restrict__ colexp, int prec, void* __restrict__ out) {
+    __shared__ double tile[32][33];
+    int64_t j0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+    int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int k = ty; k < 32; k += 8) {
+        int64_t j = j0 + tx, c = c0 + k;
+        double v = 0.0;
+        if (j < m && c < n) v = round_to_prec(ldexp(A[j + c * lda], colexp[c]), prec);
+        tile[k][tx] = v;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        int64_t j = j0 + k, c = c0 + tx;
+        if (j < m && c < n) store_prec(out, (size_t)j * n + c, tile[tx][k], prec);
+    }
+}
+
+// Ahat in COLUMN-major order with leading dimension ldq (K-major operand of
+// the Gaussian sketch GEMM).
+__global__ void k_quantize_cm(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda,
+                              const int32_t* __restrict__ colexp, int prec, void* __restrict__ out, int64_t ldq) {
+    int64_t c = blockIdx.y;
+    int e = colexp[c];
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < ldq; j += (int64_t)gridDim.x * blockDim.x) {
+        double v = j < m ? round_to_prec(ldexp(A[j + c * lda], e), prec) : 0.0;
+        store_prec(out, (size_t)c * ldq + j, v, prec);
+    }
+}
+
+// Sparse-sign gather, one block per sketch row i: acc[c] = sum over the row's
+// nonzeros (ascending j) of +-Ahat[j, c]; FP32 accumulation for low
+// precisions, FP64 for FP64.  As column-major (ld ldas), float or double.
+template <typename TS, typename TACC>
+__global__ void k_sparse_gather(const int32_t* __restrict__ rowptr, const uint32_t* __restrict__ col,
+                                const TS* __restrict__ Ahat, int64_t n, TACC* __restrict__ As, int64_t ldas) {
+    __shared__ uint32_t ent[256];
+    int64_t i = blockIdx.x;
+    int32_t lo = rowptr[i], hi = rowptr[i + 1];
+    for (int64_t c0 = 0; c0 < n; c0 += (int64_t)blockDim.x * 4) {
+        TACC acc[4] = {0, 0, 0, 0};
+        for (int32_t k0 = lo; k0 < hi; k0 += 256) {
+            int cnt = min(256, hi - k0);
+            __syncthreads();
+            if (threadIdx.x < cnt) ent[threadIdx.x] = col[k0 + threadIdx.x];
+            __syncthreads();
+            for (int q = 0; q < cnt; ++q) {
+                uint32_t e = ent[q];
+                const TS* row = Ahat + (size_t)(e & 0x7fffffffu) * n;
+                bool neg = (e >> 31) != 0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    int64_t c = c0 + (int64_t)u * blockDim.x + threadIdx.x;
+                    if (c < n) {
+                        TACC v = (TACC)to_acc<TS, TACC>(row[c]);
+                        acc[u] = neg ? acc[u] - v : acc[u] + v;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int64_t c = c0 + (int64_t)u * blockDim.x + threadIdx.x;
+            if (c < n) As[i + c * ldas] = acc[u];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gaussian operator: Omega_hat[i, j] = round_p(sqrt(-2 ln u1) cos(2 pi u2)),
+// written ROW-major (ld ldo >= m, K-major operand of the sketch GEMM), or as
+// FP64 column-major for inspection.  Products and sums are explicitly
+// rounded (no contraction) so the FP64 value matches a plain sequential
+// evaluation up to the accuracy of log and cos.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double gauss_entry(uint64_t seed, int64_t i, int64_t j) {
+    U4 w = philox(U4{(uint32_t)i, (uint32_t)j, (uint32_t)((uint64_t)j >> 32), 2u}, (uint32_t)seed,
+                  (uint32_t)(seed >> 32));
+    uint64_t a = w.x >> 5, b = w.y >> 6;
+    double u1 = __dmul_rn(__dadd_rn((double)(a * 67108864ull + b), 1.0), 0x1p-53);
+    a = w.z >> 5;
+    b = w.w >> 6;
+    double u2 = __dmul_rn((double)(a * 67108864ull + b), 0x1p-53);
+    double rad = sqrt(__dmul_rn(-2.0, log(u1)));
+    double th = __dmul_rn(6.283185307179586, u2);
+    return __dmul_rn(rad, cos(th));
+}
+
+__global__ void k_gauss_gen(uint64_t seed, int64_t s, int64_t m, int prec, void* __restrict__ Om, int64_t ldo) {
+    int64_t i = blockIdx.y;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < ldo; j += (int64_t)gridDim.x * blockDim.x) {
+        double v = j < m ? round_to_prec(gauss_entry(seed, i, j), prec) : 0.0;
+        store_prec(Om, (size_t)i * ldo + j, v, prec);
+    }
+}
+
+__global__ void k_gauss_inspect(uint64_t seed, int64_t s, int64_t m, int prec, double* __restrict__ Om) {
+    int64_t total = s * m;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q % s, j = q / s;
+        Om[q] = round_to_prec(gauss_entry(seed, i, j), prec);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+lsq_status launch_sparse_gen(uint64_t seed, int64_t m, int64_t s, int zeta, int32_t* idx, int8_t* sgn, int32_t* err,
+                             cudaStream_t st) {
+    k_sparse_gen<<<(unsigned)ceil_div(m, 128), 128, 0, st>>>(seed, m, (uint32_t)s, zeta, idx, sgn, err);
+    LSQ_LAUNCH_CHECK();
+    return LSQ_OK;
+}
+
+int sort_cap_for(int64_t m, int64_t s, int zeta) {
+    // mean + generous slack; segments above the cap are reported via err = -3
+    double mean = (double)m * zeta / (double)s;
+    double want = mean + 12.0 * sqrt(mean + 1.0) + 64.0;
+    int cap = 256;
+    while (cap < want && cap < 16384) cap <<= 1;
+    return cap;
+}
+
+lsq_status launch_sparse_csr(const int32_t* idx, const int8_t* sgn, int64_t m, int64_t s, int zeta, int32_t* counts,
+                             int32_t* rowptr, int32_t* cursor, uint32_t* col, int32_t* maxcount, int32_t* err,
+                             cudaStream_t st) {
+    LSQ_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)s, st));
+    int64_t nnz = m * zeta;
+    k_count_rows<<<(unsigned)ceil_div(nnz, 256), 256, 0, st>>>(idx, nnz, counts);
+    LSQ_LAUNCH_CHECK();
+    k_scan_rows<<<1, 1024, 0, st>>>(counts, s, rowptr, cursor, maxcount);
+    LSQ_LAUNCH_CHECK();
+    k_fill_rows<<<(unsigned)ceil_div(nnz, 256), 256, 0, st>>>(idx, sgn, m, zeta, cursor, col);
+    LSQ_LAUNCH_CHECK();
+    int cap = sort_cap_for(m, s, zeta);
+    size_t smem = sizeof(uint32_t) * (size_t)cap;
+    if (smem > 48 * 1024) LSQ_CUDA_TRY(cudaFuncSetAttribute(k_sort_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_sort_rows<<<(unsigned)s, 256, smem, st>>>(rowptr, col, cap, err);
+    LSQ_LAUNCH_CHECK();
+    return LSQ_OK;
+}
+
+lsq_status launch_colexp(const double* A, int64_t m, int64_t n, int64_t lda, int prec, unsigned long long* colmax,
+                         int32_t* colexp, cudaStream_t st) {
+    LSQ_CUDA_TRY(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)n, st));
+    int64_t rpb = 8192;
+    dim3 grid((unsigned)ceil_div(m, rpb), (unsigned)n);
+    k_colmax<<<grid, 256, 0, st>>>(A, m, n, lda, rpb, colmax);
+    LSQ_LAUNCH_CHECK();
+    k_colexp<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(colmax, n, prec, colexp);
+    LSQ_LAUNCH_CHECK();
+    return LSQ_OK;
+}
+
+lsq_status launch_quantize_rm(const double* A, int64_t m, int64_t n, int64_t lda, const int32_t* colexp, int prec,
+                              void* out, cudaStream_t st) {
+    dim3 grid((unsigned)ceil_div(m, 32), (unsigned)ceil_div(n, 32));
+    k_quantize_rm<<<grid, dim3(32, 8), 0, st>>>(A, m, n, lda, colexp, prec, out);
+    LSQ_LAUNCH_CHECK();
+    return LSQ_OK;
+}
+
+lsq_status launch_quantize_cm(const double* A, int64_t m, int64_t n, int64_t lda, const int32_t* colexp, int prec,
+                              void* out, int64_t ldq, cudaStream_t st) {
+    dim3 grid((unsigned)min64(ceil_div(ldq, 256), 64), (unsigned)n);
+    k_quantize_cm<<<grid, 256, 0, st>>>(A, m, n, lda, colexp, prec, out, ldq);
+    LSQ_LAUNCH_CHECK();
+    return LSQ_OK;
+}
+
+lsq_status launch_sparse_gather(const int32_t* rowptr, const uint32_t* col, const void* Ahat, int prec, int64_t s,
+                                int64_t n, void* As, int64_t ldas, cudaStream_t st) {
+    int threads = 256;
+    switch (prec) {
+    case LSQ_FP8_E4M3:
+        k_sparse_gather<__nv_fp8_storage_t, float><<<(unsigned)s, threads, 0, st>>>(
+            rowptr, col, (const __nv_fp8_storage_t*)Ahat, n, (float*)As, ldas);
+        break;
+    case LSQ_BF16:
+        k_sparse_gather<__nv_bfloat16, float><<<(unsigned)s, threads, 0, st>>>(rowptr, col, (const __nv_bfloat16*)Ahat,
+                                                                              n, (float*)As, ldas);
+        break;
+    case LSQ_FP16:
+        k_sparse_gather<__half, float><<<(unsigned)s, threads, 0, st>>>(rowptr, col, (const __half*)Ahat, n,
+                                                                       (float*)As, ldas);
+        break;
+    case LSQ_FP32:
+        k_sparse_gather<float, float><<<(unsigned)s, threads, 0, st>>>(rowptr, col, (const float*)Ahat, n, (float*)As,
+                                                                      ldas);
+        break;
+    default:
+        k_sparse_gather<double, double><<<(unsigned)s, threads, 0, st>>>(rowptr, col, (const double*)Ahat, n,
+                                                                        (double*)As, ldas);
+        break;
+    }
+    LSQ_LAUNCH_CHECK();
+    return LSQ_OK;
+}
+
+lsq_status launch_gauss_gen(uint64_t seed, int64_t s, int64_t m, int prec, void* Om, int64_t ldo, cudaStream_t st) {
+    dim3 grid((unsigned)min64(ceil_div(ldo, 256), 128), (unsigned)s);
+    k_gauss_gen<<<grid, 256, 0, st>>>(seed, s, m, prec, Om, ldo);
+    LSQ_LAUNCH_CHECK();
+    return LSQ_OK;
+}
+
+lsq_status launch_gauss_inspect(uint64_t seed, int64_t s, int64_t m, int prec, double* Om, cudaStream_t st) {
+    unsigned grid = (unsigned)min64(ceil_div(s * m, 256), 8192);
+    k_gauss_inspect<<<grid, 256, 0, st>>>(seed, s, m, prec, Om);
+    LSQ_LAUNCH_CHECK();
+    return LSQ_OK;
+}
+
+}  // namespace lsq

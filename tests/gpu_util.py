@@ -1,0 +1,31 @@
+"""Helpers for the GPU parity tests (CUDA path vs the CPU oracle)."""
+import numpy as np
+import torch
+
+import problems as P
+
+
+def dev_colmajor(A_np):
+    import paper_2603_16644_gb300 as lsq
+
+    return lsq.colmajor(torch.from_numpy(np.ascontiguousarray(A_np)).cuda())
+
+
+def to_np(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def assert_solution_parity(x_gpu, x_orc, x_star, kappa, rho, what=""):
+    """Solution tolerance of the method: relative difference 1e-12 from the
+    oracle when kappa(A) <= 1e4 and the residual is zero; otherwise the error
+    against x_* within 2x the oracle's own error against x_*."""
+    x_gpu = np.asarray(x_gpu)
+    assert np.all(np.isfinite(x_gpu)), what
+    if kappa <= 1e4 and rho == 0.0:
+        d = np.linalg.norm(x_gpu - x_orc) / np.linalg.norm(x_orc)
+        assert d <= 1e-12, (what, d)
+    else:
+        e_g = P.rel_error(x_gpu, x_star)
+        e_o = P.rel_error(x_orc, x_star)
+        assert e_g <= 2.0 * e_o + 1e-15, (what, e_g, e_o)
