@@ -179,6 +179,29 @@ lsq_status lsq_trsm_gram(const double* A, int64_t m, int64_t n, int64_t lda, con
                          double* G, int64_t ldg, double* c, void* ws, size_t ws_bytes,
                          void* stream);
 
+/* lsq_trsm_gram without a workspace and without allocating.  The paper has
+ * no counterpart: this is an interface for callers that cannot allocate
+ * device memory where they call (inside an allocator or memory-pool
+ * callback, in a framework that owns every device allocation, or in a loop
+ * that must not take cudaMalloc's implicit device synchronisation).  They
+ * pass the same inputs and outputs as lsq_trsm_gram; the scratch (split-K
+ * partial Gram matrices and GEMV partial sums) is a fixed 16 MiB array that
+ * every GPU loading the library holds until the process exits.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream
+ *     capture.
+ *   - Sizes whose GEMV partial sums, 8 * ceil(m / 16384) * n bytes, exceed
+ *     16 MiB are rejected with LSQ_ERR_ARG; the split-K count is capped so
+ *     the partial Gram matrices fit in the rest, so large n runs with fewer
+ *     splits (slower, same result up to summation order).
+ *   - All calls share the one array and it keeps the last call's contents;
+ *     every value read is first written by the same call, but calls that
+ *     overlap on the GPU (concurrent streams) race on it.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called. */
+lsq_status lsq_trsm_gram_noalloc(const double* A, int64_t m, int64_t n, int64_t lda, const double* Rs,
+                                 int64_t ldr, const double* b, int32_t hpne, double* Ap, int64_t ldap,
+                                 double* G, int64_t ldg, double* c, void* stream);
+
 /* Factor and solve (Eqs. e_pne / e_hpne, right-hand parts), in FP64:
  *   hpne = 0: Cholesky G = L L^T, L L^T y = c, then Rs x = y (Rs may be
  *             NULL: x = y);
