@@ -273,3 +273,60 @@ def solve(A, b, *, hpne=False, kind=SPARSE_SIGN, s=None, zeta=8, seed=0, sketch_
 def kappa(M):
     s = np.linalg.svd(np.asarray(M), compute_uv=False)
     return float(s[0] / s[-1]) if s[-1] > 0 else math.inf
+
+
+# --- learned precision proposal ----------------------------------------------
+N_FEATURES = 10
+CLASSES = [FP8_E4M3, BF16, FP32, FP64]
+
+
+def _mlp_sigs():
+    L = lib()
+    L.lsqo_mlp_param_count.restype = C.c_int64
+    L.lsqo_mlp_param_count.argtypes = [C.c_int]
+    L.lsqo_mlp_forward.restype = C.c_double
+    L.lsqo_mlp_forward.argtypes = [_d, C.c_int, C.c_int, _d, _i32, _d]
+    L.lsqo_mlp_backward.restype = C.c_double
+    L.lsqo_mlp_backward.argtypes = [_d, C.c_int, C.c_int, _d, _i32, _d]
+    L.lsqo_features.restype = C.c_int
+    L.lsqo_features.argtypes = [_d, _i64, _i64, _i64, C.c_uint64, _d]
+    return L
+
+
+def mlp_param_count(d):
+    return int(_mlp_sigs().lsqo_mlp_param_count(d))
+
+
+def mlp_forward(params, X, labels=None):
+    """(logits (batch x 4), mean cross-entropy or None)."""
+    L = _mlp_sigs()
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    B, d = X.shape
+    out = np.zeros((B, 4))
+    lab = np.ascontiguousarray(labels, dtype=np.int32) if labels is not None else None
+    loss = L.lsqo_mlp_forward(_p(params), d, B, _p(X), _p(lab, C.c_int32) if lab is not None else None, _p(out))
+    return out, (loss if lab is not None else None)
+
+
+def mlp_backward(params, X, labels):
+    """(mean cross-entropy, gradient with the packing of params)."""
+    L = _mlp_sigs()
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    B, d = X.shape
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    g = np.zeros_like(params)
+    loss = L.lsqo_mlp_backward(_p(params), d, B, _p(X), _p(lab, C.c_int32), _p(g))
+    return loss, g
+
+
+def features(A, seed):
+    L = _mlp_sigs()
+    A = _f64(A)
+    m, n = A.shape
+    f = np.zeros(N_FEATURES)
+    rc = L.lsqo_features(_p(A), m, n, m, C.c_uint64(seed), _p(f))
+    if rc:
+        raise ValueError(f"features rc={rc}")
+    return f

@@ -787,3 +787,210 @@ int lsqo_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double*
     free(As); free(ce); free(R); free(Ap); free(G); free(c); free(r); free(piv);
     return rc ? -1 : info;
 }
+
+/* ------------------------------------------------------------------------
+ * Learned precision proposal (not in the paper): a multilayer perceptron
+ * d -> 64 -> 64 -> 64 -> 4 with ReLU hidden layers and a softmax
+ * cross-entropy loss, in FP64.  Parameters are packed layer by layer as
+ * W_l (out x in, row-major) followed by b_l (out).
+ * ---------------------------------------------------------------------- */
+#define MLP_H 64
+#define MLP_C 4
+
+int64_t lsqo_mlp_param_count(int d)
+{
+    return (int64_t)MLP_H * d + MLP_H + 2 * ((int64_t)MLP_H * MLP_H + MLP_H) + (int64_t)MLP_C * MLP_H + MLP_C;
+}
+
+static void mlp_layer(const double* W, const double* b, int out, int in, const double* x, double* z)
+{
+    for (int o = 0; o < out; ++o) {
+        double acc = b[o];
+        for (int i = 0; i < in; ++i) acc += W[(int64_t)o * in + i] * x[i];
+        z[o] = acc;
+    }
+}
+
+/* Forward pass for `batch` rows of X (batch x d, row-major) -> logits
+ * (batch x 4).  Returns the mean cross-entropy if labels != NULL. */
+double lsqo_mlp_forward(const double* params, int d, int batch, const double* X, const int32_t* labels,
+                        double* logits)
+{
+    const double* W1 = params;
+    const double* b1 = W1 + MLP_H * d;
+    const double* W2 = b1 + MLP_H;
+    const double* b2 = W2 + MLP_H * MLP_H;
+    const double* W3 = b2 + MLP_H;
+    const double* b3 = W3 + MLP_H * MLP_H;
+    const double* W4 = b3 + MLP_H;
+    const double* b4 = W4 + MLP_C * MLP_H;
+    double h1[MLP_H], h2[MLP_H], h3[MLP_H], z[MLP_C];
+    double loss = 0.0;
+    for (int s = 0; s < batch; ++s) {
+        mlp_layer(W1, b1, MLP_H, d, X + (int64_t)s * d, h1);
+        for (int o = 0; o < MLP_H; ++o) h1[o] = h1[o] > 0.0 ? h1[o] : 0.0;
+        mlp_layer(W2, b2, MLP_H, MLP_H, h1, h2);
+        for (int o = 0; o < MLP_H; ++o) h2[o] = h2[o] > 0.0 ? h2[o] : 0.0;
+        mlp_layer(W3, b3, MLP_H, MLP_H, h2, h3);
+        for (int o = 0; o < MLP_H; ++o) h3[o] = h3[o] > 0.0 ? h3[o] : 0.0;
+        mlp_layer(W4, b4, MLP_C, MLP_H, h3, z);
+        if (logits)
+            for (int c = 0; c < MLP_C; ++c) logits[(int64_t)s * MLP_C + c] = z[c];
+        if (labels) {
+            double mx = z[0];
+            for (int c = 1; c < MLP_C; ++c) if (z[c] > mx) mx = z[c];
+            double se = 0.0;
+            for (int c = 0; c < MLP_C; ++c) se += exp(z[c] - mx);
+            loss += -(z[labels[s]] - mx - log(se));
+        }
+    }
+    return labels ? loss / batch : 0.0;
+}
+
+/* Gradient of the mean cross-entropy with respect to every parameter
+ * (same packing), by backpropagation.  Returns the loss. */
+double lsqo_mlp_backward(const double* params, int d, int batch, const double* X, const int32_t* labels,
+                         double* grad)
+{
+    const double* W1 = params;
+    const double* b1 = W1 + MLP_H * d;
+    const double* W2 = b1 + MLP_H;
+    const double* b2 = W2 + MLP_H * MLP_H;
+    const double* W3 = b2 + MLP_H;
+    const double* b3 = W3 + MLP_H * MLP_H;
+    const double* W4 = b3 + MLP_H;
+    const double* b4 = W4 + MLP_C * MLP_H;
+    double* gW1 = grad;
+    double* gb1 = gW1 + MLP_H * d;
+    double* gW2 = gb1 + MLP_H;
+    double* gb2 = gW2 + MLP_H * MLP_H;
+    double* gW3 = gb2 + MLP_H;
+    double* gb3 = gW3 + MLP_H * MLP_H;
+    double* gW4 = gb3 + MLP_H;
+    double* gb4 = gW4 + MLP_C * MLP_H;
+    int64_t np = lsqo_mlp_param_count(d);
+    for (int64_t q = 0; q < np; ++q) grad[q] = 0.0;
+    double z1[MLP_H], z2[MLP_H], z3[MLP_H], h1[MLP_H], h2[MLP_H], h3[MLP_H], z[MLP_C];
+    double d4[MLP_C], d3[MLP_H], d2[MLP_H], d1[MLP_H];
+    double loss = 0.0;
+    for (int s = 0; s < batch; ++s) {
+        const double* x = X + (int64_t)s * d;
+        mlp_layer(W1, b1, MLP_H, d, x, z1);
+        for (int o = 0; o < MLP_H; ++o) h1[o] = z1[o] > 0.0 ? z1[o] : 0.0;
+        mlp_layer(W2, b2, MLP_H, MLP_H, h1, z2);
+        for (int o = 0; o < MLP_H; ++o) h2[o] = z2[o] > 0.0 ? z2[o] : 0.0;
+        mlp_layer(W3, b3, MLP_H, MLP_H, h2, z3);
+        for (int o = 0; o < MLP_H; ++o) h3[o] = z3[o] > 0.0 ? z3[o] : 0.0;
+        mlp_layer(W4, b4, MLP_C, MLP_H, h3, z);
+        double mx = z[0];
+        for (int c = 1; c < MLP_C; ++c) if (z[c] > mx) mx = z[c];
+        double se = 0.0;
+        for (int c = 0; c < MLP_C; ++c) se += exp(z[c] - mx);
+        loss += -(z[labels[s]] - mx - log(se));
+        for (int c = 0; c < MLP_C; ++c) d4[c] = (exp(z[c] - mx) / se - (c == labels[s] ? 1.0 : 0.0)) / batch;
+        for (int i = 0; i < MLP_H; ++i) {
+            double t = 0.0;
+            for (int c = 0; c < MLP_C; ++c) t += W4[(int64_t)c * MLP_H + i] * d4[c];
+            d3[i] = z3[i] > 0.0 ? t : 0.0;
+        }
+        for (int i = 0; i < MLP_H; ++i) {
+            double t = 0.0;
+            for (int o = 0; o < MLP_H; ++o) t += W3[(int64_t)o * MLP_H + i] * d3[o];
+            d2[i] = z2[i] > 0.0 ? t : 0.0;
+        }
+        for (int i = 0; i < MLP_H; ++i) {
+            double t = 0.0;
+            for (int o = 0; o < MLP_H; ++o) t += W2[(int64_t)o * MLP_H + i] * d2[o];
+            d1[i] = z1[i] > 0.0 ? t : 0.0;
+        }
+        for (int c = 0; c < MLP_C; ++c) {
+            gb4[c] += d4[c];
+            for (int i = 0; i < MLP_H; ++i) gW4[(int64_t)c * MLP_H + i] += d4[c] * h3[i];
+        }
+        for (int o = 0; o < MLP_H; ++o) {
+            gb3[o] += d3[o];
+            gb2[o] += d2[o];
+            gb1[o] += d1[o];
+            for (int i = 0; i < MLP_H; ++i) {
+                gW3[(int64_t)o * MLP_H + i] += d3[o] * h2[i];
+                gW2[(int64_t)o * MLP_H + i] += d2[o] * h1[i];
+            }
+            for (int i = 0; i < d; ++i) gW1[(int64_t)o * d + i] += d1[o] * x[i];
+        }
+    }
+    return loss / batch;
+}
+
+/* Features of A for the precision proposal, in FP64 (feature k):
+ *  0 log2(m) / 16, 1 log2(n) / 10,
+ *  2 log10(max/min column 2-norm), 3 std of log10 column norms,
+ *  4 log10(max/min |diag R|), 5 std of log10 |diag R|,
+ *  6 least-squares slope of log10 |diag R_j| against j / n,
+ *  7 log10(max/min |diag R|) over the last quarter of the columns,
+ *  8 fraction of columns with |diag R_j| < 1e-2 max |diag R|,
+ *  9 log10(min |diag R| / (||A||_F / sqrt(n))).
+ * diag R is the diagonal of the preconditioner from an FP8-e4m3 sparse-sign
+ * sketch (s = min(2n, m), zeta = min(8, s)) and an FP32 QR, unscaled. */
+int lsqo_features(const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed, double* f)
+{
+    int64_t s = 2 * n < m ? 2 * n : m;
+    int zeta = s < 8 ? (int)s : 8;
+    double* As = (double*)malloc(sizeof(double) * (size_t)s * (size_t)n);
+    int32_t* ce = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    double* R = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    double* cn = (double*)malloc(sizeof(double) * (size_t)n);
+    double* ld = (double*)malloc(sizeof(double) * (size_t)n);
+    int rc = lsqo_sketch(A, m, n, lda, O_SPARSE_SIGN, s, zeta, seed, O_FP8, As, ce);
+    if (!rc) rc = lsqo_qr_r(As, s, n, s, O_FP32, R);
+    if (!rc) {
+        lsqo_unscale_r(R, n, n, ce);
+        double fro = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double t = 0.0;
+            for (int64_t i = 0; i < m; ++i) t += A[IDX(i, j, lda)] * A[IDX(i, j, lda)];
+            fro += t;
+            cn[j] = log10(sqrt(t) > 1e-300 ? sqrt(t) : 1e-300);
+            double dj = fabs(R[IDX(j, j, n)]);
+            ld[j] = log10(dj > 1e-300 ? dj : 1e-300);
+        }
+        double cmax = cn[0], cmin = cn[0], cmean = 0.0, dmax = ld[0], dmin = ld[0], dmean = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (cn[j] > cmax) cmax = cn[j];
+            if (cn[j] < cmin) cmin = cn[j];
+            if (ld[j] > dmax) dmax = ld[j];
+            if (ld[j] < dmin) dmin = ld[j];
+            cmean += cn[j];
+            dmean += ld[j];
+        }
+        cmean /= n;
+        dmean /= n;
+        double cvar = 0.0, dvar = 0.0, sxy = 0.0, sxx = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double t = (double)j / (double)n - 0.5 * (double)(n - 1) / (double)n;
+            cvar += (cn[j] - cmean) * (cn[j] - cmean);
+            dvar += (ld[j] - dmean) * (ld[j] - dmean);
+            sxy += t * (ld[j] - dmean);
+            sxx += t * t;
+        }
+        int64_t q0 = n - (n + 3) / 4;
+        double tmax = ld[q0], tmin = ld[q0];
+        for (int64_t j = q0; j < n; ++j) {
+            if (ld[j] > tmax) tmax = ld[j];
+            if (ld[j] < tmin) tmin = ld[j];
+        }
+        int64_t small = 0;
+        for (int64_t j = 0; j < n; ++j) small += (ld[j] < dmax - 2.0);
+        f[0] = log2((double)m) / 16.0;
+        f[1] = log2((double)n) / 10.0;
+        f[2] = cmax - cmin;
+        f[3] = sqrt(cvar / n);
+        f[4] = dmax - dmin;
+        f[5] = sqrt(dvar / n);
+        f[6] = sxx > 0.0 ? sxy / sxx : 0.0;
+        f[7] = tmax - tmin;
+        f[8] = (double)small / (double)n;
+        f[9] = dmin - log10(sqrt(fro / (double)n) > 1e-300 ? sqrt(fro / (double)n) : 1e-300);
+    }
+    free(As); free(ce); free(R); free(cn); free(ld);
+    return rc;
+}
