@@ -47,7 +47,41 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=6)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-rows", type=int, default=4096, help="rows of the oracle sample")
+    p.add_argument("--ncu-case", choices=["trsm_gram", "pne", "qr"], default=None,
+                   help="run a bounded case for an ncu capture (2 calls on one problem of the workload shape) and exit")
     return p.parse_args()
+
+
+def ncu_case(args):
+    """Two calls of one step on one 65536 x 1024 problem (about 1.5 GB on the
+    device): the first warms up, the second is the one to capture."""
+    import torch
+
+    import paper_2603_16644_gb300 as lsq
+    import problems as P
+
+    torch.cuda.set_device(0)
+    # Gaussian A: the kernels' cost does not depend on the conditioning, and
+    # this avoids torch's linear-algebra library under the profiler.
+    g = torch.Generator(device="cuda").manual_seed(P.seed_for(1, 4))
+    A = torch.randn((N, M), generator=g, dtype=torch.float64, device="cuda").t()
+    b = torch.randn(M, generator=g, dtype=torch.float64, device="cuda")
+    opts = opts_for(lsq, lsq.BF16, P.seed_for(1, 4))
+    if args.ncu_case == "pne":
+        ws = lsq.workspace(lsq.OP_PNE, M, N, opts)
+        for _ in range(2):
+            lsq.pne(A, b, opts=opts, ws=ws)
+    else:
+        As, ce, _ = lsq.sketch(A, opts)
+        for _ in range(2):
+            Rs, _ = lsq.precond_qr(As, ce, lsq.FP32)
+        if args.ncu_case == "trsm_gram":
+            ws = lsq.workspace(lsq.OP_TRSM_GRAM, M, N)
+            for _ in range(2):
+                lsq.trsm_gram(A, Rs, b, ws=ws)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": args.ncu_case, "ok": True}))
+    return 0
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -232,6 +266,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.ncu_case:
+        return ncu_case(args)
     import torch
 
     import paper_2603_16644_gb300 as lsq

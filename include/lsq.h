@@ -240,6 +240,99 @@ lsq_status lsq_hpne_solve_host(const double* A_host, int64_t m, int64_t n, int64
                                const double* b_host, const lsq_opts* opts, double* x_host,
                                int32_t* info_host, void* ws, size_t ws_bytes, void* stream);
 
+/* ---- Batched solves (many independent problems of uneven shape) --------- */
+
+/* One problem of a batch: device pointers A (m x n, ld lda), b (m), x (n),
+ * info (device int32), and its own options (sketch kind, s, zeta, seed,
+ * sketch precision including AUTO, QR precision, refinement). */
+typedef struct {
+    const double* A;
+    int64_t m;
+    int64_t n;
+    int64_t lda;
+    const double* b;
+    double* x;
+    int32_t* info;
+    int32_t reserved0;
+    int32_t reserved1;
+    lsq_opts opts;
+} lsq_batch_problem;
+
+/* Workspace bytes for a batch (hpne = 0 PNE, 1 HPNE); 0 on invalid input. */
+size_t lsq_batched_workspace_size(int32_t hpne, int32_t count, const lsq_batch_problem* probs);
+
+/* Alg. 1 with PNE (Eq. e_pne) or HPNE (Eq. e_hpne) on `count` independent
+ * problems.  The problems are spread over 16 internal streams (heaviest
+ * first, least-loaded stream) and the whole fan-out is captured into one
+ * CUDA graph launched on `stream`; the executable graph is cached and
+ * replayed while the descriptors (pointers, shapes, options, workspace) stay
+ * the same.  Problems with sketch_prec = AUTO first get one batched
+ * condition-estimate pass and one readback of the chosen precisions (a
+ * stream synchronisation).  Each problem's status goes to its own info.
+ * Not thread safe: one batched call at a time per process. */
+lsq_status lsq_pne_solve_batched(int32_t count, const lsq_batch_problem* probs, void* ws, size_t ws_bytes,
+                                 void* stream);
+lsq_status lsq_hpne_solve_batched(int32_t count, const lsq_batch_problem* probs, void* ws, size_t ws_bytes,
+                                  void* stream);
+
+/* ---- Learned precision proposal (an addition; the paper's estimator of
+ * Sec. 6.1 stays the fallback and the judge is its 1-norm estimator) ------ */
+
+/* Number of MLP parameters for d input features (d -> 64 -> 64 -> 64 -> 4,
+ * packed W1 b1 W2 b2 W3 b3 W4 b4, W row-major out x in), and d itself. */
+int64_t lsq_mlp_param_count(int32_t d);
+int32_t lsq_mlp_num_features(void);
+
+/* The 10 proposal features of A (FP32, device f[10]): log2 m / 16,
+ * log2 n / 10, log10 spread and std of the column 2-norms, and statistics of
+ * log10 |diag R| for the preconditioner R of an FP8-e4m3 sparse-sign sketch
+ * (s = min(2n, m), zeta = min(8, s), key seed) with an FP32 QR: spread, std,
+ * slope against j/n, spread over the last quarter, fraction more than 100x
+ * below the largest, and the smallest relative to ||A||_F / sqrt(n). */
+size_t lsq_features_workspace_size(int64_t m, int64_t n);
+lsq_status lsq_features(const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed, float* f, void* ws,
+                        size_t ws_bytes, void* stream);
+
+/* MLP in FP32 on the device.  forward: logits (batch x 4) for X (batch x d,
+ * row-major).  backward: gradient of the mean softmax cross-entropy against
+ * labels (0 FP8-e4m3, 1 BF16, 2 FP32, 3 FP64) in the parameter packing, and
+ * the loss (device float, may be NULL); sums over the batch run in sample
+ * order (deterministic).  adam: one Adam step (step counts from 1). */
+lsq_status lsq_mlp_forward(const float* params, int32_t d, int32_t batch, const float* X, float* logits,
+                           void* stream);
+size_t lsq_mlp_backward_workspace_size(int32_t d, int32_t batch);
+lsq_status lsq_mlp_backward(const float* params, int32_t d, int32_t batch, const float* X, const int32_t* labels,
+                            float* grad, float* loss, void* ws, size_t ws_bytes, void* stream);
+lsq_status lsq_mlp_adam(float* params, const float* grad, float* m1, float* m2, int64_t count, float lr,
+                        float beta1, float beta2, float eps, int32_t step, void* stream);
+
+/* Features + MLP: proposed sketch precision (device int32, lsq_prec) and
+ * the class probabilities (device float[4], may be NULL).  Workspace:
+ * lsq_features_workspace_size(m, n). */
+lsq_status lsq_propose_precision(const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed,
+                                 const float* params, int32_t d, int32_t* prec, float* probs, void* ws,
+                                 size_t ws_bytes, void* stream);
+
+/* Judge of a computed preconditioner R_s (n x n upper FP64): Hager's
+ * single-precision 1-norm estimate (Sec. 6.1) of kappa_1(R_s) -> kappa1
+ * (device double); accept (device int32) = 1 iff u_p * kappa1 <= 1 for the
+ * precision u_p it was computed in, i.e. Lemma rscond's eps kappa(R_s) < 1. */
+size_t lsq_judge_workspace_size(int64_t n);
+lsq_status lsq_judge_preconditioner(const double* Rs, int64_t n, int64_t ldr, int32_t prec, int32_t* accept,
+                                    double* kappa1, void* ws, size_t ws_bytes, void* stream);
+
+/* PNE (Alg. 1) with the learned proposal: propose u_p, compute R_s in u_p,
+ * judge it, escalate FP8 -> BF16 -> FP32 -> FP64 until accepted (FP64 needs no
+ * judge), then finish with the accepted R_s.  used_prec and escalations are
+ * HOST int32 outputs; the call synchronises the stream once per judged
+ * candidate.  opts gives the sketch kind, s, zeta, seed and refinement; its
+ * precisions are ignored. */
+size_t lsq_learned_workspace_size(int64_t m, int64_t n, const lsq_opts* opts);
+lsq_status lsq_pne_solve_learned(const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                                 const lsq_opts* opts, const float* params, int32_t d, double* x, int32_t* info,
+                                 int32_t* used_prec, int32_t* escalations, void* ws, size_t ws_bytes,
+                                 void* stream);
+
 /* ---- Instrumentation (no counterpart in the paper) --------------------- */
 
 /* Number of kernel launches this library has issued since it was loaded. */

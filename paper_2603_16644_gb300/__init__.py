@@ -300,3 +300,164 @@ def solve_host(A_host, b_host, *, hpne=False, opts: Opts = None, ws=None, x_host
     _check(fn(_ptr(A_host), m, n, lda, _ptr(b_host), C.byref(opts), _ptr(x_host), C.cast(C.pointer(info), C.c_void_p),
               _ptr(ws), ws.numel(), _stream()), "lsq_solve_host")
     return x_host, info.value
+
+
+# ---------------------------------------------------------------------------- batched
+class BatchProblem(C.Structure):
+    _fields_ = [("A", C.c_void_p), ("m", C.c_int64), ("n", C.c_int64), ("lda", C.c_int64), ("b", C.c_void_p),
+                ("x", C.c_void_p), ("info", C.c_void_p), ("reserved0", C.c_int32), ("reserved1", C.c_int32),
+                ("opts", Opts)]
+
+
+def _batch_sigs():
+    L = lib()
+    L.lsq_batched_workspace_size.restype = C.c_size_t
+    L.lsq_batched_workspace_size.argtypes = [C.c_int32, C.c_int32, C.POINTER(BatchProblem)]
+    for nm in ("lsq_pne_solve_batched", "lsq_hpne_solve_batched"):
+        f = getattr(L, nm)
+        f.restype = C.c_int32
+        f.argtypes = [C.c_int32, C.POINTER(BatchProblem), C.c_void_p, C.c_size_t, C.c_void_p]
+    return L
+
+
+def batch_descriptors(As, bs, xs, infos, opts_list):
+    """ctypes array of lsq_batch_problem for device tensors (A column-major)."""
+    arr = (BatchProblem * len(As))()
+    for i, (A, b, x, info, o) in enumerate(zip(As, bs, xs, infos, opts_list)):
+        _need_cuda(A, b, x, info)
+        m, n = A.shape
+        arr[i] = BatchProblem(A.data_ptr(), m, n, _ld(A), b.data_ptr(), x.data_ptr(), info.data_ptr(), 0, 0, o)
+    return arr
+
+
+def batched_workspace(desc, hpne=False, device=None):
+    L = _batch_sigs()
+    nbytes = int(L.lsq_batched_workspace_size(int(hpne), len(desc), desc))
+    if nbytes == 0:
+        raise LsqError("invalid batch description")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def solve_batched(desc, ws, hpne=False):
+    """Alg. 1 on every problem of `desc` (from batch_descriptors): one cached
+    CUDA-graph launch of all solves over 16 internal streams."""
+    L = _batch_sigs()
+    fn = L.lsq_hpne_solve_batched if hpne else L.lsq_pne_solve_batched
+    _check(fn(len(desc), desc, _ptr(ws), ws.numel(), _stream()), "lsq_solve_batched")
+
+
+# ---------------------------------------------------------------------------- learned proposal
+N_FEATURES = 10
+CLASS_PRECS = [FP8_E4M3, BF16, FP32, FP64]
+
+
+def _learn_sigs():
+    L = lib()
+    sigs = {
+        "lsq_mlp_param_count": (C.c_int64, [C.c_int32]),
+        "lsq_mlp_num_features": (C.c_int32, []),
+        "lsq_features_workspace_size": (C.c_size_t, [C.c_int64, C.c_int64]),
+        "lsq_features": (C.c_int32, [_vp, _i64, _i64, _i64, C.c_uint64, _vp, _vp, _sz, _vp]),
+        "lsq_mlp_forward": (C.c_int32, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp]),
+        "lsq_mlp_backward_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32]),
+        "lsq_mlp_backward": (C.c_int32, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+        "lsq_mlp_adam": (C.c_int32, [_vp, _vp, _vp, _vp, _i64, C.c_float, C.c_float, C.c_float, C.c_float,
+                                     C.c_int32, _vp]),
+        "lsq_propose_precision": (C.c_int32, [_vp, _i64, _i64, _i64, C.c_uint64, _vp, C.c_int32, _vp, _vp, _vp,
+                                              _sz, _vp]),
+        "lsq_judge_workspace_size": (C.c_size_t, [C.c_int64]),
+        "lsq_judge_preconditioner": (C.c_int32, [_vp, _i64, _i64, C.c_int32, _vp, _vp, _vp, _sz, _vp]),
+        "lsq_learned_workspace_size": (C.c_size_t, [_i64, _i64, C.POINTER(Opts)]),
+        "lsq_pne_solve_learned": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, C.POINTER(Opts), _vp, C.c_int32, _vp,
+                                              _vp, _vp, _vp, _vp, _sz, _vp]),
+    }
+    for nm, (res, args) in sigs.items():
+        f = getattr(L, nm)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+def mlp_param_count(d=N_FEATURES) -> int:
+    return int(_learn_sigs().lsq_mlp_param_count(d))
+
+
+def features(A, seed=0, ws=None):
+    """The 10 proposal features of A (float32 device tensor)."""
+    L = _learn_sigs()
+    _need_cuda(A)
+    m, n = A.shape
+    f = torch.empty(N_FEATURES, dtype=torch.float32, device=A.device)
+    ws = torch.empty(int(L.lsq_features_workspace_size(m, n)), dtype=torch.uint8, device=A.device) if ws is None else ws
+    _check(L.lsq_features(_ptr(A), m, n, _ld(A), seed, _ptr(f), _ptr(ws), ws.numel(), _stream()), "lsq_features")
+    return f
+
+
+def mlp_forward(params, X):
+    L = _learn_sigs()
+    _need_cuda(params, X)
+    B, d = X.shape
+    logits = torch.empty((B, 4), dtype=torch.float32, device=X.device)
+    _check(L.lsq_mlp_forward(_ptr(params), d, B, _ptr(X.contiguous()), _ptr(logits), _stream()), "lsq_mlp_forward")
+    return logits
+
+
+def mlp_backward(params, X, labels, ws=None):
+    """(gradient, mean loss) of the softmax cross-entropy."""
+    L = _learn_sigs()
+    _need_cuda(params, X, labels)
+    B, d = X.shape
+    grad = torch.empty_like(params)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    nbytes = int(L.lsq_mlp_backward_workspace_size(d, B))
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=X.device) if ws is None or ws.numel() < nbytes else ws
+    _check(L.lsq_mlp_backward(_ptr(params), d, B, _ptr(X.contiguous()), _ptr(labels), _ptr(grad), _ptr(loss),
+                              _ptr(ws), ws.numel(), _stream()), "lsq_mlp_backward")
+    return grad, loss
+
+
+def mlp_adam(params, grad, m1, m2, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    L = _learn_sigs()
+    _check(L.lsq_mlp_adam(_ptr(params), _ptr(grad), _ptr(m1), _ptr(m2), params.numel(), lr, beta1, beta2, eps,
+                          step, _stream()), "lsq_mlp_adam")
+
+
+def propose_precision(A, params, seed=0, ws=None):
+    """(proposed precision code, class probabilities) as device tensors."""
+    L = _learn_sigs()
+    m, n = A.shape
+    prec = torch.empty(1, dtype=torch.int32, device=A.device)
+    probs = torch.empty(4, dtype=torch.float32, device=A.device)
+    ws = torch.empty(int(L.lsq_features_workspace_size(m, n)), dtype=torch.uint8, device=A.device) if ws is None else ws
+    _check(L.lsq_propose_precision(_ptr(A), m, n, _ld(A), seed, _ptr(params), N_FEATURES, _ptr(prec), _ptr(probs),
+                                   _ptr(ws), ws.numel(), _stream()), "lsq_propose_precision")
+    return prec, probs
+
+
+def judge_preconditioner(Rs, prec):
+    """(accept (1 int32), kappa_1 estimate (1 float64)) on the device."""
+    L = _learn_sigs()
+    n = Rs.shape[0]
+    acc = torch.empty(1, dtype=torch.int32, device=Rs.device)
+    k1 = torch.empty(1, dtype=torch.float64, device=Rs.device)
+    ws = torch.empty(int(L.lsq_judge_workspace_size(n)), dtype=torch.uint8, device=Rs.device)
+    _check(L.lsq_judge_preconditioner(_ptr(Rs), n, _ld(Rs), prec, _ptr(acc), _ptr(k1), _ptr(ws), ws.numel(),
+                                      _stream()), "lsq_judge_preconditioner")
+    return acc, k1
+
+
+def pne_learned(A, b, params, opts, ws=None, x=None, info=None):
+    """PNE with the learned proposal; returns (x, info, used precision, escalations)."""
+    L = _learn_sigs()
+    _need_cuda(A, b, params)
+    m, n = A.shape
+    ws = torch.empty(int(L.lsq_learned_workspace_size(m, n, C.byref(opts))), dtype=torch.uint8,
+                     device=A.device) if ws is None else ws
+    x = torch.empty(n, dtype=torch.float64, device=A.device) if x is None else x
+    info = torch.zeros(1, dtype=torch.int32, device=A.device) if info is None else info
+    used = C.c_int32(0)
+    esc = C.c_int32(0)
+    _check(L.lsq_pne_solve_learned(_ptr(A), m, n, _ld(A), _ptr(b), C.byref(opts), _ptr(params), N_FEATURES, _ptr(x),
+                                   _ptr(info), C.cast(C.pointer(used), C.c_void_p), C.cast(C.pointer(esc), C.c_void_p),
+                                   _ptr(ws), ws.numel(), _stream()), "lsq_pne_solve_learned")
+    return x, info, used.value, esc.value

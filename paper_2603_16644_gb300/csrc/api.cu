@@ -220,7 +220,7 @@ lsq_status trsm_gram(const double* A, int64_t m, int64_t n, int64_t lda, const d
 
 lsq_status solve_impl(bool hpne, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
                       const lsq_opts* o, double* x, double* Rs_out, int32_t* info, void* ws, size_t ws_bytes,
-                      cudaStream_t st) {
+                      cudaStream_t st, const double* Rs_in = nullptr) {
     if (!A || !b || !x || !info || m <= 0 || n <= 0 || lda < m) return LSQ_ERR_ARG;
     lsq_status r = check_opts(o, m, n, true);
     if (r != LSQ_OK) return r;
@@ -260,14 +260,19 @@ lsq_status solve_impl(bool hpne, const double* A, int64_t m, int64_t n, int64_t 
     double* gv = (double*)(base + L.gv);
     int32_t* piv = (int32_t*)(base + L.piv);
     int32_t* colexp = (int32_t*)(skb + SK.colexp);
-    stage_mark(ST_SKETCH, true, st);
-    if ((r = run_sketch(A, m, n, lda, o, prec, As, s, colexp, skb, SK, err, st)) != LSQ_OK) return r;
-    stage_mark(ST_SKETCH, false, st);
-    stage_mark(ST_QR, true, st);
-    if ((r = launch_precond_qr(As, s, n, s, prec == LSQ_FP64 ? LSQ_FP64 : LSQ_FP32, qp, colexp, Rs, n, info,
-                               base + L.qr, L.qr_bytes, st)) != LSQ_OK)
-        return r;
-    stage_mark(ST_QR, false, st);
+    if (Rs_in) {
+        // preconditioner already computed (and accepted) by the caller
+        LSQ_CUDA_TRY(cudaMemcpyAsync(Rs, Rs_in, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, st));
+    } else {
+        stage_mark(ST_SKETCH, true, st);
+        if ((r = run_sketch(A, m, n, lda, o, prec, As, s, colexp, skb, SK, err, st)) != LSQ_OK) return r;
+        stage_mark(ST_SKETCH, false, st);
+        stage_mark(ST_QR, true, st);
+        if ((r = launch_precond_qr(As, s, n, s, prec == LSQ_FP64 ? LSQ_FP64 : LSQ_FP32, qp, colexp, Rs, n, info,
+                                   base + L.qr, L.qr_bytes, st)) != LSQ_OK)
+            return r;
+        stage_mark(ST_QR, false, st);
+    }
     if ((r = trsm_gram(A, m, n, lda, Rs, n, b, hpne, Ap, m, G, n, c, base + L.gemm, (double*)(base + L.gemv),
                        (int64_t)(gemv_t_ws_bytes(m, n) / sizeof(double)), sms, st)) != LSQ_OK)
         return r;
@@ -535,3 +540,19 @@ lsq_status lsq_hpne_solve_host(const double* A_host, int64_t m, int64_t n, int64
 }
 
 }  // extern "C"
+
+namespace lsq {
+
+// Entry points for the batched driver (csrc/batched.cu).
+lsq_status solve_impl_ext(bool hpne, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                          const lsq_opts* o, double* x, double* Rs_out, int32_t* info, void* ws, size_t ws_bytes,
+                          cudaStream_t st, const double* Rs_in) {
+    return solve_impl(hpne, A, m, n, lda, b, o, x, Rs_out, info, ws, ws_bytes, st, Rs_in);
+}
+
+size_t solve_ws_bytes_ext(int64_t m, int64_t n, const lsq_opts* o, bool hpne) {
+    int p = o->sketch_prec == LSQ_AUTO ? LSQ_FP64 : o->sketch_prec;
+    return solve_layout(m, n, o, p, hpne, device_sm_count()).total + 256;
+}
+
+}  // namespace lsq

@@ -347,7 +347,7 @@ lsq_status launch_lu(double* H, int64_t n, int64_t ld, int32_t* piv, int32_t* in
 // all threads.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_trsv(int kind, const T* __restrict__ M, int64_t n, int64_t ld,
+__global__ void __launch_bounds__(512) k_trsv(int kind, const T* __restrict__ M, int64_t n, int64_t ld,
                                               T* __restrict__ y, const int32_t* __restrict__ info) {
     if (info && *info != 0) return;
     extern __shared__ __align__(16) unsigned char trsv_raw[];
@@ -362,7 +362,7 @@ lsq_status launch_trsv(int kind, const T* M, int64_t n, int64_t ld, T* y, const 
     size_t smem = sizeof(T) * (size_t)n;
     if (smem > 200 * 1024) return LSQ_ERR_ARG;
     if (smem > 48 * 1024) LSQ_CUDA_TRY(cudaFuncSetAttribute(k_trsv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_trsv<T><<<1, 256, smem, st>>>(kind, M, n, ld, y, info);
+    k_trsv<T><<<1, 512, smem, st>>>(kind, M, n, ld, y, info);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
 }

@@ -9,6 +9,8 @@
 #include "common.cuh"
 #include "kernels.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 namespace lsq {
@@ -158,6 +160,182 @@ __global__ void __launch_bounds__(QPT) k_qr_panel(T* __restrict__ W, int64_t ld,
     }
 }
 
+// Same panel factorization by a cluster of QCL CTAs that keep the panel in
+// shared memory: CTA r owns rows [r R, (r+1) R) of the panel.  Per column,
+// the partial sums of sigma and of w = v^T W are published in each CTA's
+// shared memory and read back through distributed shared memory in rank
+// order, so every CTA computes identical Householder scalars.  Partial-sum
+// slots alternate between two buffers by column parity, which makes two
+// cluster barriers per column sufficient.
+constexpr int QCL = 8;
+constexpr int QCT = 256;
+
+template <typename T>
+__global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(QCT)
+    k_qr_panel_cl(T* __restrict__ W, int64_t ld, int64_t s, int64_t k0, int nb, T* __restrict__ beta_out,
+                  T* __restrict__ Tm, T* __restrict__ V, int64_t ldv) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char cl_raw[];
+    T* P = reinterpret_cast<T*>(cl_raw);  // local panel, column-major, ld R
+    __shared__ T sig_all[2][QCL];      // sigma partials of every rank, per column parity
+    __shared__ T x1_all[2];            // x1 published by the owner of the diagonal row
+    __shared__ T w_all[2][QCL][QNB];   // w partials of every rank
+    __shared__ T wred[QCT / 32][QNB];
+    __shared__ T wcol[QNB];
+    __shared__ T Ypart[QNB][QNB + 1];
+    __shared__ T Ts[QNB][QNB + 1];
+    __shared__ T red[32];
+    __shared__ T bsh[QNB];
+    const int rank = (int)cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t rows = s - k0;
+    const int64_t R = (rows + QCL - 1) / QCL;
+    const int64_t r0 = rank * R;
+    const int64_t nloc = r0 < rows ? min64(R, rows - r0) : 0;
+    for (int64_t q = tid; q < R * QNB; q += QCT) {
+        int64_t i = q % R, c = q / R;
+        P[q] = (i < nloc && c < nb) ? W[(k0 + r0 + i) + (k0 + c) * ld] : (T)0;
+    }
+    __syncthreads();
+    for (int jj = 0; jj < nb; ++jj) {
+        const int buf = jj & 1;
+        const int owner = (int)(jj / R);
+        T* colj = P + (int64_t)jj * R;
+        // rows strictly below the diagonal that this CTA owns
+        int64_t ib = max64((int64_t)jj + 1 - r0, 0);
+        T sp = (T)0;
+        for (int64_t i = ib + tid; i < nloc; i += QCT) sp = fma(colj[i], colj[i], sp);
+        for (int off = 16; off > 0; off >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, off);
+        if (lane == 0) red[warp] = sp;
+        __syncthreads();
+        if (warp == 0) {
+            T t = (T)0;
+            for (int w = 0; w < QCT / 32; ++w) t += red[w];
+            // push this rank's partial (and x1 from the owner) into every CTA
+            if (lane < QCL) {
+                *cluster.map_shared_rank(&sig_all[buf][rank], lane) = t;
+                if (rank == owner) *cluster.map_shared_rank(&x1_all[buf], lane) = colj[jj - r0];
+            }
+        }
+        cluster.sync();
+        T sigma = (T)0;
+        for (int q = 0; q < QCL; ++q) sigma += sig_all[buf][q];
+        const T x1 = x1_all[buf];
+        T mu, b, v1 = (T)1;
+        bool scale = false;
+        if (sigma == (T)0) {
+            mu = fabs(x1);
+            b = x1 >= (T)0 ? (T)0 : (T)2;
+        } else {
+            mu = sqrt(x1 * x1 + sigma);
+            v1 = x1 <= (T)0 ? x1 - mu : -sigma / (x1 + mu);
+            b = (T)2 * v1 * v1 / (sigma + v1 * v1);
+            scale = true;
+        }
+        if (scale)
+            for (int64_t i = ib + tid; i < nloc; i += QCT) colj[i] = colj[i] / v1;
+        __syncthreads();
+        if (tid == 0) bsh[jj] = b;  // identical in every CTA of the cluster
+        if (rank == owner && tid == 0) {
+            colj[jj - r0] = mu;
+            beta_out[k0 + jj] = b;
+        }
+        const int rem = nb - jj - 1;
+        if (rem > 0 && b != (T)0) {
+            // rows >= jj owned here; v_jj = 1 on the diagonal row
+            int64_t id = max64((int64_t)jj - r0, 0);
+            T acc[QNB];
+#pragma unroll
+            for (int c = 0; c < QNB; ++c) acc[c] = (T)0;
+            for (int64_t i = id + tid; i < nloc; i += QCT) {
+                T vi = (r0 + i == jj) ? (T)1 : colj[i];
+#pragma unroll
+                for (int c = 0; c < QNB; ++c)
+                    if (c < rem) acc[c] = fma(vi, P[(int64_t)(jj + 1 + c) * R + i], acc[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < QNB; ++c) {
+                T v = acc[c];
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                if (lane == 0) wred[warp][c] = v;
+            }
+            __syncthreads();
+            if (tid < rem) {
+                T t = (T)0;
+                for (int w = 0; w < QCT / 32; ++w) t += wred[w][tid];
+                for (int q = 0; q < QCL; ++q) *cluster.map_shared_rank(&w_all[buf][rank][tid], q) = t;
+            }
+            cluster.sync();
+            if (tid < rem) {
+                T t = (T)0;
+                for (int q = 0; q < QCL; ++q) t += w_all[buf][q][tid];
+                wcol[tid] = b * t;
+            }
+            __syncthreads();
+            for (int64_t i = id + tid; i < nloc; i += QCT) {
+                T vi = (r0 + i == jj) ? (T)1 : colj[i];
+                for (int c = 0; c < rem; ++c) {
+                    T* p = &P[(int64_t)(jj + 1 + c) * R + i];
+                    *p = fma(-wcol[c], vi, *p);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // Y = V^T V partial over the owned rows (V: 0 above, 1 on the diagonal)
+    for (int e = tid; e < QNB * QNB; e += QCT) {
+        int p = e % QNB, q = e / QNB;
+        T y = (T)0;
+        if (p < nb && q < nb) {
+            for (int64_t i = 0; i < nloc; ++i) {
+                int64_t gi = r0 + i;
+                T vp = gi < p ? (T)0 : (gi == p ? (T)1 : P[(int64_t)p * R + i]);
+                T vq = gi < q ? (T)0 : (gi == q ? (T)1 : P[(int64_t)q * R + i]);
+                y = fma(vp, vq, y);
+            }
+        }
+        Ypart[p][q] = y;
+    }
+    // write R / v back to W and the explicit V
+    for (int64_t q = tid; q < R * QNB; q += QCT) {
+        int64_t i = q % R, c = q / R;
+        if (i < nloc && c < nb) {
+            int64_t gi = r0 + i;
+            T pv = P[q];
+            W[(k0 + gi) + (k0 + c) * ld] = pv;
+            V[gi + c * ldv] = gi < c ? (T)0 : (gi == c ? (T)1 : pv);
+        } else if (i < nloc) {
+            V[(r0 + i) + c * ldv] = (T)0;
+        }
+    }
+    cluster.sync();
+    if (rank == 0) {
+        for (int e = tid; e < QNB * QNB; e += QCT) {
+            int p = e % QNB, q = e / QNB;
+            T y = (T)0;
+            for (int r = 0; r < QCL; ++r) y += cluster.map_shared_rank(&Ypart[p][q], r)[0];
+            Ts[p][q] = y;  // Ts holds Y for now
+        }
+        __syncthreads();
+        if (warp == 0) {
+            T trow[QNB];
+#pragma unroll
+            for (int c = 0; c < QNB; ++c) trow[c] = (T)0;
+            // column by column: T[0:j, j] = -beta_j T[0:j, 0:j] Y[0:j, j]; lane = row
+            for (int jj = 0; jj < nb; ++jj) {
+                T bj = bsh[jj];
+                T t = (T)0;
+                for (int qq = 0; qq < jj; ++qq) t = fma(trow[qq], Ts[qq][jj], t);
+                if (lane < jj) trow[jj] = -bj * t;
+                if (lane == jj) trow[jj] = bj;
+            }
+            for (int c = 0; c < QNB; ++c) Tm[lane + c * QNB] = trow[c];
+        }
+    }
+    cluster.sync();
+}
+
 // W2 = T^T Wp  (nb x nt), T upper (ld QNB), Wp (nb x nt, ld nb).
 template <typename T>
 __global__ void k_qr_tw(const T* __restrict__ Tm, const T* __restrict__ Wp, int nb, int64_t nt, T* __restrict__ W2) {
@@ -250,7 +428,13 @@ static lsq_status qr_run(const void* As, int64_t s, int64_t n, int64_t ldas, int
     for (int64_t k0 = 0; k0 < n; k0 += QNB) {
         int nb = (int)std::min<int64_t>(QNB, n - k0);
         int64_t rows = s - k0;
-        k_qr_panel<T><<<1, QPT, 0, st>>>(W, s, s, k0, nb, beta, Tm, V, rows);
+        size_t clsm = sizeof(T) * (size_t)ceil_div(rows, QCL) * QNB;
+        if (clsm <= 160 * 1024) {
+            LSQ_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)clsm));
+            k_qr_panel_cl<T><<<QCL, QCT, clsm, st>>>(W, s, s, k0, nb, beta, Tm, V, rows);
+        } else {
+            k_qr_panel<T><<<1, QPT, 0, st>>>(W, s, s, k0, nb, beta, Tm, V, rows);
+        }
         LSQ_LAUNCH_CHECK();
         int64_t nt = n - k0 - nb;
         if (nt <= 0) continue;
