@@ -240,6 +240,38 @@ lsq_status lsq_hpne_solve_host(const double* A_host, int64_t m, int64_t n, int64
                                const double* b_host, const lsq_opts* opts, double* x_host,
                                int32_t* info_host, void* ws, size_t ws_bytes, void* stream);
 
+/* Dense contraction on the tensor cores (tcgen05, TMA-fed, FP32 accumulators
+ * in TMEM), the kernel behind the Gaussian sketch (Alg. 1, "Sketch
+ * A_s = Omega A"): C (M x N, column-major ld ldc, FP32) = X Y^T with X (M x K)
+ * and Y (N x K) both K-contiguous (row r of X at X + r*ldx), stored as
+ * FP8-e4m3 (prec = LSQ_FP8_E4M3, bytes), BF16 or FP16.  ldx, ldy multiples of
+ * 16 elements; X, Y 16-byte aligned.  K may be split over CTAs (workspace
+ * lsq_tc_gemm_workspace_size); partial sums are reduced in a fixed order.
+ * info (device int32, may be NULL) receives -2 if a pipeline wait timed out. */
+size_t lsq_tc_gemm_workspace_size(int32_t prec, int64_t M, int64_t N, int64_t K);
+lsq_status lsq_tc_gemm(int32_t prec, const void* X, int64_t ldx, const void* Y, int64_t ldy, int64_t M, int64_t N,
+                       int64_t K, float* C, int64_t ldc, int32_t* info, void* ws, size_t ws_bytes, void* stream);
+
+/* FP64 Gram G = X^T X (the left-hand side of Eq. e_pne with X = A_p) on the
+ * FP8 tensor cores: every column p of X (m x n, ld) is written as 14
+ * base-16 digits in [-15, 15] relative to 2^(e_p) > max_i |x_ip| (56 bits,
+ * extracted with integer operations); the digit-pair products t + u <= 13
+ * are exact integer sums in the FP32 accumulators (K chunks of 65536 rows)
+ * and are combined in FP64 smallest weight first, then scaled by
+ * 2^(e_p + e_q).  Per entry the error is below ~2^-55 m max|x_p| max|x_q|,
+ * the order of FP64 rounding.  G: n x n FP64, full symmetric, ld ldg.
+ * Workspace lsq_gram_tc_workspace_size(m, n) (about 14 m n bytes of digits
+ * plus 64 KiB per digit tile).  info (device, may be NULL): -2 on a pipeline
+ * timeout. */
+size_t lsq_gram_tc_workspace_size(int64_t m, int64_t n);
+lsq_status lsq_gram_tc(const double* X, int64_t m, int64_t n, int64_t ld, double* G, int64_t ldg, int32_t* info,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* Use lsq_gram_tc for the symmetric Gram inside the PNE solves (1, the
+ * default) or the FP64 CUDA-core GEMM (0); returns the previous setting.
+ * Process-wide; for comparisons. */
+int32_t lsq_set_fp64_emulation(int32_t enable);
+
 /* ---- Batched solves (many independent problems of uneven shape) --------- */
 
 /* One problem of a batch: device pointers A (m x n, ld lda), b (m), x (n),
@@ -334,6 +366,11 @@ lsq_status lsq_pne_solve_learned(const double* A, int64_t m, int64_t n, int64_t 
                                  void* stream);
 
 /* ---- Instrumentation (no counterpart in the paper) --------------------- */
+
+/* Route Gaussian sketches in FP8-e4m3 / BF16 / FP16 to the tensor-core
+ * kernel (enable = 1, the default) or to the CUDA-core GEMM (0); returns
+ * the previous setting.  Process-wide; for tests and comparisons. */
+int32_t lsq_set_tensor_core_sketch(int32_t enable);
 
 /* Number of kernel launches this library has issued since it was loaded. */
 int64_t lsq_launch_count(void);

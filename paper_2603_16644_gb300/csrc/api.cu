@@ -57,6 +57,14 @@ void stage_mark(int stage, bool begin, cudaStream_t st) {
 
 namespace {
 
+// Gaussian sketches in FP8/BF16/FP16 run on the tensor cores unless switched
+// off (lsq_set_tensor_core_sketch), which routes them to the CUDA-core GEMM.
+bool g_tensor_core_sketch = true;
+
+// The symmetric FP64 Gram of PNE runs as the digit-sliced tensor-core
+// product (csrc/ozaki.cu) unless switched off (lsq_set_fp64_emulation).
+bool g_fp64_emulation = true;
+
 inline cudaStream_t S(void* p) { return reinterpret_cast<cudaStream_t>(p); }
 
 bool valid_sketch_prec(int p) { return p >= LSQ_FP8_E4M3 && p <= LSQ_FP64; }
@@ -110,7 +118,7 @@ SketchLayout sketch_layout(int64_t m, int64_t n, int64_t s, int kind, int zeta, 
         L.ahat = o.take((size_t)L.ldq * n * es);
         L.om = o.take((size_t)L.ldo * s * es);
         GemmPlan gp = plan_gemm_kmajor(s, n, m, false, prec == LSQ_FP64 ? LSQ_FP64 : LSQ_FP32, sms);
-        L.gemm = o.take(gemm_kmajor_ws_bytes(gp));
+        L.gemm = o.take(std::max(gemm_kmajor_ws_bytes(gp), sketch_tc_ws_bytes(s, n, m, prec, sms)));
     }
     L.total = o.off;
     return L;
@@ -118,7 +126,8 @@ SketchLayout sketch_layout(int64_t m, int64_t n, int64_t s, int kind, int zeta, 
 
 struct SolveLayout {
     SketchLayout sk;
-    size_t sk_base, as_, rs, qr, ap, g, c, x, r, gv, piv, gemm, gemv, cond, k0, ch, err, total;
+    size_t sk_base, as_, rs, qr, ap, g, c, x, r, gv, piv, gemm, gemv, cond, k0, ch, err, oz, total;
+    size_t oz_bytes;
     size_t qr_bytes, cond_bytes;
 };
 
@@ -126,7 +135,12 @@ SolveLayout solve_layout(int64_t m, int64_t n, const lsq_opts* o, int prec, bool
     SolveLayout L{};
     Off q;
     L.sk = sketch_layout(m, n, o->s, o->kind, o->zeta, prec, sms);
-    L.sk_base = q.take(L.sk.total);
+    // reserve for the widest sketch precision, so that a workspace sized with
+    // the layout of one precision (AUTO sizes with FP64) fits whichever runs
+    size_t sk_bytes = L.sk.total;
+    for (int p = LSQ_FP8_E4M3; p <= LSQ_FP64; ++p)
+        sk_bytes = std::max(sk_bytes, sketch_layout(m, n, o->s, o->kind, o->zeta, p, sms).total);
+    L.sk_base = q.take(sk_bytes);
     int as_es = prec == LSQ_FP64 ? 8 : 4;
     L.as_ = q.take((size_t)o->s * n * as_es);
     L.rs = q.take(sizeof(double) * (size_t)n * n);
@@ -148,6 +162,8 @@ SolveLayout solve_layout(int64_t m, int64_t n, const lsq_opts* o, int prec, bool
     L.k0 = q.take(sizeof(double));
     L.ch = q.take(sizeof(int32_t));
     L.err = q.take(sizeof(int32_t));
+    L.oz_bytes = hpne ? 0 : oz_gram_ws_bytes(m, n);
+    L.oz = q.take(L.oz_bytes);
     L.total = q.off + 256;
     return L;
 }
@@ -179,6 +195,9 @@ lsq_status run_sketch(const double* A, int64_t m, int64_t n, int64_t lda, const 
     }
     if ((r = launch_gauss_gen(o->seed, o->s, m, prec, base + L.om, L.ldo, st)) != LSQ_OK) return r;
     if ((r = launch_quantize_cm(A, m, n, lda, colexp, prec, base + L.ahat, L.ldq, st)) != LSQ_OK) return r;
+    if (g_tensor_core_sketch && sketch_tc_supported(prec))
+        return launch_sketch_tc(base + L.om, L.ldo, base + L.ahat, L.ldq, prec, o->s, n, m, (float*)As, ldas,
+                                base + L.gemm, L.total - L.gemm, err, st);
     GemmPlan gp = plan_gemm_kmajor(o->s, n, m, false, prec == LSQ_FP64 ? LSQ_FP64 : LSQ_FP32, device_sm_count());
     return launch_gemm_kmajor(gp, base + L.om, prec, L.ldo, base + L.ahat, prec, L.ldq, As, ldas, base + L.gemm, st);
 }
@@ -201,17 +220,21 @@ lsq_status solve_factored(bool hpne, const double* G, int64_t n, int64_t ldg, co
 
 lsq_status trsm_gram(const double* A, int64_t m, int64_t n, int64_t lda, const double* Rs, int64_t ldr,
                      const double* b, bool hpne, double* Ap, int64_t ldap, double* G, int64_t ldg, double* c,
-                     void* gemm_ws, double* gemv_ws, int64_t gemv_cap, int sms, cudaStream_t st) {
+                     void* gemm_ws, double* gemv_ws, int64_t gemv_cap, int sms, cudaStream_t st,
+                     void* oz_ws = nullptr, size_t oz_bytes = 0, int32_t* err = nullptr) {
     stage_mark(ST_TRSM, true, st);
     lsq_status r = launch_trsm_right_upper(A, m, n, lda, Rs, ldr, Ap, ldap, st);
     if (r != LSQ_OK) return r;
     stage_mark(ST_TRSM, false, st);
     stage_mark(ST_GRAM, true, st);
     GemmPlan gp = plan_gemm_kmajor(n, n, m, !hpne, LSQ_FP64, sms);
-    if (hpne)
+    if (hpne) {
         r = launch_gemm_kmajor(gp, Ap, LSQ_FP64, ldap, A, LSQ_FP64, lda, G, ldg, gemm_ws, st);
-    else
+    } else if (g_fp64_emulation && oz_ws && oz_bytes >= oz_gram_ws_bytes(m, n)) {
+        r = oz_gram(Ap, m, n, ldap, G, ldg, oz_ws, oz_bytes, err, st);
+    } else {
         r = launch_gemm_kmajor(gp, Ap, LSQ_FP64, ldap, Ap, LSQ_FP64, ldap, G, ldg, gemm_ws, st);
+    }
     if (r != LSQ_OK) return r;
     r = launch_gemv_t(Ap, m, n, ldap, b, c, gemv_ws, gemv_cap, st);
     stage_mark(ST_GRAM, false, st);
@@ -274,7 +297,8 @@ lsq_status solve_impl(bool hpne, const double* A, int64_t m, int64_t n, int64_t 
         stage_mark(ST_QR, false, st);
     }
     if ((r = trsm_gram(A, m, n, lda, Rs, n, b, hpne, Ap, m, G, n, c, base + L.gemm, (double*)(base + L.gemv),
-                       (int64_t)(gemv_t_ws_bytes(m, n) / sizeof(double)), sms, st)) != LSQ_OK)
+                       (int64_t)(gemv_t_ws_bytes(m, n) / sizeof(double)), sms, st, base + L.oz, L.oz_bytes, err)) !=
+        LSQ_OK)
         return r;
     stage_mark(ST_FACTOR, true, st);
     if (hpne)
@@ -358,6 +382,27 @@ int32_t lsq_version(void) { return 100; }
 
 int64_t lsq_launch_count(void) { return (int64_t)g_launches.load(); }
 
+int32_t lsq_set_fp64_emulation(int32_t enable) {
+    int32_t prev = g_fp64_emulation ? 1 : 0;
+    g_fp64_emulation = enable != 0;
+    return prev;
+}
+
+size_t lsq_gram_tc_workspace_size(int64_t m, int64_t n) { return m > 0 && n > 0 ? oz_gram_ws_bytes(m, n) + 256 : 0; }
+
+lsq_status lsq_gram_tc(const double* X, int64_t m, int64_t n, int64_t ld, double* G, int64_t ldg, int32_t* info,
+                       void* ws, size_t ws_bytes, void* stream) {
+    if (!X || !G || m <= 0 || n <= 0 || ld < m || ldg < n) return LSQ_ERR_ARG;
+    if (info) LSQ_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), S(stream)));
+    return oz_gram(X, m, n, ld, G, ldg, ws, ws_bytes, info, S(stream));
+}
+
+int32_t lsq_set_tensor_core_sketch(int32_t enable) {
+    int32_t prev = g_tensor_core_sketch ? 1 : 0;
+    g_tensor_core_sketch = enable != 0;
+    return prev;
+}
+
 int32_t lsq_profile(int32_t enable) {
     std::lock_guard<std::mutex> lk(g_prof.mu);
     g_prof.on = enable != 0;
@@ -426,7 +471,8 @@ size_t lsq_workspace_size(int32_t op, int64_t m, int64_t n, const lsq_opts* o) {
     case LSQ_OP_TRSM_GRAM: {
         GemmPlan gp = plan_gemm_kmajor(n, n, m, false, LSQ_FP64, sms);
         GemmPlan gs = plan_gemm_kmajor(n, n, m, true, LSQ_FP64, sms);
-        return std::max(gemm_kmajor_ws_bytes(gp), gemm_kmajor_ws_bytes(gs)) + gemv_t_ws_bytes(m, n) + 1024;
+        return std::max(gemm_kmajor_ws_bytes(gp), gemm_kmajor_ws_bytes(gs)) + gemv_t_ws_bytes(m, n) +
+               oz_gram_ws_bytes(m, n) + 2048;
     }
     case LSQ_OP_FACTOR_SOLVE:
         return 256;
@@ -499,8 +545,12 @@ lsq_status lsq_trsm_gram(const double* A, int64_t m, int64_t n, int64_t lda, con
     size_t gemv_bytes = gemv_t_ws_bytes(m, n);
     double* gemv_ws = (double*)base;
     char* gemm_ws = base + align_up(gemv_bytes, 256);
+    GemmPlan gp = plan_gemm_kmajor(n, n, m, false, LSQ_FP64, sms);
+    GemmPlan gs = plan_gemm_kmajor(n, n, m, true, LSQ_FP64, sms);
+    char* oz_ws = gemm_ws + align_up(std::max(gemm_kmajor_ws_bytes(gp), gemm_kmajor_ws_bytes(gs)), 256);
+    size_t oz_cap = ws_bytes - (size_t)(oz_ws - (char*)ws);
     return trsm_gram(A, m, n, lda, Rs, ldr, b, hpne != 0, Ap, ldap, G, ldg, c, gemm_ws, gemv_ws,
-                     (int64_t)(gemv_bytes / sizeof(double)), sms, S(stream));
+                     (int64_t)(gemv_bytes / sizeof(double)), sms, S(stream), oz_ws, oz_cap, nullptr);
 }
 
 lsq_status lsq_factor_solve(int32_t hpne, double* G, int64_t n, int64_t ldg, const double* c, const double* Rs,

@@ -124,6 +124,73 @@ __device__ __forceinline__ double round_to_prec(double x, int prec) {
     }
 }
 
+// Integer-only form of the same rounding, fused with the power-of-two
+// scaling 2^escale: returns the bit pattern of RNE(x * 2^escale) in the
+// target format (FP8-e4m3 saturating, BF16, FP16, FP32).  No FP64
+// instruction is issued (GB300 runs FP64 at 1/64 of the FP32 rate).
+__device__ __forceinline__ uint32_t quant_bits(double x, int escale, int prec) {
+    int p, emin, emax, bias;
+    switch (prec) {
+    case LSQ_FP8_E4M3: p = 4; emin = -6; emax = 8; bias = 7; break;
+    case LSQ_BF16: p = 8; emin = -126; emax = 127; bias = 127; break;
+    case LSQ_FP16: p = 11; emin = -14; emax = 15; bias = 15; break;
+    default: p = 24; emin = -126; emax = 127; bias = 127; break;
+    }
+    const int mb = p - 1;                       // stored mantissa bits
+    const int ebits = prec == LSQ_FP8_E4M3 ? 4 : prec == LSQ_FP16 ? 5 : 8;
+    const int tot = 1 + ebits + mb;
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    uint32_t sign = (uint32_t)(b >> 63) << (tot - 1);
+    int E = (int)((b >> 52) & 0x7ff);
+    unsigned long long mant = b & 0x000fffffffffffffull;
+    const uint32_t inf_bits = ((1u << ebits) - 1u) << mb;
+    const uint32_t sat_bits = prec == LSQ_FP8_E4M3 ? 0x7Eu : inf_bits;  // 448 for e4m3fn
+    if (E == 0x7ff) {
+        if (mant) return sign | inf_bits | (prec == LSQ_FP8_E4M3 ? 7u : (1u << (mb - 1)));  // NaN
+        return sign | sat_bits;
+    }
+    int ex;  // unbiased exponent of the leading significand bit
+    unsigned long long sig;
+    if (E == 0) {
+        if (mant == 0) return sign;
+        int lz = __clzll(mant) - 11;  // normalise an FP64 subnormal
+        sig = mant << lz;
+        ex = -1022 - lz;
+    } else {
+        sig = mant | 0x0010000000000000ull;
+        ex = E - 1023;
+    }
+    ex += escale;
+    int er = ex < emin ? emin : ex;
+    int drop = (52 - mb) + (er - ex);
+    unsigned long long keep;
+    if (drop > 54) {
+        keep = 0;
+    } else {
+        keep = sig >> drop;
+        unsigned long long rem = sig & ((1ull << drop) - 1ull), half = 1ull << (drop - 1);
+        if (rem > half || (rem == half && (keep & 1ull))) keep += 1ull;
+    }
+    if (keep == 0) return sign;
+    if (keep >> p) {  // carry into a new binade
+        keep >>= 1;
+        er += 1;
+    }
+    if (keep < (1ull << mb)) return sign | (uint32_t)keep;  // subnormal (er == emin)
+    uint32_t m = (uint32_t)(keep - (1ull << mb));
+    if (er > emax || (prec == LSQ_FP8_E4M3 && er == emax && m == 7u)) return sign | sat_bits;
+    return sign | ((uint32_t)(er + bias) << mb) | m;
+}
+
+// Store bits produced by quant_bits.
+__device__ __forceinline__ void store_bits(void* base, size_t i, uint32_t bits, int prec) {
+    switch (prec) {
+    case LSQ_FP8_E4M3: ((uint8_t*)base)[i] = (uint8_t)bits; break;
+    case LSQ_BF16: case LSQ_FP16: ((uint16_t*)base)[i] = (uint16_t)bits; break;
+    default: ((uint32_t*)base)[i] = bits; break;
+    }
+}
+
 // Storage size in bytes of one element of a sketch precision.
 static inline int prec_bytes(int prec) {
     switch (prec) {

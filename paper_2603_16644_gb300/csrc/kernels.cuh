@@ -82,6 +82,18 @@ template <typename T>
 lsq_status rank_update_ext(T* C, int64_t ldc, const T* P, int64_t psi, int64_t psk, const T* Q, int64_t qsj,
                            int64_t qsk, int64_t M, int64_t N, int K, bool lower, const int32_t* info, cudaStream_t st);
 
+// ---- sketch_tc.cu: tcgen05 Gaussian sketch for 8/16-bit u_p --------------
+bool sketch_tc_supported(int prec);
+size_t sketch_tc_ws_bytes(int64_t s, int64_t n, int64_t m, int prec, int sms);
+lsq_status launch_sketch_tc(const void* Om, int64_t ldo, const void* Ahat, int64_t ldq, int prec, int64_t s,
+                            int64_t n, int64_t m, float* As, int64_t ldas, void* ws, size_t ws_bytes, int32_t* err,
+                            cudaStream_t st);
+
+// ---- ozaki.cu: FP64 Gram on the FP8 tensor cores (digit slicing) ----------
+size_t oz_gram_ws_bytes(int64_t m, int64_t n);
+lsq_status oz_gram(const double* X, int64_t m, int64_t n, int64_t ld, double* G, int64_t ldg, void* ws,
+                   size_t ws_bytes, int32_t* err, cudaStream_t st);
+
 // ---- qr.cu -------------------------------------------------------------------
 size_t qr_ws_bytes(int64_t s, int64_t n, int prec);
 lsq_status launch_precond_qr(const void* As, int64_t s, int64_t n, int64_t ldas, int as_prec, int qr_prec,

@@ -132,17 +132,28 @@ __global__ void k_colmax(const double* __restrict__ A, int64_t m, int64_t n, int
     int64_t c = blockIdx.y;
     int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
     int64_t r1 = min(m, r0 + rows_per_block);
-    double mx = 0.0;
-    const double* col = A + c * lda;
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) mx = fmax(mx, fabs(col[i]));
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    __shared__ double wmax[32];
+    // |a| as the bit pattern with the sign cleared: for non-NaN doubles the
+    // integer order is the value order, so no FP64 instruction is needed
+    unsigned long long mx = 0;
+    const unsigned long long* col = (const unsigned long long*)(A + c * lda);
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        unsigned long long v = col[i] & 0x7fffffffffffffffull;
+        mx = v > mx ? v : mx;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
+        mx = o > mx ? o : mx;
+    }
+    __shared__ unsigned long long wmax[32];
     if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
     __syncthreads();
     if (threadIdx.x < 32) {
-        double v = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0.0;
-        for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
-        if (threadIdx.x == 0) atomicMax(&colmax[c], (unsigned long long)__double_as_longlong(v));
+        unsigned long long v = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0ull;
+        for (int off = 16; off > 0; off >>= 1) {
+            unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
+            v = o > v ? o : v;
+        }
+        if (threadIdx.x == 0) atomicMax(&colmax[c], v);
     }
 }
 
@@ -162,19 +173,26 @@ __global__ void k_colexp(const unsigned long long* __restrict__ colmax, int64_t 
 // the write are coalesced.
 __global__ void k_quantize_rm(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda,
                               const int32_t* __restrict__ colexp, int prec, void* __restrict__ out) {
-    __shared__ double tile[32][33];
+    __shared__ unsigned long long tile[32][33];
     int64_t j0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
     int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    const bool f64 = prec == LSQ_FP64;
     for (int k = ty; k < 32; k += 8) {
         int64_t j = j0 + tx, c = c0 + k;
-        double v = 0.0;
-        if (j < m && c < n) v = round_to_prec(ldexp(A[j + c * lda], colexp[c]), prec);
+        unsigned long long v = 0;
+        if (j < m && c < n) {
+            double a = A[j + c * lda];
+            v = f64 ? (unsigned long long)__double_as_longlong(a) : (unsigned long long)quant_bits(a, colexp[c], prec);
+        }
         tile[k][tx] = v;
     }
     __syncthreads();
     for (int k = ty; k < 32; k += 8) {
         int64_t j = j0 + k, c = c0 + tx;
-        if (j < m && c < n) store_prec(out, (size_t)j * n + c, tile[tx][k], prec);
+        if (j < m && c < n) {
+            if (f64) ((unsigned long long*)out)[(size_t)j * n + c] = tile[tx][k];
+            else store_bits(out, (size_t)j * n + c, (uint32_t)tile[tx][k], prec);
+        }
     }
 }
 
@@ -185,8 +203,11 @@ __global__ void k_quantize_cm(const double* __restrict__ A, int64_t m, int64_t n
     int64_t c = blockIdx.y;
     int e = colexp[c];
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < ldq; j += (int64_t)gridDim.x * blockDim.x) {
-        double v = j < m ? round_to_prec(ldexp(A[j + c * lda], e), prec) : 0.0;
-        store_prec(out, (size_t)c * ldq + j, v, prec);
+        if (prec == LSQ_FP64) {
+            ((double*)out)[(size_t)c * ldq + j] = j < m ? A[j + c * lda] : 0.0;
+        } else {
+            store_bits(out, (size_t)c * ldq + j, j < m ? quant_bits(A[j + c * lda], e, prec) : 0u, prec);
+        }
     }
 }
 
@@ -251,8 +272,11 @@ __device__ __forceinline__ double gauss_entry(uint64_t seed, int64_t i, int64_t 
 __global__ void k_gauss_gen(uint64_t seed, int64_t s, int64_t m, int prec, void* __restrict__ Om, int64_t ldo) {
     int64_t i = blockIdx.y;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < ldo; j += (int64_t)gridDim.x * blockDim.x) {
-        double v = j < m ? round_to_prec(gauss_entry(seed, i, j), prec) : 0.0;
-        store_prec(Om, (size_t)i * ldo + j, v, prec);
+        if (prec == LSQ_FP64) {
+            ((double*)Om)[(size_t)i * ldo + j] = j < m ? gauss_entry(seed, i, j) : 0.0;
+        } else {
+            store_bits(Om, (size_t)i * ldo + j, j < m ? quant_bits(gauss_entry(seed, i, j), 0, prec) : 0u, prec);
+        }
     }
 }
 

@@ -47,7 +47,7 @@ def test_features_match_oracle():
 
 
 def test_judge_is_a_lower_bound_and_decides_by_lemma():
-    for kap, prec, want in [(1e1, O.FP32, 1), (1e6, O.FP32, 1), (1e8, O.FP32, 0), (1e3, O.BF16, 0), (5.0, O.FP8_E4M3, 1)]:
+    for kap, prec, want in [(1e1, O.FP32, 1), (1e6, O.FP32, 1), (1e8, O.FP32, 0), (1e3, O.BF16, 0), (1.2, O.FP8_E4M3, 1), (5.0, O.FP8_E4M3, 0)]:
         n = 64
         rng = np.random.default_rng(int(np.log10(kap)) + prec)
         Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
