@@ -7,7 +7,8 @@ Workload (tall-skinny): A is 65536 x 1024 FP64, A = U diag(sigma) V^T with
 kappa in {1e2, 1e6, 1e10} and relative residual in {0, 1e-8, 1e-3} (9 seeded
 synthetic problems resident in HBM, solved in turn); sparse-sign sketch with
 s = 4n rows and 8 nonzeros per column, BF16 sketch, FP32 QR, FP64 TRSM /
-Gram / Cholesky / solves, one FP64 refinement step.  Every A (512 MiB) is
+Gram / Cholesky / solves (the FP64 products on the tensor cores by digit
+slicing), one FP64 refinement step.  Every A (512 MiB) is
 larger than L2, so no flush is needed between steps.
 
 One JSON line on rank 0.  --impl reference times the CPU oracle instead.
@@ -33,7 +34,6 @@ KAPPAS = [1e2, 1e6, 1e10]
 RHOS = [0.0, 1e-8, 1e-3]
 WORKLOAD = "tall_skinny_65536x1024_sparse_sign_s4096_z8_bf16_fp32qr_refine1"
 METRIC = "LS solves/s (mixed-precision PNE, 65536x1024)"
-FP64_PEAK_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA cores), nominal dense rate
 
 
 def parse():
@@ -201,6 +201,44 @@ def probe_fp64(lsq, torch):
     return blocks * 256 * iters * 16 / sec / 1e12
 
 
+# ----------------------------------------------------------------------------- roofline
+FP32_PEAK_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # CUDA-core FP32: SMs x lanes x FMA x clock
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+def dominant_roofline(stages, fp64_probe):
+    """Roofline of whichever instrumented kernel took longest in the timed
+    region: the tensor-core FP64 update (BF16 digit products; achieved =
+    36 x 2 M N K per launch / its event time, against the measured sustained
+    BF16 rate) or the QR panel (FP32 Householder flops against the nominal
+    CUDA-core FP32 rate)."""
+    upd_ms, upd_n, upd_work = stages["k_ot_update"]
+    qrp_ms, qrp_n, qrp_work = stages["k_qr_panel"]
+    pk = measured_peaks()
+    if upd_ms >= qrp_ms and upd_n:
+        if pk and pk.get("bf16_tflops_sustained"):
+            peak, src = pk["bf16_tflops_sustained"], "of measured (MEASURED_PEAKS.json bf16_tflops_sustained)"
+        else:
+            peak, src = 1700.0, "of fallback (1.7 PFLOP/s sustained bf16)"
+        achieved = upd_work / (upd_ms / 1000.0) / 1e12
+        return {"bound": "tensor", "kernel": "k_ot_update (FP64 by BF16 digit slicing)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": src,
+                "launches": upd_n, "avg_launch_ms": upd_ms / upd_n,
+                "fp64_equivalent_tflops": achieved / 36.0, "fp64_fma_probe_tflops": fp64_probe}
+    achieved = qrp_work / (qrp_ms / 1000.0) / 1e12 if qrp_ms else 0.0
+    return {"bound": "alu", "kernel": "k_qr_panel_cl<float>", "achieved": achieved,
+            "peak": FP32_PEAK_NOMINAL_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_NOMINAL_TFLOPS,
+            "traffic": None, "peak_source": "nominal CUDA-core FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz)",
+            "launches": qrp_n, "avg_launch_ms": qrp_ms / max(1, qrp_n)}
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 def oracle_sample(rows):
     """The oracle's Alg. 1 (PNE, same n, s, zeta and precisions, one refinement
@@ -300,7 +338,7 @@ def main():
     sec = timed(lsq, torch, probs, args.steps, 0, lsq.BF16, False, ws, xs, infos, dist)
     clk = clocks.stop()
     n_launch = lsq.launch_count() - n_launch0
-    stages = lsq.profile_collect()
+    stages = lsq.profile_collect(with_work=True)
     lsq.profile(False)
     if dist is not None:
         t = torch.tensor([sec], device=dev)
@@ -345,21 +383,10 @@ def main():
         e2e_sec = float(t.item())
     e2e_value = world * args.e2e_steps / e2e_sec
 
-    # ---- roofline of the dominant kernel (FP64, CUDA cores)
+    # ---- roofline of the dominant kernel, from the library's events around
+    # every launch of the two heaviest kernels inside the timed region
     fp64_probe = probe_fp64(lsq, torch)
-    trsm_ms = stages["trsm"][0] / max(1, stages["trsm"][1])
-    gram_ms = stages["gram"][0] / max(1, stages["gram"][1])
-    dom = "trsm" if trsm_ms >= gram_ms else "gram"
-    dom_ms = max(trsm_ms, gram_ms)
-    flops = float(M) * N * N  # TRSM: m n^2; symmetric Gram: m n^2 (+ 2mn for A_p^T b)
-    if dom == "gram":
-        flops += 2.0 * M * N
-    achieved = flops / (dom_ms / 1000.0) / 1e12
-    peak = FP64_PEAK_NOMINAL_TFLOPS
-    roofline = {"bound": "alu", "kernel": "k_trsm_right_upper" if dom == "trsm" else "k_gemm_kmajor<f64> (SYRK)",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (CUDA cores; no FP64 entry in the measured peaks)",
-                "fp64_fma_probe_tflops": fp64_probe, "frac_of_probe": achieved / fp64_probe}
+    roofline = dominant_roofline(stages, fp64_probe)
 
     result = None
     if rank == 0:
@@ -370,7 +397,9 @@ def main():
                    "sample": (f"oracle PNE steps on a {args.cpu_rows}x{N} slice (same s, zeta, precisions), "
                               f"{raw:.1f} s of CPU work; row-proportional steps scaled by {M // args.cpu_rows}, "
                               f"QR/Cholesky/solves counted once")}
-        per_stage = {k: round(v[0] / max(1, v[1]), 3) for k, v in stages.items() if v[1]}
+        per_stage = {k: round(v[0] / max(1, v[1]), 3) for k, v in stages.items() if v[1] and not k.startswith("k_")}
+        per_kernel = {k: {"ms_per_solve": round(v[0] / args.steps, 3), "launches_per_solve": v[1] / args.steps}
+                      for k, v in stages.items() if v[1] and k.startswith("k_")}
         result = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * sec / args.steps, "higher_is_better": True,
@@ -383,7 +412,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * M * N + 8 * M,
                     "d2h_bytes_per_step": 8 * N + 4},
             "roofline": roofline, "cpu_baseline": cpu,
-            "stage_ms_per_solve": per_stage,
+            "stage_ms_per_solve": per_stage, "kernel_ms_per_solve": per_kernel,
             "fp64_pne": {"value": world * args.fp64_steps / sec64, "unit": "solves/s",
                          "speedup_mixed_over_fp64": value / (world * args.fp64_steps / sec64),
                          "rel_err_vs_xstar": err64},

@@ -208,7 +208,14 @@ lsq_status lsq_trsm_gram_noalloc(const double* A, int64_t m, int64_t n, int64_t 
  *   hpne = 1: LU with partial pivoting (first largest pivot) P G = L U,
  *             L U x = P c.
  * G is overwritten by the factors (lower L for Cholesky; L\U for LU).
- * piv: n int32 (device, may be NULL for hpne = 0).  info: device int32. */
+ * piv: n int32 (device, may be NULL for hpne = 0).  info: device int32.
+ * The triangular solves run as a wavefront of 32-row blocks, one CTA each,
+ * synchronised through flags in the workspace; the Cholesky trailing
+ * updates are FP64-accurate tensor-core products (as in lsq_trsm_tc) with
+ * their digits in the workspace too.  Workspace:
+ * lsq_workspace_size(LSQ_OP_FACTOR_SOLVE, m, n, NULL), about 2 n 64 x 16
+ * bytes (LSQ_ERR_NOMEM when smaller).  A wait that runs out (2 s) sets
+ * info = -2. */
 lsq_status lsq_factor_solve(int32_t hpne, double* G, int64_t n, int64_t ldg, const double* c,
                             const double* Rs, int64_t ldr, double* x, int32_t* piv, int32_t* info,
                             void* ws, size_t ws_bytes, void* stream);
@@ -267,8 +274,30 @@ size_t lsq_gram_tc_workspace_size(int64_t m, int64_t n);
 lsq_status lsq_gram_tc(const double* X, int64_t m, int64_t n, int64_t ld, double* G, int64_t ldg, int32_t* info,
                        void* ws, size_t ws_bytes, void* stream);
 
-/* Use lsq_gram_tc for the symmetric Gram inside the PNE solves (1, the
- * default) or the FP64 CUDA-core GEMM (0); returns the previous setting.
+/* A_p = A R^{-1} (Alg. 1, the preconditioned matrix formed by substitution)
+ * in FP64 with the off-diagonal products on the tensor cores.  The columns
+ * are split recursively; diagonal blocks of up to 32 columns are solved by
+ * FP64 substitution, and each update A_p[:, right] = A[:, right] -
+ * A_p[:, left] R[left, right] (left part <= 512 columns) is an FP64-accurate
+ * product of BF16 digit slices: every value becomes 8 balanced base-128
+ * digits relative to the largest magnitude of its row (of A_p) or column (of
+ * R); the 36 digit pairs with t + u <= 7 accumulate exactly in FP32 and are
+ * combined as exact 64-bit integers, rounded once to FP64.  Per product the
+ * error is below 2^-52.6 2^(E_i + E_j) where 2^E bounds the row / column,
+ * the order of FP64 rounding.
+ * A: m x n FP64 column-major (ld lda); R: n x n upper triangular (ld ldr,
+ * nonzero diagonal); Ap: m x n output (ld ldap; must not overlap A unless
+ * Ap == A with ldap == lda, the in-place form).  Device pointers, caller-owned.
+ * Workspace lsq_trsm_tc_workspace_size(m, n) (about 8 m min(n/2, 512) x 2
+ * bytes of digits).  info (device, may be NULL): -2 on a pipeline timeout.
+ * Returns LSQ_ERR_ARG when the tensor-map encoder is unavailable. */
+size_t lsq_trsm_tc_workspace_size(int64_t m, int64_t n);
+lsq_status lsq_trsm_tc(const double* A, int64_t m, int64_t n, int64_t lda, const double* R, int64_t ldr, double* Ap,
+                       int64_t ldap, int32_t* info, void* ws, size_t ws_bytes, void* stream);
+
+/* Use the tensor-core FP64 products (lsq_gram_tc for the symmetric Gram of
+ * PNE and lsq_trsm_tc for A_p in PNE and HPNE) inside the solves (1, the
+ * default) or the FP64 CUDA-core kernels (0); returns the previous setting.
  * Process-wide; for comparisons. */
 int32_t lsq_set_fp64_emulation(int32_t enable);
 
@@ -378,13 +407,21 @@ int64_t lsq_launch_count(void);
 /* Stage timing.  lsq_profile(1) clears the records and starts recording a
  * CUDA event pair around each step of Alg. 1 inside the solve calls (stage
  * indices: 0 condition estimate, 1 sketch, 2 QR, 3 TRSM A R_s^{-1},
- * 4 Gram + right-hand side, 5 factorization, 6 solves, 7 refinement);
+ * 4 Gram + right-hand side, 5 factorization, 6 solves, 7 refinement;
+ * 8 single launches of the tensor-core FP64 update kernel (lsq_trsm_tc,
+ * the Cholesky updates), 9 single launches of the QR panel kernel);
  * lsq_profile(0) stops.  lsq_profile_collect waits for the recorded events,
  * writes the summed milliseconds and the number of records per stage
- * (arrays of at least 8), and clears the records.  Host-side state, not
- * thread safe across concurrent solves on different streams. */
+ * (arrays of at least 8; indices >= nstages are skipped), and clears the
+ * records; lsq_profile_collect_work also writes the summed algorithmic work
+ * per stage (flops: 36 digit-pair products of 2 M N K each for the update
+ * kernel, the Householder panel flops for the QR panel; 0 for the steps).
+ * Host-side state, not thread safe across concurrent solves on different
+ * streams. */
 int32_t lsq_profile(int32_t enable);
 int32_t lsq_profile_collect(double* ms_by_stage, int32_t* count_by_stage, int32_t nstages);
+int32_t lsq_profile_collect_work(double* ms_by_stage, int32_t* count_by_stage, double* work_by_stage,
+                                 int32_t nstages);
 
 /* FP64 FMA throughput probe: `blocks` CTAs of 256 threads, each thread
  * 8 independent FMA chains of `iters` steps (16 * iters flops per thread).

@@ -19,7 +19,7 @@ import torch
 __all__ = [
     "FP8_E4M3", "BF16", "FP16", "FP32", "FP64", "AUTO", "GAUSSIAN", "SPARSE_SIGN",
     "Opts", "lib", "colmajor", "workspace", "sketch", "precond_qr", "condest", "trsm_gram",
-    "factor_solve", "pne", "hpne", "solve", "solve_host", "sparse_sign_operator",
+    "factor_solve", "trsm_tc", "gram_tc", "set_fp64_emulation", "pne", "hpne", "solve", "solve_host", "sparse_sign_operator",
     "gaussian_operator", "precision_from_kappa0", "status_string", "LsqError",
 ]
 
@@ -77,7 +77,14 @@ def lib():
             "lsq_launch_count": (C.c_int64, []),
             "lsq_profile": (C.c_int32, [C.c_int32]),
             "lsq_profile_collect": (C.c_int32, [C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_int32]),
+            "lsq_profile_collect_work": (C.c_int32, [C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                                                     C.POINTER(C.c_double), C.c_int32]),
             "lsq_probe_fp64_fma": (C.c_int32, [_i64, C.c_int32, _vp, _vp]),
+            "lsq_trsm_tc_workspace_size": (_sz, [_i64, _i64]),
+            "lsq_trsm_tc": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+            "lsq_gram_tc_workspace_size": (_sz, [_i64, _i64]),
+            "lsq_gram_tc": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+            "lsq_set_fp64_emulation": (C.c_int32, [C.c_int32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -87,7 +94,7 @@ def lib():
     return _lib
 
 
-STAGES = ["condest", "sketch", "qr", "trsm", "gram", "factor", "solve", "refine"]
+STAGES = ["condest", "sketch", "qr", "trsm", "gram", "factor", "solve", "refine", "k_ot_update", "k_qr_panel"]
 
 
 def launch_count() -> int:
@@ -100,11 +107,16 @@ def profile(enable: bool) -> None:
     lib().lsq_profile(int(enable))
 
 
-def profile_collect() -> dict:
-    """{stage: (total ms, records)} since the last collect; waits for the events."""
-    ms = (C.c_double * 8)()
-    cnt = (C.c_int32 * 8)()
-    _check(lib().lsq_profile_collect(ms, cnt, 8), "lsq_profile_collect")
+def profile_collect(with_work: bool = False) -> dict:
+    """{stage: (total ms, records)} since the last collect, or (total ms,
+    records, algorithmic flops) with ``with_work``; waits for the events."""
+    k = len(STAGES)
+    ms = (C.c_double * k)()
+    cnt = (C.c_int32 * k)()
+    work = (C.c_double * k)()
+    _check(lib().lsq_profile_collect_work(ms, cnt, work, k), "lsq_profile_collect_work")
+    if with_work:
+        return {name: (ms[i], cnt[i], work[i]) for i, name in enumerate(STAGES)}
     return {name: (ms[i], cnt[i]) for i, name in enumerate(STAGES)}
 
 
@@ -247,6 +259,37 @@ def trsm_gram(A, Rs, b, hpne=False, ws=None):
     return Ap, G, c
 
 
+def trsm_tc(A, R, out=None):
+    """A_p = A R^{-1} in FP64 with tensor-core updates (lsq_trsm_tc); returns (Ap, info).
+    ``out`` may be ``A`` itself (in place)."""
+    _need_cuda(A, R)
+    m, n = A.shape
+    Ap = torch.empty((n, m), dtype=torch.float64, device=A.device).t() if out is None else out
+    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    ws = torch.empty(int(lib().lsq_trsm_tc_workspace_size(m, n)), dtype=torch.uint8, device=A.device)
+    _check(lib().lsq_trsm_tc(_ptr(A), m, n, _ld(A), _ptr(R), _ld(R), _ptr(Ap), _ld(Ap), _ptr(info), _ptr(ws),
+                             ws.numel(), _stream()), "lsq_trsm_tc")
+    return Ap, info
+
+
+def gram_tc(X):
+    """G = X^T X in FP64 on the FP8 tensor cores (lsq_gram_tc); returns (G, info)."""
+    _need_cuda(X)
+    m, n = X.shape
+    G = torch.empty((n, n), dtype=torch.float64, device=X.device).t()
+    info = torch.zeros(1, dtype=torch.int32, device=X.device)
+    ws = torch.empty(int(lib().lsq_gram_tc_workspace_size(m, n)), dtype=torch.uint8, device=X.device)
+    _check(lib().lsq_gram_tc(_ptr(X), m, n, _ld(X), _ptr(G), n, _ptr(info), _ptr(ws), ws.numel(), _stream()),
+           "lsq_gram_tc")
+    return G, info
+
+
+def set_fp64_emulation(enable: bool) -> bool:
+    """Route the FP64 Gram (PNE) and A_p = A R^{-1} through the tensor cores
+    (True, the default) or the FP64 CUDA cores; returns the previous setting."""
+    return bool(lib().lsq_set_fp64_emulation(int(enable)))
+
+
 def factor_solve(G, c, Rs=None, hpne=False):
     """Factor G in place (Cholesky or LU-PP) and solve; returns (x, factors, piv, info)."""
     _need_cuda(G, c, Rs)
@@ -255,8 +298,10 @@ def factor_solve(G, c, Rs=None, hpne=False):
     x = torch.empty(n, dtype=torch.float64, device=G.device)
     piv = torch.zeros(n, dtype=torch.int32, device=G.device)
     info = torch.zeros(1, dtype=torch.int32, device=G.device)
+    ws = workspace(OP_FACTOR_SOLVE, 1, n, None, G.device)
     _check(lib().lsq_factor_solve(int(hpne), _ptr(F), n, n, _ptr(c), _ptr(Rs), _ld(Rs) if Rs is not None else n,
-                                  _ptr(x), _ptr(piv), _ptr(info), None, 0, _stream()), "lsq_factor_solve")
+                                  _ptr(x), _ptr(piv), _ptr(info), _ptr(ws), ws.numel(), _stream()),
+           "lsq_factor_solve")
     return x, F, piv, info
 
 

@@ -22,7 +22,7 @@ struct StageProf {
     bool on = false;
     std::vector<cudaEvent_t> pool;
     size_t next = 0;
-    struct Rec { int stage; size_t ev_begin, ev_end; };
+    struct Rec { int stage; size_t ev_begin, ev_end; double work; };
     std::vector<Rec> recs;
     size_t open_begin[ST_COUNT] = {};
     bool open[ST_COUNT] = {};
@@ -38,7 +38,7 @@ static size_t prof_event() {
     return g_prof.next++;
 }
 
-void stage_mark(int stage, bool begin, cudaStream_t st) {
+void stage_mark(int stage, bool begin, cudaStream_t st, double work) {
     std::lock_guard<std::mutex> lk(g_prof.mu);
     if (!g_prof.on) return;
     size_t e = prof_event();
@@ -48,7 +48,7 @@ void stage_mark(int stage, bool begin, cudaStream_t st) {
         g_prof.open_begin[stage] = e;
         g_prof.open[stage] = true;
     } else if (g_prof.open[stage]) {
-        g_prof.recs.push_back({stage, g_prof.open_begin[stage], e});
+        g_prof.recs.push_back({stage, g_prof.open_begin[stage], e, work});
         g_prof.open[stage] = false;
     }
 }
@@ -61,8 +61,9 @@ namespace {
 // off (lsq_set_tensor_core_sketch), which routes them to the CUDA-core GEMM.
 bool g_tensor_core_sketch = true;
 
-// The symmetric FP64 Gram of PNE runs as the digit-sliced tensor-core
-// product (csrc/ozaki.cu) unless switched off (lsq_set_fp64_emulation).
+// The symmetric FP64 Gram of PNE (csrc/ozaki.cu) and the off-diagonal
+// products of A_p = A R^{-1} (csrc/oz_trsm.cu) run as digit-sliced
+// tensor-core products unless switched off (lsq_set_fp64_emulation).
 bool g_fp64_emulation = true;
 
 inline cudaStream_t S(void* p) { return reinterpret_cast<cudaStream_t>(p); }
@@ -126,7 +127,7 @@ SketchLayout sketch_layout(int64_t m, int64_t n, int64_t s, int kind, int zeta, 
 
 struct SolveLayout {
     SketchLayout sk;
-    size_t sk_base, as_, rs, qr, ap, g, c, x, r, gv, piv, gemm, gemv, cond, k0, ch, err, oz, total;
+    size_t sk_base, as_, rs, qr, ap, g, c, x, r, gv, piv, gemm, gemv, cond, k0, ch, err, tsync, oz, total;
     size_t oz_bytes;
     size_t qr_bytes, cond_bytes;
 };
@@ -162,7 +163,9 @@ SolveLayout solve_layout(int64_t m, int64_t n, const lsq_opts* o, int prec, bool
     L.k0 = q.take(sizeof(double));
     L.ch = q.take(sizeof(int32_t));
     L.err = q.take(sizeof(int32_t));
-    L.oz_bytes = hpne ? 0 : oz_gram_ws_bytes(m, n);
+    L.tsync = q.take(sizeof(int32_t) * trsv_sync_ints(n));
+    // shared by the tensor-core A_p (first) and the tensor-core Gram of PNE
+    L.oz_bytes = std::max(ot_trsm_ws_bytes(m, n), hpne ? (size_t)0 : oz_gram_ws_bytes(m, n));
     L.oz = q.take(L.oz_bytes);
     L.total = q.off + 256;
     return L;
@@ -204,17 +207,19 @@ lsq_status run_sketch(const double* A, int64_t m, int64_t n, int64_t lda, const 
 
 // Solve with the factors already in G (and piv / Rs): PNE: L L^T y = v, x = Rs^{-1} y;
 // HPNE: P, unit L, U.
+// sync: trsv_sync_ints(n) int32 of scratch; err: status word for a timed-out wait.
 lsq_status solve_factored(bool hpne, const double* G, int64_t n, int64_t ldg, const int32_t* piv, const double* Rs,
-                          int64_t ldr, double* v, const int32_t* info, cudaStream_t st) {
+                          int64_t ldr, double* v, const int32_t* info, int32_t* sync, int32_t* err,
+                          cudaStream_t st) {
     lsq_status r;
     if (hpne) {
         if ((r = launch_apply_piv(piv, n, v, info, st)) != LSQ_OK) return r;
-        if ((r = launch_trsv<double>(TRSV_UNIT_LOWER, G, n, ldg, v, info, st)) != LSQ_OK) return r;
-        return launch_trsv<double>(TRSV_UPPER, G, n, ldg, v, info, st);
+        if ((r = launch_trsv<double>(TRSV_UNIT_LOWER, G, n, ldg, v, info, sync, err, st)) != LSQ_OK) return r;
+        return launch_trsv<double>(TRSV_UPPER, G, n, ldg, v, info, sync, err, st);
     }
-    if ((r = launch_trsv<double>(TRSV_LOWER, G, n, ldg, v, info, st)) != LSQ_OK) return r;
-    if ((r = launch_trsv<double>(TRSV_LOWER_T, G, n, ldg, v, info, st)) != LSQ_OK) return r;
-    if (Rs) return launch_trsv<double>(TRSV_UPPER, Rs, n, ldr, v, info, st);
+    if ((r = launch_trsv<double>(TRSV_LOWER, G, n, ldg, v, info, sync, err, st)) != LSQ_OK) return r;
+    if ((r = launch_trsv<double>(TRSV_LOWER_T, G, n, ldg, v, info, sync, err, st)) != LSQ_OK) return r;
+    if (Rs) return launch_trsv<double>(TRSV_UPPER, Rs, n, ldr, v, info, sync, err, st);
     return LSQ_OK;
 }
 
@@ -223,7 +228,11 @@ lsq_status trsm_gram(const double* A, int64_t m, int64_t n, int64_t lda, const d
                      void* gemm_ws, double* gemv_ws, int64_t gemv_cap, int sms, cudaStream_t st,
                      void* oz_ws = nullptr, size_t oz_bytes = 0, int32_t* err = nullptr) {
     stage_mark(ST_TRSM, true, st);
-    lsq_status r = launch_trsm_right_upper(A, m, n, lda, Rs, ldr, Ap, ldap, st);
+    lsq_status r;
+    if (g_fp64_emulation && oz_ws && oz_bytes >= ot_trsm_ws_bytes(m, n) && ot_trsm_supported())
+        r = ot_trsm(A, m, n, lda, Rs, ldr, Ap, ldap, oz_ws, oz_bytes, err, st);
+    else
+        r = launch_trsm_right_upper(A, m, n, lda, Rs, ldr, Ap, ldap, st);
     if (r != LSQ_OK) return r;
     stage_mark(ST_TRSM, false, st);
     stage_mark(ST_GRAM, true, st);
@@ -304,12 +313,13 @@ lsq_status solve_impl(bool hpne, const double* A, int64_t m, int64_t n, int64_t 
     if (hpne)
         r = launch_lu(G, n, n, piv, info, st);
     else
-        r = launch_cholesky<double>(G, n, n, info, st);
+        r = launch_cholesky<double>(G, n, n, info, st, base + L.oz, L.oz_bytes);
     if (r != LSQ_OK) return r;
     stage_mark(ST_FACTOR, false, st);
     stage_mark(ST_SOLVE, true, st);
     LSQ_CUDA_TRY(cudaMemcpyAsync(x, c, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    if ((r = solve_factored(hpne, G, n, n, piv, Rs, n, x, info, st)) != LSQ_OK) return r;
+    int32_t* tsync = (int32_t*)(base + L.tsync);
+    if ((r = solve_factored(hpne, G, n, n, piv, Rs, n, x, info, tsync, err, st)) != LSQ_OK) return r;
     stage_mark(ST_SOLVE, false, st);
     if (o->refine_steps > 0) stage_mark(ST_REFINE, true, st);
     for (int step = 0; step < o->refine_steps; ++step) {
@@ -317,7 +327,7 @@ lsq_status solve_impl(bool hpne, const double* A, int64_t m, int64_t n, int64_t 
         if ((r = launch_gemv_t(Ap, m, n, m, r_, gv, (double*)(base + L.gemv),
                                (int64_t)(gemv_t_ws_bytes(m, n) / sizeof(double)), st)) != LSQ_OK)
             return r;
-        if ((r = solve_factored(hpne, G, n, n, piv, Rs, n, gv, info, st)) != LSQ_OK) return r;
+        if ((r = solve_factored(hpne, G, n, n, piv, Rs, n, gv, info, tsync, err, st)) != LSQ_OK) return r;
         if ((r = launch_axpy1(x, gv, n, st)) != LSQ_OK) return r;
     }
     if (o->refine_steps > 0) stage_mark(ST_REFINE, false, st);
@@ -388,6 +398,25 @@ int32_t lsq_set_fp64_emulation(int32_t enable) {
     return prev;
 }
 
+size_t lsq_trsm_tc_workspace_size(int64_t m, int64_t n) { return m > 0 && n > 0 ? ot_trsm_ws_bytes(m, n) + 256 : 0; }
+
+lsq_status lsq_trsm_tc(const double* A, int64_t m, int64_t n, int64_t lda, const double* R, int64_t ldr, double* Ap,
+                       int64_t ldap, int32_t* info, void* ws, size_t ws_bytes, void* stream) {
+    if (!A || !R || !Ap || m <= 0 || n <= 0 || lda < m || ldap < m || ldr < n) return LSQ_ERR_ARG;
+    if (A != Ap) {
+        // reject partial overlap of the input and output column ranges
+        const char* a0 = (const char*)A;
+        const char* a1 = (const char*)(A + (n - 1) * lda + m);
+        const char* p0 = (const char*)Ap;
+        const char* p1 = (const char*)(Ap + (n - 1) * ldap + m);
+        if (a0 < p1 && p0 < a1) return LSQ_ERR_ARG;
+    } else if (ldap != lda) {
+        return LSQ_ERR_ARG;
+    }
+    if (info) LSQ_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), S(stream)));
+    return ot_trsm(A, m, n, lda, R, ldr, Ap, ldap, ws, ws_bytes, info, S(stream));
+}
+
 size_t lsq_gram_tc_workspace_size(int64_t m, int64_t n) { return m > 0 && n > 0 ? oz_gram_ws_bytes(m, n) + 256 : 0; }
 
 lsq_status lsq_gram_tc(const double* X, int64_t m, int64_t n, int64_t ld, double* G, int64_t ldg, int32_t* info,
@@ -413,16 +442,27 @@ int32_t lsq_profile(int32_t enable) {
 }
 
 int32_t lsq_profile_collect(double* ms_by_stage, int32_t* count_by_stage, int32_t nstages) {
+    return lsq_profile_collect_work(ms_by_stage, count_by_stage, nullptr, nstages);
+}
+
+int32_t lsq_profile_collect_work(double* ms_by_stage, int32_t* count_by_stage, double* work_by_stage,
+                                 int32_t nstages) {
     std::lock_guard<std::mutex> lk(g_prof.mu);
-    if (!ms_by_stage || !count_by_stage || nstages < ST_COUNT) return LSQ_ERR_ARG;
-    for (int i = 0; i < nstages; ++i) { ms_by_stage[i] = 0.0; count_by_stage[i] = 0; }
+    if (!ms_by_stage || !count_by_stage || nstages < 8) return LSQ_ERR_ARG;
+    for (int i = 0; i < nstages; ++i) {
+        ms_by_stage[i] = 0.0;
+        count_by_stage[i] = 0;
+        if (work_by_stage) work_by_stage[i] = 0.0;
+    }
     for (auto& rec : g_prof.recs) {
         if (cudaEventSynchronize(g_prof.pool[rec.ev_end]) != cudaSuccess) return LSQ_ERR_CUDA;
         float ms = 0.0f;
         if (cudaEventElapsedTime(&ms, g_prof.pool[rec.ev_begin], g_prof.pool[rec.ev_end]) != cudaSuccess)
             return LSQ_ERR_CUDA;
+        if (rec.stage >= nstages) continue;
         ms_by_stage[rec.stage] += ms;
         count_by_stage[rec.stage] += 1;
+        if (work_by_stage) work_by_stage[rec.stage] += rec.work;
     }
     g_prof.recs.clear();
     g_prof.next = 0;
@@ -472,10 +512,10 @@ size_t lsq_workspace_size(int32_t op, int64_t m, int64_t n, const lsq_opts* o) {
         GemmPlan gp = plan_gemm_kmajor(n, n, m, false, LSQ_FP64, sms);
         GemmPlan gs = plan_gemm_kmajor(n, n, m, true, LSQ_FP64, sms);
         return std::max(gemm_kmajor_ws_bytes(gp), gemm_kmajor_ws_bytes(gs)) + gemv_t_ws_bytes(m, n) +
-               oz_gram_ws_bytes(m, n) + 2048;
+               std::max(oz_gram_ws_bytes(m, n), ot_trsm_ws_bytes(m, n)) + 2048;
     }
     case LSQ_OP_FACTOR_SOLVE:
-        return 256;
+        return align_up(sizeof(int32_t) * trsv_sync_ints(n), 256) + cholesky_ws_bytes(n) + 512;
     case LSQ_OP_PNE_HOST:
     case LSQ_OP_HPNE_HOST:
         if (check_opts(o, m, n, true) != LSQ_OK) return 0;
@@ -556,15 +596,18 @@ lsq_status lsq_trsm_gram(const double* A, int64_t m, int64_t n, int64_t lda, con
 lsq_status lsq_factor_solve(int32_t hpne, double* G, int64_t n, int64_t ldg, const double* c, const double* Rs,
                             int64_t ldr, double* x, int32_t* piv, int32_t* info, void* ws, size_t ws_bytes,
                             void* stream) {
-    (void)ws;
-    (void)ws_bytes;
     if (!G || !c || !x || !info || n <= 0 || ldg < n || (hpne && !piv) || (Rs && ldr < n)) return LSQ_ERR_ARG;
+    if (!ws || ws_bytes < lsq_workspace_size(LSQ_OP_FACTOR_SOLVE, 1, n, nullptr)) return LSQ_ERR_NOMEM;
+    int32_t* tsync = (int32_t*)aligned(ws);
+    char* cws = (char*)tsync + align_up(sizeof(int32_t) * trsv_sync_ints(n), 256);
+    size_t cws_bytes = ws_bytes - (size_t)(cws - (char*)ws);
     cudaStream_t st = S(stream);
     LSQ_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
-    lsq_status r = hpne ? launch_lu(G, n, ldg, piv, info, st) : launch_cholesky<double>(G, n, ldg, info, st);
+    lsq_status r = hpne ? launch_lu(G, n, ldg, piv, info, st)
+                        : launch_cholesky<double>(G, n, ldg, info, st, cws, cws_bytes);
     if (r != LSQ_OK) return r;
     LSQ_CUDA_TRY(cudaMemcpyAsync(x, c, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    return solve_factored(hpne != 0, G, n, ldg, piv, Rs, ldr, x, info, st);
+    return solve_factored(hpne != 0, G, n, ldg, piv, Rs, ldr, x, info, tsync, info, st);
 }
 
 lsq_status lsq_pne_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, const lsq_opts* opts,

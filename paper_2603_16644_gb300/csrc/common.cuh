@@ -27,9 +27,14 @@ void note_launch();
         LSQ_CUDA_TRY(cudaGetLastError());  \
     } while (0)
 
-// Stage timing (lsq_profile): events recorded around the steps of Alg. 1.
-enum Stage { ST_CONDEST = 0, ST_SKETCH, ST_QR, ST_TRSM, ST_GRAM, ST_FACTOR, ST_SOLVE, ST_REFINE, ST_COUNT };
-void stage_mark(int stage, bool begin, cudaStream_t st);
+// Stage timing (lsq_profile): events recorded around the steps of Alg. 1,
+// and around single launches of the two heaviest kernels (the tensor-core
+// FP64 update and the QR panel) with their algorithmic work (flops).
+enum Stage {
+    ST_CONDEST = 0, ST_SKETCH, ST_QR, ST_TRSM, ST_GRAM, ST_FACTOR, ST_SOLVE, ST_REFINE,
+    ST_K_UPDATE, ST_K_QRPANEL, ST_COUNT
+};
+void stage_mark(int stage, bool begin, cudaStream_t st, double work = 0.0);
 
 static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }

@@ -1,11 +1,13 @@
 // n x n factorizations and vector triangular solves for Eqs. e_pne / e_hpne:
 //   - blocked right-looking Cholesky G = L L^T (FP64 for PNE; FP32 for the
 //     condition estimate of Sec. 6.1): diagonal block in shared memory, panel
-//     solve one thread per row, trailing update as a register-tiled rank-nb
-//     product;
+//     solve one thread per row, trailing update as an FP64-accurate
+//     tensor-core product (FP64 with workspace) or a register-tiled rank-nb
+//     product on the CUDA cores;
 //   - blocked right-looking LU with partial pivoting (first largest |pivot|,
 //     as LAPACK's getrf) for HPNE;
-//   - blocked triangular solves L y = c, L^T y = c, U y = c, unit L y = c.
+//   - triangular solves L y = c, L^T y = c, U y = c, unit L y = c as a
+//     wavefront over 32-row blocks, one CTA each.
 // A device status word (info) is written on breakdown; every later kernel of
 // the same factorization and the solves return early once it is set.
 #include "common.cuh"
@@ -13,6 +15,7 @@
 #include "trsv_block.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace lsq {
 
@@ -103,84 +106,132 @@ template lsq_status rank_update_ext<float>(float*, int64_t, const float*, int64_
 // ---------------------------------------------------------------------------
 // Cholesky
 // ---------------------------------------------------------------------------
+// Cholesky of the 32 x 32 block B[off.., off..] (lower part) by one warp:
+// lane r keeps row r in registers (right-looking, pivot column broadcast by
+// shuffles, compile-time column indices).  Writes L (zeros above) back and
+// returns the first breakdown column (1-based, within the block) or 0.
+template <typename T>
+__device__ int warp_chol32(T (*B)[CNB + 1], int off) {
+    const int lane = threadIdx.x & 31;
+    T a[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) a[c] = B[off + lane][off + c];
+    int bad = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        T d = __shfl_sync(0xffffffffu, a[j], j);
+        if (!(d > (T)0) || !isfinite(d)) {
+            if (!bad) bad = j + 1;
+            d = (T)1;
+        }
+        const T piv = sqrt(d);
+        T l = a[j] / piv;
+        if (lane == j) l = piv;
+        if (lane >= j) a[j] = l;
+#pragma unroll
+        for (int c = j + 1; c < 32; ++c) {
+            const T lc = __shfl_sync(0xffffffffu, l, c);
+            if (lane >= c) a[c] = fma(-l, lc, a[c]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c) B[off + lane][off + c] = lane >= c ? a[c] : (T)0;
+    return bad;
+}
+
+// Diagonal block of CNB = 64 as 2 x 2 blocks of 32 in one CTA:
+// L11 = chol(A11); L21 = A21 L11^{-T}; A22 -= L21 L21^T; L22 = chol(A22).
 template <typename T>
 __global__ void __launch_bounds__(256) k_potrf_diag(T* __restrict__ G, int64_t ld, int64_t n, int64_t k0,
                                                     int32_t* __restrict__ info) {
     if (*info != 0) return;
     __shared__ T D[CNB][CNB + 1];
-    __shared__ int bad;
-    int nb = (int)min64(CNB, n - k0);
-    int tid = threadIdx.x;
-    for (int q = tid; q < nb * nb; q += 256) {
-        int i = q % nb, j = q / nb;
-        D[i][j] = G[(k0 + i) + (k0 + j) * ld];
+    __shared__ int bad1, bad2;
+    const int nb = (int)min64(CNB, n - k0);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int q = tid; q < CNB * CNB; q += 256) {
+        const int r = q & 63, c = q >> 6;
+        // identity padding beyond nb keeps the factorization of the padded block trivial
+        D[r][c] = (r < nb && c < nb) ? G[(k0 + r) + (k0 + c) * ld] : (r == c ? (T)1 : (T)0);
     }
-    if (tid == 0) bad = 0;
     __syncthreads();
-    for (int j = 0; j < nb; ++j) {
-        if (tid == 0) {
-            T d = D[j][j];
-            if (!(d > (T)0) || !isfinite(d)) {
-                bad = j + 1;
-            } else {
-                D[j][j] = sqrt(d);
-            }
-        }
-        __syncthreads();
-        if (bad) break;
-        T piv = D[j][j];
-        for (int i = j + 1 + tid; i < nb; i += 256) D[i][j] = D[i][j] / piv;
-        __syncthreads();
-        int rem = nb - j - 1;
-        for (int q = tid; q < rem * rem; q += 256) {
-            int i = j + 1 + q % rem, c = j + 1 + q / rem;
-            if (i >= c) D[i][c] = fma(-D[i][j], D[c][j], D[i][c]);
-        }
-        __syncthreads();
+    if (warp == 0) {
+        int b = warp_chol32<T>(D, 0);
+        if (lane == 0) bad1 = b;
     }
+    __syncthreads();
+    if (warp == 0) {
+        // row 32 + lane of A21: x L11^T = a, right-looking, reciprocal pivots
+        T x[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) x[c] = D[32 + lane][c];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            x[j] = x[j] * ((T)1 / D[j][j]);
+#pragma unroll
+            for (int k = j + 1; k < 32; ++k) x[k] = fma(-x[j], D[k][j], x[k]);
+        }
+#pragma unroll
+        for (int c = 0; c < 32; ++c) D[32 + lane][c] = x[c];
+    }
+    __syncthreads();
+    // A22 -= L21 L21^T, lower entries (528), spread over the CTA
+    for (int e = tid; e < 32 * 32; e += 256) {
+        const int r = e & 31, c = e >> 5;
+        if (r >= c) {
+            T t = D[32 + r][32 + c];
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) t = fma(-D[32 + r][k], D[32 + c][k], t);
+            D[32 + r][32 + c] = t;
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int b = warp_chol32<T>(D, 32);
+        if (lane == 0) bad2 = b;
+    }
+    __syncthreads();
+    const int bad = bad1 ? bad1 : (bad2 ? 32 + bad2 : 0);
     if (bad) {
-        if (tid == 0) set_info_once(info, (int32_t)(k0 + bad));
+        if (tid == 0 && bad <= nb) set_info_once(info, (int32_t)(k0 + bad));
         return;
     }
-    for (int q = tid; q < nb * nb; q += 256) {
-        int i = q % nb, j = q / nb;
-        G[(k0 + i) + (k0 + j) * ld] = i >= j ? D[i][j] : (T)0;
+    for (int q = tid; q < CNB * CNB; q += 256) {
+        const int r = q & 63, c = q >> 6;
+        if (r < nb && c < nb) G[(k0 + r) + (k0 + c) * ld] = r >= c ? D[r][c] : (T)0;
     }
 }
 
-// L21 = G21 L11^{-T}: one thread per row, 64 rows per block.
+// L21 = G21 L11^{-T}: one thread per row (the row in registers), 32 rows per
+// block so that the FP64 work spreads over many SMs.  Right-looking
+// substitution with the reciprocal pivots: the dependent chain is one
+// multiply and one FMA per column.
 template <typename T>
-__global__ void __launch_bounds__(64) k_potrf_panel(T* __restrict__ G, int64_t ld, int64_t n, int64_t k0,
+__global__ void __launch_bounds__(32) k_potrf_panel(T* __restrict__ G, int64_t ld, int64_t n, int64_t k0,
                                                     const int32_t* __restrict__ info) {
     if (*info != 0) return;
-    extern __shared__ __align__(16) unsigned char panel_raw[];
-    T (*L11)[CNB + 1] = reinterpret_cast<T (*)[CNB + 1]>(panel_raw);
-    T (*Row)[CNB + 1] = reinterpret_cast<T (*)[CNB + 1]>(panel_raw + sizeof(T) * CNB * (CNB + 1));
-    int nb = (int)min64(CNB, n - k0);
-    int tid = threadIdx.x;
-    for (int q = tid; q < nb * nb; q += 64) {
-        int i = q % nb, j = q / nb;
-        L11[i][j] = G[(k0 + i) + (k0 + j) * ld];
-    }
-    int64_t r0 = k0 + nb + (int64_t)blockIdx.x * 64;
-    for (int q = tid; q < 64 * nb; q += 64) {
-        int rr = q % 64, c = q / 64;
-        int64_t gi = r0 + rr;
-        Row[rr][c] = gi < n ? G[gi + (k0 + c) * ld] : (T)0;
+    __shared__ T L11[CNB][CNB + 1];
+    __shared__ T rinv[CNB];
+    for (int q = threadIdx.x; q < CNB * CNB; q += 32) {
+        int r = q & 63, c = q >> 6;
+        L11[r][c] = G[(k0 + r) + (k0 + c) * ld];
     }
     __syncthreads();
-    T* x = Row[tid];
-    for (int jj = 0; jj < nb; ++jj) {
-        T v = x[jj];
-        for (int kk = 0; kk < jj; ++kk) v = fma(-x[kk], L11[jj][kk], v);
-        x[jj] = v / L11[jj][jj];
-    }
+    for (int j = threadIdx.x; j < CNB; j += 32) rinv[j] = (T)1 / L11[j][j];
     __syncthreads();
-    for (int q = tid; q < 64 * nb; q += 64) {
-        int rr = q % 64, c = q / 64;
-        int64_t gi = r0 + rr;
-        if (gi < n) G[gi + (k0 + c) * ld] = Row[rr][c];
+    const int64_t i = k0 + CNB + (int64_t)blockIdx.x * 32 + threadIdx.x;
+    if (i >= n) return;
+    T x[CNB];
+#pragma unroll
+    for (int j = 0; j < CNB; ++j) x[j] = G[i + (k0 + j) * ld];
+#pragma unroll
+    for (int j = 0; j < CNB; ++j) {
+        x[j] = x[j] * rinv[j];
+#pragma unroll
+        for (int k = j + 1; k < CNB; ++k) x[k] = fma(-x[j], L11[k][j], x[k]);
     }
+#pragma unroll
+    for (int j = 0; j < CNB; ++j) G[i + (k0 + j) * ld] = x[j];
 }
 
 template <typename T>
@@ -193,21 +244,31 @@ __global__ void k_zero_upper(T* __restrict__ G, int64_t n, int64_t ld, const int
     }
 }
 
+size_t cholesky_ws_bytes(int64_t n) { return n > CNB ? ot_update_ws_bytes(n - CNB, n - CNB, CNB) : 256; }
+
 template <typename T>
-lsq_status launch_cholesky(T* G, int64_t n, int64_t ld, int32_t* info, cudaStream_t st) {
+lsq_status launch_cholesky(T* G, int64_t n, int64_t ld, int32_t* info, cudaStream_t st, void* ws, size_t ws_bytes) {
     for (int64_t k0 = 0; k0 < n; k0 += CNB) {
         int nb = (int)std::min<int64_t>(CNB, n - k0);
         k_potrf_diag<T><<<1, 256, 0, st>>>(G, ld, n, k0, info);
         LSQ_LAUNCH_CHECK();
         int64_t rest = n - k0 - nb;
         if (rest <= 0) break;
-        size_t psm = sizeof(T) * (size_t)(CNB + 64) * (CNB + 1);
-        LSQ_CUDA_TRY(cudaFuncSetAttribute(k_potrf_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
-        k_potrf_panel<T><<<(unsigned)ceil_div(rest, 64), 64, psm, st>>>(G, ld, n, k0, info);
+        k_potrf_panel<T><<<(unsigned)ceil_div(rest, 32), 32, 0, st>>>(G, ld, n, k0, info);
         LSQ_LAUNCH_CHECK();
         T* L21 = G + (k0 + nb) + k0 * ld;
-        lsq_status s = rank_update_ext<T>(G + (k0 + nb) + (k0 + nb) * ld, ld, L21, 1, ld, L21, 1, ld, rest, rest, nb,
-                                      true, info, st);
+        T* A22 = G + (k0 + nb) + (k0 + nb) * ld;
+        lsq_status s;
+        if constexpr (std::is_same<T, double>::value) {
+            // A22 -= L21 L21^T on the tensor cores (FP64 accuracy; the upper
+            // triangle of A22 is updated too and cleared at the end)
+            if (ws && ws_bytes >= ot_update_ws_bytes(rest, rest, nb) && ot_trsm_supported()) {
+                s = ot_gemm_update(L21, ld, L21, ld, 1, A22, ld, A22, ld, rest, rest, nb, ws, ws_bytes, nullptr, st);
+                if (s != LSQ_OK) return s;
+                continue;
+            }
+        }
+        s = rank_update_ext<T>(A22, ld, L21, 1, ld, L21, 1, ld, rest, rest, nb, true, info, st);
         if (s != LSQ_OK) return s;
     }
     k_zero_upper<T><<<(unsigned)std::min<int64_t>(ceil_div(n * n, 256), 4096), 256, 0, st>>>(G, n, ld, info);
@@ -215,8 +276,8 @@ lsq_status launch_cholesky(T* G, int64_t n, int64_t ld, int32_t* info, cudaStrea
     return LSQ_OK;
 }
 
-template lsq_status launch_cholesky<double>(double*, int64_t, int64_t, int32_t*, cudaStream_t);
-template lsq_status launch_cholesky<float>(float*, int64_t, int64_t, int32_t*, cudaStream_t);
+template lsq_status launch_cholesky<double>(double*, int64_t, int64_t, int32_t*, cudaStream_t, void*, size_t);
+template lsq_status launch_cholesky<float>(float*, int64_t, int64_t, int32_t*, cudaStream_t, void*, size_t);
 
 // ---------------------------------------------------------------------------
 // LU with partial pivoting
@@ -342,33 +403,132 @@ lsq_status launch_lu(double* H, int64_t n, int64_t ld, int32_t* piv, int32_t* in
 }
 
 // ---------------------------------------------------------------------------
-// Triangular solves on a vector, single block, y staged in shared memory.
-// Diagonal 32x32 blocks by one warp with shuffles, off-diagonal updates by
-// all threads.
+// Triangular solves on a vector, many CTAs in a wavefront.  CTA v takes its
+// row block from an atomic counter (v-th CTA to start), so every block it
+// waits for belongs to a CTA that has already started; it stages each
+// off-diagonal 32 x 32 block of the operator while the solution of that block
+// is still being computed, waits for the block's flag (bounded: 2 s of
+// %globaltimer, then an error is recorded and the failure passed on), applies
+// it, and finally solves its diagonal block with shuffles (multiplying by the
+// reciprocal of each diagonal entry) and publishes y_b with a release flag.
+// Partial sums are combined in a fixed order, so the result does not depend
+// on timing.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(512) k_trsv(int kind, const T* __restrict__ M, int64_t n, int64_t ld,
-                                              T* __restrict__ y, const int32_t* __restrict__ info) {
+__global__ void __launch_bounds__(128) k_trsv_wave(int kind, const T* __restrict__ M, int64_t n, int64_t ld, T* y,
+                                                   int32_t* sync, const int32_t* __restrict__ info,
+                                                   int32_t* __restrict__ err) {
     if (info && *info != 0) return;
-    extern __shared__ __align__(16) unsigned char trsv_raw[];
-    T* ys = reinterpret_cast<T*>(trsv_raw);
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) ys[i] = y[i];
-    block_trsv<T>(kind, M, n, ld, ys);
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) y[i] = ys[i];
+    __shared__ T blk[32][33];
+    __shared__ T part[4][32];
+    __shared__ T yk[32];
+    __shared__ int vb, failed;
+    const int tid = threadIdx.x, r = tid & 31, q = tid >> 5;
+    const int nblk = (int)((n + 31) / 32);
+    if (tid == 0) {
+        vb = atomicAdd(&sync[0], 1);
+        failed = 0;
+    }
+    __syncthreads();
+    const int v = vb;
+    const bool forward = (kind == TB_LOWER || kind == TB_UNIT_LOWER);
+    const bool trans = (kind == TB_LOWER_T);  // operator entry (i, j) = M[j + i ld]
+    const int b = forward ? v : nblk - 1 - v;
+    const int64_t b0 = (int64_t)b * 32;
+    const int bs = (int)min64(32, n - b0);
+    T acc = (T)0;
+    for (int st = 0; st < v; ++st) {
+        const int k = forward ? st : nblk - 1 - st;
+        const int64_t k0 = (int64_t)k * 32;
+        const int ks = (int)min64(32, n - k0);
+        for (int e = tid; e < 1024; e += 128) {
+            int rr, jj;
+            if (trans) { jj = e & 31; rr = e >> 5; } else { rr = e & 31; jj = e >> 5; }
+            T val = (T)0;
+            if (rr < bs && jj < ks) val = trans ? M[(k0 + jj) + (b0 + rr) * ld] : M[(b0 + rr) + (k0 + jj) * ld];
+            blk[rr][jj] = val;
+        }
+        if (tid == 0) {
+            const int32_t* f = sync + 1 + k;
+            int32_t fv = 0;
+            uint64_t t0 = 0;
+            for (uint32_t it = 0;; ++it) {
+                asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(fv) : "l"(f) : "memory");
+                if (fv != 0) break;
+                if ((it & 63u) == 0) {
+                    uint64_t t;
+                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                    if (it == 0) t0 = t;
+                    else if (t - t0 > 2000000000ull) break;
+                }
+            }
+            if (fv != 1) failed = 1;
+        }
+        __syncthreads();
+        if (failed) break;
+        if (tid < 32) yk[tid] = tid < ks ? __ldcg(y + k0 + tid) : (T)0;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc = fma(-blk[r][q * 8 + j], yk[q * 8 + j], acc);
+        __syncthreads();
+    }
+    part[q][r] = acc;
+    // diagonal block of the operator
+    for (int e = tid; e < 1024; e += 128) {
+        int rr, jj;
+        if (trans) { jj = e & 31; rr = e >> 5; } else { rr = e & 31; jj = e >> 5; }
+        T val = (T)0;
+        if (rr < bs && jj < bs) val = trans ? M[(b0 + jj) + (b0 + rr) * ld] : M[(b0 + rr) + (b0 + jj) * ld];
+        blk[rr][jj] = val;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        const bool ok = !failed;
+        const bool unit = (kind == TB_UNIT_LOWER);
+        T vv = r < bs ? y[b0 + r] : (T)0;
+        vv = vv + part[0][r] + part[1][r] + part[2][r] + part[3][r];
+        const T rinv = (r < bs && !unit) ? (T)1 / blk[r][r] : (T)1;
+        if (forward) {
+            for (int jj = 0; jj < bs; ++jj) {
+                if (r == jj) vv = vv * rinv;
+                T vj = __shfl_sync(0xffffffffu, vv, jj);
+                if (r > jj && r < bs) vv = fma(-blk[r][jj], vj, vv);
+            }
+        } else {
+            for (int jj = bs - 1; jj >= 0; --jj) {
+                if (r == jj) vv = vv * rinv;
+                T vj = __shfl_sync(0xffffffffu, vv, jj);
+                if (r < jj) vv = fma(-blk[r][jj], vj, vv);
+            }
+        }
+        if (ok && r < bs) y[b0 + r] = vv;
+        __threadfence();
+        __syncwarp();
+        if (r == 0) {
+            if (!ok) set_info_once(err, -2);
+            int32_t flag = ok ? 1 : 2;  // 2 passes the failure on to the blocks that wait
+            asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(sync + 1 + b), "r"(flag) : "memory");
+        }
+    }
 }
 
+size_t trsv_sync_ints(int64_t n) { return (size_t)ceil_div(n, 32) + 1; }
+
 template <typename T>
-lsq_status launch_trsv(int kind, const T* M, int64_t n, int64_t ld, T* y, const int32_t* info, cudaStream_t st) {
-    size_t smem = sizeof(T) * (size_t)n;
-    if (smem > 200 * 1024) return LSQ_ERR_ARG;
-    if (smem > 48 * 1024) LSQ_CUDA_TRY(cudaFuncSetAttribute(k_trsv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_trsv<T><<<1, 512, smem, st>>>(kind, M, n, ld, y, info);
+lsq_status launch_trsv(int kind, const T* M, int64_t n, int64_t ld, T* y, const int32_t* info, int32_t* sync,
+                       int32_t* err, cudaStream_t st) {
+    if (!sync || n <= 0 || n > (int64_t)1 << 30) return LSQ_ERR_ARG;
+    int64_t nblk = ceil_div(n, 32);
+    LSQ_CUDA_TRY(cudaMemsetAsync(sync, 0, sizeof(int32_t) * (size_t)(nblk + 1), st));
+    k_trsv_wave<T><<<(unsigned)nblk, 128, 0, st>>>(kind, M, n, ld, y, sync, info, err);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
 }
 
-template lsq_status launch_trsv<double>(int, const double*, int64_t, int64_t, double*, const int32_t*, cudaStream_t);
-template lsq_status launch_trsv<float>(int, const float*, int64_t, int64_t, float*, const int32_t*, cudaStream_t);
+template lsq_status launch_trsv<double>(int, const double*, int64_t, int64_t, double*, const int32_t*, int32_t*,
+                                        int32_t*, cudaStream_t);
+template lsq_status launch_trsv<float>(int, const float*, int64_t, int64_t, float*, const int32_t*, int32_t*, int32_t*,
+                                       cudaStream_t);
 
 __global__ void k_apply_piv(const int32_t* __restrict__ piv, int64_t n, double* __restrict__ y,
                             const int32_t* __restrict__ info) {

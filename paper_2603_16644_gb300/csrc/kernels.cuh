@@ -70,12 +70,19 @@ lsq_status launch_residual(const double* A, int64_t m, int64_t n, int64_t lda, c
 lsq_status launch_axpy1(double* x, const double* d, int64_t n, cudaStream_t st);
 
 // ---- factor.cu: n x n factorizations and triangular solves ------------------
+// FP64 with ws (>= cholesky_ws_bytes(n)): trailing updates on the tensor cores.
 template <typename T>
-lsq_status launch_cholesky(T* G, int64_t n, int64_t ld, int32_t* info, cudaStream_t st);
+lsq_status launch_cholesky(T* G, int64_t n, int64_t ld, int32_t* info, cudaStream_t st, void* ws = nullptr,
+                           size_t ws_bytes = 0);
+size_t cholesky_ws_bytes(int64_t n);
 lsq_status launch_lu(double* H, int64_t n, int64_t ld, int32_t* piv, int32_t* info, cudaStream_t st);
 enum TrsvKind { TRSV_LOWER = 0, TRSV_LOWER_T = 1, TRSV_UPPER = 2, TRSV_UNIT_LOWER = 3 };
+// sync: trsv_sync_ints(n) int32 of scratch (cleared by the launch); err: the
+// device status word that a timed-out wait sets to -2 (may be NULL).
+size_t trsv_sync_ints(int64_t n);
 template <typename T>
-lsq_status launch_trsv(int kind, const T* M, int64_t n, int64_t ld, T* y, const int32_t* info, cudaStream_t st);
+lsq_status launch_trsv(int kind, const T* M, int64_t n, int64_t ld, T* y, const int32_t* info, int32_t* sync,
+                       int32_t* err, cudaStream_t st);
 lsq_status launch_apply_piv(const int32_t* piv, int64_t n, double* y, const int32_t* info, cudaStream_t st);
 
 template <typename T>
@@ -93,6 +100,18 @@ lsq_status launch_sketch_tc(const void* Om, int64_t ldo, const void* Ahat, int64
 size_t oz_gram_ws_bytes(int64_t m, int64_t n);
 lsq_status oz_gram(const double* X, int64_t m, int64_t n, int64_t ld, double* G, int64_t ldg, void* ws,
                    size_t ws_bytes, int32_t* err, cudaStream_t st);
+
+// ---- oz_trsm.cu: FP64 Ap = A R^{-1} with tensor-core updates -------------
+bool ot_trsm_supported();
+size_t ot_trsm_ws_bytes(int64_t m, int64_t n);
+lsq_status ot_trsm(const double* A, int64_t m, int64_t n, int64_t lda, const double* R, int64_t ldr, double* Ap,
+                   int64_t ldap, void* ws, size_t ws_bytes, int32_t* err, cudaStream_t st);
+// C_out = C_in - X Y with FP64 accuracy on the tensor cores (X: M x K
+// column-major, ld ldx; Y entry (k, j) at Y[k sk + j sj]; K <= 512).
+size_t ot_update_ws_bytes(int64_t M, int64_t N, int64_t K);
+lsq_status ot_gemm_update(const double* X, int64_t ldx, const double* Y, int64_t sk, int64_t sj, const double* Cin,
+                          int64_t ldi, double* Cout, int64_t ldo, int64_t M, int64_t N, int64_t K, void* ws,
+                          size_t ws_bytes, int32_t* err, cudaStream_t st);
 
 // ---- qr.cu -------------------------------------------------------------------
 size_t qr_ws_bytes(int64_t s, int64_t n, int prec);

@@ -1,0 +1,564 @@
+// FP64 right triangular solve A_p = A R^{-1} (Alg. 1, "A_p = A R_s^{-1}" by
+// substitution) with the off-diagonal work on the 5th-generation tensor cores.
+//
+// The columns are split recursively, [c0, c1) -> [c0, mid) + [mid, c1):
+//   A_p[:, c0:mid]  = solve of the left part,
+//   A_p[:, mid:c1]  = A[:, mid:c1] - A_p[:, c0:mid] R[c0:mid, mid:c1],
+//   then the right part is solved in place.
+// Diagonal blocks of at most OT_NB columns are solved by FP64 substitution
+// (one thread per row).  The updates are FP64-accurate products built from
+// BF16 digit slices:
+//
+//   x = 2^(E - 55) sum_{t=0}^{7} d_t 128^(7 - t) + r,  d_t in [-64, 64],
+//   0 <= |r| < 2^(E - 55),
+//
+// with 2^E bounding the row of X (resp. the column of Y) that x belongs to.
+// Every digit-pair product d_t d_u is an integer of magnitude <= 2^12, so the
+// (d + 1) <= 8 pairs with t + u = d summed over K <= 512 stay <= 2^24 and are
+// exact in the FP32 accumulators of tcgen05.mma (kind::f16, BF16 operands).
+// Pairs with t + u <= 7 are kept (36 of 64); each group d has its own TMEM
+// accumulator.  The epilogue turns the 8 group sums into two exact 64-bit
+// fixed-point integers and rounds once to FP64:
+//
+//   sum_k X[i,k] Y[k,j] ~= 2^(Ex_i + Ey_j - 61) (hi 2^28 + lo),
+//   hi = sum_{d<4} S_d 128^(3-d),  lo = sum_{d>=4} S_d 128^(7-d).
+//
+// Per product the dropped pairs and the truncations r contribute below
+// 2^-52.6 * 2^(Ex_i + Ey_j), the order of FP64 rounding.
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tcgen05.cuh"
+
+#include <algorithm>
+
+namespace lsq {
+
+constexpr int OT_DIG = 8;                   // digits per value
+constexpr int OT_BM = 128, OT_BN = 64;      // output tile (rows x columns)
+constexpr int OT_BK = 64;                   // K per stage: 64 BF16 = 128 bytes
+constexpr int OT_XST = 6;                   // stages of X digit tiles
+constexpr int OT_KMAX = 512;                // exact FP32 group sums up to this K
+constexpr int OT_NB = 32;                   // diagonal block solved by substitution
+constexpr int OT_THREADS = 320;             // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int OT_XTILE = OT_BM * 128;       // bytes of one X digit tile
+constexpr int OT_YTILE = OT_BN * 128;       // bytes of one Y digit tile
+constexpr int32_t OT_NONFINITE = 0x7fffffff;
+
+// ---------------------------------------------------------------------------
+// Digit slicing (integer operations on the FP64 bit pattern)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int32_t ot_exp_of_max(unsigned long long mx) {
+    int Eb = (int)(mx >> 52);
+    if (Eb == 0x7ff) return OT_NONFINITE;
+    if (mx == 0) return 0;
+    return (Eb > 1 ? Eb : 1) - 1022;  // every |x| < 2^E
+}
+
+// Balanced base-128 digits of x with |x| < 2^E (see the file comment).
+__device__ __forceinline__ void ot_digits(double x, int32_t E, int (&d)[OT_DIG]) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const bool neg = (b >> 63) != 0;
+    const int Eb = (int)((b >> 52) & 0x7ff);
+    unsigned long long sig = b & 0x000fffffffffffffull;
+    if (Eb != 0) sig |= 0x0010000000000000ull;
+    const int sh = (Eb != 0 ? Eb : 1) - (E + 1022) + 2;  // <= 2, so V < 2^55
+    unsigned long long V = 0;
+    if (E != OT_NONFINITE && Eb != 0x7ff) V = sh >= 0 ? (sig << sh) : (sh > -64 ? (sig >> (-sh)) : 0ull);
+    // adding 64 to every lower digit field turns the base-128 digits into
+    // balanced ones: field - 64 in [-64, 63], the carry lands in the top digit
+    constexpr unsigned long long BIAS = 64ull * ((1ull << 42) + (1ull << 35) + (1ull << 28) + (1ull << 21) +
+                                                 (1ull << 14) + (1ull << 7) + 1ull);
+    const unsigned long long W = V + BIAS;
+    d[0] = (int)(W >> 49);  // in [0, 64]
+#pragma unroll
+    for (int t = 1; t < OT_DIG; ++t) d[t] = (int)((W >> (7 * (OT_DIG - 1 - t))) & 127ull) - 64;
+    if (neg) {
+#pragma unroll
+        for (int t = 0; t < OT_DIG; ++t) d[t] = -d[t];
+    }
+}
+
+__device__ __forceinline__ uint32_t bf16_bits_of_int(int v) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)v));  // exact for |v| <= 256
+}
+
+// Rows of X (m x K, column-major): Ex[i] and digit planes Z[(t mp + i) Kp + k]
+// (K-contiguous; zero for rows m <= i < mp and for K <= k < Kp, so that every
+// TMA box lies inside the planes).  One thread per row.
+__global__ void __launch_bounds__(128) k_ot_rowslice(const double* __restrict__ X, int64_t m, int64_t mp, int64_t K,
+                                                     int64_t ld, int64_t Kp, int32_t* __restrict__ Ex,
+                                                     uint16_t* __restrict__ Z) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= mp) return;
+    const double* row = X + i;
+    const int64_t Kr = i < m ? K : 0;
+    unsigned long long mx = 0;
+    int64_t k = 0;
+    for (; k + 8 <= Kr; k += 8) {  // 8 loads in flight per thread
+        unsigned long long v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = (unsigned long long)__double_as_longlong(row[(k + q) * ld]);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            unsigned long long a = v[q] & 0x7fffffffffffffffull;
+            mx = a > mx ? a : mx;
+        }
+    }
+    for (; k < Kr; ++k) {
+        unsigned long long v = (unsigned long long)__double_as_longlong(row[k * ld]) & 0x7fffffffffffffffull;
+        mx = v > mx ? v : mx;
+    }
+    const int32_t E = ot_exp_of_max(mx);
+    Ex[i] = E;
+    for (int64_t k0 = 0; k0 < Kp; k0 += 16) {
+        uint32_t pk[OT_DIG][8];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            int64_t k = k0 + q;
+            double x = k < Kr ? row[k * ld] : 0.0;
+            int d[OT_DIG];
+            ot_digits(x, E, d);
+#pragma unroll
+            for (int t = 0; t < OT_DIG; ++t) {
+                uint32_t h = bf16_bits_of_int(d[t]);
+                if (q & 1) pk[t][q >> 1] |= h << 16;
+                else pk[t][q >> 1] = h;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < OT_DIG; ++t) {
+            uint4* dst = (uint4*)(Z + ((int64_t)t * mp + i) * Kp + k0);
+            dst[0] = make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
+            dst[1] = make_uint4(pk[t][4], pk[t][5], pk[t][6], pk[t][7]);
+        }
+    }
+}
+
+// Columns of Y (K x N, entry (k, j) at Y[k sk + j sj]): Ey[j] and digit
+// planes Z[(u Np + j) Kp + k] (zero for columns N <= j < Np and for
+// K <= k < Kp).  One CTA per column.
+__global__ void __launch_bounds__(128) k_ot_colslice(const double* __restrict__ Y, int64_t K, int64_t N, int64_t Np,
+                                                     int64_t sk, int64_t sj, int64_t Kp, int32_t* __restrict__ Ey,
+                                                     uint16_t* __restrict__ Z) {
+    const int64_t j = blockIdx.x;
+    const double* col = Y + j * sj;
+    const int64_t Kr = j < N ? K : 0;
+    unsigned long long mx = 0;
+    for (int64_t k = threadIdx.x; k < Kr; k += blockDim.x) {
+        unsigned long long v = (unsigned long long)__double_as_longlong(col[k * sk]) & 0x7fffffffffffffffull;
+        mx = v > mx ? v : mx;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
+        mx = o > mx ? o : mx;
+    }
+    __shared__ unsigned long long w[4];
+    __shared__ int32_t Es;
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int q = 0; q < 4; ++q) t = w[q] > t ? w[q] : t;
+        Es = ot_exp_of_max(t);
+        Ey[j] = Es;
+    }
+    __syncthreads();
+    const int32_t E = Es;
+    for (int64_t k = threadIdx.x; k < Kp; k += blockDim.x) {
+        int d[OT_DIG];
+        ot_digits(k < Kr ? col[k * sk] : 0.0, E, d);
+#pragma unroll
+        for (int u = 0; u < OT_DIG; ++u) Z[((int64_t)u * Np + j) * Kp + k] = (uint16_t)bf16_bits_of_int(d[u]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Update C_out = C_in - X Y for one 128 x 64 tile (C_in may equal C_out).
+// ---------------------------------------------------------------------------
+// 2^s (hi 2^28 + lo) for |hi|, |lo| < 2^47, rounded once to nearest-even:
+// the exact 128-bit integer is normalised with integer operations and the
+// scale goes into the exponent field (no FP64 instruction); results outside
+// the normal range take the (rare) FP64 path.
+__device__ __forceinline__ double ot_fixed_to_double(long long hi, long long lo, int s) {
+    unsigned long long L = (unsigned long long)hi << 28;
+    long long H = hi >> 36;
+    const unsigned long long L2 = L + (unsigned long long)lo;
+    H += (lo >> 63) + (L2 < L ? 1 : 0);
+    L = L2;
+    const bool neg = H < 0;
+    if (neg) {
+        L = ~L + 1ull;
+        H = ~H + (L == 0 ? 1 : 0);
+    }
+    const unsigned long long uH = (unsigned long long)H;
+    if (uH == 0 && L == 0) return 0.0;
+    int p = uH ? 127 - __clzll((long long)uH) : 63 - __clzll((long long)L);
+    unsigned long long mant;
+    if (p <= 52) {
+        mant = L << (52 - p);
+    } else {
+        const int sh = p - 52;  // 1 .. 22
+        mant = (L >> sh) | (uH << (64 - sh));
+        const unsigned long long rb = (L >> (sh - 1)) & 1ull;
+        const bool sticky = (L & ((1ull << (sh - 1)) - 1ull)) != 0;
+        if (rb && (sticky || (mant & 1ull))) {
+            ++mant;
+            if (mant == (1ull << 53)) {
+                mant >>= 1;
+                ++p;
+            }
+        }
+    }
+    const int E = p + s + 1023;
+    if (E <= 0 || E >= 2047) return ldexp(fma((double)hi, 268435456.0, (double)lo), s);
+    return __longlong_as_double((long long)((neg ? 0x8000000000000000ull : 0ull) | ((unsigned long long)E << 52) |
+                                            (mant & 0x000fffffffffffffull)));
+}
+
+__global__ void __launch_bounds__(OT_THREADS, 1)
+    k_ot_update(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int64_t m,
+                int64_t N, int64_t K, const int32_t* __restrict__ Ex, const int32_t* __restrict__ Ey,
+                const double* Cin, int64_t ldi, double* Cout, int64_t ldo, int32_t* __restrict__ err) {
+    extern __shared__ unsigned char ot_raw[];
+    uint8_t* base = (uint8_t*)(((uintptr_t)ot_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sY = base;                                // 2 stages x 8 digit tiles
+    uint8_t* sX = sY + 2 * OT_DIG * OT_YTILE;          // OT_XST stages x 1 tile
+    uint64_t* yfull = (uint64_t*)(sX + OT_XST * OT_XTILE);
+    uint64_t* yempty = yfull + 2;
+    uint64_t* xfull = yempty + 2;
+    uint64_t* xempty = xfull + OT_XST;
+    uint64_t* accb = xempty + OT_XST;
+    uint32_t* tslot = (uint32_t*)(accb + 1);
+    volatile int* bad = (volatile int*)(tslot + 1);
+    int* cnt = (int*)(tslot + 2);  // issued / consumed: x, x, y, y
+    int32_t* eys = (int32_t*)(tslot + 8);  // column exponents of the tile
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // column tiles fastest: the CTAs that share a row block of X digits run
+    // together and read them from L2
+    const int64_t i0 = (int64_t)blockIdx.y * OT_BM;
+    const int64_t j0 = (int64_t)blockIdx.x * OT_BN;
+    const int nslab = (int)((K + OT_BK - 1) / OT_BK);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&yfull[s], 1);
+            mbar_init(&yempty[s], 1);
+        }
+        for (int s = 0; s < OT_XST; ++s) {
+            mbar_init(&xfull[s], 1);
+            mbar_init(&xempty[s], 1);
+        }
+        mbar_init(accb, 1);
+        *bad = 0;
+        cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tslot, 512);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0 && lane == 0) {
+        // producer: the 8 Y digit tiles of slab s + 1 go out after X tile 3
+        // of slab s (the MMAs on the rest of slab s cover their latency)
+        auto load_y = [&](int s) -> bool {
+            const int ys = s & 1;
+            if (s >= 2 && !mbar_wait(&yempty[ys], (uint32_t)(((s >> 1) - 1) & 1))) return false;
+            mbar_expect_tx(&yfull[ys], OT_DIG * OT_YTILE);
+            for (int u = 0; u < OT_DIG; ++u)
+                tma_load_3d(sY + (ys * OT_DIG + u) * OT_YTILE, &tmY, &yfull[ys], s * OT_BK, (int)j0, u);
+            cnt[2] = s + 1;
+            return true;
+        };
+        int xq = 0;
+        if (nslab > 0 && !load_y(0)) *bad = 1;
+        for (int s = 0; s < nslab && !*bad; ++s) {
+            for (int t = 0; t < OT_DIG; ++t, ++xq) {
+                if (t == 4 && s + 1 < nslab && !load_y(s + 1)) {
+                    *bad = 1;
+                    break;
+                }
+                const int xs = xq % OT_XST;
+                if (xq >= OT_XST && !mbar_wait(&xempty[xs], (uint32_t)(((xq / OT_XST) - 1) & 1))) {
+                    *bad = 1;
+                    break;
+                }
+                mbar_expect_tx(&xfull[xs], OT_XTILE);
+                tma_load_3d(sX + xs * OT_XTILE, &tmX, &xfull[xs], s * OT_BK, (int)i0, t);
+                cnt[0] = xq + 1;
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: pair (t, u) with t + u <= 7 into accumulator t + u
+        const uint32_t idesc = umma_idesc(1u, OT_BM, OT_BN);
+        int xq = 0;
+        for (int s = 0; s < nslab && !*bad; ++s) {
+            const int ys = s & 1;
+            if (!mbar_wait(&yfull[ys], (uint32_t)((s >> 1) & 1))) {
+                *bad = 1;
+                break;
+            }
+            cnt[3] = s + 1;
+            for (int t = 0; t < OT_DIG; ++t, ++xq) {
+                const int xs = xq % OT_XST;
+                if (!mbar_wait(&xfull[xs], (uint32_t)((xq / OT_XST) & 1))) {
+                    *bad = 1;
+                    break;
+                }
+                cnt[1] = xq + 1;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t ad = umma_desc(smem_u32(sX + xs * OT_XTILE));
+                for (int u = 0; u + t < OT_DIG; ++u) {
+                    const uint64_t bd = umma_desc(smem_u32(sY + (ys * OT_DIG + u) * OT_YTILE));
+                    const uint32_t acc = tmem + (uint32_t)((t + u) * OT_BN);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)  // 4 x 16 BF16 of K per stage
+                        umma_f16(acc, ad + 2 * kk, bd + 2 * kk, idesc, (s | t | kk) != 0 ? 1u : 0u);
+                }
+                umma_commit(&xempty[xs]);
+            }
+            umma_commit(&yempty[ys]);
+        }
+        umma_commit(accb);  // fires when every MMA issued above has completed
+    } else if (warp >= 2) {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and
+        // one half of the 64 columns.  While the MMAs run it prefetches its
+        // C_in entries into registers and the column exponents into shared
+        // memory, so that no load latency is left for after the MMAs.
+        const int quad = warp & 3, half = (warp - 2) >> 2;
+        const int64_t row = i0 + quad * 32 + lane;
+        const int32_t ex = row < m ? Ex[row] : 0;
+        double cin[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int64_t col = j0 + half * 32 + j;
+            cin[j] = (row < m && col < N) ? Cin[row + col * ldi] : 0.0;
+        }
+        if (threadIdx.x - 64 < OT_BN) {
+            const int64_t col = j0 + (threadIdx.x - 64);
+            eys[threadIdx.x - 64] = col < N ? Ey[col] : 0;
+        }
+        asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 epilogue warps
+        bool ok = mbar_wait(accb, 0);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok) *bad = 1;
+        const bool go = __all_sync(0xffffffffu, ok && !*bad && nslab > 0);
+        if (go) {
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                const int c = half * 32 + cc * 16;
+                long long hi[16], lo[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
+#pragma unroll
+                for (int d = 0; d < OT_DIG; ++d) {
+                    uint32_t v[16];
+                    tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(d * OT_BN + c), v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const long long S = (long long)__float2int_rn(__uint_as_float(v[j]));
+                        if (d < 4) hi[j] = hi[j] * 128 + S;
+                        else lo[j] = lo[j] * 128 + S;
+                    }
+                }
+                if (row < m) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int64_t col = j0 + c + j;
+                        if (col < N) {
+                            const int32_t ey = eys[c + j];
+                            double val;
+                            if (ex == OT_NONFINITE || ey == OT_NONFINITE) {
+                                val = __longlong_as_double(0x7ff8000000000000ll);
+                            } else {
+                                val = ot_fixed_to_double(hi[j], lo[j], ex + ey - 61);
+                            }
+                            Cout[row + col * ldo] = cin[cc * 16 + j] - val;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (*bad) {
+        if (threadIdx.x == 0) {
+            set_info_once(err, -2);
+            // wait (bounded) for copies issued but never consumed, then the MMAs
+            for (int q = cnt[1]; q < cnt[0]; ++q) mbar_wait(&xfull[q % OT_XST], (uint32_t)((q / OT_XST) & 1));
+            for (int s = cnt[3]; s < cnt[2]; ++s) mbar_wait(&yfull[s & 1], (uint32_t)((s >> 1) & 1));
+            mbar_wait(accb, 0);
+        }
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal block: Ap[i, 0:nc] = src[i, 0:nc] R_jj^{-1} (R_jj upper, nc <= NB)
+// by substitution, one thread per row.  Each x_j is scaled by the reciprocal
+// of R[j, j] (one rounding more than a division).
+// ---------------------------------------------------------------------------
+template <int NB>
+__global__ void __launch_bounds__(128) k_ot_diag(const double* src, int64_t lds, const double* __restrict__ R,
+                                                 int64_t ldr, int nc, int64_t m, double* Ap, int64_t ldap) {
+    __shared__ double Rb[NB][NB];
+    __shared__ double rinv[NB];
+    for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) {
+        int k = q % NB, j = q / NB;
+        Rb[k][j] = (k < nc && j < nc) ? R[k + (int64_t)j * ldr] : (k == j ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    if (threadIdx.x < NB) rinv[threadIdx.x] = 1.0 / Rb[threadIdx.x][threadIdx.x];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double x[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) x[j] = j < nc ? src[i + (int64_t)j * lds] : 0.0;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        double v = x[j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) v = fma(-x[k], Rb[k][j], v);
+        x[j] = v * rinv[j];
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if (j < nc) Ap[i + (int64_t)j * ldap] = x[j];
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static int64_t ot_kp(int64_t K) { return ceil_div(K, OT_BK) * OT_BK; }
+static int64_t ot_pad(int64_t v, int64_t b) { return ceil_div(v, b) * b; }
+
+// Split point of [c0, c1): the left part is a multiple of OT_NB columns and
+// at most OT_KMAX (the K of the update that follows).
+static int64_t ot_mid(int64_t c0, int64_t c1) {
+    int64_t w = c1 - c0;
+    int64_t left = ceil_div(ceil_div(w, 2), OT_NB) * OT_NB;
+    return c0 + std::min<int64_t>(left, OT_KMAX);
+}
+
+static bool ot_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t rows, int box_rows);
+static size_t ot_update_smem() { return 1024 + 2 * OT_DIG * OT_YTILE + OT_XST * OT_XTILE + 512; }
+
+// Scratch of one update with M rows, N columns and inner dimension K.
+size_t ot_update_ws_bytes(int64_t M, int64_t N, int64_t K) {
+    const int64_t mp = ot_pad(M, OT_BM), Np = ot_pad(N, OT_BN), Kp = ot_kp(K);
+    return align_up(sizeof(uint16_t) * OT_DIG * (size_t)mp * Kp, 256) + align_up(sizeof(int32_t) * mp, 256) +
+           align_up(sizeof(uint16_t) * OT_DIG * (size_t)Np * Kp, 256) + align_up(sizeof(int32_t) * Np, 256) + 256;
+}
+
+// C_out = C_in - X Y (M x N; X: M x K column-major, ld ldx; Y: entry (k, j)
+// at Y[k sk + j sj]) with FP64 accuracy on the tensor cores; K <= 512.
+// C_in may equal C_out (same ld).
+lsq_status ot_gemm_update(const double* X, int64_t ldx, const double* Y, int64_t sk, int64_t sj, const double* Cin,
+                          int64_t ldi, double* Cout, int64_t ldo, int64_t M, int64_t N, int64_t K, void* ws,
+                          size_t ws_bytes, int32_t* err, cudaStream_t st) {
+    if (M <= 0 || N <= 0 || K <= 0) return LSQ_OK;
+    if (K > OT_KMAX || !ws || ws_bytes < ot_update_ws_bytes(M, N, K)) return LSQ_ERR_ARG;
+    const int64_t mp = ot_pad(M, OT_BM), Np = ot_pad(N, OT_BN), Kp = ot_kp(K);
+    char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    uint16_t* Zx = (uint16_t*)base;
+    base += align_up(sizeof(uint16_t) * OT_DIG * (size_t)mp * Kp, 256);
+    int32_t* Ex = (int32_t*)base;
+    base += align_up(sizeof(int32_t) * mp, 256);
+    uint16_t* Zy = (uint16_t*)base;
+    base += align_up(sizeof(uint16_t) * OT_DIG * (size_t)Np * Kp, 256);
+    int32_t* Ey = (int32_t*)base;
+    k_ot_rowslice<<<(unsigned)(mp / 128), 128, 0, st>>>(X, M, mp, K, ldx, Kp, Ex, Zx);
+    LSQ_LAUNCH_CHECK();
+    k_ot_colslice<<<(unsigned)Np, 128, 0, st>>>(Y, K, N, Np, sk, sj, Kp, Ey, Zy);
+    LSQ_LAUNCH_CHECK();
+    CUtensorMap tx, ty;
+    if (!ot_map(&tx, Zx, Kp, mp, OT_BM) || !ot_map(&ty, Zy, Kp, Np, OT_BN)) return LSQ_ERR_CUDA;
+    const size_t smem = ot_update_smem();
+    LSQ_CUDA_TRY(cudaFuncSetAttribute(k_ot_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)(Np / OT_BN), (unsigned)(mp / OT_BM));
+    stage_mark(ST_K_UPDATE, true, st);
+    k_ot_update<<<grid, OT_THREADS, smem, st>>>(tx, ty, M, N, Kp, Ex, Ey, Cin, ldi, Cout, ldo, err);
+    LSQ_LAUNCH_CHECK();
+    stage_mark(ST_K_UPDATE, false, st, 36.0 * 2.0 * (double)M * (double)N * (double)K);
+    return LSQ_OK;
+}
+
+static void ot_max_update(int64_t m, int64_t c0, int64_t c1, size_t& need) {
+    if (c1 - c0 <= OT_NB) return;
+    int64_t mid = ot_mid(c0, c1);
+    need = std::max(need, ot_update_ws_bytes(m, c1 - mid, mid - c0));
+    ot_max_update(m, c0, mid, need);
+    ot_max_update(m, mid, c1, need);
+}
+
+size_t ot_trsm_ws_bytes(int64_t m, int64_t n) {
+    size_t need = 256;
+    ot_max_update(m, 0, n, need);
+    return need + 256;
+}
+
+// Digit planes as a 3-D tensor (k, row, digit); Kp and rows are multiples of
+// the box, so no box reaches outside.
+static bool ot_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t rows, int box_rows) {
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)OT_DIG};
+    cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2)};
+    cuuint32_t box[3] = {(cuuint32_t)OT_BK, (cuuint32_t)box_rows, 1u};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct OtCtx {
+    int64_t m;
+    const double* R;
+    int64_t ldr;
+    double* Ap;
+    int64_t ldap;
+    void* ws;
+    size_t ws_bytes;
+    int32_t* err;
+    cudaStream_t st;
+};
+
+// Columns [c0, c1) of the right-hand side are in src (ld lds); results in Ap.
+static lsq_status ot_solve(const OtCtx& C, int64_t c0, int64_t c1, const double* src, int64_t lds) {
+    if (c1 - c0 <= OT_NB) {
+        k_ot_diag<OT_NB><<<(unsigned)ceil_div(C.m, 128), 128, 0, C.st>>>(src + c0 * lds, lds, C.R + c0 + c0 * C.ldr,
+                                                                         C.ldr, (int)(c1 - c0), C.m,
+                                                                         C.Ap + c0 * C.ldap, C.ldap);
+        LSQ_LAUNCH_CHECK();
+        return LSQ_OK;
+    }
+    const int64_t mid = ot_mid(c0, c1);
+    lsq_status r = ot_solve(C, c0, mid, src, lds);
+    if (r != LSQ_OK) return r;
+    r = ot_gemm_update(C.Ap + c0 * C.ldap, C.ldap, C.R + c0 + mid * C.ldr, 1, C.ldr, src + mid * lds, lds,
+                       C.Ap + mid * C.ldap, C.ldap, C.m, c1 - mid, mid - c0, C.ws, C.ws_bytes, C.err, C.st);
+    if (r != LSQ_OK) return r;
+    return ot_solve(C, mid, c1, C.Ap, C.ldap);
+}
+
+bool ot_trsm_supported() { return tensor_map_encoder() != nullptr; }
+
+lsq_status ot_trsm(const double* A, int64_t m, int64_t n, int64_t lda, const double* R, int64_t ldr, double* Ap,
+                   int64_t ldap, void* ws, size_t ws_bytes, int32_t* err, cudaStream_t st) {
+    if (!A || !R || !Ap || m <= 0 || n <= 0 || lda < m || ldap < m || ldr < n) return LSQ_ERR_ARG;
+    if (!ot_trsm_supported()) return LSQ_ERR_ARG;
+    if (!ws || ws_bytes < ot_trsm_ws_bytes(m, n)) return LSQ_ERR_NOMEM;
+    OtCtx C{m, R, ldr, Ap, ldap, ws, ws_bytes, err, st};
+    return ot_solve(C, 0, n, A, lda);
+}
+
+}  // namespace lsq

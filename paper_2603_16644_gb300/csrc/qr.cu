@@ -161,12 +161,18 @@ __global__ void __launch_bounds__(QPT) k_qr_panel(T* __restrict__ W, int64_t ld,
 }
 
 // Same panel factorization by a cluster of QCL CTAs that keep the panel in
-// shared memory: CTA r owns rows [r R, (r+1) R) of the panel.  Per column,
-// the partial sums of sigma and of w = v^T W are published in each CTA's
-// shared memory and read back through distributed shared memory in rank
-// order, so every CTA computes identical Householder scalars.  Partial-sum
-// slots alternate between two buffers by column parity, which makes two
-// cluster barriers per column sufficient.
+// shared memory: CTA r owns rows [r R, (r+1) R) of the panel (local leading
+// dimension Rp = R | 1, odd, so that lanes reading different columns of one
+// row hit different banks).  Per column j each CTA computes, in one pass over
+// its rows below the diagonal, sigma = sum x_i^2 and d_c = sum x_i a_c[i] for
+// every later column c (warp = row group, lane = column); the partials and
+// the diagonal row (x1, a_c[j], from its owner) are pushed into every CTA's
+// shared memory, and after ONE cluster barrier every CTA sums them in rank
+// order and gets identical Householder scalars and
+//   v^T a_c = a_c[j] + d_c / v1,   w_c = beta v^T a_c
+// (v = [1; x(2:)/v1]).  Slots alternate between two buffers by column parity:
+// a CTA can only write a buffer again after the next barrier, which every CTA
+// reaches after reading it.
 constexpr int QCL = 8;
 constexpr int QCT = 256;
 
@@ -177,51 +183,52 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(QCT)
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char cl_raw[];
-    T* P = reinterpret_cast<T*>(cl_raw);  // local panel, column-major, ld R
-    __shared__ T sig_all[2][QCL];      // sigma partials of every rank, per column parity
-    __shared__ T x1_all[2];            // x1 published by the owner of the diagonal row
-    __shared__ T w_all[2][QCL][QNB];   // w partials of every rank
-    __shared__ T wred[QCT / 32][QNB];
-    __shared__ T wcol[QNB];
+    T* P = reinterpret_cast<T*>(cl_raw);  // local panel, column-major, ld Rp
+    __shared__ T all_part[2][QCL][QNB];  // per rank: d_c (sigma at c = j)
+    __shared__ T all_row[2][QNB];        // the diagonal row: x1 at j, a_c[j] at c > j
+    __shared__ T part[QCT / 32][QNB];
+    __shared__ T wsh[QNB];
     __shared__ T Ypart[QNB][QNB + 1];
     __shared__ T Ts[QNB][QNB + 1];
-    __shared__ T red[32];
     __shared__ T bsh[QNB];
     const int rank = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t rows = s - k0;
     const int64_t R = (rows + QCL - 1) / QCL;
+    const int64_t Rp = R | 1;
     const int64_t r0 = rank * R;
     const int64_t nloc = r0 < rows ? min64(R, rows - r0) : 0;
+    const int64_t chunk = (R + (QCT / 32) - 1) / (QCT / 32);
+    const int64_t g0 = warp * chunk, g1 = min64(nloc, g0 + chunk);  // this warp's rows
     for (int64_t q = tid; q < R * QNB; q += QCT) {
         int64_t i = q % R, c = q / R;
-        P[q] = (i < nloc && c < nb) ? W[(k0 + r0 + i) + (k0 + c) * ld] : (T)0;
+        P[c * Rp + i] = (i < nloc && c < nb) ? W[(k0 + r0 + i) + (k0 + c) * ld] : (T)0;
     }
     __syncthreads();
     for (int jj = 0; jj < nb; ++jj) {
         const int buf = jj & 1;
         const int owner = (int)(jj / R);
-        T* colj = P + (int64_t)jj * R;
-        // rows strictly below the diagonal that this CTA owns
-        int64_t ib = max64((int64_t)jj + 1 - r0, 0);
-        T sp = (T)0;
-        for (int64_t i = ib + tid; i < nloc; i += QCT) sp = fma(colj[i], colj[i], sp);
-        for (int off = 16; off > 0; off >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, off);
-        if (lane == 0) red[warp] = sp;
+        T* xj = P + (int64_t)jj * Rp;
+        T* ac = P + (int64_t)lane * Rp;
+        const int64_t ib = max64((int64_t)jj + 1 - r0, 0);  // first owned row strictly below the diagonal
+        T acc = (T)0;
+        if (lane >= jj && lane < nb)
+            for (int64_t i = max64(ib, g0); i < g1; ++i) acc = fma(xj[i], ac[i], acc);
+        part[warp][lane] = acc;
         __syncthreads();
         if (warp == 0) {
             T t = (T)0;
-            for (int w = 0; w < QCT / 32; ++w) t += red[w];
-            // push this rank's partial (and x1 from the owner) into every CTA
-            if (lane < QCL) {
-                *cluster.map_shared_rank(&sig_all[buf][rank], lane) = t;
-                if (rank == owner) *cluster.map_shared_rank(&x1_all[buf], lane) = colj[jj - r0];
+            for (int g = 0; g < QCT / 32; ++g) t += part[g][lane];
+            for (int q = 0; q < QCL; ++q) *cluster.map_shared_rank(&all_part[buf][rank][lane], q) = t;
+            if (rank == owner) {
+                const T rv = P[(int64_t)lane * Rp + (jj - r0)];
+                for (int q = 0; q < QCL; ++q) *cluster.map_shared_rank(&all_row[buf][lane], q) = rv;
             }
         }
         cluster.sync();
         T sigma = (T)0;
-        for (int q = 0; q < QCL; ++q) sigma += sig_all[buf][q];
-        const T x1 = x1_all[buf];
+        for (int q = 0; q < QCL; ++q) sigma += all_part[buf][q][jj];
+        const T x1 = all_row[buf][jj];
         T mu, b, v1 = (T)1;
         bool scale = false;
         if (sigma == (T)0) {
@@ -233,53 +240,28 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(QCT)
             b = (T)2 * v1 * v1 / (sigma + v1 * v1);
             scale = true;
         }
-        if (scale)
-            for (int64_t i = ib + tid; i < nloc; i += QCT) colj[i] = colj[i] / v1;
-        __syncthreads();
-        if (tid == 0) bsh[jj] = b;  // identical in every CTA of the cluster
-        if (rank == owner && tid == 0) {
-            colj[jj - r0] = mu;
-            beta_out[k0 + jj] = b;
+        if (warp == 0 && lane > jj && lane < nb) {
+            T d = (T)0;
+            for (int q = 0; q < QCL; ++q) d += all_part[buf][q][lane];
+            wsh[lane] = b * (all_row[buf][lane] + (scale ? d / v1 : (T)0));
         }
-        const int rem = nb - jj - 1;
-        if (rem > 0 && b != (T)0) {
-            // rows >= jj owned here; v_jj = 1 on the diagonal row
-            int64_t id = max64((int64_t)jj - r0, 0);
-            T acc[QNB];
-#pragma unroll
-            for (int c = 0; c < QNB; ++c) acc[c] = (T)0;
-            for (int64_t i = id + tid; i < nloc; i += QCT) {
-                T vi = (r0 + i == jj) ? (T)1 : colj[i];
-#pragma unroll
-                for (int c = 0; c < QNB; ++c)
-                    if (c < rem) acc[c] = fma(vi, P[(int64_t)(jj + 1 + c) * R + i], acc[c]);
+        if (tid == 0) bsh[jj] = b;  // identical in every CTA of the cluster
+        // v below the diagonal
+        if (scale)
+            for (int64_t i = ib + tid; i < nloc; i += QCT) xj[i] = xj[i] / v1;
+        __syncthreads();
+        if (lane > jj && lane < nb && b != (T)0) {
+            const T wc = wsh[lane];
+            const int64_t id = max64((int64_t)jj - r0, 0);  // owned rows >= the diagonal
+            for (int64_t i = max64(id, g0); i < g1; ++i) {
+                const T vi = (r0 + i == jj) ? (T)1 : xj[i];
+                ac[i] = fma(-wc, vi, ac[i]);
             }
-#pragma unroll
-            for (int c = 0; c < QNB; ++c) {
-                T v = acc[c];
-                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-                if (lane == 0) wred[warp][c] = v;
-            }
-            __syncthreads();
-            if (tid < rem) {
-                T t = (T)0;
-                for (int w = 0; w < QCT / 32; ++w) t += wred[w][tid];
-                for (int q = 0; q < QCL; ++q) *cluster.map_shared_rank(&w_all[buf][rank][tid], q) = t;
-            }
-            cluster.sync();
-            if (tid < rem) {
-                T t = (T)0;
-                for (int q = 0; q < QCL; ++q) t += w_all[buf][q][tid];
-                wcol[tid] = b * t;
-            }
-            __syncthreads();
-            for (int64_t i = id + tid; i < nloc; i += QCT) {
-                T vi = (r0 + i == jj) ? (T)1 : colj[i];
-                for (int c = 0; c < rem; ++c) {
-                    T* p = &P[(int64_t)(jj + 1 + c) * R + i];
-                    *p = fma(-wcol[c], vi, *p);
-                }
-            }
+        }
+        __syncthreads();
+        if (rank == owner && tid == 0) {
+            xj[jj - r0] = mu;
+            beta_out[k0 + jj] = b;
         }
         __syncthreads();
     }
@@ -290,8 +272,8 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(QCT)
         if (p < nb && q < nb) {
             for (int64_t i = 0; i < nloc; ++i) {
                 int64_t gi = r0 + i;
-                T vp = gi < p ? (T)0 : (gi == p ? (T)1 : P[(int64_t)p * R + i]);
-                T vq = gi < q ? (T)0 : (gi == q ? (T)1 : P[(int64_t)q * R + i]);
+                T vp = gi < p ? (T)0 : (gi == p ? (T)1 : P[(int64_t)p * Rp + i]);
+                T vq = gi < q ? (T)0 : (gi == q ? (T)1 : P[(int64_t)q * Rp + i]);
                 y = fma(vp, vq, y);
             }
         }
@@ -302,7 +284,7 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(QCT)
         int64_t i = q % R, c = q / R;
         if (i < nloc && c < nb) {
             int64_t gi = r0 + i;
-            T pv = P[q];
+            T pv = P[c * Rp + i];
             W[(k0 + gi) + (k0 + c) * ld] = pv;
             V[gi + c * ldv] = gi < c ? (T)0 : (gi == c ? (T)1 : pv);
         } else if (i < nloc) {
@@ -428,7 +410,11 @@ static lsq_status qr_run(const void* As, int64_t s, int64_t n, int64_t ldas, int
     for (int64_t k0 = 0; k0 < n; k0 += QNB) {
         int nb = (int)std::min<int64_t>(QNB, n - k0);
         int64_t rows = s - k0;
-        size_t clsm = sizeof(T) * (size_t)ceil_div(rows, QCL) * QNB;
+        size_t clsm = sizeof(T) * (size_t)(ceil_div(rows, QCL) | 1) * QNB;
+        // Householder panel: sum over its columns of 4 (rows - j)(nb - j) flops
+        double pflops = 0.0;
+        for (int j = 0; j < nb; ++j) pflops += 4.0 * (double)(rows - j) * (double)(nb - j);
+        stage_mark(ST_K_QRPANEL, true, st);
         if (clsm <= 160 * 1024) {
             LSQ_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)clsm));
             k_qr_panel_cl<T><<<QCL, QCT, clsm, st>>>(W, s, s, k0, nb, beta, Tm, V, rows);
@@ -436,6 +422,7 @@ static lsq_status qr_run(const void* As, int64_t s, int64_t n, int64_t ldas, int
             k_qr_panel<T><<<1, QPT, 0, st>>>(W, s, s, k0, nb, beta, Tm, V, rows);
         }
         LSQ_LAUNCH_CHECK();
+        stage_mark(ST_K_QRPANEL, false, st, pflops);
         int64_t nt = n - k0 - nb;
         if (nt <= 0) continue;
         T* C = W + k0 + (k0 + nb) * s;

@@ -17,8 +17,7 @@
 // its TMEM and returns.
 #include "common.cuh"
 #include "kernels.cuh"
-
-#include <cuda.h>
+#include "tcgen05.cuh"
 
 #include <algorithm>
 #include <mutex>
@@ -27,92 +26,16 @@ namespace lsq {
 
 constexpr int TC_BM = 128, TC_BN = 128, TC_STAGES = 6, TC_THREADS = 192;
 constexpr int TC_TILE_BYTES = 128 * 128;  // 128 rows x 128 bytes of K
-constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t gtimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    uint64_t t0 = gtimer();
-    for (uint32_t it = 0;; ++it) {
-        if (mbar_try(bar, parity)) return true;
-        if ((it & 255u) == 255u && gtimer() - t0 > TC_WAIT_NS) return false;
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;             // descriptor version of this architecture
-    d |= (uint64_t)2 << 61;             // 128-byte swizzle
-    return d;
-}
-
 // Instruction descriptor: D = F32, A/B format, both K-major, M = 128, N = 128.
 template <int KIND>
-__device__ __forceinline__ uint32_t umma_idesc() {
-    uint32_t fmt = KIND == 0 ? 1u : 0u;  // kind::f16: BF16 = 1, F16 = 0; kind::f8f6f4: E4M3 = 0
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+__device__ __forceinline__ uint32_t tc_idesc() {
+    return umma_idesc(KIND == 0 ? 1u : 0u, TC_BM, TC_BN);
 }
 
 template <int KIND>
 __device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
-    if (KIND == 2) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-            "l"(a), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
-    } else {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-            "l"(a), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
-    }
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
+    if (KIND == 2) umma_f8(tmem_d, a, b, idesc, accum);
+    else umma_f16(tmem_d, a, b, idesc, accum);
 }
 
 template <int KIND>
@@ -183,7 +106,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
-        const uint32_t idesc = umma_idesc<KIND>();
+        const uint32_t idesc = tc_idesc<KIND>();
         for (int kb = 0; kb < nk; ++kb) {
             int s = kb % TC_STAGES, r = kb / TC_STAGES;
             if (!mbar_wait(&full[s], (uint32_t)(r & 1))) {
@@ -265,11 +188,7 @@ __global__ void k_reduce_f32(const float* __restrict__ part, int splits, int64_t
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn tensor_map_encoder() {
+EncodeTiledFn tensor_map_encoder() {
     static std::once_flag once;
     static EncodeTiledFn fn = nullptr;
     std::call_once(once, [] {

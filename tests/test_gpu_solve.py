@@ -82,7 +82,10 @@ def test_auto_precision_matches_oracle(kap, want):
     k0, ch = lsq.condest(dev_colmajor(pr.A))
     assert int(to_np(ch)[0]) == want
     assert info == 0
-    assert_solution_parity(x, ref["x"], pr.x_star, kap, 1e-6, refined=False)
+    # unrefined at kappa = 1e10 the error (~1e-4) is rounding noise amplified
+    # by kappa^2 rho: judge it against several oracle realizations
+    more = oracle_realizations(pr, hpne=False, kind=O.GAUSSIAN, s=192, zeta=0, seed=8, sketch_prec=O.AUTO)
+    assert_solution_parity(x, ref["x"], pr.x_star, kap, 1e-6, refined=False, realizations=more)
 
 
 def test_edge_shapes():

@@ -150,7 +150,7 @@ def test_trsm_gram(hpne, m, n, kap):
         np.linalg.norm(Ap_o) * np.linalg.norm(pr.b) / np.linalg.norm(c_o)
 
 
-@pytest.mark.parametrize("n", [1, 7, 64, 65, 200, 1024])
+@pytest.mark.parametrize("n", [1, 7, 64, 65, 200, 1024, 1500])
 def test_cholesky_solve(n):
     rng = np.random.default_rng(n)
     X = rng.standard_normal((3 * n + 5, n))

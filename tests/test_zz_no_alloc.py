@@ -57,8 +57,14 @@ def test_noalloc_matches_workspace_entry_point(order):
     for (m, n, hpne) in order:
         A, R, b = _case(m, n, 1e3, m + n)
         Ap, G, c = _noalloc(A, R, b, hpne)
-        Ap_ref, G_ref, c_ref = (t.cpu().numpy() for t in lsq.trsm_gram(A, R, b, hpne=hpne))
-        # same TRSM kernel; the Gram may use fewer K splits (summation order only)
+        # the workspace entry point with the tensor-core FP64 products switched
+        # off runs the same CUDA-core TRSM kernel; the Gram may use fewer K
+        # splits (summation order only)
+        prev = lsq.set_fp64_emulation(False)
+        try:
+            Ap_ref, G_ref, c_ref = (t.cpu().numpy() for t in lsq.trsm_gram(A, R, b, hpne=hpne))
+        finally:
+            lsq.set_fp64_emulation(prev)
         np.testing.assert_array_equal(Ap, Ap_ref)
         assert _rel(G, G_ref) <= 4 * m * U64
         assert _rel(c, c_ref) <= 4 * m * U64
