@@ -106,94 +106,83 @@ template lsq_status rank_update_ext<float>(float*, int64_t, const float*, int64_
 // ---------------------------------------------------------------------------
 // Cholesky
 // ---------------------------------------------------------------------------
-// Cholesky of the 32 x 32 block B[off.., off..] (lower part) by one warp:
-// lane r keeps row r in registers (right-looking, pivot column broadcast by
-// shuffles, compile-time column indices).  Writes L (zeros above) back and
-// returns the first breakdown column (1-based, within the block) or 0.
+// 1 / sqrt(d) for d > 0.  FP64: an FP32 estimate refined by two Newton steps
+// y <- y + y (1 - d y^2) / 2 in FP64 (six dependent FP64 operations instead of
+// a square root and a division, each of which costs about ten times an FMA
+// on this part); relative error a few units in the last place.
 template <typename T>
-__device__ int warp_chol32(T (*B)[CNB + 1], int off) {
-    const int lane = threadIdx.x & 31;
-    T a[32];
+__device__ __forceinline__ T rsqrt_pivot(T d) {
+    if constexpr (sizeof(T) == 4) {
+        return (T)1 / sqrtf(d);
+    } else {
+        if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+        double y = (double)rsqrtf((float)d);
 #pragma unroll
-    for (int c = 0; c < 32; ++c) a[c] = B[off + lane][off + c];
-    int bad = 0;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        T d = __shfl_sync(0xffffffffu, a[j], j);
-        if (!(d > (T)0) || !isfinite(d)) {
-            if (!bad) bad = j + 1;
-            d = (T)1;
+        for (int it = 0; it < 2; ++it) {
+            const double h = d * y;
+            const double e = fma(-h, y, 1.0);
+            y = fma(0.5 * y, e, y);
         }
-        const T piv = sqrt(d);
-        T l = a[j] / piv;
-        if (lane == j) l = piv;
-        if (lane >= j) a[j] = l;
-#pragma unroll
-        for (int c = j + 1; c < 32; ++c) {
-            const T lc = __shfl_sync(0xffffffffu, l, c);
-            if (lane >= c) a[c] = fma(-l, lc, a[c]);
-        }
+        return y;
     }
-#pragma unroll
-    for (int c = 0; c < 32; ++c) B[off + lane][off + c] = lane >= c ? a[c] : (T)0;
-    return bad;
 }
 
-// Diagonal block of CNB = 64 as 2 x 2 blocks of 32 in one CTA:
-// L11 = chol(A11); L21 = A21 L11^{-T}; A22 -= L21 L21^T; L22 = chol(A22).
+// Diagonal block (CNB x CNB) in one CTA, right-looking.  Per column j: one
+// thread forms the pivot (L_jj = d r, r = 1/sqrt(d)), the column is scaled by
+// r into a separate buffer, and the update L[r][c] -= l_r l_c visits only the
+// active triangle j < c <= r, spread over all threads so that every warp
+// issues full-width FP64 instructions.
 template <typename T>
 __global__ void __launch_bounds__(256) k_potrf_diag(T* __restrict__ G, int64_t ld, int64_t n, int64_t k0,
                                                     int32_t* __restrict__ info) {
     if (*info != 0) return;
     __shared__ T D[CNB][CNB + 1];
-    __shared__ int bad1, bad2;
+    __shared__ T colj[CNB];
+    __shared__ T rj;
+    __shared__ int bad;
     const int nb = (int)min64(CNB, n - k0);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x;
     for (int q = tid; q < CNB * CNB; q += 256) {
         const int r = q & 63, c = q >> 6;
-        // identity padding beyond nb keeps the factorization of the padded block trivial
-        D[r][c] = (r < nb && c < nb) ? G[(k0 + r) + (k0 + c) * ld] : (r == c ? (T)1 : (T)0);
+        D[r][c] = (r < nb && c < nb) ? G[(k0 + r) + (k0 + c) * ld] : (T)0;
     }
+    if (tid == 0) bad = 0;
     __syncthreads();
-    if (warp == 0) {
-        int b = warp_chol32<T>(D, 0);
-        if (lane == 0) bad1 = b;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        // row 32 + lane of A21: x L11^T = a, right-looking, reciprocal pivots
-        T x[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) x[c] = D[32 + lane][c];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            x[j] = x[j] * ((T)1 / D[j][j]);
-#pragma unroll
-            for (int k = j + 1; k < 32; ++k) x[k] = fma(-x[j], D[k][j], x[k]);
+    for (int j = 0; j < nb; ++j) {
+        if (tid == 0) {
+            const T d = D[j][j];
+            if (!(d > (T)0) || !isfinite(d)) {
+                bad = j + 1;
+            } else {
+                const T r = rsqrt_pivot<T>(d);
+                rj = r;
+                D[j][j] = d * r;
+            }
         }
-#pragma unroll
-        for (int c = 0; c < 32; ++c) D[32 + lane][c] = x[c];
-    }
-    __syncthreads();
-    // A22 -= L21 L21^T, lower entries (528), spread over the CTA
-    for (int e = tid; e < 32 * 32; e += 256) {
-        const int r = e & 31, c = e >> 5;
-        if (r >= c) {
-            T t = D[32 + r][32 + c];
-#pragma unroll 8
-            for (int k = 0; k < 32; ++k) t = fma(-D[32 + r][k], D[32 + c][k], t);
-            D[32 + r][32 + c] = t;
+        __syncthreads();
+        if (bad) break;
+        if (tid > j && tid < nb) {
+            const T l = D[tid][j] * rj;
+            D[tid][j] = l;
+            colj[tid] = l;
         }
+        __syncthreads();
+        // active triangle: a = nb - 1 - j rows/columns below the pivot; entry e
+        // -> (cc, rr) with cc <= rr (row-major over the lower triangle)
+        const int a = nb - 1 - j;
+        const int E = a * (a + 1) / 2;
+        for (int e = tid; e < E; e += 256) {
+            int rr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+            while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+            while (rr * (rr + 1) / 2 > e) --rr;
+            const int cc = e - rr * (rr + 1) / 2;
+            const int r = j + 1 + rr, c = j + 1 + cc;
+            D[r][c] = fma(-colj[r], colj[c], D[r][c]);
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    if (warp == 0) {
-        int b = warp_chol32<T>(D, 32);
-        if (lane == 0) bad2 = b;
-    }
-    __syncthreads();
-    const int bad = bad1 ? bad1 : (bad2 ? 32 + bad2 : 0);
     if (bad) {
-        if (tid == 0 && bad <= nb) set_info_once(info, (int32_t)(k0 + bad));
+        if (tid == 0) set_info_once(info, (int32_t)(k0 + bad));
         return;
     }
     for (int q = tid; q < CNB * CNB; q += 256) {
@@ -202,36 +191,43 @@ __global__ void __launch_bounds__(256) k_potrf_diag(T* __restrict__ G, int64_t l
     }
 }
 
-// L21 = G21 L11^{-T}: one thread per row (the row in registers), 32 rows per
-// block so that the FP64 work spreads over many SMs.  Right-looking
-// substitution with the reciprocal pivots: the dependent chain is one
-// multiply and one FMA per column.
+// L21 = G21 L11^{-T}, right-looking with reciprocal pivots.  16 threads per
+// row (2 rows per warp), thread `sub` owning columns sub, sub+16, sub+32,
+// sub+48 in registers; x_j is broadcast within the half-warp by a shuffle.
 template <typename T>
-__global__ void __launch_bounds__(32) k_potrf_panel(T* __restrict__ G, int64_t ld, int64_t n, int64_t k0,
-                                                    const int32_t* __restrict__ info) {
+__global__ void __launch_bounds__(128) k_potrf_panel(T* __restrict__ G, int64_t ld, int64_t n, int64_t k0,
+                                                     const int32_t* __restrict__ info) {
     if (*info != 0) return;
     __shared__ T L11[CNB][CNB + 1];
     __shared__ T rinv[CNB];
-    for (int q = threadIdx.x; q < CNB * CNB; q += 32) {
+    for (int q = threadIdx.x; q < CNB * CNB; q += 128) {
         int r = q & 63, c = q >> 6;
         L11[r][c] = G[(k0 + r) + (k0 + c) * ld];
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < CNB; j += 32) rinv[j] = (T)1 / L11[j][j];
+    for (int j = threadIdx.x; j < CNB; j += 128) rinv[j] = (T)1 / L11[j][j];
     __syncthreads();
-    const int64_t i = k0 + CNB + (int64_t)blockIdx.x * 32 + threadIdx.x;
-    if (i >= n) return;
-    T x[CNB];
+    const int lane = threadIdx.x & 31, sub = lane & 15;
+    const int64_t i = k0 + CNB + (int64_t)blockIdx.x * 8 + (threadIdx.x >> 4);
+    const bool live = i < n;
+    T x[4];
 #pragma unroll
-    for (int j = 0; j < CNB; ++j) x[j] = G[i + (k0 + j) * ld];
+    for (int q = 0; q < 4; ++q) x[q] = live ? G[i + (k0 + sub + 16 * q) * ld] : (T)0;
 #pragma unroll
     for (int j = 0; j < CNB; ++j) {
-        x[j] = x[j] * rinv[j];
+        const int qj = j >> 4, sj = j & 15;
+        if (sub == sj) x[qj] = x[qj] * rinv[j];
+        const T xj = __shfl_sync(0xffffffffu, x[qj], (lane & 16) | sj);
 #pragma unroll
-        for (int k = j + 1; k < CNB; ++k) x[k] = fma(-x[j], L11[k][j], x[k]);
+        for (int q = 0; q < 4; ++q) {
+            const int k = sub + 16 * q;
+            if (k > j) x[q] = fma(-xj, L11[k][j], x[q]);
+        }
     }
+    if (live) {
 #pragma unroll
-    for (int j = 0; j < CNB; ++j) G[i + (k0 + j) * ld] = x[j];
+        for (int q = 0; q < 4; ++q) G[i + (k0 + sub + 16 * q) * ld] = x[q];
+    }
 }
 
 template <typename T>
@@ -254,7 +250,7 @@ lsq_status launch_cholesky(T* G, int64_t n, int64_t ld, int32_t* info, cudaStrea
         LSQ_LAUNCH_CHECK();
         int64_t rest = n - k0 - nb;
         if (rest <= 0) break;
-        k_potrf_panel<T><<<(unsigned)ceil_div(rest, 32), 32, 0, st>>>(G, ld, n, k0, info);
+        k_potrf_panel<T><<<(unsigned)ceil_div(rest, 8), 128, 0, st>>>(G, ld, n, k0, info);
         LSQ_LAUNCH_CHECK();
         T* L21 = G + (k0 + nb) + k0 * ld;
         T* A22 = G + (k0 + nb) + (k0 + nb) * ld;
@@ -409,8 +405,11 @@ lsq_status launch_lu(double* H, int64_t n, int64_t ld, int32_t* piv, int32_t* in
 // off-diagonal 32 x 32 block of the operator while the solution of that block
 // is still being computed, waits for the block's flag (bounded: 2 s of
 // %globaltimer, then an error is recorded and the failure passed on), applies
-// it, and finally solves its diagonal block with shuffles (multiplying by the
-// reciprocal of each diagonal entry) and publishes y_b with a release flag.
+// it, and finally solves its diagonal block with shuffles and publishes y_b
+// with a release flag.  The diagonal block, its reciprocal pivots and the
+// block's own right-hand side are staged before the first wait; the block's
+// rows are scaled to a unit diagonal, so the dependent chain of the diagonal
+// solve is one shuffle and one FMA per column.
 // Partial sums are combined in a fixed order, so the result does not depend
 // on timing.
 // ---------------------------------------------------------------------------
@@ -420,8 +419,10 @@ __global__ void __launch_bounds__(128) k_trsv_wave(int kind, const T* __restrict
                                                    int32_t* __restrict__ err) {
     if (info && *info != 0) return;
     __shared__ T blk[32][33];
+    __shared__ T dgb[32][33];  // diagonal block, rows scaled to a unit diagonal
     __shared__ T part[4][32];
     __shared__ T yk[32];
+    __shared__ T rin[32];
     __shared__ int vb, failed;
     const int tid = threadIdx.x, r = tid & 31, q = tid >> 5;
     const int nblk = (int)((n + 31) / 32);
@@ -433,10 +434,28 @@ __global__ void __launch_bounds__(128) k_trsv_wave(int kind, const T* __restrict
     const int v = vb;
     const bool forward = (kind == TB_LOWER || kind == TB_UNIT_LOWER);
     const bool trans = (kind == TB_LOWER_T);  // operator entry (i, j) = M[j + i ld]
+    const bool unit = (kind == TB_UNIT_LOWER);
     const int b = forward ? v : nblk - 1 - v;
     const int64_t b0 = (int64_t)b * 32;
     const int bs = (int)min64(32, n - b0);
-    T acc = (T)0;
+    // everything that does not depend on other blocks, before the first wait:
+    // the diagonal block, the reciprocal pivots and this block's right-hand side
+    for (int e = tid; e < 1024; e += 128) {
+        int rr, jj;
+        if (trans) { jj = e & 31; rr = e >> 5; } else { rr = e & 31; jj = e >> 5; }
+        T val = (T)0;
+        if (rr < bs && jj < bs) val = trans ? M[(b0 + jj) + (b0 + rr) * ld] : M[(b0 + rr) + (b0 + jj) * ld];
+        dgb[rr][jj] = val;
+    }
+    T vv = (tid < 32 && r < bs) ? y[b0 + r] : (T)0;
+    __syncthreads();
+    if (tid < 32) rin[r] = (r < bs && !unit) ? (T)1 / dgb[r][r] : (T)1;
+    __syncthreads();
+    for (int e = tid; e < 1024; e += 128) {
+        const int rr = e & 31, jj = e >> 5;
+        if (rr != jj) dgb[rr][jj] *= rin[rr];
+    }
+    T acc0 = (T)0, acc1 = (T)0;
     for (int st = 0; st < v; ++st) {
         const int k = forward ? st : nblk - 1 - st;
         const int64_t k0 = (int64_t)k * 32;
@@ -469,36 +488,27 @@ __global__ void __launch_bounds__(128) k_trsv_wave(int kind, const T* __restrict
         if (tid < 32) yk[tid] = tid < ks ? __ldcg(y + k0 + tid) : (T)0;
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc = fma(-blk[r][q * 8 + j], yk[q * 8 + j], acc);
+        for (int j = 0; j < 8; j += 2) {
+            acc0 = fma(-blk[r][q * 8 + j], yk[q * 8 + j], acc0);
+            acc1 = fma(-blk[r][q * 8 + j + 1], yk[q * 8 + j + 1], acc1);
+        }
         __syncthreads();
     }
-    part[q][r] = acc;
-    // diagonal block of the operator
-    for (int e = tid; e < 1024; e += 128) {
-        int rr, jj;
-        if (trans) { jj = e & 31; rr = e >> 5; } else { rr = e & 31; jj = e >> 5; }
-        T val = (T)0;
-        if (rr < bs && jj < bs) val = trans ? M[(b0 + jj) + (b0 + rr) * ld] : M[(b0 + rr) + (b0 + jj) * ld];
-        blk[rr][jj] = val;
-    }
+    part[q][r] = acc0 + acc1;
     __syncthreads();
     if (tid < 32) {
         const bool ok = !failed;
-        const bool unit = (kind == TB_UNIT_LOWER);
-        T vv = r < bs ? y[b0 + r] : (T)0;
         vv = vv + part[0][r] + part[1][r] + part[2][r] + part[3][r];
-        const T rinv = (r < bs && !unit) ? (T)1 / blk[r][r] : (T)1;
+        vv = vv * rin[r];  // unit-diagonal system from here on
         if (forward) {
             for (int jj = 0; jj < bs; ++jj) {
-                if (r == jj) vv = vv * rinv;
-                T vj = __shfl_sync(0xffffffffu, vv, jj);
-                if (r > jj && r < bs) vv = fma(-blk[r][jj], vj, vv);
+                const T vj = __shfl_sync(0xffffffffu, vv, jj);
+                if (r > jj && r < bs) vv = fma(-dgb[r][jj], vj, vv);
             }
         } else {
             for (int jj = bs - 1; jj >= 0; --jj) {
-                if (r == jj) vv = vv * rinv;
-                T vj = __shfl_sync(0xffffffffu, vv, jj);
-                if (r < jj) vv = fma(-blk[r][jj], vj, vv);
+                const T vj = __shfl_sync(0xffffffffu, vv, jj);
+                if (r < jj) vv = fma(-dgb[r][jj], vj, vv);
             }
         }
         if (ok && r < bs) y[b0 + r] = vv;

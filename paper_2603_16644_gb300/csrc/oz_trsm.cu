@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(128) k_ot_colslice(const double* __restrict__ 
 // the exact 128-bit integer is normalised with integer operations and the
 // scale goes into the exponent field (no FP64 instruction); results outside
 // the normal range take the (rare) FP64 path.
-__device__ __forceinline__ double ot_fixed_to_double(long long hi, long long lo, int s) {
+__device__ __noinline__ double ot_fixed_to_double(long long hi, long long lo, int s) {
     unsigned long long L = (unsigned long long)hi << 28;
     long long H = hi >> 36;
     const unsigned long long L2 = L + (unsigned long long)lo;
@@ -310,6 +310,9 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
                 cnt[1] = xq + 1;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint64_t ad = umma_desc(smem_u32(sX + xs * OT_XTILE));
+                // the 4 K steps of one digit pair go back to back into the
+                // same accumulator (measured: interleaving accumulators, even
+                // with operand A kept in the collector, is 3x slower)
                 for (int u = 0; u + t < OT_DIG; ++u) {
                     const uint64_t bd = umma_desc(smem_u32(sY + (ys * OT_DIG + u) * OT_YTILE));
                     const uint32_t acc = tmem + (uint32_t)((t + u) * OT_BN);
@@ -330,11 +333,11 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
         const int quad = warp & 3, half = (warp - 2) >> 2;
         const int64_t row = i0 + quad * 32 + lane;
         const int32_t ex = row < m ? Ex[row] : 0;
-        double cin[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const int64_t col = j0 + half * 32 + j;
-            cin[j] = (row < m && col < N) ? Cin[row + col * ldi] : 0.0;
+        if (row < m) {
+            for (int j = 0; j < 32; ++j) {
+                const int64_t col = j0 + half * 32 + j;
+                if (col < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(Cin + row + col * ldi));
+            }
         }
         if (threadIdx.x - 64 < OT_BN) {
             const int64_t col = j0 + (threadIdx.x - 64);
@@ -346,21 +349,45 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
         if (!ok) *bad = 1;
         const bool go = __all_sync(0xffffffffu, ok && !*bad && nslab > 0);
         if (go) {
-#pragma unroll
+            const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
+#pragma unroll 1
             for (int cc = 0; cc < 2; ++cc) {
                 const int c = half * 32 + cc * 16;
+                double cin[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int64_t col = j0 + c + j;
+                    cin[j] = (row < m && col < N) ? Cin[row + col * ldi] : 0.0;
+                }
                 long long hi[16], lo[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
-#pragma unroll
-                for (int d = 0; d < OT_DIG; ++d) {
-                    uint32_t v[16];
-                    tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(d * OT_BN + c), v);
+                {
+                    uint32_t v0[16], v1[16], v2[16], v3[16];
+                    tmem_ld16_nowait(tl + (uint32_t)(0 * OT_BN + c), v0);
+                    tmem_ld16_nowait(tl + (uint32_t)(1 * OT_BN + c), v1);
+                    tmem_ld16_nowait(tl + (uint32_t)(2 * OT_BN + c), v2);
+                    tmem_ld16_nowait(tl + (uint32_t)(3 * OT_BN + c), v3);
+                    tmem_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const long long S = (long long)__float2int_rn(__uint_as_float(v[j]));
-                        if (d < 4) hi[j] = hi[j] * 128 + S;
-                        else lo[j] = lo[j] * 128 + S;
+                        long long h = (long long)__float2int_rn(__uint_as_float(v0[j]));
+                        h = h * 128 + (long long)__float2int_rn(__uint_as_float(v1[j]));
+                        h = h * 128 + (long long)__float2int_rn(__uint_as_float(v2[j]));
+                        hi[j] = h * 128 + (long long)__float2int_rn(__uint_as_float(v3[j]));
+                    }
+                }
+                {
+                    uint32_t v0[16], v1[16], v2[16], v3[16];
+                    tmem_ld16_nowait(tl + (uint32_t)(4 * OT_BN + c), v0);
+                    tmem_ld16_nowait(tl + (uint32_t)(5 * OT_BN + c), v1);
+                    tmem_ld16_nowait(tl + (uint32_t)(6 * OT_BN + c), v2);
+                    tmem_ld16_nowait(tl + (uint32_t)(7 * OT_BN + c), v3);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        long long l = (long long)__float2int_rn(__uint_as_float(v0[j]));
+                        l = l * 128 + (long long)__float2int_rn(__uint_as_float(v1[j]));
+                        l = l * 128 + (long long)__float2int_rn(__uint_as_float(v2[j]));
+                        lo[j] = l * 128 + (long long)__float2int_rn(__uint_as_float(v3[j]));
                     }
                 }
                 if (row < m) {
@@ -375,7 +402,7 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
                             } else {
                                 val = ot_fixed_to_double(hi[j], lo[j], ex + ey - 61);
                             }
-                            Cout[row + col * ldo] = cin[cc * 16 + j] - val;
+                            Cout[row + col * ldo] = cin[j] - val;
                         }
                     }
                 }

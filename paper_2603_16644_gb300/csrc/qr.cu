@@ -212,8 +212,18 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(QCT)
         T* ac = P + (int64_t)lane * Rp;
         const int64_t ib = max64((int64_t)jj + 1 - r0, 0);  // first owned row strictly below the diagonal
         T acc = (T)0;
-        if (lane >= jj && lane < nb)
-            for (int64_t i = max64(ib, g0); i < g1; ++i) acc = fma(xj[i], ac[i], acc);
+        if (lane >= jj && lane < nb) {
+            T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+            int64_t i = max64(ib, g0);
+            for (; i + 4 <= g1; i += 4) {
+                a0 = fma(xj[i], ac[i], a0);
+                a1 = fma(xj[i + 1], ac[i + 1], a1);
+                a2 = fma(xj[i + 2], ac[i + 2], a2);
+                a3 = fma(xj[i + 3], ac[i + 3], a3);
+            }
+            for (; i < g1; ++i) a0 = fma(xj[i], ac[i], a0);
+            acc = (a0 + a1) + (a2 + a3);
+        }
         part[warp][lane] = acc;
         __syncthreads();
         if (warp == 0) {
@@ -253,8 +263,22 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(QCT)
         if (lane > jj && lane < nb && b != (T)0) {
             const T wc = wsh[lane];
             const int64_t id = max64((int64_t)jj - r0, 0);  // owned rows >= the diagonal
-            for (int64_t i = max64(id, g0); i < g1; ++i) {
-                const T vi = (r0 + i == jj) ? (T)1 : xj[i];
+            const int64_t dr = (int64_t)jj - r0;             // local index of the diagonal row
+            int64_t i = max64(id, g0);
+            // blocks of 8 rows: all loads before the stores (the column of v and
+            // the updated column never overlap)
+            for (; i + 8 <= g1; i += 8) {
+                T v[8], a[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    v[q] = (i + q == dr) ? (T)1 : xj[i + q];
+                    a[q] = ac[i + q];
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) ac[i + q] = fma(-wc, v[q], a[q]);
+            }
+            for (; i < g1; ++i) {
+                const T vi = (i == dr) ? (T)1 : xj[i];
                 ac[i] = fma(-wc, vi, ac[i]);
             }
         }
@@ -265,21 +289,7 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(QCT)
         }
         __syncthreads();
     }
-    // Y = V^T V partial over the owned rows (V: 0 above, 1 on the diagonal)
-    for (int e = tid; e < QNB * QNB; e += QCT) {
-        int p = e % QNB, q = e / QNB;
-        T y = (T)0;
-        if (p < nb && q < nb) {
-            for (int64_t i = 0; i < nloc; ++i) {
-                int64_t gi = r0 + i;
-                T vp = gi < p ? (T)0 : (gi == p ? (T)1 : P[(int64_t)p * Rp + i]);
-                T vq = gi < q ? (T)0 : (gi == q ? (T)1 : P[(int64_t)q * Rp + i]);
-                y = fma(vp, vq, y);
-            }
-        }
-        Ypart[p][q] = y;
-    }
-    // write R / v back to W and the explicit V
+    // write R / v back to W and the explicit V (0 above, 1 on the diagonal)
     for (int64_t q = tid; q < R * QNB; q += QCT) {
         int64_t i = q % R, c = q / R;
         if (i < nloc && c < nb) {
@@ -291,6 +301,31 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(QCT)
             V[(r0 + i) + c * ldv] = (T)0;
         }
     }
+    __syncthreads();
+    // make the local panel the explicit V, then Y = V^T V over the owned rows
+    for (int64_t q = tid; q < R * QNB; q += QCT) {
+        int64_t i = q % R, c = q / R;
+        int64_t gi = r0 + i;
+        if (c < nb && gi <= c) P[c * Rp + i] = gi == c ? (T)1 : (T)0;
+    }
+    __syncthreads();
+    {
+        const int p = lane, q0 = warp * 4;  // Y[p][q0 .. q0 + 3]
+        T y0 = (T)0, y1 = (T)0, y2 = (T)0, y3 = (T)0;
+        const T* vp = P + (int64_t)p * Rp;
+        const T* vq = P + (int64_t)q0 * Rp;
+        for (int64_t i = 0; i < nloc; ++i) {
+            const T a = vp[i];
+            y0 = fma(a, vq[i], y0);
+            y1 = fma(a, vq[Rp + i], y1);
+            y2 = fma(a, vq[2 * Rp + i], y2);
+            y3 = fma(a, vq[3 * Rp + i], y3);
+        }
+        Ypart[p][q0] = y0;
+        Ypart[p][q0 + 1] = y1;
+        Ypart[p][q0 + 2] = y2;
+        Ypart[p][q0 + 3] = y3;
+    }
     cluster.sync();
     if (rank == 0) {
         for (int e = tid; e < QNB * QNB; e += QCT) {
@@ -301,17 +336,17 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(QCT)
         }
         __syncthreads();
         if (warp == 0) {
+            // column by column: T[0:j, j] = -beta_j T[0:j, 0:j] Y[0:j, j]; lane = row
             T trow[QNB];
 #pragma unroll
-            for (int c = 0; c < QNB; ++c) trow[c] = (T)0;
-            // column by column: T[0:j, j] = -beta_j T[0:j, 0:j] Y[0:j, j]; lane = row
-            for (int jj = 0; jj < nb; ++jj) {
-                T bj = bsh[jj];
+            for (int jj = 0; jj < QNB; ++jj) {
                 T t = (T)0;
+#pragma unroll
                 for (int qq = 0; qq < jj; ++qq) t = fma(trow[qq], Ts[qq][jj], t);
-                if (lane < jj) trow[jj] = -bj * t;
-                if (lane == jj) trow[jj] = bj;
+                const T bj = jj < nb ? bsh[jj] : (T)0;
+                trow[jj] = lane < jj ? -bj * t : (lane == jj ? bj : (T)0);
             }
+#pragma unroll
             for (int c = 0; c < QNB; ++c) Tm[lane + c * QNB] = trow[c];
         }
     }
