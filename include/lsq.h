@@ -422,6 +422,11 @@ int32_t lsq_profile(int32_t enable);
 int32_t lsq_profile_collect(double* ms_by_stage, int32_t* count_by_stage, int32_t nstages);
 int32_t lsq_profile_collect_work(double* ms_by_stage, int32_t* count_by_stage, double* work_by_stage,
                                  int32_t nstages);
+/* The individual records of one stage since the last collect (before
+ * lsq_profile_collect*, which clears them): milliseconds and work of the
+ * first `cap` records into ms / work; returns the number of records of that
+ * stage (negative status on error).  Waits for the events. */
+int32_t lsq_profile_records(int32_t stage, double* ms, double* work, int32_t cap);
 
 /* FP64 FMA throughput probe: `blocks` CTAs of 256 threads, each thread
  * 8 independent FMA chains of `iters` steps (16 * iters flops per thread).

@@ -79,6 +79,7 @@ def lib():
             "lsq_profile_collect": (C.c_int32, [C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_int32]),
             "lsq_profile_collect_work": (C.c_int32, [C.POINTER(C.c_double), C.POINTER(C.c_int32),
                                                      C.POINTER(C.c_double), C.c_int32]),
+            "lsq_profile_records": (C.c_int32, [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int32]),
             "lsq_probe_fp64_fma": (C.c_int32, [_i64, C.c_int32, _vp, _vp]),
             "lsq_trsm_tc_workspace_size": (_sz, [_i64, _i64]),
             "lsq_trsm_tc": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
@@ -118,6 +119,18 @@ def profile_collect(with_work: bool = False) -> dict:
     if with_work:
         return {name: (ms[i], cnt[i], work[i]) for i, name in enumerate(STAGES)}
     return {name: (ms[i], cnt[i]) for i, name in enumerate(STAGES)}
+
+
+def profile_records(stage: str) -> list:
+    """[(ms, work)] of every record of one stage since the last collect."""
+    idx = STAGES.index(stage)
+    n = int(lib().lsq_profile_records(idx, (C.c_double * 1)(), (C.c_double * 1)(), 0))
+    if n < 0:
+        raise LsqError(f"lsq_profile_records failed: {status_string(-n)}")
+    ms = (C.c_double * max(1, n))()
+    work = (C.c_double * max(1, n))()
+    lib().lsq_profile_records(idx, ms, work, n)
+    return [(ms[i], work[i]) for i in range(n)]
 
 
 def probe_fp64_fma(iters: int, blocks: int, scratch: torch.Tensor) -> None:

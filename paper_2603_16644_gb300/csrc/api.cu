@@ -469,6 +469,25 @@ int32_t lsq_profile_collect_work(double* ms_by_stage, int32_t* count_by_stage, d
     return LSQ_OK;
 }
 
+int32_t lsq_profile_records(int32_t stage, double* ms, double* work, int32_t cap) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (!ms || !work || cap < 0) return -LSQ_ERR_ARG;
+    int32_t k = 0;
+    for (auto& rec : g_prof.recs) {
+        if (rec.stage != stage) continue;
+        if (k < cap) {
+            if (cudaEventSynchronize(g_prof.pool[rec.ev_end]) != cudaSuccess) return -LSQ_ERR_CUDA;
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, g_prof.pool[rec.ev_begin], g_prof.pool[rec.ev_end]) != cudaSuccess)
+                return -LSQ_ERR_CUDA;
+            ms[k] = t;
+            work[k] = rec.work;
+        }
+        ++k;
+    }
+    return k;
+}
+
 const char* lsq_status_string(int32_t s) {
     switch (s) {
     case LSQ_OK: return "LSQ_OK";
