@@ -401,6 +401,10 @@ lsq_status lsq_pne_solve_learned(const double* A, int64_t m, int64_t n, int64_t 
  * the previous setting.  Process-wide; for tests and comparisons. */
 int32_t lsq_set_tensor_core_sketch(int32_t enable);
 
+/* The CUDA error string behind the most recent LSQ_ERR_CUDA of this
+ * process ("no error" if none). */
+const char* lsq_last_cuda_error(void);
+
 /* Number of kernel launches this library has issued since it was loaded. */
 int64_t lsq_launch_count(void);
 

@@ -55,6 +55,7 @@ def lib():
         sig = {
             "lsq_version": (C.c_int32, []),
             "lsq_status_string": (C.c_char_p, [C.c_int32]),
+            "lsq_last_cuda_error": (C.c_char_p, []),
             "lsq_workspace_size": (_sz, [C.c_int32, _i64, _i64, C.POINTER(Opts)]),
             "lsq_precision_from_kappa0": (C.c_int32, [C.c_double]),
             "lsq_sparse_sign_operator": (C.c_int32, [C.c_uint64, _i64, _i64, C.c_int32, _vp, _vp, _vp]),
@@ -143,7 +144,8 @@ def status_string(rc: int) -> str:
 
 def _check(rc, what):
     if rc != 0:
-        raise LsqError(f"{what} failed: {status_string(rc)} ({rc})")
+        extra = f" [{lib().lsq_last_cuda_error().decode()}]" if rc == 5 else ""
+        raise LsqError(f"{what} failed: {status_string(rc)} ({rc}){extra}")
 
 
 def _stream(device=None):

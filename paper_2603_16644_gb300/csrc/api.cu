@@ -38,6 +38,9 @@ static size_t prof_event() {
     return g_prof.next++;
 }
 
+static std::atomic<int> g_last_cuda_error{0};
+void note_cuda_error(cudaError_t e) { g_last_cuda_error.store((int)e); }
+
 void stage_mark(int stage, bool begin, cudaStream_t st, double work) {
     std::lock_guard<std::mutex> lk(g_prof.mu);
     if (!g_prof.on) return;
@@ -389,6 +392,8 @@ lsq_status solve_host_impl(bool hpne, const double* A_host, int64_t m, int64_t n
 extern "C" {
 
 int32_t lsq_version(void) { return 100; }
+
+const char* lsq_last_cuda_error(void) { return cudaGetErrorString((cudaError_t)g_last_cuda_error.load()); }
 
 int64_t lsq_launch_count(void) { return (int64_t)g_launches.load(); }
 

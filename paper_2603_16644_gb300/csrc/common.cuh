@@ -12,10 +12,15 @@
 
 namespace lsq {
 
+// Remembers the CUDA error behind the last LSQ_ERR_CUDA (lsq_last_cuda_error).
+void note_cuda_error(cudaError_t e);
 #define LSQ_CUDA_TRY(expr)                                  \
     do {                                                    \
         cudaError_t e__ = (expr);                           \
-        if (e__ != cudaSuccess) return LSQ_ERR_CUDA;        \
+        if (e__ != cudaSuccess) {                           \
+            ::lsq::note_cuda_error(e__);                    \
+            return LSQ_ERR_CUDA;                            \
+        }                                                   \
     } while (0)
 
 // Every kernel launch goes through this check; it also counts launches

@@ -39,7 +39,7 @@ constexpr int OT_BK = 64;                   // K per stage: 64 BF16 = 128 bytes
 constexpr int OT_XST = 6;                   // stages of X digit tiles
 constexpr int OT_KMAX = 512;                // exact FP32 group sums up to this K
 constexpr int OT_NB = 32;                   // diagonal block solved by substitution
-constexpr int OT_THREADS = 320;             // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int OT_THREADS = 576;             // warp 0 TMA, warp 1 MMA, warps 2-17 epilogue
 constexpr int OT_XTILE = OT_BM * 128;       // bytes of one X digit tile
 constexpr int OT_YTILE = OT_BN * 128;       // bytes of one Y digit tile
 constexpr int32_t OT_NONFINITE = 0x7fffffff;
@@ -173,52 +173,60 @@ __global__ void __launch_bounds__(128) k_ot_colslice(const double* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Update C_out = C_in - X Y for one 128 x 64 tile (C_in may equal C_out).
+// Update C_out = C_in - X Y over 128 x 64 tiles (C_in may equal C_out).
 // ---------------------------------------------------------------------------
 // 2^s (hi 2^28 + lo) for |hi|, |lo| < 2^47, rounded once to nearest-even:
 // the exact 128-bit integer is normalised with integer operations and the
-// scale goes into the exponent field (no FP64 instruction); results outside
-// the normal range take the (rare) FP64 path.
-__device__ __noinline__ double ot_fixed_to_double(long long hi, long long lo, int s) {
+// scale goes into the exponent field (no FP64 instruction).  Straight-line
+// code (selects), so that the compiler interleaves independent conversions;
+// results outside the normal range take the (rare) FP64 path.
+__device__ __forceinline__ double ot_fixed_to_double(long long hi, long long lo, int s) {
     unsigned long long L = (unsigned long long)hi << 28;
     long long H = hi >> 36;
     const unsigned long long L2 = L + (unsigned long long)lo;
     H += (lo >> 63) + (L2 < L ? 1 : 0);
     L = L2;
-    const bool neg = H < 0;
-    if (neg) {
-        L = ~L + 1ull;
-        H = ~H + (L == 0 ? 1 : 0);
-    }
-    const unsigned long long uH = (unsigned long long)H;
-    if (uH == 0 && L == 0) return 0.0;
-    int p = uH ? 127 - __clzll((long long)uH) : 63 - __clzll((long long)L);
-    unsigned long long mant;
-    if (p <= 52) {
-        mant = L << (52 - p);
-    } else {
-        const int sh = p - 52;  // 1 .. 22
-        mant = (L >> sh) | (uH << (64 - sh));
-        const unsigned long long rb = (L >> (sh - 1)) & 1ull;
-        const bool sticky = (L & ((1ull << (sh - 1)) - 1ull)) != 0;
-        if (rb && (sticky || (mant & 1ull))) {
-            ++mant;
-            if (mant == (1ull << 53)) {
-                mant >>= 1;
-                ++p;
-            }
-        }
-    }
+    // magnitude: two's-complement negation of (H:L) when negative
+    const unsigned long long sgn = (unsigned long long)(H >> 63);
+    const unsigned long long neg = sgn & 1ull;
+    const unsigned long long uL = (L ^ sgn) + neg;
+    const unsigned long long uH = ((unsigned long long)H ^ sgn) + (neg & (uL == 0 ? 1ull : 0ull));
+    const bool zero = (uH | uL) == 0;
+    int p = uH ? 127 - __clzll((long long)uH) : 63 - __clzll((long long)uL);
+    const int shl = p <= 52 ? 52 - p : 0;            // 0 .. 52
+    const int shr = p > 52 ? p - 52 : 0;             // 0 .. 22
+    const unsigned long long small = uL << shl;
+    const unsigned long long big = (uL >> shr) | (shr ? (uH << ((64 - shr) & 63)) : 0ull);
+    unsigned long long mant = p > 52 ? big : small;
+    const unsigned long long rb = shr ? (uL >> ((shr - 1) & 63)) & 1ull : 0ull;
+    const bool sticky = shr > 1 ? (uL & ((1ull << ((shr - 1) & 63)) - 1ull)) != 0 : false;
+    mant += (rb && (sticky || (mant & 1ull))) ? 1ull : 0ull;
+    const bool carry = mant == (1ull << 53);
+    mant = carry ? mant >> 1 : mant;
+    p += carry ? 1 : 0;
     const int E = p + s + 1023;
-    if (E <= 0 || E >= 2047) return ldexp(fma((double)hi, 268435456.0, (double)lo), s);
-    return __longlong_as_double((long long)((neg ? 0x8000000000000000ull : 0ull) | ((unsigned long long)E << 52) |
-                                            (mant & 0x000fffffffffffffull)));
+    double r = __longlong_as_double((long long)((sgn & 0x8000000000000000ull) | ((unsigned long long)(E & 2047) << 52) |
+                                                (mant & 0x000fffffffffffffull)));
+    if (zero) r = 0.0;
+    if (!zero && (E <= 0 || E >= 2047)) r = ldexp(fma((double)hi, 268435456.0, (double)lo), s);
+    return r;
 }
+
+// Persistent: one CTA per SM walks the tiles (column tiles fastest, so that
+// CTAs sharing a row block of X digits run together).  Warp 0 streams the
+// digit tiles of consecutive tiles through the rings; warp 1 issues the MMAs
+// of a tile as soon as the epilogue has taken the previous tile's group sums
+// out of TMEM (tfree); warps 2-17 drain TMEM into registers, release it, and
+// convert and store while the next tile's MMAs run.
+// 18 warps: two of the four schedulers hold 5 warps, and a scheduler's
+// register file (16 K registers) then allows 96 registers per thread.
+constexpr int OT_EPI_WARPS = 16;
 
 __global__ void __launch_bounds__(OT_THREADS, 1)
     k_ot_update(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int64_t m,
                 int64_t N, int64_t K, const int32_t* __restrict__ Ex, const int32_t* __restrict__ Ey,
-                const double* Cin, int64_t ldi, double* Cout, int64_t ldo, int32_t* __restrict__ err) {
+                const double* Cin, int64_t ldi, double* Cout, int64_t ldo, int32_t* __restrict__ err, int ntj,
+                int ntiles) {
     extern __shared__ unsigned char ot_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)ot_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sY = base;                                // 2 stages x 8 digit tiles
@@ -227,18 +235,16 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
     uint64_t* yempty = yfull + 2;
     uint64_t* xfull = yempty + 2;
     uint64_t* xempty = xfull + OT_XST;
-    uint64_t* accb = xempty + OT_XST;
-    uint32_t* tslot = (uint32_t*)(accb + 1);
+    uint64_t* accf = xempty + OT_XST;  // MMA -> epilogue: a tile's group sums are complete
+    uint64_t* tfree = accf + 1;        // epilogue -> MMA: TMEM has been read
+    uint64_t* mdone = tfree + 1;       // every MMA of the CTA has completed
+    uint32_t* tslot = (uint32_t*)(mdone + 1);
     volatile int* bad = (volatile int*)(tslot + 1);
     int* cnt = (int*)(tslot + 2);  // issued / consumed: x, x, y, y
-    int32_t* eys = (int32_t*)(tslot + 8);  // column exponents of the tile
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // column tiles fastest: the CTAs that share a row block of X digits run
-    // together and read them from L2
-    const int64_t i0 = (int64_t)blockIdx.y * OT_BM;
-    const int64_t j0 = (int64_t)blockIdx.x * OT_BN;
     const int nslab = (int)((K + OT_BK - 1) / OT_BK);
+    const int ntl = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2; ++s) {
@@ -249,7 +255,9 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
             mbar_init(&xfull[s], 1);
             mbar_init(&xempty[s], 1);
         }
-        mbar_init(accb, 1);
+        mbar_init(accf, 1);
+        mbar_init(tfree, OT_EPI_WARPS);
+        mbar_init(mdone, 1);
         *bad = 0;
         cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -261,22 +269,35 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
     const uint32_t tmem = *tslot;
 
     if (warp == 0 && lane == 0) {
-        // producer: the 8 Y digit tiles of slab s + 1 go out after X tile 3
-        // of slab s (the MMAs on the rest of slab s cover their latency)
-        auto load_y = [&](int s) -> bool {
-            const int ys = s & 1;
-            if (s >= 2 && !mbar_wait(&yempty[ys], (uint32_t)(((s >> 1) - 1) & 1))) return false;
+        // producer: per slab the 8 Y digit tiles (the next slab's go out after
+        // X tile 3 of the current one), then the 8 X digit tiles
+        const int total = ntl * nslab;  // slabs over all tiles of this CTA
+        auto slab_tile = [&](int g, int64_t& i0, int64_t& j0, int& s) {
+            const int tl = (int)blockIdx.x + (g / nslab) * (int)gridDim.x;
+            s = g % nslab;
+            i0 = (int64_t)(tl / ntj) * OT_BM;
+            j0 = (int64_t)(tl % ntj) * OT_BN;
+        };
+        auto load_y = [&](int g) -> bool {
+            int64_t i0, j0;
+            int s;
+            slab_tile(g, i0, j0, s);
+            const int ys = g & 1;
+            if (g >= 2 && !mbar_wait(&yempty[ys], (uint32_t)(((g >> 1) - 1) & 1))) return false;
             mbar_expect_tx(&yfull[ys], OT_DIG * OT_YTILE);
             for (int u = 0; u < OT_DIG; ++u)
                 tma_load_3d(sY + (ys * OT_DIG + u) * OT_YTILE, &tmY, &yfull[ys], s * OT_BK, (int)j0, u);
-            cnt[2] = s + 1;
+            cnt[2] = g + 1;
             return true;
         };
         int xq = 0;
-        if (nslab > 0 && !load_y(0)) *bad = 1;
-        for (int s = 0; s < nslab && !*bad; ++s) {
+        if (total > 0 && !load_y(0)) *bad = 1;
+        for (int g = 0; g < total && !*bad; ++g) {
+            int64_t i0, j0;
+            int s;
+            slab_tile(g, i0, j0, s);
             for (int t = 0; t < OT_DIG; ++t, ++xq) {
-                if (t == 4 && s + 1 < nslab && !load_y(s + 1)) {
+                if (t == 4 && g + 1 < total && !load_y(g + 1)) {
                     *bad = 1;
                     break;
                 }
@@ -291,117 +312,107 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
             }
         }
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer: pair (t, u) with t + u <= 7 into accumulator t + u
+        // MMA issuer: pair (t, u) with t + u <= 7 into accumulator t + u; the
+        // 4 K steps of one pair go back to back into the same accumulator
+        // (measured: interleaving accumulators, even with operand A kept in
+        // the collector buffer, is 40 % - 3x slower)
         const uint32_t idesc = umma_idesc(1u, OT_BM, OT_BN);
-        int xq = 0;
-        for (int s = 0; s < nslab && !*bad; ++s) {
-            const int ys = s & 1;
-            if (!mbar_wait(&yfull[ys], (uint32_t)((s >> 1) & 1))) {
+        int xq = 0, g = 0;
+        for (int i = 0; i < ntl && !*bad; ++i) {
+            if (i > 0 && !mbar_wait(tfree, (uint32_t)((i - 1) & 1))) {
                 *bad = 1;
                 break;
             }
-            cnt[3] = s + 1;
-            for (int t = 0; t < OT_DIG; ++t, ++xq) {
-                const int xs = xq % OT_XST;
-                if (!mbar_wait(&xfull[xs], (uint32_t)((xq / OT_XST) & 1))) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int s = 0; s < nslab && !*bad; ++s, ++g) {
+                const int ys = g & 1;
+                if (!mbar_wait(&yfull[ys], (uint32_t)((g >> 1) & 1))) {
                     *bad = 1;
                     break;
                 }
-                cnt[1] = xq + 1;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint64_t ad = umma_desc(smem_u32(sX + xs * OT_XTILE));
-                // the 4 K steps of one digit pair go back to back into the
-                // same accumulator (measured: interleaving accumulators, even
-                // with operand A kept in the collector, is 3x slower)
-                for (int u = 0; u + t < OT_DIG; ++u) {
-                    const uint64_t bd = umma_desc(smem_u32(sY + (ys * OT_DIG + u) * OT_YTILE));
-                    const uint32_t acc = tmem + (uint32_t)((t + u) * OT_BN);
+                cnt[3] = g + 1;
+                for (int t = 0; t < OT_DIG; ++t, ++xq) {
+                    const int xs = xq % OT_XST;
+                    if (!mbar_wait(&xfull[xs], (uint32_t)((xq / OT_XST) & 1))) {
+                        *bad = 1;
+                        break;
+                    }
+                    cnt[1] = xq + 1;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint64_t ad = umma_desc(smem_u32(sX + xs * OT_XTILE));
+                    for (int u = 0; u + t < OT_DIG; ++u) {
+                        const uint64_t bd = umma_desc(smem_u32(sY + (ys * OT_DIG + u) * OT_YTILE));
+                        const uint32_t acc = tmem + (uint32_t)((t + u) * OT_BN);
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)  // 4 x 16 BF16 of K per stage
-                        umma_f16(acc, ad + 2 * kk, bd + 2 * kk, idesc, (s | t | kk) != 0 ? 1u : 0u);
+                        for (int kk = 0; kk < 4; ++kk)  // 4 x 16 BF16 of K per stage
+                            umma_f16(acc, ad + 2 * kk, bd + 2 * kk, idesc, (s | t | kk) != 0 ? 1u : 0u);
+                    }
+                    umma_commit(&xempty[xs]);
                 }
-                umma_commit(&xempty[xs]);
+                umma_commit(&yempty[ys]);
             }
-            umma_commit(&yempty[ys]);
+            umma_commit(accf);  // fires when this tile's MMAs have completed
         }
-        umma_commit(accb);  // fires when every MMA issued above has completed
     } else if (warp >= 2) {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and
-        // one half of the 64 columns.  While the MMAs run it prefetches its
-        // C_in entries into registers and the column exponents into shared
-        // memory, so that no load latency is left for after the MMAs.
-        const int quad = warp & 3, half = (warp - 2) >> 2;
-        const int64_t row = i0 + quad * 32 + lane;
-        const int32_t ex = row < m ? Ex[row] : 0;
-        if (row < m) {
-            for (int j = 0; j < 32; ++j) {
-                const int64_t col = j0 + half * 32 + j;
-                if (col < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(Cin + row + col * ldi));
+        // epilogue warp e = warp - 2: TMEM lane quadrant warp % 4 (its rows),
+        // columns [16 (e / 4), +16) of the tile
+        const int quad = warp & 3, cq = (warp - 2) >> 2;
+        const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cq * 16);
+        for (int i = 0; i < ntl; ++i) {
+            const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+            const int64_t i0 = (int64_t)(tile / ntj) * OT_BM, j0 = (int64_t)(tile % ntj) * OT_BN;
+            const int64_t row = i0 + quad * 32 + lane;
+            const int64_t c0 = j0 + cq * 16;
+            if (row < m) {  // this tile's C_in entries into L2 while its MMAs run
+                for (int j = 0; j < 16; ++j)
+                    if (c0 + j < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(Cin + row + (c0 + j) * ldi));
             }
-        }
-        if (threadIdx.x - 64 < OT_BN) {
-            const int64_t col = j0 + (threadIdx.x - 64);
-            eys[threadIdx.x - 64] = col < N ? Ey[col] : 0;
-        }
-        asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 epilogue warps
-        bool ok = mbar_wait(accb, 0);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!ok) *bad = 1;
-        const bool go = __all_sync(0xffffffffu, ok && !*bad && nslab > 0);
-        if (go) {
-            const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
-#pragma unroll 1
-            for (int cc = 0; cc < 2; ++cc) {
-                const int c = half * 32 + cc * 16;
-                double cin[16];
+            const bool ok = mbar_wait(accf, (uint32_t)(i & 1));
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!ok) *bad = 1;
+            if (!__all_sync(0xffffffffu, ok && !*bad)) break;
+            long long hi[16], lo[16];
+#pragma unroll
+            for (int d = 0; d < OT_DIG; d += 2) {
+                uint32_t va[16], vb[16];
+                tmem_ld16_nowait(tl + (uint32_t)(d * OT_BN), va);
+                tmem_ld16_nowait(tl + (uint32_t)((d + 1) * OT_BN), vb);
+                tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int64_t col = j0 + c + j;
-                    cin[j] = (row < m && col < N) ? Cin[row + col * ldi] : 0.0;
+                    const long long a = (long long)__float2int_rn(__uint_as_float(va[j]));
+                    const long long b = (long long)__float2int_rn(__uint_as_float(vb[j]));
+                    if (d == 0) hi[j] = a * 128 + b;
+                    else if (d == 2) hi[j] = (hi[j] * 128 + a) * 128 + b;
+                    else if (d == 4) lo[j] = a * 128 + b;
+                    else lo[j] = (lo[j] * 128 + a) * 128 + b;
                 }
-                long long hi[16], lo[16];
-                {
-                    uint32_t v0[16], v1[16], v2[16], v3[16];
-                    tmem_ld16_nowait(tl + (uint32_t)(0 * OT_BN + c), v0);
-                    tmem_ld16_nowait(tl + (uint32_t)(1 * OT_BN + c), v1);
-                    tmem_ld16_nowait(tl + (uint32_t)(2 * OT_BN + c), v2);
-                    tmem_ld16_nowait(tl + (uint32_t)(3 * OT_BN + c), v3);
-                    tmem_wait_ld();
+            }
+            // this tile's TMEM is read: the next tile's MMAs may start
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tfree);
+            if (row < m) {
+                const int32_t ex = Ex[row];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        long long h = (long long)__float2int_rn(__uint_as_float(v0[j]));
-                        h = h * 128 + (long long)__float2int_rn(__uint_as_float(v1[j]));
-                        h = h * 128 + (long long)__float2int_rn(__uint_as_float(v2[j]));
-                        hi[j] = h * 128 + (long long)__float2int_rn(__uint_as_float(v3[j]));
+                for (int h = 0; h < 2; ++h) {
+                    double cin[8];
+                    int32_t ey[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int64_t col = c0 + 8 * h + j;
+                        cin[j] = col < N ? Cin[row + col * ldi] : 0.0;
+                        ey[j] = col < N ? Ey[col] : 0;
                     }
-                }
-                {
-                    uint32_t v0[16], v1[16], v2[16], v3[16];
-                    tmem_ld16_nowait(tl + (uint32_t)(4 * OT_BN + c), v0);
-                    tmem_ld16_nowait(tl + (uint32_t)(5 * OT_BN + c), v1);
-                    tmem_ld16_nowait(tl + (uint32_t)(6 * OT_BN + c), v2);
-                    tmem_ld16_nowait(tl + (uint32_t)(7 * OT_BN + c), v3);
-                    tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        long long l = (long long)__float2int_rn(__uint_as_float(v0[j]));
-                        l = l * 128 + (long long)__float2int_rn(__uint_as_float(v1[j]));
-                        l = l * 128 + (long long)__float2int_rn(__uint_as_float(v2[j]));
-                        lo[j] = l * 128 + (long long)__float2int_rn(__uint_as_float(v3[j]));
-                    }
-                }
-                if (row < m) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int64_t col = j0 + c + j;
+                    for (int j = 0; j < 8; ++j) {
+                        const int64_t col = c0 + 8 * h + j;
                         if (col < N) {
-                            const int32_t ey = eys[c + j];
                             double val;
-                            if (ex == OT_NONFINITE || ey == OT_NONFINITE) {
+                            if (ex == OT_NONFINITE || ey[j] == OT_NONFINITE)
                                 val = __longlong_as_double(0x7ff8000000000000ll);
-                            } else {
-                                val = ot_fixed_to_double(hi[j], lo[j], ex + ey - 61);
-                            }
+                            else
+                                val = ot_fixed_to_double(hi[8 * h + j], lo[8 * h + j], ex + ey[j] - 61);
                             Cout[row + col * ldo] = cin[j] - val;
                         }
                     }
@@ -409,14 +420,15 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
             }
         }
     }
+    if (warp == 1 && lane == 0) umma_commit(mdone);  // fires when every MMA issued above has completed
     __syncthreads();
     if (*bad) {
         if (threadIdx.x == 0) {
             set_info_once(err, -2);
             // wait (bounded) for copies issued but never consumed, then the MMAs
             for (int q = cnt[1]; q < cnt[0]; ++q) mbar_wait(&xfull[q % OT_XST], (uint32_t)((q / OT_XST) & 1));
-            for (int s = cnt[3]; s < cnt[2]; ++s) mbar_wait(&yfull[s & 1], (uint32_t)((s >> 1) & 1));
-            mbar_wait(accb, 0);
+            for (int g = cnt[3]; g < cnt[2]; ++g) mbar_wait(&yfull[g & 1], (uint32_t)((g >> 1) & 1));
+            mbar_wait(mdone, 0);
         }
         __syncthreads();
     }
@@ -511,9 +523,10 @@ lsq_status ot_gemm_update(const double* X, int64_t ldx, const double* Y, int64_t
     if (!ot_map(&tx, Zx, Kp, mp, OT_BM) || !ot_map(&ty, Zy, Kp, Np, OT_BN)) return LSQ_ERR_CUDA;
     const size_t smem = ot_update_smem();
     LSQ_CUDA_TRY(cudaFuncSetAttribute(k_ot_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)(Np / OT_BN), (unsigned)(mp / OT_BM));
+    const int ntj = (int)(Np / OT_BN), ntiles = (int)(ntj * (mp / OT_BM));
+    const int grid = std::min(ntiles, device_sm_count());
     stage_mark(ST_K_UPDATE, true, st);
-    k_ot_update<<<grid, OT_THREADS, smem, st>>>(tx, ty, M, N, Kp, Ex, Ey, Cin, ldi, Cout, ldo, err);
+    k_ot_update<<<grid, OT_THREADS, smem, st>>>(tx, ty, M, N, Kp, Ex, Ey, Cin, ldi, Cout, ldo, err, ntj, ntiles);
     LSQ_LAUNCH_CHECK();
     stage_mark(ST_K_UPDATE, false, st, 36.0 * 2.0 * (double)M * (double)N * (double)K);
     return LSQ_OK;

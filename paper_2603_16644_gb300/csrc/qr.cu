@@ -12,6 +12,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <mutex>
 
 namespace lsq {
 
@@ -394,8 +395,11 @@ __global__ void k_check_diag(const double* __restrict__ Rs, int64_t n, int64_t l
     if (!(d > 0.0) || !isfinite(d)) set_info_once(info, (int32_t)(j + 1));
 }
 
+// V and T are double-buffered by panel parity; the trailing update of a panel
+// has its own scratch for the narrow part (the next panel's columns) and the
+// wide part (the rest), which may run at the same time.
 struct QrLayout {
-    size_t w, beta, tm, v, wp, w2, gemm;
+    size_t w, beta, tm[2], v[2], wp[2], w2[2], gemm[2];
     size_t total;
 };
 
@@ -405,14 +409,54 @@ static QrLayout qr_layout(int64_t s, int64_t n, int es, int num_sms) {
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
     L.w = take((size_t)s * n * es);
     L.beta = take((size_t)n * es);
-    L.tm = take((size_t)QNB * QNB * es);
-    L.v = take((size_t)s * QNB * es);
-    L.wp = take((size_t)QNB * n * es);
-    L.w2 = take((size_t)QNB * n * es);
+    for (int b = 0; b < 2; ++b) {
+        L.tm[b] = take((size_t)QNB * QNB * es);
+        L.v[b] = take((size_t)s * QNB * es);
+        L.wp[b] = take((size_t)QNB * n * es);
+        L.w2[b] = take((size_t)QNB * n * es);
+        L.gemm[b] = take((size_t)64 * QNB * n * es + 256);  // at most 64 split partials of nb x nt
+    }
     (void)num_sms;
-    L.gemm = take((size_t)64 * QNB * n * es + 256);  // at most 64 split partials of nb x nt
     L.total = off;
     return L;
+}
+
+// C (rows x nt, ld s) <- (I - V T^T V^T) C, as W = V^T C, W2 = T^T W, C -= V W2.
+template <typename T>
+static lsq_status qr_apply(const T* V, const T* Tm, int nb, int64_t rows, T* C, int64_t s, int64_t nt, T* Wp, T* W2,
+                           void* gws, int sms, cudaStream_t st) {
+    if (nt <= 0) return LSQ_OK;
+    const int accp = sizeof(T) == 8 ? LSQ_FP64 : LSQ_FP32;
+    GemmPlan gp = plan_gemm_kmajor(nb, nt, rows, false, accp, sms);
+    lsq_status r = launch_gemm_kmajor(gp, V, accp, rows, C, accp, s, Wp, nb, gws, st);
+    if (r != LSQ_OK) return r;
+    k_qr_tw<T><<<(unsigned)ceil_div(nb * nt, 256), 256, 0, st>>>(Tm, Wp, nb, nt, W2);
+    LSQ_LAUNCH_CHECK();
+    // C -= V W2:  P(i,p) = V[i + p rows],  Q(c,p) = W2[p + c nb]
+    return rank_update_ext<T>(C, s, V, 1, rows, W2, nb, 1, rows, nt, nb, false, nullptr, st);
+}
+
+// Internal streams for the look-ahead QR (one pair per device): panels on a
+// high-priority stream, the wide trailing updates on a low-priority one.
+struct QrStreams {
+    cudaStream_t hi = nullptr, lo = nullptr;
+    bool ok = false;
+};
+static std::mutex g_qr_mu;
+
+static QrStreams* qr_streams() {
+    static QrStreams per_dev[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    QrStreams& q = per_dev[dev];
+    if (!q.ok) {
+        int lo_p = 0, hi_p = 0;
+        if (cudaDeviceGetStreamPriorityRange(&lo_p, &hi_p) != cudaSuccess) return nullptr;
+        if (cudaStreamCreateWithPriority(&q.hi, cudaStreamNonBlocking, hi_p) != cudaSuccess) return nullptr;
+        if (cudaStreamCreateWithPriority(&q.lo, cudaStreamNonBlocking, lo_p) != cudaSuccess) return nullptr;
+        q.ok = true;
+    }
+    return &q;
 }
 
 size_t qr_ws_bytes(int64_t s, int64_t n, int prec) {
@@ -430,48 +474,108 @@ static lsq_status qr_run(const void* As, int64_t s, int64_t n, int64_t ldas, int
     if (!ws || L.total + ((char*)base - (char*)ws) > ws_bytes) return LSQ_ERR_NOMEM;
     T* W = (T*)(base + L.w);
     T* beta = (T*)(base + L.beta);
-    T* Tm = (T*)(base + L.tm);
-    T* V = (T*)(base + L.v);
-    T* Wp = (T*)(base + L.wp);
-    T* W2 = (T*)(base + L.w2);
-    void* gws = base + L.gemm;
     unsigned g = (unsigned)std::min<int64_t>(ceil_div(s * n, 256), 8192);
     if (as_prec == LSQ_FP64)
         k_qr_load<double, T><<<g, 256, 0, st>>>((const double*)As, s, n, ldas, W);
     else
         k_qr_load<float, T><<<g, 256, 0, st>>>((const float*)As, s, n, ldas, W);
     LSQ_LAUNCH_CHECK();
-    int accp = sizeof(T) == 8 ? LSQ_FP64 : LSQ_FP32;
-    for (int64_t k0 = 0; k0 < n; k0 += QNB) {
+    // look-ahead: while panel k + 1 is factored (high-priority stream), the
+    // wide part of panel k's trailing update runs on the low-priority stream;
+    // the narrow part (the next panel's columns) goes first on the panel
+    // stream.  Not while the caller's stream is being captured into a graph
+    // (the batched solver), where concurrent problems must not share streams.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    LSQ_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+    QrStreams* qs = (cap == cudaStreamCaptureStatusNone && n > 2 * QNB) ? qr_streams() : nullptr;
+    std::unique_lock<std::mutex> lk(g_qr_mu, std::defer_lock);
+    cudaEvent_t ev_fork = nullptr, ev_p = nullptr, ev_w[2] = {nullptr, nullptr}, ev_join = nullptr;
+    auto cleanup = [&]() {
+        for (cudaEvent_t e : {ev_fork, ev_p, ev_w[0], ev_w[1], ev_join})
+            if (e) cudaEventDestroy(e);
+    };
+    cudaStream_t sh = st, sl = st;
+    if (qs) {
+        lk.lock();
+        bool good = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&ev_p, cudaEventDisableTiming) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&ev_w[0], cudaEventDisableTiming) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&ev_w[1], cudaEventDisableTiming) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) == cudaSuccess &&
+                    cudaEventRecord(ev_fork, st) == cudaSuccess && cudaStreamWaitEvent(qs->hi, ev_fork, 0) == cudaSuccess &&
+                    cudaStreamWaitEvent(qs->lo, ev_fork, 0) == cudaSuccess;
+        if (!good) {
+            cleanup();
+            return LSQ_ERR_CUDA;
+        }
+        sh = qs->hi;
+        sl = qs->lo;
+    }
+    lsq_status r = LSQ_OK;
+    int k = 0;
+    for (int64_t k0 = 0; k0 < n && r == LSQ_OK; k0 += QNB, ++k) {
+        const int b = k & 1;
         int nb = (int)std::min<int64_t>(QNB, n - k0);
         int64_t rows = s - k0;
+        T* Tm = (T*)(base + L.tm[b]);
+        T* V = (T*)(base + L.v[b]);
         size_t clsm = sizeof(T) * (size_t)(ceil_div(rows, QCL) | 1) * QNB;
         // Householder panel: sum over its columns of 4 (rows - j)(nb - j) flops
         double pflops = 0.0;
         for (int j = 0; j < nb; ++j) pflops += 4.0 * (double)(rows - j) * (double)(nb - j);
-        stage_mark(ST_K_QRPANEL, true, st);
+        stage_mark(ST_K_QRPANEL, true, sh);
         if (clsm <= 160 * 1024) {
-            LSQ_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)clsm));
-            k_qr_panel_cl<T><<<QCL, QCT, clsm, st>>>(W, s, s, k0, nb, beta, Tm, V, rows);
+            if (cudaFuncSetAttribute(k_qr_panel_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)clsm) !=
+                cudaSuccess) {
+                r = LSQ_ERR_CUDA;
+                break;
+            }
+            k_qr_panel_cl<T><<<QCL, QCT, clsm, sh>>>(W, s, s, k0, nb, beta, Tm, V, rows);
         } else {
-            k_qr_panel<T><<<1, QPT, 0, st>>>(W, s, s, k0, nb, beta, Tm, V, rows);
+            k_qr_panel<T><<<1, QPT, 0, sh>>>(W, s, s, k0, nb, beta, Tm, V, rows);
         }
-        LSQ_LAUNCH_CHECK();
-        stage_mark(ST_K_QRPANEL, false, st, pflops);
-        int64_t nt = n - k0 - nb;
-        if (nt <= 0) continue;
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) {
+            r = LSQ_ERR_CUDA;
+            break;
+        }
+        stage_mark(ST_K_QRPANEL, false, sh, pflops);
+        const int64_t nt = n - k0 - nb;
+        if (nt <= 0) break;
+        const int64_t nn = std::min<int64_t>(QNB, nt), nw = nt - nn;  // narrow / wide columns
         T* C = W + k0 + (k0 + nb) * s;
-        // Wp = V^T C   (nb x nt; K = rows)
-        GemmPlan gp = plan_gemm_kmajor(nb, nt, rows, false, accp, sms);
-        lsq_status r = launch_gemm_kmajor(gp, V, sizeof(T) == 8 ? LSQ_FP64 : LSQ_FP32, rows, C,
-                                          sizeof(T) == 8 ? LSQ_FP64 : LSQ_FP32, s, Wp, nb, gws, st);
-        if (r != LSQ_OK) return r;
-        k_qr_tw<T><<<(unsigned)ceil_div(nb * nt, 256), 256, 0, st>>>(Tm, Wp, nb, nt, W2);
-        LSQ_LAUNCH_CHECK();
-        // C -= V W2:  P(i,p) = V[i + p rows],  Q(c,p) = W2[p + c nb]
-        r = rank_update_ext<T>(C, s, V, 1, rows, W2, nb, 1, rows, nt, nb, false, nullptr, st);
-        if (r != LSQ_OK) return r;
+        if (qs) {
+            // the wide part on the low-priority stream, after this panel
+            if (cudaEventRecord(ev_p, sh) != cudaSuccess || cudaStreamWaitEvent(sl, ev_p, 0) != cudaSuccess) {
+                r = LSQ_ERR_CUDA;
+                break;
+            }
+            r = qr_apply<T>(V, Tm, nb, rows, C + nn * s, s, nw, (T*)(base + L.wp[1]), (T*)(base + L.w2[1]),
+                            base + L.gemm[1], sms, sl);
+            if (r != LSQ_OK || cudaEventRecord(ev_w[b], sl) != cudaSuccess) {
+                r = r != LSQ_OK ? r : LSQ_ERR_CUDA;
+                break;
+            }
+            // the next panel's columns also hold the previous panel's wide update
+            if (k >= 1 && cudaStreamWaitEvent(sh, ev_w[b ^ 1], 0) != cudaSuccess) {
+                r = LSQ_ERR_CUDA;
+                break;
+            }
+            r = qr_apply<T>(V, Tm, nb, rows, C, s, nn, (T*)(base + L.wp[0]), (T*)(base + L.w2[0]),
+                            base + L.gemm[0], sms, sh);
+        } else {
+            r = qr_apply<T>(V, Tm, nb, rows, C, s, nt, (T*)(base + L.wp[0]), (T*)(base + L.w2[0]),
+                            base + L.gemm[0], sms, st);
+        }
     }
+    if (qs) {
+        // join both internal streams back into the caller's stream
+        bool good = cudaEventRecord(ev_join, sh) == cudaSuccess && cudaStreamWaitEvent(st, ev_join, 0) == cudaSuccess &&
+                    cudaEventRecord(ev_fork, sl) == cudaSuccess && cudaStreamWaitEvent(st, ev_fork, 0) == cudaSuccess;
+        cleanup();
+        if (!good && r == LSQ_OK) r = LSQ_ERR_CUDA;
+    }
+    if (r != LSQ_OK) return r;
     k_qr_extract<T><<<(unsigned)std::min<int64_t>(ceil_div(n * n, 256), 4096), 256, 0, st>>>(W, s, n, colexp, Rs, ldr);
     LSQ_LAUNCH_CHECK();
     if (info) {
