@@ -274,6 +274,17 @@ size_t lsq_gram_tc_workspace_size(int64_t m, int64_t n);
 lsq_status lsq_gram_tc(const double* X, int64_t m, int64_t n, int64_t ld, double* G, int64_t ldg, int32_t* info,
                        void* ws, size_t ws_bytes, void* stream);
 
+/* G = X^T Y (n x n, FP64 accuracy) for two m x n column-major FP64 matrices,
+ * by the same FP8 digit slicing as lsq_gram_tc with one exponent per column
+ * of X and of Y; the HPNE matrix A_p^T A (Eq. e_hpne).  All 105 digit-pair
+ * blocks are formed (no symmetry).  Per entry the error is below ~2^-55 m
+ * max|x_p| max|y_q|.  Workspace lsq_gemm_tn_tc_workspace_size(m, n) (about
+ * 28 m n bytes of digits plus 64 KiB per digit tile).  info (device, may be
+ * NULL): -2 on a pipeline timeout. */
+size_t lsq_gemm_tn_tc_workspace_size(int64_t m, int64_t n);
+lsq_status lsq_gemm_tn_tc(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t n,
+                          double* G, int64_t ldg, int32_t* info, void* ws, size_t ws_bytes, void* stream);
+
 /* A_p = A R^{-1} (Alg. 1, the preconditioned matrix formed by substitution)
  * in FP64 with the off-diagonal products on the tensor cores.  The columns
  * are split recursively; diagonal blocks of up to 32 columns are solved by
@@ -296,7 +307,8 @@ lsq_status lsq_trsm_tc(const double* A, int64_t m, int64_t n, int64_t lda, const
                        int64_t ldap, int32_t* info, void* ws, size_t ws_bytes, void* stream);
 
 /* Use the tensor-core FP64 products (lsq_gram_tc for the symmetric Gram of
- * PNE and lsq_trsm_tc for A_p in PNE and HPNE) inside the solves (1, the
+ * PNE, lsq_gemm_tn_tc for A_p^T A of HPNE, lsq_trsm_tc for A_p and the
+ * Cholesky updates) inside the solves (1, the
  * default) or the FP64 CUDA-core kernels (0); returns the previous setting.
  * Process-wide; for comparisons. */
 int32_t lsq_set_fp64_emulation(int32_t enable);

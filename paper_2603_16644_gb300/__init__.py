@@ -19,7 +19,7 @@ import torch
 __all__ = [
     "FP8_E4M3", "BF16", "FP16", "FP32", "FP64", "AUTO", "GAUSSIAN", "SPARSE_SIGN",
     "Opts", "lib", "colmajor", "workspace", "sketch", "precond_qr", "condest", "trsm_gram",
-    "factor_solve", "trsm_tc", "gram_tc", "set_fp64_emulation", "pne", "hpne", "solve", "solve_host", "sparse_sign_operator",
+    "factor_solve", "trsm_tc", "gram_tc", "gemm_tn_tc", "set_fp64_emulation", "pne", "hpne", "solve", "solve_host", "sparse_sign_operator",
     "gaussian_operator", "precision_from_kappa0", "status_string", "LsqError",
 ]
 
@@ -87,6 +87,8 @@ def lib():
             "lsq_gram_tc_workspace_size": (_sz, [_i64, _i64]),
             "lsq_gram_tc": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
             "lsq_set_fp64_emulation": (C.c_int32, [C.c_int32]),
+            "lsq_gemm_tn_tc_workspace_size": (_sz, [_i64, _i64]),
+            "lsq_gemm_tn_tc": (C.c_int32, [_vp, _i64, _vp, _i64, _i64, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -296,6 +298,20 @@ def gram_tc(X):
     ws = torch.empty(int(lib().lsq_gram_tc_workspace_size(m, n)), dtype=torch.uint8, device=X.device)
     _check(lib().lsq_gram_tc(_ptr(X), m, n, _ld(X), _ptr(G), n, _ptr(info), _ptr(ws), ws.numel(), _stream()),
            "lsq_gram_tc")
+    return G, info
+
+
+def gemm_tn_tc(X, Y):
+    """G = X^T Y in FP64 on the FP8 tensor cores (lsq_gemm_tn_tc); returns (G, info)."""
+    _need_cuda(X, Y)
+    m, n = X.shape
+    if Y.shape != (m, n):
+        raise LsqError("X and Y must have the same shape")
+    G = torch.empty((n, n), dtype=torch.float64, device=X.device).t()
+    info = torch.zeros(1, dtype=torch.int32, device=X.device)
+    ws = torch.empty(int(lib().lsq_gemm_tn_tc_workspace_size(m, n)), dtype=torch.uint8, device=X.device)
+    _check(lib().lsq_gemm_tn_tc(_ptr(X), _ld(X), _ptr(Y), _ld(Y), m, n, _ptr(G), n, _ptr(info), _ptr(ws), ws.numel(),
+                                _stream()), "lsq_gemm_tn_tc")
     return G, info
 
 

@@ -168,7 +168,7 @@ SolveLayout solve_layout(int64_t m, int64_t n, const lsq_opts* o, int prec, bool
     L.err = q.take(sizeof(int32_t));
     L.tsync = q.take(sizeof(int32_t) * trsv_sync_ints(n));
     // shared by the tensor-core A_p (first) and the tensor-core Gram of PNE
-    L.oz_bytes = std::max(ot_trsm_ws_bytes(m, n), hpne ? (size_t)0 : oz_gram_ws_bytes(m, n));
+    L.oz_bytes = std::max(ot_trsm_ws_bytes(m, n), hpne ? oz_gemm_tn_ws_bytes(m, n) : oz_gram_ws_bytes(m, n));
     L.oz = q.take(L.oz_bytes);
     L.total = q.off + 256;
     return L;
@@ -241,7 +241,10 @@ lsq_status trsm_gram(const double* A, int64_t m, int64_t n, int64_t lda, const d
     stage_mark(ST_GRAM, true, st);
     GemmPlan gp = plan_gemm_kmajor(n, n, m, !hpne, LSQ_FP64, sms);
     if (hpne) {
-        r = launch_gemm_kmajor(gp, Ap, LSQ_FP64, ldap, A, LSQ_FP64, lda, G, ldg, gemm_ws, st);
+        if (g_fp64_emulation && oz_ws && oz_bytes >= oz_gemm_tn_ws_bytes(m, n))
+            r = oz_gemm_tn(Ap, ldap, A, lda, m, n, G, ldg, oz_ws, oz_bytes, err, st);
+        else
+            r = launch_gemm_kmajor(gp, Ap, LSQ_FP64, ldap, A, LSQ_FP64, lda, G, ldg, gemm_ws, st);
     } else if (g_fp64_emulation && oz_ws && oz_bytes >= oz_gram_ws_bytes(m, n)) {
         r = oz_gram(Ap, m, n, ldap, G, ldg, oz_ws, oz_bytes, err, st);
     } else {
@@ -422,6 +425,17 @@ lsq_status lsq_trsm_tc(const double* A, int64_t m, int64_t n, int64_t lda, const
     return ot_trsm(A, m, n, lda, R, ldr, Ap, ldap, ws, ws_bytes, info, S(stream));
 }
 
+size_t lsq_gemm_tn_tc_workspace_size(int64_t m, int64_t n) {
+    return m > 0 && n > 0 ? oz_gemm_tn_ws_bytes(m, n) + 256 : 0;
+}
+
+lsq_status lsq_gemm_tn_tc(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t n,
+                          double* G, int64_t ldg, int32_t* info, void* ws, size_t ws_bytes, void* stream) {
+    if (!X || !Y || !G || m <= 0 || n <= 0 || ldx < m || ldy < m || ldg < n) return LSQ_ERR_ARG;
+    if (info) LSQ_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), S(stream)));
+    return oz_gemm_tn(X, ldx, Y, ldy, m, n, G, ldg, ws, ws_bytes, info, S(stream));
+}
+
 size_t lsq_gram_tc_workspace_size(int64_t m, int64_t n) { return m > 0 && n > 0 ? oz_gram_ws_bytes(m, n) + 256 : 0; }
 
 lsq_status lsq_gram_tc(const double* X, int64_t m, int64_t n, int64_t ld, double* G, int64_t ldg, int32_t* info,
@@ -536,7 +550,7 @@ size_t lsq_workspace_size(int32_t op, int64_t m, int64_t n, const lsq_opts* o) {
         GemmPlan gp = plan_gemm_kmajor(n, n, m, false, LSQ_FP64, sms);
         GemmPlan gs = plan_gemm_kmajor(n, n, m, true, LSQ_FP64, sms);
         return std::max(gemm_kmajor_ws_bytes(gp), gemm_kmajor_ws_bytes(gs)) + gemv_t_ws_bytes(m, n) +
-               std::max(oz_gram_ws_bytes(m, n), ot_trsm_ws_bytes(m, n)) + 2048;
+               std::max(std::max(oz_gram_ws_bytes(m, n), oz_gemm_tn_ws_bytes(m, n)), ot_trsm_ws_bytes(m, n)) + 2048;
     }
     case LSQ_OP_FACTOR_SOLVE:
         return align_up(sizeof(int32_t) * trsv_sync_ints(n), 256) + cholesky_ws_bytes(n) + 512;

@@ -100,6 +100,10 @@ lsq_status launch_sketch_tc(const void* Om, int64_t ldo, const void* Ahat, int64
 size_t oz_gram_ws_bytes(int64_t m, int64_t n);
 lsq_status oz_gram(const double* X, int64_t m, int64_t n, int64_t ld, double* G, int64_t ldg, void* ws,
                    size_t ws_bytes, int32_t* err, cudaStream_t st);
+// G = X^T Y (both m x n column-major), FP64 accuracy, non-symmetric.
+size_t oz_gemm_tn_ws_bytes(int64_t m, int64_t n);
+lsq_status oz_gemm_tn(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t n, double* G,
+                      int64_t ldg, void* ws, size_t ws_bytes, int32_t* err, cudaStream_t st);
 
 // ---- oz_trsm.cu: FP64 Ap = A R^{-1} with tensor-core updates -------------
 bool ot_trsm_supported();
@@ -111,7 +115,8 @@ lsq_status ot_trsm(const double* A, int64_t m, int64_t n, int64_t lda, const dou
 size_t ot_update_ws_bytes(int64_t M, int64_t N, int64_t K);
 lsq_status ot_gemm_update(const double* X, int64_t ldx, const double* Y, int64_t sk, int64_t sj, const double* Cin,
                           int64_t ldi, double* Cout, int64_t ldo, int64_t M, int64_t N, int64_t K, void* ws,
-                          size_t ws_bytes, int32_t* err, cudaStream_t st);
+                          size_t ws_bytes, int32_t* err, cudaStream_t st, int xmode = 0,
+                          const int32_t* Eblk = nullptr, int64_t b0 = 0, int nbk = 0);
 
 // ---- qr.cu -------------------------------------------------------------------
 size_t qr_ws_bytes(int64_t s, int64_t n, int prec);

@@ -47,8 +47,11 @@ constexpr int32_t OT_NONFINITE = 0x7fffffff;
 // ---------------------------------------------------------------------------
 // Digit slicing (integer operations on the FP64 bit pattern)
 // ---------------------------------------------------------------------------
+// mx: the largest |x| bit pattern of a row or column.  The exponent field is
+// masked: a NaN produced by arithmetic may keep its sign bit even after the
+// magnitude mask (the compiler may fold the mask into an FP absolute value).
 __device__ __forceinline__ int32_t ot_exp_of_max(unsigned long long mx) {
-    int Eb = (int)(mx >> 52);
+    int Eb = (int)((mx >> 52) & 0x7ff);
     if (Eb == 0x7ff) return OT_NONFINITE;
     if (mx == 0) return 0;
     return (Eb > 1 ? Eb : 1) - 1022;  // every |x| < 2^E
@@ -61,9 +64,14 @@ __device__ __forceinline__ void ot_digits(double x, int32_t E, int (&d)[OT_DIG])
     const int Eb = (int)((b >> 52) & 0x7ff);
     unsigned long long sig = b & 0x000fffffffffffffull;
     if (Eb != 0) sig |= 0x0010000000000000ull;
-    const int sh = (Eb != 0 ? Eb : 1) - (E + 1022) + 2;  // <= 2, so V < 2^55
     unsigned long long V = 0;
-    if (E != OT_NONFINITE && Eb != 0x7ff) V = sh >= 0 ? (sig << sh) : (sh > -64 ? (sig >> (-sh)) : 0ull);
+    if (E != OT_NONFINITE && Eb != 0x7ff) {
+        // only for a finite row exponent: E + 1022 must not be formed from the
+        // non-finite marker (signed overflow would let the compiler assume
+        // that E is never the marker)
+        const int sh = (Eb != 0 ? Eb : 1) - (E + 1022) + 2;  // <= 2, so V < 2^55
+        V = sh >= 0 ? (sig << sh) : (sh > -64 ? (sig >> (-sh)) : 0ull);
+    }
     // adding 64 to every lower digit field turns the base-128 digits into
     // balanced ones: field - 64 in [-64, 63], the carry lands in the top digit
     constexpr unsigned long long BIAS = 64ull * ((1ull << 42) + (1ull << 35) + (1ull << 28) + (1ull << 21) +
@@ -118,6 +126,50 @@ __global__ void __launch_bounds__(128) k_ot_rowslice(const double* __restrict__ 
             double x = k < Kr ? row[k * ld] : 0.0;
             int d[OT_DIG];
             ot_digits(x, E, d);
+#pragma unroll
+            for (int t = 0; t < OT_DIG; ++t) {
+                uint32_t h = bf16_bits_of_int(d[t]);
+                if (q & 1) pk[t][q >> 1] |= h << 16;
+                else pk[t][q >> 1] = h;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < OT_DIG; ++t) {
+            uint4* dst = (uint4*)(Z + ((int64_t)t * mp + i) * Kp + k0);
+            dst[0] = make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
+            dst[1] = make_uint4(pk[t][4], pk[t][5], pk[t][6], pk[t][7]);
+        }
+    }
+}
+
+// The same with the row exponents from the per-block exponents (Eblk[b m +
+// i] for blocks b0 .. b0+nbk-1, INT32_MIN for an all-zero block): a 2-D grid,
+// one thread per row and 64-wide range of K (blockIdx.y), so that many more
+// loads are in flight than with one thread per row.
+__global__ void __launch_bounds__(128) k_ot_rowslice_e(const double* __restrict__ X, int64_t m, int64_t mp,
+                                                       int64_t K, int64_t ld, int64_t Kp, int32_t* __restrict__ Ex,
+                                                       uint16_t* __restrict__ Z, const int32_t* __restrict__ Eblk,
+                                                       int64_t b0, int nbk) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= mp) return;
+    int32_t eb = INT32_MIN;
+    if (i < m)
+        for (int b = 0; b < nbk; ++b) eb = max(eb, Eblk[(b0 + b) * m + i]);
+    const int32_t E = eb == INT32_MIN ? 0 : eb;
+    const int64_t kb = (int64_t)blockIdx.y * 64;
+    if (blockIdx.y == 0) Ex[i] = E;
+    const double* row = X + i;
+    const int64_t Kr = i < m ? K : 0;
+#pragma unroll 1
+    for (int64_t k0 = kb; k0 < kb + 64; k0 += 16) {
+        double xv[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) xv[q] = k0 + q < Kr ? row[(k0 + q) * ld] : 0.0;
+        uint32_t pk[OT_DIG][8];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            int d[OT_DIG];
+            ot_digits(xv[q], E, d);
 #pragma unroll
             for (int t = 0; t < OT_DIG; ++t) {
                 uint32_t h = bf16_bits_of_int(d[t]);
@@ -445,9 +497,13 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
 // by substitution, one thread per row.  Each x_j is scaled by the reciprocal
 // of R[j, j] (one rounding more than a division).
 // ---------------------------------------------------------------------------
+// Also records, per row, the exponent of the largest |x| of the block
+// (Eblk[blk m + i], INT32_MIN if the block row is zero), from which the
+// updates take the row exponents of their X operand without a pass over it.
 template <int NB>
 __global__ void __launch_bounds__(128) k_ot_diag(const double* src, int64_t lds, const double* __restrict__ R,
-                                                 int64_t ldr, int nc, int64_t m, double* Ap, int64_t ldap) {
+                                                 int64_t ldr, int nc, int64_t m, double* Ap, int64_t ldap,
+                                                 int32_t* __restrict__ Eblk, int64_t blk) {
     __shared__ double Rb[NB][NB];
     __shared__ double rinv[NB];
     for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) {
@@ -472,6 +528,16 @@ __global__ void __launch_bounds__(128) k_ot_diag(const double* src, int64_t lds,
 #pragma unroll
     for (int j = 0; j < NB; ++j)
         if (j < nc) Ap[i + (int64_t)j * ldap] = x[j];
+    // the row maximum from the values just stored (this thread's own writes),
+    // so that the substitution keeps its register footprint
+    unsigned long long mx = 0;
+    for (int j = 0; j < nc; ++j) {
+        const unsigned long long a =
+            (unsigned long long)__double_as_longlong(*(volatile const double*)(Ap + i + (int64_t)j * ldap)) &
+            0x7fffffffffffffffull;
+        mx = a > mx ? a : mx;
+    }
+    Eblk[blk * m + i] = mx == 0 ? INT32_MIN : ot_exp_of_max(mx);
 }
 
 // ---------------------------------------------------------------------------
@@ -498,35 +564,60 @@ size_t ot_update_ws_bytes(int64_t M, int64_t N, int64_t K) {
            align_up(sizeof(uint16_t) * OT_DIG * (size_t)Np * Kp, 256) + align_up(sizeof(int32_t) * Np, 256) + 256;
 }
 
+// Pieces of an update's scratch: X digit planes and row exponents, then the Y
+// digit planes and column exponents.
+struct OtUpd {
+    uint16_t* Zx;
+    int32_t* Ex;
+    uint16_t* Zy;
+    int32_t* Ey;
+    int64_t mp, Np, Kp;
+};
+
+static OtUpd ot_upd_ptrs(void* ws, int64_t M, int64_t N, int64_t K) {
+    OtUpd U;
+    U.mp = ot_pad(M, OT_BM);
+    U.Np = ot_pad(N, OT_BN);
+    U.Kp = ot_kp(K);
+    char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    U.Zx = (uint16_t*)base;
+    base += align_up(sizeof(uint16_t) * OT_DIG * (size_t)U.mp * U.Kp, 256);
+    U.Ex = (int32_t*)base;
+    base += align_up(sizeof(int32_t) * U.mp, 256);
+    U.Zy = (uint16_t*)base;
+    base += align_up(sizeof(uint16_t) * OT_DIG * (size_t)U.Np * U.Kp, 256);
+    U.Ey = (int32_t*)base;
+    return U;
+}
+
 // C_out = C_in - X Y (M x N; X: M x K column-major, ld ldx; Y: entry (k, j)
 // at Y[k sk + j sj]) with FP64 accuracy on the tensor cores; K <= 512.
-// C_in may equal C_out (same ld).
+// C_in may equal C_out (same ld).  xmode: 0 slice X here; 1 slice X with the
+// row exponents from the per-block exponents Eblk (blocks b0 .. b0+nbk-1).
 lsq_status ot_gemm_update(const double* X, int64_t ldx, const double* Y, int64_t sk, int64_t sj, const double* Cin,
                           int64_t ldi, double* Cout, int64_t ldo, int64_t M, int64_t N, int64_t K, void* ws,
-                          size_t ws_bytes, int32_t* err, cudaStream_t st) {
+                          size_t ws_bytes, int32_t* err, cudaStream_t st, int xmode, const int32_t* Eblk, int64_t b0,
+                          int nbk) {
     if (M <= 0 || N <= 0 || K <= 0) return LSQ_OK;
     if (K > OT_KMAX || !ws || ws_bytes < ot_update_ws_bytes(M, N, K)) return LSQ_ERR_ARG;
-    const int64_t mp = ot_pad(M, OT_BM), Np = ot_pad(N, OT_BN), Kp = ot_kp(K);
-    char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-    uint16_t* Zx = (uint16_t*)base;
-    base += align_up(sizeof(uint16_t) * OT_DIG * (size_t)mp * Kp, 256);
-    int32_t* Ex = (int32_t*)base;
-    base += align_up(sizeof(int32_t) * mp, 256);
-    uint16_t* Zy = (uint16_t*)base;
-    base += align_up(sizeof(uint16_t) * OT_DIG * (size_t)Np * Kp, 256);
-    int32_t* Ey = (int32_t*)base;
-    k_ot_rowslice<<<(unsigned)(mp / 128), 128, 0, st>>>(X, M, mp, K, ldx, Kp, Ex, Zx);
+    const OtUpd U = ot_upd_ptrs(ws, M, N, K);
+    if (xmode == 1)
+        k_ot_rowslice_e<<<dim3((unsigned)(U.mp / 128), (unsigned)(U.Kp / 64)), 128, 0, st>>>(
+            X, M, U.mp, K, ldx, U.Kp, U.Ex, U.Zx, Eblk, b0, nbk);
+    else
+        k_ot_rowslice<<<(unsigned)(U.mp / 128), 128, 0, st>>>(X, M, U.mp, K, ldx, U.Kp, U.Ex, U.Zx);
     LSQ_LAUNCH_CHECK();
-    k_ot_colslice<<<(unsigned)Np, 128, 0, st>>>(Y, K, N, Np, sk, sj, Kp, Ey, Zy);
+    k_ot_colslice<<<(unsigned)U.Np, 128, 0, st>>>(Y, K, N, U.Np, sk, sj, U.Kp, U.Ey, U.Zy);
     LSQ_LAUNCH_CHECK();
     CUtensorMap tx, ty;
-    if (!ot_map(&tx, Zx, Kp, mp, OT_BM) || !ot_map(&ty, Zy, Kp, Np, OT_BN)) return LSQ_ERR_CUDA;
+    if (!ot_map(&tx, U.Zx, U.Kp, U.mp, OT_BM) || !ot_map(&ty, U.Zy, U.Kp, U.Np, OT_BN)) return LSQ_ERR_CUDA;
     const size_t smem = ot_update_smem();
     LSQ_CUDA_TRY(cudaFuncSetAttribute(k_ot_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int ntj = (int)(Np / OT_BN), ntiles = (int)(ntj * (mp / OT_BM));
+    const int ntj = (int)(U.Np / OT_BN), ntiles = (int)(ntj * (U.mp / OT_BM));
     const int grid = std::min(ntiles, device_sm_count());
     stage_mark(ST_K_UPDATE, true, st);
-    k_ot_update<<<grid, OT_THREADS, smem, st>>>(tx, ty, M, N, Kp, Ex, Ey, Cin, ldi, Cout, ldo, err, ntj, ntiles);
+    k_ot_update<<<grid, OT_THREADS, smem, st>>>(tx, ty, M, N, U.Kp, U.Ex, U.Ey, Cin, ldi, Cout, ldo, err, ntj,
+                                                ntiles);
     LSQ_LAUNCH_CHECK();
     stage_mark(ST_K_UPDATE, false, st, 36.0 * 2.0 * (double)M * (double)N * (double)K);
     return LSQ_OK;
@@ -540,10 +631,15 @@ static void ot_max_update(int64_t m, int64_t c0, int64_t c1, size_t& need) {
     ot_max_update(m, mid, c1, need);
 }
 
-size_t ot_trsm_ws_bytes(int64_t m, int64_t n) {
+// Update scratch, then the per-block row exponents (m x ceil(n / OT_NB) int32).
+static size_t ot_eblk_offset(int64_t m, int64_t n) {
     size_t need = 256;
     ot_max_update(m, 0, n, need);
-    return need + 256;
+    return align_up(need, 256);
+}
+
+size_t ot_trsm_ws_bytes(int64_t m, int64_t n) {
+    return ot_eblk_offset(m, n) + align_up(sizeof(int32_t) * (size_t)m * ceil_div(n, OT_NB), 256) + 512;
 }
 
 // Digit planes as a 3-D tensor (k, row, digit); Kp and rows are multiples of
@@ -568,6 +664,7 @@ struct OtCtx {
     int64_t ldap;
     void* ws;
     size_t ws_bytes;
+    int32_t* Eblk;
     int32_t* err;
     cudaStream_t st;
 };
@@ -577,7 +674,8 @@ static lsq_status ot_solve(const OtCtx& C, int64_t c0, int64_t c1, const double*
     if (c1 - c0 <= OT_NB) {
         k_ot_diag<OT_NB><<<(unsigned)ceil_div(C.m, 128), 128, 0, C.st>>>(src + c0 * lds, lds, C.R + c0 + c0 * C.ldr,
                                                                          C.ldr, (int)(c1 - c0), C.m,
-                                                                         C.Ap + c0 * C.ldap, C.ldap);
+                                                                         C.Ap + c0 * C.ldap, C.ldap, C.Eblk,
+                                                                         c0 / OT_NB);
         LSQ_LAUNCH_CHECK();
         return LSQ_OK;
     }
@@ -585,7 +683,8 @@ static lsq_status ot_solve(const OtCtx& C, int64_t c0, int64_t c1, const double*
     lsq_status r = ot_solve(C, c0, mid, src, lds);
     if (r != LSQ_OK) return r;
     r = ot_gemm_update(C.Ap + c0 * C.ldap, C.ldap, C.R + c0 + mid * C.ldr, 1, C.ldr, src + mid * lds, lds,
-                       C.Ap + mid * C.ldap, C.ldap, C.m, c1 - mid, mid - c0, C.ws, C.ws_bytes, C.err, C.st);
+                       C.Ap + mid * C.ldap, C.ldap, C.m, c1 - mid, mid - c0, C.ws, C.ws_bytes, C.err, C.st, 1,
+                       C.Eblk, c0 / OT_NB, (int)((mid - c0) / OT_NB));
     if (r != LSQ_OK) return r;
     return ot_solve(C, mid, c1, C.Ap, C.ldap);
 }
@@ -597,7 +696,8 @@ lsq_status ot_trsm(const double* A, int64_t m, int64_t n, int64_t lda, const dou
     if (!A || !R || !Ap || m <= 0 || n <= 0 || lda < m || ldap < m || ldr < n) return LSQ_ERR_ARG;
     if (!ot_trsm_supported()) return LSQ_ERR_ARG;
     if (!ws || ws_bytes < ot_trsm_ws_bytes(m, n)) return LSQ_ERR_NOMEM;
-    OtCtx C{m, R, ldr, Ap, ldap, ws, ws_bytes, err, st};
+    char* base = (char*)ws;
+    OtCtx C{m, R, ldr, Ap, ldap, ws, ws_bytes, (int32_t*)(base + ot_eblk_offset(m, n) + 256), err, st};
     return ot_solve(C, 0, n, A, lda);
 }
 

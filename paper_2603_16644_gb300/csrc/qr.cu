@@ -174,11 +174,13 @@ __global__ void __launch_bounds__(QPT) k_qr_panel(T* __restrict__ W, int64_t ld,
 // (v = [1; x(2:)/v1]).  Slots alternate between two buffers by column parity:
 // a CTA can only write a buffer again after the next barrier, which every CTA
 // reaches after reading it.
-constexpr int QCL = 8;
 constexpr int QCT = 256;
 
-template <typename T>
-__global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(QCT)
+// QCL: CTAs per cluster (16, non-portable, where the device allows it; else
+// 8).  Dynamic shared memory: the local panel (Rp x QNB) and, used by rank 0,
+// the V^T V partials of every rank (QCL x QNB x (QNB + 1)).
+template <typename T, int QCL>
+__global__ void __launch_bounds__(QCT)
     k_qr_panel_cl(T* __restrict__ W, int64_t ld, int64_t s, int64_t k0, int nb, T* __restrict__ beta_out,
                   T* __restrict__ Tm, T* __restrict__ V, int64_t ldv) {
     namespace cg = cooperative_groups;
@@ -189,33 +191,32 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(QCT)
     __shared__ T all_row[2][QNB];        // the diagonal row: x1 at j, a_c[j] at c > j
     __shared__ T part[QCT / 32][QNB];
     __shared__ T wsh[QNB];
-    __shared__ T Ypart[QNB][QNB + 1];
     __shared__ T Ts[QNB][QNB + 1];
     __shared__ T bsh[QNB];
     const int rank = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t rows = s - k0;
-    const int64_t R = (rows + QCL - 1) / QCL;
-    const int64_t Rp = R | 1;
-    const int64_t r0 = rank * R;
-    const int64_t nloc = r0 < rows ? min64(R, rows - r0) : 0;
-    const int64_t chunk = (R + (QCT / 32) - 1) / (QCT / 32);
-    const int64_t g0 = warp * chunk, g1 = min64(nloc, g0 + chunk);  // this warp's rows
-    for (int64_t q = tid; q < R * QNB; q += QCT) {
-        int64_t i = q % R, c = q / R;
-        P[c * Rp + i] = (i < nloc && c < nb) ? W[(k0 + r0 + i) + (k0 + c) * ld] : (T)0;
-    }
+    const int rows = (int)(s - k0);
+    const int R = (rows + QCL - 1) / QCL;
+    const int Rp = R | 1;
+    const int r0 = rank * R;
+    const int nloc = r0 < rows ? min(R, rows - r0) : 0;
+    T* Yall = P + (int64_t)Rp * QNB;  // [QCL][QNB][QNB + 1], rank 0 only
+    const int chunk = (R + (QCT / 32) - 1) / (QCT / 32);
+    const int g0 = warp * chunk, g1 = min(nloc, g0 + chunk);  // this warp's rows
+    for (int c = 0; c < QNB; ++c)
+        for (int i = tid; i < R; i += QCT)
+            P[c * Rp + i] = (i < nloc && c < nb) ? W[(k0 + r0 + i) + (k0 + c) * ld] : (T)0;
     __syncthreads();
     for (int jj = 0; jj < nb; ++jj) {
         const int buf = jj & 1;
         const int owner = (int)(jj / R);
-        T* xj = P + (int64_t)jj * Rp;
-        T* ac = P + (int64_t)lane * Rp;
-        const int64_t ib = max64((int64_t)jj + 1 - r0, 0);  // first owned row strictly below the diagonal
+        T* xj = P + jj * Rp;
+        T* ac = P + lane * Rp;
+        const int ib = max(jj + 1 - r0, 0);  // first owned row strictly below the diagonal
         T acc = (T)0;
         if (lane >= jj && lane < nb) {
             T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
-            int64_t i = max64(ib, g0);
+            int i = max(ib, g0);
             for (; i + 4 <= g1; i += 4) {
                 a0 = fma(xj[i], ac[i], a0);
                 a1 = fma(xj[i + 1], ac[i + 1], a1);
@@ -232,7 +233,7 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(QCT)
             for (int g = 0; g < QCT / 32; ++g) t += part[g][lane];
             for (int q = 0; q < QCL; ++q) *cluster.map_shared_rank(&all_part[buf][rank][lane], q) = t;
             if (rank == owner) {
-                const T rv = P[(int64_t)lane * Rp + (jj - r0)];
+                const T rv = P[lane * Rp + (jj - r0)];
                 for (int q = 0; q < QCL; ++q) *cluster.map_shared_rank(&all_row[buf][lane], q) = rv;
             }
         }
@@ -259,13 +260,13 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(QCT)
         if (tid == 0) bsh[jj] = b;  // identical in every CTA of the cluster
         // v below the diagonal
         if (scale)
-            for (int64_t i = ib + tid; i < nloc; i += QCT) xj[i] = xj[i] / v1;
+            for (int i = ib + tid; i < nloc; i += QCT) xj[i] = xj[i] / v1;
         __syncthreads();
         if (lane > jj && lane < nb && b != (T)0) {
             const T wc = wsh[lane];
-            const int64_t id = max64((int64_t)jj - r0, 0);  // owned rows >= the diagonal
-            const int64_t dr = (int64_t)jj - r0;             // local index of the diagonal row
-            int64_t i = max64(id, g0);
+            const int id = max(jj - r0, 0);  // owned rows >= the diagonal
+            const int dr = jj - r0;           // local index of the diagonal row
+            int i = max(id, g0);
             // blocks of 8 rows: all loads before the stores (the column of v and
             // the updated column never overlap)
             for (; i + 8 <= g1; i += 8) {
@@ -291,48 +292,47 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(QCT)
         __syncthreads();
     }
     // write R / v back to W and the explicit V (0 above, 1 on the diagonal)
-    for (int64_t q = tid; q < R * QNB; q += QCT) {
-        int64_t i = q % R, c = q / R;
-        if (i < nloc && c < nb) {
-            int64_t gi = r0 + i;
-            T pv = P[c * Rp + i];
-            W[(k0 + gi) + (k0 + c) * ld] = pv;
-            V[gi + c * ldv] = gi < c ? (T)0 : (gi == c ? (T)1 : pv);
-        } else if (i < nloc) {
-            V[(r0 + i) + c * ldv] = (T)0;
+    for (int c = 0; c < QNB; ++c)
+        for (int i = tid; i < nloc; i += QCT) {
+            const int64_t gi = r0 + i;
+            if (c < nb) {
+                const T pv = P[c * Rp + i];
+                W[(k0 + gi) + (k0 + c) * ld] = pv;
+                V[gi + c * ldv] = gi < c ? (T)0 : (gi == c ? (T)1 : pv);
+            } else {
+                V[gi + c * ldv] = (T)0;
+            }
         }
-    }
     __syncthreads();
     // make the local panel the explicit V, then Y = V^T V over the owned rows
-    for (int64_t q = tid; q < R * QNB; q += QCT) {
-        int64_t i = q % R, c = q / R;
-        int64_t gi = r0 + i;
-        if (c < nb && gi <= c) P[c * Rp + i] = gi == c ? (T)1 : (T)0;
-    }
+    for (int c = 0; c < nb; ++c)
+        for (int i = tid; i < R && r0 + i <= c; i += QCT) P[c * Rp + i] = r0 + i == c ? (T)1 : (T)0;
     __syncthreads();
     {
         const int p = lane, q0 = warp * 4;  // Y[p][q0 .. q0 + 3]
         T y0 = (T)0, y1 = (T)0, y2 = (T)0, y3 = (T)0;
-        const T* vp = P + (int64_t)p * Rp;
-        const T* vq = P + (int64_t)q0 * Rp;
-        for (int64_t i = 0; i < nloc; ++i) {
+        const T* vp = P + p * Rp;
+        const T* vq = P + q0 * Rp;
+        for (int i = 0; i < nloc; ++i) {
             const T a = vp[i];
             y0 = fma(a, vq[i], y0);
             y1 = fma(a, vq[Rp + i], y1);
             y2 = fma(a, vq[2 * Rp + i], y2);
             y3 = fma(a, vq[3 * Rp + i], y3);
         }
-        Ypart[p][q0] = y0;
-        Ypart[p][q0 + 1] = y1;
-        Ypart[p][q0 + 2] = y2;
-        Ypart[p][q0 + 3] = y3;
+        // into rank 0's shared memory (pushed, so that rank 0 sums locally)
+        T* dst = cluster.map_shared_rank(Yall, 0) + (rank * QNB + p) * (QNB + 1);
+        dst[q0] = y0;
+        dst[q0 + 1] = y1;
+        dst[q0 + 2] = y2;
+        dst[q0 + 3] = y3;
     }
     cluster.sync();
     if (rank == 0) {
         for (int e = tid; e < QNB * QNB; e += QCT) {
-            int p = e % QNB, q = e / QNB;
+            const int p = e % QNB, q = e / QNB;
             T y = (T)0;
-            for (int r = 0; r < QCL; ++r) y += cluster.map_shared_rank(&Ypart[p][q], r)[0];
+            for (int r = 0; r < QCL; ++r) y += Yall[(r * QNB + p) * (QNB + 1) + q];
             Ts[p][q] = y;  // Ts holds Y for now
         }
         __syncthreads();
@@ -393,6 +393,81 @@ __global__ void k_check_diag(const double* __restrict__ Rs, int64_t n, int64_t l
     if (j >= n) return;
     double d = Rs[j + j * ldr];
     if (!(d > 0.0) || !isfinite(d)) set_info_once(info, (int32_t)(j + 1));
+}
+
+template <typename T>
+static size_t qr_cluster_smem(int64_t rows, int qcl) {
+    return sizeof(T) * ((size_t)(ceil_div(rows, qcl) | 1) * QNB + (size_t)qcl * QNB * (QNB + 1));
+}
+
+// 16 CTAs per cluster where the device can schedule that with the panel's
+// shared memory (non-portable size), else 8; 0 if neither fits (the
+// single-CTA panel kernel then runs).  Decided once per precision and size.
+template <typename T>
+static int qr_cluster_size_query(int64_t s) {
+    const size_t lim = 200 * 1024;
+    for (int qcl : {16, 8}) {
+        const size_t sm = qr_cluster_smem<T>(s, qcl);
+        if (sm > lim) continue;
+        auto kern = qcl == 16 ? k_qr_panel_cl<T, 16> : k_qr_panel_cl<T, 8>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+            (qcl > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = qcl;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(qcl);
+        cfg.blockDim = dim3(QCT);
+        cfg.dynamicSmemBytes = sm;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters >= 1) return qcl;
+        cudaGetLastError();
+    }
+    return 0;
+}
+
+template <typename T>
+static int qr_cluster_size(int64_t s) {
+    static std::mutex mu;
+    static int64_t last_s = -1;
+    static int last_dev = -1, last_q = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (s != last_s || dev != last_dev) {
+        last_q = qr_cluster_size_query<T>(s);
+        last_s = s;
+        last_dev = dev;
+    }
+    return last_q;
+}
+
+template <typename T>
+static cudaError_t qr_launch_cluster(int qcl, size_t smem, cudaStream_t st, T* W, int64_t s, int64_t k0, int nb,
+                                     T* beta, T* Tm, T* V, int64_t rows) {
+    auto kern = qcl == 16 ? k_qr_panel_cl<T, 16> : k_qr_panel_cl<T, 8>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = qcl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(qcl);
+    cfg.blockDim = dim3(QCT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, W, s, s, k0, nb, beta, Tm, V, rows);
 }
 
 // V and T are double-buffered by panel parity; the trailing update of a panel
@@ -512,6 +587,7 @@ static lsq_status qr_run(const void* As, int64_t s, int64_t n, int64_t ldas, int
         sl = qs->lo;
     }
     lsq_status r = LSQ_OK;
+    const int qcl = qr_cluster_size<T>(s);
     int k = 0;
     for (int64_t k0 = 0; k0 < n && r == LSQ_OK; k0 += QNB, ++k) {
         const int b = k & 1;
@@ -519,18 +595,16 @@ static lsq_status qr_run(const void* As, int64_t s, int64_t n, int64_t ldas, int
         int64_t rows = s - k0;
         T* Tm = (T*)(base + L.tm[b]);
         T* V = (T*)(base + L.v[b]);
-        size_t clsm = sizeof(T) * (size_t)(ceil_div(rows, QCL) | 1) * QNB;
+        const size_t clsm = qcl > 0 ? qr_cluster_smem<T>(rows, qcl) : 0;
         // Householder panel: sum over its columns of 4 (rows - j)(nb - j) flops
         double pflops = 0.0;
         for (int j = 0; j < nb; ++j) pflops += 4.0 * (double)(rows - j) * (double)(nb - j);
         stage_mark(ST_K_QRPANEL, true, sh);
-        if (clsm <= 160 * 1024) {
-            if (cudaFuncSetAttribute(k_qr_panel_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)clsm) !=
-                cudaSuccess) {
+        if (qcl > 0) {
+            if (qr_launch_cluster<T>(qcl, clsm, sh, W, s, k0, nb, beta, Tm, V, rows) != cudaSuccess) {
                 r = LSQ_ERR_CUDA;
                 break;
             }
-            k_qr_panel_cl<T><<<QCL, QCT, clsm, sh>>>(W, s, s, k0, nb, beta, Tm, V, rows);
         } else {
             k_qr_panel<T><<<1, QPT, 0, sh>>>(W, s, s, k0, nb, beta, Tm, V, rows);
         }

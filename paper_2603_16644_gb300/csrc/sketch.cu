@@ -9,6 +9,8 @@
 #include "common.cuh"
 #include "kernels.cuh"
 
+#include <type_traits>
+
 namespace lsq {
 
 // ---------------------------------------------------------------------------
@@ -196,6 +198,49 @@ __global__ void k_quantize_rm(const double* __restrict__ A, int64_t m, int64_t n
     }
 }
 
+// The same with 64 x 64 tiles and 16-byte row-major stores (ES bytes per
+// element; n * ES a multiple of 16).
+template <int ES>
+__global__ void __launch_bounds__(256) k_quantize_rm_v(const double* __restrict__ A, int64_t m, int64_t n,
+                                                       int64_t lda, const int32_t* __restrict__ colexp, int prec,
+                                                       void* __restrict__ out) {
+    using W = typename std::conditional<ES == 8, unsigned long long, uint32_t>::type;
+    __shared__ W tile[64][65];  // [column][row]
+    const int64_t j0 = (int64_t)blockIdx.x * 64, c0 = (int64_t)blockIdx.y * 64;
+    const int t = threadIdx.x, tx = t & 63, ty = t >> 6;
+    for (int c = ty; c < 64; c += 4) {
+        const int64_t j = j0 + tx, cc = c0 + c;
+        W v = 0;
+        if (j < m && cc < n) {
+            const double a = A[j + cc * lda];
+            if constexpr (ES == 8) v = (W)__double_as_longlong(a);
+            else v = (W)quant_bits(a, colexp[cc], prec);
+        }
+        tile[c][tx] = v;
+    }
+    __syncthreads();
+    constexpr int PER = 16 / ES;  // elements per 16-byte store
+    constexpr int GRP = 64 / PER;  // stores per row of the tile
+    for (int q = t; q < 64 * GRP; q += 256) {
+        const int r = q / GRP, g = q % GRP;
+        const int64_t j = j0 + r, cc = c0 + (int64_t)g * PER;
+        if (j >= m || cc >= n) continue;
+        uint32_t w[4] = {0, 0, 0, 0};
+        if constexpr (ES == 8) {
+            const unsigned long long a = tile[g * 2][r], b = tile[g * 2 + 1][r];
+            w[0] = (uint32_t)a; w[1] = (uint32_t)(a >> 32); w[2] = (uint32_t)b; w[3] = (uint32_t)(b >> 32);
+        } else {
+#pragma unroll
+            for (int e = 0; e < PER; ++e) {
+                const uint32_t bits = tile[g * PER + e][r];
+                const int word = (e * ES) / 4, sh = ((e * ES) % 4) * 8;
+                w[word] |= (ES == 4 ? bits : (bits & ((1u << (8 * ES)) - 1u))) << sh;
+            }
+        }
+        *(uint4*)((char*)out + ((size_t)j * n + cc) * ES) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
 // Ahat in COLUMN-major order with leading dimension ldq (K-major operand of
 // the Gaussian sketch GEMM).
 __global__ void k_quantize_cm(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda,
@@ -245,6 +290,68 @@ __global__ void k_sparse_gather(const int32_t* __restrict__ rowptr, const uint32
         for (int u = 0; u < 4; ++u) {
             int64_t c = c0 + (int64_t)u * blockDim.x + threadIdx.x;
             if (c < n) As[i + c * ldas] = acc[u];
+        }
+    }
+}
+
+// The same gather with 16-byte loads: 8 sketch rows per block (one warp each),
+// lane l owning VW = 16 / sizeof(TS) consecutive columns of a 32 VW chunk; 8
+// entries' rows are loaded before they are added in the row's order (so the
+// sums are the same, bit for bit); the 8 rows of a chunk go out through
+// shared memory so that each column's 8 consecutive rows form one store.
+// Needs n * sizeof(TS) to be a multiple of 16.
+template <typename TS, typename TACC>
+__global__ void __launch_bounds__(256) k_sparse_gather_v(const int32_t* __restrict__ rowptr,
+                                                         const uint32_t* __restrict__ col,
+                                                         const TS* __restrict__ Ahat, int64_t s, int64_t n,
+                                                         TACC* __restrict__ As, int64_t ldas) {
+    constexpr int VW = 16 / (int)sizeof(TS);
+    constexpr int CH = 32 * VW;  // columns per chunk
+    __shared__ TACC tile[8][CH + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+    const bool live = i < s;
+    const int32_t lo = live ? rowptr[i] : 0, hi = live ? rowptr[i + 1] : 0;
+    for (int64_t c0 = 0; c0 < n; c0 += CH) {
+        const int64_t cl = c0 + (int64_t)lane * VW;  // first column of this lane
+        const bool cin = cl < n;
+        TACC acc[VW];
+#pragma unroll
+        for (int v = 0; v < VW; ++v) acc[v] = (TACC)0;
+        for (int32_t k0 = lo; k0 < hi; k0 += 32) {
+            const int cnt = min(32, hi - k0);
+            const uint32_t my = lane < cnt ? col[k0 + lane] : 0u;
+            for (int q0 = 0; q0 < cnt; q0 += 8) {
+                uint4 raw[8];
+                uint32_t e[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    e[u] = __shfl_sync(0xffffffffu, my, (q0 + u) & 31);
+                    const TS* row = Ahat + (size_t)(e[u] & 0x7fffffffu) * n;
+                    raw[u] = (q0 + u < cnt && cin) ? *(const uint4*)(row + cl) : make_uint4(0, 0, 0, 0);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (q0 + u < cnt) {
+                        const bool neg = (e[u] >> 31) != 0;
+                        const TS* vals = reinterpret_cast<const TS*>(&raw[u]);
+#pragma unroll
+                        for (int v = 0; v < VW; ++v) {
+                            const TACC x = (TACC)to_acc<TS, TACC>(vals[v]);
+                            acc[v] = neg ? acc[v] - x : acc[v] + x;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int v = 0; v < VW; ++v) tile[warp][lane * VW + v] = acc[v];
+        __syncthreads();
+        for (int q = threadIdx.x; q < 8 * CH; q += 256) {
+            const int r = q & 7, c = q >> 3;
+            const int64_t gi = (int64_t)blockIdx.x * 8 + r, gc = c0 + c;
+            if (gi < s && gc < n) As[gi + gc * ldas] = tile[r][c];
         }
     }
 }
@@ -340,6 +447,18 @@ lsq_status launch_colexp(const double* A, int64_t m, int64_t n, int64_t lda, int
 
 lsq_status launch_quantize_rm(const double* A, int64_t m, int64_t n, int64_t lda, const int32_t* colexp, int prec,
                               void* out, cudaStream_t st) {
+    const int es = prec_bytes(prec);
+    if ((n * es) % 16 == 0 && ((uintptr_t)out % 16) == 0) {
+        dim3 g((unsigned)ceil_div(m, 64), (unsigned)ceil_div(n, 64));
+        switch (es) {
+        case 1: k_quantize_rm_v<1><<<g, 256, 0, st>>>(A, m, n, lda, colexp, prec, out); break;
+        case 2: k_quantize_rm_v<2><<<g, 256, 0, st>>>(A, m, n, lda, colexp, prec, out); break;
+        case 4: k_quantize_rm_v<4><<<g, 256, 0, st>>>(A, m, n, lda, colexp, prec, out); break;
+        default: k_quantize_rm_v<8><<<g, 256, 0, st>>>(A, m, n, lda, colexp, prec, out); break;
+        }
+        LSQ_LAUNCH_CHECK();
+        return LSQ_OK;
+    }
     dim3 grid((unsigned)ceil_div(m, 32), (unsigned)ceil_div(n, 32));
     k_quantize_rm<<<grid, dim3(32, 8), 0, st>>>(A, m, n, lda, colexp, prec, out);
     LSQ_LAUNCH_CHECK();
@@ -357,6 +476,33 @@ lsq_status launch_quantize_cm(const double* A, int64_t m, int64_t n, int64_t lda
 lsq_status launch_sparse_gather(const int32_t* rowptr, const uint32_t* col, const void* Ahat, int prec, int64_t s,
                                 int64_t n, void* As, int64_t ldas, cudaStream_t st) {
     int threads = 256;
+    if ((n * prec_bytes(prec)) % 16 == 0 && ((uintptr_t)Ahat % 16) == 0) {
+        const unsigned g = (unsigned)ceil_div(s, 8);
+        switch (prec) {
+        case LSQ_FP8_E4M3:
+            k_sparse_gather_v<__nv_fp8_storage_t, float><<<g, 256, 0, st>>>(
+                rowptr, col, (const __nv_fp8_storage_t*)Ahat, s, n, (float*)As, ldas);
+            break;
+        case LSQ_BF16:
+            k_sparse_gather_v<__nv_bfloat16, float><<<g, 256, 0, st>>>(rowptr, col, (const __nv_bfloat16*)Ahat, s, n,
+                                                                       (float*)As, ldas);
+            break;
+        case LSQ_FP16:
+            k_sparse_gather_v<__half, float><<<g, 256, 0, st>>>(rowptr, col, (const __half*)Ahat, s, n, (float*)As,
+                                                                ldas);
+            break;
+        case LSQ_FP32:
+            k_sparse_gather_v<float, float><<<g, 256, 0, st>>>(rowptr, col, (const float*)Ahat, s, n, (float*)As,
+                                                               ldas);
+            break;
+        default:
+            k_sparse_gather_v<double, double><<<g, 256, 0, st>>>(rowptr, col, (const double*)Ahat, s, n,
+                                                                 (double*)As, ldas);
+            break;
+        }
+        LSQ_LAUNCH_CHECK();
+        return LSQ_OK;
+    }
     switch (prec) {
     case LSQ_FP8_E4M3:
         k_sparse_gather<__nv_fp8_storage_t, float><<<(unsigned)s, threads, 0, st>>>(

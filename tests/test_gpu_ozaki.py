@@ -1,7 +1,8 @@
-"""FP64 Gram on the FP8 tensor cores by digit slicing (lsq_gram_tc): exact on
-integer data, within the FP64 error order on general data (also with K split
-into several exact chunks and with badly scaled columns), and PNE solves that
-use it meet the solution tolerance against the oracle."""
+"""FP64 products on the FP8 tensor cores by digit slicing (lsq_gram_tc for
+X^T X, lsq_gemm_tn_tc for X^T Y): exact on integer data, within the FP64
+error order on general data (also with K split into several exact chunks and
+with badly scaled columns), and PNE / HPNE solves that use them meet the
+solution tolerance against the oracle."""
 import ctypes as C
 from fractions import Fraction
 
@@ -73,7 +74,34 @@ def test_within_fp64_error_order(m, n, spread):
     np.testing.assert_array_equal(G, G.T)
 
 
-@pytest.mark.parametrize("hpne", [False])
+@pytest.mark.parametrize("m,n", [(3000, 200), (70000, 130), (1000, 1)])
+def test_gemm_tn_exact_on_integer_data(m, n):
+    rng = np.random.default_rng(m + 3 * n)
+    Xi = rng.integers(-8, 9, size=(m, n))
+    Yi = rng.integers(-8, 9, size=(m, n))
+    G, info = lsq.gemm_tn_tc(dev_colmajor(Xi.astype(np.float64)), dev_colmajor(Yi.astype(np.float64)))
+    assert int(to_np(info)[0]) == 0
+    np.testing.assert_array_equal(to_np(G), (Xi.T @ Yi).astype(np.float64))
+
+
+@pytest.mark.parametrize("m,n,spread", [(5000, 257, 0), (4000, 64, 30)])
+def test_gemm_tn_within_fp64_error_order(m, n, spread):
+    rng = np.random.default_rng(11 + n)
+    X = np.asfortranarray(rng.standard_normal((m, n)) * np.exp2(rng.integers(-spread, spread + 1, n))[None, :])
+    Y = np.asfortranarray(rng.standard_normal((m, n)) * np.exp2(rng.integers(-spread, spread + 1, n))[None, :])
+    Gd, info = lsq.gemm_tn_tc(dev_colmajor(X), dev_colmajor(Y))
+    assert int(to_np(info)[0]) == 0
+    G = to_np(Gd)
+    Go, _ = O.gram(X, Y)
+    tol_scheme = 2 * m * 2.0 ** -53 * np.outer(np.abs(X).max(axis=0), np.abs(Y).max(axis=0))
+    for (p, q) in [(0, 0), (n - 1, n - 1), (3, 1), (1, 3), (n - 1, 0), (0, n - 1), (n // 3, n // 5)]:
+        ex = sum((Fraction(float(a)) * Fraction(float(b)) for a, b in zip(X[:, p], Y[:, q])), Fraction(0))
+        assert abs(G[p, q] - float(ex)) <= tol_scheme[p, q], (p, q)
+    gamma = m * 2.0 ** -53 / (1 - m * 2.0 ** -53)
+    assert np.all(np.abs(G - Go) <= tol_scheme + gamma * (np.abs(X).T @ np.abs(Y)))
+
+
+@pytest.mark.parametrize("hpne", [False, True])
 def test_pne_with_emulated_gram_matches_oracle(hpne):
     m, n = 20000, 300
     for kap, rho in [(1e2, 0.0), (1e6, 1e-8), (1e10, 1e-3)]:
@@ -82,15 +110,16 @@ def test_pne_with_emulated_gram_matches_oracle(hpne):
                              refine_steps=1)
         A = dev_colmajor(pr.A)
         b = torch.from_numpy(pr.b).cuda()
+        solve = lsq.hpne if hpne else lsq.pne
         prev = set_emulation(True)
         try:
-            x_em, info = lsq.pne(A, b, opts=opts)
+            x_em, info = solve(A, b, opts=opts)
             assert int(to_np(info)[0]) == 0
             set_emulation(False)
-            x_64, _ = lsq.pne(A, b, opts=opts)
+            x_64, _ = solve(A, b, opts=opts)
         finally:
             set_emulation(prev)
-        ref = O.solve(pr.A, pr.b, kind=O.SPARSE_SIGN, s=4 * n, zeta=8, seed=3, sketch_prec=O.FP32,
+        ref = O.solve(pr.A, pr.b, hpne=hpne, kind=O.SPARSE_SIGN, s=4 * n, zeta=8, seed=3, sketch_prec=O.FP32,
                       qr_prec=O.FP32, refine_steps=1)
         assert_solution_parity(to_np(x_em), ref["x"], pr.x_star, kap, rho, f"kappa={kap}")
         e_em = P.rel_error(to_np(x_em), pr.x_star)
