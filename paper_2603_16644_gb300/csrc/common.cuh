@@ -245,4 +245,42 @@ __device__ __forceinline__ void set_info_once(int32_t* info, int32_t v) {
     if (info) atomicCAS(info, 0, v);
 }
 
+// 2^s (H 2^64 + L), a two's-complement 128-bit integer, rounded once to the
+// nearest double (ties to even): the integer is normalised with integer
+// operations and the scale goes into the exponent field (no FP64
+// instruction).  Straight-line code (selects), so that the compiler
+// interleaves independent conversions; results outside the normal range
+// scale the rounded 53-bit significand with ldexp (rare).
+__device__ __forceinline__ double fixed128_to_double(long long H, unsigned long long L, int s) {
+    // magnitude: two's-complement negation of (H:L) when negative
+    const unsigned long long sgn = (unsigned long long)(H >> 63);
+    const unsigned long long neg = sgn & 1ull;
+    const unsigned long long uL = (L ^ sgn) + neg;
+    const unsigned long long uH = ((unsigned long long)H ^ sgn) + (neg & (uL == 0 ? 1ull : 0ull));
+    const bool zero = (uH | uL) == 0;
+    int p = uH ? 127 - __clzll((long long)uH) : 63 - __clzll((long long)uL);
+    const int shl = p <= 52 ? 52 - p : 0;  // 0 .. 52
+    const int shr = p > 52 ? p - 52 : 0;   // 0 .. 75
+    const unsigned long long small = uL << shl;
+    // bits p-52 .. p of the magnitude, the round bit below them and the sticky rest
+    const unsigned long long big = shr < 64 ? ((uL >> shr) | (shr ? (uH << ((64 - shr) & 63)) : 0ull)) : (uH >> (shr - 64));
+    unsigned long long mant = p > 52 ? big : small;
+    const int rp = shr - 1;  // position of the round bit (when shr > 0)
+    const unsigned long long rb =
+        shr == 0 ? 0ull : (rp < 64 ? (uL >> (rp & 63)) & 1ull : (uH >> ((rp - 64) & 63)) & 1ull);
+    const bool sticky = shr <= 1 ? false
+                        : rp <= 64 ? (uL & ((rp == 64) ? ~0ull : ((1ull << (rp & 63)) - 1ull))) != 0
+                                   : (uL != 0 || (uH & ((1ull << ((rp - 64) & 63)) - 1ull)) != 0);
+    mant += (rb && (sticky || (mant & 1ull))) ? 1ull : 0ull;
+    const bool carry = mant == (1ull << 53);
+    mant = carry ? mant >> 1 : mant;
+    p += carry ? 1 : 0;
+    const int E = p + s + 1023;
+    double r = __longlong_as_double((long long)((sgn & 0x8000000000000000ull) | ((unsigned long long)(E & 2047) << 52) |
+                                                (mant & 0x000fffffffffffffull)));
+    if (zero) r = 0.0;
+    if (!zero && (E <= 0 || E >= 2047)) r = ldexp(neg ? -(double)mant : (double)mant, p - 52 + s);
+    return r;
+}
+
 }  // namespace lsq

@@ -127,17 +127,20 @@ __device__ __forceinline__ T rsqrt_pivot(T d) {
     }
 }
 
-// Diagonal block (CNB x CNB) in one CTA, right-looking.  Per column j: one
-// thread forms the pivot (L_jj = d r, r = 1/sqrt(d)), the column is scaled by
-// r into a separate buffer, and the update L[r][c] -= l_r l_c visits only the
-// active triangle j < c <= r, spread over all threads so that every warp
-// issues full-width FP64 instructions.
+// Diagonal block (CNB x CNB) in one CTA, right-looking.  Per column j the
+// column is scaled by r_j = 1/sqrt(d_j) into a separate buffer; then thread 0
+// applies column j's update to the next diagonal entry and forms the next
+// pivot (L_jj = d r, r = 1/sqrt(d)) while warps 1-7 update the rest of the
+// active triangle j < c <= r (row-major enumeration from a table, so that
+// every warp issues full-width FP64 instructions): the pivot's dependent
+// FP64 chain overlaps the update.
 template <typename T>
 __global__ void __launch_bounds__(256) k_potrf_diag(T* __restrict__ G, int64_t ld, int64_t n, int64_t k0,
                                                     int32_t* __restrict__ info) {
     if (*info != 0) return;
     __shared__ T D[CNB][CNB + 1];
     __shared__ T colj[CNB];
+    __shared__ uint16_t tri[CNB * (CNB - 1) / 2];  // e -> (rr << 8) | cc, lower triangle by rows
     __shared__ T rj;
     __shared__ int bad;
     const int nb = (int)min64(CNB, n - k0);
@@ -146,38 +149,54 @@ __global__ void __launch_bounds__(256) k_potrf_diag(T* __restrict__ G, int64_t l
         const int r = q & 63, c = q >> 6;
         D[r][c] = (r < nb && c < nb) ? G[(k0 + r) + (k0 + c) * ld] : (T)0;
     }
-    if (tid == 0) bad = 0;
+    for (int e = tid; e < CNB * (CNB - 1) / 2; e += 256) {
+        int rr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+        while (rr * (rr + 1) / 2 > e) --rr;
+        tri[e] = (uint16_t)((rr << 8) | (e - rr * (rr + 1) / 2));
+    }
+    __syncthreads();
+    if (tid == 0) {
+        bad = 0;
+        const T d = D[0][0];
+        if (!(d > (T)0) || !isfinite(d)) {
+            bad = 1;
+        } else {
+            const T r = rsqrt_pivot<T>(d);
+            rj = r;
+            D[0][0] = d * r;
+        }
+    }
     __syncthreads();
     for (int j = 0; j < nb; ++j) {
-        if (tid == 0) {
-            const T d = D[j][j];
-            if (!(d > (T)0) || !isfinite(d)) {
-                bad = j + 1;
-            } else {
-                const T r = rsqrt_pivot<T>(d);
-                rj = r;
-                D[j][j] = d * r;
-            }
-        }
-        __syncthreads();
         if (bad) break;
+        const T r = rj;
         if (tid > j && tid < nb) {
-            const T l = D[tid][j] * rj;
+            const T l = D[tid][j] * r;
             D[tid][j] = l;
             colj[tid] = l;
         }
         __syncthreads();
-        // active triangle: a = nb - 1 - j rows/columns below the pivot; entry e
-        // -> (cc, rr) with cc <= rr (row-major over the lower triangle)
-        const int a = nb - 1 - j;
-        const int E = a * (a + 1) / 2;
-        for (int e = tid; e < E; e += 256) {
-            int rr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-            while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
-            while (rr * (rr + 1) / 2 > e) --rr;
-            const int cc = e - rr * (rr + 1) / 2;
-            const int r = j + 1 + rr, c = j + 1 + cc;
-            D[r][c] = fma(-colj[r], colj[c], D[r][c]);
+        if (j + 1 < nb) {
+            if (tid == 0) {
+                const T d = fma(-colj[j + 1], colj[j + 1], D[j + 1][j + 1]);
+                if (!(d > (T)0) || !isfinite(d)) {
+                    bad = j + 2;
+                } else {
+                    const T rn = rsqrt_pivot<T>(d);
+                    rj = rn;
+                    D[j + 1][j + 1] = d * rn;
+                }
+            } else if (tid >= 32) {
+                // entries 1 .. E-1 of the active triangle (entry 0 is the next pivot)
+                const int a = nb - 1 - j;
+                const int E = a * (a + 1) / 2;
+                for (int e = tid - 31; e < E; e += 224) {
+                    const int rc = tri[e];
+                    const int rr = j + 1 + (rc >> 8), cc = j + 1 + (rc & 255);
+                    D[rr][cc] = fma(-colj[rr], colj[cc], D[rr][cc]);
+                }
+            }
         }
         __syncthreads();
     }

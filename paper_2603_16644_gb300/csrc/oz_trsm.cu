@@ -39,7 +39,7 @@ constexpr int OT_BK = 64;                   // K per stage: 64 BF16 = 128 bytes
 constexpr int OT_XST = 6;                   // stages of X digit tiles
 constexpr int OT_KMAX = 512;                // exact FP32 group sums up to this K
 constexpr int OT_NB = 32;                   // diagonal block solved by substitution
-constexpr int OT_THREADS = 576;             // warp 0 TMA, warp 1 MMA, warps 2-17 epilogue
+constexpr int OT_THREADS = 608;             // warp 0 TMA, warps 1-2 MMA, warps 3-18 epilogue
 constexpr int OT_XTILE = OT_BM * 128;       // bytes of one X digit tile
 constexpr int OT_YTILE = OT_BN * 128;       // bytes of one Y digit tile
 constexpr int32_t OT_NONFINITE = 0x7fffffff;
@@ -57,8 +57,12 @@ __device__ __forceinline__ int32_t ot_exp_of_max(unsigned long long mx) {
     return (Eb > 1 ? Eb : 1) - 1022;  // every |x| < 2^E
 }
 
-// Balanced base-128 digits of x with |x| < 2^E (see the file comment).
-__device__ __forceinline__ void ot_digits(double x, int32_t E, int (&d)[OT_DIG]) {
+// Balanced base-128 digits of x with |x| < 2^E (see the file comment), as
+// the fields of W = V + BIAS, V = trunc(x 2^(55 - E)) in two's complement:
+// adding 64 to every lower 7-bit field makes each field t >= 1 equal to
+// d_t + 64 (d_t in [-64, 63]), and the arithmetic top W >> 49 is d_0 in
+// [-64, 64].  A non-finite x or row exponent gives V = 0.
+__device__ __forceinline__ unsigned long long ot_fields(double x, int32_t E) {
     unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const bool neg = (b >> 63) != 0;
     const int Eb = (int)((b >> 52) & 0x7ff);
@@ -72,22 +76,23 @@ __device__ __forceinline__ void ot_digits(double x, int32_t E, int (&d)[OT_DIG])
         const int sh = (Eb != 0 ? Eb : 1) - (E + 1022) + 2;  // <= 2, so V < 2^55
         V = sh >= 0 ? (sig << sh) : (sh > -64 ? (sig >> (-sh)) : 0ull);
     }
-    // adding 64 to every lower digit field turns the base-128 digits into
-    // balanced ones: field - 64 in [-64, 63], the carry lands in the top digit
     constexpr unsigned long long BIAS = 64ull * ((1ull << 42) + (1ull << 35) + (1ull << 28) + (1ull << 21) +
                                                  (1ull << 14) + (1ull << 7) + 1ull);
-    const unsigned long long W = V + BIAS;
-    d[0] = (int)(W >> 49);  // in [0, 64]
-#pragma unroll
-    for (int t = 1; t < OT_DIG; ++t) d[t] = (int)((W >> (7 * (OT_DIG - 1 - t))) & 127ull) - 64;
-    if (neg) {
-#pragma unroll
-        for (int t = 0; t < OT_DIG; ++t) d[t] = -d[t];
-    }
+    return (neg ? 0ull - V : V) + BIAS;
 }
 
-__device__ __forceinline__ uint32_t bf16_bits_of_int(int v) {
-    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)v));  // exact for |v| <= 256
+// Digit t of W as an FP32 value: 2^23 1.5 + field, minus the same plus 64
+// (exact integer arithmetic in FP32, no conversion instruction).  Its upper
+// half is the BF16 encoding (the digit has at most 7 significant bits).
+__device__ __forceinline__ uint32_t ot_digit_f32(unsigned long long W, int t) {
+    const uint32_t f = t == 0 ? (uint32_t)((int)((long long)W >> 49) + 64)
+                              : (uint32_t)((W >> (7 * (OT_DIG - 1 - t))) & 127ull);
+    return __float_as_uint(__uint_as_float(0x4B400000u | f) - 12582976.0f);
+}
+
+// BF16 digits t of two values, packed (first value in the low half).
+__device__ __forceinline__ uint32_t ot_digit_pair(unsigned long long W0, unsigned long long W1, int t) {
+    return __byte_perm(ot_digit_f32(W0, t), ot_digit_f32(W1, t), 0x7632);
 }
 
 // Rows of X (m x K, column-major): Ex[i] and digit planes Z[(t mp + i) Kp + k]
@@ -121,17 +126,12 @@ __global__ void __launch_bounds__(128) k_ot_rowslice(const double* __restrict__ 
     for (int64_t k0 = 0; k0 < Kp; k0 += 16) {
         uint32_t pk[OT_DIG][8];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            int64_t k = k0 + q;
-            double x = k < Kr ? row[k * ld] : 0.0;
-            int d[OT_DIG];
-            ot_digits(x, E, d);
+        for (int q2 = 0; q2 < 8; ++q2) {
+            const int64_t k = k0 + 2 * q2;
+            const unsigned long long W0 = ot_fields(k < Kr ? row[k * ld] : 0.0, E);
+            const unsigned long long W1 = ot_fields(k + 1 < Kr ? row[(k + 1) * ld] : 0.0, E);
 #pragma unroll
-            for (int t = 0; t < OT_DIG; ++t) {
-                uint32_t h = bf16_bits_of_int(d[t]);
-                if (q & 1) pk[t][q >> 1] |= h << 16;
-                else pk[t][q >> 1] = h;
-            }
+            for (int t = 0; t < OT_DIG; ++t) pk[t][q2] = ot_digit_pair(W0, W1, t);
         }
 #pragma unroll
         for (int t = 0; t < OT_DIG; ++t) {
@@ -167,16 +167,12 @@ __global__ void __launch_bounds__(128) k_ot_rowslice_e(const double* __restrict_
         for (int q = 0; q < 16; ++q) xv[q] = k0 + q < Kr ? row[(k0 + q) * ld] : 0.0;
         uint32_t pk[OT_DIG][8];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            int d[OT_DIG];
-            ot_digits(xv[q], E, d);
+        for (int q2 = 0; q2 < 8; ++q2) {
+            const unsigned long long W0 = ot_fields(xv[2 * q2], E), W1 = ot_fields(xv[2 * q2 + 1], E);
 #pragma unroll
-            for (int t = 0; t < OT_DIG; ++t) {
-                uint32_t h = bf16_bits_of_int(d[t]);
-                if (q & 1) pk[t][q >> 1] |= h << 16;
-                else pk[t][q >> 1] = h;
-            }
+            for (int t = 0; t < OT_DIG; ++t) pk[t][q2] = ot_digit_pair(W0, W1, t);
         }
+        // 32 bytes (one sector) per digit plane
 #pragma unroll
         for (int t = 0; t < OT_DIG; ++t) {
             uint4* dst = (uint4*)(Z + ((int64_t)t * mp + i) * Kp + k0);
@@ -217,60 +213,32 @@ __global__ void __launch_bounds__(128) k_ot_colslice(const double* __restrict__ 
     __syncthreads();
     const int32_t E = Es;
     for (int64_t k = threadIdx.x; k < Kp; k += blockDim.x) {
-        int d[OT_DIG];
-        ot_digits(k < Kr ? col[k * sk] : 0.0, E, d);
+        const unsigned long long W = ot_fields(k < Kr ? col[k * sk] : 0.0, E);
 #pragma unroll
-        for (int u = 0; u < OT_DIG; ++u) Z[((int64_t)u * Np + j) * Kp + k] = (uint16_t)bf16_bits_of_int(d[u]);
+        for (int u = 0; u < OT_DIG; ++u) Z[((int64_t)u * Np + j) * Kp + k] = (uint16_t)(ot_digit_f32(W, u) >> 16);
     }
 }
 
 // ---------------------------------------------------------------------------
 // Update C_out = C_in - X Y over 128 x 64 tiles (C_in may equal C_out).
 // ---------------------------------------------------------------------------
-// 2^s (hi 2^28 + lo) for |hi|, |lo| < 2^47, rounded once to nearest-even:
-// the exact 128-bit integer is normalised with integer operations and the
-// scale goes into the exponent field (no FP64 instruction).  Straight-line
-// code (selects), so that the compiler interleaves independent conversions;
-// results outside the normal range take the (rare) FP64 path.
+// 2^s (hi 2^28 + lo) for |hi|, |lo| < 2^47, rounded once to nearest-even
+// (the 128-bit sum is formed exactly, then converted by fixed128_to_double).
 __device__ __forceinline__ double ot_fixed_to_double(long long hi, long long lo, int s) {
     unsigned long long L = (unsigned long long)hi << 28;
     long long H = hi >> 36;
     const unsigned long long L2 = L + (unsigned long long)lo;
     H += (lo >> 63) + (L2 < L ? 1 : 0);
-    L = L2;
-    // magnitude: two's-complement negation of (H:L) when negative
-    const unsigned long long sgn = (unsigned long long)(H >> 63);
-    const unsigned long long neg = sgn & 1ull;
-    const unsigned long long uL = (L ^ sgn) + neg;
-    const unsigned long long uH = ((unsigned long long)H ^ sgn) + (neg & (uL == 0 ? 1ull : 0ull));
-    const bool zero = (uH | uL) == 0;
-    int p = uH ? 127 - __clzll((long long)uH) : 63 - __clzll((long long)uL);
-    const int shl = p <= 52 ? 52 - p : 0;            // 0 .. 52
-    const int shr = p > 52 ? p - 52 : 0;             // 0 .. 22
-    const unsigned long long small = uL << shl;
-    const unsigned long long big = (uL >> shr) | (shr ? (uH << ((64 - shr) & 63)) : 0ull);
-    unsigned long long mant = p > 52 ? big : small;
-    const unsigned long long rb = shr ? (uL >> ((shr - 1) & 63)) & 1ull : 0ull;
-    const bool sticky = shr > 1 ? (uL & ((1ull << ((shr - 1) & 63)) - 1ull)) != 0 : false;
-    mant += (rb && (sticky || (mant & 1ull))) ? 1ull : 0ull;
-    const bool carry = mant == (1ull << 53);
-    mant = carry ? mant >> 1 : mant;
-    p += carry ? 1 : 0;
-    const int E = p + s + 1023;
-    double r = __longlong_as_double((long long)((sgn & 0x8000000000000000ull) | ((unsigned long long)(E & 2047) << 52) |
-                                                (mant & 0x000fffffffffffffull)));
-    if (zero) r = 0.0;
-    if (!zero && (E <= 0 || E >= 2047)) r = ldexp(fma((double)hi, 268435456.0, (double)lo), s);
-    return r;
+    return fixed128_to_double(H, L2, s);
 }
 
 // Persistent: one CTA per SM walks the tiles (column tiles fastest, so that
 // CTAs sharing a row block of X digits run together).  Warp 0 streams the
-// digit tiles of consecutive tiles through the rings; warp 1 issues the MMAs
-// of a tile as soon as the epilogue has taken the previous tile's group sums
-// out of TMEM (tfree); warps 2-17 drain TMEM into registers, release it, and
-// convert and store while the next tile's MMAs run.
-// 18 warps: two of the four schedulers hold 5 warps, and a scheduler's
+// digit tiles of consecutive tiles through the rings; warps 1 and 2 issue the
+// MMAs of a tile as soon as the epilogue has taken the previous tile's group
+// sums out of TMEM (tfree); warps 3-18 drain TMEM into registers, release it,
+// and convert and store while the next tile's MMAs run.
+// 19 warps: three of the four schedulers hold 5 warps, and a scheduler's
 // register file (16 K registers) then allows 96 registers per thread.
 constexpr int OT_EPI_WARPS = 16;
 
@@ -292,7 +260,7 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
     uint64_t* mdone = tfree + 1;       // every MMA of the CTA has completed
     uint32_t* tslot = (uint32_t*)(mdone + 1);
     volatile int* bad = (volatile int*)(tslot + 1);
-    int* cnt = (int*)(tslot + 2);  // issued / consumed: x, x, y, y
+    int* cnt = (int*)(tslot + 2);  // x issued, x consumed (issuer 0), y issued, y consumed (0), x / y consumed (1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nslab = (int)((K + OT_BK - 1) / OT_BK);
@@ -301,17 +269,17 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2; ++s) {
             mbar_init(&yfull[s], 1);
-            mbar_init(&yempty[s], 1);
+            mbar_init(&yempty[s], 2);
         }
         for (int s = 0; s < OT_XST; ++s) {
             mbar_init(&xfull[s], 1);
-            mbar_init(&xempty[s], 1);
+            mbar_init(&xempty[s], 2);
         }
-        mbar_init(accf, 1);
+        mbar_init(accf, 2);
         mbar_init(tfree, OT_EPI_WARPS);
-        mbar_init(mdone, 1);
+        mbar_init(mdone, 2);
         *bad = 0;
-        cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
+        cnt[0] = cnt[1] = cnt[2] = cnt[3] = cnt[4] = cnt[5] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) tmem_alloc(tslot, 512);
@@ -363,11 +331,16 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
                 cnt[0] = xq + 1;
             }
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer: pair (t, u) with t + u <= 7 into accumulator t + u; the
-        // 4 K steps of one pair go back to back into the same accumulator
-        // (measured: interleaving accumulators, even with operand A kept in
-        // the collector buffer, is 40 % - 3x slower)
+    } else if ((warp == 1 || warp == 2) && lane == 0) {
+        // MMA issuers: pair (t, u) with t + u <= 7 into accumulator t + u.
+        // One thread issues an MMA only every ~90 cycles, so two warps issue,
+        // each owning the accumulators of its groups (18 pairs each): no two
+        // threads accumulate into the same TMEM columns.  The 4 K steps of one
+        // pair go back to back into the same accumulator (measured:
+        // interleaving accumulators, even with operand A kept in the collector
+        // buffer, is 40 % - 3x slower).  Both commit every stage and tile.
+        const int iss = warp - 1;
+        constexpr unsigned OWN1 = (1u << 1) | (1u << 2) | (1u << 5) | (1u << 6);  // groups of issuer 1
         const uint32_t idesc = umma_idesc(1u, OT_BM, OT_BN);
         int xq = 0, g = 0;
         for (int i = 0; i < ntl && !*bad; ++i) {
@@ -382,17 +355,18 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
                     *bad = 1;
                     break;
                 }
-                cnt[3] = g + 1;
+                cnt[iss ? 5 : 3] = g + 1;
                 for (int t = 0; t < OT_DIG; ++t, ++xq) {
                     const int xs = xq % OT_XST;
                     if (!mbar_wait(&xfull[xs], (uint32_t)((xq / OT_XST) & 1))) {
                         *bad = 1;
                         break;
                     }
-                    cnt[1] = xq + 1;
+                    cnt[iss ? 4 : 1] = xq + 1;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint64_t ad = umma_desc(smem_u32(sX + xs * OT_XTILE));
                     for (int u = 0; u + t < OT_DIG; ++u) {
+                        if ((int)((OWN1 >> (t + u)) & 1u) != iss) continue;
                         const uint64_t bd = umma_desc(smem_u32(sY + (ys * OT_DIG + u) * OT_YTILE));
                         const uint32_t acc = tmem + (uint32_t)((t + u) * OT_BN);
 #pragma unroll
@@ -403,12 +377,12 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
                 }
                 umma_commit(&yempty[ys]);
             }
-            umma_commit(accf);  // fires when this tile's MMAs have completed
+            umma_commit(accf);  // fires when this issuer's MMAs of the tile have completed
         }
-    } else if (warp >= 2) {
-        // epilogue warp e = warp - 2: TMEM lane quadrant warp % 4 (its rows),
+    } else if (warp >= 3) {
+        // epilogue warp e = warp - 3: TMEM lane quadrant warp % 4 (its rows),
         // columns [16 (e / 4), +16) of the tile
-        const int quad = warp & 3, cq = (warp - 2) >> 2;
+        const int quad = warp & 3, cq = (warp - 3) >> 2;
         const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cq * 16);
         for (int i = 0; i < ntl; ++i) {
             const int tile = (int)blockIdx.x + i * (int)gridDim.x;
@@ -472,14 +446,15 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
             }
         }
     }
-    if (warp == 1 && lane == 0) umma_commit(mdone);  // fires when every MMA issued above has completed
+    if ((warp == 1 || warp == 2) && lane == 0) umma_commit(mdone);  // fires when every MMA issued has completed
     __syncthreads();
     if (*bad) {
         if (threadIdx.x == 0) {
             set_info_once(err, -2);
             // wait (bounded) for copies issued but never consumed, then the MMAs
-            for (int q = cnt[1]; q < cnt[0]; ++q) mbar_wait(&xfull[q % OT_XST], (uint32_t)((q / OT_XST) & 1));
-            for (int g = cnt[3]; g < cnt[2]; ++g) mbar_wait(&yfull[g & 1], (uint32_t)((g >> 1) & 1));
+            for (int q = min(cnt[1], cnt[4]); q < cnt[0]; ++q)
+                mbar_wait(&xfull[q % OT_XST], (uint32_t)((q / OT_XST) & 1));
+            for (int g = min(cnt[3], cnt[5]); g < cnt[2]; ++g) mbar_wait(&yfull[g & 1], (uint32_t)((g >> 1) & 1));
             mbar_wait(mdone, 0);
         }
         __syncthreads();

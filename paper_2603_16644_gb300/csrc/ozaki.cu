@@ -10,9 +10,9 @@
 // a K-chunk of up to 65536 rows sums exactly in the FP32 accumulators of
 // tcgen05.mma (kind::f8f6f4, E4M3 operands).  Every digit-pair block (t, u)
 // with t + u <= S - 1 is one tensor-core contraction over the rows; the
-// blocks are combined in FP64 in a fixed order (smallest weight first) and
-// scaled by 2^(e_p + e_q).  Dropped pairs and the residuals r contribute
-// below 2^-55 of |x_p| |x_q| per row, the same order as FP64 rounding.
+// blocks are combined exactly in integers, scaled by 2^(e_p + e_q) and
+// rounded once.  Dropped pairs and the residuals r contribute below 2^-55 of
+// |x_p| |x_q| per row, the same order as FP64 rounding.
 //
 // Digits are extracted with integer operations on the FP64 bit pattern (no
 // FP64 instruction in the slicing pass).
@@ -25,6 +25,7 @@ namespace lsq {
 
 constexpr int OZ_S = 14;        // digits per value (4 bits each: 56 bits)
 constexpr int64_t OZ_KCHUNK = 65536;  // rows summed exactly per FP32 accumulator
+constexpr int32_t OZ_NONFINITE = INT32_MAX;  // column exponent of a column holding an Inf or NaN
 
 lsq_status launch_tc_tiles_fp8(const void* X, int64_t ldx, int64_t rowsX, const void* Y, int64_t ldy, int64_t rowsY,
                                int64_t K, int64_t kchunk, const int2* tiles, int64_t ntiles, float* out, int32_t* err,
@@ -51,76 +52,193 @@ __global__ void k_oz_colexp(const double* __restrict__ X, int64_t m, int64_t ld,
         unsigned long long t = 0;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t = w[q] > t ? w[q] : t;
         int Eb = (int)((t >> 52) & 0x7ff);
-        e[p] = (t == 0 || Eb == 0) ? 0 : Eb - 1022;
+        e[p] = Eb == 0x7ff ? OZ_NONFINITE : (t == 0 || Eb == 0) ? 0 : Eb - 1022;
     }
 }
 
-__device__ __forceinline__ uint8_t e4m3_of_digit(int d) {
-    // exact E4M3 encoding of an integer in [-15, 15]
-    uint32_t a = (uint32_t)(d < 0 ? -d : d);
-    if (a == 0) return 0;
-    int E = 31 - __clz(a);                       // 0..3
-    uint32_t mant = (a - (1u << E)) << (3 - E);  // 3 bits
-    return (uint8_t)(((d < 0) ? 0x80u : 0u) | ((uint32_t)(E + 7) << 3) | mant);
+// Two FP32 values to E4M3 (the first in the upper byte); exact for the
+// integer digits in [-15, 15].
+__device__ __forceinline__ uint32_t e4m3x2(float hi, float lo) {
+    unsigned short r;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+    return r;
 }
 
 // Z row (t * np + p), column i  <-  digit t of x_ip.  Rows p >= n and
-// columns i >= m (padding) are zero.
-__global__ void k_oz_slice(const double* __restrict__ X, int64_t m, int64_t n, int64_t ld,
-                           const int32_t* __restrict__ e, int64_t np, int64_t ldz, uint8_t* __restrict__ Z) {
-    int64_t p = blockIdx.y;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ldz; i += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long V = 0;
-        bool neg = false;
-        if (p < n && i < m) {
-            unsigned long long b = (unsigned long long)__double_as_longlong(X[i + p * ld]);
-            neg = (b >> 63) != 0;
-            int Eb = (int)((b >> 52) & 0x7ff);
-            if (Eb != 0 && Eb != 0x7ff) {
-                unsigned long long sig = (b & 0x000fffffffffffffull) | 0x0010000000000000ull;
-                int sh = (Eb - 1023) - e[p] + 4;  // x 2^(56 - e_p) = sig 2^(E_a - 52 + 56 - e_p)
-                if (sh >= 0) V = sig << sh;       // sh <= 3: V < 2^56
-                else if (sh > -64) V = sig >> (-sh);
+// columns i >= m (padding) are zero.  4 consecutive rows per thread: a warp
+// reads 1 KB of a column and writes 128 contiguous bytes of every digit
+// plane.  Digit t of |x| is a nibble of V = |x| 2^(56 - e_p); its signed FP32
+// value is s (2^23 1.5 + nibble) - s 2^23 1.5 (s = +-1; exact, and +0 for a
+// zero nibble), converted in pairs by the hardware.
+__global__ void __launch_bounds__(256) k_oz_slice(const double* __restrict__ X, int64_t m, int64_t n, int64_t ld,
+                                                  const int32_t* __restrict__ e, int64_t np, int64_t ldz,
+                                                  uint8_t* __restrict__ Z) {
+    const int64_t p = blockIdx.y;
+    const int32_t ep = p < n ? e[p] : 0;
+    const double* col = X + p * ld;
+    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i0 < ldz;
+         i0 += (int64_t)gridDim.x * blockDim.x * 4) {
+        unsigned long long V[4];
+        float sg[4], off[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const unsigned long long b =
+                (p < n && i0 + q < m) ? (unsigned long long)__double_as_longlong(col[i0 + q]) : 0ull;
+            const int Eb = (int)((b >> 52) & 0x7ff);
+            V[q] = 0;
+            if (Eb != 0 && Eb != 0x7ff && ep != OZ_NONFINITE) {
+                const unsigned long long sig = (b & 0x000fffffffffffffull) | 0x0010000000000000ull;
+                const int sh = (Eb - 1023) - ep + 4;  // x 2^(56 - e_p) = sig 2^(E_a - 52 + 56 - e_p)
+                if (sh >= 0) V[q] = sig << sh;        // sh <= 3: V < 2^56
+                else if (sh > -64) V[q] = sig >> (-sh);
             }
+            sg[q] = (b >> 63) ? -1.0f : 1.0f;
+            off[q] = -sg[q] * 12582912.0f;
         }
 #pragma unroll
         for (int t = 0; t < OZ_S; ++t) {
-            int d = (int)((V >> (4 * (OZ_S - 1 - t))) & 15ull);
-            Z[((int64_t)t * np + p) * ldz + i] = e4m3_of_digit(neg ? -d : d);
+            float d[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t nib = (uint32_t)(V[q] >> (4 * (OZ_S - 1 - t))) & 15u;
+                d[q] = fmaf(sg[q], __uint_as_float(0x4B400000u | nib), off[q]);
+            }
+            *(uint32_t*)(Z + ((int64_t)t * np + p) * ldz + i0) = e4m3x2(d[1], d[0]) | (e4m3x2(d[3], d[2]) << 16);
         }
     }
 }
 
 // G[p, q] from the digit-pair tiles.  pair_tile[(t * S + u) * nb * nb + P * nb
 // + Q] = index of the tile holding C_tu[P block, Q block], or -1 (symmetric
-// case: then C_tu = C_ut^T is read from the (u, t) tile at (Q, P)).  sym:
-// only p >= q is formed and mirrored; ex / ey: column exponents of X / Y.
-__global__ void k_oz_combine(const float* __restrict__ T, const int32_t* __restrict__ pair_tile, int64_t ntiles,
-                             int chunks, int64_t n, int64_t nb, const int32_t* __restrict__ ex,
-                             const int32_t* __restrict__ ey, int sym, double* __restrict__ G, int64_t ldg) {
-    int64_t total = n * n;
-    for (int64_t q2 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q2 < total; q2 += (int64_t)gridDim.x * blockDim.x) {
-        int64_t p = q2 % n, q = q2 / n;
-        if (sym && p < q) continue;
-        int64_t P = p >> 7, Q = q >> 7, r = p & 127, c = q & 127;
-        double acc = 0.0;
-        for (int d = 2 * OZ_S - 2; d >= 0; --d) {  // weight 16^-(d+2), smallest first
-            if (d > OZ_S - 1) continue;               // dropped: t + u > S - 1
-            double w = ldexp(1.0, -4 * (d + 2));
-            for (int t = 0; t <= d; ++t) {
-                int u = d - t;
-                int32_t id = pair_tile[((int64_t)(t * OZ_S + u) * nb + P) * nb + Q];
-                int64_t off;
-                if (id >= 0) {
-                    off = (int64_t)id * 16384 + r + c * 128;
-                } else {
-                    id = pair_tile[((int64_t)(u * OZ_S + t) * nb + Q) * nb + P];
-                    off = (int64_t)id * 16384 + c + r * 128;
-                }
-                for (int z = 0; z < chunks; ++z) acc = fma(w, (double)T[(int64_t)z * ntiles * 16384 + off], acc);
+// case: then C_tu = C_ut^T is read from the (u, t) tile at (Q, P)).  Tiles are
+// 128 x 128 FP32, column-major; chunk z of tile id starts at (z ntiles + id)
+// 16384.  Every tile value is an integer below 2^24 in magnitude, so each
+// weight class d = t + u sums exactly in 64-bit integers,
+//   S_d = sum_{t + u = d} sum_z C_tu,z[p, q],
+// and I = sum_{d=0}^{S-1} S_d 16^(S-1-d) (Horner, 128-bit) is the exact
+// digit-sliced sum: G[p, q] = I 2^(e_p + e_q - 4 (S + 1)), rounded once.
+// One CTA per (P, Q) block (P >= Q when sym) and 32-column quarter; thread
+// (r = tid mod 128, c = c0 + tid / 128 + 2k, k < 16) owns 16 entries.  Tiles
+// read transposed are staged through shared memory; the loads of the next
+// tile are issued before the current one is summed.  sym: only p >= q is
+// formed and mirrored; ex / ey: column exponents of X / Y (OZ_NONFINITE
+// marks a column holding an Inf or NaN: its entries are NaN).
+constexpr int OZ_CB_THREADS = 256;
+
+__device__ __forceinline__ int64_t oz_item_base(const int32_t* __restrict__ pair_tile, int64_t ntiles, int64_t nb,
+                                                int64_t P, int64_t Q, int d, int t, int z, bool& tr) {
+    const int u = d - t;
+    int32_t id = pair_tile[((int64_t)(t * OZ_S + u) * nb + P) * nb + Q];
+    tr = false;
+    if (id < 0) {
+        id = pair_tile[((int64_t)(u * OZ_S + t) * nb + Q) * nb + P];
+        tr = true;
+    }
+    return id < 0 ? -1 : ((int64_t)z * ntiles + id) * 16384;
+}
+
+__device__ __forceinline__ void oz_item_load(const float* __restrict__ T, int64_t base, bool tr, int r, int cb,
+                                             int c0, float (&v)[16]) {
+    if (base < 0) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = 0.f;
+    } else if (!tr) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = T[base + r + (int64_t)(cb + 2 * k) * 128];
+    } else {
+        // rows r' of the stored (u, t) tile hold our columns c0 .. c0 + 31 at r' 128 + c
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int f = threadIdx.x + OZ_CB_THREADS * j;
+            const float4 w = *(const float4*)(T + base + (int64_t)(f >> 3) * 128 + c0 + (f & 7) * 4);
+            v[4 * j] = w.x;
+            v[4 * j + 1] = w.y;
+            v[4 * j + 2] = w.z;
+            v[4 * j + 3] = w.w;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(OZ_CB_THREADS) k_oz_combine(const float* __restrict__ T,
+                                                              const int32_t* __restrict__ pair_tile, int64_t ntiles,
+                                                              int chunks, int64_t n, int64_t nb,
+                                                              const int32_t* __restrict__ ex,
+                                                              const int32_t* __restrict__ ey, int sym,
+                                                              double* __restrict__ G, int64_t ldg) {
+    __shared__ float tr_s[128][33];
+    const int c0 = (int)(blockIdx.x & 3) * 32;
+    const int64_t blk = blockIdx.x >> 2;
+    int64_t P, Q;
+    if (sym) {
+        P = 0;
+        while ((P + 1) * (P + 2) / 2 <= blk) ++P;
+        Q = blk - P * (P + 1) / 2;
+    } else {
+        P = blk % nb;
+        Q = blk / nb;
+    }
+    const int r = threadIdx.x & 127;
+    const int cb = c0 + (threadIdx.x >> 7);
+    long long H[16], S[16];
+    unsigned long long L[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) H[k] = 0, L[k] = 0, S[k] = 0;
+    int d = 0, t = 0, z = 0;
+    bool tr;
+    int64_t base = oz_item_base(pair_tile, ntiles, nb, P, Q, d, t, z, tr);
+    float cur[16];
+    oz_item_load(T, base, tr, r, cb, c0, cur);
+    for (;;) {
+        // next item in the order d, t, z
+        int dn = d, tn = t, zn = z + 1;
+        if (zn == chunks) zn = 0, ++tn;
+        if (tn > dn) tn = 0, ++dn;
+        const bool more = dn < OZ_S;
+        bool trn = false;
+        float nxt[16];
+        if (more) {
+            const int64_t bn = oz_item_base(pair_tile, ntiles, nb, P, Q, dn, tn, zn, trn);
+            oz_item_load(T, bn, trn, r, cb, c0, nxt);
+        }
+        if (!tr) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) S[k] += (long long)__float2int_rz(cur[k]);
+        } else {
+            __syncthreads();  // the previous transposed tile has been read
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int f = threadIdx.x + OZ_CB_THREADS * j;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) tr_s[f >> 3][(f & 7) * 4 + e] = cur[4 * j + e];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < 16; ++k) S[k] += (long long)__float2int_rz(tr_s[r][cb - c0 + 2 * k]);
+        }
+        if (dn != d || !more) {
+            // weight class d complete: I = 16 I + S_d
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                H[k] = (long long)(((unsigned long long)H[k] << 4) | (L[k] >> 60));
+                L[k] <<= 4;
+                const unsigned long long l2 = L[k] + (unsigned long long)S[k];
+                H[k] += (S[k] >> 63) + (l2 < L[k] ? 1 : 0);
+                L[k] = l2;
+                S[k] = 0;
             }
         }
-        double g = ldexp(acc, ex[p] + ey[q]);
+        if (!more) break;
+        d = dn, t = tn, z = zn, tr = trn;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) cur[k] = nxt[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int64_t p = P * 128 + r, q = Q * 128 + cb + 2 * k;
+        if (p >= n || q >= n || (sym && p < q)) continue;
+        const int32_t a = ex[p], b = ey[q];
+        const double g = (a == OZ_NONFINITE || b == OZ_NONFINITE) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                                  : fixed128_to_double(H[k], L[k], a + b - 4 * (OZ_S + 1));
         G[p + q * ldg] = g;
         if (sym) G[q + p * ldg] = g;
     }
@@ -159,23 +277,45 @@ size_t oz_gram_ws_bytes(int64_t m, int64_t n) { return oz_plan(m, n, true).total
 size_t oz_gemm_tn_ws_bytes(int64_t m, int64_t n) { return oz_plan(m, n, false).total; }
 
 // Tile list (grouped so that neighbouring CTAs share the Y-row block of a
-// pair) and the (t, u, P, Q) -> tile map, built on the device by one thread in
-// a fixed order (no host copies: the call stays capturable in a CUDA graph).
+// pair) and the (t, u, P, Q) -> tile map, built on the device in a fixed
+// order (no host copies: the call stays capturable in a CUDA graph).  One CTA:
+// the tiles of each (u, Q) are counted, prefix summed in (u, Q) order, and
+// each (u, Q) range is filled by its own thread, so the list is the sequential
+// enumeration u, Q, t, P.
 __global__ void k_oz_tiles(int64_t nb, int64_t np, int sym, int2* __restrict__ tiles, int32_t* __restrict__ map) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    for (int64_t q = 0; q < (int64_t)OZ_S * OZ_S * nb * nb; ++q) map[q] = -1;
-    int32_t k = 0;
-    for (int u = 0; u < OZ_S; ++u)
-        for (int64_t Q = 0; Q < nb; ++Q)
-            for (int t = 0; t < OZ_S; ++t) {
-                if (t + u > OZ_S - 1 || (sym && t > u)) continue;
-                for (int64_t Pb = 0; Pb < nb; ++Pb) {
-                    if (sym && t == u && Pb < Q) continue;
-                    map[((int64_t)(t * OZ_S + u) * nb + Pb) * nb + Q] = k;
-                    tiles[k] = make_int2((int)(t * np + Pb * 128), (int)(u * np + Q * 128));
-                    ++k;
-                }
+    extern __shared__ int32_t oz_cnt[];  // OZ_S * nb + 1
+    const int64_t nuq = (int64_t)OZ_S * nb;
+    for (int64_t q = threadIdx.x; q < (int64_t)OZ_S * OZ_S * nb * nb; q += blockDim.x) map[q] = -1;
+    for (int64_t uq = threadIdx.x; uq < nuq; uq += blockDim.x) {
+        const int u = (int)(uq / nb);
+        const int64_t Q = uq % nb;
+        int32_t c = 0;
+        for (int t = 0; t < OZ_S; ++t) {
+            if (t + u > OZ_S - 1 || (sym && t > u)) continue;
+            c += (int32_t)((sym && t == u) ? nb - Q : nb);
+        }
+        oz_cnt[uq + 1] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        oz_cnt[0] = 0;
+        for (int64_t uq = 0; uq < nuq; ++uq) oz_cnt[uq + 1] += oz_cnt[uq];
+    }
+    __syncthreads();
+    for (int64_t uq = threadIdx.x; uq < nuq; uq += blockDim.x) {
+        const int u = (int)(uq / nb);
+        const int64_t Q = uq % nb;
+        int32_t k = oz_cnt[uq];
+        for (int t = 0; t < OZ_S; ++t) {
+            if (t + u > OZ_S - 1 || (sym && t > u)) continue;
+            for (int64_t Pb = 0; Pb < nb; ++Pb) {
+                if (sym && t == u && Pb < Q) continue;
+                map[((int64_t)(t * OZ_S + u) * nb + Pb) * nb + Q] = k;
+                tiles[k] = make_int2((int)(t * np + Pb * 128), (int)(u * np + Q * 128));
+                ++k;
             }
+        }
+    }
 }
 
 // G = X^T Y (n x n) from the digit planes of X and Y (the same planes when
@@ -194,9 +334,11 @@ static lsq_status oz_run(const double* X, int64_t ldx, const double* Y, int64_t 
     int32_t* map = (int32_t*)(base + P.z_bytes + P.t_bytes + P.tiles_bytes);
     int32_t* ex = (int32_t*)(base + P.z_bytes + P.t_bytes + P.tiles_bytes + P.map_bytes);
     int32_t* ey = sym ? ex : (int32_t*)((char*)ex + eb);
-    k_oz_tiles<<<1, 1, 0, st>>>(P.nb, P.np, sym ? 1 : 0, tiles, map);
+    const size_t tsm = sizeof(int32_t) * (size_t)(OZ_S * P.nb + 1);
+    if (tsm > 48 * 1024) return LSQ_ERR_ARG;
+    k_oz_tiles<<<1, 256, tsm, st>>>(P.nb, P.np, sym ? 1 : 0, tiles, map);
     LSQ_LAUNCH_CHECK();
-    dim3 gs((unsigned)std::min<int64_t>(ceil_div(P.ldz, 256), 64), (unsigned)P.np);
+    dim3 gs((unsigned)std::min<int64_t>(ceil_div(P.ldz, 256 * 4), 64), (unsigned)P.np);
     k_oz_colexp<<<(unsigned)n, 256, 0, st>>>(X, m, ldx, ex);
     LSQ_LAUNCH_CHECK();
     k_oz_slice<<<gs, 256, 0, st>>>(X, m, n, ldx, ex, P.np, P.ldz, Zx);
@@ -210,7 +352,8 @@ static lsq_status oz_run(const double* X, int64_t ldx, const double* Y, int64_t 
     lsq_status r = launch_tc_tiles_fp8(Zx, P.ldz, OZ_S * P.np, Zy, P.ldz, OZ_S * P.np, P.ldz, P.kchunk, tiles,
                                        P.ntiles, T, err, st);
     if (r != LSQ_OK) return r;
-    k_oz_combine<<<(unsigned)std::min<int64_t>(ceil_div(n * n, 256), 16384), 256, 0, st>>>(
+    const int64_t cblocks = (sym ? P.nb * (P.nb + 1) / 2 : P.nb * P.nb) * 4;
+    k_oz_combine<<<(unsigned)cblocks, OZ_CB_THREADS, 0, st>>>(
         T, map, P.ntiles, P.chunks, n, P.nb, ex, ey, sym ? 1 : 0, G, ldg);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;

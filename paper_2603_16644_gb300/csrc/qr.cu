@@ -2,10 +2,11 @@
 // FP64 arithmetic, R only, then promotion to FP64 and removal of the
 // column scaling.  Blocked Householder QR with the compact WY form
 // (Schreiber & Van Loan 1989):
-//   panel of QNB columns in one CTA (Householder vectors as in Golub & Van
-//   Loan Alg. 5.1.1, which maps x to +||x|| e1, so diag(R) >= 0), the
-//   triangular factor T of  H_1...H_nb = I - V T V^T, and the trailing update
-//   C <- (I - V T^T V^T) C as two contractions (W = V^T C, C -= V (T^T W)).
+//   panel of QNB columns in a cluster of CTAs (Householder vectors as in
+//   Golub & Van Loan Alg. 5.1.1, which maps x to +||x|| e1, so diag(R) >= 0),
+//   the triangular factor T of  H_1...H_nb = I - V T V^T, and the trailing
+//   update C <- (I - V T^T V^T) C as W = V^T C, C -= V (T^T W) in one fused
+//   cluster kernel.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -182,7 +183,8 @@ constexpr int QCT = 256;
 template <typename T, int QCL>
 __global__ void __launch_bounds__(QCT)
     k_qr_panel_cl(T* __restrict__ W, int64_t ld, int64_t s, int64_t k0, int nb, T* __restrict__ beta_out,
-                  T* __restrict__ Tm, T* __restrict__ V, int64_t ldv) {
+                  T* __restrict__ Tm, T* __restrict__ V, int64_t ldv, const T* __restrict__ Vp, int64_t ldvp,
+                  const T* __restrict__ Tp) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char cl_raw[];
@@ -190,9 +192,9 @@ __global__ void __launch_bounds__(QCT)
     __shared__ T all_part[2][QCL][QNB];  // per rank: d_c (sigma at c = j)
     __shared__ T all_row[2][QNB];        // the diagonal row: x1 at j, a_c[j] at c > j
     __shared__ T part[QCT / 32][QNB];
-    __shared__ T wsh[QNB];
     __shared__ T Ts[QNB][QNB + 1];
     __shared__ T bsh[QNB];
+    __shared__ T Wr[QNB][QNB + 1];  // this CTA's partial V_p^T C (read by the whole cluster)
     const int rank = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rows = (int)(s - k0);
@@ -203,29 +205,164 @@ __global__ void __launch_bounds__(QCT)
     T* Yall = P + (int64_t)Rp * QNB;  // [QCL][QNB][QNB + 1], rank 0 only
     const int chunk = (R + (QCT / 32) - 1) / (QCT / 32);
     const int g0 = warp * chunk, g1 = min(nloc, g0 + chunk);  // this warp's rows
-    for (int c = 0; c < QNB; ++c)
-        for (int i = tid; i < R; i += QCT)
-            P[c * Rp + i] = (i < nloc && c < nb) ? W[(k0 + r0 + i) + (k0 + c) * ld] : (T)0;
+    // loads of all columns of a row in flight before the stores
+    for (int i = tid; i < R; i += QCT) {
+        T x[QNB];
+#pragma unroll
+        for (int c = 0; c < QNB; ++c) x[c] = (i < nloc && c < nb) ? W[(k0 + r0 + i) + (k0 + c) * ld] : (T)0;
+#pragma unroll
+        for (int c = 0; c < QNB; ++c) P[c * Rp + i] = x[c];
+    }
     __syncthreads();
+    if (Vp != nullptr) {
+        // The previous panel's reflectors applied to this panel's columns,
+        // C <- (I - V_p T_p^T V_p^T) C over rows k0 - QNB .. s - 1 (V_p: QNB
+        // columns, ld ldvp, row 0 at k0 - QNB): this CTA's rows in shared
+        // memory, the QNB rows above the panel by rank 0 from global memory.
+        T* Vl = Yall;                      // [QNB][Rp]: rows QNB + r0 + i of V_p
+        T* Wk = Yall + (int64_t)QNB * Rp;  // [4][QNB][QNB + 1] row-group partials, then W and W2
+        T* Ct = Wk + 4 * QNB * (QNB + 1);  // rank 0: [QNB][QNB + 1] the rows above, then their V_p rows
+        T* Vt = Ct + QNB * (QNB + 1);
+        for (int i = tid; i < R; i += QCT) {
+            T x[QNB];
+#pragma unroll
+            for (int c = 0; c < QNB; ++c) x[c] = i < nloc ? Vp[(QNB + r0 + i) + c * ldvp] : (T)0;
+#pragma unroll
+            for (int c = 0; c < QNB; ++c) Vl[c * Rp + i] = x[c];
+        }
+        if (rank == 0 && tid < QNB) {
+            T x[QNB], v[QNB];
+#pragma unroll
+            for (int c = 0; c < QNB; ++c) {
+                x[c] = c < nb ? W[(k0 - QNB + tid) + (k0 + c) * ld] : (T)0;
+                v[c] = Vp[tid + c * ldvp];
+            }
+#pragma unroll
+            for (int c = 0; c < QNB; ++c) {
+                Ct[tid * (QNB + 1) + c] = x[c];
+                Vt[tid * (QNB + 1) + c] = v[c];
+            }
+        }
+        __syncthreads();
+        {
+            // partial W = V_p^T C: 4 row groups of 64 threads, 4 x 4 blocks
+            const int kg = tid >> 6, tl = tid & 63, tp = tl & 7, tq = tl >> 3;
+            const int span = (R + 3) / 4;
+            const int i0 = kg * span, i1 = min(nloc, i0 + span);
+            T acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+            for (int i = i0; i < i1; ++i) {
+                T v[4], c[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) v[a] = Vl[(4 * tp + a) * Rp + i];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) c[b] = P[(4 * tq + b) * Rp + i];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = fma(v[a], c[b], acc[a][b]);
+            }
+            if (rank == 0 && kg == 0)
+                for (int i = 0; i < QNB; ++i) {
+                    T v[4], c[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) v[a] = Vt[i * (QNB + 1) + 4 * tp + a];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) c[b] = Ct[i * (QNB + 1) + 4 * tq + b];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(v[a], c[b], acc[a][b]);
+                }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) Wk[(kg * QNB + 4 * tp + a) * (QNB + 1) + 4 * tq + b] = acc[a][b];
+        }
+        __syncthreads();
+        for (int q = tid; q < QNB * QNB; q += QCT) {
+            const int p = q >> 5, c = q & 31;
+            Wr[p][c] = ((Wk[p * (QNB + 1) + c] + Wk[(QNB + p) * (QNB + 1) + c]) + Wk[(2 * QNB + p) * (QNB + 1) + c]) +
+                       Wk[(3 * QNB + p) * (QNB + 1) + c];
+        }
+        cluster.sync();
+        // W: the partials of every rank in rank order (the column loop's
+        // cluster barriers keep them in place until every CTA has read them)
+        T* Wf = Wk;                     // [QNB][QNB + 1]
+        T* W2 = Wk + QNB * (QNB + 1);   // [QNB][QNB]
+        for (int q = tid; q < QNB * QNB; q += QCT) {
+            const int p = q >> 5, c = q & 31;
+            T w = (T)0;
+            for (int r = 0; r < QCL; ++r) w += cluster.map_shared_rank(&Wr[0][0], r)[p * (QNB + 1) + c];
+            Wf[p * (QNB + 1) + c] = w;
+        }
+        for (int q = tid; q < QNB * QNB; q += QCT) Ts[q & 31][q >> 5] = Tp[q];  // Ts[k][p] = T_p[k, p]
+        __syncthreads();
+        for (int q = tid; q < QNB * QNB; q += QCT) {
+            const int p = q >> 5, c = q & 31;
+            T w = (T)0;
+            for (int kk = 0; kk <= p; ++kk) w = fma(Ts[kk][p], Wf[kk * (QNB + 1) + c], w);
+            W2[p * QNB + c] = w;  // (T_p^T W)[p, c]
+        }
+        __syncthreads();
+        // C -= V_p W2, one row per thread
+        for (int i = tid; i < nloc; i += QCT) {
+            T a[QNB];
+#pragma unroll
+            for (int c = 0; c < QNB; ++c) a[c] = P[c * Rp + i];
+            for (int p = 0; p < QNB; ++p) {
+                const T v = Vl[p * Rp + i];
+#pragma unroll
+                for (int c = 0; c < QNB; ++c) a[c] = fma(-v, W2[p * QNB + c], a[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < QNB; ++c) P[c * Rp + i] = a[c];
+        }
+        if (rank == 0 && tid < QNB) {
+            const int64_t gi = k0 - QNB + tid;
+            T a[QNB];
+#pragma unroll
+            for (int c = 0; c < QNB; ++c) a[c] = Ct[tid * (QNB + 1) + c];
+            for (int p = 0; p < QNB; ++p) {
+                const T v = Vt[tid * (QNB + 1) + p];
+#pragma unroll
+                for (int c = 0; c < QNB; ++c) a[c] = fma(-v, W2[p * QNB + c], a[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < QNB; ++c)
+                if (c < nb) W[gi + (k0 + c) * ld] = a[c];
+        }
+        __syncthreads();
+    }
+    // partial dots of column j over this warp's rows strictly below row j
+    // (lane = column c >= j): sum x_j[i] a_c[i]; sigma at c = j
+    auto dots = [&](int j) -> T {
+        if (!(lane >= j && lane < nb)) return (T)0;
+        const T* x = P + j * Rp;
+        const T* a = P + lane * Rp;
+        T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+        int i = max(max(j + 1 - r0, 0), g0);
+        for (; i + 4 <= g1; i += 4) {
+            a0 = fma(x[i], a[i], a0);
+            a1 = fma(x[i + 1], a[i + 1], a1);
+            a2 = fma(x[i + 2], a[i + 2], a2);
+            a3 = fma(x[i + 3], a[i + 3], a3);
+        }
+        for (; i < g1; ++i) a0 = fma(x[i], a[i], a0);
+        return (a0 + a1) + (a2 + a3);
+    };
+    // Every per-row step (scaling of v, the update, the next column's dots)
+    // stays within the warp's own rows, so a column needs one CTA barrier
+    // (the partial dots) and one cluster barrier (their exchange).
+    T acc = dots(0);
     for (int jj = 0; jj < nb; ++jj) {
         const int buf = jj & 1;
         const int owner = (int)(jj / R);
         T* xj = P + jj * Rp;
         T* ac = P + lane * Rp;
-        const int ib = max(jj + 1 - r0, 0);  // first owned row strictly below the diagonal
-        T acc = (T)0;
-        if (lane >= jj && lane < nb) {
-            T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
-            int i = max(ib, g0);
-            for (; i + 4 <= g1; i += 4) {
-                a0 = fma(xj[i], ac[i], a0);
-                a1 = fma(xj[i + 1], ac[i + 1], a1);
-                a2 = fma(xj[i + 2], ac[i + 2], a2);
-                a3 = fma(xj[i + 3], ac[i + 3], a3);
-            }
-            for (; i < g1; ++i) a0 = fma(xj[i], ac[i], a0);
-            acc = (a0 + a1) + (a2 + a3);
-        }
         part[warp][lane] = acc;
         __syncthreads();
         if (warp == 0) {
@@ -252,18 +389,23 @@ __global__ void __launch_bounds__(QCT)
             b = (T)2 * v1 * v1 / (sigma + v1 * v1);
             scale = true;
         }
-        if (warp == 0 && lane > jj && lane < nb) {
+        T wc = (T)0;
+        if (lane > jj && lane < nb) {
             T d = (T)0;
             for (int q = 0; q < QCL; ++q) d += all_part[buf][q][lane];
-            wsh[lane] = b * (all_row[buf][lane] + (scale ? d / v1 : (T)0));
+            wc = b * (all_row[buf][lane] + (scale ? d / v1 : (T)0));
         }
         if (tid == 0) bsh[jj] = b;  // identical in every CTA of the cluster
-        // v below the diagonal
+        if (rank == owner && tid == 0) {
+            xj[jj - r0] = mu;  // the diagonal entry is not read again (v there is 1)
+            beta_out[k0 + jj] = b;
+        }
+        // v below the diagonal, this warp's rows
+        const int ib = max(jj + 1 - r0, 0);
         if (scale)
-            for (int i = ib + tid; i < nloc; i += QCT) xj[i] = xj[i] / v1;
-        __syncthreads();
+            for (int i = max(ib, g0) + lane; i < g1; i += 32) xj[i] = xj[i] / v1;
+        __syncwarp();
         if (lane > jj && lane < nb && b != (T)0) {
-            const T wc = wsh[lane];
             const int id = max(jj - r0, 0);  // owned rows >= the diagonal
             const int dr = jj - r0;           // local index of the diagonal row
             int i = max(id, g0);
@@ -284,13 +426,10 @@ __global__ void __launch_bounds__(QCT)
                 ac[i] = fma(-wc, vi, ac[i]);
             }
         }
-        __syncthreads();
-        if (rank == owner && tid == 0) {
-            xj[jj - r0] = mu;
-            beta_out[k0 + jj] = b;
-        }
-        __syncthreads();
+        __syncwarp();
+        acc = jj + 1 < nb ? dots(jj + 1) : (T)0;
     }
+    __syncthreads();
     // write R / v back to W and the explicit V (0 above, 1 on the diagonal)
     for (int c = 0; c < QNB; ++c)
         for (int i = tid; i < nloc; i += QCT) {
@@ -354,16 +493,187 @@ __global__ void __launch_bounds__(QCT)
     cluster.sync();
 }
 
-// W2 = T^T Wp  (nb x nt), T upper (ld QNB), Wp (nb x nt, ld nb).
+// ---------------------------------------------------------------------------
+// Trailing update C <- (I - V T^T V^T) C in one launch.  A cluster of QUC CTAs
+// owns a block of 32 columns of C; its CTAs take the 128-row sub-tiles of the
+// block in turn (rank, rank + QUC, ...).  Per CTA:
+//   1. W_r = V^T C over its sub-tiles (32 x 32), four row groups of 64 threads
+//      with 4 x 4 register tiles, summed in a fixed order;
+//   2. W = sum_r W_r over the cluster (rank order, read through distributed
+//      shared memory), W2 = T^T W (T upper, so W2[p] uses T[0..p][p]);
+//   3. C -= V W2 over its sub-tiles, written back coalesced.
+// Sub-tiles are staged in shared memory as [32 columns][128 rows] with the
+// 4-element groups of a row XOR-swizzled by (column / 4), so that both the
+// transposing stores and the 4-wide reads of either phase are free of bank
+// conflicts.  V columns >= nb load as zero (so do rows >= rows, columns >= nt).
+// ---------------------------------------------------------------------------
+constexpr int QUC = 8;    // CTAs per cluster
+constexpr int QUR = 128;  // rows per sub-tile
+constexpr int QUT = 256;  // threads per CTA
+
 template <typename T>
-__global__ void k_qr_tw(const T* __restrict__ Tm, const T* __restrict__ Wp, int nb, int64_t nt, T* __restrict__ W2) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nb * nt) return;
-    int p = (int)(q % nb);
-    int64_t c = q / nb;
-    T t = (T)0;
-    for (int k = 0; k <= p; ++k) t = fma(Tm[k + p * QNB], Wp[k + c * nb], t);
-    W2[p + c * nb] = t;
+struct alignas(4 * sizeof(T)) QuVec {
+    T v[4];
+};
+
+// position of (column c, row i) in a swizzled [32][QUR] sub-tile
+__device__ __forceinline__ int qu_idx(int c, int i) { return c * QUR + ((((i >> 2) ^ (c >> 2)) << 2) | (i & 3)); }
+
+template <typename T>
+static size_t qu_smem_bytes() {
+    // V and C sub-tiles (the row-group partials of phase 1 reuse them), the
+    // cluster-visible partial W_r, the summed W, W2 and T
+    return sizeof(T) * (2 * 32 * QUR + 3 * 32 * 33 + 32 * 32);
+}
+
+// A sub-tile in registers: thread t holds row t mod QUR of columns
+// t / QUR + 2 j, j < 16, of V and C (consecutive threads read consecutive rows).
+template <typename T>
+struct QuRegs {
+    T v[16], c[16];
+};
+
+template <typename T>
+__device__ __forceinline__ void qu_fetch(QuRegs<T>& rg, const T* __restrict__ V, int64_t ldv, int nb,
+                                         const T* __restrict__ C, int64_t ldc, int64_t ncols, int64_t rows,
+                                         int64_t r0) {
+    const int i = threadIdx.x & (QUR - 1), c0 = threadIdx.x >> 7;
+    const int64_t gi = r0 + i;
+    const bool ok = gi < rows;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int c = c0 + 2 * j;
+        rg.v[j] = (ok && c < nb) ? V[gi + c * ldv] : (T)0;
+        rg.c[j] = (ok && c < ncols) ? C[gi + c * ldc] : (T)0;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void qu_put(const QuRegs<T>& rg, T* __restrict__ Vs, T* __restrict__ Cs) {
+    const int i = threadIdx.x & (QUR - 1), c0 = threadIdx.x >> 7;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        Vs[qu_idx(c0 + 2 * j, i)] = rg.v[j];
+        Cs[qu_idx(c0 + 2 * j, i)] = rg.c[j];
+    }
+}
+
+template <typename T>
+__global__ void __cluster_dims__(QUC, 1, 1) __launch_bounds__(QUT)
+    k_qr_update(T* __restrict__ C, int64_t ldc, int64_t nt, const T* __restrict__ V, int64_t ldv, int nb,
+                const T* __restrict__ Tm, int64_t rows) {
+    extern __shared__ __align__(16) unsigned char qu_raw[];
+    T* Vs = (T*)qu_raw;
+    T* Cs = Vs + 32 * QUR;
+    T* Wr = Cs + 32 * QUR;  // [32][33] this CTA's partial, read by the whole cluster
+    T* Wf = Wr + 32 * 33;   // [32][33] the cluster sum
+    T* Ts = Wf + 32 * 33;   // [32][33] T
+    T* W2 = Ts + 32 * 33;   // [32][32] T^T W
+    T* Wk = Vs;             // [4][32][33] row-group partials (after phase 1)
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int64_t c0 = (int64_t)(blockIdx.x / QUC) * 32;
+    const int64_t ncols = min64(32, nt - c0);
+    T* Cb = C + c0 * ldc;
+    const int tid = threadIdx.x;
+    const int64_t nsub = (rows + QUR - 1) / QUR;
+    for (int q = tid; q < 32 * 32; q += QUT) Ts[(q & 31) * 33 + (q >> 5)] = Tm[q];  // Ts[k][p] = T[k, p]
+
+    // 1. W_r = V^T C over this CTA's sub-tiles (the next sub-tile is fetched
+    // into registers while the current one is used)
+    QuRegs<T> rg;
+    if (rank < nsub) qu_fetch<T>(rg, V, ldv, nb, Cb, ldc, ncols, rows, (int64_t)rank * QUR);
+    {
+        const int kg = tid >> 6, tl = tid & 63, tp = tl & 7, tq = tl >> 3;
+        T acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+        for (int64_t sb = rank; sb < nsub; sb += QUC) {
+            __syncthreads();
+            qu_put<T>(rg, Vs, Cs);
+            __syncthreads();
+            if (sb + QUC < nsub) qu_fetch<T>(rg, V, ldv, nb, Cb, ldc, ncols, rows, (sb + QUC) * QUR);
+#pragma unroll 2
+            for (int s4 = 0; s4 < QUR / 16; ++s4) {
+                const int i = kg * (QUR / 4) + 4 * s4;
+                QuVec<T> va[4], cb[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) va[a] = *(const QuVec<T>*)(Vs + qu_idx(4 * tp + a, i));
+#pragma unroll
+                for (int b = 0; b < 4; ++b) cb[b] = *(const QuVec<T>*)(Cs + qu_idx(4 * tq + b, i));
+#pragma unroll
+                for (int w = 0; w < 4; ++w)
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(va[a].v[w], cb[b].v[w], acc[a][b]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) Wk[(kg * 32 + 4 * tp + a) * 33 + 4 * tq + b] = acc[a][b];
+        __syncthreads();
+        for (int q = tid; q < 32 * 32; q += QUT) {
+            const int p = q >> 5, c = q & 31;
+            Wr[p * 33 + c] = ((Wk[p * 33 + c] + Wk[(32 + p) * 33 + c]) + Wk[(64 + p) * 33 + c]) + Wk[(96 + p) * 33 + c];
+        }
+    }
+    // the first sub-tile of step 3 (C is not written before step 3)
+    if (rank < nsub) qu_fetch<T>(rg, V, ldv, nb, Cb, ldc, ncols, rows, (int64_t)rank * QUR);
+    // 2. W = sum over the cluster, W2 = T^T W
+    cluster.sync();
+    for (int q = tid; q < 32 * 32; q += QUT) {
+        const int p = q >> 5, c = q & 31;
+        T w = (T)0;
+        for (int r = 0; r < QUC; ++r) w += cluster.map_shared_rank(Wr, r)[p * 33 + c];
+        Wf[p * 33 + c] = w;
+    }
+    // this CTA's reads of the other CTAs' partials are done; they may exit
+    // once every CTA has arrived (waited for at the end)
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    __syncthreads();
+    for (int q = tid; q < 32 * 32; q += QUT) {
+        const int p = q >> 5, c = q & 31;
+        T w = (T)0;
+        for (int k = 0; k <= p; ++k) w = fma(Ts[k * 33 + p], Wf[k * 33 + c], w);
+        W2[p * 32 + c] = w;
+    }
+    // 3. C -= V W2 over this CTA's sub-tiles
+    {
+        const int ti = tid & 31, tq = tid >> 5;  // rows 4 ti .. 4 ti + 3, columns 4 tq .. 4 tq + 3
+        for (int64_t sb = rank; sb < nsub; sb += QUC) {
+            __syncthreads();
+            qu_put<T>(rg, Vs, Cs);
+            __syncthreads();
+            if (sb + QUC < nsub) qu_fetch<T>(rg, V, ldv, nb, Cb, ldc, ncols, rows, (sb + QUC) * QUR);
+            QuVec<T> cv[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) cv[b] = *(const QuVec<T>*)(Cs + qu_idx(4 * tq + b, 4 * ti));
+#pragma unroll 4
+            for (int p = 0; p < 32; ++p) {
+                const QuVec<T> v = *(const QuVec<T>*)(Vs + qu_idx(p, 4 * ti));
+                const QuVec<T> w = *(const QuVec<T>*)(W2 + p * 32 + 4 * tq);
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) cv[b].v[a] = fma(-v.v[a], w.v[b], cv[b].v[a]);
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) *(QuVec<T>*)(Cs + qu_idx(4 * tq + b, 4 * ti)) = cv[b];
+            __syncthreads();
+            const int64_t r0 = sb * QUR;
+            for (int e = tid; e < 32 * QUR; e += QUT) {
+                const int i = e & (QUR - 1), c = e >> 7;
+                if (r0 + i < rows && c < ncols) Cb[(r0 + i) + c * ldc] = Cs[qu_idx(c, i)];
+            }
+        }
+    }
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 template <typename TI, typename T>
@@ -395,54 +705,75 @@ __global__ void k_check_diag(const double* __restrict__ Rs, int64_t n, int64_t l
     if (!(d > 0.0) || !isfinite(d)) set_info_once(info, (int32_t)(j + 1));
 }
 
+// Dynamic shared memory of the cluster panel: the local panel and, after it,
+// rank 0's V^T V partials of every rank or (fused: the previous panel's
+// update applied first) the local rows of V_p and the row-group partials.
 template <typename T>
-static size_t qr_cluster_smem(int64_t rows, int qcl) {
-    return sizeof(T) * ((size_t)(ceil_div(rows, qcl) | 1) * QNB + (size_t)qcl * QNB * (QNB + 1));
+static size_t qr_cluster_smem(int64_t rows, int qcl, bool fused) {
+    const size_t Rp = (size_t)(ceil_div(rows, qcl) | 1);
+    const size_t yall = (size_t)qcl * QNB * (QNB + 1);
+    const size_t pre = Rp * QNB + (size_t)6 * QNB * (QNB + 1);
+    return sizeof(T) * (Rp * QNB + (fused ? std::max(yall, pre) : yall));
 }
+
+struct QrCluster {
+    int qcl = 0;         // CTAs per cluster, 0: single-CTA panel kernel
+    bool fused = false;  // each panel applies the previous panel's update to its own columns
+};
 
 // 16 CTAs per cluster where the device can schedule that with the panel's
 // shared memory (non-portable size), else 8; 0 if neither fits (the
-// single-CTA panel kernel then runs).  Decided once per precision and size.
+// single-CTA panel kernel then runs).  The fused form (each panel applies the
+// previous panel's update to its own columns) is preferred where its shared
+// memory fits.  Decided once per precision and size.
 template <typename T>
-static int qr_cluster_size_query(int64_t s) {
+static QrCluster qr_cluster_query(int64_t s) {
     const size_t lim = 200 * 1024;
-    for (int qcl : {16, 8}) {
-        const size_t sm = qr_cluster_smem<T>(s, qcl);
-        if (sm > lim) continue;
-        auto kern = qcl == 16 ? k_qr_panel_cl<T, 16> : k_qr_panel_cl<T, 8>;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
-            (qcl > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+    for (bool fused : {true, false})
+        for (int qcl : {16, 8}) {
+            const size_t sm = qr_cluster_smem<T>(s, qcl, fused);
+            if (sm > lim) continue;
+            auto kern = qcl == 16 ? k_qr_panel_cl<T, 16> : k_qr_panel_cl<T, 8>;
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+                (qcl > 8 &&
+                 cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+                cudaGetLastError();
+                continue;
+            }
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = qcl;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(qcl);
+            cfg.blockDim = dim3(QCT);
+            cfg.dynamicSmemBytes = sm;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters >= 1) {
+                QrCluster q;
+                q.qcl = qcl;
+                q.fused = fused;
+                return q;
+            }
             cudaGetLastError();
-            continue;
         }
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = qcl;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(qcl);
-        cfg.blockDim = dim3(QCT);
-        cfg.dynamicSmemBytes = sm;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters >= 1) return qcl;
-        cudaGetLastError();
-    }
-    return 0;
+    return QrCluster();
 }
 
 template <typename T>
-static int qr_cluster_size(int64_t s) {
+static QrCluster qr_cluster_size(int64_t s) {
     static std::mutex mu;
     static int64_t last_s = -1;
-    static int last_dev = -1, last_q = 0;
+    static int last_dev = -1;
+    static QrCluster last_q;
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(mu);
     if (s != last_s || dev != last_dev) {
-        last_q = qr_cluster_size_query<T>(s);
+        last_q = qr_cluster_query<T>(s);
         last_s = s;
         last_dev = dev;
     }
@@ -451,7 +782,7 @@ static int qr_cluster_size(int64_t s) {
 
 template <typename T>
 static cudaError_t qr_launch_cluster(int qcl, size_t smem, cudaStream_t st, T* W, int64_t s, int64_t k0, int nb,
-                                     T* beta, T* Tm, T* V, int64_t rows) {
+                                     T* beta, T* Tm, T* V, int64_t rows, const T* Vp, int64_t ldvp, const T* Tp) {
     auto kern = qcl == 16 ? k_qr_panel_cl<T, 16> : k_qr_panel_cl<T, 8>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -467,18 +798,18 @@ static cudaError_t qr_launch_cluster(int qcl, size_t smem, cudaStream_t st, T* W
     cfg.stream = st;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, W, s, s, k0, nb, beta, Tm, V, rows);
+    return cudaLaunchKernelEx(&cfg, kern, W, s, s, k0, nb, beta, Tm, V, rows, Vp, ldvp, Tp);
 }
 
-// V and T are double-buffered by panel parity; the trailing update of a panel
-// has its own scratch for the narrow part (the next panel's columns) and the
-// wide part (the rest), which may run at the same time.
+// V and T are double-buffered by panel parity (a panel's V and T are read by
+// its trailing update and by the next panel while the next panel writes the
+// other buffer).
 struct QrLayout {
-    size_t w, beta, tm[2], v[2], wp[2], w2[2], gemm[2];
+    size_t w, beta, tm[2], v[2];
     size_t total;
 };
 
-static QrLayout qr_layout(int64_t s, int64_t n, int es, int num_sms) {
+static QrLayout qr_layout(int64_t s, int64_t n, int es) {
     QrLayout L;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
@@ -487,28 +818,22 @@ static QrLayout qr_layout(int64_t s, int64_t n, int es, int num_sms) {
     for (int b = 0; b < 2; ++b) {
         L.tm[b] = take((size_t)QNB * QNB * es);
         L.v[b] = take((size_t)s * QNB * es);
-        L.wp[b] = take((size_t)QNB * n * es);
-        L.w2[b] = take((size_t)QNB * n * es);
-        L.gemm[b] = take((size_t)64 * QNB * n * es + 256);  // at most 64 split partials of nb x nt
     }
-    (void)num_sms;
     L.total = off;
     return L;
 }
 
-// C (rows x nt, ld s) <- (I - V T^T V^T) C, as W = V^T C, W2 = T^T W, C -= V W2.
+// C (rows x nt, ld s) <- (I - V T^T V^T) C
 template <typename T>
-static lsq_status qr_apply(const T* V, const T* Tm, int nb, int64_t rows, T* C, int64_t s, int64_t nt, T* Wp, T* W2,
-                           void* gws, int sms, cudaStream_t st) {
+static lsq_status qr_apply(const T* V, const T* Tm, int nb, int64_t rows, T* C, int64_t s, int64_t nt,
+                           cudaStream_t st) {
     if (nt <= 0) return LSQ_OK;
-    const int accp = sizeof(T) == 8 ? LSQ_FP64 : LSQ_FP32;
-    GemmPlan gp = plan_gemm_kmajor(nb, nt, rows, false, accp, sms);
-    lsq_status r = launch_gemm_kmajor(gp, V, accp, rows, C, accp, s, Wp, nb, gws, st);
-    if (r != LSQ_OK) return r;
-    k_qr_tw<T><<<(unsigned)ceil_div(nb * nt, 256), 256, 0, st>>>(Tm, Wp, nb, nt, W2);
+    const size_t sm = qu_smem_bytes<T>();
+    LSQ_CUDA_TRY(cudaFuncSetAttribute(k_qr_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const unsigned grid = (unsigned)(ceil_div(nt, 32) * QUC);
+    k_qr_update<T><<<grid, QUT, sm, st>>>(C, s, nt, V, rows, nb, Tm, rows);
     LSQ_LAUNCH_CHECK();
-    // C -= V W2:  P(i,p) = V[i + p rows],  Q(c,p) = W2[p + c nb]
-    return rank_update_ext<T>(C, s, V, 1, rows, W2, nb, 1, rows, nt, nb, false, nullptr, st);
+    return LSQ_OK;
 }
 
 // Internal streams for the look-ahead QR (one pair per device): panels on a
@@ -536,15 +861,14 @@ static QrStreams* qr_streams() {
 
 size_t qr_ws_bytes(int64_t s, int64_t n, int prec) {
     int es = prec == LSQ_FP64 ? 8 : 4;
-    return qr_layout(s, n, es, device_sm_count()).total + 256;
+    return qr_layout(s, n, es).total + 256;
 }
 
 template <typename T>
 static lsq_status qr_run(const void* As, int64_t s, int64_t n, int64_t ldas, int as_prec, const int32_t* colexp,
                          double* Rs, int64_t ldr, int32_t* info, void* ws, size_t ws_bytes, cudaStream_t st) {
     int es = sizeof(T);
-    int sms = device_sm_count();
-    QrLayout L = qr_layout(s, n, es, sms);
+    QrLayout L = qr_layout(s, n, es);
     char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
     if (!ws || L.total + ((char*)base - (char*)ws) > ws_bytes) return LSQ_ERR_NOMEM;
     T* W = (T*)(base + L.w);
@@ -587,7 +911,12 @@ static lsq_status qr_run(const void* As, int64_t s, int64_t n, int64_t ldas, int
         sl = qs->lo;
     }
     lsq_status r = LSQ_OK;
-    const int qcl = qr_cluster_size<T>(s);
+    const QrCluster qc = qr_cluster_size<T>(s);
+    const int qcl = qc.qcl;
+    // the previous panel's V and T when this panel applies its update itself
+    const T* Vprev = nullptr;
+    const T* Tprev = nullptr;
+    int64_t ldvprev = 0;
     int k = 0;
     for (int64_t k0 = 0; k0 < n && r == LSQ_OK; k0 += QNB, ++k) {
         const int b = k & 1;
@@ -595,13 +924,14 @@ static lsq_status qr_run(const void* As, int64_t s, int64_t n, int64_t ldas, int
         int64_t rows = s - k0;
         T* Tm = (T*)(base + L.tm[b]);
         T* V = (T*)(base + L.v[b]);
-        const size_t clsm = qcl > 0 ? qr_cluster_smem<T>(rows, qcl) : 0;
+        const size_t clsm = qcl > 0 ? qr_cluster_smem<T>(rows, qcl, qc.fused) : 0;
         // Householder panel: sum over its columns of 4 (rows - j)(nb - j) flops
         double pflops = 0.0;
         for (int j = 0; j < nb; ++j) pflops += 4.0 * (double)(rows - j) * (double)(nb - j);
         stage_mark(ST_K_QRPANEL, true, sh);
         if (qcl > 0) {
-            if (qr_launch_cluster<T>(qcl, clsm, sh, W, s, k0, nb, beta, Tm, V, rows) != cudaSuccess) {
+            if (qr_launch_cluster<T>(qcl, clsm, sh, W, s, k0, nb, beta, Tm, V, rows, Vprev, ldvprev, Tprev) !=
+                cudaSuccess) {
                 r = LSQ_ERR_CUDA;
                 break;
             }
@@ -618,29 +948,35 @@ static lsq_status qr_run(const void* As, int64_t s, int64_t n, int64_t ldas, int
         if (nt <= 0) break;
         const int64_t nn = std::min<int64_t>(QNB, nt), nw = nt - nn;  // narrow / wide columns
         T* C = W + k0 + (k0 + nb) * s;
+        // the next panel's columns (narrow part): by the next panel kernel
+        // itself when fused (a full panel only: V then has QNB columns), else
+        // a separate update on the panel stream
+        const bool fuse_next = qcl > 0 && qc.fused && nb == QNB;
         if (qs) {
             // the wide part on the low-priority stream, after this panel
             if (cudaEventRecord(ev_p, sh) != cudaSuccess || cudaStreamWaitEvent(sl, ev_p, 0) != cudaSuccess) {
                 r = LSQ_ERR_CUDA;
                 break;
             }
-            r = qr_apply<T>(V, Tm, nb, rows, C + nn * s, s, nw, (T*)(base + L.wp[1]), (T*)(base + L.w2[1]),
-                            base + L.gemm[1], sms, sl);
+            r = qr_apply<T>(V, Tm, nb, rows, C + nn * s, s, nw, sl);
             if (r != LSQ_OK || cudaEventRecord(ev_w[b], sl) != cudaSuccess) {
                 r = r != LSQ_OK ? r : LSQ_ERR_CUDA;
                 break;
             }
-            // the next panel's columns also hold the previous panel's wide update
+            // the next panel's columns also hold the previous panel's wide
+            // update, and the next panel overwrites that update's V and T
             if (k >= 1 && cudaStreamWaitEvent(sh, ev_w[b ^ 1], 0) != cudaSuccess) {
                 r = LSQ_ERR_CUDA;
                 break;
             }
-            r = qr_apply<T>(V, Tm, nb, rows, C, s, nn, (T*)(base + L.wp[0]), (T*)(base + L.w2[0]),
-                            base + L.gemm[0], sms, sh);
+            if (!fuse_next) r = qr_apply<T>(V, Tm, nb, rows, C, s, nn, sh);
         } else {
-            r = qr_apply<T>(V, Tm, nb, rows, C, s, nt, (T*)(base + L.wp[0]), (T*)(base + L.w2[0]),
-                            base + L.gemm[0], sms, st);
+            r = fuse_next ? qr_apply<T>(V, Tm, nb, rows, C + nn * s, s, nw, st)
+                          : qr_apply<T>(V, Tm, nb, rows, C, s, nt, st);
         }
+        Vprev = fuse_next ? V : nullptr;
+        Tprev = fuse_next ? Tm : nullptr;
+        ldvprev = rows;
     }
     if (qs) {
         // join both internal streams back into the caller's stream

@@ -53,6 +53,41 @@ def test_exact_on_integer_data(m, n):
     np.testing.assert_array_equal(G, (Xi.T @ Xi).astype(np.float64))
 
 
+def test_correctly_rounded_on_wide_integer_data():
+    # |x| < 2^26: every value has an exact digit representation, and the exact
+    # Gram entries (up to ~2^68, two K-chunks) exceed FP64: the combined digit
+    # products are summed exactly and rounded once, so every entry is the
+    # correctly rounded exact integer (Python's int -> float rounds to nearest even)
+    m, n = 70000, 24
+    rng = np.random.default_rng(3)
+    Xi = rng.integers(-(2 ** 26), 2 ** 26, size=(m, n))
+    G = gram_tc(Xi.astype(np.float64))
+    Xo = Xi.astype(object)
+    exact = Xo.T.dot(Xo)
+    want = np.array([[float(exact[p, q]) for q in range(n)] for p in range(n)])
+    np.testing.assert_array_equal(G, want)
+    Yi = rng.integers(-(2 ** 26), 2 ** 26, size=(m, n))
+    Gxy, info = lsq.gemm_tn_tc(dev_colmajor(Xi.astype(np.float64)), dev_colmajor(Yi.astype(np.float64)))
+    assert int(to_np(info)[0]) == 0
+    exy = Xo.T.dot(Yi.astype(object))
+    np.testing.assert_array_equal(to_np(Gxy), np.array([[float(exy[p, q]) for q in range(n)] for p in range(n)]))
+
+
+def test_nonfinite_columns_give_nan_rows_and_columns():
+    m, n = 3000, 150
+    rng = np.random.default_rng(4)
+    Xi = rng.integers(-8, 9, size=(m, n)).astype(np.float64)
+    X = Xi.copy()
+    X[5, 3] = np.nan
+    X[70, 140] = -np.inf
+    G = gram_tc(X)
+    bad = np.zeros(n, bool)
+    bad[[3, 140]] = True
+    assert np.isnan(G[bad, :]).all() and np.isnan(G[:, bad]).all()
+    ok = ~bad
+    np.testing.assert_array_equal(G[np.ix_(ok, ok)], (Xi.T @ Xi)[np.ix_(ok, ok)])
+
+
 @pytest.mark.parametrize("m,n,spread", [(5000, 257, 0), (70000, 130, 0), (4000, 64, 30)])
 def test_within_fp64_error_order(m, n, spread):
     rng = np.random.default_rng(7 + n)
