@@ -177,6 +177,31 @@ __global__ void __launch_bounds__(QPT) k_qr_panel(T* __restrict__ W, int64_t ld,
 // reaches after reading it.
 constexpr int QCT = 256;
 
+constexpr int QRC = 32;  // panel rows per warp kept in registers
+
+// 4 consecutive values from 16-byte aligned shared memory
+__device__ __forceinline__ void load4(const float* p, float (&o)[4]) {
+    const float4 v = *(const float4*)p;
+    o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&o)[4]) {
+    const double2 v0 = *(const double2*)p, v1 = *(const double2*)(p + 2);
+    o[0] = v0.x, o[1] = v0.y, o[2] = v1.x, o[3] = v1.y;
+}
+
+// sum_{q < QCL} x[q * stride], pairwise (the same order in every CTA)
+template <typename T, int QCL>
+__device__ __forceinline__ T tree_sum(const T* x, int stride) {
+    T v[QCL];
+#pragma unroll
+    for (int q = 0; q < QCL; ++q) v[q] = x[q * stride];
+#pragma unroll
+    for (int h = QCL / 2; h >= 1; h >>= 1)
+#pragma unroll
+        for (int q = 0; q < h; ++q) v[q] += v[q + h];
+    return v[0];
+}
+
 // QCL: CTAs per cluster (16, non-portable, where the device allows it; else
 // 8).  Dynamic shared memory: the local panel (Rp x QNB) and, used by rank 0,
 // the V^T V partials of every rank (QCL x QNB x (QNB + 1)).
@@ -195,6 +220,10 @@ __global__ void __launch_bounds__(QCT)
     __shared__ T Ts[QNB][QNB + 1];
     __shared__ T bsh[QNB];
     __shared__ T Wr[QNB][QNB + 1];  // this CTA's partial V_p^T C (read by the whole cluster)
+    __shared__ T Ysm[QNB][QNB + 1];  // rank 0: Y = V^T V (strictly upper part), built column by column
+    __shared__ __align__(16) T bcv[QCT / 32][QRC];  // per warp: v_jj on its rows
+    __shared__ __align__(16) T bcx[QCT / 32][QRC];  // per warp: x_{jj+1} below its diagonal
+    __shared__ T rowbuf[QNB];                      // row jj of the panel (owning CTA)
     const int rank = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rows = (int)(s - k0);
@@ -295,9 +324,14 @@ __global__ void __launch_bounds__(QCT)
         T* W2 = Wk + QNB * (QNB + 1);   // [QNB][QNB]
         for (int q = tid; q < QNB * QNB; q += QCT) {
             const int p = q >> 5, c = q & 31;
-            T w = (T)0;
-            for (int r = 0; r < QCL; ++r) w += cluster.map_shared_rank(&Wr[0][0], r)[p * (QNB + 1) + c];
-            Wf[p * (QNB + 1) + c] = w;
+            T v[QCL];
+#pragma unroll
+            for (int r = 0; r < QCL; ++r) v[r] = cluster.map_shared_rank(&Wr[0][0], r)[p * (QNB + 1) + c];
+#pragma unroll
+            for (int h = QCL / 2; h >= 1; h >>= 1)
+#pragma unroll
+                for (int r = 0; r < h; ++r) v[r] += v[r + h];
+            Wf[p * (QNB + 1) + c] = v[0];
         }
         for (int q = tid; q < QNB * QNB; q += QCT) Ts[q & 31][q >> 5] = Tp[q];  // Ts[k][p] = T_p[k, p]
         __syncthreads();
@@ -354,15 +388,47 @@ __global__ void __launch_bounds__(QCT)
         for (; i < g1; ++i) a0 = fma(x[i], a[i], a0);
         return (a0 + a1) + (a2 + a3);
     };
+    // After column j: lanes c > j the partial dots of column j + 1 (rows
+    // below j + 1), lanes i < j the partial Y[i][j] = v_i^T v_j = v_i[j] +
+    // sum_{r > j} v_i[r] v_j[r] (rows of this warp) in the same pass: both
+    // read one broadcast column (x_{j+1} or v_j) against the lane's own.
+    auto dots_y = [&](int j) -> T {
+        const int jn = j + 1;
+        const bool ylane = lane < j, dlane = lane >= jn && lane < nb && jn < nb;
+        if (!(ylane || dlane)) return (T)0;
+        const T* x = P + (ylane ? j : jn) * Rp;
+        const T* a = P + lane * Rp;
+        T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+        int i = max(max(jn + 1 - r0, 0), g0);
+        for (; i + 4 <= g1; i += 4) {
+            a0 = fma(x[i], a[i], a0);
+            a1 = fma(x[i + 1], a[i + 1], a1);
+            a2 = fma(x[i + 2], a[i + 2], a2);
+            a3 = fma(x[i + 3], a[i + 3], a3);
+        }
+        for (; i < g1; ++i) a0 = fma(x[i], a[i], a0);
+        T acc2 = (a0 + a1) + (a2 + a3);
+        if (ylane) {
+            const int lj = j - r0, lj1 = jn - r0;
+            if (lj1 >= g0 && lj1 < g1) acc2 = fma(x[lj1], a[lj1], acc2);  // row j + 1
+            if (lj >= g0 && lj < g1) acc2 += a[lj];                        // row j: v_j = 1 there
+        }
+        return acc2;
+    };
     // Every per-row step (scaling of v, the update, the next column's dots)
     // stays within the warp's own rows, so a column needs one CTA barrier
     // (the partial dots) and one cluster barrier (their exchange).
-    T acc = dots(0);
-    for (int jj = 0; jj < nb; ++jj) {
+    // Column jj's exchange: the partials of every warp summed (part), pushed
+    // with the diagonal row (rowv, from the CTA that owns row jj) into every
+    // CTA; after the cluster barrier every thread forms the same Householder
+    // scalars, w_c for its column and (rank 0) column jj - 1 of Y.
+    struct Scal {
+        T mu, b, v1, wc;
+        bool scale;
+    };
+    auto exchange = [&](int jj, T acc, const T* rowsrc, int rowstride) -> Scal {
         const int buf = jj & 1;
         const int owner = (int)(jj / R);
-        T* xj = P + jj * Rp;
-        T* ac = P + lane * Rp;
         part[warp][lane] = acc;
         __syncthreads();
         if (warp == 0) {
@@ -370,66 +436,179 @@ __global__ void __launch_bounds__(QCT)
             for (int g = 0; g < QCT / 32; ++g) t += part[g][lane];
             for (int q = 0; q < QCL; ++q) *cluster.map_shared_rank(&all_part[buf][rank][lane], q) = t;
             if (rank == owner) {
-                const T rv = P[lane * Rp + (jj - r0)];
+                const T rv = rowsrc[lane * rowstride];
                 for (int q = 0; q < QCL; ++q) *cluster.map_shared_rank(&all_row[buf][lane], q) = rv;
             }
         }
         cluster.sync();
-        T sigma = (T)0;
-        for (int q = 0; q < QCL; ++q) sigma += all_part[buf][q][jj];
+        Scal sc;
+        const T sigma = tree_sum<T, QCL>(&all_part[buf][0][jj], QNB);
         const T x1 = all_row[buf][jj];
-        T mu, b, v1 = (T)1;
-        bool scale = false;
+        sc.v1 = (T)1;
+        sc.scale = false;
         if (sigma == (T)0) {
-            mu = fabs(x1);
-            b = x1 >= (T)0 ? (T)0 : (T)2;
+            sc.mu = fabs(x1);
+            sc.b = x1 >= (T)0 ? (T)0 : (T)2;
         } else {
-            mu = sqrt(x1 * x1 + sigma);
-            v1 = x1 <= (T)0 ? x1 - mu : -sigma / (x1 + mu);
-            b = (T)2 * v1 * v1 / (sigma + v1 * v1);
-            scale = true;
+            sc.mu = sqrt(x1 * x1 + sigma);
+            sc.v1 = x1 <= (T)0 ? x1 - sc.mu : -sigma / (x1 + sc.mu);
+            sc.b = (T)2 * sc.v1 * sc.v1 / (sigma + sc.v1 * sc.v1);
+            sc.scale = true;
         }
-        T wc = (T)0;
-        if (lane > jj && lane < nb) {
-            T d = (T)0;
-            for (int q = 0; q < QCL; ++q) d += all_part[buf][q][lane];
-            wc = b * (all_row[buf][lane] + (scale ? d / v1 : (T)0));
-        }
-        if (tid == 0) bsh[jj] = b;  // identical in every CTA of the cluster
-        if (rank == owner && tid == 0) {
-            xj[jj - r0] = mu;  // the diagonal entry is not read again (v there is 1)
-            beta_out[k0 + jj] = b;
-        }
-        // v below the diagonal, this warp's rows
-        const int ib = max(jj + 1 - r0, 0);
-        if (scale)
-            for (int i = max(ib, g0) + lane; i < g1; i += 32) xj[i] = xj[i] / v1;
-        __syncwarp();
-        if (lane > jj && lane < nb && b != (T)0) {
-            const int id = max(jj - r0, 0);  // owned rows >= the diagonal
-            const int dr = jj - r0;           // local index of the diagonal row
-            int i = max(id, g0);
-            // blocks of 8 rows: all loads before the stores (the column of v and
-            // the updated column never overlap)
-            for (; i + 8 <= g1; i += 8) {
-                T v[8], a[8];
+        // lane > jj: d_c of this column; lane < jj - 1: Y[lane][jj - 1] of the previous one
+        const T dsum = tree_sum<T, QCL>(&all_part[buf][0][lane], QNB);
+        sc.wc = (T)0;
+        if (lane > jj && lane < nb) sc.wc = sc.b * (all_row[buf][lane] + (sc.scale ? dsum / sc.v1 : (T)0));
+        if (rank == 0 && warp == 0 && lane + 1 < jj) Ysm[lane][jj - 1] = dsum;
+        if (tid == 0) bsh[jj] = sc.b;  // identical in every CTA of the cluster
+        if (rank == owner && tid == 0) beta_out[k0 + jj] = sc.b;
+        return sc;
+    };
+    T acc;
+    if (chunk <= QRC) {
+        // Each thread keeps its column's QRC rows of this warp in registers
+        // (rows g0 + q); per column a warp broadcasts v_jj and x_{jj+1} through
+        // its own QRC-entry shared buffers, read 4 rows per load.
+        T a[QRC];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    v[q] = (i + q == dr) ? (T)1 : xj[i + q];
-                    a[q] = ac[i + q];
+        for (int q = 0; q < QRC; ++q) a[q] = g0 + q < g1 ? P[lane * Rp + g0 + q] : (T)0;
+        T* bv = &bcv[warp][0];
+        T* bx = &bcx[warp][0];
+        const int gr0 = r0 + g0;  // global row (from k0) of a[0]
+        const int nv = g1 - g0;   // valid rows of this warp (<= 0: none)
+        // the diagonal row value a_lane[row] of this warp (0 when not here)
+        auto row_of = [&](int row) -> T {
+            T v = (T)0;
+#pragma unroll
+            for (int q = 0; q < QRC; ++q)
+                if (gr0 + q == row && q < nv) v = a[q];
+            return v;
+        };
+        // x_0 below row 0, then the dots of column 0
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < QRC; ++q) bx[q] = (q < nv && gr0 + q > 0) ? a[q] : (T)0;
+        }
+        if (0 >= gr0 && 0 < gr0 + nv) rowbuf[lane] = row_of(0);
+        __syncwarp();
+        acc = (T)0;
+        if (lane < nb) {
+#pragma unroll
+            for (int q = 0; q < QRC; q += 4) {
+                T xv[4];
+                load4(bx + q, xv);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc = fma(xv[e], a[q + e], acc);
+            }
+        }
+        for (int jj = 0; jj < nb; ++jj) {
+            // rowbuf (row jj, written by the warp that owns it) is read after
+            // the CTA barrier inside the exchange
+            const Scal sc = exchange(jj, acc, rowbuf, 1);
+            // v_jj of this warp's rows: raw column from lane jj, scaled by all lanes
+            if (lane == jj) {
+#pragma unroll
+                for (int q = 0; q < QRC; ++q) bv[q] = a[q];
+            }
+            __syncwarp();
+            {
+                const int gr = gr0 + lane;
+                const T x = bv[lane];
+                bv[lane] = (gr < jj || lane >= nv) ? (T)0 : (gr == jj ? (T)1 : (sc.scale ? x / sc.v1 : x));
+            }
+            __syncwarp();
+            if (lane == jj) {
+#pragma unroll
+                for (int q = 0; q < QRC; ++q) {
+                    if (q < nv && gr0 + q > jj) a[q] = bv[q];
+                    if (q < nv && gr0 + q == jj) a[q] = sc.mu;  // R diagonal (v there is 1)
                 }
-#pragma unroll
-                for (int q = 0; q < 8; ++q) ac[i + q] = fma(-wc, v[q], a[q]);
             }
-            for (; i < g1; ++i) {
-                const T vi = (i == dr) ? (T)1 : xj[i];
-                ac[i] = fma(-wc, vi, ac[i]);
+            if (lane > jj && lane < nb && sc.b != (T)0) {
+#pragma unroll
+                for (int q = 0; q < QRC; q += 4) {
+                    T vv[4];
+                    load4(bv + q, vv);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) a[q + e] = fma(-sc.wc, vv[e], a[q + e]);
+                }
+            }
+            // x_{jj+1} below its diagonal and row jj + 1 for the next exchange
+            const int jn = jj + 1;
+            if (jn < nb) {
+                if (lane == jn) {
+#pragma unroll
+                    for (int q = 0; q < QRC; ++q) bx[q] = (q < nv && gr0 + q > jn) ? a[q] : (T)0;
+                }
+                if (jn >= gr0 && jn < gr0 + nv) rowbuf[lane] = row_of(jn);
+            }
+            __syncwarp();
+            // lanes c > jj: dots of column jj + 1; lanes i < jj: Y[i][jj]
+            const bool ylane = lane < jj, dlane = lane >= jn && lane < nb && jn < nb;
+            acc = (T)0;
+            if (ylane || dlane) {
+                const T* src = ylane ? bv : bx;
+#pragma unroll
+                for (int q = 0; q < QRC; q += 4) {
+                    T xv[4];
+                    load4(src + q, xv);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc = fma(xv[e], a[q + e], acc);
+                }
             }
         }
-        __syncwarp();
-        acc = jj + 1 < nb ? dots(jj + 1) : (T)0;
+#pragma unroll
+        for (int q = 0; q < QRC; ++q)
+            if (q < nv) P[lane * Rp + g0 + q] = a[q];
+    } else {
+        acc = dots(0);
+        for (int jj = 0; jj < nb; ++jj) {
+            T* xj = P + jj * Rp;
+            T* ac = P + lane * Rp;
+            const int owner = (int)(jj / R);
+            const Scal sc = exchange(jj, acc, P + (jj - r0), Rp);
+            const T b = sc.b, wc = sc.wc;
+            if (rank == owner && tid == 0) xj[jj - r0] = sc.mu;  // the diagonal entry is not read again (v there is 1)
+            // v below the diagonal, this warp's rows
+            const int ib = max(jj + 1 - r0, 0);
+            if (sc.scale)
+                for (int i = max(ib, g0) + lane; i < g1; i += 32) xj[i] = xj[i] / sc.v1;
+            __syncwarp();
+            if (lane > jj && lane < nb && b != (T)0) {
+                const int id = max(jj - r0, 0);  // owned rows >= the diagonal
+                const int dr = jj - r0;           // local index of the diagonal row
+                int i = max(id, g0);
+                // blocks of 8 rows: all loads before the stores (the column of v and
+                // the updated column never overlap)
+                for (; i + 8 <= g1; i += 8) {
+                    T v[8], av[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        v[q] = (i + q == dr) ? (T)1 : xj[i + q];
+                        av[q] = ac[i + q];
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) ac[i + q] = fma(-wc, v[q], av[q]);
+                }
+                for (; i < g1; ++i) {
+                    const T vi = (i == dr) ? (T)1 : xj[i];
+                    ac[i] = fma(-wc, vi, ac[i]);
+                }
+            }
+            __syncwarp();
+            acc = dots_y(jj);
+        }
     }
+    // Y[:, nb - 1] of the last column: one more reduction, into rank 0
+    part[warp][lane] = acc;
     __syncthreads();
+    if (warp == 0) {
+        T t = (T)0;
+        for (int g = 0; g < QCT / 32; ++g) t += part[g][lane];
+        *cluster.map_shared_rank(&all_part[nb & 1][rank][lane], 0) = t;
+    }
+    cluster.sync();
+    if (rank == 0 && warp == 0 && lane + 1 < nb) Ysm[lane][nb - 1] = tree_sum<T, QCL>(&all_part[nb & 1][0][lane], QNB);
     // write R / v back to W and the explicit V (0 above, 1 on the diagonal)
     for (int c = 0; c < QNB; ++c)
         for (int i = tid; i < nloc; i += QCT) {
@@ -443,37 +622,7 @@ __global__ void __launch_bounds__(QCT)
             }
         }
     __syncthreads();
-    // make the local panel the explicit V, then Y = V^T V over the owned rows
-    for (int c = 0; c < nb; ++c)
-        for (int i = tid; i < R && r0 + i <= c; i += QCT) P[c * Rp + i] = r0 + i == c ? (T)1 : (T)0;
-    __syncthreads();
-    {
-        const int p = lane, q0 = warp * 4;  // Y[p][q0 .. q0 + 3]
-        T y0 = (T)0, y1 = (T)0, y2 = (T)0, y3 = (T)0;
-        const T* vp = P + p * Rp;
-        const T* vq = P + q0 * Rp;
-        for (int i = 0; i < nloc; ++i) {
-            const T a = vp[i];
-            y0 = fma(a, vq[i], y0);
-            y1 = fma(a, vq[Rp + i], y1);
-            y2 = fma(a, vq[2 * Rp + i], y2);
-            y3 = fma(a, vq[3 * Rp + i], y3);
-        }
-        // into rank 0's shared memory (pushed, so that rank 0 sums locally)
-        T* dst = cluster.map_shared_rank(Yall, 0) + (rank * QNB + p) * (QNB + 1);
-        dst[q0] = y0;
-        dst[q0 + 1] = y1;
-        dst[q0 + 2] = y2;
-        dst[q0 + 3] = y3;
-    }
-    cluster.sync();
     if (rank == 0) {
-        for (int e = tid; e < QNB * QNB; e += QCT) {
-            const int p = e % QNB, q = e / QNB;
-            T y = (T)0;
-            for (int r = 0; r < QCL; ++r) y += Yall[(r * QNB + p) * (QNB + 1) + q];
-            Ts[p][q] = y;  // Ts holds Y for now
-        }
         __syncthreads();
         if (warp == 0) {
             // column by column: T[0:j, j] = -beta_j T[0:j, 0:j] Y[0:j, j]; lane = row
@@ -481,8 +630,9 @@ __global__ void __launch_bounds__(QCT)
 #pragma unroll
             for (int jj = 0; jj < QNB; ++jj) {
                 T t = (T)0;
+                if (jj < nb)
 #pragma unroll
-                for (int qq = 0; qq < jj; ++qq) t = fma(trow[qq], Ts[qq][jj], t);
+                    for (int qq = 0; qq < jj; ++qq) t = fma(trow[qq], Ysm[qq][jj], t);
                 const T bj = jj < nb ? bsh[jj] : (T)0;
                 trow[jj] = lane < jj ? -bj * t : (lane == jj ? bj : (T)0);
             }
@@ -490,7 +640,6 @@ __global__ void __launch_bounds__(QCT)
             for (int c = 0; c < QNB; ++c) Tm[lane + c * QNB] = trow[c];
         }
     }
-    cluster.sync();
 }
 
 // ---------------------------------------------------------------------------
