@@ -189,6 +189,12 @@ __device__ __forceinline__ void load4(const double* p, double (&o)[4]) {
     o[0] = v0.x, o[1] = v0.y, o[2] = v1.x, o[3] = v1.y;
 }
 
+__device__ __forceinline__ void store4(float* p, float a, float b, float c, float d) { *(float4*)p = make_float4(a, b, c, d); }
+__device__ __forceinline__ void store4(double* p, double a, double b, double c, double d) {
+    *(double2*)p = make_double2(a, b);
+    *(double2*)(p + 2) = make_double2(c, d);
+}
+
 // sum_{q < QCL} x[q * stride], pairwise (the same order in every CTA)
 template <typename T, int QCL>
 __device__ __forceinline__ T tree_sum(const T* x, int stride) {
@@ -487,7 +493,12 @@ __global__ void __launch_bounds__(QCT)
         // x_0 below row 0, then the dots of column 0
         if (lane == 0) {
 #pragma unroll
-            for (int q = 0; q < QRC; ++q) bx[q] = (q < nv && gr0 + q > 0) ? a[q] : (T)0;
+            for (int q = 0; q < QRC; q += 4) {
+                T o[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) o[e] = (q + e < nv && gr0 + q + e > 0) ? a[q + e] : (T)0;
+                store4(bx + q, o[0], o[1], o[2], o[3]);
+            }
         }
         if (0 >= gr0 && 0 < gr0 + nv) rowbuf[lane] = row_of(0);
         __syncwarp();
@@ -508,7 +519,7 @@ __global__ void __launch_bounds__(QCT)
             // v_jj of this warp's rows: raw column from lane jj, scaled by all lanes
             if (lane == jj) {
 #pragma unroll
-                for (int q = 0; q < QRC; ++q) bv[q] = a[q];
+                for (int q = 0; q < QRC; q += 4) store4(bv + q, a[q], a[q + 1], a[q + 2], a[q + 3]);
             }
             __syncwarp();
             {
@@ -519,9 +530,14 @@ __global__ void __launch_bounds__(QCT)
             __syncwarp();
             if (lane == jj) {
 #pragma unroll
-                for (int q = 0; q < QRC; ++q) {
-                    if (q < nv && gr0 + q > jj) a[q] = bv[q];
-                    if (q < nv && gr0 + q == jj) a[q] = sc.mu;  // R diagonal (v there is 1)
+                for (int q = 0; q < QRC; q += 4) {
+                    T vv[4];
+                    load4(bv + q, vv);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (q + e < nv && gr0 + q + e > jj) a[q + e] = vv[e];
+                        if (q + e < nv && gr0 + q + e == jj) a[q + e] = sc.mu;  // R diagonal (v there is 1)
+                    }
                 }
             }
             if (lane > jj && lane < nb && sc.b != (T)0) {
@@ -538,7 +554,12 @@ __global__ void __launch_bounds__(QCT)
             if (jn < nb) {
                 if (lane == jn) {
 #pragma unroll
-                    for (int q = 0; q < QRC; ++q) bx[q] = (q < nv && gr0 + q > jn) ? a[q] : (T)0;
+                    for (int q = 0; q < QRC; q += 4) {
+                        T o[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) o[e] = (q + e < nv && gr0 + q + e > jn) ? a[q + e] : (T)0;
+                        store4(bx + q, o[0], o[1], o[2], o[3]);
+                    }
                 }
                 if (jn >= gr0 && jn < gr0 + nv) rowbuf[lane] = row_of(jn);
             }
