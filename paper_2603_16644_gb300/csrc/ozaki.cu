@@ -257,15 +257,23 @@ static OzPlan oz_plan(int64_t m, int64_t n, bool sym) {
     P.ldz = ceil_div(m, 128) * 128;
     P.kchunk = std::min<int64_t>(OZ_KCHUNK, P.ldz);
     P.chunks = (int)ceil_div(P.ldz, P.kchunk);
-    // symmetric: pairs t <= u with t + u <= S-1, blocks P >= Q for t == u, all
-    // (P, Q) for t < u; otherwise every pair with t + u <= S-1 and every block
+    // tiles of 128 x 256: an X block P against the Y blocks 2 Qp and 2 Qp + 1.
+    // Symmetric: pairs t <= u with t + u <= S-1, all (P, Qp) for t < u and
+    // those with 2 Qp <= P for t == u; otherwise every pair with t + u <= S-1
+    // and every (P, Qp).  ntiles counts 128-column halves (2 per tile).
+    const int64_t nq = ceil_div(P.nb, 2);
     int64_t nt = 0;
     for (int t = 0; t < OZ_S; ++t)
-        for (int u = sym ? t : 0; u < OZ_S; ++u)
-            if (t + u <= OZ_S - 1) nt += (sym && t == u) ? P.nb * (P.nb + 1) / 2 : P.nb * P.nb;
-    P.ntiles = nt;
+        for (int u = sym ? t : 0; u < OZ_S; ++u) {
+            if (t + u > OZ_S - 1) continue;
+            if (sym && t == u)
+                for (int64_t Pb = 0; Pb < P.nb; ++Pb) nt += Pb / 2 + 1;
+            else
+                nt += P.nb * nq;
+        }
+    P.ntiles = 2 * nt;
     P.z_bytes = align_up((size_t)OZ_S * P.np * P.ldz, 256) * (sym ? 1 : 2);
-    P.t_bytes = align_up(sizeof(float) * 16384 * (size_t)nt * P.chunks, 256);
+    P.t_bytes = align_up(sizeof(float) * 16384 * (size_t)P.ntiles * P.chunks, 256);
     P.tiles_bytes = align_up(sizeof(int2) * (size_t)nt, 256);
     P.map_bytes = align_up(sizeof(int32_t) * (size_t)OZ_S * OZ_S * P.nb * P.nb, 256);
     P.e_bytes = align_up(sizeof(int32_t) * (size_t)n, 256) * (sym ? 1 : 2);
@@ -276,23 +284,25 @@ static OzPlan oz_plan(int64_t m, int64_t n, bool sym) {
 size_t oz_gram_ws_bytes(int64_t m, int64_t n) { return oz_plan(m, n, true).total; }
 size_t oz_gemm_tn_ws_bytes(int64_t m, int64_t n) { return oz_plan(m, n, false).total; }
 
-// Tile list (grouped so that neighbouring CTAs share the Y-row block of a
-// pair) and the (t, u, P, Q) -> tile map, built on the device in a fixed
-// order (no host copies: the call stays capturable in a CUDA graph).  One CTA:
-// the tiles of each (u, Q) are counted, prefix summed in (u, Q) order, and
-// each (u, Q) range is filled by its own thread, so the list is the sequential
-// enumeration u, Q, t, P.
+// Tile list (ordered so that neighbouring CTAs share the Y rows of a pair)
+// and the (t, u, P, Q) -> half-tile map (2 k + (Q & 1) for tile k, i.e. the
+// 128 x 128 block at (2 k + (Q & 1)) 16384 of the output), built on the
+// device in a fixed order (no host copies: the call stays capturable in a
+// CUDA graph).  One CTA: the tiles of each (u, Qp) are counted, prefix summed
+// in (u, Qp) order, and each (u, Qp) range is filled by its own thread, so the
+// list is the sequential enumeration u, Qp, t, P.
 __global__ void k_oz_tiles(int64_t nb, int64_t np, int sym, int2* __restrict__ tiles, int32_t* __restrict__ map) {
-    extern __shared__ int32_t oz_cnt[];  // OZ_S * nb + 1
-    const int64_t nuq = (int64_t)OZ_S * nb;
+    extern __shared__ int32_t oz_cnt[];  // OZ_S * nq + 1
+    const int64_t nq = (nb + 1) / 2;
+    const int64_t nuq = (int64_t)OZ_S * nq;
     for (int64_t q = threadIdx.x; q < (int64_t)OZ_S * OZ_S * nb * nb; q += blockDim.x) map[q] = -1;
     for (int64_t uq = threadIdx.x; uq < nuq; uq += blockDim.x) {
-        const int u = (int)(uq / nb);
-        const int64_t Q = uq % nb;
+        const int u = (int)(uq / nq);
+        const int64_t Qp = uq % nq;
         int32_t c = 0;
         for (int t = 0; t < OZ_S; ++t) {
             if (t + u > OZ_S - 1 || (sym && t > u)) continue;
-            c += (int32_t)((sym && t == u) ? nb - Q : nb);
+            c += (int32_t)((sym && t == u) ? nb - 2 * Qp : nb);  // P >= 2 Qp when t == u
         }
         oz_cnt[uq + 1] = c;
     }
@@ -303,15 +313,19 @@ __global__ void k_oz_tiles(int64_t nb, int64_t np, int sym, int2* __restrict__ t
     }
     __syncthreads();
     for (int64_t uq = threadIdx.x; uq < nuq; uq += blockDim.x) {
-        const int u = (int)(uq / nb);
-        const int64_t Q = uq % nb;
+        const int u = (int)(uq / nq);
+        const int64_t Qp = uq % nq;
         int32_t k = oz_cnt[uq];
         for (int t = 0; t < OZ_S; ++t) {
             if (t + u > OZ_S - 1 || (sym && t > u)) continue;
             for (int64_t Pb = 0; Pb < nb; ++Pb) {
-                if (sym && t == u && Pb < Q) continue;
-                map[((int64_t)(t * OZ_S + u) * nb + Pb) * nb + Q] = k;
-                tiles[k] = make_int2((int)(t * np + Pb * 128), (int)(u * np + Q * 128));
+                if (sym && t == u && Pb < 2 * Qp) continue;
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t Q = 2 * Qp + h;
+                    if (Q < nb && !(sym && t == u && Q > Pb))
+                        map[((int64_t)(t * OZ_S + u) * nb + Pb) * nb + Q] = 2 * k + h;
+                }
+                tiles[k] = make_int2((int)(t * np + Pb * 128), (int)(u * np + 2 * Qp * 128));
                 ++k;
             }
         }
@@ -334,7 +348,7 @@ static lsq_status oz_run(const double* X, int64_t ldx, const double* Y, int64_t 
     int32_t* map = (int32_t*)(base + P.z_bytes + P.t_bytes + P.tiles_bytes);
     int32_t* ex = (int32_t*)(base + P.z_bytes + P.t_bytes + P.tiles_bytes + P.map_bytes);
     int32_t* ey = sym ? ex : (int32_t*)((char*)ex + eb);
-    const size_t tsm = sizeof(int32_t) * (size_t)(OZ_S * P.nb + 1);
+    const size_t tsm = sizeof(int32_t) * (size_t)(OZ_S * ceil_div(P.nb, 2) + 1);
     if (tsm > 48 * 1024) return LSQ_ERR_ARG;
     k_oz_tiles<<<1, 256, tsm, st>>>(P.nb, P.np, sym ? 1 : 0, tiles, map);
     LSQ_LAUNCH_CHECK();
@@ -350,7 +364,7 @@ static lsq_status oz_run(const double* X, int64_t ldx, const double* Y, int64_t 
         LSQ_LAUNCH_CHECK();
     }
     lsq_status r = launch_tc_tiles_fp8(Zx, P.ldz, OZ_S * P.np, Zy, P.ldz, OZ_S * P.np, P.ldz, P.kchunk, tiles,
-                                       P.ntiles, T, err, st);
+                                       P.ntiles / 2, T, err, st);
     if (r != LSQ_OK) return r;
     const int64_t cblocks = (sym ? P.nb * (P.nb + 1) / 2 : P.nb * P.nb) * 4;
     k_oz_combine<<<(unsigned)cblocks, OZ_CB_THREADS, 0, st>>>(

@@ -26,10 +26,12 @@ namespace lsq {
 
 constexpr int TC_BM = 128, TC_BN = 128, TC_STAGES = 6, TC_THREADS = 192;
 constexpr int TC_TILE_BYTES = 128 * 128;  // 128 rows x 128 bytes of K
-// Instruction descriptor: D = F32, A/B format, both K-major, M = 128, N = 128.
-template <int KIND>
+// stages of the A / B ring for a tile N wide (192 KB of shared memory)
+__host__ __device__ constexpr int tc_stages(int BN) { return (12 * TC_TILE_BYTES) / (TC_TILE_BYTES + BN * 128); }
+// Instruction descriptor: D = F32, A/B format, both K-major, M = 128, N = BN.
+template <int KIND, int BN>
 __device__ __forceinline__ uint32_t tc_idesc() {
-    return umma_idesc(KIND == 0 ? 1u : 0u, TC_BM, TC_BN);
+    return umma_idesc(KIND == 0 ? 1u : 0u, TC_BM, BN);
 }
 
 template <int KIND>
@@ -38,20 +40,22 @@ __device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, ui
     else umma_f16(tmem_d, a, b, idesc, accum);
 }
 
-template <int KIND>
+template <int KIND, int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_sketch_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t M, int64_t N,
                 int64_t K, int64_t kchunk, float* __restrict__ out, int64_t ldo, int64_t split_stride,
                 int32_t* __restrict__ err, const int2* __restrict__ tiles, int64_t ntiles) {
     constexpr int ES = KIND == 2 ? 1 : 2;  // element bytes
     constexpr int BKE = 128 / ES;          // K elements per stage
+    constexpr int ST = tc_stages(BN);
+    constexpr int BBYTES = BN * 128;       // B tile: BN rows x 128 bytes of K
     extern __shared__ unsigned char tc_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = base;
-    uint8_t* sB = sA + TC_STAGES * TC_TILE_BYTES;
-    uint64_t* full = (uint64_t*)(sB + TC_STAGES * TC_TILE_BYTES);
-    uint64_t* empty = full + TC_STAGES;
-    uint64_t* accb = empty + TC_STAGES;
+    uint8_t* sB = sA + ST * TC_TILE_BYTES;
+    uint64_t* full = (uint64_t*)(sB + ST * BBYTES);
+    uint64_t* empty = full + ST;
+    uint64_t* accb = empty + ST;
     uint32_t* tslot = (uint32_t*)(accb + 1);
     volatile int* bad = (volatile int*)(tslot + 1);
     int* issued = (int*)(tslot + 2);
@@ -62,13 +66,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // own 128 x 128 slot (column-major, ld 128) of `out`
     const int2 tl = tiles ? tiles[blockIdx.x] : make_int2(0, 0);
     const int64_t m0 = tiles ? (int64_t)tl.x : (int64_t)blockIdx.x * TC_BM;
-    const int64_t n0 = tiles ? (int64_t)tl.y : (int64_t)blockIdx.y * TC_BN;
+    const int64_t n0 = tiles ? (int64_t)tl.y : (int64_t)blockIdx.y * BN;
     const int64_t kb0 = (int64_t)blockIdx.z * kchunk;
     const int64_t kb1 = min64(K, kb0 + kchunk);
     const int nk = (int)((kb1 - kb0 + BKE - 1) / BKE);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < ST; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -80,7 +84,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(TC_BN)
+                     "r"(BN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -92,23 +96,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 0 && lane == 0) {
         // producer
         for (int kb = 0; kb < nk; ++kb) {
-            int s = kb % TC_STAGES, r = kb / TC_STAGES;
-            if (kb >= TC_STAGES && !mbar_wait(&empty[s], (uint32_t)((r - 1) & 1))) {
+            int s = kb % ST, r = kb / ST;
+            if (kb >= ST && !mbar_wait(&empty[s], (uint32_t)((r - 1) & 1))) {
                 *bad = 1;
                 break;
             }
             if (*bad) break;
-            mbar_expect_tx(&full[s], 2 * TC_TILE_BYTES);
+            mbar_expect_tx(&full[s], TC_TILE_BYTES + BBYTES);
             int x = (int)(kb0 + (int64_t)kb * BKE);
             tma_load_2d(sA + s * TC_TILE_BYTES, &tmA, &full[s], x, (int)m0);
-            tma_load_2d(sB + s * TC_TILE_BYTES, &tmB, &full[s], x, (int)n0);
+            tma_load_2d(sB + s * BBYTES, &tmB, &full[s], x, (int)n0);
             *issued = kb + 1;
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
-        const uint32_t idesc = tc_idesc<KIND>();
+        const uint32_t idesc = tc_idesc<KIND, BN>();
         for (int kb = 0; kb < nk; ++kb) {
-            int s = kb % TC_STAGES, r = kb / TC_STAGES;
+            int s = kb % ST, r = kb / ST;
             if (!mbar_wait(&full[s], (uint32_t)(r & 1))) {
                 *bad = 1;
                 break;
@@ -116,7 +120,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             *consumed = kb + 1;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             uint64_t ad = umma_desc(smem_u32(sA + s * TC_TILE_BYTES));
-            uint64_t bd = umma_desc(smem_u32(sB + s * TC_TILE_BYTES));
+            uint64_t bd = umma_desc(smem_u32(sB + s * BBYTES));
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)  // 4 x 32 bytes of K per stage
                 umma<KIND>(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0 ? 1u : 0u);
@@ -133,10 +137,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (go) {
             const int quad = warp & 3;
             const int64_t row = m0 + quad * 32 + lane;
-            float* o = tiles ? out + ((int64_t)blockIdx.z * ntiles + blockIdx.x) * (TC_BM * TC_BN) - m0 - n0 * ldo
+            float* o = tiles ? out + ((int64_t)blockIdx.z * ntiles + blockIdx.x) * (TC_BM * BN) - m0 - n0 * ldo
                              : out + (int64_t)blockIdx.z * split_stride;
 #pragma unroll 1
-            for (int c0 = 0; c0 < TC_BN; c0 += 16) {
+            for (int c0 = 0; c0 < BN; c0 += 16) {
                 uint32_t v[16];
                 uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0;
                 asm volatile(
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (threadIdx.x == 0) {
             set_info_once(err, -2);
             // wait (bounded) for loads issued but never consumed, then for the MMAs
-            for (int kb = *consumed; kb < *issued; ++kb) mbar_wait(&full[kb % TC_STAGES], (uint32_t)((kb / TC_STAGES) & 1));
+            for (int kb = *consumed; kb < *issued; ++kb) mbar_wait(&full[kb % ST], (uint32_t)((kb / ST) & 1));
             mbar_wait(accb, 0);
         }
         __syncthreads();
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
     }
 }
 
@@ -203,7 +207,8 @@ EncodeTiledFn tensor_map_encoder() {
     return fn;
 }
 
-static bool make_map(CUtensorMap* map, const void* base, int prec, int64_t K, int64_t rows, int64_t ld) {
+static bool make_map(CUtensorMap* map, const void* base, int prec, int64_t K, int64_t rows, int64_t ld,
+                     int box_rows = 128) {
     EncodeTiledFn enc = tensor_map_encoder();
     if (!enc) return false;
     int es = prec == LSQ_FP8_E4M3 ? 1 : 2;
@@ -212,7 +217,7 @@ static bool make_map(CUtensorMap* map, const void* base, int prec, int64_t K, in
                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
-    cuuint32_t box[2] = {(cuuint32_t)(128 / es), 128u};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1u, 1u};
     CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -263,16 +268,16 @@ lsq_status launch_sketch_tc(const void* Om, int64_t ldo, const void* Ahat, int64
     dim3 grid((unsigned)ceil_div(s, TC_BM), (unsigned)ceil_div(n, TC_BN), (unsigned)splits);
     switch (prec) {
     case LSQ_BF16:
-        LSQ_CUDA_TRY(cudaFuncSetAttribute(k_sketch_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_sketch_tc<0><<<grid, TC_THREADS, smem, st>>>(ta, tb, s, n, m, kchunk, out, ldout, stride, err, nullptr, 0);
+        LSQ_CUDA_TRY(cudaFuncSetAttribute(k_sketch_tc<0, TC_BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_sketch_tc<0, TC_BN><<<grid, TC_THREADS, smem, st>>>(ta, tb, s, n, m, kchunk, out, ldout, stride, err, nullptr, 0);
         break;
     case LSQ_FP16:
-        LSQ_CUDA_TRY(cudaFuncSetAttribute(k_sketch_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_sketch_tc<1><<<grid, TC_THREADS, smem, st>>>(ta, tb, s, n, m, kchunk, out, ldout, stride, err, nullptr, 0);
+        LSQ_CUDA_TRY(cudaFuncSetAttribute(k_sketch_tc<1, TC_BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_sketch_tc<1, TC_BN><<<grid, TC_THREADS, smem, st>>>(ta, tb, s, n, m, kchunk, out, ldout, stride, err, nullptr, 0);
         break;
     default:
-        LSQ_CUDA_TRY(cudaFuncSetAttribute(k_sketch_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_sketch_tc<2><<<grid, TC_THREADS, smem, st>>>(ta, tb, s, n, m, kchunk, out, ldout, stride, err, nullptr, 0);
+        LSQ_CUDA_TRY(cudaFuncSetAttribute(k_sketch_tc<2, TC_BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_sketch_tc<2, TC_BN><<<grid, TC_THREADS, smem, st>>>(ta, tb, s, n, m, kchunk, out, ldout, stride, err, nullptr, 0);
         break;
     }
     LSQ_LAUNCH_CHECK();
@@ -289,19 +294,24 @@ lsq_status launch_sketch_tc(const void* Om, int64_t ldo, const void* Ahat, int64
 namespace lsq {
 
 // Tile-list launch (FP8-e4m3 operands): tiles[i] = (row of X, row of Y) of a
-// 128 x 128 output tile; tile i of K chunk z goes to out + (z ntiles + i) 16384.
+// 128 x 256 output tile (256 consecutive rows of Y); tile i of K chunk z goes
+// to out + (z ntiles + i) 32768 (column-major, ld 128).  The wide tile reads
+// 12 KB of operands per 128 x 256 x 32 MMA instead of 8 KB per 128 x 128 x 32:
+// 25 % less shared-memory traffic per flop (operands and TMA writes).
 lsq_status launch_tc_tiles_fp8(const void* X, int64_t ldx, int64_t rowsX, const void* Y, int64_t ldy, int64_t rowsY,
                                int64_t K, int64_t kchunk, const int2* tiles, int64_t ntiles, float* out, int32_t* err,
                                cudaStream_t st) {
+    constexpr int BN = 256;
     if ((ldx % 16) || (ldy % 16) || ((uintptr_t)X % 16) || ((uintptr_t)Y % 16) || kchunk % 128) return LSQ_ERR_ARG;
     CUtensorMap ta, tb;
-    if (!make_map(&ta, X, LSQ_FP8_E4M3, K, rowsX, ldx) || !make_map(&tb, Y, LSQ_FP8_E4M3, K, rowsY, ldy))
+    if (!make_map(&ta, X, LSQ_FP8_E4M3, K, rowsX, ldx) || !make_map(&tb, Y, LSQ_FP8_E4M3, K, rowsY, ldy, BN))
         return LSQ_ERR_CUDA;
     int chunks = (int)ceil_div(K, kchunk);
-    size_t smem = 1024 + 2 * (size_t)TC_STAGES * TC_TILE_BYTES + 256;
-    LSQ_CUDA_TRY(cudaFuncSetAttribute(k_sketch_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    size_t smem = 1024 + (size_t)tc_stages(BN) * (TC_TILE_BYTES + BN * 128) + 256;
+    LSQ_CUDA_TRY(cudaFuncSetAttribute(k_sketch_tc<2, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)ntiles, 1, (unsigned)chunks);
-    k_sketch_tc<2><<<grid, TC_THREADS, smem, st>>>(ta, tb, rowsX, rowsY, K, kchunk, out, TC_BM, 0, err, tiles, ntiles);
+    k_sketch_tc<2, BN><<<grid, TC_THREADS, smem, st>>>(ta, tb, rowsX, rowsY, K, kchunk, out, TC_BM, 0, err, tiles,
+                                                      ntiles);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
 }
