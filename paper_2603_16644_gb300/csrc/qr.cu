@@ -438,8 +438,7 @@ __global__ void __launch_bounds__(QCT)
         part[warp][lane] = acc;
         __syncthreads();
         if (warp == 0) {
-            T t = (T)0;
-            for (int g = 0; g < QCT / 32; ++g) t += part[g][lane];
+            const T t = tree_sum<T, QCT / 32>(&part[0][lane], QNB);
             for (int q = 0; q < QCL; ++q) *cluster.map_shared_rank(&all_part[buf][rank][lane], q) = t;
             if (rank == owner) {
                 const T rv = rowsrc[lane * rowstride];
@@ -504,13 +503,15 @@ __global__ void __launch_bounds__(QCT)
         __syncwarp();
         acc = (T)0;
         if (lane < nb) {
+            T s4[4] = {(T)0, (T)0, (T)0, (T)0};  // 4 chains of 8 FMAs
 #pragma unroll
             for (int q = 0; q < QRC; q += 4) {
                 T xv[4];
                 load4(bx + q, xv);
 #pragma unroll
-                for (int e = 0; e < 4; ++e) acc = fma(xv[e], a[q + e], acc);
+                for (int e = 0; e < 4; ++e) s4[e] = fma(xv[e], a[q + e], s4[e]);
             }
+            acc = (s4[0] + s4[1]) + (s4[2] + s4[3]);
         }
         for (int jj = 0; jj < nb; ++jj) {
             // rowbuf (row jj, written by the warp that owns it) is read after
@@ -569,13 +570,15 @@ __global__ void __launch_bounds__(QCT)
             acc = (T)0;
             if (ylane || dlane) {
                 const T* src = ylane ? bv : bx;
+                T s4[4] = {(T)0, (T)0, (T)0, (T)0};  // 4 chains of 8 FMAs
 #pragma unroll
                 for (int q = 0; q < QRC; q += 4) {
                     T xv[4];
                     load4(src + q, xv);
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) acc = fma(xv[e], a[q + e], acc);
+                    for (int e = 0; e < 4; ++e) s4[e] = fma(xv[e], a[q + e], s4[e]);
                 }
+                acc = (s4[0] + s4[1]) + (s4[2] + s4[3]);
             }
         }
 #pragma unroll
