@@ -30,6 +30,7 @@
 #include "tcgen05.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace lsq {
 
@@ -222,14 +223,48 @@ __global__ void __launch_bounds__(128) k_ot_colslice(const double* __restrict__ 
 // ---------------------------------------------------------------------------
 // Update C_out = C_in - X Y over 128 x 64 tiles (C_in may equal C_out).
 // ---------------------------------------------------------------------------
-// 2^s (hi 2^28 + lo) for |hi|, |lo| < 2^47, rounded once to nearest-even
-// (the 128-bit sum is formed exactly, then converted by fixed128_to_double).
+// Results outside the normal range (rare): scaled in FP64.  Not inlined, so
+// that the FP64 instructions of this path are never executed speculatively.
+__device__ __noinline__ double ot_fixed_to_double_slow(long long hi, long long lo, int s) {
+    return ldexp(fma((double)hi, 268435456.0, (double)lo), s);
+}
+
+// 2^s (hi 2^28 + lo) for |hi|, |lo| < 2^47, rounded once to nearest-even:
+// the exact integer (below 2^76) is normalised with integer operations and
+// the scale goes into the exponent field (no FP64 instruction on the common
+// path).  Straight-line code (selects), so that the compiler interleaves
+// independent conversions; the epilogue's throughput is bound by these
+// integer operations when K is small.
 __device__ __forceinline__ double ot_fixed_to_double(long long hi, long long lo, int s) {
     unsigned long long L = (unsigned long long)hi << 28;
     long long H = hi >> 36;
     const unsigned long long L2 = L + (unsigned long long)lo;
     H += (lo >> 63) + (L2 < L ? 1 : 0);
-    return fixed128_to_double(H, L2, s);
+    L = L2;
+    // magnitude: two's-complement negation of (H:L) when negative (H < 2^11)
+    const unsigned long long sgn = (unsigned long long)(H >> 63);
+    const unsigned long long neg = sgn & 1ull;
+    const unsigned long long uL = (L ^ sgn) + neg;
+    const unsigned long long uH = ((unsigned long long)H ^ sgn) + (neg & (uL == 0 ? 1ull : 0ull));
+    const bool zero = (uH | uL) == 0;
+    int p = uH ? 127 - __clzll((long long)uH) : 63 - __clzll((long long)uL);
+    const int shl = p <= 52 ? 52 - p : 0;  // 0 .. 52
+    const int shr = p > 52 ? p - 52 : 0;   // 0 .. 22
+    const unsigned long long small = uL << shl;
+    const unsigned long long big = (uL >> shr) | (shr ? (uH << ((64 - shr) & 63)) : 0ull);
+    unsigned long long mant = p > 52 ? big : small;
+    const unsigned long long rb = shr ? (uL >> ((shr - 1) & 63)) & 1ull : 0ull;
+    const bool sticky = shr > 1 ? (uL & ((1ull << ((shr - 1) & 63)) - 1ull)) != 0 : false;
+    mant += (rb && (sticky || (mant & 1ull))) ? 1ull : 0ull;
+    const bool carry = mant == (1ull << 53);
+    mant = carry ? mant >> 1 : mant;
+    p += carry ? 1 : 0;
+    const int E = p + s + 1023;
+    double r = __longlong_as_double((long long)((sgn & 0x8000000000000000ull) | ((unsigned long long)(E & 2047) << 52) |
+                                                (mant & 0x000fffffffffffffull)));
+    if (zero) r = 0.0;
+    if (!zero && (E <= 0 || E >= 2047)) r = ot_fixed_to_double_slow(hi, lo, s);
+    return r;
 }
 
 // Persistent: one CTA per SM walks the tiles (column tiles fastest, so that
@@ -380,32 +415,30 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
             umma_commit(accf);  // fires when this issuer's MMAs of the tile have completed
         }
     } else if (warp >= 3) {
-        // epilogue warp e = warp - 3: TMEM lane quadrant warp % 4 (its rows),
-        // columns [16 (e / 4), +16) of the tile
+        // epilogue warp e = warp - 3: TMEM lane quadrant warp % 4 (its rows)
+        // and a quarter of the tile's columns: [16 (e / 4), +16), or
+        // [8 (e / 4), +8) when the tile has at most 32 valid columns (so that
+        // every epilogue warp has work in the narrow updates)
         const int quad = warp & 3, cq = (warp - 3) >> 2;
-        const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cq * 16);
-        for (int i = 0; i < ntl; ++i) {
-            const int tile = (int)blockIdx.x + i * (int)gridDim.x;
-            const int64_t i0 = (int64_t)(tile / ntj) * OT_BM, j0 = (int64_t)(tile % ntj) * OT_BN;
-            const int64_t row = i0 + quad * 32 + lane;
-            const int64_t c0 = j0 + cq * 16;
-            if (row < m) {  // this tile's C_in entries into L2 while its MMAs run
-                for (int j = 0; j < 16; ++j)
-                    if (c0 + j < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(Cin + row + (c0 + j) * ldi));
-            }
-            const bool ok = mbar_wait(accf, (uint32_t)(i & 1));
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (!ok) *bad = 1;
-            if (!__all_sync(0xffffffffu, ok && !*bad)) break;
-            long long hi[16], lo[16];
+        const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16);
+        // drain W columns of the 8 group sums, release the TMEM, convert and store
+        auto epi = [&](auto Wc, int64_t row, int64_t c0) {
+            constexpr int W = decltype(Wc)::value;
+            const uint32_t tl = tq + (uint32_t)(cq * W);
+            long long hi[W], lo[W];
 #pragma unroll
             for (int d = 0; d < OT_DIG; d += 2) {
-                uint32_t va[16], vb[16];
-                tmem_ld16_nowait(tl + (uint32_t)(d * OT_BN), va);
-                tmem_ld16_nowait(tl + (uint32_t)((d + 1) * OT_BN), vb);
+                uint32_t va[W], vb[W];
+                if constexpr (W == 16) {
+                    tmem_ld16_nowait(tl + (uint32_t)(d * OT_BN), va);
+                    tmem_ld16_nowait(tl + (uint32_t)((d + 1) * OT_BN), vb);
+                } else {
+                    tmem_ld8_nowait(tl + (uint32_t)(d * OT_BN), va);
+                    tmem_ld8_nowait(tl + (uint32_t)((d + 1) * OT_BN), vb);
+                }
                 tmem_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
+                for (int j = 0; j < W; ++j) {
                     const long long a = (long long)__float2int_rn(__uint_as_float(va[j]));
                     const long long b = (long long)__float2int_rn(__uint_as_float(vb[j]));
                     if (d == 0) hi[j] = a * 128 + b;
@@ -421,7 +454,7 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
             if (row < m) {
                 const int32_t ex = Ex[row];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
+                for (int h = 0; h < W / 8; ++h) {
                     double cin[8];
                     int32_t ey[8];
 #pragma unroll
@@ -444,6 +477,23 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
                     }
                 }
             }
+        };
+        for (int i = 0; i < ntl; ++i) {
+            const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+            const int64_t i0 = (int64_t)(tile / ntj) * OT_BM, j0 = (int64_t)(tile % ntj) * OT_BN;
+            const int64_t row = i0 + quad * 32 + lane;
+            const bool narrow = N - j0 <= 32;
+            const int64_t c0 = j0 + cq * (narrow ? 8 : 16);
+            if (row < m) {  // this tile's C_in entries into L2 while its MMAs run
+                for (int j = 0; j < (narrow ? 8 : 16); ++j)
+                    if (c0 + j < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(Cin + row + (c0 + j) * ldi));
+            }
+            const bool ok = mbar_wait(accf, (uint32_t)(i & 1));
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!ok) *bad = 1;
+            if (!__all_sync(0xffffffffu, ok && !*bad)) break;
+            if (narrow) epi(std::integral_constant<int, 8>(), row, c0);
+            else epi(std::integral_constant<int, 16>(), row, c0);
         }
     }
     if ((warp == 1 || warp == 2) && lane == 0) umma_commit(mdone);  // fires when every MMA issued has completed
