@@ -106,23 +106,31 @@ template lsq_status rank_update_ext<float>(float*, int64_t, const float*, int64_
 // ---------------------------------------------------------------------------
 // Cholesky
 // ---------------------------------------------------------------------------
-// 1 / sqrt(d) for d > 0.  FP64: an FP32 estimate refined by two Newton steps
-// y <- y + y (1 - d y^2) / 2 in FP64 (six dependent FP64 operations instead of
-// a square root and a division, each of which costs about ten times an FMA
-// on this part); relative error a few units in the last place.
+// 1 / sqrt(d) for d > 0.  FP64: an FP32 estimate (the operand and the
+// estimate moved between FP64 and FP32 with integer operations on the bit
+// patterns, no conversion instruction) refined by one third-order step
+//   e = 1 - d y^2,  y <- y + y e (1/2 + 3/8 e)
+// (from ~23 correct bits to beyond FP64 precision): four dependent FP64
+// operations, since each costs about a hundred cycles of latency on this part
+// and the pivots form the factorization's critical path.  Relative error a
+// few units in the last place.
 template <typename T>
 __device__ __forceinline__ T rsqrt_pivot(T d) {
     if constexpr (sizeof(T) == 4) {
         return (T)1 / sqrtf(d);
     } else {
         if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-        double y = (double)rsqrtf((float)d);
-#pragma unroll
-        for (int it = 0; it < 2; ++it) {
-            const double h = d * y;
-            const double e = fma(-h, y, 1.0);
-            y = fma(0.5 * y, e, y);
-        }
+        const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+        // d in the FP32 normal range: rebias the exponent, keep 23 bits of the significand
+        const uint32_t fb = (uint32_t)((((b >> 52) & 0x7ff) - 1023 + 127) << 23) | (uint32_t)((b >> 29) & 0x7fffff);
+        const uint32_t yb = __float_as_uint(rsqrtf(__uint_as_float(fb)));
+        double y = __longlong_as_double((long long)(((unsigned long long)(((yb >> 23) & 0xff) - 127 + 1023) << 52) |
+                                                    ((unsigned long long)(yb & 0x7fffff) << 29)));
+        const double t = d * y;
+        const double e = fma(-t, y, 1.0);
+        const double c = fma(0.375, e, 0.5);
+        const double ye = y * e;
+        y = fma(ye, c, y);
         return y;
     }
 }
@@ -130,10 +138,11 @@ __device__ __forceinline__ T rsqrt_pivot(T d) {
 // Diagonal block (CNB x CNB) in one CTA, right-looking.  Per column j the
 // column is scaled by r_j = 1/sqrt(d_j) into a separate buffer; then thread 0
 // applies column j's update to the next diagonal entry and forms the next
-// pivot (L_jj = d r, r = 1/sqrt(d)) while warps 1-7 update the rest of the
-// active triangle j < c <= r (row-major enumeration from a table, so that
-// every warp issues full-width FP64 instructions): the pivot's dependent
-// FP64 chain overlaps the update.
+// pivot (L_jj = d r, r = 1/sqrt(d)) while the six warps of the other three
+// schedulers (warps 1-3, 5-7) update the rest of the active triangle
+// j < c <= r (row-major enumeration from a table, so that every warp issues
+// full-width FP64 instructions): the pivot's dependent FP64 chain runs on a
+// scheduler whose FP64 pipe the update leaves idle, overlapping the update.
 template <typename T>
 __global__ void __launch_bounds__(256) k_potrf_diag(T* __restrict__ G, int64_t ld, int64_t n, int64_t k0,
                                                     int32_t* __restrict__ info) {
@@ -145,9 +154,19 @@ __global__ void __launch_bounds__(256) k_potrf_diag(T* __restrict__ G, int64_t l
     __shared__ int bad;
     const int nb = (int)min64(CNB, n - k0);
     const int tid = threadIdx.x;
-    for (int q = tid; q < CNB * CNB; q += 256) {
-        const int r = q & 63, c = q >> 6;
-        D[r][c] = (r < nb && c < nb) ? G[(k0 + r) + (k0 + c) * ld] : (T)0;
+    {
+        // all loads of the block in flight before the stores
+        T x[CNB * CNB / 256];
+#pragma unroll
+        for (int u = 0; u < CNB * CNB / 256; ++u) {
+            const int q = tid + 256 * u, r = q & 63, c = q >> 6;
+            x[u] = (r < nb && c < nb) ? G[(k0 + r) + (k0 + c) * ld] : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < CNB * CNB / 256; ++u) {
+            const int q = tid + 256 * u;
+            D[q & 63][q >> 6] = x[u];
+        }
     }
     for (int e = tid; e < CNB * (CNB - 1) / 2; e += 256) {
         int rr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
@@ -187,11 +206,14 @@ __global__ void __launch_bounds__(256) k_potrf_diag(T* __restrict__ G, int64_t l
                     rj = rn;
                     D[j + 1][j + 1] = d * rn;
                 }
-            } else if (tid >= 32) {
-                // entries 1 .. E-1 of the active triangle (entry 0 is the next pivot)
+            } else if ((tid >> 5) & 3) {
+                // entries 1 .. E-1 of the active triangle (entry 0 is the next
+                // pivot), over warps 1-3 and 5-7
+                const int w = tid >> 5;
+                const int widx = (w - 1 - (w > 4 ? 1 : 0)) * 32 + (tid & 31);  // 0 .. 191
                 const int a = nb - 1 - j;
                 const int E = a * (a + 1) / 2;
-                for (int e = tid - 31; e < E; e += 224) {
+                for (int e = widx + 1; e < E; e += 192) {
                     const int rc = tri[e];
                     const int rr = j + 1 + (rc >> 8), cc = j + 1 + (rc & 255);
                     D[rr][cc] = fma(-colj[rr], colj[cc], D[rr][cc]);
