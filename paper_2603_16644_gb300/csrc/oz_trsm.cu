@@ -183,6 +183,65 @@ __global__ void __launch_bounds__(128) k_ot_rowslice_e(const double* __restrict_
     }
 }
 
+// The same, with the digit planes written as whole 128-byte lines: a CTA
+// converts a 64-row x 64-column block of X (two threads per row, 32 columns
+// each, reading X a column at a time, coalesced over rows), stages the 8 BF16
+// digit tiles in shared memory in the 128-byte-swizzled layout of the TMA
+// (16-byte chunk j of row r at chunk j ^ (r mod 8): conflict-free for one
+// thread per row), and stores each plane's tile with one TMA store.  (Stores
+// of 16 bytes to 32 different rows per warp instruction reach ~1 TB/s; whole
+// lines reach ~6 TB/s.)  tmZ: the X digit planes, boxes of 64 columns x 64
+// rows x 1 plane.
+constexpr int OT_RS_ROWS = 64;
+__global__ void __launch_bounds__(128) k_ot_rowslice_s(const __grid_constant__ CUtensorMap tmZ,
+                                                       const double* __restrict__ X, int64_t m, int64_t mp, int64_t K,
+                                                       int64_t ld, int32_t* __restrict__ Ex,
+                                                       const int32_t* __restrict__ Eblk, int64_t b0, int nbk) {
+    extern __shared__ unsigned char rs_raw[];
+    uint8_t* stage = (uint8_t*)(((uintptr_t)rs_raw + 1023) & ~(uintptr_t)1023);  // [8][64 rows][128 B]
+    const int r = threadIdx.x & (OT_RS_ROWS - 1), h = threadIdx.x >> 6;
+    const int64_t i0 = (int64_t)blockIdx.x * OT_RS_ROWS, kb = (int64_t)blockIdx.y * 64;
+    const int64_t i = i0 + r;
+    int32_t eb = INT32_MIN;
+    if (i < m)
+        for (int b = 0; b < nbk; ++b) eb = max(eb, Eblk[(b0 + b) * m + i]);
+    const int32_t E = eb == INT32_MIN ? 0 : eb;
+    if (blockIdx.y == 0 && h == 0) Ex[i] = E;
+    const double* row = X + i;
+    const int64_t Kr = i < m ? K : 0;
+#pragma unroll 1
+    for (int bb = 0; bb < 2; ++bb) {
+        const int kl = 32 * h + 16 * bb;  // first of 16 columns within the block
+        const int64_t k0 = kb + kl;
+        double xv[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) xv[q] = k0 + q < Kr ? row[(k0 + q) * ld] : 0.0;
+        uint32_t pk[OT_DIG][8];
+#pragma unroll
+        for (int q2 = 0; q2 < 8; ++q2) {
+            const unsigned long long W0 = ot_fields(xv[2 * q2], E), W1 = ot_fields(xv[2 * q2 + 1], E);
+#pragma unroll
+            for (int t = 0; t < OT_DIG; ++t) pk[t][q2] = ot_digit_pair(W0, W1, t);
+        }
+        const int j = kl / 8;  // first 16-byte chunk of the 32 bytes of these columns
+#pragma unroll
+        for (int t = 0; t < OT_DIG; ++t) {
+            uint8_t* rowp = stage + ((size_t)t * OT_RS_ROWS + r) * 128;
+            *(uint4*)(rowp + ((j ^ (r & 7)) << 4)) = make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
+            *(uint4*)(rowp + (((j + 1) ^ (r & 7)) << 4)) = make_uint4(pk[t][4], pk[t][5], pk[t][6], pk[t][7]);
+        }
+    }
+    // the tiles are written through the generic proxy and read by the TMA
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int t = 0; t < OT_DIG; ++t)
+            tma_store_3d(&tmZ, stage + (size_t)t * OT_RS_ROWS * 128, (int)kb, (int)i0, t);
+        tma_store_wait();
+    }
+    __syncthreads();
+}
+
 // Columns of Y (K x N, entry (k, j) at Y[k sk + j sj]): Ey[j] and digit
 // planes Z[(u Np + j) Kp + k] (zero for columns N <= j < Np and for
 // K <= k < Kp).  One CTA per column.
@@ -626,7 +685,13 @@ lsq_status ot_gemm_update(const double* X, int64_t ldx, const double* Y, int64_t
     if (M <= 0 || N <= 0 || K <= 0) return LSQ_OK;
     if (K > OT_KMAX || !ws || ws_bytes < ot_update_ws_bytes(M, N, K)) return LSQ_ERR_ARG;
     const OtUpd U = ot_upd_ptrs(ws, M, N, K);
-    if (xmode == 1)
+    CUtensorMap tzs;
+    if (xmode == 1 && ot_map(&tzs, U.Zx, U.Kp, U.mp, OT_RS_ROWS)) {
+        const size_t rsm = 1024 + (size_t)OT_DIG * OT_RS_ROWS * 128;
+        LSQ_CUDA_TRY(cudaFuncSetAttribute(k_ot_rowslice_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+        k_ot_rowslice_s<<<dim3((unsigned)(U.mp / OT_RS_ROWS), (unsigned)(U.Kp / 64)), 128, rsm, st>>>(
+            tzs, X, M, U.mp, K, ldx, U.Ex, Eblk, b0, nbk);
+    } else if (xmode == 1)
         k_ot_rowslice_e<<<dim3((unsigned)(U.mp / 128), (unsigned)(U.Kp / 64)), 128, 0, st>>>(
             X, M, U.mp, K, ldx, U.Kp, U.Ex, U.Zx, Eblk, b0, nbk);
     else

@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(QPT) k_qr_panel(T* __restrict__ W, int64_t ld,
 // a CTA can only write a buffer again after the next barrier, which every CTA
 // reaches after reading it.
 constexpr int QCT = 256;
+constexpr int QKG = QCT / 64;  // row groups of the previous-panel product (64 threads each)
 
 constexpr int QRC = 32;  // panel rows per warp kept in registers
 
@@ -255,8 +256,8 @@ __global__ void __launch_bounds__(QCT)
         // columns, ld ldvp, row 0 at k0 - QNB): this CTA's rows in shared
         // memory, the QNB rows above the panel by rank 0 from global memory.
         T* Vl = Yall;                      // [QNB][Rp]: rows QNB + r0 + i of V_p
-        T* Wk = Yall + (int64_t)QNB * Rp;  // [4][QNB][QNB + 1] row-group partials, then W and W2
-        T* Ct = Wk + 4 * QNB * (QNB + 1);  // rank 0: [QNB][QNB + 1] the rows above, then their V_p rows
+        T* Wk = Yall + (int64_t)QNB * Rp;    // [QKG][QNB][QNB + 1] row-group partials, then W and W2
+        T* Ct = Wk + QKG * QNB * (QNB + 1);  // rank 0: [QNB][QNB + 1] the rows above, then their V_p rows
         T* Vt = Ct + QNB * (QNB + 1);
         for (int i = tid; i < R; i += QCT) {
             T x[QNB];
@@ -280,9 +281,9 @@ __global__ void __launch_bounds__(QCT)
         }
         __syncthreads();
         {
-            // partial W = V_p^T C: 4 row groups of 64 threads, 4 x 4 blocks
+            // partial W = V_p^T C: QKG row groups of 64 threads, 4 x 4 blocks
             const int kg = tid >> 6, tl = tid & 63, tp = tl & 7, tq = tl >> 3;
-            const int span = (R + 3) / 4;
+            const int span = (R + QKG - 1) / QKG;
             const int i0 = kg * span, i1 = min(nloc, i0 + span);
             T acc[4][4];
 #pragma unroll
@@ -320,8 +321,7 @@ __global__ void __launch_bounds__(QCT)
         __syncthreads();
         for (int q = tid; q < QNB * QNB; q += QCT) {
             const int p = q >> 5, c = q & 31;
-            Wr[p][c] = ((Wk[p * (QNB + 1) + c] + Wk[(QNB + p) * (QNB + 1) + c]) + Wk[(2 * QNB + p) * (QNB + 1) + c]) +
-                       Wk[(3 * QNB + p) * (QNB + 1) + c];
+            Wr[p][c] = tree_sum<T, QKG>(&Wk[p * (QNB + 1) + c], QNB * (QNB + 1));
         }
         cluster.sync();
         // W: the partials of every rank in rank order (the column loop's
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(QCT)
                 for (int q = 0; q < QRC; q += 4) store4(bv + q, a[q], a[q + 1], a[q + 2], a[q + 3]);
             }
             __syncwarp();
-            {
+            if (lane < QRC) {  // lane = row of this warp here
                 const int gr = gr0 + lane;
                 const T x = bv[lane];
                 bv[lane] = (gr < jj || lane >= nv) ? (T)0 : (gr == jj ? (T)1 : (sc.scale ? x / sc.v1 : x));
@@ -627,8 +627,7 @@ __global__ void __launch_bounds__(QCT)
     part[warp][lane] = acc;
     __syncthreads();
     if (warp == 0) {
-        T t = (T)0;
-        for (int g = 0; g < QCT / 32; ++g) t += part[g][lane];
+        const T t = tree_sum<T, QCT / 32>(&part[0][lane], QNB);
         *cluster.map_shared_rank(&all_part[nb & 1][rank][lane], 0) = t;
     }
     cluster.sync();
@@ -885,7 +884,7 @@ template <typename T>
 static size_t qr_cluster_smem(int64_t rows, int qcl, bool fused) {
     const size_t Rp = (size_t)(ceil_div(rows, qcl) | 1);
     const size_t yall = (size_t)qcl * QNB * (QNB + 1);
-    const size_t pre = Rp * QNB + (size_t)6 * QNB * (QNB + 1);
+    const size_t pre = Rp * QNB + (size_t)(QKG + 2) * QNB * (QNB + 1);
     return sizeof(T) * (Rp * QNB + (fused ? std::max(yall, pre) : yall));
 }
 
