@@ -193,29 +193,84 @@ __global__ void __launch_bounds__(128) k_ot_rowslice_e(const double* __restrict_
 // lines reach ~6 TB/s.)  tmZ: the X digit planes, boxes of 64 columns x 64
 // rows x 1 plane.
 constexpr int OT_RS_ROWS = 64;
+// tma_x: X's block comes in by one TMA load (tmX: FP64, boxes of 64 rows x 64
+// columns, zero outside) into shared memory [64 columns][64 rows]; otherwise
+// every thread loads its values (coalesced over rows, a column at a time).
+// own_exp (with tma_x, K <= 64): the row exponents are those of the rows'
+// largest values, formed here (the two threads of a row combine their maxima)
+// instead of from the diagonal kernel's per-block exponents.
+template <bool tma_x, bool own_exp>
 __global__ void __launch_bounds__(128) k_ot_rowslice_s(const __grid_constant__ CUtensorMap tmZ,
+                                                       const __grid_constant__ CUtensorMap tmX,
                                                        const double* __restrict__ X, int64_t m, int64_t mp, int64_t K,
                                                        int64_t ld, int32_t* __restrict__ Ex,
-                                                       const int32_t* __restrict__ Eblk, int64_t b0, int nbk) {
+                                                       const int32_t* __restrict__ Eblk, int64_t b0, int nbk,
+                                                       int32_t* __restrict__ err) {
     extern __shared__ unsigned char rs_raw[];
     uint8_t* stage = (uint8_t*)(((uintptr_t)rs_raw + 1023) & ~(uintptr_t)1023);  // [8][64 rows][128 B]
+    const double* xt = (const double*)(stage + OT_DIG * OT_RS_ROWS * 128);      // [64 columns][64 rows]
+    __shared__ uint64_t xfull;
+    __shared__ unsigned long long rmax[2][OT_RS_ROWS];
+    __shared__ int rs_bad;
     const int r = threadIdx.x & (OT_RS_ROWS - 1), h = threadIdx.x >> 6;
     const int64_t i0 = (int64_t)blockIdx.x * OT_RS_ROWS, kb = (int64_t)blockIdx.y * 64;
     const int64_t i = i0 + r;
-    int32_t eb = INT32_MIN;
-    if (i < m)
-        for (int b = 0; b < nbk; ++b) eb = max(eb, Eblk[(b0 + b) * m + i]);
-    const int32_t E = eb == INT32_MIN ? 0 : eb;
-    if (blockIdx.y == 0 && h == 0) Ex[i] = E;
+    static_assert(tma_x || !own_exp, "own exponents need the staged block");
+    if constexpr (tma_x) {
+        if (threadIdx.x == 0) {
+            rs_bad = 0;
+            mbar_init(&xfull, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            mbar_expect_tx(&xfull, OT_RS_ROWS * 64 * 8);
+            tma_load_2d((void*)xt, &tmX, &xfull, (int)i0, (int)kb);
+        }
+        __syncthreads();
+    }
+    int32_t E = 0;
+    if constexpr (!own_exp) {
+        int32_t eb = INT32_MIN;
+        if (i < m)
+            for (int b = 0; b < nbk; ++b) eb = max(eb, Eblk[(b0 + b) * m + i]);
+        E = eb == INT32_MIN ? 0 : eb;
+    }
     const double* row = X + i;
     const int64_t Kr = i < m ? K : 0;
+    if constexpr (tma_x) {
+        if (!mbar_wait(&xfull, 0)) rs_bad = 1;
+        __syncthreads();
+        if (rs_bad) {  // every thread leaves here together
+            if (threadIdx.x == 0) {
+                set_info_once(err, -2);
+                mbar_wait(&xfull, 0);  // bounded: the copy in flight, before the CTA ends
+            }
+            return;
+        }
+    }
+    if constexpr (own_exp) {
+        unsigned long long mx = 0;
+        for (int q = 0; q < 32; ++q) {
+            const unsigned long long v =
+                (unsigned long long)__double_as_longlong(xt[(32 * h + q) * OT_RS_ROWS + r]) & 0x7fffffffffffffffull;
+            mx = v > mx ? v : mx;
+        }
+        rmax[h][r] = mx;
+        __syncthreads();
+        mx = rmax[0][r] > rmax[1][r] ? rmax[0][r] : rmax[1][r];
+        E = ot_exp_of_max(mx);
+    }
+    if (blockIdx.y == 0 && h == 0) Ex[i] = E;
 #pragma unroll 1
     for (int bb = 0; bb < 2; ++bb) {
         const int kl = 32 * h + 16 * bb;  // first of 16 columns within the block
         const int64_t k0 = kb + kl;
         double xv[16];
+        if constexpr (tma_x) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) xv[q] = k0 + q < Kr ? row[(k0 + q) * ld] : 0.0;
+            for (int q = 0; q < 16; ++q) xv[q] = xt[(kl + q) * OT_RS_ROWS + r];  // zero outside X (TMA fill)
+        } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) xv[q] = k0 + q < Kr ? row[(k0 + q) * ld] : 0.0;
+        }
         uint32_t pk[OT_DIG][8];
 #pragma unroll
         for (int q2 = 0; q2 < 8; ++q2) {
@@ -639,6 +694,7 @@ static int64_t ot_mid(int64_t c0, int64_t c1) {
 }
 
 static bool ot_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t rows, int box_rows);
+static bool ot_map_f64(CUtensorMap* map, const double* base, int64_t rows, int64_t cols, int64_t ld);
 static size_t ot_update_smem() { return 1024 + 2 * OT_DIG * OT_YTILE + OT_XST * OT_XTILE + 512; }
 
 // Scratch of one update with M rows, N columns and inner dimension K.
@@ -685,12 +741,27 @@ lsq_status ot_gemm_update(const double* X, int64_t ldx, const double* Y, int64_t
     if (M <= 0 || N <= 0 || K <= 0) return LSQ_OK;
     if (K > OT_KMAX || !ws || ws_bytes < ot_update_ws_bytes(M, N, K)) return LSQ_ERR_ARG;
     const OtUpd U = ot_upd_ptrs(ws, M, N, K);
-    CUtensorMap tzs;
+    CUtensorMap tzs, txs;
     if (xmode == 1 && ot_map(&tzs, U.Zx, U.Kp, U.mp, OT_RS_ROWS)) {
-        const size_t rsm = 1024 + (size_t)OT_DIG * OT_RS_ROWS * 128;
-        LSQ_CUDA_TRY(cudaFuncSetAttribute(k_ot_rowslice_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
-        k_ot_rowslice_s<<<dim3((unsigned)(U.mp / OT_RS_ROWS), (unsigned)(U.Kp / 64)), 128, rsm, st>>>(
-            tzs, X, M, U.mp, K, ldx, U.Ex, Eblk, b0, nbk);
+        const dim3 rg((unsigned)(U.mp / OT_RS_ROWS), (unsigned)(U.Kp / 64));
+        if (ldx % 2 == 0 && ((uintptr_t)X % 16) == 0 && ot_map_f64(&txs, X, M, K, ldx)) {
+            const size_t rsm = 1024 + (size_t)OT_DIG * OT_RS_ROWS * 128 + (size_t)OT_RS_ROWS * 64 * 8;
+            LSQ_CUDA_TRY(
+                cudaFuncSetAttribute(k_ot_rowslice_s<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+            k_ot_rowslice_s<true, false><<<rg, 128, rsm, st>>>(tzs, txs, X, M, U.mp, K, ldx, U.Ex, Eblk, b0, nbk, err);
+        } else {
+            const size_t rsm = 1024 + (size_t)OT_DIG * OT_RS_ROWS * 128;
+            LSQ_CUDA_TRY(
+                cudaFuncSetAttribute(k_ot_rowslice_s<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+            k_ot_rowslice_s<false, false><<<rg, 128, rsm, st>>>(tzs, tzs, X, M, U.mp, K, ldx, U.Ex, Eblk, b0, nbk, err);
+        }
+    } else if (xmode == 0 && K <= 64 && ldx % 2 == 0 && ((uintptr_t)X % 16) == 0 &&
+               ot_map(&tzs, U.Zx, U.Kp, U.mp, OT_RS_ROWS) && ot_map_f64(&txs, X, M, K, ldx)) {
+        const size_t rsm = 1024 + (size_t)OT_DIG * OT_RS_ROWS * 128 + (size_t)OT_RS_ROWS * 64 * 8;
+        LSQ_CUDA_TRY(cudaFuncSetAttribute(k_ot_rowslice_s<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)rsm));
+        k_ot_rowslice_s<true, true><<<dim3((unsigned)(U.mp / OT_RS_ROWS), 1u), 128, rsm, st>>>(
+            tzs, txs, X, M, U.mp, K, ldx, U.Ex, nullptr, 0, 0, err);
     } else if (xmode == 1)
         k_ot_rowslice_e<<<dim3((unsigned)(U.mp / 128), (unsigned)(U.Kp / 64)), 128, 0, st>>>(
             X, M, U.mp, K, ldx, U.Kp, U.Ex, U.Zx, Eblk, b0, nbk);
@@ -743,6 +814,20 @@ static bool ot_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t rows,
     cuuint32_t estr[3] = {1u, 1u, 1u};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// FP64 column-major rows x cols (leading dimension ld, even; base 16-byte
+// aligned): boxes of 64 rows x 64 columns, no swizzle, zero fill outside.
+static bool ot_map_f64(CUtensorMap* map, const double* base, int64_t rows, int64_t cols, int64_t ld) {
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 8)};
+    cuuint32_t box[2] = {(cuuint32_t)OT_RS_ROWS, 64u};
+    cuuint32_t estr[2] = {1u, 1u};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
