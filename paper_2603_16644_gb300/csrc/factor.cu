@@ -442,33 +442,79 @@ lsq_status launch_lu(double* H, int64_t n, int64_t ld, int32_t* piv, int32_t* in
 // ---------------------------------------------------------------------------
 // Triangular solves on a vector, many CTAs in a wavefront.  CTA v takes its
 // row block from an atomic counter (v-th CTA to start), so every block it
-// waits for belongs to a CTA that has already started; it stages each
+// waits for belongs to a CTA that has already started.  It stages each
 // off-diagonal 32 x 32 block of the operator while the solution of that block
-// is still being computed, waits for the block's flag (bounded: 2 s of
-// %globaltimer, then an error is recorded and the failure passed on), applies
-// it, and finally solves its diagonal block with shuffles and publishes y_b
-// with a release flag.  The diagonal block, its reciprocal pivots and the
-// block's own right-hand side are staged before the first wait; the block's
-// rows are scaled to a unit diagonal, so the dependent chain of the diagonal
-// solve is one shuffle and one FMA per column.
+// is still being computed, waits for that solution (bounded: 2 s of
+// %globaltimer, then an error is recorded and NaN passed on), applies it, and
+// finally solves its diagonal block and publishes y_b.
+//
+// Publication: the solution is also written to a scratch copy `pub` that the
+// launch fills with all-ones bit patterns (a NaN that arithmetic does not
+// produce; a computed value with that pattern is published as the default
+// NaN).  A waiting CTA polls the 32 entries it needs directly, one lane each,
+// so a block's solution reaches the next CTA in one trip through L2 (no flag,
+// no fence).
+//
+// Diagonal block: staged before the first wait with its reciprocal pivots and
+// the block's own right-hand side, rows scaled to a unit diagonal.  For the
+// Cholesky factor (L and L^T) a CTA that has a block to wait for also forms
+// the inverse of its diagonal block while it waits, and applies it as a
+// product: a few dependent FP64 operations instead of a 32-step chain.  The
+// explicit inverse adds an error of order u kappa(L_bb) |y_b|, below the
+// u kappa(A_p)^2 that the normal equations carry; the other factors (R_s, the
+// LU factors) keep the substitution.
 // Partial sums are combined in a fixed order, so the result does not depend
 // on timing.
 // ---------------------------------------------------------------------------
 template <typename T>
+struct TrsvPub;
+template <>
+struct TrsvPub<double> {
+    static __device__ __forceinline__ void put(double* p, double v) {
+        unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        if (b == ~0ull) b = 0x7ff8000000000000ull;
+        asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(b) : "memory");
+    }
+    // the entry, or false while it is unpublished
+    static __device__ __forceinline__ bool get(const double* p, double& v) {
+        unsigned long long b;
+        asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(b) : "l"(p) : "memory");
+        v = __longlong_as_double((long long)b);
+        return b != ~0ull;
+    }
+};
+template <>
+struct TrsvPub<float> {
+    static __device__ __forceinline__ void put(float* p, float v) {
+        unsigned b = __float_as_uint(v);
+        if (b == ~0u) b = 0x7fc00000u;
+        asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(b) : "memory");
+    }
+    static __device__ __forceinline__ bool get(const float* p, float& v) {
+        unsigned b;
+        asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(b) : "l"(p) : "memory");
+        v = __uint_as_float(b);
+        return b != ~0u;
+    }
+};
+
+template <typename T>
 __global__ void __launch_bounds__(128) k_trsv_wave(int kind, const T* __restrict__ M, int64_t n, int64_t ld, T* y,
-                                                   int32_t* sync, const int32_t* __restrict__ info,
+                                                   int32_t* sync, T* pub, const int32_t* __restrict__ info,
                                                    int32_t* __restrict__ err) {
     if (info && *info != 0) return;
     __shared__ T blk[32][33];
-    __shared__ T dgb[32][33];  // diagonal block, rows scaled to a unit diagonal
+    __shared__ T dgb[32][33];  // diagonal block, rows scaled to a unit diagonal (then its inverse, see below)
+    __shared__ T xin[32][33];  // inverse of the scaled block
     __shared__ T part[4][32];
     __shared__ T yk[32];
     __shared__ T rin[32];
+    __shared__ T wsh[32];
     __shared__ int vb, failed;
     const int tid = threadIdx.x, r = tid & 31, q = tid >> 5;
     const int nblk = (int)((n + 31) / 32);
     if (tid == 0) {
-        vb = atomicAdd(&sync[0], 1);
+        vb = atomicAdd(&sync[0], 1) + 1;  // the counter starts at -1 (all-ones fill)
         failed = 0;
     }
     __syncthreads();
@@ -476,6 +522,7 @@ __global__ void __launch_bounds__(128) k_trsv_wave(int kind, const T* __restrict
     const bool forward = (kind == TB_LOWER || kind == TB_UNIT_LOWER);
     const bool trans = (kind == TB_LOWER_T);  // operator entry (i, j) = M[j + i ld]
     const bool unit = (kind == TB_UNIT_LOWER);
+    const bool use_inv = (kind == TB_LOWER || kind == TB_LOWER_T) && v > 0;
     const int b = forward ? v : nblk - 1 - v;
     const int64_t b0 = (int64_t)b * 32;
     const int bs = (int)min64(32, n - b0);
@@ -495,6 +542,27 @@ __global__ void __launch_bounds__(128) k_trsv_wave(int kind, const T* __restrict
     for (int e = tid; e < 1024; e += 128) {
         const int rr = e & 31, jj = e >> 5;
         if (rr != jj) dgb[rr][jj] *= rin[rr];
+        if (use_inv) xin[rr][jj] = rr == jj ? (T)1 : (T)0;
+    }
+    if (use_inv) {
+        // X = D'^{-1} for the unit triangular D' (rows and columns in solve
+        // order: ascending for L, descending for L^T), right-looking: after
+        // step j, row j of X is final and updates the rows solved after it.
+        __syncthreads();
+        for (int j = 0; j < 31; ++j) {
+            const int w = j + 1, cnt = (31 - j) * w;
+            for (int e = tid; e < cnt; e += 128) {
+                const int ro = j + 1 + e / w, co = e % w;  // solve-order row (> j) and column (<= j)
+                const int jr = forward ? j : 31 - j, rr = forward ? ro : 31 - ro, cc = forward ? co : 31 - co;
+                xin[rr][cc] = fma(-dgb[rr][jr], xin[jr][cc], xin[rr][cc]);
+            }
+            __syncthreads();
+        }
+        // y_b = X diag(rin) w: fold the pivots into the columns
+        for (int e = tid; e < 1024; e += 128) {
+            const int rr = e & 31, cc = e >> 5;
+            dgb[rr][cc] = xin[rr][cc] * rin[cc];
+        }
     }
     T acc0 = (T)0, acc1 = (T)0;
     for (int st = 0; st < v; ++st) {
@@ -508,26 +576,30 @@ __global__ void __launch_bounds__(128) k_trsv_wave(int kind, const T* __restrict
             if (rr < bs && jj < ks) val = trans ? M[(k0 + jj) + (b0 + rr) * ld] : M[(b0 + rr) + (k0 + jj) * ld];
             blk[rr][jj] = val;
         }
-        if (tid == 0) {
-            const int32_t* f = sync + 1 + k;
-            int32_t fv = 0;
+        if (tid < 32) {
+            // poll the ks published entries of block k, one lane each
+            T got = (T)0;
+            bool have = r >= ks;
+            bool timed_out = false;
             uint64_t t0 = 0;
             for (uint32_t it = 0;; ++it) {
-                asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(fv) : "l"(f) : "memory");
-                if (fv != 0) break;
-                if ((it & 63u) == 0) {
+                if (!have) have = TrsvPub<T>::get(pub + k0 + r, got);
+                if (__all_sync(0xffffffffu, have)) break;
+                if ((it & 63u) == 63u) {
                     uint64_t t;
                     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-                    if (it == 0) t0 = t;
-                    else if (t - t0 > 2000000000ull) break;
+                    if (it == 63u) t0 = t;
+                    if (__shfl_sync(0xffffffffu, t - t0 > 2000000000ull ? 1 : 0, 0)) {
+                        timed_out = true;
+                        break;
+                    }
                 }
             }
-            if (fv != 1) failed = 1;
+            yk[r] = r < ks ? got : (T)0;
+            if (timed_out && r == 0) failed = 1;
         }
         __syncthreads();
         if (failed) break;
-        if (tid < 32) yk[tid] = tid < ks ? __ldcg(y + k0 + tid) : (T)0;
-        __syncthreads();
 #pragma unroll
         for (int j = 0; j < 8; j += 2) {
             acc0 = fma(-blk[r][q * 8 + j], yk[q * 8 + j], acc0);
@@ -537,41 +609,58 @@ __global__ void __launch_bounds__(128) k_trsv_wave(int kind, const T* __restrict
     }
     part[q][r] = acc0 + acc1;
     __syncthreads();
+    if (use_inv) {
+        // w = c_b - sum of the applied blocks, then y_b = (X diag(rin)) w,
+        // 8 columns per warp in two chains, the warps' parts summed pairwise
+        if (tid < 32) wsh[r] = vv + ((part[0][r] + part[1][r]) + (part[2][r] + part[3][r]));
+        __syncthreads();
+        T s0 = (T)0, s1 = (T)0;
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            s0 = fma(dgb[r][q * 8 + j], wsh[q * 8 + j], s0);
+            s1 = fma(dgb[r][q * 8 + j + 1], wsh[q * 8 + j + 1], s1);
+        }
+        part[q][r] = s0 + s1;
+        __syncthreads();
+        if (tid < 32) vv = (part[0][r] + part[1][r]) + (part[2][r] + part[3][r]);
+    }
     if (tid < 32) {
         const bool ok = !failed;
-        vv = vv + part[0][r] + part[1][r] + part[2][r] + part[3][r];
-        vv = vv * rin[r];  // unit-diagonal system from here on
-        if (forward) {
-            for (int jj = 0; jj < bs; ++jj) {
-                const T vj = __shfl_sync(0xffffffffu, vv, jj);
-                if (r > jj && r < bs) vv = fma(-dgb[r][jj], vj, vv);
-            }
-        } else {
-            for (int jj = bs - 1; jj >= 0; --jj) {
-                const T vj = __shfl_sync(0xffffffffu, vv, jj);
-                if (r < jj) vv = fma(-dgb[r][jj], vj, vv);
+        if (!use_inv) {
+            vv = vv + part[0][r] + part[1][r] + part[2][r] + part[3][r];
+            vv = vv * rin[r];  // unit-diagonal system from here on
+            if (forward) {
+                for (int jj = 0; jj < bs; ++jj) {
+                    const T vj = __shfl_sync(0xffffffffu, vv, jj);
+                    if (r > jj && r < bs) vv = fma(-dgb[r][jj], vj, vv);
+                }
+            } else {
+                for (int jj = bs - 1; jj >= 0; --jj) {
+                    const T vj = __shfl_sync(0xffffffffu, vv, jj);
+                    if (r < jj) vv = fma(-dgb[r][jj], vj, vv);
+                }
             }
         }
-        if (ok && r < bs) y[b0 + r] = vv;
-        __threadfence();
-        __syncwarp();
-        if (r == 0) {
-            if (!ok) set_info_once(err, -2);
-            int32_t flag = ok ? 1 : 2;  // 2 passes the failure on to the blocks that wait
-            asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(sync + 1 + b), "r"(flag) : "memory");
+        if (r < bs) {
+            if (ok) y[b0 + r] = vv;
+            // a failed block passes NaN on, so that the blocks after it do not wait
+            TrsvPub<T>::put(pub + b0 + r, ok ? vv : (T)NAN);
         }
+        if (!ok && r == 0) set_info_once(err, -2);
     }
 }
 
-size_t trsv_sync_ints(int64_t n) { return (size_t)ceil_div(n, 32) + 1; }
+// Scratch: the block counter, then the published copy of the solution (8-byte aligned).
+size_t trsv_sync_ints(int64_t n) { return 2 + 2 * (size_t)n; }
 
 template <typename T>
 lsq_status launch_trsv(int kind, const T* M, int64_t n, int64_t ld, T* y, const int32_t* info, int32_t* sync,
                        int32_t* err, cudaStream_t st) {
-    if (!sync || n <= 0 || n > (int64_t)1 << 30) return LSQ_ERR_ARG;
+    if (!sync || n <= 0 || n > (int64_t)1 << 30 || ((uintptr_t)sync % 8) != 0) return LSQ_ERR_ARG;
     int64_t nblk = ceil_div(n, 32);
-    LSQ_CUDA_TRY(cudaMemsetAsync(sync, 0, sizeof(int32_t) * (size_t)(nblk + 1), st));
-    k_trsv_wave<T><<<(unsigned)nblk, 128, 0, st>>>(kind, M, n, ld, y, sync, info, err);
+    // all ones: the counter reads -1, every published entry is unset
+    LSQ_CUDA_TRY(cudaMemsetAsync(sync, 0xff, sizeof(int32_t) * trsv_sync_ints(n), st));
+    k_trsv_wave<T><<<(unsigned)nblk, 128, 0, st>>>(kind, M, n, ld, y, sync, (T*)(sync + 2), info, err);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
 }

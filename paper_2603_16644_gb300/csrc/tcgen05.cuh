@@ -78,9 +78,12 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void*
                  : "memory");
 }
 
-__device__ __forceinline__ void tma_store_wait() {
+// Commit the bulk stores issued by this thread and wait until their shared
+// memory sources have been read (the source may then be reused or the CTA
+// may end; the global writes complete with the grid).
+__device__ __forceinline__ void tma_store_wait_read() {
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
