@@ -480,54 +480,69 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
                 cnt[0] = xq + 1;
             }
         }
-    } else if ((warp == 1 || warp == 2) && lane == 0) {
+    } else if (warp == 1 || warp == 2) {
         // MMA issuers: pair (t, u) with t + u <= 7 into accumulator t + u.
-        // One thread issues an MMA only every ~90 cycles, so two warps issue,
-        // each owning the accumulators of its groups (18 pairs each): no two
-        // threads accumulate into the same TMEM columns.  The 4 K steps of one
-        // pair go back to back into the same accumulator (measured:
-        // interleaving accumulators, even with operand A kept in the collector
-        // buffer, is 40 % - 3x slower).  Both commit every stage and tile.
-        const int iss = warp - 1;
-        constexpr unsigned OWN1 = (1u << 1) | (1u << 2) | (1u << 5) | (1u << 6);  // groups of issuer 1
-        const uint32_t idesc = umma_idesc(1u, OT_BM, OT_BN);
-        int xq = 0, g = 0;
-        for (int i = 0; i < ntl && !*bad; ++i) {
-            if (i > 0 && !mbar_wait(tfree, (uint32_t)((i - 1) & 1))) {
-                *bad = 1;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int s = 0; s < nslab && !*bad; ++s, ++g) {
-                const int ys = g & 1;
-                if (!mbar_wait(&yfull[ys], (uint32_t)((g >> 1) & 1))) {
+        // Two warps issue, each owning the accumulators of its groups (18
+        // pairs each): no two threads accumulate into the same TMEM columns.
+        // The 4 K steps of one pair go back to back into the same accumulator
+        // (measured: interleaving accumulators, even with operand A kept in
+        // the collector buffer, is 40 % - 3x slower).  Each warp runs its loop
+        // in convergence, fully unrolled over the digits with the ownership
+        // fixed at compile time, so that the descriptors are warp-uniform
+        // values; lane 0 issues (measured: descriptors formed per MMA by a
+        // single divergent thread cost ~160 cycles per MMA and issuer, against
+        // ~48 cycles per MMA for the pair when they are uniform).  Both
+        // commit every stage and tile.
+        const uint32_t lead = lane == 0 ? 1u : 0u;
+        auto issue = [&](auto issc) {
+            constexpr int ISS = decltype(issc)::value;
+            constexpr unsigned OWN1 = (1u << 1) | (1u << 2) | (1u << 5) | (1u << 6);  // groups of issuer 1
+            constexpr uint32_t idesc = umma_idesc(1u, OT_BM, OT_BN);
+            const uint64_t dx0 = umma_desc(smem_u32(sX)), dy0 = umma_desc(smem_u32(sY));
+            int xq = 0, g = 0;
+            for (int i = 0; i < ntl; ++i) {
+                if (__shfl_sync(0xffffffffu, *bad, 0)) return;
+                if (i > 0 && !__all_sync(0xffffffffu, mbar_wait(tfree, (uint32_t)((i - 1) & 1)))) {
                     *bad = 1;
-                    break;
+                    return;
                 }
-                cnt[iss ? 5 : 3] = g + 1;
-                for (int t = 0; t < OT_DIG; ++t, ++xq) {
-                    const int xs = xq % OT_XST;
-                    if (!mbar_wait(&xfull[xs], (uint32_t)((xq / OT_XST) & 1))) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int s = 0; s < nslab; ++s, ++g, xq += OT_DIG) {
+                    const int ys = g & 1;
+                    if (!__all_sync(0xffffffffu, mbar_wait(&yfull[ys], (uint32_t)((g >> 1) & 1)))) {
                         *bad = 1;
-                        break;
+                        return;
                     }
-                    cnt[iss ? 4 : 1] = xq + 1;
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint64_t ad = umma_desc(smem_u32(sX + xs * OT_XTILE));
-                    for (int u = 0; u + t < OT_DIG; ++u) {
-                        if ((int)((OWN1 >> (t + u)) & 1u) != iss) continue;
-                        const uint64_t bd = umma_desc(smem_u32(sY + (ys * OT_DIG + u) * OT_YTILE));
-                        const uint32_t acc = tmem + (uint32_t)((t + u) * OT_BN);
+                    if (lead) cnt[ISS ? 5 : 3] = g + 1;
+                    const uint64_t dy = dy0 + (uint64_t)(ys * (OT_DIG * OT_YTILE >> 4));
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)  // 4 x 16 BF16 of K per stage
-                            umma_f16(acc, ad + 2 * kk, bd + 2 * kk, idesc, (s | t | kk) != 0 ? 1u : 0u);
+                    for (int t = 0; t < OT_DIG; ++t) {
+                        const int xs = (xq + t) % OT_XST;
+                        if (!__all_sync(0xffffffffu, mbar_wait(&xfull[xs], (uint32_t)(((xq + t) / OT_XST) & 1)))) {
+                            *bad = 1;
+                            return;
+                        }
+                        if (lead) cnt[ISS ? 4 : 1] = xq + t + 1;
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint64_t ad = dx0 + (uint64_t)(xs * (OT_XTILE >> 4));
+#pragma unroll
+                        for (int u = 0; u + t < OT_DIG; ++u) {
+                            if ((int)((OWN1 >> (t + u)) & 1u) != ISS) continue;
+                            const uint64_t bd = dy + (uint64_t)(u * (OT_YTILE >> 4));
+                            const uint32_t acc = tmem + (uint32_t)((t + u) * OT_BN);
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)  // 4 x 16 BF16 of K per stage
+                                umma_f16_w(acc, ad + 2 * kk, bd + 2 * kk, idesc, (s | t | kk) != 0 ? 1u : 0u, lead);
+                        }
+                        umma_commit_w(&xempty[xs], lead);
                     }
-                    umma_commit(&xempty[xs]);
+                    umma_commit_w(&yempty[ys], lead);
                 }
-                umma_commit(&yempty[ys]);
+                umma_commit_w(accf, lead);  // fires when this issuer's MMAs of the tile have completed
             }
-            umma_commit(accf);  // fires when this issuer's MMAs of the tile have completed
-        }
+        };
+        if (warp == 1) issue(std::integral_constant<int, 0>());
+        else issue(std::integral_constant<int, 1>());
     } else if (warp >= 3) {
         // epilogue warp e = warp - 3: TMEM lane quadrant warp % 4 (its rows)
         // and a quarter of the tile's columns: [16 (e / 4), +16), or

@@ -147,6 +147,27 @@ __device__ __forceinline__ void umma_f8(uint32_t tmem_d, uint64_t a, uint64_t b,
         : "memory");
 }
 
+// The same MMA executed by a whole warp in convergence (so that the compiler
+// keeps the warp-uniform descriptors in uniform registers), issued by the
+// lanes with lead != 0 (one lane).
+__device__ __forceinline__ void umma_f16_w(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum,
+                                           uint32_t lead) {
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.ne.b32 q, %5, 0;\n\t"
+        "@q tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum), "r"(lead)
+        : "memory");
+}
+
+// Commit by the lanes with lead != 0 (the lane that issued the MMAs).
+__device__ __forceinline__ void umma_commit_w(uint64_t* bar, uint32_t lead) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %1, 0;\n\t"
+        "@q tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(smem_u32(bar)),
+        "r"(lead)
+        : "memory");
+}
+
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
