@@ -515,6 +515,10 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
                     }
                     if (lead) cnt[ISS ? 5 : 3] = g + 1;
                     const uint64_t dy = dy0 + (uint64_t)(ys * (OT_DIG * OT_YTILE >> 4));
+                    // 16-wide K steps past K (zero digits) are not issued: lane
+                    // 0's issue predicate per step, set once per slab
+                    const int64_t krem = K - (int64_t)s * OT_BK;
+                    const uint32_t lk[4] = {lead, krem > 16 ? lead : 0u, krem > 32 ? lead : 0u, krem > 48 ? lead : 0u};
 #pragma unroll
                     for (int t = 0; t < OT_DIG; ++t) {
                         const int xs = (xq + t) % OT_XST;
@@ -532,7 +536,7 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
                             const uint32_t acc = tmem + (uint32_t)((t + u) * OT_BN);
 #pragma unroll
                             for (int kk = 0; kk < 4; ++kk)  // 4 x 16 BF16 of K per stage
-                                umma_f16_w(acc, ad + 2 * kk, bd + 2 * kk, idesc, (s | t | kk) != 0 ? 1u : 0u, lead);
+                                umma_f16_w(acc, ad + 2 * kk, bd + 2 * kk, idesc, (s | t | kk) != 0 ? 1u : 0u, lk[kk]);
                         }
                         umma_commit_w(&xempty[xs], lead);
                     }
@@ -792,7 +796,7 @@ lsq_status ot_gemm_update(const double* X, int64_t ldx, const double* Y, int64_t
     const int ntj = (int)(U.Np / OT_BN), ntiles = (int)(ntj * (U.mp / OT_BM));
     const int grid = std::min(ntiles, device_sm_count());
     stage_mark(ST_K_UPDATE, true, st);
-    k_ot_update<<<grid, OT_THREADS, smem, st>>>(tx, ty, M, N, U.Kp, U.Ex, U.Ey, Cin, ldi, Cout, ldo, err, ntj,
+    k_ot_update<<<grid, OT_THREADS, smem, st>>>(tx, ty, M, N, K, U.Ex, U.Ey, Cin, ldi, Cout, ldo, err, ntj,
                                                 ntiles);
     LSQ_LAUNCH_CHECK();
     stage_mark(ST_K_UPDATE, false, st, 36.0 * 2.0 * (double)M * (double)N * (double)K);

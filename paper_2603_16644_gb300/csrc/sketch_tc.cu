@@ -34,10 +34,12 @@ __device__ __forceinline__ uint32_t tc_idesc() {
     return umma_idesc(KIND == 0 ? 1u : 0u, TC_BM, BN);
 }
 
+// executed by the whole issuer warp; lane `lead` issues
 template <int KIND>
-__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
-    if (KIND == 2) umma_f8(tmem_d, a, b, idesc, accum);
-    else umma_f16(tmem_d, a, b, idesc, accum);
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum,
+                                     uint32_t lead) {
+    if (KIND == 2) umma_f8_w(tmem_d, a, b, idesc, accum, lead);
+    else umma_f16_w(tmem_d, a, b, idesc, accum, lead);
 }
 
 template <int KIND, int BN>
@@ -108,25 +110,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tma_load_2d(sB + s * BBYTES, &tmB, &full[s], x, (int)n0);
             *issued = kb + 1;
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
+    } else if (warp == 1) {
+        // MMA issuer: the whole warp runs the loop in convergence, so that the
+        // stage descriptors are warp-uniform values; lane 0 issues
+        const uint32_t lead = lane == 0 ? 1u : 0u;
         const uint32_t idesc = tc_idesc<KIND, BN>();
+        const uint64_t da0 = umma_desc(smem_u32(sA)), db0 = umma_desc(smem_u32(sB));
         for (int kb = 0; kb < nk; ++kb) {
-            int s = kb % ST, r = kb / ST;
-            if (!mbar_wait(&full[s], (uint32_t)(r & 1))) {
+            const int s = kb % ST, r = kb / ST;
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (uint32_t)(r & 1)))) {
                 *bad = 1;
                 break;
             }
-            *consumed = kb + 1;
+            if (lead) *consumed = kb + 1;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            uint64_t ad = umma_desc(smem_u32(sA + s * TC_TILE_BYTES));
-            uint64_t bd = umma_desc(smem_u32(sB + s * BBYTES));
+            const uint64_t ad = da0 + (uint64_t)(s * (TC_TILE_BYTES >> 4));
+            const uint64_t bd = db0 + (uint64_t)(s * (BBYTES >> 4));
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)  // 4 x 32 bytes of K per stage
-                umma<KIND>(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0 ? 1u : 0u);
-            umma_commit(&empty[s]);
+                umma<KIND>(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0 ? 1u : 0u, lead);
+            umma_commit_w(&empty[s], lead);
         }
-        umma_commit(accb);  // fires when every MMA issued above has completed
+        umma_commit_w(accb, lead);  // fires when every MMA issued above has completed
     } else if (warp >= 2) {
         // epilogue: TMEM lanes 32*(warp % 4) .. +31 hold rows of the tile
         bool ok = mbar_wait(accb, 0);

@@ -159,6 +159,16 @@ __device__ __forceinline__ void umma_f16_w(uint32_t tmem_d, uint64_t a, uint64_t
         : "memory");
 }
 
+// kind::f8f6f4 (E4M3 operands) in the same warp-converged form.
+__device__ __forceinline__ void umma_f8_w(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum,
+                                          uint32_t lead) {
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.ne.b32 q, %5, 0;\n\t"
+        "@q tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum), "r"(lead)
+        : "memory");
+}
+
 // Commit by the lanes with lead != 0 (the lane that issued the MMAs).
 __device__ __forceinline__ void umma_commit_w(uint64_t* bar, uint32_t lead) {
     asm volatile(
