@@ -219,23 +219,33 @@ def measured_peaks():
 # DRAM traffic of one top-level update launch (M = 65536, N = K = 512: the
 # largest update of A_p = A R^{-1} at this shape), dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the kernel built from the
-# source whose hash is recorded; reported only while the source is unchanged.
-OT_UPDATE_TOP_TRAFFIC = {"bytes": 824.383488e6 + 283.055104e6, "src_sha256_16": "19d365b90fb4a45b",
+# source whose hash is recorded; reported only while that source is unchanged.
+OT_UPDATE_TOP_TRAFFIC = {"bytes": 829.841920e6 + 280.099072e6, "src_sha256_16": "6464514722d30c43",
                          "profile": "profiles/k_ot_update_65536x512x512.md"}
 
 
-def _src_hash(*rels):
+def update_kernel_src_hash():
+    """sha256 (first 16 hex digits) of the source of the update kernel: the
+    constants and the code from the FP64 converters through the end of
+    k_ot_update in oz_trsm.cu, and the two headers it includes; None if the
+    markers are missing."""
     import hashlib
 
-    h = hashlib.sha256()
-    for rel in rels:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()[:16]
-
-
-OT_UPDATE_SOURCES = ("paper_2603_16644_gb300/csrc/oz_trsm.cu", "paper_2603_16644_gb300/csrc/tcgen05.cuh",
-                     "paper_2603_16644_gb300/csrc/common.cuh")
+    csrc = os.path.join(ROOT, "paper_2603_16644_gb300", "csrc")
+    try:
+        with open(os.path.join(csrc, "oz_trsm.cu")) as f:
+            src = f.read()
+        c0, c1 = src.index("constexpr int OT_DIG"), src.index("constexpr int32_t OT_NONFINITE")
+        k0, k1 = src.index("// Results outside the normal range (rare)"), src.index("// Diagonal block:")
+        h = hashlib.sha256()
+        h.update(src[c0:c1].encode())
+        h.update(src[k0:k1].encode())
+        for name in ("tcgen05.cuh", "common.cuh"):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+        return h.hexdigest()[:16]
+    except (OSError, ValueError):
+        return None
 
 
 def dominant_roofline(stages, upd_records, fp64_probe):
@@ -258,7 +268,7 @@ def dominant_roofline(stages, upd_records, fp64_probe):
         top = [(ms, w) for ms, w in upd_records if w == wmax]
         top_ms = sum(ms for ms, _ in top) / max(1, len(top))
         achieved = wmax / (top_ms / 1000.0) / 1e12 if top else 0.0
-        fresh = _src_hash(*OT_UPDATE_SOURCES) == OT_UPDATE_TOP_TRAFFIC["src_sha256_16"]
+        fresh = update_kernel_src_hash() == OT_UPDATE_TOP_TRAFFIC["src_sha256_16"]
         return {"bound": "tensor", "kernel": "k_ot_update (FP64 by BF16 digit slicing), top-level launch M=65536 N=K=512",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": OT_UPDATE_TOP_TRAFFIC["bytes"] if fresh else None,
