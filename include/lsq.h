@@ -313,6 +313,14 @@ lsq_status lsq_trsm_tc(const double* A, int64_t m, int64_t n, int64_t lda, const
  * Process-wide; for comparisons. */
 int32_t lsq_set_fp64_emulation(int32_t enable);
 
+/* Test-only fault injection (no GPU fault): the bound, in nanoseconds, of
+ * each wait of the wavefront triangular solves for another block's solution
+ * (default 2e9).  A wait that runs out records -2 in `info` and passes NaN on
+ * to the blocks after it; the kernel returns normally and the context stays
+ * usable.  Process-wide; returns the previous bound, or -1 (unchanged) for
+ * ns <= 0. */
+int64_t lsq_test_set_solve_wait_ns(int64_t ns);
+
 /* ---- Batched solves (many independent problems of uneven shape) --------- */
 
 /* One problem of a batch: device pointers A (m x n, ld lda), b (m), x (n),

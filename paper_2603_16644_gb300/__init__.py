@@ -87,6 +87,7 @@ def lib():
             "lsq_gram_tc_workspace_size": (_sz, [_i64, _i64]),
             "lsq_gram_tc": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
             "lsq_set_fp64_emulation": (C.c_int32, [C.c_int32]),
+            "lsq_test_set_solve_wait_ns": (_i64, [_i64]),
             "lsq_gemm_tn_tc_workspace_size": (_sz, [_i64, _i64]),
             "lsq_gemm_tn_tc": (C.c_int32, [_vp, _i64, _vp, _i64, _i64, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
         }
@@ -319,6 +320,13 @@ def set_fp64_emulation(enable: bool) -> bool:
     """Route the FP64 Gram (PNE) and A_p = A R^{-1} through the tensor cores
     (True, the default) or the FP64 CUDA cores; returns the previous setting."""
     return bool(lib().lsq_set_fp64_emulation(int(enable)))
+
+
+def test_set_solve_wait_ns(ns: int) -> int:
+    """Test-only: bound (ns) of each wait of the triangular solves for another
+    block's solution; a wait that runs out records -2 in info.  Returns the
+    previous bound."""
+    return int(lib().lsq_test_set_solve_wait_ns(int(ns)))
 
 
 def factor_solve(G, c, Rs=None, hpne=False):

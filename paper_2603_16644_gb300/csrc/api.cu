@@ -400,6 +400,11 @@ const char* lsq_last_cuda_error(void) { return cudaGetErrorString((cudaError_t)g
 
 int64_t lsq_launch_count(void) { return (int64_t)g_launches.load(); }
 
+int64_t lsq_test_set_solve_wait_ns(int64_t ns) {
+    if (ns <= 0) return -1;
+    return (int64_t)lsq::set_trsv_wait_ns((uint64_t)ns);
+}
+
 int32_t lsq_set_fp64_emulation(int32_t enable) {
     int32_t prev = g_fp64_emulation ? 1 : 0;
     g_fp64_emulation = enable != 0;

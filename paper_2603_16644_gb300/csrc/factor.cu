@@ -445,7 +445,8 @@ lsq_status launch_lu(double* H, int64_t n, int64_t ld, int32_t* piv, int32_t* in
 // waits for belongs to a CTA that has already started.  It stages each
 // off-diagonal 32 x 32 block of the operator while the solution of that block
 // is still being computed, waits for that solution (bounded: 2 s of
-// %globaltimer, then an error is recorded and NaN passed on), applies it, and
+// %globaltimer unless a test shortened it, then -2 is recorded and NaN passed
+// on), applies it, and
 // finally solves its diagonal block and publishes y_b.
 //
 // Publication: the solution is also written to a scratch copy `pub` that the
@@ -501,7 +502,7 @@ struct TrsvPub<float> {
 template <typename T>
 __global__ void __launch_bounds__(128) k_trsv_wave(int kind, const T* __restrict__ M, int64_t n, int64_t ld, T* y,
                                                    int32_t* sync, T* pub, const int32_t* __restrict__ info,
-                                                   int32_t* __restrict__ err) {
+                                                   int32_t* __restrict__ err, uint64_t wait_ns) {
     if (info && *info != 0) return;
     __shared__ T blk[32][33];
     __shared__ T dgb[32][33];  // diagonal block, rows scaled to a unit diagonal (then its inverse, see below)
@@ -581,18 +582,16 @@ __global__ void __launch_bounds__(128) k_trsv_wave(int kind, const T* __restrict
             T got = (T)0;
             bool have = r >= ks;
             bool timed_out = false;
-            uint64_t t0 = 0;
-            for (uint32_t it = 0;; ++it) {
+            uint64_t t0;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+            for (;;) {
                 if (!have) have = TrsvPub<T>::get(pub + k0 + r, got);
                 if (__all_sync(0xffffffffu, have)) break;
-                if ((it & 63u) == 63u) {
-                    uint64_t t;
-                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-                    if (it == 63u) t0 = t;
-                    if (__shfl_sync(0xffffffffu, t - t0 > 2000000000ull ? 1 : 0, 0)) {
-                        timed_out = true;
-                        break;
-                    }
+                uint64_t t;  // lane 0's clock decides for the warp
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                if (__shfl_sync(0xffffffffu, t - t0 > wait_ns ? 1 : 0, 0)) {
+                    timed_out = true;
+                    break;
                 }
             }
             yk[r] = r < ks ? got : (T)0;
@@ -653,6 +652,15 @@ __global__ void __launch_bounds__(128) k_trsv_wave(int kind, const T* __restrict
 // Scratch: the block counter, then the published copy of the solution (8-byte aligned).
 size_t trsv_sync_ints(int64_t n) { return 2 + 2 * (size_t)n; }
 
+// Bound of one wait for another block's solution (2 s; shorter only in tests).
+static uint64_t g_trsv_wait_ns = 2000000000ull;
+
+uint64_t set_trsv_wait_ns(uint64_t ns) {
+    const uint64_t old = g_trsv_wait_ns;
+    g_trsv_wait_ns = ns;
+    return old;
+}
+
 template <typename T>
 lsq_status launch_trsv(int kind, const T* M, int64_t n, int64_t ld, T* y, const int32_t* info, int32_t* sync,
                        int32_t* err, cudaStream_t st) {
@@ -660,7 +668,8 @@ lsq_status launch_trsv(int kind, const T* M, int64_t n, int64_t ld, T* y, const 
     int64_t nblk = ceil_div(n, 32);
     // all ones: the counter reads -1, every published entry is unset
     LSQ_CUDA_TRY(cudaMemsetAsync(sync, 0xff, sizeof(int32_t) * trsv_sync_ints(n), st));
-    k_trsv_wave<T><<<(unsigned)nblk, 128, 0, st>>>(kind, M, n, ld, y, sync, (T*)(sync + 2), info, err);
+    k_trsv_wave<T><<<(unsigned)nblk, 128, 0, st>>>(kind, M, n, ld, y, sync, (T*)(sync + 2), info, err,
+                                                   g_trsv_wait_ns);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
 }

@@ -80,6 +80,8 @@ enum TrsvKind { TRSV_LOWER = 0, TRSV_LOWER_T = 1, TRSV_UPPER = 2, TRSV_UNIT_LOWE
 // sync: trsv_sync_ints(n) int32 of scratch (cleared by the launch); err: the
 // device status word that a timed-out wait sets to -2 (may be NULL).
 size_t trsv_sync_ints(int64_t n);
+// Bound of the wavefront solves' waits (process-wide; returns the previous one).
+uint64_t set_trsv_wait_ns(uint64_t ns);
 template <typename T>
 lsq_status launch_trsv(int kind, const T* M, int64_t n, int64_t ld, T* y, const int32_t* info, int32_t* sync,
                        int32_t* err, cudaStream_t st);

@@ -43,6 +43,14 @@ def test_host_only_calls(liblsq):
     liblsq.lsq_status_string.restype = C.c_char_p
     assert liblsq.lsq_status_string(0) == b"LSQ_OK"
     assert liblsq.lsq_version() >= 100
+    # test-only wait bound of the triangular solves: host state only
+    liblsq.lsq_test_set_solve_wait_ns.restype = C.c_int64
+    liblsq.lsq_test_set_solve_wait_ns.argtypes = [C.c_int64]
+    s = liblsq.lsq_test_set_solve_wait_ns
+    assert s(0) == -1 and s(-5) == -1
+    old = s(1000)
+    assert old == 2_000_000_000
+    assert s(old) == 1000
 
 
 def test_binding_matches_oracle_precision_table(liblsq):

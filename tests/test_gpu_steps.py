@@ -181,6 +181,31 @@ def test_lu_solve(n):
     assert np.linalg.norm(to_np(x) - x_o) / np.linalg.norm(x_o) <= 8 * n * U64 * kH
 
 
+def test_solve_wait_timeout_reports_and_recovers():
+    """Fault injected on the host side (no GPU fault): with the test-only wait
+    bound of the triangular solves cut to 1 ns, the blocks that find their
+    predecessor's solution unpublished give up, record -2 in info and pass
+    NaN on; the kernels return, and the next solve on the same context with
+    the default bound is correct."""
+    n = 1024
+    rng = np.random.default_rng(11)
+    X = rng.standard_normal((3 * n, n))
+    G = X.T @ X
+    c = rng.standard_normal(n)
+    old = lsq.test_set_solve_wait_ns(1)
+    try:
+        _, _, _, info = lsq.factor_solve(dev_colmajor(G), torch.from_numpy(c).cuda())
+        torch.cuda.synchronize()
+        assert int(to_np(info)[0]) == -2
+    finally:
+        assert lsq.test_set_solve_wait_ns(old) == 1
+    x, _, _, info = lsq.factor_solve(dev_colmajor(G), torch.from_numpy(c).cuda())
+    assert int(to_np(info)[0]) == 0
+    L_o, _ = O.cholesky(G)
+    y_o = O.solve_lower_t(L_o, O.solve_lower(L_o, c))
+    assert np.linalg.norm(to_np(x) - y_o) / np.linalg.norm(y_o) <= 8 * n * U64 * O.kappa(G)
+
+
 def test_factor_breakdown_indices():
     G = np.diag([4.0, 1.0, -1.0, 2.0])
     _, _, _, info = lsq.factor_solve(dev_colmajor(G), torch.ones(4, dtype=torch.float64).cuda())
