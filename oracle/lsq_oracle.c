@@ -32,8 +32,9 @@
  * the sketch Gram matrix; PNE/HPNE against exact solutions for any
  * nonsingular R_s and against the error bounds Eq. (eq41)/(eq32); the
  * condition estimate against the exact inverse 1-norm (it is a lower bound)
- * and the kappa^2 inequality of Sec. 6.1.  Parity unpinned: the Gaussian
- * entry values beyond their moments (Box-Muller through libm).
+ * and the kappa^2 inequality of Sec. 6.1; the Gaussian entries against
+ * Box-Muller evaluated in 50-digit decimal arithmetic (within the FP64 error
+ * of the libm calls) besides their moments.
  */
 #include <math.h>
 #include <stdint.h>
