@@ -39,7 +39,7 @@ METRIC = "LS solves/s (mixed-precision PNE, 65536x1024)"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=18)
+    p.add_argument("--steps", type=int, default=36)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--fp64-steps", type=int, default=6, help="steps of the all-FP64 PNE comparison")
@@ -100,16 +100,24 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.t = None
+        self.first = 0
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # the timed region starts once nvidia-smi is sampling (at most 3 s);
+        # only the samples after this point are reported
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.02)
+        self.first = len(self.lines)
 
     def _read(self):
         for ln in self.proc.stdout:
@@ -126,7 +134,7 @@ class ClockSampler:
         self.t.join(timeout=2)
         sm, mx, pw, reasons = [], None, [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.first:] or self.lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
