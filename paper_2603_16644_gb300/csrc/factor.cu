@@ -446,8 +446,7 @@ lsq_status launch_lu(double* H, int64_t n, int64_t ld, int32_t* piv, int32_t* in
 // off-diagonal 32 x 32 block of the operator while the solution of that block
 // is still being computed, waits for that solution (bounded: 2 s of
 // %globaltimer unless a test shortened it, then -2 is recorded and NaN passed
-// on), applies it, and
-// finally solves its diagonal block and publishes y_b.
+// on), applies it, and finally solves its diagonal block and publishes y_b.
 //
 // Publication: the solution is also written to a scratch copy `pub` that the
 // launch fills with all-ones bit patterns (a NaN that arithmetic does not
