@@ -180,6 +180,23 @@ def run_steps(lsq, probs, steps, prec, hpne, ws, xs, infos, start=0):
                   info=infos[(start + k) % len(probs)])
 
 
+def max_over_ranks(sec, dist, device):
+    """The slowest rank's time (every rank gets it); `sec` itself on one rank."""
+    if dist is None:
+        return sec
+    import torch
+
+    t = torch.tensor([float(sec)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(world, steps, sec):
+    """Whole-job throughput of `world` replicas that each ran `steps` solves
+    in at most `sec` seconds."""
+    return world * steps / sec
+
+
 def timed(lsq, torch, probs, steps, warmup, prec, hpne, ws, xs, infos, dist=None):
     run_steps(lsq, probs, warmup, prec, hpne, ws, xs, infos)
     torch.cuda.synchronize()
@@ -395,11 +412,8 @@ def main():
     upd_records = lsq.profile_records("k_ot_update")
     stages = lsq.profile_collect(with_work=True)
     lsq.profile(False)
-    if dist is not None:
-        t = torch.tensor([sec], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec = float(t.item())
-    value = world * args.steps / sec
+    sec = max_over_ranks(sec, dist, dev)
+    value = weak_value(world, args.steps, sec)
 
     # accuracy of the timed solves (not timed)
     errs = {}
@@ -432,11 +446,8 @@ def main():
         lsq.solve_host(Ah[k % 3].t(), bh[k % 3], opts=opts_for(lsq, lsq.BF16, probs[k % 3]["seed"]), ws=wsh,
                        x_host=xh)
     e2e_sec = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_sec], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_sec = float(t.item())
-    e2e_value = world * args.e2e_steps / e2e_sec
+    e2e_sec = max_over_ranks(e2e_sec, dist, dev)
+    e2e_value = weak_value(world, args.e2e_steps, e2e_sec)
 
     # ---- roofline of the dominant kernel, from the library's events around
     # every launch of the two heaviest kernels inside the timed region
