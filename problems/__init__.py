@@ -107,6 +107,52 @@ def make_problem_torch(m: int, n: int, kappa: float, rho: float, seed: int, devi
     return A, b, x_star, sigma, V
 
 
+def make_problem_hadamard_torch(m: int, n: int, kappa: float, rho: float, seed: int, device="cuda"):
+    """The same construction with U from signed columns of the normalised
+    Sylvester-Hadamard matrix (m a power of two): U = D H[:, J] / sqrt(m),
+    D a seeded diagonal of signs, J n seeded distinct column indices, so U
+    has orthonormal columns exactly, and A = U diag(sigma) V^T is formed by
+    fast Walsh-Hadamard transforms of the columns of diag(sigma) V^T placed at
+    rows J (n m log2 m additions instead of an m x n QR and an m n^2 product;
+    used for the largest shapes).  r_perp is another signed Hadamard column,
+    orthogonal to range(A).  Returns (A, b, x_star, sigma, V) as float64 torch
+    tensors; A is column-major (stride (1, m))."""
+    import torch
+    if m & (m - 1) or n >= m:
+        raise ValueError("m must be a power of two larger than n")
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    perm = torch.randperm(m, generator=g)
+    J, k_perp = perm[:n].to(device), int(perm[n])
+    D = (torch.randint(0, 2, (m,), generator=g) * 2 - 1).to(device=device, dtype=torch.float64)
+    H = torch.randn(n, n, generator=g, dtype=torch.float64).to(device)
+    V, Rv = torch.linalg.qr(H)
+    V = V * torch.sign(torch.diagonal(Rv))
+    sigma = torch.logspace(0.0, -math.log10(kappa), n, dtype=torch.float64, device=device)
+    # rows of A^T (= columns of A): the rows of (diag(sigma) V^T)^T = V diag(sigma)
+    # placed at positions J, then the Walsh-Hadamard transform along them
+    X = torch.zeros(n, m, dtype=torch.float64, device=device)
+    X[:, J] = V * sigma
+    h = 1
+    while h < m:
+        Y = X.view(n, m // (2 * h), 2, h)
+        a, c = Y[:, :, 0, :], Y[:, :, 1, :]
+        X = torch.stack((a + c, a - c), dim=2).view(n, m)
+        h *= 2
+    X.mul_(D / math.sqrt(m))
+    A = X.t()  # column-major m x n
+    x_star = torch.randn(n, generator=g, dtype=torch.float64).to(device)
+    # r_perp: Hadamard column k_perp (not in J), signed by D, unit norm
+    idx = torch.arange(m, device=device, dtype=torch.int64) & k_perp
+    par = torch.zeros(m, dtype=torch.int64, device=device)
+    while bool(idx.any()):
+        par ^= idx & 1
+        idx >>= 1
+    r = D * (1.0 - 2.0 * par.to(torch.float64)) / math.sqrt(m)
+    beta = rho * float(sigma[0]) * float(torch.linalg.norm(x_star))
+    b = A @ x_star + beta * r
+    return A, b, x_star, sigma, V
+
+
 def rel_error(x_hat, x_star) -> float:
     """||x_hat - x_*|| / ||x_hat||, the error measure of the paper's figures."""
     x_hat = np.asarray(x_hat, dtype=np.float64)

@@ -149,6 +149,37 @@ def test_deterministic_and_host_path_identical():
 
 
 @pytest.mark.parametrize("hpne", [False, True])
+def test_large_single_problem_within_bound(hpne):
+    # the 262144 x 4096 problem (8.6 GB): Gaussian sketch s = 2n with
+    # per-column power-of-two scaling, its precision chosen by the condition
+    # estimate, FP64 rest.  kappa = 1e4 (at 1e8 the estimate selects an FP64
+    # sketch, a CUDA-core product of ~17 s).  Exact orthonormal U from signed
+    # Hadamard columns; the bound is evaluated on the device.
+    m, n, kap, rho = 262144, 4096, 1e4, 1e-8
+    A, b, x_star, sigma, V = P.make_problem_hadamard_torch(m, n, kap, rho, P.seed_for(2, 0))
+    opts = lsq.make_opts(kind=lsq.GAUSSIAN, s=2 * n, seed=P.seed_for(2, 0), sketch_prec=lsq.AUTO,
+                         qr_prec=lsq.FP32, refine_steps=0)
+    Rs = torch.zeros((n, n), dtype=torch.float64, device="cuda").t()
+    x, info = lsq.solve(A, b, hpne=hpne, opts=opts, Rs_out=Rs)
+    assert int(to_np(info)[0]) == 0
+    Rs = torch.triu(Rs)
+    # Eq. (eq41) / (eq32) with exact condition numbers: A_p = U diag(sigma) V^T R_s^{-1}
+    MT = torch.linalg.solve_triangular(Rs.t(), V * sigma, upper=False)  # (diag(sigma) V^T R_s^{-1})^T
+    kappa = lambda X: float((lambda s_: s_[0] / s_[-1])(torch.linalg.svdvals(X)))
+    kAp, kR = kappa(MT), kappa(Rs)
+    res = float(torch.linalg.norm(b - A @ x) / torch.linalg.norm(x))
+    u2 = 2.0 ** -52
+    if hpne:
+        H = MT @ (sigma[:, None] * V.t())  # A_p^T A = M^T diag(sigma) V^T
+        nu = float(torch.linalg.matrix_norm(MT, 2) / torch.linalg.matrix_norm(H, 2))
+        bound = kappa(H) * nu * u2 * (kR * res + 1 + kap * u2)
+    else:
+        bound = kR * kAp * u2 * (kAp * kR * res + 1 + kap * u2)
+    err = float(torch.linalg.norm(x - x_star) / torch.linalg.norm(x))
+    assert err <= n * bound, (err, bound, kAp)
+
+
+@pytest.mark.parametrize("hpne", [False, True])
 def test_full_size_tall_skinny_within_bound(hpne):
     # the 65536 x 1024 workload: sparse-sign s = 4n, zeta = 8, BF16 sketch, FP32 QR,
     # FP64 rest, one refinement step, in the launch configuration the benchmark times
