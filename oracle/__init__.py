@@ -34,6 +34,7 @@ def lib():
         path = _build.build()
         L = C.CDLL(path)
         sig = {
+            "lsqo_set_threads": (C.c_int, [C.c_int]),
             "lsqo_round": (C.c_double, [C.c_double, C.c_int]),
             "lsqo_round_array": (None, [_d, _i64, C.c_int, _d]),
             "lsqo_philox4x32_10": (None, [_u32, _u32, _u32]),
@@ -59,6 +60,10 @@ def lib():
             "lsqo_condest": (C.c_int, [_d, _i64, _i64, _i64, _d, _i32, _d, _d]),
             "lsqo_solve": (C.c_int, [_d, _i64, _i64, _i64, _d, C.c_int, C.c_int, _i64, C.c_int, C.c_uint64,
                                      C.c_int, C.c_int, C.c_int, _d, _d, _d, _i32]),
+            "lsqo_solve_method": (C.c_int, [_d, _i64, _i64, _i64, _d, C.c_int, C.c_int, _i64, C.c_int, C.c_uint64,
+                                            C.c_int, C.c_int, C.c_int, _d, _d, _d, _i32]),
+            "lsqo_lu_tall_u": (C.c_int, [_d, _i64, _i64, _i64, C.c_int, _d]),
+            "lsqo_solve_upper_t": (None, [_d, _i64, _i64, _d]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -66,6 +71,12 @@ def lib():
             f.argtypes = args
         _lib = L
     return _lib
+
+
+def set_threads(n):
+    """Threads of the oracle's parallel loops (n <= 0: unchanged); returns
+    the previous count.  Results do not depend on it."""
+    return int(lib().lsqo_set_threads(int(n)))
 
 
 def _p(a, ct=C.c_double):
@@ -254,20 +265,45 @@ def condest(A):
     return k0.value, ch.value, nr.value, ga.value, info
 
 
-def solve(A, b, *, hpne=False, kind=SPARSE_SIGN, s=None, zeta=8, seed=0, sketch_prec=FP32,
+PNE, HPNE, HPNE_QR, SNE, NNE_LU = 0, 1, 2, 3, 4
+METHODS = {"pne": PNE, "hpne": HPNE, "hpne_qr": HPNE_QR, "sne": SNE, "nne_lu": NNE_LU}
+
+
+def solve(A, b, *, hpne=False, method=None, kind=SPARSE_SIGN, s=None, zeta=8, seed=0, sketch_prec=FP32,
           qr_prec=FP32, refine_steps=0):
-    """Alg. 1 end to end.  Returns dict(x, Rs, info, kappa0, prec)."""
+    """Alg. 1 end to end.  `method` (a code or a name: pne, hpne, hpne_qr,
+    sne, nne_lu) overrides `hpne`.  Returns dict(x, Rs, info, kappa0, prec);
+    Rs is U_s for the not-normal equations."""
     A = _f64(A)
     m, n = A.shape
     s = 2 * n if s is None else s
+    if method is None:
+        method = HPNE if hpne else PNE
+    method = METHODS.get(method, method)
     b = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros(n, dtype=np.float64)
     Rs = np.zeros((n, n), dtype=np.float64, order="F")
     k0 = C.c_double()
     pr = C.c_int32()
-    info = lib().lsqo_solve(_p(A), m, n, m, _p(b), int(hpne), kind, s, zeta, C.c_uint64(seed),
-                            sketch_prec, qr_prec, refine_steps, _p(x), _p(Rs), C.byref(k0), C.byref(pr))
+    info = lib().lsqo_solve_method(_p(A), m, n, m, _p(b), int(method), kind, s, zeta, C.c_uint64(seed),
+                                   sketch_prec, qr_prec, refine_steps, _p(x), _p(Rs), C.byref(k0), C.byref(pr))
     return {"x": x, "Rs": Rs, "info": info, "kappa0": k0.value, "prec": pr.value}
+
+
+def lu_tall_u(As, prec=FP64):
+    """U of the LU with partial pivoting of a tall s x n matrix; returns (U, info)."""
+    As = _f64(As)
+    s_, n = As.shape
+    U = np.zeros((n, n), dtype=np.float64, order="F")
+    info = lib().lsqo_lu_tall_u(_p(As), s_, n, s_, prec, _p(U))
+    return U, info
+
+
+def solve_upper_t(U, y):
+    U = _f64(U)
+    y = np.array(y, dtype=np.float64)
+    lib().lsqo_solve_upper_t(_p(U), U.shape[0], U.shape[0], _p(y))
+    return y
 
 
 def kappa(M):

@@ -18,6 +18,11 @@
  *     fused behind our back: every product and sum below is rounded once.
  *   - Loops run in plain index order; there is no blocking, fusion or
  *     reordering, so each function can be checked against its source by eye.
+ *   - Loops whose iterations are independent (rows of a substitution,
+ *     entries of a Gram matrix, columns of a reflector update, rows of the
+ *     sketch) are spread over threads with OpenMP.  Every sum still runs in
+ *     its own index order inside one thread, so the result is bit-identical
+ *     for any thread count (lsqo_set_threads; a CPU test checks this).
  *
  * Precision codes: 0 FP8-e4m3 (OCP "fn", saturating), 1 BF16, 2 FP16,
  * 3 FP32, 4 FP64, 5 AUTO (choose by the condition estimate).
@@ -40,11 +45,28 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 enum { O_FP8 = 0, O_BF16 = 1, O_FP16 = 2, O_FP32 = 3, O_FP64 = 4, O_AUTO = 5 };
 enum { O_GAUSSIAN = 0, O_SPARSE_SIGN = 1 };
 
 #define IDX(i, j, ld) ((size_t)(i) + (size_t)(j) * (size_t)(ld))
+
+/* Threads used by the parallel loops (n <= 0 leaves the setting); returns
+ * the previous count.  1 when built without OpenMP. */
+int lsqo_set_threads(int n)
+{
+#ifdef _OPENMP
+    int prev = omp_get_max_threads();
+    if (n > 0) omp_set_num_threads(n);
+    return prev;
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------
  * Rounding FP64 -> lower precision, one rounding, RNE, subnormals kept.
@@ -148,11 +170,13 @@ int lsqo_sparse_sign_column(uint64_t seed, int64_t j, int64_t s, int zeta,
 int lsqo_sparse_sign_indices(uint64_t seed, int64_t m, int64_t s, int zeta,
                              int32_t* idx /* m*zeta */, int8_t* sgn /* m*zeta */)
 {
+    int rc = 0;
+#pragma omp parallel for schedule(static) reduction(min : rc)
     for (int64_t j = 0; j < m; ++j) {
-        int rc = lsqo_sparse_sign_column(seed, j, s, zeta, idx + j * zeta, sgn + j * zeta);
-        if (rc) return rc;
+        int r = lsqo_sparse_sign_column(seed, j, s, zeta, idx + j * zeta, sgn + j * zeta);
+        if (r < rc) rc = r;
     }
-    return 0;
+    return rc;
 }
 
 /* Gaussian entry Omega(i, j): counter (i, j_lo, j_hi, 2); two 53-bit
@@ -175,6 +199,7 @@ double lsqo_gaussian_entry(uint64_t seed, int64_t i, int64_t j)
 
 void lsqo_gaussian_operator(uint64_t seed, int64_t s, int64_t m, int prec, double* Om /* s-by-m, ld s */)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < m; ++j)
         for (int64_t i = 0; i < s; ++i)
             Om[IDX(i, j, s)] = lsqo_round(lsqo_gaussian_entry(seed, i, j), prec);
@@ -193,13 +218,13 @@ static int scale_target(int prec)
 
 void lsqo_colexp(const double* A, int64_t m, int64_t n, int64_t lda, int prec, int32_t* colexp)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) {
         double mx = 0.0;
         for (int64_t i = 0; i < m; ++i) { double v = fabs(A[IDX(i, j, lda)]); if (v > mx) mx = v; }
-        if (prec == O_FP64 || mx == 0.0 || !isfinite(mx)) { colexp[j] = 0; continue; }
-        int E;
+        int E = 0;
         frexp(mx, &E);
-        colexp[j] = scale_target(prec) - E;
+        colexp[j] = (prec == O_FP64 || mx == 0.0 || !isfinite(mx)) ? 0 : scale_target(prec) - E;
     }
 }
 
@@ -207,6 +232,7 @@ void lsqo_colexp(const double* A, int64_t m, int64_t n, int64_t lda, int prec, i
 void lsqo_quantize(const double* A, int64_t m, int64_t n, int64_t lda, int prec,
                    const int32_t* colexp, double* Ahat)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j)
         for (int64_t i = 0; i < m; ++i)
             Ahat[IDX(i, j, m)] = lsqo_round(ldexp(A[IDX(i, j, lda)], colexp[j]), prec);
@@ -228,34 +254,42 @@ int lsqo_sketch(const double* A, int64_t m, int64_t n, int64_t lda, int kind, in
     lsqo_quantize(A, m, n, lda, prec, colexp, Ahat);
     int rc = 0;
     if (kind == O_SPARSE_SIGN) {
-        int32_t idx[32];
-        int8_t sgn[32];
-        if (prec == O_FP64) {
-            for (size_t q = 0; q < (size_t)s * (size_t)n; ++q) As[q] = 0.0;
-            for (int64_t j = 0; j < m && !rc; ++j) {
-                rc = lsqo_sparse_sign_column(seed, j, s, zeta, idx, sgn);
-                for (int t = 0; t < zeta && !rc; ++t)
-                    for (int64_t c = 0; c < n; ++c)
-                        As[IDX(idx[t], c, s)] += (double)sgn[t] * Ahat[IDX(j, c, m)];
+        /* Column j of Omega adds sgn * Ahat[j, :] to the rows idx of A_s; every
+         * entry of A_s is summed in ascending j (its rows within one column of
+         * Omega are distinct).  The columns of A_s are independent. */
+        int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)m * (size_t)zeta);
+        int8_t* sgn = (int8_t*)malloc((size_t)m * (size_t)zeta);
+        if (!idx || !sgn) { free(idx); free(sgn); free(Ahat); return -3; }
+        rc = lsqo_sparse_sign_indices(seed, m, s, zeta, idx, sgn);
+        if (!rc) {
+#pragma omp parallel for schedule(static)
+            for (int64_t c = 0; c < n; ++c) {
+                if (prec == O_FP64) {
+                    for (int64_t i = 0; i < s; ++i) As[IDX(i, c, s)] = 0.0;
+                    for (int64_t j = 0; j < m; ++j)
+                        for (int t = 0; t < zeta; ++t) {
+                            size_t r = IDX(idx[(size_t)j * zeta + t], c, s);
+                            As[r] += (double)sgn[(size_t)j * zeta + t] * Ahat[IDX(j, c, m)];
+                        }
+                } else {
+                    float* acc = (float*)calloc((size_t)s, sizeof(float));
+                    for (int64_t j = 0; j < m; ++j)
+                        for (int t = 0; t < zeta; ++t) {
+                            int32_t r = idx[(size_t)j * zeta + t];
+                            float term = (float)((double)sgn[(size_t)j * zeta + t] * Ahat[IDX(j, c, m)]);
+                            acc[r] = acc[r] + term;
+                        }
+                    for (int64_t i = 0; i < s; ++i) As[IDX(i, c, s)] = (double)acc[i];
+                    free(acc);
+                }
             }
-        } else {
-            float* acc = (float*)calloc((size_t)s * (size_t)n, sizeof(float));
-            if (!acc) { free(Ahat); return -3; }
-            for (int64_t j = 0; j < m && !rc; ++j) {
-                rc = lsqo_sparse_sign_column(seed, j, s, zeta, idx, sgn);
-                for (int t = 0; t < zeta && !rc; ++t)
-                    for (int64_t c = 0; c < n; ++c) {
-                        float term = (float)((double)sgn[t] * Ahat[IDX(j, c, m)]);
-                        acc[IDX(idx[t], c, s)] = acc[IDX(idx[t], c, s)] + term;
-                    }
-            }
-            for (size_t q = 0; q < (size_t)s * (size_t)n; ++q) As[q] = (double)acc[q];
-            free(acc);
         }
+        free(idx); free(sgn);
     } else if (kind == O_GAUSSIAN) {
-        double* om = (double*)malloc(sizeof(double) * (size_t)m);
-        if (!om) { free(Ahat); return -3; }
+        /* Row i of A_s: Omega_hat[i, :] Ahat, each entry summed in ascending j. */
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < s; ++i) {
+            double* om = (double*)malloc(sizeof(double) * (size_t)m);
             for (int64_t j = 0; j < m; ++j) om[j] = lsqo_round(lsqo_gaussian_entry(seed, i, j), prec);
             for (int64_t c = 0; c < n; ++c) {
                 if (prec == O_FP64) {
@@ -271,8 +305,8 @@ int lsqo_sketch(const double* A, int64_t m, int64_t n, int64_t lda, int kind, in
                     As[IDX(i, c, s)] = (double)acc;
                 }
             }
+            free(om);
         }
-        free(om);
     } else {
         rc = -1;
     }
@@ -342,6 +376,7 @@ int lsqo_qr_r(const double* As, int64_t s, int64_t n, int64_t ldas, int prec, do
             double beta = house64(&W[IDX(k, k, s)], s - k, v, &mu);
             W[IDX(k, k, s)] = mu;
             for (int64_t i = k + 1; i < s; ++i) W[IDX(i, k, s)] = 0.0;
+#pragma omp parallel for schedule(static)
             for (int64_t c = k + 1; c < n; ++c) {
                 double w = 0.0;
                 for (int64_t i = k; i < s; ++i) w += v[i - k] * W[IDX(i, c, s)];
@@ -362,6 +397,7 @@ int lsqo_qr_r(const double* As, int64_t s, int64_t n, int64_t ldas, int prec, do
             float beta = house32(&W[IDX(k, k, s)], s - k, v, &mu);
             W[IDX(k, k, s)] = mu;
             for (int64_t i = k + 1; i < s; ++i) W[IDX(i, k, s)] = 0.0f;
+#pragma omp parallel for schedule(static)
             for (int64_t c = k + 1; c < n; ++c) {
                 float w = 0.0f;
                 for (int64_t i = k; i < s; ++i) w = w + v[i - k] * W[IDX(i, c, s)];
@@ -393,16 +429,20 @@ void lsqo_unscale_r(double* R, int64_t n, int64_t ldr, const int32_t* colexp)
 int lsqo_trsm_right_upper(const double* A, int64_t m, int64_t n, int64_t lda,
                           const double* R, int64_t ldr, double* Ap /* ld m */)
 {
-    double* y = (double*)malloc(sizeof(double) * (size_t)n);
-    for (int64_t i = 0; i < m; ++i) {
-        for (int64_t j = 0; j < n; ++j) {
-            double t = A[IDX(i, j, lda)];
-            for (int64_t k = 0; k < j; ++k) t = t - y[k] * R[IDX(k, j, ldr)];
-            y[j] = t / R[IDX(j, j, ldr)];
+#pragma omp parallel
+    {
+        double* y = (double*)malloc(sizeof(double) * (size_t)n);
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < m; ++i) {
+            for (int64_t j = 0; j < n; ++j) {
+                double t = A[IDX(i, j, lda)];
+                for (int64_t k = 0; k < j; ++k) t = t - y[k] * R[IDX(k, j, ldr)];
+                y[j] = t / R[IDX(j, j, ldr)];
+            }
+            for (int64_t j = 0; j < n; ++j) Ap[IDX(i, j, m)] = y[j];
         }
-        for (int64_t j = 0; j < n; ++j) Ap[IDX(i, j, m)] = y[j];
+        free(y);
     }
-    free(y);
     return 0;
 }
 
@@ -411,6 +451,7 @@ int lsqo_trsm_right_upper(const double* A, int64_t m, int64_t n, int64_t lda,
 void lsqo_gram(const double* X, const double* Y, int64_t m, int64_t n, int64_t ldx, int64_t ldy,
                const double* b, double* C /* ld n */, double* c)
 {
+#pragma omp parallel for schedule(dynamic, 1) collapse(2)
     for (int64_t q = 0; q < n; ++q)
         for (int64_t p = 0; p < n; ++p) {
             double acc = 0.0;
@@ -418,6 +459,7 @@ void lsqo_gram(const double* X, const double* Y, int64_t m, int64_t n, int64_t l
             C[IDX(p, q, n)] = acc;
         }
     if (b && c)
+#pragma omp parallel for schedule(static)
         for (int64_t p = 0; p < n; ++p) {
             double acc = 0.0;
             for (int64_t i = 0; i < m; ++i) acc += X[IDX(i, p, ldx)] * b[i];
@@ -436,6 +478,7 @@ int lsqo_cholesky(double* G, int64_t n, int64_t ld)
         if (!(d > 0.0) || !isfinite(d)) return (int)(j + 1);
         double ljj = sqrt(d);
         G[IDX(j, j, ld)] = ljj;
+#pragma omp parallel for schedule(static)
         for (int64_t i = j + 1; i < n; ++i) {
             double t = G[IDX(i, j, ld)];
             for (int64_t k = 0; k < j; ++k) t = t - G[IDX(i, k, ld)] * G[IDX(j, k, ld)];
@@ -469,6 +512,7 @@ int lsqo_lu(double* H, int64_t n, int64_t ld, int32_t* piv)
         double d = H[IDX(k, k, ld)];
         if (d == 0.0 || !isfinite(d)) { if (!info) info = (int)(k + 1); continue; }
         for (int64_t i = k + 1; i < n; ++i) H[IDX(i, k, ld)] = H[IDX(i, k, ld)] / d;
+#pragma omp parallel for schedule(static)
         for (int64_t j = k + 1; j < n; ++j)
             for (int64_t i = k + 1; i < n; ++i)
                 H[IDX(i, j, ld)] = H[IDX(i, j, ld)] - H[IDX(i, k, ld)] * H[IDX(k, j, ld)];
@@ -537,6 +581,7 @@ int lsqo_lstsq_qr(const double* A, int64_t m, int64_t n, int64_t lda, const doub
         double beta = house64(&W[IDX(k, k, m)], m - k, v, &mu);
         W[IDX(k, k, m)] = mu;
         for (int64_t i = k + 1; i < m; ++i) W[IDX(i, k, m)] = 0.0;
+#pragma omp parallel for schedule(static)
         for (int64_t c = k + 1; c < n; ++c) {
             double w = 0.0;
             for (int64_t i = k; i < m; ++i) w += v[i - k] * W[IDX(i, c, m)];
@@ -576,6 +621,7 @@ static int chol32(float* G, int64_t n)
         if (!(d > 0.0f) || !isfinite(d)) return (int)(j + 1);
         float ljj = sqrtf(d);
         G[IDX(j, j, n)] = ljj;
+#pragma omp parallel for schedule(static)
         for (int64_t i = j + 1; i < n; ++i) {
             float t = G[IDX(i, j, n)];
             for (int64_t k = 0; k < j; ++k) t = t - G[IDX(i, k, n)] * G[IDX(j, k, n)];
@@ -671,6 +717,7 @@ int lsqo_condest(const double* A, int64_t m, int64_t n, int64_t lda,
                  double* kappa0, int32_t* chosen, double* norm1_out, double* gamma_out)
 {
     float* G = (float*)malloc(sizeof(float) * (size_t)n * (size_t)n);
+#pragma omp parallel for schedule(dynamic, 1)
     for (int64_t q = 0; q < n; ++q)
         for (int64_t p = q; p < n; ++p) {
             float acc = 0.0f;
@@ -706,22 +753,136 @@ int lsqo_condest(const double* A, int64_t m, int64_t n, int64_t lda,
 }
 
 /* ------------------------------------------------------------------------
- * Alg. 1 end to end: PNE (Eq. e_pne) or HPNE (Eq. e_hpne) with a randomized
+ * LU with partial pivoting of a tall s-by-n matrix (s >= n), Golub & Van
+ * Loan Alg. 3.4.1 run over the n columns with the pivot searched over all s
+ * rows (the FIRST row of largest magnitude): P A = L U with L s-by-n unit
+ * lower trapezoidal and U n-by-n upper.  In FP64 or FP32 arithmetic; U is
+ * returned in FP64 (n-by-n, ld n, zero below the diagonal).  Returns 0 or
+ * k > 0 for a zero pivot at step k.
+ * ---------------------------------------------------------------------- */
+int lsqo_lu_tall_u(const double* As, int64_t s, int64_t n, int64_t ldas, int prec, double* U)
+{
+    if (s < n || n <= 0) return -1;
+    int info = 0;
+    if (prec == O_FP64) {
+        double* W = (double*)malloc(sizeof(double) * (size_t)s * (size_t)n);
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = 0; i < s; ++i) W[IDX(i, j, s)] = As[IDX(i, j, ldas)];
+        for (int64_t k = 0; k < n; ++k) {
+            int64_t p = k;
+            double best = fabs(W[IDX(k, k, s)]);
+            for (int64_t i = k + 1; i < s; ++i)
+                if (fabs(W[IDX(i, k, s)]) > best) { best = fabs(W[IDX(i, k, s)]); p = i; }
+            if (p != k)
+                for (int64_t j = 0; j < n; ++j) {
+                    double t = W[IDX(k, j, s)]; W[IDX(k, j, s)] = W[IDX(p, j, s)]; W[IDX(p, j, s)] = t;
+                }
+            double d = W[IDX(k, k, s)];
+            if (d == 0.0 || !isfinite(d)) { if (!info) info = (int)(k + 1); continue; }
+            for (int64_t i = k + 1; i < s; ++i) W[IDX(i, k, s)] = W[IDX(i, k, s)] / d;
+#pragma omp parallel for schedule(static)
+            for (int64_t j = k + 1; j < n; ++j)
+                for (int64_t i = k + 1; i < s; ++i)
+                    W[IDX(i, j, s)] = W[IDX(i, j, s)] - W[IDX(i, k, s)] * W[IDX(k, j, s)];
+        }
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = 0; i < n; ++i) U[IDX(i, j, n)] = (i <= j) ? W[IDX(i, j, s)] : 0.0;
+        free(W);
+    } else {
+        float* W = (float*)malloc(sizeof(float) * (size_t)s * (size_t)n);
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = 0; i < s; ++i) W[IDX(i, j, s)] = (float)As[IDX(i, j, ldas)];
+        for (int64_t k = 0; k < n; ++k) {
+            int64_t p = k;
+            float best = fabsf(W[IDX(k, k, s)]);
+            for (int64_t i = k + 1; i < s; ++i)
+                if (fabsf(W[IDX(i, k, s)]) > best) { best = fabsf(W[IDX(i, k, s)]); p = i; }
+            if (p != k)
+                for (int64_t j = 0; j < n; ++j) {
+                    float t = W[IDX(k, j, s)]; W[IDX(k, j, s)] = W[IDX(p, j, s)]; W[IDX(p, j, s)] = t;
+                }
+            float d = W[IDX(k, k, s)];
+            if (d == 0.0f || !isfinite(d)) { if (!info) info = (int)(k + 1); continue; }
+            for (int64_t i = k + 1; i < s; ++i) W[IDX(i, k, s)] = W[IDX(i, k, s)] / d;
+#pragma omp parallel for schedule(static)
+            for (int64_t j = k + 1; j < n; ++j)
+                for (int64_t i = k + 1; i < s; ++i)
+                    W[IDX(i, j, s)] = W[IDX(i, j, s)] - W[IDX(i, k, s)] * W[IDX(k, j, s)];
+        }
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = 0; i < n; ++i) U[IDX(i, j, n)] = (i <= j) ? (double)W[IDX(i, j, s)] : 0.0;
+        free(W);
+    }
+    return info;
+}
+
+/* U^T y = c for upper U (forward substitution with the transpose). */
+void lsqo_solve_upper_t(const double* U, int64_t n, int64_t ld, double* y)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double t = y[i];
+        for (int64_t k = 0; k < i; ++k) t = t - U[IDX(k, i, ld)] * y[k];
+        y[i] = t / U[IDX(i, i, ld)];
+    }
+}
+
+/* HPNE through a QR factorization of H = A_p^T A (Sec. 1 lists QR beside LU
+ * for Eq. e_hpne): the Householder R of the (n+1)-by-(n+1) matrix
+ * [[H, c], [0, 1]] holds R_H in its leading block and Q_H^T c in the top of
+ * its last column (the reflectors of the first n columns leave the zero row
+ * alone), so x = R_H^{-1} (Q_H^T c).  FP64. */
+static int hpne_qr_solve(const double* H, int64_t n, const double* c, double* x)
+{
+    int64_t n1 = n + 1;
+    double* M = (double*)calloc((size_t)n1 * (size_t)n1, sizeof(double));
+    double* R = (double*)malloc(sizeof(double) * (size_t)n1 * (size_t)n1);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < n; ++i) M[IDX(i, j, n1)] = H[IDX(i, j, n)];
+    for (int64_t i = 0; i < n; ++i) M[IDX(i, n, n1)] = c[i];
+    M[IDX(n, n, n1)] = 1.0;
+    int rc = lsqo_qr_r(M, n1, n1, n1, O_FP64, R);
+    int info = 0;
+    for (int64_t i = 0; i < n && !rc; ++i)
+        if (!(R[IDX(i, i, n1)] != 0.0) || !isfinite(R[IDX(i, i, n1)])) { info = (int)(i + 1); break; }
+    if (!rc && !info) {
+        for (int64_t i = 0; i < n; ++i) x[i] = R[IDX(i, n, n1)];
+        lsqo_solve_upper(R, n, n1, x);
+    }
+    free(M); free(R);
+    return rc ? -1 : info;
+}
+
+/* ------------------------------------------------------------------------
+ * Alg. 1 end to end with one of the solution methods, a randomized
  * preconditioner computed in precision u_p, then optionally one FP64
  * residual-refinement step (not part of the paper's algorithm):
- *   r = b - A x;  g = A_p^T r;
- *   PNE:  (A_p^T A_p) z = g, delta = R_s^{-1} z;   HPNE: (A_p^T A) delta = g;
- *   x = x + delta.
+ *   method 0  PNE (Eq. e_pne):  A_p^T A_p y = A_p^T b (Cholesky), R_s x = y;
+ *   method 1  HPNE (Eq. e_hpne): A_p^T A x = A_p^T b, LU with partial pivoting;
+ *   method 2  HPNE with a QR factorization of A_p^T A (above);
+ *   method 3  seminormal equations (Eq. e_sne) R^T R x = A^T b, with R the
+ *             triangular factor of a thin QR of A obtained from the
+ *             preconditioner: A_p = A R_s^{-1} = Q R_p with
+ *             R_p^T R_p = A_p^T A_p (Cholesky, R_p = L^T), so A = Q (R_p R_s)
+ *             and R = L^T R_s, applied in factored form:
+ *             x = R_s^{-1} L^{-T} L^{-1} R_s^{-T} (A^T b);
+ *   method 4  not-normal equations (Eq. e_nne) B^T A x = B^T b with
+ *             B = A U_s^{-1}, U_s the upper factor of the LU with partial
+ *             pivoting of the sketch A_s in u_p (so B has the column space of
+ *             A and Omega B = P^T L_s is well conditioned), solved by LU with
+ *             partial pivoting.
+ * Refinement: r = b - A x, then the same method for the correction with the
+ * factorizations reused (PNE, HPNE: A_p^T r; SNE: A^T r; NNE: B^T r; HPNE
+ * through QR: a second QR with the new right-hand side), x = x + delta.
  * Returns 0, k > 0 for a factorization breakdown at pivot k, -1 for bad
- * arguments.  Rs_out (n-by-n, may be NULL) receives R_s; kappa0_out and
- * prec_out (may be NULL) the estimate and the precision used.
+ * arguments.  Rs_out (n-by-n, may be NULL) receives R_s (U_s for method 4);
+ * kappa0_out and prec_out (may be NULL) the estimate and the precision used.
  * ---------------------------------------------------------------------- */
-int lsqo_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
-               int hpne, int kind, int64_t s, int zeta, uint64_t seed,
-               int sketch_prec, int qr_prec, int refine_steps,
-               double* x, double* Rs_out, double* kappa0_out, int32_t* prec_out)
+int lsqo_solve_method(const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                      int method, int kind, int64_t s, int zeta, uint64_t seed,
+                      int sketch_prec, int qr_prec, int refine_steps,
+                      double* x, double* Rs_out, double* kappa0_out, int32_t* prec_out)
 {
-    if (m <= 0 || n <= 0 || s < n || m < s) return -1;
+    if (m <= 0 || n <= 0 || s < n || m < s || method < 0 || method > 4) return -1;
     double k0 = NAN;
     int prec = sketch_prec;
     if (prec == O_AUTO) {
@@ -734,6 +895,7 @@ int lsqo_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double*
     if (qp != O_FP32 && qp != O_FP64) qp = O_FP32;
     if (kappa0_out) *kappa0_out = k0;
     if (prec_out) *prec_out = prec;
+    int hp = (method == 1 || method == 2 || method == 4);  /* nonsymmetric n-by-n system */
 
     size_t mn = (size_t)m * (size_t)n, nn = (size_t)n * (size_t)n;
     double* As = (double*)malloc(sizeof(double) * (size_t)s * (size_t)n);
@@ -745,38 +907,64 @@ int lsqo_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double*
     double* r = (double*)malloc(sizeof(double) * (size_t)m);
     int32_t* piv = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
     int rc = lsqo_sketch(A, m, n, lda, kind, s, zeta, seed, prec, As, ce);
-    if (!rc) rc = lsqo_qr_r(As, s, n, s, qp, R);
     int info = 0;
     if (!rc) {
+        if (method == 4) info = lsqo_lu_tall_u(As, s, n, s, qp, R);
+        else rc = lsqo_qr_r(As, s, n, s, qp, R);
+    }
+    if (!rc && !info) {
         lsqo_unscale_r(R, n, n, ce);
         if (Rs_out) memcpy(Rs_out, R, sizeof(double) * nn);
         lsqo_trsm_right_upper(A, m, n, lda, R, n, Ap);
-        if (hpne) lsqo_gram(Ap, A, m, n, m, lda, b, G, c);
-        else      lsqo_gram(Ap, Ap, m, n, m, m, b, G, c);
-        info = hpne ? lsqo_lu(G, n, n, piv) : lsqo_cholesky(G, n, n);
+        if (hp) lsqo_gram(Ap, A, m, n, m, lda, b, G, c);
+        else    lsqo_gram(Ap, Ap, m, n, m, m, b, G, c);
+        if (method == 3) {
+            /* c = A^T b, then R_s^{-T} c */
+#pragma omp parallel for schedule(static)
+            for (int64_t p = 0; p < n; ++p) {
+                double acc = 0.0;
+                for (int64_t i = 0; i < m; ++i) acc += A[IDX(i, p, lda)] * b[i];
+                c[p] = acc;
+            }
+            lsqo_solve_upper_t(R, n, n, c);
+        }
+        if (method == 1 || method == 4) info = lsqo_lu(G, n, n, piv);
+        else if (method != 2) info = lsqo_cholesky(G, n, n);
         if (!info) {
             for (int64_t i = 0; i < n; ++i) x[i] = c[i];
-            if (hpne) {
+            if (method == 1 || method == 4) {
                 lsqo_lu_solve(G, n, n, piv, x);
+            } else if (method == 2) {
+                info = hpne_qr_solve(G, n, c, x);
             } else {
                 lsqo_solve_lower(G, n, n, 0, x);
                 lsqo_solve_lower_t(G, n, n, x);
                 lsqo_solve_upper(R, n, n, x);
             }
-            for (int step = 0; step < refine_steps; ++step) {
+            for (int step = 0; step < refine_steps && !info; ++step) {
+#pragma omp parallel for schedule(static)
                 for (int64_t i = 0; i < m; ++i) {
                     double t = b[i];
                     for (int64_t j = 0; j < n; ++j) t = t - A[IDX(i, j, lda)] * x[j];
                     r[i] = t;
                 }
+                const double* X = (method == 3) ? A : Ap;
+                int64_t ldX = (method == 3) ? lda : m;
+#pragma omp parallel for schedule(static)
                 for (int64_t p = 0; p < n; ++p) {
                     double acc = 0.0;
-                    for (int64_t i = 0; i < m; ++i) acc += Ap[IDX(i, p, m)] * r[i];
+                    for (int64_t i = 0; i < m; ++i) acc += X[IDX(i, p, ldX)] * r[i];
                     c[p] = acc;
                 }
-                if (hpne) {
+                if (method == 1 || method == 4) {
                     lsqo_lu_solve(G, n, n, piv, c);
+                } else if (method == 2) {
+                    double* d = (double*)malloc(sizeof(double) * (size_t)n);
+                    info = hpne_qr_solve(G, n, c, d);
+                    memcpy(c, d, sizeof(double) * (size_t)n);
+                    free(d);
                 } else {
+                    if (method == 3) lsqo_solve_upper_t(R, n, n, c);
                     lsqo_solve_lower(G, n, n, 0, c);
                     lsqo_solve_lower_t(G, n, n, c);
                     lsqo_solve_upper(R, n, n, c);
@@ -787,6 +975,16 @@ int lsqo_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double*
     }
     free(As); free(ce); free(R); free(Ap); free(G); free(c); free(r); free(piv);
     return rc ? -1 : info;
+}
+
+/* PNE (hpne = 0) or HPNE with LU (hpne = 1): lsqo_solve_method 0 or 1. */
+int lsqo_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+               int hpne, int kind, int64_t s, int zeta, uint64_t seed,
+               int sketch_prec, int qr_prec, int refine_steps,
+               double* x, double* Rs_out, double* kappa0_out, int32_t* prec_out)
+{
+    return lsqo_solve_method(A, m, n, lda, b, hpne ? 1 : 0, kind, s, zeta, seed, sketch_prec, qr_prec,
+                             refine_steps, x, Rs_out, kappa0_out, prec_out);
 }
 
 /* ------------------------------------------------------------------------
