@@ -72,13 +72,10 @@ def test_batched_against_oracle(hpne):
         ref = O.solve(p.A, p.b, hpne=hpne, kind=o.kind, s=o.s, zeta=o.zeta, seed=o.seed, sketch_prec=o.sketch_prec,
                       qr_prec=o.qr_prec, refine_steps=o.refine_steps)
         assert int(to_np(infos[i])[0]) == ref["info"] == 0
-        # errors at the FP64 floor kappa(A) u: compared with the worst of three
-        # oracle realizations (the oracle's own error moves by its size with
-        # the summation order, across row permutations and across machines)
         more = oracle_realizations(p, hpne=hpne, kind=o.kind, s=o.s, zeta=o.zeta, seed=o.seed,
                                    sketch_prec=o.sketch_prec, qr_prec=o.qr_prec, refine_steps=o.refine_steps)
         assert_solution_parity(to_np(xs[i]), ref["x"], p.x_star, p.kappa, p.rho, f"problem {i}",
-                               refined=o.refine_steps > 0, realizations=more)
+                               refined=o.refine_steps > 0, u_p=o.sketch_prec, realizations=more)
 
 
 def test_batched_auto_precision_per_problem():

@@ -80,7 +80,7 @@ def test_training_learns_and_learned_solve_matches_oracle():
                       qr_prec=O.FP64 if used == O.FP64 else O.FP32, refine_steps=1)
         more = oracle_realizations(pr, kind=O.SPARSE_SIGN, s=160, zeta=8, seed=5, sketch_prec=used,
                                    qr_prec=O.FP64 if used == O.FP64 else O.FP32, refine_steps=1)
-        assert_solution_parity(to_np(x), ref["x"], pr.x_star, kap, 1e-6, realizations=more)
+        assert_solution_parity(to_np(x), ref["x"], pr.x_star, kap, 1e-6, u_p=used, realizations=more)
         # an accepted low precision satisfies the judge's rule on the oracle's own R_s
         if used != O.FP64:
             u = {O.FP8_E4M3: 2.0 ** -4, O.BF16: 2.0 ** -8, O.FP32: 2.0 ** -24}[used]

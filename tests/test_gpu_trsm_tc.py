@@ -8,7 +8,7 @@ import torch
 
 import oracle as O
 import problems as P
-from tests.gpu_util import dev_colmajor, to_np
+from tests.gpu_util import dev_colmajor, substitution_perturbation_bound, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -47,13 +47,7 @@ def perturbation_bound(Ap_ref, R, K):
     |E| <= n u |Ap| |R|; a digit-sliced update adds per entry at most
     K 2^-50.6 max_k |Ap[i, k]| max_k |R[k, j]|.  So |Ap_tc - Ap_ref| <=
     (|E_tc| + |E_ref|) |R^{-1}|."""
-    n = R.shape[0]
-    aAp, aR = np.abs(Ap_ref), np.abs(R)
-    Rinv = np.abs(np.linalg.inv(R))
-    rowmax = aAp.max(axis=1)
-    colmax = aR.max(axis=0)
-    E = 2 * n * U * (aAp @ aR) + K * 2.0 ** -50.6 * np.outer(rowmax, colmax)
-    return E @ Rinv
+    return substitution_perturbation_bound(Ap_ref, R, K)
 
 
 @pytest.mark.parametrize("m,n,kappa", [(3000, 200, 1e2), (3000, 200, 1e10), (2500, 600, 1e8)])
