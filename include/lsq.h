@@ -189,7 +189,9 @@ lsq_status lsq_trsm_gram(const double* A, int64_t m, int64_t n, int64_t lda, con
  * every GPU loading the library holds until the process exits.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream
- *     capture.
+ *     capture.  The address is looked up again when the device's current
+ *     context changes (after cudaDeviceReset, for instance), so such a call
+ *     must not be the first one inside a capture either.
  *   - Sizes whose GEMV partial sums, 8 * ceil(m / 16384) * n bytes, exceed
  *     16 MiB are rejected with LSQ_ERR_ARG; the split-K count is capped so
  *     the partial Gram matrices fit in the rest, so large n runs with fewer

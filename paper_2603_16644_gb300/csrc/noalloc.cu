@@ -23,20 +23,46 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
+// Per device: the context the address was looked up in, and the address.
+// A device reset (cudaDeviceReset) or a new primary context invalidates the
+// address, so it is looked up again whenever the current context changes.
+void* g_noalloc_ctx[kMaxDevices] = {};
 void* g_noalloc_ptr[kMaxDevices] = {};
+
+// The driver's cuCtxGetCurrent, reached through the runtime (no link to the
+// driver library); nullptr if unavailable.
+typedef int (*CtxGetCurrentFn)(void**);
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            return (CtxGetCurrentFn)p;
+        return (CtxGetCurrentFn) nullptr;
+    }();
+    return fn;
+}
 
 // Device address of the scratch array for the current device.  Host code may
 // not use the symbol itself (it is a host-side stand-in); the address comes
-// from cudaGetSymbolAddress, once per device, with that device current.
+// from cudaGetSymbolAddress, with that device current, once per device and
+// context.
 lsq_status noalloc_scratch(void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LSQ_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return LSQ_ERR_ARG;
+    // (before the first runtime call that creates the primary context, ctx is
+    // null; the lookup then runs again on the next call, harmlessly)
+    void* ctx = nullptr;
+    CtxGetCurrentFn get = ctx_get_current();
+    if (get && get(&ctx) != 0) ctx = nullptr;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    if (!g_noalloc_ptr[dev] || g_noalloc_ctx[dev] != ctx) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LSQ_ERR_CUDA;
         g_noalloc_ptr[dev] = p;
+        g_noalloc_ctx[dev] = ctx;
     }
     *out = g_noalloc_ptr[dev];
     return LSQ_OK;

@@ -3,9 +3,13 @@ cannot allocate device memory where they call it (allocator callbacks,
 frameworks that own every allocation, loops that must not synchronise on
 cudaMalloc).  Its scratch is a fixed per-device array inside the library.
 
-Checked through the C ABI against the workspace entry point lsq_trsm_gram on
-the same inputs, on two calls in a row with different shapes and modes (the
-second call must not see anything the first left in the shared array).
+Checked through the C ABI against the oracle (A_p elementwise within the
+perturbation bound of two backward-stable substitutions; G and c against the
+oracle's sequential sums of the same A_p, elementwise within both sums'
+error bounds) and against the workspace entry point lsq_trsm_gram on the same
+inputs, on two calls in a row with different shapes and modes (the second
+call must not see anything the first left in the shared array), including a
+shape whose split-K count has to be cut to fit the fixed array.
 This file sorts last so a stop-at-first-failure run has done every other
 test first; it also passes on its own in a fresh process.
 """
@@ -15,7 +19,9 @@ import numpy as np
 import pytest
 import torch
 
+import oracle as O
 import problems as P
+from tests.gpu_util import substitution_perturbation_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -52,11 +58,40 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("order", [((5000, 300, False), (70000, 1100, True)), ((70000, 1100, False), (3000, 64, True))])
-def test_noalloc_matches_workspace_entry_point(order):
+def _check_against_oracle(A, R, b, hpne, Ap, G, c, sample_rows=None):
+    """A_p: the oracle's substitution on (a sample of) the rows, elementwise
+    within the perturbation bound of two backward-stable solves.  G, c: the
+    oracle's dot products of the same A_p (and A), elementwise within
+    2 gamma_m (|X|^T |Y|): both are FP64 sums of the same m products, in
+    different orders."""
+    A_np, R_np, b_np = A.cpu().numpy(), R.cpu().numpy(), b.cpu().numpy()
+    m = A_np.shape[0]
+    rows = np.arange(m) if sample_rows is None else sample_rows
+    Ap_or = O.trsm_right_upper(np.asfortranarray(A_np[rows]), R_np)
+    tol = substitution_perturbation_bound(Ap_or, R_np)
+    bad = np.abs(Ap[rows] - Ap_or) > tol
+    assert not bad.any(), (np.argwhere(bad)[:5], (np.abs(Ap[rows] - Ap_or) / tol).max())
+    Y = A_np if hpne else Ap
+    Go, co = O.gram(np.asfortranarray(Ap), np.asfortranarray(Y), b_np)
+    gamma = m * U64 / (1 - m * U64)
+    assert np.all(np.abs(G - Go) <= 2 * gamma * (np.abs(Ap).T @ np.abs(Y)))
+    assert np.all(np.abs(c - co) <= 2 * gamma * (np.abs(Ap).T @ np.abs(b_np)))
+
+
+# (m, n, hpne).  120000 x 512 HPNE plans 19 K splits of its Gram, but only 7
+# partial 512 x 512 matrices fit beside the GEMV partials in the fixed array:
+# the call runs with the K range cut into 7 chunks.
+@pytest.mark.parametrize("order", [((5000, 300, False), (70000, 1100, True)), ((70000, 1100, False), (3000, 64, True)),
+                                   ((120000, 512, True), (4000, 100, False))])
+def test_noalloc_matches_oracle_and_workspace_entry_point(order):
     for (m, n, hpne) in order:
         A, R, b = _case(m, n, 1e3, m + n)
         Ap, G, c = _noalloc(A, R, b, hpne)
+        rows = None
+        if m > 20000:
+            rng = np.random.default_rng(m)
+            rows = np.concatenate([np.arange(3), rng.choice(m, 200, replace=False), np.arange(m - 3, m)])
+        _check_against_oracle(A, R, b, hpne, Ap, G, c, rows)
         # the workspace entry point with the tensor-core FP64 products switched
         # off runs the same CUDA-core TRSM kernel; the Gram may use fewer K
         # splits (summation order only)
