@@ -15,9 +15,10 @@ import numpy as np
 
 from . import build as _build
 
-FP8_E4M3, BF16, FP16, FP32, FP64, AUTO = 0, 1, 2, 3, 4, 5
+FP8_E4M3, BF16, FP16, FP32, FP64, AUTO, AUTO_SKETCH = 0, 1, 2, 3, 4, 5, 6
 GAUSSIAN, SPARSE_SIGN = 0, 1
-PREC_NAMES = {FP8_E4M3: "fp8_e4m3", BF16: "bf16", FP16: "fp16", FP32: "fp32", FP64: "fp64", AUTO: "auto"}
+PREC_NAMES = {FP8_E4M3: "fp8_e4m3", BF16: "bf16", FP16: "fp16", FP32: "fp32", FP64: "fp64", AUTO: "auto",
+              AUTO_SKETCH: "auto_sketch"}
 
 _lib = None
 
@@ -63,6 +64,8 @@ def lib():
             "lsqo_solve_method": (C.c_int, [_d, _i64, _i64, _i64, _d, C.c_int, C.c_int, _i64, C.c_int, C.c_uint64,
                                             C.c_int, C.c_int, C.c_int, _d, _d, _d, _i32]),
             "lsqo_lu_tall_u": (C.c_int, [_d, _i64, _i64, _i64, C.c_int, _d]),
+            "lsqo_condest_sketch": (C.c_int, [_d, _i64, _i64, _i64, C.c_uint64, _d, _i32, _d]),
+            "lsqo_kappa1_upper32": (C.c_double, [_d, _i64, _i64]),
             "lsqo_solve_upper_t": (None, [_d, _i64, _i64, _d]),
         }
         for name, (res, args) in sig.items():
@@ -288,6 +291,23 @@ def solve(A, b, *, hpne=False, method=None, kind=SPARSE_SIGN, s=None, zeta=8, se
     info = lib().lsqo_solve_method(_p(A), m, n, m, _p(b), int(method), kind, s, zeta, C.c_uint64(seed),
                                    sketch_prec, qr_prec, refine_steps, _p(x), _p(Rs), C.byref(k0), C.byref(pr))
     return {"x": x, "Rs": Rs, "info": info, "kappa0": k0.value, "prec": pr.value}
+
+
+def condest_sketch(A, seed):
+    """Condition estimate on an FP32 sparse-sign sketch: (kappa0, chosen, kappa_1(R_e), rc)."""
+    A = _f64(A)
+    m, n = A.shape
+    k0 = C.c_double()
+    ch = C.c_int32()
+    k1 = C.c_double()
+    rc = lib().lsqo_condest_sketch(_p(A), m, n, m, C.c_uint64(seed), C.byref(k0), C.byref(ch), C.byref(k1))
+    return k0.value, ch.value, k1.value, rc
+
+
+def kappa1_upper32(R):
+    """||R||_1 times Hager's FP32 estimate of ||R^{-1}||_1 for upper triangular R."""
+    R = _f64(R)
+    return float(lib().lsqo_kappa1_upper32(_p(R), R.shape[0], R.shape[0]))
 
 
 def lu_tall_u(As, prec=FP64):

@@ -25,7 +25,8 @@
  *     for any thread count (lsqo_set_threads; a CPU test checks this).
  *
  * Precision codes: 0 FP8-e4m3 (OCP "fn", saturating), 1 BF16, 2 FP16,
- * 3 FP32, 4 FP64, 5 AUTO (choose by the condition estimate).
+ * 3 FP32, 4 FP64, 5 AUTO (choose by the condition estimate of A^T A),
+ * 6 AUTO_SKETCH (choose by the condition estimate on a sketch).
  * Sketch kinds: 0 Gaussian, 1 sparse sign.
  *
  * Pins (checked by the CPU-only tests against the mathematics, never
@@ -49,7 +50,7 @@
 #include <omp.h>
 #endif
 
-enum { O_FP8 = 0, O_BF16 = 1, O_FP16 = 2, O_FP32 = 3, O_FP64 = 4, O_AUTO = 5 };
+enum { O_FP8 = 0, O_BF16 = 1, O_FP16 = 2, O_FP32 = 3, O_FP64 = 4, O_AUTO = 5, O_AUTO_SKETCH = 6 };
 enum { O_GAUSSIAN = 0, O_SPARSE_SIGN = 1 };
 
 #define IDX(i, j, ld) ((size_t)(i) + (size_t)(j) * (size_t)(ld))
@@ -753,6 +754,158 @@ int lsqo_condest(const double* A, int64_t m, int64_t n, int64_t lda,
 }
 
 /* ------------------------------------------------------------------------
+ * Condition estimate on the sketch (a reading of Alg. 1's first line,
+ * "estimate kappa0 ~ log10 kappa(A) in single precision", that replaces the
+ * m n^2 Gram A^T A of Sec. 6.1 by the Gram of a sketch):
+ *   1. A_e = Omega_e A, an FP32 sparse-sign sketch (s_e = min(2n, m) rows,
+ *      zeta = min(8, s_e), Philox stream keyed by `seed`), so that
+ *      G_s = A_e^T A_e approximates A^T A on range(A) (Omega_e embeds it);
+ *   2. R_e by Householder QR of A_e in FP32, unscaled to A's columns;
+ *   3. the estimator of Sec. 6.1 on G_s = fl32(A_e^T A_e) (with the sketch's
+ *      column scaling undone): ||G_s||_1, and Hager's estimate gamma of
+ *      ||G_s^{-1}||_1 with G_s^{-1} applied through the triangular factor
+ *      L = R_e^T from the QR (R_e^T R_e = G_s) instead of an FP32 Cholesky
+ *      of G_s, which breaks down once kappa(A)^2 > 1/u32;
+ *      kappa0 = 0.5 log10(n ||G_s||_1 gamma);
+ *   4. an FP32 R_e resolves kappa(A) only while u32 kappa(R_e) < 1 (Lemma
+ *      rscond for the FP32 factor itself): if Hager's estimate of
+ *      kappa_1(R_e) = ||R_e||_1 ||R_e^{-1}||_1 gives u32 kappa_1 > 1, the
+ *      estimate is the "overflow" case, kappa0 = +inf (FP64).
+ * ---------------------------------------------------------------------- */
+static void upper32_solve(const float* R, int64_t n, float* y)        /* R y = c */
+{
+    for (int64_t i = n - 1; i >= 0; --i) {
+        float t = y[i];
+        for (int64_t k = i + 1; k < n; ++k) t = t - R[IDX(i, k, n)] * y[k];
+        y[i] = t / R[IDX(i, i, n)];
+    }
+}
+
+static void upper32_solve_t(const float* R, int64_t n, float* y)      /* R^T y = c */
+{
+    for (int64_t i = 0; i < n; ++i) {
+        float t = y[i];
+        for (int64_t k = 0; k < i; ++k) t = t - R[IDX(k, i, n)] * y[k];
+        y[i] = t / R[IDX(i, i, n)];
+    }
+}
+
+/* Hager / Higham estimate of ||R^{-1}||_1 for upper triangular R (FP32):
+ * products with R^{-1} and R^{-T} by substitution. */
+static float hager_rinv_norm1(const float* R, int64_t n, int maxit)
+{
+    float* x = (float*)malloc(sizeof(float) * (size_t)n);
+    float* y = (float*)malloc(sizeof(float) * (size_t)n);
+    float* xi = (float*)malloc(sizeof(float) * (size_t)n);
+    float* z = (float*)malloc(sizeof(float) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) x[i] = 1.0f / (float)n;
+    for (int64_t i = 0; i < n; ++i) y[i] = x[i];
+    upper32_solve(R, n, y);
+    float est = norm1_32(y, n);
+    for (int64_t i = 0; i < n; ++i) xi[i] = (y[i] >= 0.0f) ? 1.0f : -1.0f;
+    for (int64_t i = 0; i < n; ++i) z[i] = xi[i];
+    upper32_solve_t(R, n, z);
+    int64_t jlast = -1;
+    for (int it = 1; it < maxit; ++it) {
+        int64_t j = 0;
+        float zmax = fabsf(z[0]);
+        for (int64_t i = 1; i < n; ++i) if (fabsf(z[i]) > zmax) { zmax = fabsf(z[i]); j = i; }
+        float ztx = 0.0f;
+        for (int64_t i = 0; i < n; ++i) ztx = ztx + z[i] * x[i];
+        if (zmax <= ztx || j == jlast) break;
+        jlast = j;
+        for (int64_t i = 0; i < n; ++i) x[i] = 0.0f;
+        x[j] = 1.0f;
+        for (int64_t i = 0; i < n; ++i) y[i] = x[i];
+        upper32_solve(R, n, y);
+        float est_new = norm1_32(y, n);
+        int same = 1;
+        for (int64_t i = 0; i < n; ++i) same &= (((y[i] >= 0.0f) ? 1.0f : -1.0f) == xi[i]);
+        if (same || est_new <= est) { if (est_new > est) est = est_new; break; }
+        est = est_new;
+        for (int64_t i = 0; i < n; ++i) xi[i] = (y[i] >= 0.0f) ? 1.0f : -1.0f;
+        for (int64_t i = 0; i < n; ++i) z[i] = xi[i];
+        upper32_solve_t(R, n, z);
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        float mag = (n > 1) ? 1.0f + (float)i / (float)(n - 1) : 1.0f;
+        y[i] = (i % 2 == 0) ? mag : -mag;
+    }
+    upper32_solve(R, n, y);
+    float alt = 2.0f * norm1_32(y, n) / (3.0f * (float)n);
+    if (alt > est) est = alt;
+    free(x); free(y); free(xi); free(z);
+    return est;
+}
+
+/* kappa_1(R) = ||R||_1 * Hager's estimate of ||R^{-1}||_1, R n-by-n upper
+ * (FP64 storage, ld) taken to FP32; +inf if not finite or not positive. */
+double lsqo_kappa1_upper32(const double* R, int64_t n, int64_t ld)
+{
+    float* Rf = (float*)calloc((size_t)n * (size_t)n, sizeof(float));
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i <= j; ++i) Rf[IDX(i, j, n)] = (float)R[IDX(i, j, ld)];
+    float rn = 0.0f;
+    for (int64_t j = 0; j < n; ++j) {
+        float cs = 0.0f;
+        for (int64_t i = 0; i <= j; ++i) cs = cs + fabsf(Rf[IDX(i, j, n)]);
+        if (cs > rn) rn = cs;
+    }
+    float inv = hager_rinv_norm1(Rf, n, 5);
+    free(Rf);
+    double k1 = (double)rn * (double)inv;
+    return (isfinite(k1) && k1 > 0.0) ? k1 : INFINITY;
+}
+
+int lsqo_condest_sketch(const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed,
+                        double* kappa0, int32_t* chosen, double* kappa1_out)
+{
+    int64_t se = 2 * n < m ? 2 * n : m;
+    int zeta = se < 8 ? (int)se : 8;
+    double* As = (double*)malloc(sizeof(double) * (size_t)se * (size_t)n);
+    int32_t* ce = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    double* R = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    float* G = (float*)malloc(sizeof(float) * (size_t)n * (size_t)n);
+    float* L = (float*)calloc((size_t)n * (size_t)n, sizeof(float));
+    int rc = lsqo_sketch(A, m, n, lda, O_SPARSE_SIGN, se, zeta, seed, O_FP32, As, ce);
+    if (!rc) rc = lsqo_qr_r(As, se, n, se, O_FP32, R);
+    double k1 = INFINITY, k0 = INFINITY;
+    if (!rc) {
+        lsqo_unscale_r(R, n, n, ce);
+        k1 = lsqo_kappa1_upper32(R, n, n);
+        /* G_s = fl32(A_e^T A_e) of the unscaled sketch, products rounded then
+         * summed in row order (as for A^T A in lsqo_condest) */
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t q = 0; q < n; ++q)
+            for (int64_t p = q; p < n; ++p) {
+                float acc = 0.0f;
+                for (int64_t i = 0; i < se; ++i) {
+                    float prod = (float)ldexp(As[IDX(i, p, se)], -ce[p]) * (float)ldexp(As[IDX(i, q, se)], -ce[q]);
+                    acc = acc + prod;
+                }
+                G[IDX(p, q, n)] = acc;
+                G[IDX(q, p, n)] = acc;
+            }
+        float nrm = 0.0f;
+        for (int64_t q = 0; q < n; ++q) {
+            float cs = 0.0f;
+            for (int64_t p = 0; p < n; ++p) cs = cs + fabsf(G[IDX(p, q, n)]);
+            if (cs > nrm) nrm = cs;
+        }
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = j; i < n; ++i) L[IDX(i, j, n)] = (float)R[IDX(j, i, n)];
+        float gam = hager_inv_norm1(L, n, 5);
+        double prod = (double)n * (double)nrm * (double)gam;
+        if (isfinite(k1) && 0x1p-24 * k1 <= 1.0 && isfinite(prod) && prod > 0.0) k0 = 0.5 * log10(prod);
+    }
+    if (kappa0) *kappa0 = k0;
+    if (chosen) *chosen = lsqo_precision_from_kappa0(k0);
+    if (kappa1_out) *kappa1_out = k1;
+    free(As); free(ce); free(R); free(G); free(L);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------
  * LU with partial pivoting of a tall s-by-n matrix (s >= n), Golub & Van
  * Loan Alg. 3.4.1 run over the n columns with the pivot searched over all s
  * rows (the FIRST row of largest magnitude): P A = L U with L s-by-n unit
@@ -888,6 +1041,10 @@ int lsqo_solve_method(const double* A, int64_t m, int64_t n, int64_t lda, const 
     if (prec == O_AUTO) {
         int32_t ch;
         lsqo_condest(A, m, n, lda, &k0, &ch, NULL, NULL);
+        prec = ch;
+    } else if (prec == O_AUTO_SKETCH) {
+        int32_t ch;
+        lsqo_condest_sketch(A, m, n, lda, seed, &k0, &ch, NULL);
         prec = ch;
     }
     if (prec < O_FP8 || prec > O_FP64) return -1;

@@ -188,3 +188,43 @@ def test_refinement_does_not_hurt(method):
     e0 = P.rel_error(O.solve(pr.A, pr.b, refine_steps=0, **kw)["x"], pr.x_star)
     e1 = P.rel_error(O.solve(pr.A, pr.b, refine_steps=1, **kw)["x"], pr.x_star)
     assert e1 <= 2 * e0 + 1e-15
+
+
+# --- condition estimate on a sketch -------------------------------------------
+def test_kappa1_upper32_is_a_lower_bound_and_close():
+    rng = np.random.default_rng(12)
+    for kap in (1e1, 1e3, 1e5):
+        n = 80
+        Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        R = np.linalg.qr(Q @ np.diag(np.logspace(0, -np.log10(kap), n)) @ Q.T, mode="r")
+        R = R * np.sign(np.diag(R))[:, None]
+        R32 = R.astype(np.float32).astype(np.float64)
+        exact = np.abs(R32).sum(0).max() * np.abs(np.linalg.inv(R32)).sum(0).max()
+        k1 = O.kappa1_upper32(R)
+        assert exact / 3 <= k1 <= exact * (1 + 1e-3), (kap, k1, exact)
+
+
+@pytest.mark.parametrize("m,n", [(4000, 64), (6000, 300)])
+def test_condest_sketch_tracks_kappa(m, n):
+    for kap in (1e1, 1e2, 1e3, 1e4, 1e5):
+        pr = P.make_problem(m, n, kap, 0.0, 17)
+        k0, ch, k1, rc = O.condest_sketch(pr.A, 4)
+        assert rc == 0
+        if np.isinf(k0):
+            # only where the FP32 factor itself does not resolve A
+            assert 2.0 ** -24 * k1 > 1.0
+            continue
+        # like the estimate on A^T A (Sec. 6.1): kappa(A)^2 <= n ||G||_1 ||G^{-1}||_1
+        # <= n^2 kappa(A)^2, up to the sketch's distortion of kappa(A) (a
+        # factor ~2 for s = 2n) and Hager's underestimate (at most 3x)
+        assert np.log10(kap) - 0.3 - 0.5 * np.log10(3) <= k0 <= np.log10(kap) + np.log10(n) + 0.3, (kap, k0)
+        assert ch == O.precision_from_kappa0(k0)
+        kl = O.condest(pr.A)[0]
+        if np.isfinite(kl):
+            assert abs(k0 - kl) <= 0.5, (kap, k0, kl)
+
+
+def test_condest_sketch_saturates_to_double():
+    pr = P.make_problem(4000, 64, 1e10, 0.0, 18)
+    k0, ch, k1, rc = O.condest_sketch(pr.A, 4)
+    assert rc == 0 and np.isinf(k0) and ch == O.FP64 and 2.0 ** -24 * k1 > 1.0
