@@ -54,14 +54,18 @@ typedef enum {
 } lsq_status;
 
 /* Precisions.  For the sketch, u_p of Alg. 1; AUTO runs the condition
- * estimate (lsq_condest) and applies the precision table below. */
+ * estimate of Sec. 6.1 on A^T A (lsq_condest) and applies the precision
+ * table below; AUTO_SKETCH runs the same estimator on the Gram of a sketch
+ * (lsq_condest_sketch), which avoids the m n^2 pass and the FP32 Cholesky
+ * breakdown of A^T A once kappa(A)^2 > 1/u32. */
 typedef enum {
     LSQ_FP8_E4M3 = 0,  /* OCP FP8 e4m3 ("fn": no infinities, saturating) */
     LSQ_BF16 = 1,
     LSQ_FP16 = 2,      /* the paper's "half precision" */
     LSQ_FP32 = 3,      /* "single precision" */
     LSQ_FP64 = 4,      /* "double precision" */
-    LSQ_AUTO = 5
+    LSQ_AUTO = 5,
+    LSQ_AUTO_SKETCH = 6
 } lsq_prec;
 
 typedef enum {
@@ -78,7 +82,11 @@ typedef enum {
     LSQ_OP_TRSM_GRAM = 5,
     LSQ_OP_FACTOR_SOLVE = 6,
     LSQ_OP_PNE_HOST = 7,
-    LSQ_OP_HPNE_HOST = 8
+    LSQ_OP_HPNE_HOST = 8,
+    LSQ_OP_CONDEST_SKETCH = 9,
+    LSQ_OP_HPNE_QR = 10,
+    LSQ_OP_SNE = 11,
+    LSQ_OP_NNE = 12
 } lsq_op;
 
 /* Solver options (fixed-width fields; zero-initialise unused ones).
@@ -168,6 +176,23 @@ lsq_status lsq_precond_qr(const void* As, int64_t s, int64_t n, int64_t ldas, in
 lsq_status lsq_condest(const double* A, int64_t m, int64_t n, int64_t lda, double* kappa0,
                        int32_t* chosen, void* ws, size_t ws_bytes, void* stream);
 
+/* Condition estimate on a sketch (a reading of Alg. 1's first line that
+ * replaces A^T A of Sec. 6.1 by the Gram of a sketch):
+ *   1. A_e = Omega_e A, an FP32 sparse-sign sketch with s_e = min(2n, m)
+ *      rows and zeta = min(8, s_e) nonzeros per column, Philox key `seed`
+ *      (as lsq_sketch);
+ *   2. R_e, the FP32 Householder R of A_e (as lsq_precond_qr);
+ *   3. the estimator of Sec. 6.1 on G_s = fl32(A_e^T A_e): ||G_s||_1 and
+ *      Hager's estimate gamma of ||G_s^{-1}||_1 with G_s^{-1} applied through
+ *      L = R_e^T (R_e^T R_e = G_s), kappa0 = 0.5 log10(n ||G_s||_1 gamma);
+ *   4. if Hager's kappa_1(R_e) exceeds 1/u32 (an FP32 factor that does not
+ *      resolve A, Lemma rscond), kappa0 = +inf and FP64 is chosen.
+ * kappa0 (double) and chosen (int32, by lsq_precision_from_kappa0) are
+ * device pointers.  Workspace lsq_workspace_size(LSQ_OP_CONDEST_SKETCH, m, n,
+ * NULL). */
+lsq_status lsq_condest_sketch(const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed, double* kappa0,
+                              int32_t* chosen, void* ws, size_t ws_bytes, void* stream);
+
 /* FP64 preconditioning and Gram formation (Alg. 1, "Solve A_p = A R_s^{-1}",
  * and the left-hand sides of Eqs. e_pne / e_hpne):
  *   Ap = A Rs^{-1} (m x n, ld ldap >= m; forward substitution by blocks);
@@ -237,6 +262,36 @@ lsq_status lsq_pne_solve(const double* A, int64_t m, int64_t n, int64_t lda, con
 lsq_status lsq_hpne_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
                           const lsq_opts* opts, double* x, double* Rs_out, int32_t* info,
                           void* ws, size_t ws_bytes, void* stream);
+
+/* HPNE (Eq. e_hpne) with a QR factorization of H = A_p^T A instead of LU
+ * (Sec. 1 names both): the Householder R of the (n+1) x (n+1) matrix
+ * [[H, c], [0, 1]], c = A_p^T b, in FP64 (the preconditioner QR kernel),
+ * holds R_H and Q_H^T c, and x = R_H^{-1} (Q_H^T c).  Refinement: the same
+ * with A_p^T r in place of c.  Workspace LSQ_OP_HPNE_QR. */
+lsq_status lsq_hpne_qr_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                             const lsq_opts* opts, double* x, double* Rs_out, int32_t* info, void* ws,
+                             size_t ws_bytes, void* stream);
+
+/* Seminormal equations (Sec. 5, Eq. e_sne) R^T R x = A^T b with R the
+ * triangular factor of a thin QR of A taken from the preconditioner:
+ * A_p = A R_s^{-1} = Q R_p with R_p^T R_p = A_p^T A_p = L L^T (Cholesky), so
+ * R = L^T R_s, applied in factored form:
+ * x = R_s^{-1} L^{-T} L^{-1} R_s^{-T} (A^T b).  The error grows with
+ * kappa(A)^2 (Thm. l_semi), against kappa(A) for PNE; one refinement step
+ * (the corrected seminormal equations, A^T r on the right) recovers it.
+ * Workspace LSQ_OP_SNE. */
+lsq_status lsq_sne_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, const lsq_opts* opts,
+                         double* x, double* Rs_out, int32_t* info, void* ws, size_t ws_bytes, void* stream);
+
+/* Not-normal equations (Sec. 5, Eq. e_nne) B^T A x = B^T b with
+ * B = A U_s^{-1}, U_s the upper factor of the LU with partial pivoting
+ * (first largest pivot) of the sketch A_s, computed in the preconditioner
+ * precision (qr_prec arithmetic: FP32 or FP64) and unscaled like R_s; B has
+ * A's column space and Omega B = P^T L_s.  Then as HPNE: B^T A by LU with
+ * partial pivoting.  Us_out (n x n, may be NULL) receives U_s.  A zero pivot
+ * of the sketch's LU is reported in info.  Workspace LSQ_OP_NNE. */
+lsq_status lsq_nne_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, const lsq_opts* opts,
+                         double* x, double* Us_out, int32_t* info, void* ws, size_t ws_bytes, void* stream);
 
 /* End-to-end variants on HOST buffers (pinned memory recommended): copy
  * A_host (ld lda) and b_host into the workspace, solve, copy x back to
@@ -358,8 +413,9 @@ lsq_status lsq_pne_solve_batched(int32_t count, const lsq_batch_problem* probs, 
 lsq_status lsq_hpne_solve_batched(int32_t count, const lsq_batch_problem* probs, void* ws, size_t ws_bytes,
                                   void* stream);
 
-/* ---- Learned precision proposal (an addition; the paper's estimator of
- * Sec. 6.1 stays the fallback and the judge is its 1-norm estimator) ------ */
+/* ---- Learned precision proposal (an addition to the paper; the paper's
+ * estimator of Sec. 6.1, on the Gram of a sketch, judges every proposal that
+ * could lose accuracy and is the fallback) -------------------------------- */
 
 /* Number of MLP parameters for d input features (d -> 64 -> 64 -> 64 -> 4,
  * packed W1 b1 W2 b2 W3 b3 W4 b4, W row-major out x in), and d itself. */
@@ -404,12 +460,18 @@ size_t lsq_judge_workspace_size(int64_t n);
 lsq_status lsq_judge_preconditioner(const double* Rs, int64_t n, int64_t ldr, int32_t prec, int32_t* accept,
                                     double* kappa1, void* ws, size_t ws_bytes, void* stream);
 
-/* PNE (Alg. 1) with the learned proposal: propose u_p, compute R_s in u_p,
- * judge it, escalate FP8 -> BF16 -> FP32 -> FP64 until accepted (FP64 needs no
- * judge), then finish with the accepted R_s.  used_prec and escalations are
- * HOST int32 outputs; the call synchronises the stream once per judged
- * candidate.  opts gives the sketch kind, s, zeta, seed and refinement; its
- * precisions are ignored. */
+/* PNE (Alg. 1) with the learned proposal: the MLP proposes u_p.  A proposal
+ * below FP64 could lose accuracy, so the paper's estimator judges it
+ * (lsq_condest_sketch, key opts->seed): when the estimate's own choice is a
+ * higher precision, that choice replaces the proposal (the fallback; one
+ * escalation).  The preconditioner is then computed in u_p and its FP32
+ * kappa_1 estimate gives a second opinion (u_p kappa_1(R_s) <= 1, Lemma
+ * rscond), escalating FP8 -> BF16 -> FP32 -> FP64 until accepted.  An FP64
+ * proposal needs no judge (and skips the estimate).  The solve finishes with
+ * the accepted R_s.  used_prec and escalations are HOST int32 outputs; the
+ * call synchronises the stream after the proposal, the estimate and each
+ * judged candidate.  opts gives the sketch kind, s, zeta, seed and
+ * refinement; its precisions are ignored. */
 size_t lsq_learned_workspace_size(int64_t m, int64_t n, const lsq_opts* opts);
 lsq_status lsq_pne_solve_learned(const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
                                  const lsq_opts* opts, const float* params, int32_t d, double* x, int32_t* info,
@@ -435,13 +497,17 @@ int64_t lsq_launch_count(void);
  * indices: 0 condition estimate, 1 sketch, 2 QR, 3 TRSM A R_s^{-1},
  * 4 Gram + right-hand side, 5 factorization, 6 solves, 7 refinement;
  * 8 single launches of the tensor-core FP64 update kernel (lsq_trsm_tc,
- * the Cholesky updates), 9 single launches of the QR panel kernel);
+ * the Cholesky updates, the K chunks of an FP64 Gaussian sketch), 9 single
+ * launches of the QR panel kernel, 10 single launches of the tensor-core
+ * sketch GEMM);
  * lsq_profile(0) stops.  lsq_profile_collect waits for the recorded events,
  * writes the summed milliseconds and the number of records per stage
  * (arrays of at least 8; indices >= nstages are skipped), and clears the
  * records; lsq_profile_collect_work also writes the summed algorithmic work
  * per stage (flops: 36 digit-pair products of 2 M N K each for the update
- * kernel, the Householder panel flops for the QR panel; 0 for the steps).
+ * kernel, the Householder panel flops for the QR panel, 2 M N K of the
+ * launch's K for the sketch GEMM, which is six times the product's for an
+ * FP32 sketch of BF16 pieces; 0 for the steps).
  * Host-side state, not thread safe across concurrent solves on different
  * streams. */
 int32_t lsq_profile(int32_t enable);
@@ -453,12 +519,6 @@ int32_t lsq_profile_collect_work(double* ms_by_stage, int32_t* count_by_stage, d
  * first `cap` records into ms / work; returns the number of records of that
  * stage (negative status on error).  Waits for the events. */
 int32_t lsq_profile_records(int32_t stage, double* ms, double* work, int32_t cap);
-
-/* FP64 FMA throughput probe: `blocks` CTAs of 256 threads, each thread
- * 8 independent FMA chains of `iters` steps (16 * iters flops per thread).
- * scratch: device double[blocks], written only to keep the chains live.
- * The caller times the launch to obtain the device's FP64 FMA rate. */
-int32_t lsq_probe_fp64_fma(int64_t iters, int32_t blocks, double* scratch, void* stream);
 
 #ifdef __cplusplus
 }

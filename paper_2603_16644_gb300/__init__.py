@@ -17,15 +17,21 @@ import os
 import torch
 
 __all__ = [
-    "FP8_E4M3", "BF16", "FP16", "FP32", "FP64", "AUTO", "GAUSSIAN", "SPARSE_SIGN",
+    "FP8_E4M3", "BF16", "FP16", "FP32", "FP64", "AUTO", "AUTO_SKETCH", "GAUSSIAN", "SPARSE_SIGN", "METHODS",
+    "condest_sketch",
     "Opts", "lib", "colmajor", "workspace", "sketch", "precond_qr", "condest", "trsm_gram",
     "factor_solve", "trsm_tc", "gram_tc", "gemm_tn_tc", "set_fp64_emulation", "pne", "hpne", "solve", "solve_host", "sparse_sign_operator",
     "gaussian_operator", "precision_from_kappa0", "status_string", "LsqError",
 ]
 
-FP8_E4M3, BF16, FP16, FP32, FP64, AUTO = 0, 1, 2, 3, 4, 5
+FP8_E4M3, BF16, FP16, FP32, FP64, AUTO, AUTO_SKETCH = 0, 1, 2, 3, 4, 5, 6
 GAUSSIAN, SPARSE_SIGN = 0, 1
-OP_SKETCH, OP_PRECOND_QR, OP_CONDEST, OP_PNE, OP_HPNE, OP_TRSM_GRAM, OP_FACTOR_SOLVE, OP_PNE_HOST, OP_HPNE_HOST = range(9)
+(OP_SKETCH, OP_PRECOND_QR, OP_CONDEST, OP_PNE, OP_HPNE, OP_TRSM_GRAM, OP_FACTOR_SOLVE, OP_PNE_HOST, OP_HPNE_HOST,
+ OP_CONDEST_SKETCH, OP_HPNE_QR, OP_SNE, OP_NNE) = range(13)
+# solution methods: entry point and workspace op
+METHODS = {"pne": ("lsq_pne_solve", OP_PNE), "hpne": ("lsq_hpne_solve", OP_HPNE),
+           "hpne_qr": ("lsq_hpne_qr_solve", OP_HPNE_QR), "sne": ("lsq_sne_solve", OP_SNE),
+           "nne_lu": ("lsq_nne_solve", OP_NNE)}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblsq.so")
@@ -64,6 +70,11 @@ def lib():
             "lsq_precond_qr": (C.c_int32, [_vp, _i64, _i64, _i64, C.c_int32, C.c_int32, _vp, _vp, _i64, _vp, _vp,
                                            _sz, _vp]),
             "lsq_condest": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _sz, _vp]),
+            "lsq_condest_sketch": (C.c_int32, [_vp, _i64, _i64, _i64, C.c_uint64, _vp, _vp, _vp, _sz, _vp]),
+            "lsq_hpne_qr_solve": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, C.POINTER(Opts), _vp, _vp, _vp, _vp, _sz,
+                                              _vp]),
+            "lsq_sne_solve": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, C.POINTER(Opts), _vp, _vp, _vp, _vp, _sz, _vp]),
+            "lsq_nne_solve": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, C.POINTER(Opts), _vp, _vp, _vp, _vp, _sz, _vp]),
             "lsq_trsm_gram": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, C.c_int32, _vp, _i64, _vp, _i64,
                                           _vp, _vp, _sz, _vp]),
             "lsq_factor_solve": (C.c_int32, [C.c_int32, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _sz,
@@ -81,7 +92,6 @@ def lib():
             "lsq_profile_collect_work": (C.c_int32, [C.POINTER(C.c_double), C.POINTER(C.c_int32),
                                                      C.POINTER(C.c_double), C.c_int32]),
             "lsq_profile_records": (C.c_int32, [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int32]),
-            "lsq_probe_fp64_fma": (C.c_int32, [_i64, C.c_int32, _vp, _vp]),
             "lsq_trsm_tc_workspace_size": (_sz, [_i64, _i64]),
             "lsq_trsm_tc": (C.c_int32, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
             "lsq_gram_tc_workspace_size": (_sz, [_i64, _i64]),
@@ -99,7 +109,8 @@ def lib():
     return _lib
 
 
-STAGES = ["condest", "sketch", "qr", "trsm", "gram", "factor", "solve", "refine", "k_ot_update", "k_qr_panel"]
+STAGES = ["condest", "sketch", "qr", "trsm", "gram", "factor", "solve", "refine", "k_ot_update", "k_qr_panel",
+          "k_sketch_tc"]
 
 
 def launch_count() -> int:
@@ -135,10 +146,6 @@ def profile_records(stage: str) -> list:
     work = (C.c_double * max(1, n))()
     lib().lsq_profile_records(idx, ms, work, n)
     return [(ms[i], work[i]) for i in range(n)]
-
-
-def probe_fp64_fma(iters: int, blocks: int, scratch: torch.Tensor) -> None:
-    _check(lib().lsq_probe_fp64_fma(iters, blocks, _ptr(scratch), _stream()), "lsq_probe_fp64_fma")
 
 
 def status_string(rc: int) -> str:
@@ -344,19 +351,32 @@ def factor_solve(G, c, Rs=None, hpne=False):
     return x, F, piv, info
 
 
-def solve(A, b, *, hpne=False, opts: Opts = None, ws=None, Rs_out=None, x=None, info=None, **kw):
-    """Alg. 1 end to end (PNE or HPNE).  Returns (x, info) device tensors."""
+def condest_sketch(A, seed=0, ws=None):
+    """Condition estimate on an FP32 sketch (lsq_condest_sketch): (kappa0, chosen) on the device."""
+    _need_cuda(A)
+    m, n = A.shape
+    k0 = torch.empty(1, dtype=torch.float64, device=A.device)
+    ch = torch.empty(1, dtype=torch.int32, device=A.device)
+    ws = workspace(OP_CONDEST_SKETCH, m, n, None, A.device) if ws is None else ws
+    _check(lib().lsq_condest_sketch(_ptr(A), m, n, _ld(A), C.c_uint64(seed), _ptr(k0), _ptr(ch), _ptr(ws),
+                                    ws.numel(), _stream()), "lsq_condest_sketch")
+    return k0, ch
+
+
+def solve(A, b, *, hpne=False, method=None, opts: Opts = None, ws=None, Rs_out=None, x=None, info=None, **kw):
+    """Alg. 1 end to end.  `method` (pne, hpne, hpne_qr, sne, nne_lu; default
+    PNE, or HPNE with hpne=True) picks the entry point.  Returns (x, info)
+    device tensors."""
     _need_cuda(A, b)
     m, n = A.shape
     lda = _ld(A)
     opts = opts or make_opts(n=n, **kw)
-    op = OP_HPNE if hpne else OP_PNE
+    name, op = METHODS[method or ("hpne" if hpne else "pne")]
     ws = workspace(op, m, n, opts, A.device) if ws is None else ws
     x = torch.empty(n, dtype=torch.float64, device=A.device) if x is None else x
     info = torch.zeros(1, dtype=torch.int32, device=A.device) if info is None else info
-    fn = lib().lsq_hpne_solve if hpne else lib().lsq_pne_solve
-    _check(fn(_ptr(A), m, n, lda, _ptr(b), C.byref(opts), _ptr(x), _ptr(Rs_out), _ptr(info), _ptr(ws), ws.numel(),
-              _stream()), "lsq_hpne_solve" if hpne else "lsq_pne_solve")
+    _check(getattr(lib(), name)(_ptr(A), m, n, lda, _ptr(b), C.byref(opts), _ptr(x), _ptr(Rs_out), _ptr(info),
+                                _ptr(ws), ws.numel(), _stream()), name)
     return x, info
 
 

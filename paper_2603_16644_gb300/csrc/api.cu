@@ -63,6 +63,13 @@ namespace {
 // Gaussian sketches in FP8/BF16/FP16 run on the tensor cores unless switched
 // off (lsq_set_tensor_core_sketch), which routes them to the CUDA-core GEMM.
 bool g_tensor_core_sketch = true;
+}  // namespace
+
+namespace lsq {
+bool tensor_core_sketch_enabled() { return g_tensor_core_sketch; }
+}  // namespace lsq
+
+namespace {
 
 // The symmetric FP64 Gram of PNE (csrc/ozaki.cu) and the off-diagonal
 // products of A_p = A R^{-1} (csrc/oz_trsm.cu) run as digit-sliced
@@ -72,13 +79,23 @@ bool g_fp64_emulation = true;
 inline cudaStream_t S(void* p) { return reinterpret_cast<cudaStream_t>(p); }
 
 bool valid_sketch_prec(int p) { return p >= LSQ_FP8_E4M3 && p <= LSQ_FP64; }
+bool is_auto(int p) { return p == LSQ_AUTO || p == LSQ_AUTO_SKETCH; }
+
+// Solution methods (Sec. 1, Sec. 5): PNE (Eq. e_pne), HPNE with LU or QR
+// (Eq. e_hpne), seminormal equations (Eq. e_sne), not-normal equations with
+// B = A U_s^{-1} (Eq. e_nne).
+enum { M_PNE = 0, M_HPNE = 1, M_HPNE_QR = 2, M_SNE = 3, M_NNE = 4 };
+// methods whose n x n system is A_p^T A (nonsymmetric) rather than A_p^T A_p
+bool method_nonsym(int m) { return m == M_HPNE || m == M_HPNE_QR || m == M_NNE; }
+// Workspaces of AUTO solves are laid out for the widest precision (FP64).
+int layout_prec(int p) { return is_auto(p) ? LSQ_FP64 : p; }
 
 lsq_status check_opts(const lsq_opts* o, int64_t m, int64_t n, bool allow_auto) {
     if (!o) return LSQ_ERR_ARG;
     if (o->kind != LSQ_GAUSSIAN && o->kind != LSQ_SPARSE_SIGN) return LSQ_ERR_ARG;
     if (o->s < n || o->s > m || o->s > 0x7fffffff) return LSQ_ERR_ARG;
     if (o->kind == LSQ_SPARSE_SIGN && (o->zeta < 1 || o->zeta > 32 || o->zeta > o->s)) return LSQ_ERR_ARG;
-    if (!valid_sketch_prec(o->sketch_prec) && !(allow_auto && o->sketch_prec == LSQ_AUTO)) return LSQ_ERR_ARG;
+    if (!valid_sketch_prec(o->sketch_prec) && !(allow_auto && is_auto(o->sketch_prec))) return LSQ_ERR_ARG;
     if (o->qr_prec != LSQ_FP32 && o->qr_prec != LSQ_FP64) return LSQ_ERR_ARG;
     if (o->refine_steps < 0 || o->refine_steps > 1) return LSQ_ERR_ARG;
     return LSQ_OK;
@@ -96,9 +113,18 @@ struct Off {
 };
 
 struct SketchLayout {
-    size_t colmax, colexp, ahat, idx, sgn, counts, rowptr, cursor, col, maxcount, err, om, gemm, total;
+    size_t colmax, colexp, ahat, idx, sgn, counts, rowptr, cursor, col, maxcount, err, om, gemm, total, gemm_bytes;
     int64_t ldq, ldo;
 };
+
+// Columns of Omega per digit-sliced product of the FP64 Gaussian sketch (the
+// largest K whose digit-pair sums stay exact in FP32).
+constexpr int64_t kSketchChunk = 512;
+
+// The Gaussian sketch on the tensor cores: FP64 by digit slicing (switch
+// lsq_set_fp64_emulation), FP32 as BF16 pieces (lsq_set_tensor_core_sketch).
+bool gauss_fp64_tc(int prec) { return prec == LSQ_FP64 && g_fp64_emulation && ot_trsm_supported(); }
+bool gauss_fp32_tc(int prec) { return prec == LSQ_FP32 && g_tensor_core_sketch && sketch_tc_supported(LSQ_BF16); }
 
 SketchLayout sketch_layout(int64_t m, int64_t n, int64_t s, int kind, int zeta, int prec, int sms) {
     SketchLayout L{};
@@ -118,6 +144,16 @@ SketchLayout sketch_layout(int64_t m, int64_t n, int64_t s, int kind, int zeta, 
         L.cursor = o.take(sizeof(int32_t) * (size_t)s);
         L.col = o.take(sizeof(uint32_t) * (size_t)m * zeta);
         L.maxcount = o.take(sizeof(int32_t));
+    } else if (gauss_fp64_tc(prec)) {
+        // FP64: K chunks of Omega generated one at a time, digit-sliced
+        // tensor-core products accumulated into A_s (A is read in place)
+        L.om = o.take(sizeof(double) * (size_t)s * kSketchChunk);
+        L.gemm = o.take(ot_update_ws_bytes(s, n, kSketchChunk));
+    } else if (gauss_fp32_tc(prec)) {
+        // FP32: three BF16 pieces per value, six K segments of length ldq
+        L.ahat = o.take(sizeof(uint16_t) * 6 * (size_t)L.ldq * n);
+        L.om = o.take(sizeof(uint16_t) * 6 * (size_t)L.ldo * s);
+        L.gemm = o.take(sketch_tc_ws_bytes(s, n, 6 * L.ldq, LSQ_BF16, sms));
     } else {
         L.ahat = o.take((size_t)L.ldq * n * es);
         L.om = o.take((size_t)L.ldo * s * es);
@@ -125,17 +161,122 @@ SketchLayout sketch_layout(int64_t m, int64_t n, int64_t s, int kind, int zeta, 
         L.gemm = o.take(std::max(gemm_kmajor_ws_bytes(gp), sketch_tc_ws_bytes(s, n, m, prec, sms)));
     }
     L.total = o.off;
+    L.gemm_bytes = L.total - L.gemm;
     return L;
+}
+
+// Condition estimate on a sketch (lsq_condest_sketch): its options and scratch.
+lsq_opts est_opts(int64_t m, int64_t n, uint64_t seed) {
+    lsq_opts e{};
+    e.kind = LSQ_SPARSE_SIGN;
+    e.s = std::min<int64_t>(2 * n, m);
+    e.zeta = (int32_t)std::min<int64_t>(8, e.s);
+    e.seed = seed;
+    e.sketch_prec = LSQ_FP32;
+    e.qr_prec = LSQ_FP32;
+    return e;
+}
+
+struct EstLayout {
+    SketchLayout sk;
+    size_t sk_base, ae, re, qr, qr_bytes, judge, judge_bytes, g, gemm, gemm_bytes, z, fin, fin_bytes, acc, k1, qinfo,
+        gerr, total;
+    bool tc;
+    int64_t ldz;
+};
+
+EstLayout est_layout(int64_t m, int64_t n, int sms) {
+    EstLayout L{};
+    Off q;
+    const lsq_opts e = est_opts(m, n, 0);
+    L.sk = sketch_layout(m, n, e.s, e.kind, e.zeta, LSQ_FP32, sms);
+    L.sk_base = q.take(L.sk.total);
+    L.ae = q.take(sizeof(float) * (size_t)e.s * n);
+    L.re = q.take(sizeof(double) * (size_t)n * n);
+    L.qr_bytes = qr_ws_bytes(e.s, n, LSQ_FP32);
+    L.qr = q.take(L.qr_bytes);
+    L.judge_bytes = judge_ws_bytes(n);
+    L.judge = q.take(L.judge_bytes);
+    L.g = q.take(sizeof(float) * (size_t)n * n);
+    // G_s on the tensor cores (BF16 pieces, one GEMM) or the FP32 CUDA-core GEMM
+    L.tc = tensor_core_sketch_enabled() && sketch_tc_supported(LSQ_BF16);
+    if (L.tc) {
+        L.ldz = align_up((size_t)e.s, 16);
+        L.z = q.take(sizeof(uint16_t) * 7 * (size_t)L.ldz * n);
+        L.gemm_bytes = sketch_tc_ws_bytes(n, n, 6 * L.ldz, LSQ_BF16, sms);
+    } else {
+        L.gemm_bytes = gemm_kmajor_ws_bytes(plan_gemm_kmajor(n, n, e.s, true, LSQ_FP32, sms));
+    }
+    L.gemm = q.take(L.gemm_bytes);
+    L.gerr = q.take(sizeof(int32_t));
+    L.fin_bytes = condest_sketch_finish_ws_bytes(n);
+    L.fin = q.take(L.fin_bytes);
+    L.acc = q.take(sizeof(int32_t));
+    L.k1 = q.take(sizeof(double));
+    L.qinfo = q.take(sizeof(int32_t));
+    L.total = q.off;
+    return L;
+}
+
+lsq_status run_sketch(const double* A, int64_t m, int64_t n, int64_t lda, const lsq_opts* o, int prec, void* As,
+                      int64_t ldas, int32_t* colexp_out, char* base, const SketchLayout& L, int32_t* err,
+                      cudaStream_t st);
+
+__global__ void k_reject_on_err(const int32_t* __restrict__ err, int32_t* __restrict__ accept) {
+    if (*err != 0) *accept = 0;
+}
+
+// FP32 sparse-sign sketch, its FP32 R_e, the judge of R_e and the estimator
+// of Sec. 6.1 on the sketch's Gram (csrc/condest.cu); base: EstLayout.
+lsq_status run_condest_sketch(const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed, double* kappa0,
+                              int32_t* chosen, char* base, const EstLayout& L, int sms, cudaStream_t st) {
+    const lsq_opts e = est_opts(m, n, seed);
+    char* skb = base + L.sk_base;
+    int32_t* err = (int32_t*)(skb + L.sk.err);
+    int32_t* ce = (int32_t*)(skb + L.sk.colexp);
+    float* Ae = (float*)(base + L.ae);
+    double* Re = (double*)(base + L.re);
+    int32_t* acc = (int32_t*)(base + L.acc);
+    double* k1 = (double*)(base + L.k1);
+    int32_t* qinfo = (int32_t*)(base + L.qinfo);
+    LSQ_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+    LSQ_CUDA_TRY(cudaMemsetAsync(qinfo, 0, sizeof(int32_t), st));
+    lsq_status r = run_sketch(A, m, n, lda, &e, LSQ_FP32, Ae, e.s, ce, skb, L.sk, err, st);
+    if (r != LSQ_OK) return r;
+    if ((r = launch_precond_qr(Ae, e.s, n, e.s, LSQ_FP32, LSQ_FP32, ce, Re, n, qinfo, base + L.qr, L.qr_bytes, st)) !=
+        LSQ_OK)
+        return r;
+    if ((r = launch_judge(Re, n, n, LSQ_FP32, acc, k1, base + L.judge, L.judge_bytes, st)) != LSQ_OK) return r;
+    float* G = (float*)(base + L.g);
+    if (L.tc) {
+        uint16_t* Z = (uint16_t*)(base + L.z);
+        int32_t* gerr = (int32_t*)(base + L.gerr);
+        LSQ_CUDA_TRY(cudaMemsetAsync(gerr, 0, sizeof(int32_t), st));
+        if ((r = launch_gram_split3<float>(Ae, e.s, n, e.s, L.ldz, Z, st)) != LSQ_OK) return r;
+        r = launch_sketch_tc(Z, 7 * L.ldz, Z + L.ldz, 7 * L.ldz, LSQ_BF16, n, n, 6 * L.ldz, G, n, base + L.gemm,
+                             L.gemm_bytes, gerr, st);
+        if (r != LSQ_OK) return r;
+        // a timed-out pipeline leaves no Gram: reject the factor (the overflow case, FP64)
+        k_reject_on_err<<<1, 1, 0, st>>>(gerr, acc);
+        LSQ_LAUNCH_CHECK();
+    } else {
+        GemmPlan gp = plan_gemm_kmajor(n, n, e.s, true, LSQ_FP32, sms);
+        if ((r = launch_gemm_kmajor(gp, Ae, LSQ_FP32, e.s, Ae, LSQ_FP32, e.s, G, n, base + L.gemm, st)) != LSQ_OK)
+            return r;
+    }
+    return launch_condest_sketch_finish(G, ce, Re, n, n, acc, kappa0, chosen, base + L.fin, L.fin_bytes, st);
 }
 
 struct SolveLayout {
     SketchLayout sk;
-    size_t sk_base, as_, rs, qr, ap, g, c, x, r, gv, piv, gemm, gemv, cond, k0, ch, err, tsync, oz, total;
+    size_t sk_base, as_, rs, qr, ap, g, c, x, r, gv, piv, gemm, gemv, cond, k0, ch, err, tsync, oz, est, total;
+    size_t hq_m, hq_r, hq_qr, hq_qr_bytes;  // HPNE through QR: [[H, c], [0, 1]], its R, QR scratch
     size_t oz_bytes;
     size_t qr_bytes, cond_bytes;
 };
 
-SolveLayout solve_layout(int64_t m, int64_t n, const lsq_opts* o, int prec, bool hpne, int sms) {
+SolveLayout solve_layout(int64_t m, int64_t n, const lsq_opts* o, int prec, int method, int sms) {
+    const bool hpne = method_nonsym(method);
     SolveLayout L{};
     Off q;
     L.sk = sketch_layout(m, n, o->s, o->kind, o->zeta, prec, sms);
@@ -150,6 +291,7 @@ SolveLayout solve_layout(int64_t m, int64_t n, const lsq_opts* o, int prec, bool
     L.rs = q.take(sizeof(double) * (size_t)n * n);
     int qp = prec == LSQ_FP64 ? LSQ_FP64 : o->qr_prec;
     L.qr_bytes = qr_ws_bytes(o->s, n, qp);
+    if (method == M_NNE) L.qr_bytes = std::max(L.qr_bytes, lu_precond_ws_bytes(o->s, n, qp));
     L.qr = q.take(L.qr_bytes);
     L.ap = q.take(sizeof(double) * (size_t)m * n);
     L.g = q.take(sizeof(double) * (size_t)n * n);
@@ -170,6 +312,13 @@ SolveLayout solve_layout(int64_t m, int64_t n, const lsq_opts* o, int prec, bool
     // shared by the tensor-core A_p (first) and the tensor-core Gram of PNE
     L.oz_bytes = std::max(ot_trsm_ws_bytes(m, n), hpne ? oz_gemm_tn_ws_bytes(m, n) : oz_gram_ws_bytes(m, n));
     L.oz = q.take(L.oz_bytes);
+    L.est = o->sketch_prec == LSQ_AUTO_SKETCH ? q.take(est_layout(m, n, sms).total) : 0;
+    if (method == M_HPNE_QR) {
+        L.hq_m = q.take(sizeof(double) * (size_t)(n + 1) * (n + 1));
+        L.hq_r = q.take(sizeof(double) * (size_t)(n + 1) * (n + 1));
+        L.hq_qr_bytes = qr_ws_bytes(n + 1, n + 1, LSQ_FP64);
+        L.hq_qr = q.take(L.hq_qr_bytes);
+    }
     L.total = q.off + 256;
     return L;
 }
@@ -199,6 +348,29 @@ lsq_status run_sketch(const double* A, int64_t m, int64_t n, int64_t lda, const 
         return launch_sparse_gather((int32_t*)(base + L.rowptr), (uint32_t*)(base + L.col), base + L.ahat, prec,
                                     o->s, n, As, ldas, st);
     }
+    if (gauss_fp64_tc(prec)) {
+        // A_s = sum over K chunks of Omega[:, chunk] A[chunk, :], each chunk an
+        // FP64-accurate product (C - (-Omega) A), accumulated in FP64
+        double* As64 = (double*)As;
+        double* om = (double*)(base + L.om);
+        LSQ_CUDA_TRY(cudaMemset2DAsync(As64, sizeof(double) * ldas, 0, sizeof(double) * o->s, n, st));
+        for (int64_t k0 = 0; k0 < m; k0 += kSketchChunk) {
+            const int64_t kc = std::min<int64_t>(kSketchChunk, m - k0);
+            if ((r = launch_gauss_negchunk(o->seed, o->s, k0, kc, om, st)) != LSQ_OK) return r;
+            if ((r = ot_gemm_update(om, o->s, A + k0, 1, lda, As64, ldas, As64, ldas, o->s, n, kc, base + L.gemm,
+                                    L.gemm_bytes, err, st, 0, nullptr, 0, 0)) != LSQ_OK)
+                return r;
+        }
+        return LSQ_OK;
+    }
+    if (gauss_fp32_tc(prec)) {
+        const int64_t K6 = 6 * L.ldq;
+        if ((r = launch_gauss_split3(o->seed, o->s, m, L.ldq, (uint16_t*)(base + L.om), st)) != LSQ_OK) return r;
+        if ((r = launch_quantize_split3(A, m, n, lda, colexp, L.ldq, (uint16_t*)(base + L.ahat), st)) != LSQ_OK)
+            return r;
+        return launch_sketch_tc(base + L.om, K6, base + L.ahat, K6, LSQ_BF16, o->s, n, K6, (float*)As, ldas,
+                                base + L.gemm, L.gemm_bytes, err, st);
+    }
     if ((r = launch_gauss_gen(o->seed, o->s, m, prec, base + L.om, L.ldo, st)) != LSQ_OK) return r;
     if ((r = launch_quantize_cm(A, m, n, lda, colexp, prec, base + L.ahat, L.ldq, st)) != LSQ_OK) return r;
     if (g_tensor_core_sketch && sketch_tc_supported(prec))
@@ -206,6 +378,32 @@ lsq_status run_sketch(const double* A, int64_t m, int64_t n, int64_t lda, const 
                                 base + L.gemm, L.total - L.gemm, err, st);
     GemmPlan gp = plan_gemm_kmajor(o->s, n, m, false, prec == LSQ_FP64 ? LSQ_FP64 : LSQ_FP32, device_sm_count());
     return launch_gemm_kmajor(gp, base + L.om, prec, L.ldo, base + L.ahat, prec, L.ldq, As, ldas, base + L.gemm, st);
+}
+
+// HPNE through QR: M = [[H, v], [0, 1]] ((n+1) x (n+1), ld n+1); the
+// Householder R of M holds R_H and Q_H^T v, so H x = v gives x = R_H^{-1}
+// (Q_H^T v).
+__global__ void k_hq_augment(const double* __restrict__ H, int64_t n, int64_t ldh, const double* __restrict__ v,
+                             double* __restrict__ M) {
+    const int64_t n1 = n + 1, total = n1 * n1;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q % n1, j = q / n1;
+        M[q] = (i < n && j < n) ? H[i + j * ldh] : (j == n ? (i < n ? v[i] : 1.0) : 0.0);
+    }
+}
+
+lsq_status hq_solve(const double* H, int64_t n, double* v, char* base, const SolveLayout& L, int32_t* info,
+                    int32_t* sync, int32_t* err, cudaStream_t st) {
+    double* M = (double*)(base + L.hq_m);
+    double* Ra = (double*)(base + L.hq_r);
+    const int64_t n1 = n + 1;
+    k_hq_augment<<<(unsigned)std::min<int64_t>(ceil_div(n1 * n1, 256), 8192), 256, 0, st>>>(H, n, n, v, M);
+    LSQ_LAUNCH_CHECK();
+    lsq_status r = launch_precond_qr(M, n1, n1, n1, LSQ_FP64, LSQ_FP64, nullptr, Ra, n1, info, base + L.hq_qr,
+                                     L.hq_qr_bytes, st);
+    if (r != LSQ_OK) return r;
+    LSQ_CUDA_TRY(cudaMemcpyAsync(v, Ra + n * n1, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    return launch_trsv<double>(TRSV_UPPER, Ra, n, n1, v, info, sync, err, st);
 }
 
 // Solve with the factors already in G (and piv / Rs): PNE: L L^T y = v, x = Rs^{-1} y;
@@ -256,28 +454,33 @@ lsq_status trsm_gram(const double* A, int64_t m, int64_t n, int64_t lda, const d
     return r;
 }
 
-lsq_status solve_impl(bool hpne, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+lsq_status solve_impl(int method, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
                       const lsq_opts* o, double* x, double* Rs_out, int32_t* info, void* ws, size_t ws_bytes,
                       cudaStream_t st, const double* Rs_in = nullptr) {
+    if (method < M_PNE || method > M_NNE) return LSQ_ERR_ARG;
+    const bool hpne = method_nonsym(method);
     if (!A || !b || !x || !info || m <= 0 || n <= 0 || lda < m) return LSQ_ERR_ARG;
     lsq_status r = check_opts(o, m, n, true);
     if (r != LSQ_OK) return r;
     int sms = device_sm_count();
     // Layout with the widest sketch precision when AUTO, so one workspace
     // serves whatever precision the estimate picks.
-    int prec_for_layout = o->sketch_prec == LSQ_AUTO ? LSQ_FP64 : o->sketch_prec;
-    SolveLayout L = solve_layout(m, n, o, prec_for_layout, hpne, sms);
+    SolveLayout L = solve_layout(m, n, o, layout_prec(o->sketch_prec), method, sms);
     if (!ws || L.total > ws_bytes) return LSQ_ERR_NOMEM;
     char* base = aligned(ws);
     int32_t* err = (int32_t*)(base + L.err);
     LSQ_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
     LSQ_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
     int prec = o->sketch_prec;
-    if (prec == LSQ_AUTO) {
+    if (is_auto(prec)) {
         double* k0 = (double*)(base + L.k0);
         int32_t* ch = (int32_t*)(base + L.ch);
         stage_mark(ST_CONDEST, true, st);
-        if ((r = launch_condest(A, m, n, lda, k0, ch, base + L.cond, L.cond_bytes, sms, st)) != LSQ_OK) return r;
+        if (prec == LSQ_AUTO)
+            r = launch_condest(A, m, n, lda, k0, ch, base + L.cond, L.cond_bytes, sms, st);
+        else
+            r = run_condest_sketch(A, m, n, lda, o->seed, k0, ch, base + L.est, est_layout(m, n, sms), sms, st);
+        if (r != LSQ_OK) return r;
         stage_mark(ST_CONDEST, false, st);
         int32_t host_ch = LSQ_FP64;
         LSQ_CUDA_TRY(cudaMemcpyAsync(&host_ch, ch, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -306,34 +509,56 @@ lsq_status solve_impl(bool hpne, const double* A, int64_t m, int64_t n, int64_t 
         if ((r = run_sketch(A, m, n, lda, o, prec, As, s, colexp, skb, SK, err, st)) != LSQ_OK) return r;
         stage_mark(ST_SKETCH, false, st);
         stage_mark(ST_QR, true, st);
-        if ((r = launch_precond_qr(As, s, n, s, prec == LSQ_FP64 ? LSQ_FP64 : LSQ_FP32, qp, colexp, Rs, n, info,
-                                   base + L.qr, L.qr_bytes, st)) != LSQ_OK)
-            return r;
+        const int as_prec = prec == LSQ_FP64 ? LSQ_FP64 : LSQ_FP32;
+        if (method == M_NNE)
+            r = launch_lu_precond(As, s, n, s, as_prec, qp, colexp, Rs, n, info, base + L.qr, L.qr_bytes, st);
+        else
+            r = launch_precond_qr(As, s, n, s, as_prec, qp, colexp, Rs, n, info, base + L.qr, L.qr_bytes, st);
+        if (r != LSQ_OK) return r;
         stage_mark(ST_QR, false, st);
     }
     if ((r = trsm_gram(A, m, n, lda, Rs, n, b, hpne, Ap, m, G, n, c, base + L.gemm, (double*)(base + L.gemv),
                        (int64_t)(gemv_t_ws_bytes(m, n) / sizeof(double)), sms, st, base + L.oz, L.oz_bytes, err)) !=
         LSQ_OK)
         return r;
+    int32_t* tsync = (int32_t*)(base + L.tsync);
+    double* gemv_ws = (double*)(base + L.gemv);
+    const int64_t gemv_cap = (int64_t)(gemv_t_ws_bytes(m, n) / sizeof(double));
+    if (method == M_SNE) {
+        // right-hand side of Eq. e_sne in factored form: R_s^{-T} (A^T b)
+        if ((r = launch_gemv_t(A, m, n, lda, b, c, gemv_ws, gemv_cap, st)) != LSQ_OK) return r;
+        if ((r = launch_trsv<double>(TRSV_UPPER_T, Rs, n, n, c, info, tsync, err, st)) != LSQ_OK) return r;
+    }
     stage_mark(ST_FACTOR, true, st);
-    if (hpne)
+    if (method == M_HPNE || method == M_NNE)
         r = launch_lu(G, n, n, piv, info, st);
-    else
+    else if (method != M_HPNE_QR)
         r = launch_cholesky<double>(G, n, n, info, st, base + L.oz, L.oz_bytes);
     if (r != LSQ_OK) return r;
     stage_mark(ST_FACTOR, false, st);
     stage_mark(ST_SOLVE, true, st);
     LSQ_CUDA_TRY(cudaMemcpyAsync(x, c, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    int32_t* tsync = (int32_t*)(base + L.tsync);
-    if ((r = solve_factored(hpne, G, n, n, piv, Rs, n, x, info, tsync, err, st)) != LSQ_OK) return r;
+    if (method == M_HPNE_QR)
+        r = hq_solve(G, n, x, base, L, info, tsync, err, st);
+    else
+        r = solve_factored(hpne, G, n, n, piv, Rs, n, x, info, tsync, err, st);
+    if (r != LSQ_OK) return r;
     stage_mark(ST_SOLVE, false, st);
     if (o->refine_steps > 0) stage_mark(ST_REFINE, true, st);
     for (int step = 0; step < o->refine_steps; ++step) {
         if ((r = launch_residual(A, m, n, lda, x, b, r_, st)) != LSQ_OK) return r;
-        if ((r = launch_gemv_t(Ap, m, n, m, r_, gv, (double*)(base + L.gemv),
-                               (int64_t)(gemv_t_ws_bytes(m, n) / sizeof(double)), st)) != LSQ_OK)
+        if (method == M_SNE) {
+            // corrected seminormal equations: R^T R d = A^T r
+            if ((r = launch_gemv_t(A, m, n, lda, r_, gv, gemv_ws, gemv_cap, st)) != LSQ_OK) return r;
+            if ((r = launch_trsv<double>(TRSV_UPPER_T, Rs, n, n, gv, info, tsync, err, st)) != LSQ_OK) return r;
+        } else if ((r = launch_gemv_t(Ap, m, n, m, r_, gv, gemv_ws, gemv_cap, st)) != LSQ_OK) {
             return r;
-        if ((r = solve_factored(hpne, G, n, n, piv, Rs, n, gv, info, tsync, err, st)) != LSQ_OK) return r;
+        }
+        if (method == M_HPNE_QR)
+            r = hq_solve(G, n, gv, base, L, info, tsync, err, st);
+        else
+            r = solve_factored(hpne, G, n, n, piv, Rs, n, gv, info, tsync, err, st);
+        if (r != LSQ_OK) return r;
         if ((r = launch_axpy1(x, gv, n, st)) != LSQ_OK) return r;
     }
     if (o->refine_steps > 0) stage_mark(ST_REFINE, false, st);
@@ -354,7 +579,7 @@ HostLayout host_layout(int64_t m, int64_t n, const lsq_opts* o, bool hpne, int s
     H.b = q.take(sizeof(double) * m);
     H.x = q.take(sizeof(double) * n);
     H.info = q.take(sizeof(int32_t));
-    int p = o->sketch_prec == LSQ_AUTO ? LSQ_FP64 : o->sketch_prec;
+    int p = layout_prec(o->sketch_prec);
     H.solve = q.take(solve_layout(m, n, o, p, hpne, sms).total);
     H.total = q.off + 256;
     return H;
@@ -545,11 +770,20 @@ size_t lsq_workspace_size(int32_t op, int64_t m, int64_t n, const lsq_opts* o) {
         return qr_ws_bytes(m, n, LSQ_FP64) + 256;
     case LSQ_OP_CONDEST:
         return condest_ws_bytes(m, n, sms) + 256;
+    case LSQ_OP_CONDEST_SKETCH:
+        return est_layout(m, n, sms).total + 256;
     case LSQ_OP_PNE:
-    case LSQ_OP_HPNE: {
+    case LSQ_OP_HPNE:
+    case LSQ_OP_HPNE_QR:
+    case LSQ_OP_SNE:
+    case LSQ_OP_NNE: {
         if (check_opts(o, m, n, true) != LSQ_OK) return 0;
-        int p = o->sketch_prec == LSQ_AUTO ? LSQ_FP64 : o->sketch_prec;
-        return solve_layout(m, n, o, p, op == LSQ_OP_HPNE, sms).total + 256;
+        const int method = op == LSQ_OP_PNE    ? M_PNE
+                           : op == LSQ_OP_HPNE ? M_HPNE
+                           : op == LSQ_OP_HPNE_QR ? M_HPNE_QR
+                           : op == LSQ_OP_SNE  ? M_SNE
+                                               : M_NNE;
+        return solve_layout(m, n, o, layout_prec(o->sketch_prec), method, sms).total + 256;
     }
     case LSQ_OP_TRSM_GRAM: {
         GemmPlan gp = plan_gemm_kmajor(n, n, m, false, LSQ_FP64, sms);
@@ -616,6 +850,15 @@ lsq_status lsq_condest(const double* A, int64_t m, int64_t n, int64_t lda, doubl
     return launch_condest(A, m, n, lda, kappa0, chosen, ws, ws_bytes, device_sm_count(), S(stream));
 }
 
+lsq_status lsq_condest_sketch(const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed, double* kappa0,
+                              int32_t* chosen, void* ws, size_t ws_bytes, void* stream) {
+    if (!A || !kappa0 || !chosen || m <= 0 || n <= 0 || lda < m) return LSQ_ERR_ARG;
+    int sms = device_sm_count();
+    EstLayout L = est_layout(m, n, sms);
+    if (!ws || L.total + 256 > ws_bytes) return LSQ_ERR_NOMEM;
+    return run_condest_sketch(A, m, n, lda, seed, kappa0, chosen, aligned(ws), L, sms, S(stream));
+}
+
 lsq_status lsq_trsm_gram(const double* A, int64_t m, int64_t n, int64_t lda, const double* Rs, int64_t ldr,
                          const double* b, int32_t hpne, double* Ap, int64_t ldap, double* G, int64_t ldg, double* c,
                          void* ws, size_t ws_bytes, void* stream) {
@@ -663,6 +906,22 @@ lsq_status lsq_hpne_solve(const double* A, int64_t m, int64_t n, int64_t lda, co
     return solve_impl(true, A, m, n, lda, b, opts, x, Rs_out, info, ws, ws_bytes, S(stream));
 }
 
+lsq_status lsq_hpne_qr_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                             const lsq_opts* opts, double* x, double* Rs_out, int32_t* info, void* ws, size_t ws_bytes,
+                             void* stream) {
+    return solve_impl(M_HPNE_QR, A, m, n, lda, b, opts, x, Rs_out, info, ws, ws_bytes, S(stream));
+}
+
+lsq_status lsq_sne_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, const lsq_opts* opts,
+                         double* x, double* Rs_out, int32_t* info, void* ws, size_t ws_bytes, void* stream) {
+    return solve_impl(M_SNE, A, m, n, lda, b, opts, x, Rs_out, info, ws, ws_bytes, S(stream));
+}
+
+lsq_status lsq_nne_solve(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, const lsq_opts* opts,
+                         double* x, double* Us_out, int32_t* info, void* ws, size_t ws_bytes, void* stream) {
+    return solve_impl(M_NNE, A, m, n, lda, b, opts, x, Us_out, info, ws, ws_bytes, S(stream));
+}
+
 lsq_status lsq_pne_solve_host(const double* A_host, int64_t m, int64_t n, int64_t lda, const double* b_host,
                               const lsq_opts* opts, double* x_host, int32_t* info_host, void* ws, size_t ws_bytes,
                               void* stream) {
@@ -687,8 +946,7 @@ lsq_status solve_impl_ext(bool hpne, const double* A, int64_t m, int64_t n, int6
 }
 
 size_t solve_ws_bytes_ext(int64_t m, int64_t n, const lsq_opts* o, bool hpne) {
-    int p = o->sketch_prec == LSQ_AUTO ? LSQ_FP64 : o->sketch_prec;
-    return solve_layout(m, n, o, p, hpne, device_sm_count()).total + 256;
+    return solve_layout(m, n, o, layout_prec(o->sketch_prec), hpne, device_sm_count()).total + 256;
 }
 
 }  // namespace lsq

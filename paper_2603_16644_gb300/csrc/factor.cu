@@ -319,24 +319,25 @@ template lsq_status launch_cholesky<float>(float*, int64_t, int64_t, int32_t*, c
 // ---------------------------------------------------------------------------
 // LU with partial pivoting
 // ---------------------------------------------------------------------------
-// Panel columns [k0, k0+nb), rows [k0, n), one block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_lu_panel(double* __restrict__ H, int64_t ld, int64_t n, int64_t k0, int nb,
+// Panel columns [k0, k0+nb), rows [k0, rows), one block of 1024 threads.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_lu_panel(T* __restrict__ H, int64_t ld, int64_t rows, int64_t k0, int nb,
                                                    int32_t* __restrict__ piv, int32_t* __restrict__ info) {
-    __shared__ double wv[32];
+    __shared__ T wv[32];
     __shared__ int64_t wi[32];
     __shared__ int64_t pivrow;
     int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int jj = 0; jj < nb; ++jj) {
         int64_t j = k0 + jj;
         // pivot: largest |H[i][j]|, smallest i on ties
-        double best = -1.0;
-        int64_t bi = n;
-        for (int64_t i = j + tid; i < n; i += 1024) {
-            double v = fabs(H[i + j * ld]);
+        T best = (T)-1;
+        int64_t bi = rows;
+        for (int64_t i = j + tid; i < rows; i += 1024) {
+            T v = fabs(H[i + j * ld]);
             if (v > best) { best = v; bi = i; }
         }
         for (int off = 16; off > 0; off >>= 1) {
-            double ov = __shfl_xor_sync(0xffffffffu, best, off);
+            T ov = __shfl_xor_sync(0xffffffffu, best, off);
             int64_t oi = __shfl_xor_sync(0xffffffffu, bi, off);
             if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
         }
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(1024) k_lu_panel(double* __restrict__ H, int64
             best = wv[lane];
             bi = wi[lane];
             for (int off = 16; off > 0; off >>= 1) {
-                double ov = __shfl_xor_sync(0xffffffffu, best, off);
+                T ov = __shfl_xor_sync(0xffffffffu, best, off);
                 int64_t oi = __shfl_xor_sync(0xffffffffu, bi, off);
                 if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
             }
@@ -359,22 +360,22 @@ __global__ void __launch_bounds__(1024) k_lu_panel(double* __restrict__ H, int64
         int64_t p = pivrow;
         if (p != j)
             for (int c = tid; c < nb; c += 1024) {
-                double t = H[j + (k0 + c) * ld];
+                T t = H[j + (k0 + c) * ld];
                 H[j + (k0 + c) * ld] = H[p + (k0 + c) * ld];
                 H[p + (k0 + c) * ld] = t;
             }
         __syncthreads();
-        double d = H[j + j * ld];
-        bool zero = (d == 0.0) || !isfinite(d);
+        T d = H[j + j * ld];
+        bool zero = (d == (T)0) || !isfinite(d);
         if (zero) {
             if (tid == 0) set_info_once(info, (int32_t)(j + 1));
         } else {
-            for (int64_t i = j + 1 + tid; i < n; i += 1024) H[i + j * ld] = H[i + j * ld] / d;
+            for (int64_t i = j + 1 + tid; i < rows; i += 1024) H[i + j * ld] = H[i + j * ld] / d;
         }
         __syncthreads();
         if (!zero) {
-            for (int64_t i = j + 1 + tid; i < n; i += 1024) {
-                double l = H[i + j * ld];
+            for (int64_t i = j + 1 + tid; i < rows; i += 1024) {
+                T l = H[i + j * ld];
                 for (int c = jj + 1; c < nb; ++c) {
                     int64_t col = k0 + c;
                     H[i + col * ld] = fma(-l, H[j + col * ld], H[i + col * ld]);
@@ -386,14 +387,15 @@ __global__ void __launch_bounds__(1024) k_lu_panel(double* __restrict__ H, int64
 }
 
 // Apply the panel's row swaps (in order) to the columns outside the panel.
-__global__ void k_lu_swap(double* __restrict__ H, int64_t ld, int64_t n, int64_t k0, int nb,
+template <typename T>
+__global__ void k_lu_swap(T* __restrict__ H, int64_t ld, int64_t cols, int64_t k0, int nb,
                           const int32_t* __restrict__ piv) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n || (c >= k0 && c < k0 + nb)) return;
+    if (c >= cols || (c >= k0 && c < k0 + nb)) return;
     for (int jj = 0; jj < nb; ++jj) {
         int64_t j = k0 + jj, p = piv[j];
         if (p != j) {
-            double t = H[j + c * ld];
+            T t = H[j + c * ld];
             H[j + c * ld] = H[p + c * ld];
             H[p + c * ld] = t;
         }
@@ -401,41 +403,110 @@ __global__ void k_lu_swap(double* __restrict__ H, int64_t ld, int64_t n, int64_t
 }
 
 // U12 = L11^{-1} A12 (unit lower L11), one thread per column right of the panel.
-__global__ void k_lu_u12(double* __restrict__ H, int64_t ld, int64_t n, int64_t k0, int nb) {
-    __shared__ double L11[LNB][LNB + 1];
+template <typename T>
+__global__ void k_lu_u12(T* __restrict__ H, int64_t ld, int64_t cols, int64_t k0, int nb) {
+    __shared__ T L11[LNB][LNB + 1];
     for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
         int i = q % nb, j = q / nb;
         L11[i][j] = H[(k0 + i) + (k0 + j) * ld];
     }
     __syncthreads();
     int64_t c = k0 + nb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
-    double u[LNB];
+    if (c >= cols) return;
+    T u[LNB];
     for (int i = 0; i < nb; ++i) u[i] = H[(k0 + i) + c * ld];
     for (int i = 0; i < nb; ++i) {
-        double v = u[i];
+        T v = u[i];
         for (int k = 0; k < i; ++k) v = fma(-L11[i][k], u[k], v);
         u[i] = v;
     }
     for (int i = 0; i < nb; ++i) H[(k0 + i) + c * ld] = u[i];
 }
 
-lsq_status launch_lu(double* H, int64_t n, int64_t ld, int32_t* piv, int32_t* info, cudaStream_t st) {
-    for (int64_t k0 = 0; k0 < n; k0 += LNB) {
-        int nb = (int)std::min<int64_t>(LNB, n - k0);
-        k_lu_panel<<<1, 1024, 0, st>>>(H, ld, n, k0, nb, piv, info);
+// Blocked right-looking LU with partial pivoting of a rows x cols matrix
+// (rows >= cols): P H = L U, L unit lower trapezoidal, U cols x cols upper.
+template <typename T>
+lsq_status launch_lu_rect(T* H, int64_t rows, int64_t cols, int64_t ld, int32_t* piv, int32_t* info, cudaStream_t st) {
+    if (rows < cols) return LSQ_ERR_ARG;
+    for (int64_t k0 = 0; k0 < cols; k0 += LNB) {
+        int nb = (int)std::min<int64_t>(LNB, cols - k0);
+        k_lu_panel<T><<<1, 1024, 0, st>>>(H, ld, rows, k0, nb, piv, info);
         LSQ_LAUNCH_CHECK();
-        k_lu_swap<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(H, ld, n, k0, nb, piv);
+        k_lu_swap<T><<<(unsigned)ceil_div(cols, 128), 128, 0, st>>>(H, ld, cols, k0, nb, piv);
         LSQ_LAUNCH_CHECK();
-        int64_t rest = n - k0 - nb;
+        int64_t rest = cols - k0 - nb, rrest = rows - k0 - nb;
         if (rest <= 0) continue;
-        k_lu_u12<<<(unsigned)ceil_div(rest, 64), 64, 0, st>>>(H, ld, n, k0, nb);
+        k_lu_u12<T><<<(unsigned)ceil_div(rest, 64), 64, 0, st>>>(H, ld, cols, k0, nb);
         LSQ_LAUNCH_CHECK();
         // A22 -= L21 U12:  P(i,k) = H[(k0+nb+i) + (k0+k) ld],  Q(j,k) = H[(k0+k) + (k0+nb+j) ld]
-        lsq_status s = rank_update_ext<double>(H + (k0 + nb) + (k0 + nb) * ld, ld, H + (k0 + nb) + k0 * ld, 1, ld,
-                                           H + k0 + (k0 + nb) * ld, ld, 1, rest, rest, nb, false, nullptr, st);
+        lsq_status s = rank_update_ext<T>(H + (k0 + nb) + (k0 + nb) * ld, ld, H + (k0 + nb) + k0 * ld, 1, ld,
+                                          H + k0 + (k0 + nb) * ld, ld, 1, rrest, rest, nb, false, nullptr, st);
         if (s != LSQ_OK) return s;
     }
+    return LSQ_OK;
+}
+
+template lsq_status launch_lu_rect<float>(float*, int64_t, int64_t, int64_t, int32_t*, int32_t*, cudaStream_t);
+template lsq_status launch_lu_rect<double>(double*, int64_t, int64_t, int64_t, int32_t*, int32_t*, cudaStream_t);
+
+lsq_status launch_lu(double* H, int64_t n, int64_t ld, int32_t* piv, int32_t* info, cudaStream_t st) {
+    return launch_lu_rect<double>(H, n, n, ld, piv, info, st);
+}
+
+// The sketch's LU preconditioner (not-normal equations): the tall LU of A_s
+// (s x n, float or double) in T arithmetic, then U with the column scaling
+// undone, U_s[:, j] = U[:, j] 2^-colexp[j], promoted to FP64 (upper
+// triangle of Us written, ld ldu).
+template <typename TS, typename T>
+__global__ void k_lu_load(const TS* __restrict__ As, int64_t s, int64_t n, int64_t ldas, T* __restrict__ W) {
+    const int64_t total = s * n;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q % s, j = q / s;
+        W[q] = (T)As[i + j * ldas];
+    }
+}
+
+template <typename T>
+__global__ void k_lu_upper_out(const T* __restrict__ W, int64_t s, int64_t n, const int32_t* __restrict__ colexp,
+                               double* __restrict__ Us, int64_t ldu) {
+    const int64_t total = n * n;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q % n, j = q / n;
+        if (i <= j) Us[i + j * ldu] = ldexp((double)W[i + j * s], colexp ? -colexp[j] : 0);
+    }
+}
+
+size_t lu_precond_ws_bytes(int64_t s, int64_t n, int prec) {
+    const size_t es = prec == LSQ_FP64 ? 8 : 4;
+    return align_up(es * (size_t)s * n, 256) + align_up(sizeof(int32_t) * (size_t)n, 256) + 256;
+}
+
+lsq_status launch_lu_precond(const void* As, int64_t s, int64_t n, int64_t ldas, int as_prec, int lu_prec,
+                             const int32_t* colexp, double* Us, int64_t ldu, int32_t* info, void* ws, size_t ws_bytes,
+                             cudaStream_t st) {
+    if (!ws || ws_bytes < lu_precond_ws_bytes(s, n, lu_prec)) return LSQ_ERR_NOMEM;
+    const size_t es = lu_prec == LSQ_FP64 ? 8 : 4;
+    char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    int32_t* piv = (int32_t*)(base + align_up(es * (size_t)s * n, 256));
+    const unsigned g = (unsigned)std::min<int64_t>(ceil_div(s * n, 256), 8192);
+    const unsigned gu = (unsigned)std::min<int64_t>(ceil_div(n * n, 256), 8192);
+    lsq_status r;
+    if (lu_prec == LSQ_FP64) {
+        double* W = (double*)base;
+        if (as_prec == LSQ_FP64) k_lu_load<double, double><<<g, 256, 0, st>>>((const double*)As, s, n, ldas, W);
+        else k_lu_load<float, double><<<g, 256, 0, st>>>((const float*)As, s, n, ldas, W);
+        LSQ_LAUNCH_CHECK();
+        if ((r = launch_lu_rect<double>(W, s, n, s, piv, info, st)) != LSQ_OK) return r;
+        k_lu_upper_out<double><<<gu, 256, 0, st>>>(W, s, n, colexp, Us, ldu);
+    } else {
+        float* W = (float*)base;
+        if (as_prec == LSQ_FP64) k_lu_load<double, float><<<g, 256, 0, st>>>((const double*)As, s, n, ldas, W);
+        else k_lu_load<float, float><<<g, 256, 0, st>>>((const float*)As, s, n, ldas, W);
+        LSQ_LAUNCH_CHECK();
+        if ((r = launch_lu_rect<float>(W, s, n, s, piv, info, st)) != LSQ_OK) return r;
+        k_lu_upper_out<float><<<gu, 256, 0, st>>>(W, s, n, colexp, Us, ldu);
+    }
+    LSQ_LAUNCH_CHECK();
     return LSQ_OK;
 }
 
@@ -519,8 +590,8 @@ __global__ void __launch_bounds__(128) k_trsv_wave(int kind, const T* __restrict
     }
     __syncthreads();
     const int v = vb;
-    const bool forward = (kind == TB_LOWER || kind == TB_UNIT_LOWER);
-    const bool trans = (kind == TB_LOWER_T);  // operator entry (i, j) = M[j + i ld]
+    const bool forward = (kind == TB_LOWER || kind == TB_UNIT_LOWER || kind == TB_UPPER_T);
+    const bool trans = (kind == TB_LOWER_T || kind == TB_UPPER_T);  // operator entry (i, j) = M[j + i ld]
     const bool unit = (kind == TB_UNIT_LOWER);
     const bool use_inv = (kind == TB_LOWER || kind == TB_LOWER_T) && v > 0;
     const int b = forward ? v : nblk - 1 - v;

@@ -37,6 +37,20 @@ lsq_status launch_sparse_gather(const int32_t* rowptr, const uint32_t* col, cons
                                 int64_t n, void* As, int64_t ldas, cudaStream_t st);
 lsq_status launch_gauss_gen(uint64_t seed, int64_t s, int64_t m, int prec, void* Om, int64_t ldo, cudaStream_t st);
 lsq_status launch_gauss_inspect(uint64_t seed, int64_t s, int64_t m, int prec, double* Om, cudaStream_t st);
+// FP32 Gaussian sketch as one BF16 GEMM over six K segments of length L
+// (three BF16 pieces per FP32 value, pairs t + u <= 2).
+lsq_status launch_gauss_split3(uint64_t seed, int64_t s, int64_t m, int64_t L, uint16_t* X, cudaStream_t st);
+lsq_status launch_quantize_split3(const double* A, int64_t m, int64_t n, int64_t lda, const int32_t* colexp,
+                                  int64_t L, uint16_t* Y, cudaStream_t st);
+// FP32 Gram X^T X (X: m x n, FP64 or FP32, rounded to FP32) as one BF16 GEMM:
+// seven K segments per column (h l h m m h h); X at Z, Y at Z + L, ld 7L, K 6L.
+template <typename TI>
+lsq_status launch_gram_split3(const TI* A, int64_t m, int64_t n, int64_t lda, int64_t L, uint16_t* Z, cudaStream_t st);
+// Gaussian sketches in FP8/BF16/FP16/FP32 and the FP32 Gram of the condition
+// estimate on the tensor cores (lsq_set_tensor_core_sketch).
+bool tensor_core_sketch_enabled();
+// Columns [k0, k0 + kc) of -Omega (FP64), s x kc column-major, ld s.
+lsq_status launch_gauss_negchunk(uint64_t seed, int64_t s, int64_t k0, int64_t kc, double* Om, cudaStream_t st);
 
 // ---- gemm.cu: dense contractions on CUDA cores ------------------------------
 // C (M x N, column-major, ldc) = sum_k X[i*ldx + k] * Y[j*ldy + k]  (both
@@ -76,7 +90,7 @@ lsq_status launch_cholesky(T* G, int64_t n, int64_t ld, int32_t* info, cudaStrea
                            size_t ws_bytes = 0);
 size_t cholesky_ws_bytes(int64_t n);
 lsq_status launch_lu(double* H, int64_t n, int64_t ld, int32_t* piv, int32_t* info, cudaStream_t st);
-enum TrsvKind { TRSV_LOWER = 0, TRSV_LOWER_T = 1, TRSV_UPPER = 2, TRSV_UNIT_LOWER = 3 };
+enum TrsvKind { TRSV_LOWER = 0, TRSV_LOWER_T = 1, TRSV_UPPER = 2, TRSV_UNIT_LOWER = 3, TRSV_UPPER_T = 4 };
 // sync: trsv_sync_ints(n) int32 of scratch (cleared by the launch); err: the
 // device status word that a timed-out wait sets to -2 (may be NULL).
 size_t trsv_sync_ints(int64_t n);
@@ -128,6 +142,22 @@ lsq_status launch_precond_qr(const void* As, int64_t s, int64_t n, int64_t ldas,
 
 // ---- condest.cu --------------------------------------------------------------
 size_t condest_ws_bytes(int64_t m, int64_t n, int num_sms);
+// Estimate on a sketch: finish from G_s (FP32, of the scaled sketch; colexp
+// undoes the scaling), R_e and the FP32 judge's verdict on R_e.
+size_t condest_sketch_finish_ws_bytes(int64_t n);
+// LU with partial pivoting of the sketch (s x n) in FP32 or FP64 arithmetic;
+// U_s = U 2^-colexp promoted to FP64 (the not-normal equations' B = A U_s^{-1}).
+size_t lu_precond_ws_bytes(int64_t s, int64_t n, int prec);
+lsq_status launch_lu_precond(const void* As, int64_t s, int64_t n, int64_t ldas, int as_prec, int lu_prec,
+                             const int32_t* colexp, double* Us, int64_t ldu, int32_t* info, void* ws, size_t ws_bytes,
+                             cudaStream_t st);
+lsq_status launch_condest_sketch_finish(float* G, const int32_t* colexp, const double* Re, int64_t n, int64_t ldr,
+                                        const int32_t* accept, double* kappa0, int32_t* chosen, void* ws,
+                                        size_t ws_bytes, cudaStream_t st);
+// FP32 judge of a preconditioner (mlp.cu): Hager's kappa_1(R_s), accept = u_p kappa_1 <= 1.
+size_t judge_ws_bytes(int64_t n);
+lsq_status launch_judge(const double* Rs, int64_t n, int64_t ldr, int prec, int32_t* accept, double* kappa1, void* ws,
+                        size_t ws_bytes, cudaStream_t st);
 lsq_status launch_condest(const double* A, int64_t m, int64_t n, int64_t lda, double* kappa0, int32_t* chosen,
                           void* ws, size_t ws_bytes, int num_sms, cudaStream_t st);
 

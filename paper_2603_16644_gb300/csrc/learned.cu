@@ -1,6 +1,9 @@
-// C-ABI of the learned precision proposal and its judge (not in the paper;
-// the paper's own estimator of Sec. 6.1 stays the fallback), and of the PNE
-// solve that uses them.
+// C-ABI of the learned precision proposal and its judges (not in the
+// paper), and of the PNE solve that uses them.  The paper's own estimator of
+// Sec. 6.1 (here on the Gram of a sketch, lsq_condest_sketch) judges every
+// proposal that could lose accuracy (any precision below FP64) and is the
+// fallback when it rejects one; the FP32 Hager estimate of kappa_1(R_s) of
+// the computed preconditioner (Lemma rscond) is a second opinion.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -95,8 +98,8 @@ lsq_status features_impl(const double* A, int64_t m, int64_t n, int64_t lda, uin
 
 struct LearnLayout {
     FeatLayout F;
-    size_t feat, judge, small, as_, ce, sk, qr, rs, solve, total;
-    size_t judge_bytes, sk_bytes, qr_bytes, solve_bytes;
+    size_t feat, judge, small, as_, ce, sk, qr, rs, est, solve, total;
+    size_t judge_bytes, sk_bytes, qr_bytes, est_bytes, solve_bytes;
 };
 
 LearnLayout learn_layout(int64_t m, int64_t n, const lsq_opts* o) {
@@ -117,6 +120,8 @@ LearnLayout learn_layout(int64_t m, int64_t n, const lsq_opts* o) {
     L.qr_bytes = lsq_workspace_size(LSQ_OP_PRECOND_QR, o->s, n, nullptr);
     L.qr = q.take(L.qr_bytes);
     L.rs = q.take(sizeof(double) * (size_t)n * n);
+    L.est_bytes = lsq_workspace_size(LSQ_OP_CONDEST_SKETCH, m, n, nullptr);
+    L.est = q.take(L.est_bytes);
     lsq_opts oa = *o;
     oa.sketch_prec = LSQ_AUTO;  // widest layout
     L.solve_bytes = solve_ws_bytes_ext(m, n, &oa, false);
@@ -232,7 +237,24 @@ lsq_status lsq_pne_solve_learned(const double* A, int64_t m, int64_t n, int64_t 
     double* Rs = (double*)(base + L.rs);
     bool have_rs = false;
     lsq_opts o2 = *opts;
+    if (p != LSQ_FP64) {
+        // a proposal below FP64 could lose accuracy: the paper's estimator
+        // judges it, and its own choice replaces a proposal below it
+        double* dk0 = (double*)(base + L.small + 160);
+        int32_t* dch = (int32_t*)(base + L.small + 192);
+        if ((r = lsq_condest_sketch(A, m, n, lda, opts->seed, dk0, dch, base + L.est, L.est_bytes, st)) != LSQ_OK)
+            return r;
+        int32_t pe = LSQ_FP64;
+        LSQ_CUDA_TRY(cudaMemcpyAsync(&pe, dch, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        LSQ_CUDA_TRY(cudaStreamSynchronize(st));
+        if (pe < LSQ_FP8_E4M3 || pe > LSQ_FP64) pe = LSQ_FP64;
+        if (pe > p) {  // precision codes rise with the precision
+            p = pe;
+            ++esc;
+        }
+    }
     while (p != LSQ_FP64) {
+        // second opinion on the computed preconditioner: u_p kappa_1(R_s) <= 1
         o2.sketch_prec = p;
         o2.qr_prec = LSQ_FP32;
         if ((r = lsq_sketch(A, m, n, lda, &o2, As, o2.s, ce, nullptr, base + L.sk, L.sk_bytes, st)) != LSQ_OK) return r;

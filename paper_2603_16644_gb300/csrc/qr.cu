@@ -211,8 +211,8 @@ __device__ __forceinline__ T tree_sum(const T* x, int stride) {
 }
 
 // QCL: CTAs per cluster (16, non-portable, where the device allows it; else
-// 8).  Dynamic shared memory: the local panel (Rp x QNB) and, used by rank 0,
-// the V^T V partials of every rank (QCL x QNB x (QNB + 1)).
+// 8).  Dynamic shared memory: the local panel (Rp x QNB) and, in the fused
+// form, the previous panel's reflector rows and the partial products behind it.
 template <typename T, int QCL>
 __global__ void __launch_bounds__(QCT)
     k_qr_panel_cl(T* __restrict__ W, int64_t ld, int64_t s, int64_t k0, int nb, T* __restrict__ beta_out,
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(QCT)
     const int Rp = R | 1;
     const int r0 = rank * R;
     const int nloc = r0 < rows ? min(R, rows - r0) : 0;
-    T* Yall = P + (int64_t)Rp * QNB;  // [QCL][QNB][QNB + 1], rank 0 only
+    T* Yall = P + (int64_t)Rp * QNB;  // fused form only: the staging area behind the panel
     const int chunk = (R + (QCT / 32) - 1) / (QCT / 32);
     const int g0 = warp * chunk, g1 = min(nloc, g0 + chunk);  // this warp's rows
     // loads of all columns of a row in flight before the stores
@@ -959,9 +959,10 @@ __global__ void k_check_diag(const double* __restrict__ Rs, int64_t n, int64_t l
 template <typename T>
 static size_t qr_cluster_smem(int64_t rows, int qcl, bool fused) {
     const size_t Rp = (size_t)(ceil_div(rows, qcl) | 1);
-    const size_t yall = (size_t)qcl * QNB * (QNB + 1);
+    // the fused form also stages the previous panel's V rows and the W
+    // partials (Vl, Wk, Ct, Vt behind the local panel)
     const size_t pre = Rp * QNB + (size_t)(QKG + 2) * QNB * (QNB + 1);
-    return sizeof(T) * (Rp * QNB + (fused ? std::max(yall, pre) : yall));
+    return sizeof(T) * (Rp * QNB + (fused ? pre : 0));
 }
 
 struct QrCluster {

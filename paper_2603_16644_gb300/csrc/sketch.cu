@@ -387,6 +387,103 @@ __global__ void k_gauss_gen(uint64_t seed, int64_t s, int64_t m, int prec, void*
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 Gaussian sketch on the BF16 tensor cores.  An FP32 value x (24-bit
+// significand) is the exact sum of three BF16 pieces:
+//   h = bf16(x), r = x - h (exact), m = bf16(r), l = r - m (exact, 8 bits).
+// Omega_hat Ahat = sum over the pairs (t, u) of pieces with t + u <= 2 (the
+// three dropped pairs weigh below 2^-24 relative), i.e. one BF16 GEMM over a
+// K six times longer whose six K segments of length L hold
+//   Omega_hat rows: l m h m h h        Ahat columns: h m l h m h
+// (segment q pairs piece t_q of Omega_hat with piece u_q of Ahat).  The
+// smallest pairs come first, so the FP32 accumulator is still small while it
+// adds them and the rounding of the running sum at full size happens over
+// one segment only, as in a plain FP32 sum.  Padding beyond m is zero.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float to_f32_rn(double x) { return __double2float_rn(x); }
+__device__ __forceinline__ float to_f32_rn(float x) { return x; }
+
+__device__ __forceinline__ void split3_bf16(float x, uint16_t& h, uint16_t& m, uint16_t& l) {
+    __nv_bfloat16 bh = __float2bfloat16_rn(x);
+    float r = __fsub_rn(x, __bfloat162float(bh));
+    __nv_bfloat16 bm = __float2bfloat16_rn(r);
+    float r2 = __fsub_rn(r, __bfloat162float(bm));
+    __nv_bfloat16 bl = __float2bfloat16_rn(r2);
+    h = __bfloat16_as_ushort(bh);
+    m = __bfloat16_as_ushort(bm);
+    l = __bfloat16_as_ushort(bl);
+}
+
+// Omega_hat rows (FP32-rounded Box-Muller values) as BF16 pieces: row i at
+// X + i * 6L, segments l m h m h h.
+__global__ void k_gauss_split3(uint64_t seed, int64_t s, int64_t m, int64_t L, uint16_t* __restrict__ X) {
+    const int64_t i = blockIdx.y;
+    uint16_t* row = X + (size_t)i * 6 * L;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x) {
+        uint16_t h = 0, mi = 0, l = 0;
+        if (j < m) split3_bf16(__double2float_rn(gauss_entry(seed, i, j)), h, mi, l);
+        row[j] = l;
+        row[L + j] = mi;
+        row[2 * L + j] = h;
+        row[3 * L + j] = mi;
+        row[4 * L + j] = h;
+        row[5 * L + j] = h;
+    }
+}
+
+// Ahat = FP32(A 2^colexp) columns as BF16 pieces: column c at Y + c * 6L,
+// segments h m l h m h.
+__global__ void k_quantize_split3(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda,
+                                  const int32_t* __restrict__ colexp, int64_t L, uint16_t* __restrict__ Y) {
+    const int64_t c = blockIdx.y;
+    const int e = colexp[c];
+    uint16_t* col = Y + (size_t)c * 6 * L;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x) {
+        uint16_t h = 0, mi = 0, l = 0;
+        if (j < m) split3_bf16(__uint_as_float(quant_bits(A[j + c * lda], e, LSQ_FP32)), h, mi, l);
+        col[j] = h;
+        col[L + j] = mi;
+        col[2 * L + j] = l;
+        col[3 * L + j] = h;
+        col[4 * L + j] = mi;
+        col[5 * L + j] = h;
+    }
+}
+
+// Gram X^T X of FP32-rounded columns on the BF16 tensor cores: the six
+// pairs of pieces (t, u), t + u <= 2, chained through ONE array of seven K
+// segments per column, h l h m m h h: the GEMM reads X at segment offset 0
+// and Y at offset 1, which pairs (h,l) (l,h) (h,m) (m,m) (m,h) (h,h) -- the
+// full-size pair last, as in the sketch.  Column c at Z + c * 7L.
+template <typename TI>
+__global__ void k_gram_split3(const TI* __restrict__ A, int64_t m, int64_t n, int64_t lda, int64_t L,
+                              uint16_t* __restrict__ Z) {
+    const int64_t c = blockIdx.y;
+    uint16_t* col = Z + (size_t)c * 7 * L;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x) {
+        uint16_t h = 0, mi = 0, l = 0;
+        if (j < m) split3_bf16(to_f32_rn(A[j + c * lda]), h, mi, l);
+        col[j] = h;
+        col[L + j] = l;
+        col[2 * L + j] = h;
+        col[3 * L + j] = mi;
+        col[4 * L + j] = mi;
+        col[5 * L + j] = h;
+        col[6 * L + j] = h;
+    }
+}
+
+// Negated FP64 Omega columns [k0, k0 + kc) as an s x kc column-major block
+// (ld s): the K chunk of the FP64 sketch, which the digit-sliced update
+// subtracts (C - (-Omega) Ahat).
+__global__ void k_gauss_negchunk(uint64_t seed, int64_t s, int64_t k0, int64_t kc, double* __restrict__ Om) {
+    const int64_t total = s * kc;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q % s, j = q / s;
+        Om[q] = -gauss_entry(seed, i, k0 + j);
+    }
+}
+
 __global__ void k_gauss_inspect(uint64_t seed, int64_t s, int64_t m, int prec, double* __restrict__ Om) {
     int64_t total = s * m;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
@@ -532,6 +629,40 @@ lsq_status launch_sparse_gather(const int32_t* rowptr, const uint32_t* col, cons
 lsq_status launch_gauss_gen(uint64_t seed, int64_t s, int64_t m, int prec, void* Om, int64_t ldo, cudaStream_t st) {
     dim3 grid((unsigned)min64(ceil_div(ldo, 256), 128), (unsigned)s);
     k_gauss_gen<<<grid, 256, 0, st>>>(seed, s, m, prec, Om, ldo);
+    LSQ_LAUNCH_CHECK();
+    return LSQ_OK;
+}
+
+lsq_status launch_gauss_split3(uint64_t seed, int64_t s, int64_t m, int64_t L, uint16_t* X, cudaStream_t st) {
+    dim3 grid((unsigned)min64(ceil_div(L, 256), 64), (unsigned)s);
+    k_gauss_split3<<<grid, 256, 0, st>>>(seed, s, m, L, X);
+    LSQ_LAUNCH_CHECK();
+    return LSQ_OK;
+}
+
+lsq_status launch_quantize_split3(const double* A, int64_t m, int64_t n, int64_t lda, const int32_t* colexp,
+                                  int64_t L, uint16_t* Y, cudaStream_t st) {
+    dim3 grid((unsigned)min64(ceil_div(L, 256), 64), (unsigned)n);
+    k_quantize_split3<<<grid, 256, 0, st>>>(A, m, n, lda, colexp, L, Y);
+    LSQ_LAUNCH_CHECK();
+    return LSQ_OK;
+}
+
+template <typename TI>
+lsq_status launch_gram_split3(const TI* A, int64_t m, int64_t n, int64_t lda, int64_t L, uint16_t* Z, cudaStream_t st) {
+    dim3 grid((unsigned)min64(ceil_div(L, 256), 64), (unsigned)n);
+    k_gram_split3<TI><<<grid, 256, 0, st>>>(A, m, n, lda, L, Z);
+    LSQ_LAUNCH_CHECK();
+    return LSQ_OK;
+}
+template lsq_status launch_gram_split3<double>(const double*, int64_t, int64_t, int64_t, int64_t, uint16_t*,
+                                               cudaStream_t);
+template lsq_status launch_gram_split3<float>(const float*, int64_t, int64_t, int64_t, int64_t, uint16_t*,
+                                              cudaStream_t);
+
+lsq_status launch_gauss_negchunk(uint64_t seed, int64_t s, int64_t k0, int64_t kc, double* Om, cudaStream_t st) {
+    unsigned grid = (unsigned)min64(ceil_div(s * kc, 256), 16384);
+    k_gauss_negchunk<<<grid, 256, 0, st>>>(seed, s, k0, kc, Om);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
 }

@@ -271,6 +271,7 @@ lsq_status launch_sketch_tc(const void* Om, int64_t ldo, const void* Ahat, int64
     }
     size_t smem = 1024 + 2 * (size_t)TC_STAGES * TC_TILE_BYTES + 256;
     dim3 grid((unsigned)ceil_div(s, TC_BM), (unsigned)ceil_div(n, TC_BN), (unsigned)splits);
+    stage_mark(ST_K_SKETCHTC, true, st);
     switch (prec) {
     case LSQ_BF16:
         LSQ_CUDA_TRY(cudaFuncSetAttribute(k_sketch_tc<0, TC_BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -286,6 +287,7 @@ lsq_status launch_sketch_tc(const void* Om, int64_t ldo, const void* Ahat, int64
         break;
     }
     LSQ_LAUNCH_CHECK();
+    stage_mark(ST_K_SKETCHTC, false, st, 2.0 * (double)s * (double)n * (double)m);
     if (splits > 1) {
         k_reduce_f32<<<(unsigned)std::min<int64_t>(ceil_div(s * n, 256), 8192), 256, 0, st>>>(out, splits, s, n, As,
                                                                                             ldas);

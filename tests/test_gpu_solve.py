@@ -39,7 +39,8 @@ def test_fig1_config_residual_sweep(hpne):
         assert info == 0 == ref["info"]
         more = oracle_realizations(pr, hpne=hpne, kind=O.GAUSSIAN, s=200, seed=17 + k, sketch_prec=O.FP32,
                                    qr_prec=O.FP32)
-        assert_solution_parity(x, ref["x"], pr.x_star, 1e8, rho, f"rho={rho}", refined=False, realizations=more)
+        assert_solution_parity(x, ref["x"], pr.x_star, 1e8, rho, f"rho={rho}", refined=False, u_p=O.FP32,
+                               realizations=more)
 
 
 CASES = [
@@ -65,12 +66,9 @@ def test_solver_parity(hpne, case):
     pr = P.make_problem(m, n, kap, rho, P.seed_for(1, int(np.log10(kap)) + 20 * n))
     x, info, ref = run_both(pr, hpne, kind, s, zeta, 3, prec, refine=refine)
     assert info == ref["info"] == 0
-    u_p = {O.FP8_E4M3: 2.0 ** -4, O.BF16: 2.0 ** -8, O.FP16: 2.0 ** -11, O.FP32: 2.0 ** -24, O.FP64: 2.0 ** -53}[prec]
-    more = None
-    if u_p * kap > 1:  # outside Lemma rscond's regime: realization-dependent error
-        more = oracle_realizations(pr, hpne=hpne, kind=kind, s=s, zeta=zeta, seed=3, sketch_prec=prec,
-                                   qr_prec=O.FP32, refine_steps=refine)
-    assert_solution_parity(x, ref["x"], pr.x_star, kap, rho, refined=refine > 0, realizations=more)
+    more = oracle_realizations(pr, hpne=hpne, kind=kind, s=s, zeta=zeta, seed=3, sketch_prec=prec,
+                               qr_prec=O.FP32, refine_steps=refine)
+    assert_solution_parity(x, ref["x"], pr.x_star, kap, rho, refined=refine > 0, u_p=prec, realizations=more)
 
 
 @pytest.mark.parametrize("kap,want", [(1e2, O.FP16), (1e10, O.FP64)])
@@ -82,10 +80,7 @@ def test_auto_precision_matches_oracle(kap, want):
     k0, ch = lsq.condest(dev_colmajor(pr.A))
     assert int(to_np(ch)[0]) == want
     assert info == 0
-    # unrefined at kappa = 1e10 the error (~1e-4) is rounding noise amplified
-    # by kappa^2 rho: judge it against several oracle realizations
-    more = oracle_realizations(pr, hpne=False, kind=O.GAUSSIAN, s=192, zeta=0, seed=8, sketch_prec=O.AUTO)
-    assert_solution_parity(x, ref["x"], pr.x_star, kap, 1e-6, refined=False, realizations=more)
+    assert_solution_parity(x, ref["x"], pr.x_star, kap, 1e-6, refined=False, u_p=want)
 
 
 def test_edge_shapes():
@@ -148,16 +143,23 @@ def test_deterministic_and_host_path_identical():
     np.testing.assert_array_equal(xh.numpy(), x1)
 
 
+@pytest.mark.parametrize("kap,want", [(1e4, O.FP32), (1e8, O.FP64)])
 @pytest.mark.parametrize("hpne", [False, True])
-def test_large_single_problem_within_bound(hpne):
-    # the 262144 x 4096 problem (8.6 GB): Gaussian sketch s = 2n with
-    # per-column power-of-two scaling, its precision chosen by the condition
-    # estimate, FP64 rest.  kappa = 1e4 (at 1e8 the estimate selects an FP64
-    # sketch, a CUDA-core product of ~17 s).  Exact orthonormal U from signed
-    # Hadamard columns; the bound is evaluated on the device.
-    m, n, kap, rho = 262144, 4096, 1e4, 1e-8
+def test_large_single_problem_within_bound(hpne, kap, want):
+    # the 262144 x 4096 problem (8.6 GB) the benchmark times: Gaussian sketch
+    # s = 2n with per-column power-of-two scaling, its precision chosen by the
+    # condition estimate on a sketch (FP32 at kappa = 1e4, FP64 at 1e8), FP64
+    # rest.  Exact orthonormal U from signed Hadamard columns; the bound is
+    # evaluated on the device with exact condition numbers.  The paper
+    # evaluates its bounds with eps_A = u; a backward-stable FP64 evaluation
+    # has eps_A = gamma_n, but at this size the measured error stays within
+    # 10x the bound (the oracle's own ratios on the Fig. 1-5 shapes with
+    # u_p kappa(A) << 1 are below 0.4).
+    m, n, rho = 262144, 4096, 1e-6
     A, b, x_star, sigma, V = P.make_problem_hadamard_torch(m, n, kap, rho, P.seed_for(2, 0))
-    opts = lsq.make_opts(kind=lsq.GAUSSIAN, s=2 * n, seed=P.seed_for(2, 0), sketch_prec=lsq.AUTO,
+    k0, ch = lsq.condest_sketch(A, seed=P.seed_for(2, 0))
+    assert int(to_np(ch)[0]) == want, float(to_np(k0)[0])
+    opts = lsq.make_opts(kind=lsq.GAUSSIAN, s=2 * n, seed=P.seed_for(2, 0), sketch_prec=lsq.AUTO_SKETCH,
                          qr_prec=lsq.FP32, refine_steps=0)
     Rs = torch.zeros((n, n), dtype=torch.float64, device="cuda").t()
     x, info = lsq.solve(A, b, hpne=hpne, opts=opts, Rs_out=Rs)
@@ -176,7 +178,10 @@ def test_large_single_problem_within_bound(hpne):
     else:
         bound = kR * kAp * u2 * (kAp * kR * res + 1 + kap * u2)
     err = float(torch.linalg.norm(x - x_star) / torch.linalg.norm(x))
-    assert err <= n * bound, (err, bound, kAp)
+    print(f"262144x4096 kappa={kap:.0e} hpne={hpne}: err={err:.3e} bound={bound:.3e} ratio={err / bound:.3g} "
+          f"kappa(A_p)={kAp:.3g}")
+    assert kAp <= 10.0
+    assert err <= 10 * bound, (err, bound, kAp)
 
 
 @pytest.mark.parametrize("hpne", [False, True])
@@ -207,3 +212,32 @@ def test_full_size_tall_skinny_within_bound(hpne):
         bound = kR * kAp * u2 * (kAp * kR * res + 1 + kap * u2)
     err = P.rel_error(x, to_np(x_star))
     assert err <= n * bound, (err, bound, kAp)
+
+
+# The nine 65536 x 1024 problems the benchmark times (its seeds, its launch
+# configuration: sparse sign s = 4n, zeta = 8, BF16 sketch, FP32 QR, one
+# refinement step), each against the oracle at full size under the solution
+# tolerance of the method.
+C1_KAPPAS, C1_RHOS = [1e2, 1e6, 1e10], [0.0, 1e-8, 1e-3]
+C1_CASES = [(i, j, False) for i in range(3) for j in range(3)] + [(0, 2, True), (1, 1, True), (2, 0, True)]
+
+
+@pytest.mark.parametrize("i,j,hpne", C1_CASES,
+                         ids=lambda v: str(v) if not isinstance(v, bool) else ("hpne" if v else "pne"))
+def test_tall_skinny_bench_problems_against_oracle(i, j, hpne):
+    from types import SimpleNamespace
+
+    m, n = 65536, 1024
+    kap, rho = C1_KAPPAS[i], C1_RHOS[j]
+    seed = P.seed_for(1, 3 * i + j)
+    A, b, x_star, sigma, V = P.make_problem_torch(m, n, kap, rho, seed)
+    kw = dict(kind=O.SPARSE_SIGN, s=4 * n, zeta=8, seed=seed, sketch_prec=O.BF16, qr_prec=O.FP32, refine_steps=1)
+    opts = lsq.make_opts(**kw)
+    x, info = lsq.solve(A, b, hpne=hpne, opts=opts)
+    assert int(to_np(info)[0]) == 0
+    A_np, b_np = to_np(A), to_np(b)
+    ref = O.solve(A_np, b_np, hpne=hpne, **kw)
+    assert ref["info"] == 0
+    more = oracle_realizations(SimpleNamespace(A=A_np, b=b_np), hpne=hpne, **kw)
+    assert_solution_parity(to_np(x), ref["x"], to_np(x_star), kap, rho, f"kappa={kap} rho={rho}", refined=True,
+                           u_p=O.BF16, realizations=more)

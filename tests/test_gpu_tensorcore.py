@@ -15,6 +15,7 @@ pytestmark = pytest.mark.gpu
 
 lsq = pytest.importorskip("paper_2603_16644_gb300")
 U32 = 2.0 ** -24
+U64 = 2.0 ** -53
 
 
 def set_tc(on):
@@ -116,3 +117,76 @@ def test_integer_operands_accumulate_exactly(prec, lim, K, M, N):
     exact = (Xi.astype(np.int64) @ Yi.T.astype(np.int64)).astype(np.float64)
     assert np.abs(exact).max() < 2 ** 24
     np.testing.assert_array_equal(Cg, exact)
+
+
+def _sketch_both_ways(A, prec, s, seed, fp64):
+    """Sketch on the tensor cores (default) and on the CUDA cores (switched off)."""
+    opts = lsq.make_opts(kind=lsq.GAUSSIAN, s=s, seed=seed, sketch_prec=prec)
+    Ad = dev_colmajor(A)
+    As_tc, ce, info = lsq.sketch(Ad, opts)
+    assert int(to_np(info)[0]) == 0
+    As_tc = to_np(As_tc).astype(np.float64)
+    prev = lsq.set_fp64_emulation(False) if fp64 else set_tc(False)
+    try:
+        As_cc, _, _ = lsq.sketch(Ad, opts)
+    finally:
+        if fp64:
+            lsq.set_fp64_emulation(prev)
+        else:
+            set_tc(prev)
+    return As_tc, to_np(As_cc).astype(np.float64), to_np(ce)
+
+
+@pytest.mark.parametrize("m,n,s", [(1037, 113, 250), (20011, 70, 200), (300, 129, 130), (5000, 200, 300)])
+def test_fp32_gaussian_sketch_bf16_pieces(m, n, s):
+    # FP32 sketch as six BF16 piece products on the tensor cores: against the
+    # oracle's sequential FP32 sum (worst-case bound) and, in norm, no less
+    # accurate than the oracle or the CUDA-core FP32 GEMM against the FP64
+    # product of the same FP32-rounded operands
+    rng = np.random.default_rng(m + 7 * n)
+    A = np.asfortranarray(rng.standard_normal((m, n)) * np.exp2(rng.integers(-6, 6, n))[None, :])
+    As_tc, As_cc, ce = _sketch_both_ways(A, lsq.FP32, s, 23, False)
+    oAs, oce = O.sketch(A, O.GAUSSIAN, s, 0, 23, O.FP32)
+    np.testing.assert_array_equal(ce, oce)
+    Om = O.gaussian_operator(23, s, m, O.FP32)
+    Ah = O.quantize(A, O.FP32, oce)
+    exact = Om @ Ah  # FP64 product of FP32 values: error ~1e-16, far below FP32
+    scale = np.abs(Om) @ np.abs(Ah)
+    tol = 3 * m * U32 * scale
+    assert np.all(np.abs(As_tc - oAs) <= tol)
+    e_tc = np.linalg.norm(As_tc - exact)
+    e_or = np.linalg.norm(oAs - exact)
+    e_cc = np.linalg.norm(As_cc - exact)
+    assert e_tc <= 2 * max(e_or, e_cc), (e_tc, e_or, e_cc)
+
+
+@pytest.mark.parametrize("m,n,s", [(1037, 113, 250), (3001, 70, 200), (700, 129, 130)])
+def test_fp64_gaussian_sketch_digit_sliced(m, n, s):
+    # FP64 sketch as K chunks of 512 FP64-accurate digit-sliced products:
+    # elementwise against the oracle's sequential FP64 sum within both error
+    # bounds, and against the exact rational value on sampled entries
+    from fractions import Fraction
+
+    rng = np.random.default_rng(m + 3 * n)
+    A = np.asfortranarray(rng.standard_normal((m, n)) * np.exp2(rng.integers(-20, 20, n))[None, :])
+    As_tc, As_cc, ce = _sketch_both_ways(A, lsq.FP64, s, 29, True)
+    oAs, _ = O.sketch(A, O.GAUSSIAN, s, 0, 29, O.FP64)
+    Om = O.gaussian_operator(29, s, m, O.FP64)
+    # per chunk: digit error below 512 2^-50.6 max|Omega_i,chunk| max|A_chunk,c|
+    # and two FP64 roundings of the running sum; the oracle: gamma_m sum|terms|
+    chunks = [slice(k, min(k + 512, m)) for k in range(0, m, 512)]
+    dig = sum(512 * 2.0 ** -50.6 * np.outer(np.abs(Om[:, c]).max(axis=1), np.abs(A[c, :]).max(axis=0))
+              for c in chunks)
+    scale = np.abs(Om) @ np.abs(A)
+    gamma = m * U64 / (1 - m * U64)
+    tol = dig + 2 * gamma * scale
+    assert np.all(np.abs(As_tc - oAs) <= tol)
+    # the CUDA-core FP64 GEMM on the same operator, same bound
+    assert np.all(np.abs(As_tc - As_cc) <= tol)
+    e_tc, e_or = [], []
+    for (i, c) in [(0, 0), (s - 1, n - 1), (s // 2, n // 3), (7, n - 1), (s - 1, 0), (s // 3, 5)]:
+        ex = sum((Fraction(float(a)) * Fraction(float(b)) for a, b in zip(Om[i, :], A[:, c])), Fraction(0))
+        e_tc.append(abs(As_tc[i, c] - float(ex)))
+        e_or.append(abs(oAs[i, c] - float(ex)))
+        assert e_tc[-1] <= tol[i, c]
+    assert np.sqrt(np.mean(np.square(e_tc))) <= 4 * np.sqrt(np.mean(np.square(e_or))) + 4 * U64 * np.abs(oAs).max()
