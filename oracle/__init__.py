@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 FP8_E4M3, BF16, FP16, FP32, FP64, AUTO, AUTO_SKETCH = 0, 1, 2, 3, 4, 5, 6
-GAUSSIAN, SPARSE_SIGN = 0, 1
+GAUSSIAN, SPARSE_SIGN, SRFT = 0, 1, 2
 PREC_NAMES = {FP8_E4M3: "fp8_e4m3", BF16: "bf16", FP16: "fp16", FP32: "fp32", FP64: "fp64", AUTO: "auto",
               AUTO_SKETCH: "auto_sketch"}
 
@@ -36,6 +36,10 @@ def lib():
         L = C.CDLL(path)
         sig = {
             "lsqo_set_threads": (C.c_int, [C.c_int]),
+            "lsqo_srft_order": (_i64, [_i64]),
+            "lsqo_srft_sign": (C.c_int, [C.c_uint64, _i64]),
+            "lsqo_srft_row": (_i64, [C.c_uint64, _i64, _i64]),
+            "lsqo_fwht": (None, [_d, _i64]),
             "lsqo_round": (C.c_double, [C.c_double, C.c_int]),
             "lsqo_round_array": (None, [_d, _i64, C.c_int, _d]),
             "lsqo_philox4x32_10": (None, [_u32, _u32, _u32]),
@@ -308,6 +312,22 @@ def kappa1_upper32(R):
     """||R||_1 times Hager's FP32 estimate of ||R^{-1}||_1 for upper triangular R."""
     R = _f64(R)
     return float(lib().lsqo_kappa1_upper32(_p(R), R.shape[0], R.shape[0]))
+
+
+def srft_operator(seed, m, s):
+    """(signs (m,), sampled rows (s,), m') of the SRFT sketch S F D."""
+    L = lib()
+    mp = int(L.lsqo_srft_order(m))
+    sg = np.array([L.lsqo_srft_sign(C.c_uint64(seed), j) for j in range(m)], dtype=np.int8)
+    rows = np.array([L.lsqo_srft_row(C.c_uint64(seed), t, mp) for t in range(s)], dtype=np.int64)
+    return sg, rows, mp
+
+
+def fwht(x):
+    """The oracle's Walsh-Hadamard butterflies (FP64) on a copy of x (length a power of two)."""
+    y = np.array(x, dtype=np.float64)
+    lib().lsqo_fwht(_p(y), len(y))
+    return y
 
 
 def lu_tall_u(As, prec=FP64):

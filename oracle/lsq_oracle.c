@@ -27,7 +27,8 @@
  * Precision codes: 0 FP8-e4m3 (OCP "fn", saturating), 1 BF16, 2 FP16,
  * 3 FP32, 4 FP64, 5 AUTO (choose by the condition estimate of A^T A),
  * 6 AUTO_SKETCH (choose by the condition estimate on a sketch).
- * Sketch kinds: 0 Gaussian, 1 sparse sign.
+ * Sketch kinds: 0 Gaussian, 1 sparse sign, 2 subsampled randomized
+ * Walsh-Hadamard transform (the paper's S F D of Eq. e_sketch).
  *
  * Pins (checked by the CPU-only tests against the mathematics, never
  * against the CUDA path): rounding exhaustively against the IEEE/OCP format
@@ -51,7 +52,7 @@
 #endif
 
 enum { O_FP8 = 0, O_BF16 = 1, O_FP16 = 2, O_FP32 = 3, O_FP64 = 4, O_AUTO = 5, O_AUTO_SKETCH = 6 };
-enum { O_GAUSSIAN = 0, O_SPARSE_SIGN = 1 };
+enum { O_GAUSSIAN = 0, O_SPARSE_SIGN = 1, O_SRFT = 2 };
 
 #define IDX(i, j, ld) ((size_t)(i) + (size_t)(j) * (size_t)(ld))
 
@@ -207,6 +208,68 @@ void lsqo_gaussian_operator(uint64_t seed, int64_t s, int64_t m, int prec, doubl
 }
 
 /* ------------------------------------------------------------------------
+ * Subsampled randomized trigonometric transform, Omega = S F D (Eq. e_sketch,
+ * Sec. 6.2), with F the real Sylvester-Walsh-Hadamard transform of order
+ * m' = the smallest power of two >= m (A padded with zero rows), unscaled
+ * entries +-1:
+ *   D: sign of row j < m from the Philox stream key = seed, counter
+ *      (j >> 7, 0, 0, 3): bit (j & 31) of word (j >> 5) & 3, set = -1;
+ *   F: (F x)_r = sum_j (-1)^popcount(r & j) x_j, evaluated by the butterfly
+ *      levels h = 1, 2, 4, ..., m'/2 in that order, (a, b) -> (a + b, a - b)
+ *      on the pairs (i, i + h) with i & h = 0;
+ *   S: d rows of I_{m'} sampled uniformly WITH replacement: row of sample t
+ *      = word (t & 3) of counter (t >> 2, 0, 0, 4), masked to [0, m').
+ * ---------------------------------------------------------------------- */
+int64_t lsqo_srft_order(int64_t m)
+{
+    int64_t mp = 1;
+    while (mp < m) mp <<= 1;
+    return mp;
+}
+
+int lsqo_srft_sign(uint64_t seed, int64_t j)
+{
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t ctr[4] = { (uint32_t)((uint64_t)j >> 7), 0u, 0u, 3u };
+    uint32_t w[4];
+    lsqo_philox4x32_10(ctr, key, w);
+    return ((w[(j >> 5) & 3] >> (j & 31)) & 1u) ? -1 : 1;
+}
+
+int64_t lsqo_srft_row(uint64_t seed, int64_t t, int64_t mp)
+{
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t ctr[4] = { (uint32_t)((uint64_t)t >> 2), 0u, 0u, 4u };
+    uint32_t w[4];
+    lsqo_philox4x32_10(ctr, key, w);
+    return (int64_t)(w[t & 3] & (uint32_t)(mp - 1));
+}
+
+/* In-place Walsh-Hadamard transform of length mp (a power of two), FP64 and
+ * FP32 arithmetic. */
+void lsqo_fwht(double* x, int64_t mp)
+{
+    for (int64_t h = 1; h < mp; h <<= 1)
+        for (int64_t i = 0; i < mp; ++i)
+            if (!(i & h)) {
+                double a = x[i], b = x[i + h];
+                x[i] = a + b;
+                x[i + h] = a - b;
+            }
+}
+
+static void fwht32(float* x, int64_t mp)
+{
+    for (int64_t h = 1; h < mp; h <<= 1)
+        for (int64_t i = 0; i < mp; ++i)
+            if (!(i & h)) {
+                float a = x[i], b = x[i + h];
+                x[i] = a + b;
+                x[i + h] = a - b;
+            }
+}
+
+/* ------------------------------------------------------------------------
  * Per-column power-of-two scaling before rounding A to the sketch precision
  * u_p (Alg. 1 computes the sketch in u_p).  Column j is multiplied by
  * 2^e_j so that max_i |a_ij| * 2^e_j lies in [2^(t-1), 2^t) with t = 8 for
@@ -308,6 +371,31 @@ int lsqo_sketch(const double* A, int64_t m, int64_t n, int64_t lda, int kind, in
             }
             free(om);
         }
+    } else if (kind == O_SRFT) {
+        /* Column c of A_s: (F D Ahat[:, c])[rows], the transform in FP32
+         * arithmetic (FP64 when prec = FP64) */
+        int64_t mp = lsqo_srft_order(m);
+        int64_t* rows = (int64_t*)malloc(sizeof(int64_t) * (size_t)s);
+        int* sg = (int*)malloc(sizeof(int) * (size_t)m);
+        for (int64_t t = 0; t < s; ++t) rows[t] = lsqo_srft_row(seed, t, mp);
+        for (int64_t j = 0; j < m; ++j) sg[j] = lsqo_srft_sign(seed, j);
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t c = 0; c < n; ++c) {
+            if (prec == O_FP64) {
+                double* v = (double*)calloc((size_t)mp, sizeof(double));
+                for (int64_t j = 0; j < m; ++j) v[j] = (double)sg[j] * Ahat[IDX(j, c, m)];
+                lsqo_fwht(v, mp);
+                for (int64_t t = 0; t < s; ++t) As[IDX(t, c, s)] = v[rows[t]];
+                free(v);
+            } else {
+                float* v = (float*)calloc((size_t)mp, sizeof(float));
+                for (int64_t j = 0; j < m; ++j) v[j] = (float)((double)sg[j] * Ahat[IDX(j, c, m)]);
+                fwht32(v, mp);
+                for (int64_t t = 0; t < s; ++t) As[IDX(t, c, s)] = (double)v[rows[t]];
+                free(v);
+            }
+        }
+        free(rows); free(sg);
     } else {
         rc = -1;
     }
