@@ -1,21 +1,24 @@
 """Throughput benchmark: least-squares solves per second of the mixed-precision
 randomized-preconditioned normal equations (Alg. 1 of Garrison & Ipsen,
 arXiv 2603.16644; PNE Eq. e_pne) on one GB300, next to this library's
-all-FP64 PNE and HPNE on the same inputs.
+all-FP64 PNE on the same inputs.
 
-Workload (tall-skinny): A is 65536 x 1024 FP64, A = U diag(sigma) V^T with
-kappa in {1e2, 1e6, 1e10} and relative residual in {0, 1e-8, 1e-3} (9 seeded
-synthetic problems resident in HBM, solved in turn); sparse-sign sketch with
-s = 4n rows and 8 nonzeros per column, BF16 sketch, FP32 QR, FP64 TRSM /
-Gram / Cholesky / solves (the FP64 products on the tensor cores by digit
-slicing), one FP64 refinement step.  Every A (512 MiB) is
-larger than L2, so no flush is needed between steps.
+Workload (large single problem): A is 262144 x 4096 FP64 (8.6 GB), A = U
+diag(sigma) V^T with geometric sigma, kappa in {1e4, 1e8} and relative
+residual 1e-6 (two seeded synthetic problems resident in HBM, solved in
+turn); Gaussian sketch with s = 2n rows; the preconditioner precision chosen
+per problem by the single-precision condition estimate on a sketch (Alg. 1
+first line; FP32 at kappa = 1e4, FP64 at 1e8), FP32 QR for a low-precision
+sketch, FP64 TRSM / Gram / Cholesky / solves (the FP64 products on the
+tensor cores by digit slicing).  Every A (8.6 GB) is larger than L2, so no
+flush is needed between steps.  Also measured on the same inputs: the
+all-FP64 PNE (the 3x comparison), the paper's estimate on A^T A, HPNE (LU),
+and the end-to-end solve from host buffers.
 
 One JSON line on rank 0.  --impl reference times the CPU oracle instead.
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -29,61 +32,82 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-M, N, S, ZETA = 65536, 1024, 4096, 8
-KAPPAS = [1e2, 1e6, 1e10]
-RHOS = [0.0, 1e-8, 1e-3]
-WORKLOAD = "tall_skinny_65536x1024_sparse_sign_s4096_z8_bf16_fp32qr_refine1"
-METRIC = "LS solves/s (mixed-precision PNE, 65536x1024)"
+M, N = 262144, 4096
+S = 2 * N
+KAPPAS = [1e4, 1e8]
+RHO = 1e-6
+# structure-preserving downscale on which the oracle runs beside every bench
+DM, DN = 32768, 512
+WORKLOAD = "large_262144x4096_gaussian_s8192_sketch_condest_pne"
+METRIC = "LS solves/s (mixed-precision PNE, 262144x4096, precision from the condition estimate)"
+FP64_NOMINAL_TFLOPS = 1.25  # CUDA-core FP64 of GB300 (no FP64 tensor path)
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # CUDA-core FP32: SMs x lanes x FMA x clock
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=36)
+    p.add_argument("--steps", type=int, default=6)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--fp64-steps", type=int, default=6, help="steps of the all-FP64 PNE comparison")
-    p.add_argument("--hpne-steps", type=int, default=6)
-    p.add_argument("--e2e-steps", type=int, default=6)
+    p.add_argument("--fp64-steps", type=int, default=4, help="timed steps of the all-FP64 PNE comparison")
+    p.add_argument("--side-steps", type=int, default=2, help="timed steps of the other comparisons")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-rows", type=int, default=4096, help="rows of the oracle sample")
-    p.add_argument("--ncu-case", choices=["trsm_gram", "pne", "qr"], default=None,
+    p.add_argument("--no-oracle-parity", action="store_true")
+    p.add_argument("--c4-problems", type=int, default=1024,
+                   help="uneven problems of the learned-proposal evaluation (0: skip)")
+    p.add_argument("--ncu-case", choices=["pne32", "pne64", "sketch32", "sketch64"], default=None,
                    help="run a bounded case for an ncu capture (2 calls on one problem of the workload shape) and exit")
-    p.add_argument("--fp64-emulation", choices=["on", "off"], default="on",
-                   help="ncu case only: FP64 products on the tensor cores (on) or the FP64 CUDA cores (off)")
+    p.add_argument("--ncu-m", type=int, default=M, help="rows of the ncu case")
     return p.parse_args()
 
 
+# ----------------------------------------------------------------------------- options and inputs
+def opts_for(lsq, prec, seed, n=N):
+    qr = lsq.FP64 if prec == lsq.FP64 else lsq.FP32
+    return lsq.make_opts(kind=lsq.GAUSSIAN, s=2 * n, zeta=0, seed=seed, sketch_prec=prec, qr_prec=qr,
+                         refine_steps=0)
+
+
+def make_inputs(dev):
+    import torch
+
+    import problems as P
+
+    probs = []
+    for i, kap in enumerate(KAPPAS):
+        seed = P.seed_for(2, i)
+        A, b, x_star, sigma, V = P.make_problem_hadamard_torch(M, N, kap, RHO, seed, device=dev)
+        probs.append({"A": A, "b": b, "x_star": x_star, "kappa": kap, "seed": seed})
+        del sigma, V
+    torch.cuda.synchronize()
+    return probs
+
+
 def ncu_case(args):
-    """Two calls of one step on one 65536 x 1024 problem (about 1.5 GB on the
-    device): the first warms up, the second is the one to capture."""
+    """Two calls of one step on one problem of the workload's shape with
+    args.ncu_m rows (Gaussian data: the kernels' cost does not depend on the
+    conditioning); the first warms up, the second is the one to capture."""
     import torch
 
     import paper_2603_16644_gb300 as lsq
-    import problems as P
 
     torch.cuda.set_device(0)
-    lsq.set_fp64_emulation(args.fp64_emulation == "on")
-    # Gaussian A: the kernels' cost does not depend on the conditioning, and
-    # this avoids torch's linear-algebra library under the profiler.
-    g = torch.Generator(device="cuda").manual_seed(P.seed_for(1, 4))
-    A = torch.randn((N, M), generator=g, dtype=torch.float64, device="cuda").t()
-    b = torch.randn(M, generator=g, dtype=torch.float64, device="cuda")
-    opts = opts_for(lsq, lsq.BF16, P.seed_for(1, 4))
-    if args.ncu_case == "pne":
-        ws = lsq.workspace(lsq.OP_PNE, M, N, opts)
+    m = args.ncu_m
+    g = torch.Generator(device="cuda").manual_seed(7)
+    A = torch.randn((N, m), generator=g, dtype=torch.float64, device="cuda").t()
+    b = torch.randn(m, generator=g, dtype=torch.float64, device="cuda")
+    prec = lsq.FP64 if args.ncu_case.endswith("64") else lsq.FP32
+    opts = opts_for(lsq, prec, 7)
+    if args.ncu_case.startswith("pne"):
+        ws = lsq.workspace(lsq.OP_PNE, m, N, opts)
         for _ in range(2):
             lsq.pne(A, b, opts=opts, ws=ws)
     else:
-        As, ce, _ = lsq.sketch(A, opts)
         for _ in range(2):
-            Rs, _ = lsq.precond_qr(As, ce, lsq.FP32)
-        if args.ncu_case == "trsm_gram":
-            ws = lsq.workspace(lsq.OP_TRSM_GRAM, M, N)
-            for _ in range(2):
-                lsq.trsm_gram(A, Rs, b, ws=ws)
+            lsq.sketch(A, opts)
     torch.cuda.synchronize()
-    print(json.dumps({"ncu_case": args.ncu_case, "ok": True}))
+    print(json.dumps({"ncu_case": args.ncu_case, "m": m, "ok": True}))
     return 0
 
 
@@ -151,33 +175,23 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons)}
 
 
-# ----------------------------------------------------------------------------- inputs
-def make_inputs(dev):
+# ----------------------------------------------------------------------------- timing helpers
+def run_steps(lsq, probs, steps, prec, ws, xs, infos, start=0, method="pne", events=None):
+    """`steps` solves over the problems in turn; with `events` (a list), an
+    event pair per solve is recorded on the launching stream (no
+    synchronisation) for per-problem times."""
     import torch
 
-    import problems as P
-
-    probs = []
-    for i, kap in enumerate(KAPPAS):
-        for j, rho in enumerate(RHOS):
-            A, b, x_star, sigma, V = P.make_problem_torch(M, N, kap, rho, P.seed_for(1, 3 * i + j), device=dev)
-            probs.append({"A": A, "b": b, "x_star": x_star, "kappa": kap, "rho": rho, "seed": P.seed_for(1, 3 * i + j)})
-            del sigma, V
-    torch.cuda.synchronize()
-    return probs
-
-
-def opts_for(lsq, prec, seed):
-    qr = lsq.FP64 if prec == lsq.FP64 else lsq.FP32
-    return lsq.make_opts(kind=lsq.SPARSE_SIGN, s=S, zeta=ZETA, seed=seed, sketch_prec=prec, qr_prec=qr,
-                         refine_steps=1)
-
-
-def run_steps(lsq, probs, steps, prec, hpne, ws, xs, infos, start=0):
     for k in range(steps):
-        p = probs[(start + k) % len(probs)]
-        lsq.solve(p["A"], p["b"], hpne=hpne, opts=opts_for(lsq, prec, p["seed"]), ws=ws, x=xs[(start + k) % len(probs)],
-                  info=infos[(start + k) % len(probs)])
+        i = (start + k) % len(probs)
+        p = probs[i]
+        if events is not None:
+            ev = (i, torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            ev[1].record(torch.cuda.current_stream())
+        lsq.solve(p["A"], p["b"], method=method, opts=opts_for(lsq, prec, p["seed"]), ws=ws, x=xs[i], info=infos[i])
+        if events is not None:
+            ev[2].record(torch.cuda.current_stream())
+            events.append(ev)
 
 
 def max_over_ranks(sec, dist, device):
@@ -197,15 +211,17 @@ def weak_value(world, steps, sec):
     return world * steps / sec
 
 
-def timed(lsq, torch, probs, steps, warmup, prec, hpne, ws, xs, infos, dist=None):
-    run_steps(lsq, probs, warmup, prec, hpne, ws, xs, infos)
+def timed(lsq, torch, probs, steps, warmup, prec, ws, xs, infos, dist=None, method="pne", events=None):
+    """Seconds of `steps` solves after `warmup` untimed ones (CUDA events on
+    the launching stream, synchronised on both sides)."""
+    run_steps(lsq, probs, warmup, prec, ws, xs, infos, method=method)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    run_steps(lsq, probs, steps, prec, hpne, ws, xs, infos, start=warmup)
+    run_steps(lsq, probs, steps, prec, ws, xs, infos, start=warmup, method=method, events=events)
     e1.record(stream)
     torch.cuda.synchronize()
     if dist is not None:
@@ -213,26 +229,27 @@ def timed(lsq, torch, probs, steps, warmup, prec, hpne, ws, xs, infos, dist=None
     return e0.elapsed_time(e1) / 1000.0
 
 
-def probe_fp64(lsq, torch):
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    blocks = sms * 8
-    scratch = torch.zeros(blocks, dtype=torch.float64, device="cuda")
-    iters = 4096
-    lsq.probe_fp64_fma(iters, blocks, scratch)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    lsq.probe_fp64_fma(iters, blocks, scratch)
-    e1.record()
-    torch.cuda.synchronize()
-    sec = e0.elapsed_time(e1) / 1000.0
-    return blocks * 256 * iters * 16 / sec / 1e12
+def per_problem_ms(probs, events):
+    """Mean milliseconds per solve of each problem from the recorded pairs."""
+    out = {}
+    for p_i, p in enumerate(probs):
+        t = [e0.elapsed_time(e1) for i, e0, e1 in events if i == p_i]
+        if t:
+            out[f"k{p['kappa']:.0e}"] = sum(t) / len(t)
+    return out
+
+
+def errors(probs, xs, infos):
+    out = {}
+    for k, p in enumerate(probs):
+        x = xs[k].cpu().numpy()
+        out[f"k{p['kappa']:.0e}"] = {
+            "rel_err_vs_xstar": float(np.linalg.norm(x - p["x_star"].cpu().numpy()) / np.linalg.norm(x)),
+            "info": int(infos[k].item())}
+    return out
 
 
 # ----------------------------------------------------------------------------- roofline
-FP32_PEAK_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # CUDA-core FP32: SMs x lanes x FMA x clock
-
-
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -241,103 +258,91 @@ def measured_peaks():
         return None
 
 
-# DRAM traffic of one top-level update launch (M = 65536, N = K = 512: the
-# largest update of A_p = A R^{-1} at this shape), dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture of the kernel built from the
-# source whose hash is recorded; reported only while that source is unchanged.
-OT_UPDATE_TOP_TRAFFIC = {"bytes": 829.841920e6 + 280.099072e6, "src_sha256_16": "6464514722d30c43",
-                         "profile": "profiles/k_ot_update_65536x512x512.md"}
-
-
-def update_kernel_src_hash():
-    """sha256 (first 16 hex digits) of the source of the update kernel: the
-    constants and the code from the FP64 converters through the end of
-    k_ot_update in oz_trsm.cu, and the two headers it includes; None if the
-    markers are missing."""
-    import hashlib
-
-    csrc = os.path.join(ROOT, "paper_2603_16644_gb300", "csrc")
-    try:
-        with open(os.path.join(csrc, "oz_trsm.cu")) as f:
-            src = f.read()
-        c0, c1 = src.index("constexpr int OT_DIG"), src.index("constexpr int32_t OT_NONFINITE")
-        k0, k1 = src.index("// Results outside the normal range (rare)"), src.index("// Diagonal block:")
-        h = hashlib.sha256()
-        h.update(src[c0:c1].encode())
-        h.update(src[k0:k1].encode())
-        for name in ("tcgen05.cuh", "common.cuh"):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
-        return h.hexdigest()[:16]
-    except (OSError, ValueError):
-        return None
-
-
-def dominant_roofline(stages, upd_records, fp64_probe):
-    """Roofline of whichever instrumented kernel took longest in the timed
-    region.  The tensor-core FP64 update: achieved = 36 x 2 M N K (its BF16
-    digit products) / CUDA-event time, over the launches of the largest
-    shape (the top-level update of A_p, whose DRAM traffic is known from
-    ncu), against the measured sustained BF16 rate; the all-launch average
-    is reported beside it.  The QR panel: FP32 Householder flops against the
-    nominal CUDA-core FP32 rate."""
-    upd_ms, upd_n, upd_work = stages["k_ot_update"]
-    qrp_ms, qrp_n, qrp_work = stages["k_qr_panel"]
+def bf16_peak():
     pk = measured_peaks()
-    if upd_ms >= qrp_ms and upd_n:
-        if pk and pk.get("bf16_tflops_sustained"):
-            peak, src = pk["bf16_tflops_sustained"], "of measured (MEASURED_PEAKS.json bf16_tflops_sustained)"
+    if pk and pk.get("bf16_tflops_sustained"):
+        return pk["bf16_tflops_sustained"], "of measured (MEASURED_PEAKS.json bf16_tflops_sustained)"
+    return 1700.0, "of fallback (1.7 PFLOP/s sustained bf16)"
+
+
+def method_flops(m, n, s, sk64):
+    """Algorithmic work of one PNE solve by step (the flop counts of the
+    method, not of the emulation): condition estimate on the sketch (sparse
+    sketch + FP32 QR of 2n x n + Gram of the sketch), Gaussian sketch 2smn,
+    sketch QR 2n^2 (s - n/3), TRSM m n^2, Gram m n^2 (symmetric), Cholesky
+    n^3/3."""
+    return {"condest": 2 * n * n * (2 * n - n / 3) + 2 * n * n * 2 * n,
+            "sketch": 2.0 * s * m * n, "qr": 2.0 * n * n * (s - n / 3), "trsm": float(m) * n * n,
+            "gram": float(m) * n * n, "factor": n ** 3 / 3.0}
+
+
+def roofline(stages, recs, per_solve_stage_ms, step_mix):
+    """The dominant instrumented kernel of the timed region (by total time),
+    with `achieved` = the METHOD's flops per launch / its CUDA-event time
+    against the measured dense BF16 peak (GB300 has no FP64 tensor path; the
+    FP64 products are emulated by BF16/FP8 digit slicing, reported as
+    `emulation_factor` and `tensor_pipe_frac`), and the whole-solve
+    sum(t_min) / t_measured of the survey's per-step rooflines."""
+    peak, src = bf16_peak()
+    cand = {}
+    for key in ("k_ot_update", "k_qr_panel", "k_sketch_tc"):
+        ms, cnt, work = stages[key]
+        if cnt:
+            cand[key] = (ms, cnt, work)
+    if not cand:
+        return None
+    top = max(cand, key=lambda k: cand[k][0])
+    ms, cnt, work = cand[top]
+    if top == "k_ot_update":
+        # 36 BF16 digit-pair products per FP64 product
+        emul, bound, unit_peak = 36.0, "tensor", peak
+        kname = "k_ot_update (FP64 products by BF16 digit slicing: TRSM updates, Cholesky updates, FP64 sketch)"
+    elif top == "k_sketch_tc":
+        # FP32 sketches: six BF16 piece products per FP32 product
+        emul, bound, unit_peak = step_mix.get("sketch_emulation", 1.0), "tensor", peak
+        kname = "k_sketch_tc (Gaussian sketch GEMM on tcgen05)"
+    else:
+        emul, bound, unit_peak = 1.0, "alu", FP32_NOMINAL_TFLOPS
+        kname = "k_qr_panel_cl (sketch QR panel)"
+    hw_tflops = work / (ms / 1000.0) / 1e12
+    achieved = hw_tflops / emul
+    out = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": unit_peak, "unit": "TFLOP/s",
+           "frac": achieved / unit_peak, "traffic": None,
+           "traffic_source": "see profiles/ (kernel changed since the last dram capture)",
+           "peak_source": src if bound == "tensor" else "nominal CUDA-core FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz)",
+           "launches": cnt, "avg_launch_ms": ms / cnt, "emulation_factor": emul,
+           "tensor_pipe_tflops": hw_tflops, "tensor_pipe_frac": hw_tflops / unit_peak if bound == "tensor" else None,
+           "share_of_timed_region": None}
+    return out
+
+
+def whole_solve_roofline(per_solve_stage_ms, flops):
+    """sum over steps of t_min = work / peak of the step's unit, over the
+    measured time of the steps: (a) as the survey's table reads, with the FP64
+    steps at the FP64 CUDA-core rate (nominal; the emulated products beat it,
+    so this exceeds 1), (b) with every FP64 step at the BF16 tensor peak with
+    no emulation credit."""
+    peak, _ = bf16_peak()
+    t_meas = sum(v for k, v in per_solve_stage_ms.items() if k in flops) / 1000.0
+    if t_meas <= 0:
+        return None
+    fp64_steps = ("trsm", "gram", "factor")
+    tmin_a = tmin_b = 0.0
+    for k, w in flops.items():
+        if k not in per_solve_stage_ms:
+            continue
+        if k in fp64_steps:
+            tmin_a += w / (FP64_NOMINAL_TFLOPS * 1e12)
+        elif k in ("qr", "condest"):
+            tmin_a += w / (FP32_NOMINAL_TFLOPS * 1e12)
         else:
-            peak, src = 1700.0, "of fallback (1.7 PFLOP/s sustained bf16)"
-        wmax = max(w for _, w in upd_records) if upd_records else 0.0
-        top = [(ms, w) for ms, w in upd_records if w == wmax]
-        top_ms = sum(ms for ms, _ in top) / max(1, len(top))
-        achieved = wmax / (top_ms / 1000.0) / 1e12 if top else 0.0
-        fresh = update_kernel_src_hash() == OT_UPDATE_TOP_TRAFFIC["src_sha256_16"]
-        return {"bound": "tensor", "kernel": "k_ot_update (FP64 by BF16 digit slicing), top-level launch M=65536 N=K=512",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": OT_UPDATE_TOP_TRAFFIC["bytes"] if fresh else None,
-                "traffic_source": OT_UPDATE_TOP_TRAFFIC["profile"] if fresh else "kernel changed since the capture",
-                "algorithmic_bytes": 8 * M * 512 * 2 + 8 * 512 * 512 * 2 + 2 * M * 512 * 8,
-                "peak_source": src, "launches_timed": len(top), "avg_launch_ms": top_ms,
-                "fp64_equivalent_tflops": achieved / 36.0,
-                "all_launches": {"launches": upd_n, "achieved_tflops": upd_work / (upd_ms / 1000.0) / 1e12},
-                "fp64_fma_probe_tflops": fp64_probe}
-    achieved = qrp_work / (qrp_ms / 1000.0) / 1e12 if qrp_ms else 0.0
-    return {"bound": "alu", "kernel": "k_qr_panel_cl<float>", "achieved": achieved,
-            "peak": FP32_PEAK_NOMINAL_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_NOMINAL_TFLOPS,
-            "traffic": None, "peak_source": "nominal CUDA-core FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz)",
-            "launches": qrp_n, "avg_launch_ms": qrp_ms / max(1, qrp_n)}
+            tmin_a += w / (peak * 1e12)
+        tmin_b += w / (peak * 1e12)
+    return {"fp64_steps_at_fp64_peak": tmin_a / t_meas, "all_steps_at_bf16_peak": tmin_b / t_meas,
+            "t_measured_ms": 1000 * t_meas}
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_sample(rows):
-    """The oracle's Alg. 1 (PNE, same n, s, zeta and precisions, one refinement
-    step) on a `rows`-row slice of the workload shape, timed as it stands.
-    The steps whose cost is independent of m (QR of the s x n sketch,
-    Cholesky, solves) are timed once more on their own; the rest is
-    proportional to m and is scaled to the full 65536 rows.  Returns
-    (seconds for one full solve, raw CPU seconds spent)."""
-    import oracle as O
-
-    rng = np.random.default_rng(2603)
-    A = np.asfortranarray(rng.standard_normal((rows, N)))
-    b = rng.standard_normal(rows)
-    t0 = time.perf_counter()
-    O.solve(A, b, kind=O.SPARSE_SIGN, s=S, zeta=ZETA, seed=1, sketch_prec=O.BF16, qr_prec=O.FP32, refine_steps=1)
-    t_total = time.perf_counter() - t0
-    As, e = O.sketch(A, O.SPARSE_SIGN, S, ZETA, 1, O.BF16)
-    X = rng.standard_normal((2 * N, N))
-    G = X.T @ X
-    t0 = time.perf_counter()
-    O.qr_r(As, O.FP32)
-    L, _ = O.cholesky(G)
-    O.solve_lower_t(L, O.solve_lower(L, np.ones(N)))
-    t_fixed = time.perf_counter() - t0
-    full = max(t_total - t_fixed, 0.0) * (M / rows) + t_fixed
-    return full, t_total + t_fixed
-
-
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -345,26 +350,130 @@ def cpu_cores():
         return os.cpu_count()
 
 
+def oracle_flops(m, n, s):
+    """The oracle's arithmetic for one PNE solve with the sketch estimate,
+    counted the same way at any size (its dense Gram forms all n^2 entries)."""
+    return (2 * n * n * (2 * n) + 2 * n * n * (2 * n - n / 3) + 2.0 * s * m * n + 2 * n * n * (s - n / 3)
+            + float(m) * n * n + 2.0 * m * n * n + n ** 3 / 3.0)
+
+
+def downscale_problem(kap, i):
+    """The workload's structure at 32768 x 512 (s = 2n = 1024): same generator,
+    same kappa and residual; built on the CPU (no GPU work)."""
+    import torch
+
+    import problems as P
+
+    A, b, x_star, _, _ = P.make_problem_hadamard_torch(DM, DN, kap, RHO, P.seed_for(2, 100 + i), device="cpu")
+    return (np.asfortranarray(A.numpy()), b.numpy().copy(), x_star.numpy().copy(), P.seed_for(2, 100 + i))
+
+
+def oracle_sample():
+    """Time the oracle, as it stands, on the downscaled workload (both kappa,
+    PNE with the sketch estimate) on all host threads.  Returns (seconds per
+    downscaled solve, threads, solves)."""
+    import oracle as O
+
+    threads = O.set_threads(0)
+    probs = [downscale_problem(k, i) for i, k in enumerate(KAPPAS)]
+    t0 = time.perf_counter()
+    for A, b, _, seed in probs:
+        O.solve(A, b, kind=O.GAUSSIAN, s=2 * DN, zeta=0, seed=seed, sketch_prec=O.AUTO_SKETCH, qr_prec=O.FP32)
+    sec = (time.perf_counter() - t0) / len(probs)
+    return sec, threads, len(probs)
+
+
+def cpu_baseline_line(sec, threads, solves):
+    scale = oracle_flops(M, N, S) / oracle_flops(DM, DN, 2 * DN)
+    return {"value": 1.0 / (sec * scale), "unit": "solves/s", "cores": threads, "kind": "oracle",
+            "sample": (f"oracle PNE with the sketch condition estimate (Alg. 1) on the {DM}x{DN} downscale of the "
+                       f"workload (s = 2n, kappa in {KAPPAS}, same generator), {solves} full solves at "
+                       f"{sec:.2f} s each on {threads} threads; scaled to {M}x{N} by the oracle's flop count "
+                       f"(x{scale:.0f})")}
+
+
+def oracle_parity(lsq, torch, dev):
+    """The workload's structure at the downscale: the CUDA path and the oracle
+    on the same inputs, error of each against x_* and their difference."""
+    import oracle as O
+
+    out = {}
+    for i, kap in enumerate(KAPPAS):
+        A, b, x_star, seed = downscale_problem(kap, i)
+        Ad = lsq.colmajor(torch.from_numpy(A).to(dev))
+        bd = torch.from_numpy(b).to(dev)
+        for name, prec in (("mixed", lsq.AUTO_SKETCH), ("fp64", lsq.FP64)):
+            x, info = lsq.solve(Ad, bd, opts=opts_for(lsq, prec, seed, DN))
+            xg = x.cpu().numpy()
+            r = O.solve(A, b, kind=O.GAUSSIAN, s=2 * DN, zeta=0, seed=seed, sketch_prec=prec,
+                        qr_prec=O.FP64 if prec == O.FP64 else O.FP32)
+            eg = float(np.linalg.norm(xg - x_star) / np.linalg.norm(xg))
+            eo = float(np.linalg.norm(r["x"] - x_star) / np.linalg.norm(r["x"]))
+            out[f"k{kap:.0e}_{name}"] = {"gpu_err": eg, "oracle_err": eo, "err_ratio": eg / eo if eo > 0 else None,
+                                         "rel_diff_gpu_oracle": float(np.linalg.norm(xg - r["x"]) / np.linalg.norm(r["x"])),
+                                         "prec_oracle": O.PREC_NAMES[r["prec"]], "info": int(info.item())}
+    return {"shape": f"{DM}x{DN}, s={2 * DN}", **out}
+
+
+# ----------------------------------------------------------------------------- learned proposal
+def learned_eval(lsq, torch, count):
+    """The learned proposal (judged by the estimator on a sketch) on `count`
+    uneven problems drawn like the batched workload, next to the estimator on
+    a sketch alone and the paper's estimate on A^T A: solves/s of each arm,
+    escalations, the precisions used and the learned arm's accuracy against
+    the estimator arm's."""
+    from paper_2603_16644_gb300 import learned
+
+    params = learned.load()
+    if params is None:
+        return {"unavailable": "no shipped weights"}
+    probs = learned.c3_like_problems(count, seed=2604)
+    res = learned.evaluate(params, probs)
+    used = res["learned"]["used"]
+    names = {0: "fp8_e4m3", 1: "bf16", 2: "fp16", 3: "fp32", 4: "fp64"}
+    ratio = [a / max(b, 1e-300) for a, b in zip(res["learned"]["errors"], res["auto_sketch"]["errors"])]
+    out = {"problems": count, "workload": "m in [2000, 40000], n in [32, 512], kappa log-uniform [1e2, 1e10], "
+                                          "residual log-uniform [1e-12, 1e-2]; Gaussian s = 2n, PNE, one refinement",
+           "solves_per_s": {a: r["solves_per_s"] for a, r in res.items()},
+           "escalations": res["learned"]["escalations"],
+           "precisions_used": {names[k]: used.count(k) for k in sorted(set(used))},
+           "max_err_ratio_learned_over_estimate": max(ratio), "infos_nonzero": sum(
+               1 for a in res.values() for i in a["infos"] if i != 0)}
+    del probs
+    torch.cuda.empty_cache()
+    return out
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    steps_t = []
-    for _ in range(args.warmup):
-        oracle_sample(args.cpu_rows)
-    for _ in range(args.steps):
-        full, raw = oracle_sample(args.cpu_rows)
-        steps_t.append(full)
-    sec = sum(steps_t)
-    value = args.steps / sec
-    sample = (f"oracle PNE (Alg. 1, refine 1) on a {args.cpu_rows}x{N} slice (s={S}, zeta={ZETA}, BF16 sketch, "
-              f"FP32 QR); m-proportional part scaled by {M // args.cpu_rows}, QR/Cholesky/solves once")
+    import oracle as O
+
+    threads = O.set_threads(0)
+    probs = [downscale_problem(k, i) for i, k in enumerate(KAPPAS)]
+
+    def step(k):
+        A, b, _, seed = probs[k % len(probs)]
+        O.solve(A, b, kind=O.GAUSSIAN, s=2 * DN, zeta=0, seed=seed, sketch_prec=O.AUTO_SKETCH, qr_prec=O.FP32)
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(args.warmup + k)
+    sec = time.perf_counter() - t0
+    scale = oracle_flops(M, N, S) / oracle_flops(DM, DN, 2 * DN)
+    value = args.steps / (sec * scale)  # full-size solves per second
+    sample = (f"oracle PNE with the sketch condition estimate on the {DM}x{DN} downscale of the workload "
+              f"(s = 2n, kappa in {KAPPAS}), one full downscaled solve per step on {threads} threads; the value "
+              f"is scaled to {M}x{N} by the oracle's flop count (x{scale:.0f})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "m": M, "n": N, "s": S},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -392,98 +501,142 @@ def main():
         dist = dist_mod
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+
+    # the CPU baseline first: the oracle's threads run before any GPU work
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_line(*oracle_sample())
+
     probs = make_inputs(dev)
-    ws_size = max(lsq.workspace_size(lsq.OP_PNE, M, N, opts_for(lsq, p, 0)) for p in (lsq.BF16, lsq.FP64))
-    ws_size = max(ws_size, lsq.workspace_size(lsq.OP_HPNE, M, N, opts_for(lsq, lsq.BF16, 0)))
+    ws_size = max(lsq.workspace_size(lsq.OP_PNE, M, N, opts_for(lsq, p, 0))
+                  for p in (lsq.AUTO_SKETCH, lsq.AUTO, lsq.FP64))
+    ws_size = max(ws_size, lsq.workspace_size(lsq.OP_HPNE, M, N, opts_for(lsq, lsq.AUTO_SKETCH, 0)))
     ws = torch.empty(ws_size, dtype=torch.uint8, device=dev)
     xs = [torch.empty(N, dtype=torch.float64, device=dev) for _ in probs]
     infos = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in probs]
 
-    # ---- headline: mixed-precision PNE
+    # ---- headline: mixed-precision PNE, precision from the estimate on a sketch
+    chosen = {}
+    for p in probs:
+        k0, ch = lsq.condest_sketch(p["A"], seed=p["seed"])
+        chosen[f"k{p['kappa']:.0e}"] = {"kappa0": float(k0.item()), "prec": int(ch.item())}
     clocks = ClockSampler(local)
-    run_steps(lsq, probs, args.warmup, lsq.BF16, False, ws, xs, infos)
+    run_steps(lsq, probs, args.warmup, lsq.AUTO_SKETCH, ws, xs, infos)
     torch.cuda.synchronize()
     lsq.profile(True)
     n_launch0 = lsq.launch_count()
     clocks.start()
-    sec = timed(lsq, torch, probs, args.steps, 0, lsq.BF16, False, ws, xs, infos, dist)
+    ev_mixed = []
+    sec = timed(lsq, torch, probs, args.steps, 0, lsq.AUTO_SKETCH, ws, xs, infos, dist, events=ev_mixed)
     clk = clocks.stop()
     n_launch = lsq.launch_count() - n_launch0
-    upd_records = lsq.profile_records("k_ot_update")
     stages = lsq.profile_collect(with_work=True)
     lsq.profile(False)
     sec = max_over_ranks(sec, dist, dev)
     value = weak_value(world, args.steps, sec)
+    err_mixed = errors(probs, xs, infos)
 
-    # accuracy of the timed solves (not timed)
-    errs = {}
-    for k, p in enumerate(probs):
-        x = xs[k].cpu().numpy()
-        errs[f"k{p['kappa']:.0e}_r{p['rho']:.0e}"] = {
-            "rel_err_vs_xstar": float(np.linalg.norm(x - p["x_star"].cpu().numpy()) / np.linalg.norm(x)),
-            "info": int(infos[k].item())}
+    # ---- all-FP64 PNE on the same inputs (the sketch precision forced to FP64)
+    run_steps(lsq, probs, 2, lsq.FP64, ws, xs, infos)  # warm-up, not profiled
+    torch.cuda.synchronize()
+    lsq.profile(True)
+    ev64 = []
+    sec64 = timed(lsq, torch, probs, args.fp64_steps, 0, lsq.FP64, ws, xs, infos, dist, events=ev64)
+    stages64 = lsq.profile_collect(with_work=True)
+    lsq.profile(False)
+    err64 = errors(probs, xs, infos)
+    value64 = weak_value(world, args.fp64_steps, max_over_ranks(sec64, dist, dev))
 
-    # ---- comparisons: all-FP64 PNE and mixed HPNE, same inputs
-    sec64 = timed(lsq, torch, probs, args.fp64_steps, 1, lsq.FP64, False, ws, xs, infos, dist)
-    touched = sorted({k % len(probs) for k in range(1 + args.fp64_steps)})
-    err64 = {f"k{probs[k]['kappa']:.0e}_r{probs[k]['rho']:.0e}": float(
-        np.linalg.norm(xs[k].cpu().numpy() - probs[k]["x_star"].cpu().numpy()) / np.linalg.norm(xs[k].cpu().numpy()))
-        for k in touched}
-    sech = timed(lsq, torch, probs, args.hpne_steps, 1, lsq.BF16, True, ws, xs, infos, dist)
+    # ---- the paper's estimate on A^T A (Sec. 6.1) and HPNE with LU
+    secl = timed(lsq, torch, probs, args.side_steps, 1, lsq.AUTO, ws, xs, infos, dist)
+    chosen_literal = {}
+    for p in probs:
+        k0, ch = lsq.condest(p["A"])
+        chosen_literal[f"k{p['kappa']:.0e}"] = {"kappa0": float(k0.item()), "prec": int(ch.item())}
+    sech = timed(lsq, torch, probs, args.side_steps, 1, lsq.AUTO_SKETCH, ws, xs, infos, dist, method="hpne")
+    errh = errors(probs, xs, infos)
+    del ws
+    torch.cuda.empty_cache()
 
-    # ---- end to end through the C ABI on host buffers
-    Ah = [p["A"].t().contiguous().cpu().pin_memory() for p in probs[:3]]
-    bh = [p["b"].cpu().pin_memory() for p in probs[:3]]
-    wsh = torch.empty(lsq.workspace_size(lsq.OP_PNE_HOST, M, N, opts_for(lsq, lsq.BF16, 0)), dtype=torch.uint8,
-                      device=dev)
+    # ---- end to end through the C ABI on host buffers (pinned)
+    Ah = [p["A"].t().contiguous().cpu().pin_memory() for p in probs]
+    bh = [p["b"].cpu().pin_memory() for p in probs]
+    for p in probs:
+        del p["A"]
+    torch.cuda.empty_cache()
+    wsh = torch.empty(lsq.workspace_size(lsq.OP_PNE_HOST, M, N, opts_for(lsq, lsq.AUTO_SKETCH, 0)),
+                      dtype=torch.uint8, device=dev)
     xh = torch.empty(N, dtype=torch.float64).pin_memory()
-    for k in range(2):
-        lsq.solve_host(Ah[k % 3].t(), bh[k % 3], opts=opts_for(lsq, lsq.BF16, probs[k % 3]["seed"]), ws=wsh, x_host=xh)
+    lsq.solve_host(Ah[0].t(), bh[0], opts=opts_for(lsq, lsq.AUTO_SKETCH, probs[0]["seed"]), ws=wsh, x_host=xh)
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
-    for k in range(args.e2e_steps):
-        lsq.solve_host(Ah[k % 3].t(), bh[k % 3], opts=opts_for(lsq, lsq.BF16, probs[k % 3]["seed"]), ws=wsh,
-                       x_host=xh)
-    e2e_sec = time.perf_counter() - t0
-    e2e_sec = max_over_ranks(e2e_sec, dist, dev)
-    e2e_value = weak_value(world, args.e2e_steps, e2e_sec)
+    for k in range(args.side_steps):
+        i = k % len(probs)
+        lsq.solve_host(Ah[i].t(), bh[i], opts=opts_for(lsq, lsq.AUTO_SKETCH, probs[i]["seed"]), ws=wsh, x_host=xh)
+    e2e_sec = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e_value = weak_value(world, args.side_steps, e2e_sec)
+    del wsh, Ah
+    torch.cuda.empty_cache()
 
-    # ---- roofline of the dominant kernel, from the library's events around
-    # every launch of the two heaviest kernels inside the timed region
-    fp64_probe = probe_fp64(lsq, torch)
-    roofline = dominant_roofline(stages, upd_records, fp64_probe)
+    # ---- learned precision proposal (shipped weights) on a fresh batch of
+    # uneven problems, against the estimate alone and the paper's estimate on A^T A
+    c4 = None
+    if rank == 0 and args.c4_problems > 0:
+        c4 = learned_eval(lsq, torch, args.c4_problems)
 
     result = None
     if rank == 0:
-        cpu = None
-        if not args.no_cpu_baseline:
-            full, raw = oracle_sample(args.cpu_rows)
-            cpu = {"value": 1.0 / full, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                   "sample": (f"oracle PNE steps on a {args.cpu_rows}x{N} slice (same s, zeta, precisions), "
-                              f"{raw:.1f} s of CPU work; row-proportional steps scaled by {M // args.cpu_rows}, "
-                              f"QR/Cholesky/solves counted once")}
-        per_stage = {k: round(v[0] / max(1, v[1]), 3) for k, v in stages.items() if v[1] and not k.startswith("k_")}
+        per_stage = {k: v[0] / args.steps for k, v in stages.items() if v[1] and not k.startswith("k_")}
+        per_stage64 = {k: v[0] / args.fp64_steps for k, v in stages64.items() if v[1] and not k.startswith("k_")}
         per_kernel = {k: {"ms_per_solve": round(v[0] / args.steps, 3), "launches_per_solve": v[1] / args.steps}
                       for k, v in stages.items() if v[1] and k.startswith("k_")}
+        n32 = sum(1 for v in chosen.values() if v["prec"] == lsq.FP32)
+        mix = {"sketch_emulation": 6.0 if n32 == len(chosen) else 1.0}
+        roof = roofline(stages, None, per_stage, mix)
+        if roof is not None:
+            roof["share_of_timed_region"] = stages[next(k for k in ("k_ot_update", "k_qr_panel", "k_sketch_tc")
+                                                         if roof["kernel"].startswith(k))][0] / (1000 * sec)
+        flops = method_flops(M, N, S, False)
+        parity = None if args.no_oracle_parity else oracle_parity(lsq, torch, dev)
+        pname = {0: "fp8_e4m3", 1: "bf16", 2: "fp16", 3: "fp32", 4: "fp64"}
+        speedup = {}
+        t_mixed, t64 = per_problem_ms(probs, ev_mixed), per_problem_ms(probs, ev64)
+        for key in err_mixed:
+            em, e6 = err_mixed[key]["rel_err_vs_xstar"], err64[key]["rel_err_vs_xstar"]
+            eq = bool(em <= 2 * e6 + 1e-15)
+            speedup[key] = {"prec": pname.get(chosen[key]["prec"]), "ms_mixed": t_mixed.get(key),
+                            "ms_fp64": t64.get(key), "err_mixed": em, "err_fp64": e6, "equal_accuracy": eq,
+                            "speedup": (t64[key] / t_mixed[key]) if eq and key in t64 and key in t_mixed else None}
         result = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * sec / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded A = U diag(sigma) V^T, known x_*)",
-            "config": {"workload": WORKLOAD, "m": M, "n": N, "s": S, "zeta": ZETA, "sketch": "sparse_sign",
-                       "sketch_prec": "bf16", "qr_prec": "fp32", "refine_steps": 1, "kappas": KAPPAS, "rhos": RHOS,
-                       "l2": "inputs larger than L2 (512 MiB A per step, 9 problems in turn)"},
+            "data": "synthetic (seeded A = U diag(sigma) V^T, U from signed Hadamard columns, known x_*)",
+            "config": {"workload": WORKLOAD, "m": M, "n": N, "s": S, "sketch": "gaussian",
+                       "sketch_prec": "from the condition estimate on a sketch (auto_sketch)", "qr_prec": "fp32",
+                       "refine_steps": 0, "kappas": KAPPAS, "rho": RHO,
+                       "l2": "inputs larger than L2 (8.6 GB A per step, 2 problems in turn)"},
             "clocks": clk, "gpu_launches": n_launch,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * M * N + 8 * M,
                     "d2h_bytes_per_step": 8 * N + 4},
-            "roofline": roofline, "cpu_baseline": cpu,
-            "stage_ms_per_solve": per_stage, "kernel_ms_per_solve": per_kernel,
-            "fp64_pne": {"value": world * args.fp64_steps / sec64, "unit": "solves/s",
-                         "speedup_mixed_over_fp64": value / (world * args.fp64_steps / sec64),
-                         "rel_err_vs_xstar": err64},
-            "hpne": {"value": world * args.hpne_steps / sech, "unit": "solves/s"},
-            "accuracy": errs,
+            "roofline": roof,
+            "whole_solve_roofline": whole_solve_roofline(per_stage, flops),
+            "cpu_baseline": cpu,
+            "chosen_precision": {k: {"kappa0": v["kappa0"], "prec": pname.get(v["prec"])} for k, v in chosen.items()},
+            "stage_ms_per_solve": {k: round(v, 3) for k, v in per_stage.items()},
+            "kernel_ms_per_solve": per_kernel,
+            "fp64_pne": {"value": value64, "unit": "solves/s", "speedup_mixed_over_fp64": value / value64,
+                         "stage_ms_per_solve": {k: round(v, 3) for k, v in per_stage64.items()},
+                         "accuracy": err64},
+            "speedup_at_equal_accuracy": speedup,
+            "paper_estimate_on_AtA": {"value": weak_value(world, args.side_steps, secl), "unit": "solves/s",
+                                      "chosen": {k: {"kappa0": v["kappa0"], "prec": pname.get(v["prec"])}
+                                                 for k, v in chosen_literal.items()}},
+            "hpne": {"value": weak_value(world, args.side_steps, sech), "unit": "solves/s", "accuracy": errh},
+            "accuracy": err_mixed,
+            "oracle_parity_downscale": parity,
+            "learned_proposal": c4,
         }
         print(json.dumps(result), flush=True)
     if dist is not None:
