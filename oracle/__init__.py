@@ -46,6 +46,7 @@ def lib():
             "lsqo_sparse_sign_column": (C.c_int, [C.c_uint64, _i64, _i64, C.c_int, _i32, _i8]),
             "lsqo_sparse_sign_indices": (C.c_int, [C.c_uint64, _i64, _i64, C.c_int, _i32, _i8]),
             "lsqo_gaussian_entry": (C.c_double, [C.c_uint64, _i64, _i64]),
+            "lsqo_zig_tables": (None, [_d, _d]),
             "lsqo_gaussian_operator": (None, [C.c_uint64, _i64, _i64, C.c_int, _d]),
             "lsqo_colexp": (None, [_d, _i64, _i64, _i64, C.c_int, _i32]),
             "lsqo_quantize": (None, [_d, _i64, _i64, _i64, C.c_int, _i32, _d]),
@@ -123,6 +124,17 @@ def sparse_sign_indices(seed, m, s, zeta):
 
 def gaussian_entry(seed, i, j):
     return lib().lsqo_gaussian_entry(C.c_uint64(seed), i, j)
+
+
+ZIG_N = 256
+
+
+def zig_tables():
+    """The ziggurat's layer bounds x_0..x_256 and f(x_i) = exp(-x_i^2 / 2)
+    (f(x_0) stored as 0)."""
+    x, f = np.zeros(ZIG_N + 1), np.zeros(ZIG_N + 1)
+    lib().lsqo_zig_tables(_p(x), _p(f))
+    return x, f
 
 
 def gaussian_operator(seed, s, m, prec=FP64):

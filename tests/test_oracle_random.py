@@ -4,8 +4,9 @@ Philox4x32-10 against the published known-answer vectors; the sparse-sign
 operator against its defining invariants (zeta distinct rows per column,
 uniform rows, balanced signs, and the sketch it produces equals the explicit
 dense Omega times A exactly on integer data); the Gaussian operator against
-N(0, 1) (moments and a Kolmogorov-Smirnov test) and its exact entry values
-against Box-Muller evaluated in 50-digit decimal arithmetic.
+N(0, 1) (moments, a Kolmogorov-Smirnov test, the tail mass), its ziggurat
+tables against the closure equation solved afresh in 40-digit arithmetic and
+its entry values against the ziggurat evaluated in 40-digit arithmetic.
 """
 import os
 
@@ -117,79 +118,247 @@ def test_gaussian_sketch_matches_dense_product(prec):
 
 
 # --- exact Gaussian entries, independently of libm ----------------------------
-_PI50 = "3.14159265358979323846264338327950288419716939937510"
+# The ziggurat of Marsaglia & Tsang (2000) with 256 layers of equal area v
+# under f(x) = exp(-x^2 / 2): f(x_{i+1}) = f(x_i) + v / x_i from x_1 = r, the
+# top layer closing at f(0) = 1; v = r f(r) + int_r^inf f.  Everything below
+# is recomputed in 40-digit arithmetic from these definitions alone.
+mpmath = pytest.importorskip("mpmath")
 
 
-def _dec_cos(x, D):
-    """cos(x) for a Decimal x in [0, 2 pi), by reduction to [-pi, pi] and its
-    Taylor series (terms until they fall below 1e-55)."""
-    pi = D(_PI50)
-    if x > pi:
-        x -= 2 * pi
-    x2, term, total, k = x * x, D(1), D(1), 0
-    while abs(term) > D("1e-55"):
-        k += 2
-        term = -term * x2 / (k * (k - 1))
-        total += term
-    return total
+def _f(x):
+    return mpmath.exp(-x * x / 2)
 
 
-def _box_muller_exact(seed, i, j):
-    """Box & Muller (1958), z = sqrt(-2 ln u1) cos(2 pi u2), in 50-digit
-    decimal arithmetic from the uniforms of the Philox stream: counter
-    (i, j_lo, j_hi, 2), u1 = (2^26 (w0 >> 5) + (w1 >> 6) + 1) / 2^53 in (0, 1],
-    u2 = (2^26 (w2 >> 5) + (w3 >> 6)) / 2^53 in [0, 1)."""
-    import decimal
-
-    D = decimal.Decimal
-    ctx = decimal.Context(prec=50)
-    w = [int(v) for v in O.philox4x32_10([i, j & 0xFFFFFFFF, j >> 32, 2], [seed & 0xFFFFFFFF, seed >> 32])]
-    n1 = (w[0] >> 5) * 2**26 + (w[1] >> 6) + 1
-    n2 = (w[2] >> 5) * 2**26 + (w[3] >> 6)
-    with decimal.localcontext(ctx):
-        u1 = D(n1) / D(2**53)
-        u2 = D(n2) / D(2**53)
-        rad = (-2 * u1.ln()).sqrt()
-        return float(rad * _dec_cos(2 * D(_PI50) * u2, D)), float(rad)
+def _v_of(r):
+    return r * _f(r) + mpmath.sqrt(mpmath.pi / 2) * mpmath.erfc(r / mpmath.sqrt(2))
 
 
-def test_gaussian_entries_match_box_muller_in_high_precision():
-    """Pin of the exact Gaussian entry values: sampled entries recomputed with
-    Box-Muller in 50-digit decimal arithmetic (no libm), from the Philox
-    stream pinned above.  The FP64 entry can differ from the exact value only
-    by the errors of log, sqrt, cos and the products, and by the rounded
-    2 pi, a few units of 2^-52 scaled by the radius.  Swapped uniforms, sin for
-    cos or a wrong shift in forming the uniforms give O(1) differences (the
-    +1 that keeps u1 away from 0 moves an entry by less than the FP64 error
-    and is not resolved here)."""
+def _closure(r):
+    """f(x_255) + v / x_255 - 1 for the layers grown from r; +1 when a layer
+    reaches f = 1 early (too few layers: r too small)."""
+    v, x = _v_of(r), r
+    for _ in range(1, 255):
+        t = _f(x) + v / x
+        if t >= 1:
+            return mpmath.mpf(1)
+        x = mpmath.sqrt(-2 * mpmath.log(t))
+    return _f(x) + v / x - 1
+
+
+_EXACT = {}
+
+
+def _exact_tables():
+    if not _EXACT:
+        with mpmath.workdps(40):
+            lo, hi = mpmath.mpf("3.5"), mpmath.mpf("3.8")
+            assert _closure(lo) > 0 > _closure(hi)
+            for _ in range(140):
+                mid = (lo + hi) / 2
+                if _closure(mid) > 0:
+                    lo = mid
+                else:
+                    hi = mid
+            r = (lo + hi) / 2
+            v = _v_of(r)
+            x = [v / _f(r), r]
+            for _ in range(1, 255):
+                x.append(mpmath.sqrt(-2 * mpmath.log(_f(x[-1]) + v / x[-1])))
+            x.append(mpmath.mpf(0))
+            _EXACT.update(r=r, v=v, x=x, f=[mpmath.mpf(0)] + [_f(t) for t in x[1:]])
+    return _EXACT
+
+
+def test_ziggurat_tables_solve_the_closure_equation():
+    E = _exact_tables()
+    x, f = O.zig_tables()
+    assert len(x) == 257 and x[256] == 0.0 and f[256] == 1.0
+    # r: the root of the closure equation, to FP64 accuracy
+    assert abs(x[1] - float(E["r"])) <= 2.0 ** -52 * x[1], (x[1], E["r"])
+    # every bound against the 40-digit recurrence (its FP64 error grows
+    # mildly along the 255 steps)
+    for i in range(256):
+        assert abs(x[i] - float(E["x"][i])) <= 1e-12 * float(E["x"][i]), i
+        if i >= 1:
+            assert abs(f[i] - float(E["f"][i])) <= 1e-12 * float(E["f"][i]), i
+    # equal areas: base rectangle + tail, every layer, the top one closing at 1
+    v = float(E["v"])
+    assert abs(x[0] * f[1] - v) <= 1e-13 * v
+    areas = x[1:256] * (f[2:257] - f[1:256])
+    np.testing.assert_allclose(areas, v, rtol=1e-10)
+    # 256 v = sqrt(pi/2) / 0.9933..: the share of draws accepted at once
+    assert 0.993 < np.sqrt(np.pi / 2) / (256 * v) < 0.994
+
+
+def _zig_exact(seed, i, j):
+    """(value, path) of Omega(i, j) by the ziggurat in 40-digit arithmetic:
+    round k draws the Philox block of counter (i, j_lo, j_hi, 2 + 256 k); a
+    first-kind round reads layer w0 & 255, sign bit 8 of w0,
+    U = (2^30 (w0 >> 9) + (w1 >> 2)) / 2^53 and V = (2^26 (w2 >> 5) + (w3 >> 6)) / 2^53;
+    z = U x_L is kept inside the curve (z < x_{L+1}) or, in layers >= 1, under
+    it in the wedge (f(x_L) + V (f(x_{L+1}) - f(x_L)) < f(z)); layer 0 past r
+    turns to the tail, e1 = -ln(U1) / r, e2 = -ln(U2) with U1, U2 as V plus
+    1 / 2^53, kept when 2 e2 > e1^2, giving r + e1."""
+    E = _exact_tables()
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    tail, neg, path = False, False, []
+    with mpmath.workdps(40):
+        for k in range(64):
+            w = [int(t) for t in O.philox4x32_10([i, j & 0xFFFFFFFF, j >> 32, 2 + 256 * k], key)]
+            if tail:
+                u1 = mpmath.mpf((w[0] >> 5) * 2**26 + (w[1] >> 6) + 1) / 2**53
+                u2 = mpmath.mpf((w[2] >> 5) * 2**26 + (w[3] >> 6) + 1) / 2**53
+                e1, e2 = -mpmath.log(u1) / E["r"], -mpmath.log(u2)
+                if 2 * e2 > e1 * e1:
+                    z = E["r"] + e1
+                    return float(-z if neg else z), path + ["tail"]
+                path.append("tail-reject")
+                continue
+            L, neg = w[0] & 255, bool((w[0] >> 8) & 1)
+            U = mpmath.mpf((w[0] >> 9) * 2**30 + (w[1] >> 2)) / 2**53
+            z = U * E["x"][L]
+            if z < E["x"][L + 1]:
+                return float(-z if neg else z), path + ["fast"]
+            if L == 0:
+                tail = True
+                path.append("to-tail")
+                continue
+            V = mpmath.mpf((w[2] >> 5) * 2**26 + (w[3] >> 6)) / 2**53
+            if E["f"][L] + V * (E["f"][L + 1] - E["f"][L]) < _f(z):
+                return float(-z if neg else z), path + ["wedge"]
+            path.append("wedge-reject")
+    return 0.0, path
+
+
+def _philox_np(c0, c1, c2, c3, k0, k1):
+    """Philox4x32-10 (Salmon et al., SC 2011) on numpy arrays of counters,
+    for scanning many entries at once; pinned to the known answers below."""
+    M0, M1, W0, W1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57), 0x9E3779B9, 0xBB67AE85
+    mask = np.uint64(0xFFFFFFFF)
+    c = [np.asarray(t, dtype=np.uint64) & mask for t in (c0, c1, c2, c3)]
+    for r in range(10):
+        ka, kb = np.uint64((k0 + r * W0) & 0xFFFFFFFF), np.uint64((k1 + r * W1) & 0xFFFFFFFF)
+        p0, p1 = M0 * c[0], M1 * c[2]
+        c = [(p1 >> np.uint64(32)) ^ c[1] ^ ka, p1 & mask, (p0 >> np.uint64(32)) ^ c[3] ^ kb, p0 & mask]
+    return c
+
+
+def test_numpy_philox_known_answers():
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        rows = [[int(t, 16) for t in ln.split()] for ln in f if ln.strip() and not ln.startswith("#")]
+    for v in rows:
+        out = _philox_np(*[np.array([t]) for t in v[0:4]], v[4], v[5])
+        assert [int(o[0]) for o in out] == v[6:10]
+
+
+def _first_rounds(seed, i, j, x):
+    """Layer and fast-test outcome of the first round of entries (i, j)."""
+    j = np.asarray(j, dtype=np.uint64)
+    w = _philox_np(np.full(j.shape, i), j & np.uint64(0xFFFFFFFF), j >> np.uint64(32), np.full(j.shape, 2),
+                   seed & 0xFFFFFFFF, seed >> 32)
+    L = (w[0] & np.uint64(255)).astype(np.int64)
+    U = ((w[0] >> np.uint64(9)) * np.uint64(2**30) + (w[1] >> np.uint64(2))).astype(np.float64) * 2.0 ** -53
+    return L, U * x[L] < x[L + 1]
+
+
+_LIM = 8.0 - 2.0 ** -17
+
+
+def _grid(z):
+    """The entry from the draw z: nearest multiple of 2^-17 (ties to even),
+    clamped to |Omega| <= 8 - 2^-17; None when z lies within the FP64 error
+    of the tables (1e-12 relative) of a tie, where the two may round apart."""
+    t = z * 131072.0
+    if abs(abs(t - np.floor(t)) - 0.5) <= 1e-12 * abs(t) + 1e-9:
+        return None
+    return float(np.clip(np.rint(t) / 131072.0, -_LIM, _LIM))
+
+
+def test_gaussian_entries_match_the_ziggurat_in_high_precision():
+    """Pin of the exact entry values: random entries, and entries found to
+    take each slow path (the wedge, the tail, a rejected first round), against
+    the 40-digit ziggurat rounded to the 2^-17 grid.  The FP64 draw differs
+    from the exact one only by the FP64 error of the tables (1e-12 relative at
+    most) and one product, which moves the entry only next to a grid tie; a
+    wrong bit field, sign, layer or counter gives O(1) differences."""
+    x, _ = O.zig_tables()
     rng = np.random.default_rng(3)
-    worst = 0.0
+    cases = []
     for seed in (0, 2024, 0xDEADBEEFCAFE):
-        for _ in range(150):
-            i, j = int(rng.integers(0, 1 << 20)), int(rng.integers(0, 1 << 34))
-            z, rad = _box_muller_exact(seed, i, j)
-            got = O.gaussian_entry(seed, i, j)
-            err = abs(got - z)
-            assert err <= 4e-15 * rad + 1e-300, (seed, i, j, got, z)
-            worst = max(worst, err / max(rad, 1e-300))
-    assert worst < 4e-15
+        cases += [(seed, int(rng.integers(0, 1 << 20)), int(rng.integers(0, 1 << 34))) for _ in range(60)]
+    # slow first rounds are rare (the share 1 - x_{L+1} / x_L averaged over
+    # the layers, 1.5 %; the top layer is never fast; the tail 0.026 %): scan
+    # 1.2M entries for them, keep 200 wedge cases and every tail case (about
+    # 300, enough to see a wrong tail acceptance, which changes 4 % of them)
+    wedge, tails, nslow = [], [], 0
+    for i in range(8):
+        js = np.arange(150000)
+        L, fast = _first_rounds(7, i, js, x)
+        nslow += int((~fast).sum())
+        tails += [(7, i, int(j)) for j in js[~fast & (L == 0)]]
+        wedge += [(7, i, int(j)) for j in js[~fast & (L > 0)][:25]]
+    p_slow = float(np.mean(1 - x[1:] / x[:-1]))
+    assert stats.binomtest(nslow, 1200000, p_slow).pvalue > 1e-4, (nslow, p_slow)
+    assert 200 < len(tails) < 420, len(tails)
+    seen, ties = set(), 0
+    for seed, i, j in cases + wedge + tails:
+        z, path = _zig_exact(seed, i, j)
+        seen.update(path)
+        got = O.gaussian_entry(seed, i, j)
+        want = _grid(z)
+        if want is None:
+            ties += 1
+            continue
+        assert got == want, (seed, i, j, got, z, path)
+    assert {"fast", "wedge", "wedge-reject", "to-tail", "tail"} <= seen, seen
+    assert ties <= 2
+
+
+def test_entries_are_on_the_grid_with_three_digits():
+    """Every entry is a multiple of 2^-17 below 8 in magnitude; hence, for any
+    row of entries with maximum under 2^E (E <= 3), x 2^(55 - E) is an integer
+    multiple of 2^35: its balanced base-128 digits below the top three vanish
+    (the claim the FP64 sketch's three-digit product rests on)."""
+    Om = O.gaussian_operator(5, 64, 4096, O.FP64)
+    q = Om * 131072.0
+    np.testing.assert_array_equal(q, np.rint(q))
+    assert np.abs(Om).max() <= _LIM
+    for r in range(64):
+        for k0 in range(0, 4096, 512):
+            row = Om[r, k0:k0 + 512]
+            E = int(np.floor(np.log2(np.abs(row).max()))) + 1
+            assert E <= 3
+            V = [int(v) for v in (row * 2.0 ** (55 - E))]
+            assert all(v % (1 << 35) == 0 for v in V)
+
+
+def test_tail_mass_and_layer_use():
+    x, _ = O.zig_tables()
+    Om = O.gaussian_operator(11, 32, 100000, O.FP64)
+    z = np.abs(Om.ravel())
+    # P(|z| > r) = 2 (1 - Phi(r)) = 2.58e-4: the tail sampler's share
+    k = int((z > x[1]).sum())
+    assert stats.binomtest(k, z.size, 2 * stats.norm.sf(x[1])).pvalue > 1e-4, k
+    # the mass between consecutive layer bounds follows the normal law
+    edges = np.concatenate(([0.0], x[255:0:-1]))
+    cnt, _ = np.histogram(z[z < x[1]], bins=edges)
+    p = np.diff(2 * stats.norm.cdf(edges) - 1)
+    assert stats.chisquare(cnt, p / p.sum() * cnt.sum()).pvalue > 1e-4
 
 
 @pytest.mark.parametrize("prec", [O.FP8_E4M3, O.BF16, O.FP16, O.FP32])
 def test_rounded_gaussian_operator_matches_exact_values(prec):
-    """The low-precision operator holds the exact Box-Muller value rounded
-    once to the target format.  Entries whose FP64 value lies within the
-    FP64 error bound of a rounding boundary of the target are skipped:
-    there, the FP64 and the exact value may round apart."""
+    """The low-precision operator holds the grid entry (from the exact
+    ziggurat value) rounded once to the target format."""
     seed, s, m = 99, 24, 40
     Om = O.gaussian_operator(seed, s, m, prec)
     skipped = 0
     for j in range(m):
         for i in range(s):
-            z, rad = _box_muller_exact(seed, i, j)
-            lo, hi = O.round_to(np.array([z - 4e-15 * rad]), prec)[0], O.round_to(np.array([z + 4e-15 * rad]), prec)[0]
-            if lo != hi:
+            z, _ = _zig_exact(seed, i, j)
+            g = _grid(z)
+            if g is None:
                 skipped += 1
                 continue
-            assert Om[i, j] == lo, (prec, i, j, Om[i, j], z)
+            assert Om[i, j] == O.round_to(np.array([g]), prec)[0], (prec, i, j, Om[i, j], z)
     assert skipped <= 2
