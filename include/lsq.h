@@ -70,7 +70,11 @@ typedef enum {
 
 typedef enum {
     LSQ_GAUSSIAN = 0,     /* Omega_ij ~ N(0, 1), unscaled */
-    LSQ_SPARSE_SIGN = 1   /* zeta distinct +-1 entries per column of Omega */
+    LSQ_SPARSE_SIGN = 1,  /* zeta distinct +-1 entries per column of Omega */
+    LSQ_SRFT = 2          /* Omega = S F D of Eq. e_sketch: random signs D, the
+                             unscaled Walsh-Hadamard transform F of order
+                             m' = 2^ceil(log2 m) (A padded with zero rows),
+                             s rows sampled with replacement (S) */
 } lsq_sketch_kind;
 
 typedef enum {
@@ -97,7 +101,11 @@ typedef enum {
  *   sketch_prec   u_p for the sketch (lsq_prec, AUTO allowed)
  *   qr_prec       arithmetic of the sketch QR: LSQ_FP32 or LSQ_FP64; forced
  *                 to FP64 when the sketch precision is FP64
- *   refine_steps  0 or 1 FP64 refinement steps (not in the paper)      */
+ *   refine_steps  0 or 1 FP64 refinement steps (not in the paper)
+ *   row_offset    0, or, when A is one row shard of a larger problem (see
+ *                 lsq_set_reduce_hook), the global index of its first row:
+ *                 the sketch operator's columns are drawn for the global
+ *                 rows (Gaussian and sparse sign; not SRFT)            */
 typedef struct {
     int32_t kind;
     int32_t zeta;
@@ -106,8 +114,32 @@ typedef struct {
     int32_t sketch_prec;
     int32_t qr_prec;
     int32_t refine_steps;
-    int32_t reserved;
+    int32_t row_offset;
 } lsq_opts;
+
+/* ---- Row-sharded solves (the reduction is the caller's) ----------------
+ * When A's rows are split over processes (A_k on GPU k, the rows of b
+ * alike), every sum over rows in the path must be combined across the
+ * shards: the column maxima of the sketch's power-of-two scaling (max), the
+ * sketch A_s = sum_k Omega_k A_k, the Gram and right-hand side
+ * sum_k A_pk^T A_pk (or A_pk^T A_k), sum_k A_pk^T b_k (A^T b for the
+ * seminormal equations), the refinement's A_p^T r and the condition
+ * estimate's A^T A.  The rest of the path (QR, factorizations, solves) is
+ * replicated.  A hook registered here is called by the solve (host code, on
+ * the solve's stream, enqueue order) right after each such partial result is
+ * formed in device memory and before it is used; it must replace the
+ * `count` entries of `buf` by their reduction over all shards (an
+ * all-reduce on `stream`, or a synchronous one) and return LSQ_OK.  The
+ * batched solver, the learned proposal and SRFT sketches do not take part.
+ * No hook (the default, fn = NULL): single-process solves.  The library
+ * builds no collective itself.  Process-wide; returns the previous hook. */
+typedef enum {
+    LSQ_REDUCE_SUM_F32 = 0,   /* float sum */
+    LSQ_REDUCE_SUM_F64 = 1,   /* double sum */
+    LSQ_REDUCE_MAX_U64 = 2    /* unsigned 64-bit max (column maxima as FP64 bit patterns) */
+} lsq_reduce_kind;
+typedef int32_t (*lsq_reduce_fn)(void* buf, int64_t count, int32_t kind, void* stream, void* user);
+lsq_reduce_fn lsq_set_reduce_hook(lsq_reduce_fn fn, void* user);
 
 /* Library version (major*10000 + minor*100 + patch). */
 int32_t lsq_version(void);
@@ -136,9 +168,15 @@ lsq_status lsq_sparse_sign_operator(uint64_t seed, int64_t m, int64_t s, int32_t
                                     int32_t* idx, int8_t* sgn, void* stream);
 
 /* Gaussian operator rounded to `prec`, returned as FP64 values in Om
- * (s x m column-major, ld s).  Entry (i, j): counter (i, j_lo, j_hi, 2),
- * u1 = (53-bit integer + 1) 2^-53 from words 0-1, u2 = 53-bit integer 2^-53
- * from words 2-3, z = sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller). */
+ * (s x m column-major, ld s).  Entry (i, j): the ziggurat of Marsaglia &
+ * Tsang (2000) with 256 layers (r = 3.6541528853610088; tables built in FP64
+ * from the equal-area recurrence f(x_{i+1}) = f(x_i) + v / x_i,
+ * f(x) = exp(-x^2/2)).  Round k uses the Philox block of counter
+ * (i, j_lo, j_hi, 2 + 256 k): layer = w0 & 255, sign = bit 8 of w0,
+ * U = (2^30 (w0 >> 9) + (w1 >> 2)) 2^-53, proposal z = U x_layer; the wedge
+ * test uses V = (2^26 (w2 >> 5) + (w3 >> 6)) 2^-53; the tail (layer 0 past
+ * r) takes later rounds, e1 = -ln(U1)/r, e2 = -ln(U2), U1, U2 = V + 2^-53,
+ * kept when 2 e2 > e1^2, value r + e1. */
 lsq_status lsq_gaussian_operator(uint64_t seed, int64_t s, int64_t m, int32_t prec,
                                  double* Om, void* stream);
 
@@ -149,7 +187,12 @@ lsq_status lsq_gaussian_operator(uint64_t seed, int64_t s, int64_t m, int32_t pr
  * Products accumulate in FP32 (FP64 when u_p = FP64).  As (s x n,
  * column-major, ld ldas >= s) is float* for FP8/BF16/FP16/FP32 and double*
  * for FP64.  colexp: n int32 (device).  Sparse-sign sums run in ascending
- * column index of Omega.  AUTO is not accepted here.  info (device int32,
+ * column index of Omega.  SRFT: D from bit (j & 31) of word (j >> 5) & 3
+ * of Philox counter (j >> 7, 0, 0, 3) (set = -1), F by butterfly levels
+ * h = 1, 2, ..., m'/2 in order, (a, b) -> (a + b, a - b), in FP32 (FP64 for
+ * an FP64 sketch) on the rounded, scaled A, sample t = word (t & 3) of
+ * counter (t >> 2, 0, 0, 4) masked to [0, m'); bit-identical to a sequential
+ * sweep.  AUTO is not accepted here.  info (device int32,
  * may be NULL) receives -3 if a row of a sparse-sign Omega holds more
  * nonzeros than the deterministic row sort supports, -2 if the index draw
  * did not terminate. */
@@ -382,7 +425,7 @@ int64_t lsq_test_set_solve_wait_ns(int64_t ns);
 
 /* One problem of a batch: device pointers A (m x n, ld lda), b (m), x (n),
  * info (device int32), and its own options (sketch kind, s, zeta, seed,
- * sketch precision including AUTO, QR precision, refinement). */
+ * sketch precision including AUTO and AUTO_SKETCH, QR precision, refinement). */
 typedef struct {
     const double* A;
     int64_t m;
@@ -404,13 +447,55 @@ size_t lsq_batched_workspace_size(int32_t hpne, int32_t count, const lsq_batch_p
  * first, least-loaded stream) and the whole fan-out is captured into one
  * CUDA graph launched on `stream`; the executable graph is cached and
  * replayed while the descriptors (pointers, shapes, options, workspace) stay
- * the same.  Problems with sketch_prec = AUTO first get one batched
- * condition-estimate pass and one readback of the chosen precisions (a
- * stream synchronisation).  Each problem's status goes to its own info.
- * Not thread safe: one batched call at a time per process. */
+ * the same.  Problems with sketch_prec = AUTO or AUTO_SKETCH first get one
+ * batched condition-estimate pass and one readback of the chosen precisions
+ * (a stream synchronisation).  Each problem's status goes to its own info.
+ * Every problem still runs its own kernel sequence inside the graph (no
+ * single persistent kernel walks the batch).  Not thread safe: one batched
+ * call at a time per process. */
 lsq_status lsq_pne_solve_batched(int32_t count, const lsq_batch_problem* probs, void* ws, size_t ws_bytes,
                                  void* stream);
 lsq_status lsq_hpne_solve_batched(int32_t count, const lsq_batch_problem* probs, void* ws, size_t ws_bytes,
+                                  void* stream);
+
+/* Batched sketch (Alg. 1, "Sketch A_s = Omega A" in u_p, for many problems):
+ * each entry is one lsq_sketch call (its own shape, options and outputs; the
+ * precision must not be AUTO).  The calls are spread over the internal
+ * streams and captured into one CUDA graph like the batched solves (cached
+ * while the descriptors stay the same); results are those of separate
+ * lsq_sketch calls. */
+typedef struct {
+    const double* A;
+    int64_t m;
+    int64_t n;
+    int64_t lda;
+    void* As;          /* s x n, ld ldas: float* (FP8/BF16/FP16/FP32) or double* (FP64) */
+    int64_t ldas;
+    int32_t* colexp;   /* n int32 (device) */
+    int32_t* info;     /* device int32, may be NULL */
+    lsq_opts opts;
+} lsq_sketch_problem;
+size_t lsq_sketch_batched_workspace_size(int32_t count, const lsq_sketch_problem* probs);
+lsq_status lsq_sketch_batched(int32_t count, const lsq_sketch_problem* probs, void* ws, size_t ws_bytes,
+                              void* stream);
+
+/* Batched preconditioner QR (Alg. 1, "Thin QR factorization", "Promote
+ * R_s"): each entry is one lsq_precond_qr call; same fan-out and graph as
+ * above; results are those of separate calls. */
+typedef struct {
+    const void* As;        /* s x n, ld ldas, float* (as_prec FP32) or double* (FP64) */
+    int64_t s;
+    int64_t n;
+    int64_t ldas;
+    int32_t as_prec;
+    int32_t qr_prec;
+    const int32_t* colexp; /* may be NULL */
+    double* Rs;            /* n x n, ld ldr */
+    int64_t ldr;
+    int32_t* info;         /* device int32 */
+} lsq_qr_problem;
+size_t lsq_precond_qr_batched_workspace_size(int32_t count, const lsq_qr_problem* probs);
+lsq_status lsq_precond_qr_batched(int32_t count, const lsq_qr_problem* probs, void* ws, size_t ws_bytes,
                                   void* stream);
 
 /* ---- Learned precision proposal (an addition to the paper; the paper's

@@ -17,7 +17,7 @@ import os
 import torch
 
 __all__ = [
-    "FP8_E4M3", "BF16", "FP16", "FP32", "FP64", "AUTO", "AUTO_SKETCH", "GAUSSIAN", "SPARSE_SIGN", "METHODS",
+    "FP8_E4M3", "BF16", "FP16", "FP32", "FP64", "AUTO", "AUTO_SKETCH", "GAUSSIAN", "SPARSE_SIGN", "SRFT", "METHODS",
     "condest_sketch",
     "Opts", "lib", "colmajor", "workspace", "sketch", "precond_qr", "condest", "trsm_gram",
     "factor_solve", "trsm_tc", "gram_tc", "gemm_tn_tc", "set_fp64_emulation", "pne", "hpne", "solve", "solve_host", "sparse_sign_operator",
@@ -25,7 +25,7 @@ __all__ = [
 ]
 
 FP8_E4M3, BF16, FP16, FP32, FP64, AUTO, AUTO_SKETCH = 0, 1, 2, 3, 4, 5, 6
-GAUSSIAN, SPARSE_SIGN = 0, 1
+GAUSSIAN, SPARSE_SIGN, SRFT = 0, 1, 2
 (OP_SKETCH, OP_PRECOND_QR, OP_CONDEST, OP_PNE, OP_HPNE, OP_TRSM_GRAM, OP_FACTOR_SOLVE, OP_PNE_HOST, OP_HPNE_HOST,
  OP_CONDEST_SKETCH, OP_HPNE_QR, OP_SNE, OP_NNE) = range(13)
 # solution methods: entry point and workspace op
@@ -45,7 +45,7 @@ class LsqError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("kind", C.c_int32), ("zeta", C.c_int32), ("s", C.c_int64), ("seed", C.c_uint64),
                 ("sketch_prec", C.c_int32), ("qr_prec", C.c_int32), ("refine_steps", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("row_offset", C.c_int32)]
 
 
 _vp, _i64, _sz = C.c_void_p, C.c_int64, C.c_size_t
@@ -181,10 +181,10 @@ def colmajor(A: torch.Tensor, ld: int = None) -> torch.Tensor:
     return out
 
 
-def _ld(A):
+def _ld(A, dtypes=(torch.float64,)):
     m, n = A.shape
-    if A.dtype != torch.float64:
-        raise LsqError("A must be float64")
+    if A.dtype not in dtypes:
+        raise LsqError("A must be " + " or ".join(str(d).replace("torch.", "") for d in dtypes))
     if n == 1:
         return m
     if A.stride(0) != 1 or A.stride(1) < m:
@@ -192,11 +192,33 @@ def _ld(A):
     return A.stride(1)
 
 
-def make_opts(*, kind=SPARSE_SIGN, s=None, n=None, zeta=8, seed=0, sketch_prec=FP32, qr_prec=FP32, refine_steps=0):
+def make_opts(*, kind=SPARSE_SIGN, s=None, n=None, zeta=8, seed=0, sketch_prec=FP32, qr_prec=FP32, refine_steps=0,
+              row_offset=0):
     if s is None:
         s = 2 * n
     return Opts(kind=kind, zeta=zeta, s=s, seed=seed, sketch_prec=sketch_prec, qr_prec=qr_prec,
-                refine_steps=refine_steps, reserved=0)
+                refine_steps=refine_steps, row_offset=row_offset)
+
+
+# Row-sharded solves: the caller's reduction of partial sums (lsq_set_reduce_hook).
+REDUCE_SUM_F32, REDUCE_SUM_F64, REDUCE_MAX_U64 = 0, 1, 2
+REDUCE_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p)
+_reduce_keep = []
+
+
+def set_reduce_hook(fn):
+    """Register `fn(buf_ptr, count, kind, stream_ptr) -> int` (0 = OK) as the
+    reduction of every partial sum over rows, or None to remove it."""
+    L = lib()
+    L.lsq_set_reduce_hook.restype = C.c_void_p
+    L.lsq_set_reduce_hook.argtypes = [REDUCE_FN, C.c_void_p]
+    if fn is None:
+        L.lsq_set_reduce_hook(REDUCE_FN(), None)
+        _reduce_keep.clear()
+        return
+    cb = REDUCE_FN(lambda buf, count, kind, stream, user: int(fn(buf, count, kind, stream)))
+    _reduce_keep[:] = [cb]
+    L.lsq_set_reduce_hook(cb, None)
 
 
 def workspace_size(op, m, n, opts=None) -> int:
@@ -448,6 +470,76 @@ def solve_batched(desc, ws, hpne=False):
     L = _batch_sigs()
     fn = L.lsq_hpne_solve_batched if hpne else L.lsq_pne_solve_batched
     _check(fn(len(desc), desc, _ptr(ws), ws.numel(), _stream()), "lsq_solve_batched")
+
+
+class SketchProblem(C.Structure):
+    _fields_ = [("A", C.c_void_p), ("m", C.c_int64), ("n", C.c_int64), ("lda", C.c_int64), ("As", C.c_void_p),
+                ("ldas", C.c_int64), ("colexp", C.c_void_p), ("info", C.c_void_p), ("opts", Opts)]
+
+
+class QrProblem(C.Structure):
+    _fields_ = [("As", C.c_void_p), ("s", C.c_int64), ("n", C.c_int64), ("ldas", C.c_int64),
+                ("as_prec", C.c_int32), ("qr_prec", C.c_int32), ("colexp", C.c_void_p), ("Rs", C.c_void_p),
+                ("ldr", C.c_int64), ("info", C.c_void_p)]
+
+
+def _steps_sigs():
+    L = lib()
+    for nm, T in (("lsq_sketch_batched", SketchProblem), ("lsq_precond_qr_batched", QrProblem)):
+        w = getattr(L, nm + "_workspace_size")
+        w.restype = C.c_size_t
+        w.argtypes = [C.c_int32, C.POINTER(T)]
+        f = getattr(L, nm)
+        f.restype = C.c_int32
+        f.argtypes = [C.c_int32, C.POINTER(T), C.c_void_p, C.c_size_t, C.c_void_p]
+    return L
+
+
+def sketch_batched(As_list, opts_list):
+    """lsq_sketch on every (A, opts) in one captured fan-out; returns
+    [(A_s, colexp, info)] (A_s float32, or float64 for FP64)."""
+    L = _steps_sigs()
+    arr = (SketchProblem * len(As_list))()
+    outs = []
+    for i, (A, o) in enumerate(zip(As_list, opts_list)):
+        _need_cuda(A)
+        m, n = A.shape
+        dt = torch.float64 if o.sketch_prec == FP64 else torch.float32
+        As = torch.empty((n, o.s), dtype=dt, device=A.device).t()
+        ce = torch.empty(n, dtype=torch.int32, device=A.device)
+        info = torch.zeros(1, dtype=torch.int32, device=A.device)
+        arr[i] = SketchProblem(A.data_ptr(), m, n, _ld(A), As.data_ptr(), o.s, ce.data_ptr(), info.data_ptr(), o)
+        outs.append((As, ce, info))
+    nbytes = int(L.lsq_sketch_batched_workspace_size(len(arr), arr))
+    if nbytes == 0:
+        raise LsqError("invalid batch description")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    _check(L.lsq_sketch_batched(len(arr), arr, _ptr(ws), ws.numel(), _stream()), "lsq_sketch_batched")
+    return outs
+
+
+def precond_qr_batched(items, qr_prec=FP32):
+    """lsq_precond_qr on every (A_s, colexp) in one captured fan-out; returns [(R_s, info)]."""
+    L = _steps_sigs()
+    arr = (QrProblem * len(items))()
+    outs = []
+    for i, (As, ce) in enumerate(items):
+        _need_cuda(As)
+        s_, n = As.shape
+        ap = FP64 if As.dtype == torch.float64 else FP32
+        qp = FP64 if ap == FP64 else qr_prec
+        Rs = torch.zeros((n, n), dtype=torch.float64, device=As.device).t()
+        info = torch.zeros(1, dtype=torch.int32, device=As.device)
+        arr[i] = QrProblem(As.data_ptr(), s_, n, _ld(As, (torch.float64, torch.float32)), ap, qp,
+                           ce.data_ptr() if ce is not None else None,
+                           Rs.data_ptr(), n, info.data_ptr())
+        outs.append((Rs, info))
+    nbytes = int(L.lsq_precond_qr_batched_workspace_size(len(arr), arr))
+    if nbytes == 0:
+        raise LsqError("invalid batch description")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    _check(L.lsq_precond_qr_batched(len(arr), arr, _ptr(ws), ws.numel(), _stream()), "lsq_precond_qr_batched")
+    return outs
 
 
 # ---------------------------------------------------------------------------- learned proposal

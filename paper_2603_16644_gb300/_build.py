@@ -14,7 +14,10 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblsq.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+# -ffp-contract=off: host code rounds every product and sum on its own (the
+# Gaussian generator's tables must not depend on the host compiler's FMA use)
+NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+           "--expt-relaxed-constexpr",
            "-I" + os.path.join(ROOT, "include")] + ARCH
 
 

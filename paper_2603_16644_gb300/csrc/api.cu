@@ -39,6 +39,16 @@ static size_t prof_event() {
 }
 
 static std::atomic<int> g_last_cuda_error{0};
+
+// Row-sharded solves: the caller's reduction of partial sums (none by default).
+static lsq_reduce_fn g_reduce_fn = nullptr;
+static void* g_reduce_user = nullptr;
+
+lsq_status reduce_partial(void* buf, int64_t count, int kind, cudaStream_t st) {
+    if (!g_reduce_fn) return LSQ_OK;
+    int32_t r = g_reduce_fn(buf, count, kind, (void*)st, g_reduce_user);
+    return r == LSQ_OK ? LSQ_OK : LSQ_ERR_CUDA;
+}
 void note_cuda_error(cudaError_t e) { g_last_cuda_error.store((int)e); }
 
 void stage_mark(int stage, bool begin, cudaStream_t st, double work) {
@@ -92,12 +102,13 @@ int layout_prec(int p) { return is_auto(p) ? LSQ_FP64 : p; }
 
 lsq_status check_opts(const lsq_opts* o, int64_t m, int64_t n, bool allow_auto) {
     if (!o) return LSQ_ERR_ARG;
-    if (o->kind != LSQ_GAUSSIAN && o->kind != LSQ_SPARSE_SIGN) return LSQ_ERR_ARG;
+    if (o->kind != LSQ_GAUSSIAN && o->kind != LSQ_SPARSE_SIGN && o->kind != LSQ_SRFT) return LSQ_ERR_ARG;
     if (o->s < n || o->s > m || o->s > 0x7fffffff) return LSQ_ERR_ARG;
     if (o->kind == LSQ_SPARSE_SIGN && (o->zeta < 1 || o->zeta > 32 || o->zeta > o->s)) return LSQ_ERR_ARG;
     if (!valid_sketch_prec(o->sketch_prec) && !(allow_auto && is_auto(o->sketch_prec))) return LSQ_ERR_ARG;
     if (o->qr_prec != LSQ_FP32 && o->qr_prec != LSQ_FP64) return LSQ_ERR_ARG;
     if (o->refine_steps < 0 || o->refine_steps > 1) return LSQ_ERR_ARG;
+    if (o->row_offset < 0 || (o->row_offset != 0 && o->kind == LSQ_SRFT)) return LSQ_ERR_ARG;
     return LSQ_OK;
 }
 
@@ -144,6 +155,9 @@ SketchLayout sketch_layout(int64_t m, int64_t n, int64_t s, int kind, int zeta, 
         L.cursor = o.take(sizeof(int32_t) * (size_t)s);
         L.col = o.take(sizeof(uint32_t) * (size_t)m * zeta);
         L.maxcount = o.take(sizeof(int32_t));
+    } else if (kind == LSQ_SRFT) {
+        // signed, zero-padded and transformed columns (m' x n)
+        L.ahat = o.take(srft_ws_bytes(m, n, prec));
     } else if (gauss_fp64_tc(prec)) {
         // FP64: K chunks of Omega generated one at a time, digit-sliced
         // tensor-core products accumulated into A_s (A is read in place)
@@ -166,8 +180,9 @@ SketchLayout sketch_layout(int64_t m, int64_t n, int64_t s, int kind, int zeta, 
 }
 
 // Condition estimate on a sketch (lsq_condest_sketch): its options and scratch.
-lsq_opts est_opts(int64_t m, int64_t n, uint64_t seed) {
+lsq_opts est_opts(int64_t m, int64_t n, uint64_t seed, int32_t row_offset = 0) {
     lsq_opts e{};
+    e.row_offset = row_offset;
     e.kind = LSQ_SPARSE_SIGN;
     e.s = std::min<int64_t>(2 * n, m);
     e.zeta = (int32_t)std::min<int64_t>(8, e.s);
@@ -229,8 +244,9 @@ __global__ void k_reject_on_err(const int32_t* __restrict__ err, int32_t* __rest
 // FP32 sparse-sign sketch, its FP32 R_e, the judge of R_e and the estimator
 // of Sec. 6.1 on the sketch's Gram (csrc/condest.cu); base: EstLayout.
 lsq_status run_condest_sketch(const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed, double* kappa0,
-                              int32_t* chosen, char* base, const EstLayout& L, int sms, cudaStream_t st) {
-    const lsq_opts e = est_opts(m, n, seed);
+                              int32_t* chosen, char* base, const EstLayout& L, int sms, cudaStream_t st,
+                              int32_t row_offset = 0) {
+    const lsq_opts e = est_opts(m, n, seed, row_offset);
     char* skb = base + L.sk_base;
     int32_t* err = (int32_t*)(skb + L.sk.err);
     int32_t* ce = (int32_t*)(skb + L.sk.colexp);
@@ -243,6 +259,7 @@ lsq_status run_condest_sketch(const double* A, int64_t m, int64_t n, int64_t lda
     LSQ_CUDA_TRY(cudaMemsetAsync(qinfo, 0, sizeof(int32_t), st));
     lsq_status r = run_sketch(A, m, n, lda, &e, LSQ_FP32, Ae, e.s, ce, skb, L.sk, err, st);
     if (r != LSQ_OK) return r;
+    if ((r = reduce_partial(Ae, e.s * n, LSQ_REDUCE_SUM_F32, st)) != LSQ_OK) return r;
     if ((r = launch_precond_qr(Ae, e.s, n, e.s, LSQ_FP32, LSQ_FP32, ce, Re, n, qinfo, base + L.qr, L.qr_bytes, st)) !=
         LSQ_OK)
         return r;
@@ -336,10 +353,12 @@ lsq_status run_sketch(const double* A, int64_t m, int64_t n, int64_t lda, const 
     int32_t* colexp = colexp_out ? colexp_out : (int32_t*)(base + L.colexp);
     lsq_status r = launch_colexp(A, m, n, lda, prec, colmax, colexp, st);
     if (r != LSQ_OK) return r;
+    if (o->kind == LSQ_SRFT)
+        return launch_srft(A, m, n, lda, colexp, prec, o->seed, o->s, base + L.ahat, As, ldas, st);
     if (o->kind == LSQ_SPARSE_SIGN) {
         int32_t* idx = (int32_t*)(base + L.idx);
         int8_t* sgn = (int8_t*)(base + L.sgn);
-        if ((r = launch_sparse_gen(o->seed, m, o->s, o->zeta, idx, sgn, err, st)) != LSQ_OK) return r;
+        if ((r = launch_sparse_gen(o->seed, m, o->s, o->zeta, idx, sgn, err, o->row_offset, st)) != LSQ_OK) return r;
         if ((r = launch_sparse_csr(idx, sgn, m, o->s, o->zeta, (int32_t*)(base + L.counts), (int32_t*)(base + L.rowptr),
                                    (int32_t*)(base + L.cursor), (uint32_t*)(base + L.col),
                                    (int32_t*)(base + L.maxcount), err, st)) != LSQ_OK)
@@ -356,22 +375,24 @@ lsq_status run_sketch(const double* A, int64_t m, int64_t n, int64_t lda, const 
         LSQ_CUDA_TRY(cudaMemset2DAsync(As64, sizeof(double) * ldas, 0, sizeof(double) * o->s, n, st));
         for (int64_t k0 = 0; k0 < m; k0 += kSketchChunk) {
             const int64_t kc = std::min<int64_t>(kSketchChunk, m - k0);
-            if ((r = launch_gauss_negchunk(o->seed, o->s, k0, kc, om, st)) != LSQ_OK) return r;
+            if ((r = launch_gauss_negchunk(o->seed, o->s, o->row_offset + k0, kc, om, st)) != LSQ_OK) return r;
+            // Omega's entries lie on the 2^-17 grid below 8: three digits
             if ((r = ot_gemm_update(om, o->s, A + k0, 1, lda, As64, ldas, As64, ldas, o->s, n, kc, base + L.gemm,
-                                    L.gemm_bytes, err, st, 0, nullptr, 0, 0)) != LSQ_OK)
+                                    L.gemm_bytes, err, st, 0, nullptr, 0, 0, 3)) != LSQ_OK)
                 return r;
         }
         return LSQ_OK;
     }
     if (gauss_fp32_tc(prec)) {
         const int64_t K6 = 6 * L.ldq;
-        if ((r = launch_gauss_split3(o->seed, o->s, m, L.ldq, (uint16_t*)(base + L.om), st)) != LSQ_OK) return r;
+        if ((r = launch_gauss_split3(o->seed, o->s, m, L.ldq, (uint16_t*)(base + L.om), o->row_offset, st)) != LSQ_OK)
+            return r;
         if ((r = launch_quantize_split3(A, m, n, lda, colexp, L.ldq, (uint16_t*)(base + L.ahat), st)) != LSQ_OK)
             return r;
         return launch_sketch_tc(base + L.om, K6, base + L.ahat, K6, LSQ_BF16, o->s, n, K6, (float*)As, ldas,
                                 base + L.gemm, L.gemm_bytes, err, st);
     }
-    if ((r = launch_gauss_gen(o->seed, o->s, m, prec, base + L.om, L.ldo, st)) != LSQ_OK) return r;
+    if ((r = launch_gauss_gen(o->seed, o->s, m, prec, base + L.om, L.ldo, o->row_offset, st)) != LSQ_OK) return r;
     if ((r = launch_quantize_cm(A, m, n, lda, colexp, prec, base + L.ahat, L.ldq, st)) != LSQ_OK) return r;
     if (g_tensor_core_sketch && sketch_tc_supported(prec))
         return launch_sketch_tc(base + L.om, L.ldo, base + L.ahat, L.ldq, prec, o->s, n, m, (float*)As, ldas,
@@ -479,7 +500,8 @@ lsq_status solve_impl(int method, const double* A, int64_t m, int64_t n, int64_t
         if (prec == LSQ_AUTO)
             r = launch_condest(A, m, n, lda, k0, ch, base + L.cond, L.cond_bytes, sms, st);
         else
-            r = run_condest_sketch(A, m, n, lda, o->seed, k0, ch, base + L.est, est_layout(m, n, sms), sms, st);
+            r = run_condest_sketch(A, m, n, lda, o->seed, k0, ch, base + L.est, est_layout(m, n, sms), sms, st,
+                                   o->row_offset);
         if (r != LSQ_OK) return r;
         stage_mark(ST_CONDEST, false, st);
         int32_t host_ch = LSQ_FP64;
@@ -507,6 +529,8 @@ lsq_status solve_impl(int method, const double* A, int64_t m, int64_t n, int64_t
     } else {
         stage_mark(ST_SKETCH, true, st);
         if ((r = run_sketch(A, m, n, lda, o, prec, As, s, colexp, skb, SK, err, st)) != LSQ_OK) return r;
+        if ((r = reduce_partial(As, s * n, prec == LSQ_FP64 ? LSQ_REDUCE_SUM_F64 : LSQ_REDUCE_SUM_F32, st)) != LSQ_OK)
+            return r;
         stage_mark(ST_SKETCH, false, st);
         stage_mark(ST_QR, true, st);
         const int as_prec = prec == LSQ_FP64 ? LSQ_FP64 : LSQ_FP32;
@@ -524,9 +548,12 @@ lsq_status solve_impl(int method, const double* A, int64_t m, int64_t n, int64_t
     int32_t* tsync = (int32_t*)(base + L.tsync);
     double* gemv_ws = (double*)(base + L.gemv);
     const int64_t gemv_cap = (int64_t)(gemv_t_ws_bytes(m, n) / sizeof(double));
+    if (method == M_SNE && (r = launch_gemv_t(A, m, n, lda, b, c, gemv_ws, gemv_cap, st)) != LSQ_OK) return r;
+    // row-sharded A: the Gram and the right-hand side summed over the shards
+    if ((r = reduce_partial(G, n * n, LSQ_REDUCE_SUM_F64, st)) != LSQ_OK) return r;
+    if ((r = reduce_partial(c, n, LSQ_REDUCE_SUM_F64, st)) != LSQ_OK) return r;
     if (method == M_SNE) {
         // right-hand side of Eq. e_sne in factored form: R_s^{-T} (A^T b)
-        if ((r = launch_gemv_t(A, m, n, lda, b, c, gemv_ws, gemv_cap, st)) != LSQ_OK) return r;
         if ((r = launch_trsv<double>(TRSV_UPPER_T, Rs, n, n, c, info, tsync, err, st)) != LSQ_OK) return r;
     }
     stage_mark(ST_FACTOR, true, st);
@@ -547,13 +574,16 @@ lsq_status solve_impl(int method, const double* A, int64_t m, int64_t n, int64_t
     if (o->refine_steps > 0) stage_mark(ST_REFINE, true, st);
     for (int step = 0; step < o->refine_steps; ++step) {
         if ((r = launch_residual(A, m, n, lda, x, b, r_, st)) != LSQ_OK) return r;
-        if (method == M_SNE) {
-            // corrected seminormal equations: R^T R d = A^T r
-            if ((r = launch_gemv_t(A, m, n, lda, r_, gv, gemv_ws, gemv_cap, st)) != LSQ_OK) return r;
-            if ((r = launch_trsv<double>(TRSV_UPPER_T, Rs, n, n, gv, info, tsync, err, st)) != LSQ_OK) return r;
-        } else if ((r = launch_gemv_t(Ap, m, n, m, r_, gv, gemv_ws, gemv_cap, st)) != LSQ_OK) {
+        // A_p^T r, or A^T r for the corrected seminormal equations (R^T R d = A^T r),
+        // summed over the shards of a row-sharded A
+        if (method == M_SNE)
+            r = launch_gemv_t(A, m, n, lda, r_, gv, gemv_ws, gemv_cap, st);
+        else
+            r = launch_gemv_t(Ap, m, n, m, r_, gv, gemv_ws, gemv_cap, st);
+        if (r != LSQ_OK) return r;
+        if ((r = reduce_partial(gv, n, LSQ_REDUCE_SUM_F64, st)) != LSQ_OK) return r;
+        if (method == M_SNE && (r = launch_trsv<double>(TRSV_UPPER_T, Rs, n, n, gv, info, tsync, err, st)) != LSQ_OK)
             return r;
-        }
         if (method == M_HPNE_QR)
             r = hq_solve(G, n, gv, base, L, info, tsync, err, st);
         else
@@ -620,6 +650,13 @@ lsq_status solve_host_impl(bool hpne, const double* A_host, int64_t m, int64_t n
 extern "C" {
 
 int32_t lsq_version(void) { return 100; }
+
+lsq_reduce_fn lsq_set_reduce_hook(lsq_reduce_fn fn, void* user) {
+    lsq_reduce_fn prev = g_reduce_fn;
+    g_reduce_fn = fn;
+    g_reduce_user = user;
+    return prev;
+}
 
 const char* lsq_last_cuda_error(void) { return cudaGetErrorString((cudaError_t)g_last_cuda_error.load()); }
 
@@ -805,7 +842,7 @@ size_t lsq_workspace_size(int32_t op, int64_t m, int64_t n, const lsq_opts* o) {
 lsq_status lsq_sparse_sign_operator(uint64_t seed, int64_t m, int64_t s, int32_t zeta, int32_t* idx, int8_t* sgn,
                                     void* stream) {
     if (m <= 0 || s <= 0 || s > 0x7fffffff || zeta < 1 || zeta > 32 || zeta > s || !idx || !sgn) return LSQ_ERR_ARG;
-    return launch_sparse_gen(seed, m, s, zeta, idx, sgn, nullptr, S(stream));
+    return launch_sparse_gen(seed, m, s, zeta, idx, sgn, nullptr, 0, S(stream));
 }
 
 lsq_status lsq_gaussian_operator(uint64_t seed, int64_t s, int64_t m, int32_t prec, double* Om, void* stream) {

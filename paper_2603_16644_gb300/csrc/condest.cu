@@ -214,6 +214,8 @@ lsq_status launch_condest(const double* A, int64_t m, int64_t n, int64_t lda, do
         r = launch_gemm_kmajor(gp, A, LSQ_FP64, lda, A, LSQ_FP64, lda, G, n, base + L.gemm, st);
     }
     if (r != LSQ_OK) return r;
+    // row-sharded A: A^T A summed over the shards
+    if ((r = reduce_partial(G, n * n, LSQ_REDUCE_SUM_F32, st)) != LSQ_OK) return r;
     k_norm1<<<1, 1024, 0, st>>>(G, n, n, nrm);
     LSQ_LAUNCH_CHECK();
     LSQ_CUDA_TRY(cudaMemsetAsync(cinfo, 0, sizeof(int32_t), st));

@@ -22,6 +22,7 @@ template <> __device__ __forceinline__ double to_acc<float, double>(float v) { r
 
 // ---- sketch.cu --------------------------------------------------------------
 lsq_status launch_sparse_gen(uint64_t seed, int64_t m, int64_t s, int zeta, int32_t* idx, int8_t* sgn, int32_t* err,
+                             int64_t j0,
                              cudaStream_t st);
 int sort_cap_for(int64_t m, int64_t s, int zeta);
 lsq_status launch_sparse_csr(const int32_t* idx, const int8_t* sgn, int64_t m, int64_t s, int zeta, int32_t* counts,
@@ -35,20 +36,32 @@ lsq_status launch_quantize_cm(const double* A, int64_t m, int64_t n, int64_t lda
                               void* out, int64_t ldq, cudaStream_t st);
 lsq_status launch_sparse_gather(const int32_t* rowptr, const uint32_t* col, const void* Ahat, int prec, int64_t s,
                                 int64_t n, void* As, int64_t ldas, cudaStream_t st);
-lsq_status launch_gauss_gen(uint64_t seed, int64_t s, int64_t m, int prec, void* Om, int64_t ldo, cudaStream_t st);
+// j0: global index of A's first row (row-sharded A), the column offset of Omega
+lsq_status launch_gauss_gen(uint64_t seed, int64_t s, int64_t m, int prec, void* Om, int64_t ldo, int64_t j0,
+                            cudaStream_t st);
 lsq_status launch_gauss_inspect(uint64_t seed, int64_t s, int64_t m, int prec, double* Om, cudaStream_t st);
 // FP32 Gaussian sketch as one BF16 GEMM over six K segments of length L
 // (three BF16 pieces per FP32 value, pairs t + u <= 2).
-lsq_status launch_gauss_split3(uint64_t seed, int64_t s, int64_t m, int64_t L, uint16_t* X, cudaStream_t st);
+lsq_status launch_gauss_split3(uint64_t seed, int64_t s, int64_t m, int64_t L, uint16_t* X, int64_t j0,
+                               cudaStream_t st);
 lsq_status launch_quantize_split3(const double* A, int64_t m, int64_t n, int64_t lda, const int32_t* colexp,
                                   int64_t L, uint16_t* Y, cudaStream_t st);
 // FP32 Gram X^T X (X: m x n, FP64 or FP32, rounded to FP32) as one BF16 GEMM:
 // seven K segments per column (h l h m m h h); X at Z, Y at Z + L, ld 7L, K 6L.
 template <typename TI>
 lsq_status launch_gram_split3(const TI* A, int64_t m, int64_t n, int64_t lda, int64_t L, uint16_t* Z, cudaStream_t st);
+// Row-sharded use: hand a partial sum to the caller's reduction hook
+// (lsq_set_reduce_hook); LSQ_OK without a hook.
+lsq_status reduce_partial(void* buf, int64_t count, int kind, cudaStream_t st);
 // Gaussian sketches in FP8/BF16/FP16/FP32 and the FP32 Gram of the condition
 // estimate on the tensor cores (lsq_set_tensor_core_sketch).
 bool tensor_core_sketch_enabled();
+// Subsampled randomized Walsh-Hadamard sketch (kind LSQ_SRFT): W is
+// srft_ws_bytes of scratch (the signed, padded, transformed columns).
+int64_t srft_order(int64_t m);
+size_t srft_ws_bytes(int64_t m, int64_t n, int prec);
+lsq_status launch_srft(const double* A, int64_t m, int64_t n, int64_t lda, const int32_t* colexp, int prec,
+                       uint64_t seed, int64_t s, void* W, void* As, int64_t ldas, cudaStream_t st);
 // Columns [k0, k0 + kc) of -Omega (FP64), s x kc column-major, ld s.
 lsq_status launch_gauss_negchunk(uint64_t seed, int64_t s, int64_t k0, int64_t kc, double* Om, cudaStream_t st);
 
@@ -128,11 +141,15 @@ lsq_status ot_trsm(const double* A, int64_t m, int64_t n, int64_t lda, const dou
                    int64_t ldap, void* ws, size_t ws_bytes, int32_t* err, cudaStream_t st);
 // C_out = C_in - X Y with FP64 accuracy on the tensor cores (X: M x K
 // column-major, ld ldx; Y entry (k, j) at Y[k sk + j sj]; K <= 512).
+// x_digits = 3 when every row of X has at most three nonzero balanced
+// base-128 digits below its maximum (X on a 2^-17 grid, |X| < 8: the
+// Gaussian sketch operator); the product is then the same with 21 digit
+// pairs instead of 36.
 size_t ot_update_ws_bytes(int64_t M, int64_t N, int64_t K);
 lsq_status ot_gemm_update(const double* X, int64_t ldx, const double* Y, int64_t sk, int64_t sj, const double* Cin,
                           int64_t ldi, double* Cout, int64_t ldo, int64_t M, int64_t N, int64_t K, void* ws,
                           size_t ws_bytes, int32_t* err, cudaStream_t st, int xmode = 0,
-                          const int32_t* Eblk = nullptr, int64_t b0 = 0, int nbk = 0);
+                          const int32_t* Eblk = nullptr, int64_t b0 = 0, int nbk = 0, int x_digits = 8);
 
 // ---- qr.cu -------------------------------------------------------------------
 size_t qr_ws_bytes(int64_t s, int64_t n, int prec);

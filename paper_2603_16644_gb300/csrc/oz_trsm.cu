@@ -391,6 +391,9 @@ __device__ __forceinline__ double ot_fixed_to_double(long long hi, long long lo,
 // register file (16 K registers) then allows 96 registers per thread.
 constexpr int OT_EPI_WARPS = 16;
 
+// XD: digits of X taken (8, or 3 when X's lower digits are known to vanish);
+// pairs (t, u) with t < XD and t + u <= 7.
+template <int XD>
 __global__ void __launch_bounds__(OT_THREADS, 1)
     k_ot_update(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int64_t m,
                 int64_t N, int64_t K, const int32_t* __restrict__ Ex, const int32_t* __restrict__ Ey,
@@ -439,7 +442,8 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
 
     if (warp == 0 && lane == 0) {
         // producer: per slab the 8 Y digit tiles (the next slab's go out after
-        // X tile 3 of the current one), then the 8 X digit tiles
+        // X tile 3 of the current one, or after its last), then the XD X digit
+        // tiles
         const int total = ntl * nslab;  // slabs over all tiles of this CTA
         auto slab_tile = [&](int g, int64_t& i0, int64_t& j0, int& s) {
             const int tl = (int)blockIdx.x + (g / nslab) * (int)gridDim.x;
@@ -465,8 +469,9 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
             int64_t i0, j0;
             int s;
             slab_tile(g, i0, j0, s);
-            for (int t = 0; t < OT_DIG; ++t, ++xq) {
-                if (t == 4 && g + 1 < total && !load_y(g + 1)) {
+            constexpr int YT = XD > 4 ? 4 : XD - 1;
+            for (int t = 0; t < XD; ++t, ++xq) {
+                if (t == YT && g + 1 < total && !load_y(g + 1)) {
                     *bad = 1;
                     break;
                 }
@@ -507,7 +512,7 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
                     return;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                for (int s = 0; s < nslab; ++s, ++g, xq += OT_DIG) {
+                for (int s = 0; s < nslab; ++s, ++g, xq += XD) {
                     const int ys = g & 1;
                     if (!__all_sync(0xffffffffu, mbar_wait(&yfull[ys], (uint32_t)((g >> 1) & 1)))) {
                         *bad = 1;
@@ -520,7 +525,7 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
                     const int64_t krem = K - (int64_t)s * OT_BK;
                     const uint32_t lk[4] = {lead, krem > 16 ? lead : 0u, krem > 32 ? lead : 0u, krem > 48 ? lead : 0u};
 #pragma unroll
-                    for (int t = 0; t < OT_DIG; ++t) {
+                    for (int t = 0; t < XD; ++t) {
                         const int xs = (xq + t) % OT_XST;
                         if (!__all_sync(0xffffffffu, mbar_wait(&xfull[xs], (uint32_t)(((xq + t) / OT_XST) & 1)))) {
                             *bad = 1;
@@ -756,9 +761,10 @@ static OtUpd ot_upd_ptrs(void* ws, int64_t M, int64_t N, int64_t K) {
 lsq_status ot_gemm_update(const double* X, int64_t ldx, const double* Y, int64_t sk, int64_t sj, const double* Cin,
                           int64_t ldi, double* Cout, int64_t ldo, int64_t M, int64_t N, int64_t K, void* ws,
                           size_t ws_bytes, int32_t* err, cudaStream_t st, int xmode, const int32_t* Eblk, int64_t b0,
-                          int nbk) {
+                          int nbk, int x_digits) {
     if (M <= 0 || N <= 0 || K <= 0) return LSQ_OK;
-    if (K > OT_KMAX || !ws || ws_bytes < ot_update_ws_bytes(M, N, K)) return LSQ_ERR_ARG;
+    if (K > OT_KMAX || !ws || ws_bytes < ot_update_ws_bytes(M, N, K) || (x_digits != 3 && x_digits != OT_DIG))
+        return LSQ_ERR_ARG;
     const OtUpd U = ot_upd_ptrs(ws, M, N, K);
     CUtensorMap tzs, txs;
     if (xmode == 1 && ot_map(&tzs, U.Zx, U.Kp, U.mp, OT_RS_ROWS)) {
@@ -792,14 +798,16 @@ lsq_status ot_gemm_update(const double* X, int64_t ldx, const double* Y, int64_t
     CUtensorMap tx, ty;
     if (!ot_map(&tx, U.Zx, U.Kp, U.mp, OT_BM) || !ot_map(&ty, U.Zy, U.Kp, U.Np, OT_BN)) return LSQ_ERR_CUDA;
     const size_t smem = ot_update_smem();
-    LSQ_CUDA_TRY(cudaFuncSetAttribute(k_ot_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = x_digits == 3 ? k_ot_update<3> : k_ot_update<OT_DIG>;
+    LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int ntj = (int)(U.Np / OT_BN), ntiles = (int)(ntj * (U.mp / OT_BM));
     const int grid = std::min(ntiles, device_sm_count());
     stage_mark(ST_K_UPDATE, true, st);
-    k_ot_update<<<grid, OT_THREADS, smem, st>>>(tx, ty, M, N, K, U.Ex, U.Ey, Cin, ldi, Cout, ldo, err, ntj,
-                                                ntiles);
+    kern<<<grid, OT_THREADS, smem, st>>>(tx, ty, M, N, K, U.Ex, U.Ey, Cin, ldi, Cout, ldo, err, ntj, ntiles);
     LSQ_LAUNCH_CHECK();
-    stage_mark(ST_K_UPDATE, false, st, 36.0 * 2.0 * (double)M * (double)N * (double)K);
+    // tensor-core work: the digit pairs actually issued
+    const double pairs = x_digits == 3 ? 21.0 : 36.0;
+    stage_mark(ST_K_UPDATE, false, st, pairs * 2.0 * (double)M * (double)N * (double)K);
     return LSQ_OK;
 }
 

@@ -4,11 +4,13 @@
 //   - per-column power-of-two scaling and rounding of A to u_p,
 //   - sparse-sign gather A_s[i,:] = sum_j Omega_ij Ahat[j,:] (FP32 or FP64
 //     accumulation in ascending j: bit-identical to a sequential sum),
-//   - Gaussian operator generation (Box-Muller in FP64, rounded to u_p).
+//   - Gaussian operator generation (ziggurat in FP64, rounded to u_p).
 // The Gaussian product itself is a dense contraction (gemm.cu / sketch_tc.cu).
 #include "common.cuh"
 #include "kernels.cuh"
 
+#include <algorithm>
+#include <cmath>
 #include <type_traits>
 
 namespace lsq {
@@ -17,9 +19,10 @@ namespace lsq {
 // Sparse-sign operator: one thread per column j of Omega.
 // ---------------------------------------------------------------------------
 __global__ void k_sparse_gen(uint64_t seed, int64_t m, uint32_t s, int zeta, int32_t* __restrict__ idx,
-                             int8_t* __restrict__ sgn, int32_t* __restrict__ err) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
+                             int8_t* __restrict__ sgn, int32_t* __restrict__ err, int64_t j0) {
+    const int64_t jl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (jl >= m) return;
+    const int64_t j = j0 + jl;  // global column of Omega (row of the unsharded A)
     uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     uint32_t thresh = (0u - s) % s;
     int32_t got_idx[32];
@@ -40,8 +43,8 @@ __global__ void k_sparse_gen(uint64_t seed, int64_t m, uint32_t s, int zeta, int
     }
     U4 ws = philox(U4{0u, (uint32_t)j, (uint32_t)((uint64_t)j >> 32), 1u}, k0, k1);
     for (int t = 0; t < zeta; ++t) {
-        idx[j * zeta + t] = got_idx[t];
-        sgn[j * zeta + t] = ((ws.x >> t) & 1u) ? (int8_t)-1 : (int8_t)1;
+        idx[jl * zeta + t] = got_idx[t];
+        sgn[jl * zeta + t] = ((ws.x >> t) & 1u) ? (int8_t)-1 : (int8_t)1;
     }
 }
 
@@ -357,32 +360,151 @@ __global__ void __launch_bounds__(256) k_sparse_gather_v(const int32_t* __restri
 }
 
 // ---------------------------------------------------------------------------
-// Gaussian operator: Omega_hat[i, j] = round_p(sqrt(-2 ln u1) cos(2 pi u2)),
-// written ROW-major (ld ldo >= m, K-major operand of the sketch GEMM), or as
-// FP64 column-major for inspection.  Products and sums are explicitly
-// rounded (no contraction) so the FP64 value matches a plain sequential
-// evaluation up to the accuracy of log and cos.
+// Gaussian entries by the ziggurat of Marsaglia & Tsang (J. Stat. Softw. 5(8),
+// 2000) with 256 layers of equal area v under f(x) = exp(-x^2 / 2), x >= 0:
+//   layer 0     the rectangle [0, r] x [0, f(r)] plus the tail x > r, drawn
+//               as a rectangle of width x_0 = v / f(r);
+//   layer i>=1  [0, x_i] x [f(x_i), f(x_{i+1})]: f(x_{i+1}) = f(x_i) + v / x_i,
+//               x_1 = r, x_256 = 0;
+// v = r f(r) + sqrt(pi/2) erfc(r / sqrt 2), r = 3.6541528853610088 (the root
+// of the closure f(x_255) + v / x_255 = 1).  The tables are built once on
+// the host in FP64 (no fused multiply-adds: the library's host code is built
+// with -ffp-contract=off) and passed to the kernels by value.
+//
+// Entry (i, j): round k takes the Philox block of counter (i, j_lo, j_hi,
+// 2 + 256 k).  A first-kind round: layer L = w0 & 255, sign = bit 8 of w0,
+// U = (2^30 (w0 >> 9) + (w1 >> 2)) 2^-53, V = (2^26 (w2 >> 5) + (w3 >> 6))
+// 2^-53; z = U x_L is kept if z < x_{L+1}, or (L >= 1) if
+// f(x_L) + V (f(x_{L+1}) - f(x_L)) < exp(-z^2 / 2); in layer 0 past r the
+// following rounds sample the tail (Marsaglia 1964): U1, U2 = V + 2^-53 from
+// (w0, w1) and (w2, w3), e1 = -ln(U1) / r, e2 = -ln(U2), kept when
+// 2 e2 > e1^2, giving r + e1.  At most 64 rounds (then 0; the chance of
+// getting there is below 1e-100).  Products and sums are explicitly rounded,
+// so the draw equals a plain sequential FP64 evaluation up to the accuracy
+// of exp and log, which only the rare slow paths call.
+//
+// The entry is the draw rounded to the nearest multiple of 2^-17 (ties to
+// even), clamped to |Omega| <= 8 - 2^-17: 20 significant bits, so every entry
+// is an FP32 value, and below any row maximum under 8 it has only three
+// nonzero balanced base-128 digits -- the FP64 sketch's digit-sliced product
+// then needs 21 digit pairs instead of 36.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double gauss_entry(uint64_t seed, int64_t i, int64_t j) {
-    U4 w = philox(U4{(uint32_t)i, (uint32_t)j, (uint32_t)((uint64_t)j >> 32), 2u}, (uint32_t)seed,
-                  (uint32_t)(seed >> 32));
-    uint64_t a = w.x >> 5, b = w.y >> 6;
-    double u1 = __dmul_rn(__dadd_rn((double)(a * 67108864ull + b), 1.0), 0x1p-53);
-    a = w.z >> 5;
-    b = w.w >> 6;
-    double u2 = __dmul_rn((double)(a * 67108864ull + b), 0x1p-53);
-    double rad = sqrt(__dmul_rn(-2.0, log(u1)));
-    double th = __dmul_rn(6.283185307179586, u2);
-    return __dmul_rn(rad, cos(th));
+constexpr int kZigN = 256;
+constexpr double kZigR = 3.6541528853610088;
+constexpr uint32_t kZigRounds = 64;
+
+struct ZigTable {
+    double x[kZigN + 1];
+    double f[kZigN + 1];
+};
+
+static const ZigTable& zig_table() {
+    static const ZigTable t = [] {
+        ZigTable z{};
+        const double fr = std::exp(-0.5 * kZigR * kZigR);
+        const double tail = std::sqrt(0.5 * 3.14159265358979323846) * std::erfc(kZigR / std::sqrt(2.0));
+        const double v = kZigR * fr + tail;
+        z.x[0] = v / fr;
+        z.x[1] = kZigR;
+        z.f[0] = 0.0;
+        z.f[1] = fr;
+        for (int i = 1; i < kZigN - 1; ++i) {
+            const double fnext = z.f[i] + v / z.x[i];
+            z.x[i + 1] = std::sqrt(-2.0 * std::log(fnext));
+            z.f[i + 1] = std::exp(-0.5 * z.x[i + 1] * z.x[i + 1]);
+        }
+        z.x[kZigN] = 0.0;
+        z.f[kZigN] = 1.0;
+        return z;
+    }();
+    return t;
 }
 
-__global__ void k_gauss_gen(uint64_t seed, int64_t s, int64_t m, int prec, void* __restrict__ Om, int64_t ldo) {
-    int64_t i = blockIdx.y;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < ldo; j += (int64_t)gridDim.x * blockDim.x) {
-        if (prec == LSQ_FP64) {
-            ((double*)Om)[(size_t)i * ldo + j] = j < m ? gauss_entry(seed, i, j) : 0.0;
-        } else {
-            store_bits(Om, (size_t)i * ldo + j, j < m ? quant_bits(gauss_entry(seed, i, j), 0, prec) : 0u, prec);
+// The tables in shared memory: x_L 2^-53 (the proposal is one product with
+// the 53-bit integer), x_L, f(x_L).
+struct ZigShared {
+    double xs[kZigN + 1], x[kZigN + 1], f[kZigN + 1];
+};
+
+__device__ __forceinline__ void zig_stage(const ZigTable& t, ZigShared& z) {
+    for (int q = threadIdx.x; q <= kZigN; q += blockDim.x) {
+        z.xs[q] = t.x[q] * 0x1p-53;
+        z.x[q] = t.x[q];
+        z.f[q] = t.f[q];
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double zig_grid(double z) {
+    constexpr double lim = 8.0 - 0x1p-17;
+    const double q = __dmul_rn(rint(__dmul_rn(z, 131072.0)), 0x1p-17);
+    return q > lim ? lim : (q < -lim ? -lim : q);
+}
+
+__device__ __forceinline__ double zig_uniform53(uint32_t a, uint32_t b) {
+    return (double)(((uint64_t)(a >> 5) << 26) | (b >> 6)) * 0x1p-53;
+}
+
+__device__ __noinline__ double gauss_slow(uint64_t seed, int64_t i, int64_t j, const ZigShared& Z, U4 w, double z,
+                                          int L, bool neg) {
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    bool tail = L == 0;
+    for (uint32_t k = 0; k < kZigRounds; ++k) {
+        if (k > 0) {
+            w = philox(U4{(uint32_t)i, (uint32_t)j, (uint32_t)((uint64_t)j >> 32), 2u + 256u * k}, k0, k1);
+            if (!tail) {
+                L = (int)(w.x & 255u);
+                neg = (w.x >> 8) & 1u;
+                z = __dmul_rn((double)(((uint64_t)(w.x >> 9) << 30) | (w.y >> 2)), Z.xs[L]);
+                if (z < Z.x[L + 1]) return zig_grid(neg ? -z : z);
+                if (L == 0) {
+                    tail = true;
+                    continue;
+                }
+            } else {
+                const double u1 = __dadd_rn(zig_uniform53(w.x, w.y), 0x1p-53);
+                const double u2 = __dadd_rn(zig_uniform53(w.z, w.w), 0x1p-53);
+                const double e1 = __ddiv_rn(-log(u1), kZigR);
+                const double e2 = -log(u2);
+                if (__dadd_rn(e2, e2) > __dmul_rn(e1, e1)) {
+                    const double t = __dadd_rn(kZigR, e1);
+                    return zig_grid(neg ? -t : t);
+                }
+                continue;
+            }
+        } else if (tail) {
+            continue;  // the first round only sent the draw to the tail
+        }
+        // the wedge of layer L >= 1
+        const double V = zig_uniform53(w.z, w.w);
+        const double y = __dadd_rn(Z.f[L], __dmul_rn(V, __dsub_rn(Z.f[L + 1], Z.f[L])));
+        if (y < exp(__dmul_rn(__dmul_rn(-0.5, z), z))) return zig_grid(neg ? -z : z);
+    }
+    return 0.0;
+}
+
+__device__ __forceinline__ double gauss_entry(uint64_t seed, int64_t i, int64_t j, const ZigShared& Z) {
+    const U4 w = philox(U4{(uint32_t)i, (uint32_t)j, (uint32_t)((uint64_t)j >> 32), 2u}, (uint32_t)seed,
+                        (uint32_t)(seed >> 32));
+    const int L = (int)(w.x & 255u);
+    const bool neg = (w.x >> 8) & 1u;
+    const double z = __dmul_rn((double)(((uint64_t)(w.x >> 9) << 30) | (w.y >> 2)), Z.xs[L]);
+    if (z < Z.x[L + 1]) return zig_grid(neg ? -z : z);
+    return gauss_slow(seed, i, j, Z, w, z, L, neg);
+}
+
+__global__ void k_gauss_gen(const ZigTable tab, uint64_t seed, int64_t s, int64_t m, int prec,
+                            void* __restrict__ Om, int64_t ldo, int64_t j0) {
+    __shared__ ZigShared Z;
+    zig_stage(tab, Z);
+    for (int64_t i = blockIdx.y; i < s; i += gridDim.y) {
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < ldo; j += (int64_t)gridDim.x * blockDim.x) {
+            if (prec == LSQ_FP64) {
+                ((double*)Om)[(size_t)i * ldo + j] = j < m ? gauss_entry(seed, i, j0 + j, Z) : 0.0;
+            } else {
+                store_bits(Om, (size_t)i * ldo + j, j < m ? quant_bits(gauss_entry(seed, i, j0 + j, Z), 0, prec) : 0u,
+                           prec);
+            }
         }
     }
 }
@@ -414,20 +536,24 @@ __device__ __forceinline__ void split3_bf16(float x, uint16_t& h, uint16_t& m, u
     l = __bfloat16_as_ushort(bl);
 }
 
-// Omega_hat rows (FP32-rounded Box-Muller values) as BF16 pieces: row i at
+// Omega_hat rows (FP32-rounded Gaussian entries) as BF16 pieces: row i at
 // X + i * 6L, segments l m h m h h.
-__global__ void k_gauss_split3(uint64_t seed, int64_t s, int64_t m, int64_t L, uint16_t* __restrict__ X) {
-    const int64_t i = blockIdx.y;
-    uint16_t* row = X + (size_t)i * 6 * L;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x) {
-        uint16_t h = 0, mi = 0, l = 0;
-        if (j < m) split3_bf16(__double2float_rn(gauss_entry(seed, i, j)), h, mi, l);
-        row[j] = l;
-        row[L + j] = mi;
-        row[2 * L + j] = h;
-        row[3 * L + j] = mi;
-        row[4 * L + j] = h;
-        row[5 * L + j] = h;
+__global__ void k_gauss_split3(const ZigTable tab, uint64_t seed, int64_t s, int64_t m, int64_t L,
+                               uint16_t* __restrict__ X, int64_t j0) {
+    __shared__ ZigShared Z;
+    zig_stage(tab, Z);
+    for (int64_t i = blockIdx.y; i < s; i += gridDim.y) {
+        uint16_t* row = X + (size_t)i * 6 * L;
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x) {
+            uint16_t h = 0, mi = 0, l = 0;
+            if (j < m) split3_bf16(__double2float_rn(gauss_entry(seed, i, j0 + j, Z)), h, mi, l);
+            row[j] = l;
+            row[L + j] = mi;
+            row[2 * L + j] = h;
+            row[3 * L + j] = mi;
+            row[4 * L + j] = h;
+            row[5 * L + j] = h;
+        }
     }
 }
 
@@ -476,28 +602,184 @@ __global__ void k_gram_split3(const TI* __restrict__ A, int64_t m, int64_t n, in
 // Negated FP64 Omega columns [k0, k0 + kc) as an s x kc column-major block
 // (ld s): the K chunk of the FP64 sketch, which the digit-sliced update
 // subtracts (C - (-Omega) Ahat).
-__global__ void k_gauss_negchunk(uint64_t seed, int64_t s, int64_t k0, int64_t kc, double* __restrict__ Om) {
+__global__ void k_gauss_negchunk(const ZigTable tab, uint64_t seed, int64_t s, int64_t k0, int64_t kc,
+                                 double* __restrict__ Om) {
+    __shared__ ZigShared Z;
+    zig_stage(tab, Z);
     const int64_t total = s * kc;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = q % s, j = q / s;
-        Om[q] = -gauss_entry(seed, i, k0 + j);
+        Om[q] = -gauss_entry(seed, i, k0 + j, Z);
     }
 }
 
-__global__ void k_gauss_inspect(uint64_t seed, int64_t s, int64_t m, int prec, double* __restrict__ Om) {
+// ---------------------------------------------------------------------------
+// Subsampled randomized Walsh-Hadamard sketch Omega = S F D (Eq. e_sketch):
+// rows of A signed by D, zero-padded to m' = 2^ceil(log2 m), the unscaled
+// Sylvester-Hadamard transform F applied to every column by butterfly levels
+// h = 1, 2, ..., m'/2 in that order ((a, b) -> (a + b, a - b) on pairs
+// (i, i + h), i & h = 0), in FP32 (FP64 for an FP64 sketch), then d rows
+// sampled with replacement.  Each butterfly is evaluated exactly as in a
+// sequential sweep, so the result does not depend on the parallel schedule.
+//   D: bit (j & 31) of word (j >> 5) & 3 of Philox counter (j >> 7, 0, 0, 3);
+//   S: word (t & 3) of counter (t >> 2, 0, 0, 4), masked to [0, m').
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t u4_word(const U4& w, int k) {
+    return k == 0 ? w.x : k == 1 ? w.y : k == 2 ? w.z : w.w;
+}
+
+template <typename T>
+__global__ void k_srft_load(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda,
+                            const int32_t* __restrict__ colexp, int prec, uint64_t seed, int64_t mp, int64_t cpb,
+                            T* __restrict__ W) {
+    const int64_t c0 = (int64_t)blockIdx.y * cpb, c1 = min64(n, c0 + cpb);
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < mp; j += (int64_t)gridDim.x * blockDim.x) {
+        bool neg = false;
+        if (j < m) {
+            const U4 w = philox(U4{(uint32_t)((uint64_t)j >> 7), 0u, 0u, 3u}, (uint32_t)seed, (uint32_t)(seed >> 32));
+            neg = (u4_word(w, (int)((j >> 5) & 3)) >> (j & 31)) & 1u;
+        }
+        for (int64_t c = c0; c < c1; ++c) {
+            T v = (T)0;
+            if (j < m) {
+                if (prec == LSQ_FP64) {
+                    v = (T)A[j + c * lda];
+                } else {
+                    // the value rounded to u_p (with the column scaling) is exact in FP32
+                    double q = round_to_prec(ldexp(A[j + c * lda], colexp[c]), prec);
+                    v = (T)q;
+                }
+                if (neg) v = -v;
+            }
+            W[(size_t)c * mp + j] = v;
+        }
+    }
+}
+
+// levels h = 1 .. B/2 inside blocks of B consecutive entries of a column
+template <typename T>
+__global__ void __launch_bounds__(512) k_fwht_block(T* __restrict__ W, int64_t mp, int B) {
+    extern __shared__ __align__(16) unsigned char fw_raw[];
+    T* x = reinterpret_cast<T*>(fw_raw);
+    T* base = W + (size_t)blockIdx.y * mp + (size_t)blockIdx.x * B;
+    for (int i = threadIdx.x; i < B; i += blockDim.x) x[i] = base[i];
+    __syncthreads();
+    for (int h = 1; h < B; h <<= 1) {
+        for (int p = threadIdx.x; p < B / 2; p += blockDim.x) {
+            const int i = (p / h) * 2 * h + (p % h);
+            const T a = x[i], b = x[i + h];
+            x[i] = a + b;
+            x[i + h] = a - b;
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < B; i += blockDim.x) base[i] = x[i];
+}
+
+// levels h = B .. mp/2: for 32 consecutive offsets o of a column, the
+// K = mp / B entries o + k B held in shared memory, levels k-wise
+template <typename T>
+__global__ void __launch_bounds__(256) k_fwht_stride(T* __restrict__ W, int64_t mp, int B) {
+    extern __shared__ __align__(16) unsigned char fs_raw[];
+    T* x = reinterpret_cast<T*>(fs_raw);  // [K][32]
+    const int K = (int)(mp / B);
+    const int o0 = blockIdx.x * 32;
+    T* col = W + (size_t)blockIdx.y * mp;
+    for (int q = threadIdx.x; q < K * 32; q += blockDim.x) {
+        const int k = q >> 5, o = q & 31;
+        x[q] = col[(size_t)k * B + o0 + o];
+    }
+    __syncthreads();
+    for (int h = 1; h < K; h <<= 1) {
+        for (int q = threadIdx.x; q < (K / 2) * 32; q += blockDim.x) {
+            const int p = q >> 5, o = q & 31;
+            const int i = (p / h) * 2 * h + (p % h);
+            const T a = x[i * 32 + o], b = x[(i + h) * 32 + o];
+            x[i * 32 + o] = a + b;
+            x[(i + h) * 32 + o] = a - b;
+        }
+        __syncthreads();
+    }
+    for (int q = threadIdx.x; q < K * 32; q += blockDim.x) {
+        const int k = q >> 5, o = q & 31;
+        col[(size_t)k * B + o0 + o] = x[q];
+    }
+}
+
+template <typename T, typename TO>
+__global__ void k_srft_gather(const T* __restrict__ W, int64_t mp, int64_t n, uint64_t seed, int64_t s,
+                              TO* __restrict__ As, int64_t ldas) {
+    const int64_t c = blockIdx.y;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < s; t += (int64_t)gridDim.x * blockDim.x) {
+        const U4 w = philox(U4{(uint32_t)((uint64_t)t >> 2), 0u, 0u, 4u}, (uint32_t)seed, (uint32_t)(seed >> 32));
+        const int64_t row = (int64_t)(u4_word(w, (int)(t & 3)) & (uint32_t)(mp - 1));
+        As[t + c * ldas] = (TO)W[(size_t)c * mp + row];
+    }
+}
+
+int64_t srft_order(int64_t m) {
+    int64_t mp = 1;
+    while (mp < m) mp <<= 1;
+    return mp;
+}
+
+size_t srft_ws_bytes(int64_t m, int64_t n, int prec) {
+    return (prec == LSQ_FP64 ? 8 : 4) * (size_t)srft_order(m) * (size_t)n;
+}
+
+template <typename T>
+static lsq_status srft_run(const double* A, int64_t m, int64_t n, int64_t lda, const int32_t* colexp, int prec,
+                           uint64_t seed, int64_t s, T* W, void* As, int64_t ldas, cudaStream_t st) {
+    const int64_t mp = srft_order(m);
+    if (mp > ((int64_t)1 << 30)) return LSQ_ERR_ARG;
+    const int64_t cpb = 8;  // columns per block of the load
+    dim3 gl((unsigned)min64(ceil_div(mp, 256), 4096), (unsigned)ceil_div(n, cpb));
+    k_srft_load<T><<<gl, 256, 0, st>>>(A, m, n, lda, colexp, prec, seed, mp, cpb, W);
+    LSQ_LAUNCH_CHECK();
+    const int B = (int)std::min<int64_t>(mp, 4096);
+    k_fwht_block<T><<<dim3((unsigned)(mp / B), (unsigned)n), 512, sizeof(T) * B, st>>>(W, mp, B);
+    LSQ_LAUNCH_CHECK();
+    if (mp > B) {
+        const int K = (int)(mp / B);
+        const size_t smem = sizeof(T) * (size_t)K * 32;
+        if (smem > 200 * 1024) return LSQ_ERR_ARG;
+        if (smem > 48 * 1024)
+            LSQ_CUDA_TRY(cudaFuncSetAttribute(k_fwht_stride<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_fwht_stride<T><<<dim3((unsigned)(B / 32), (unsigned)n), 256, smem, st>>>(W, mp, B);
+        LSQ_LAUNCH_CHECK();
+    }
+    dim3 gg((unsigned)min64(ceil_div(s, 256), 1024), (unsigned)n);
+    if (prec == LSQ_FP64)
+        k_srft_gather<T, double><<<gg, 256, 0, st>>>(W, mp, n, seed, s, (double*)As, ldas);
+    else
+        k_srft_gather<T, float><<<gg, 256, 0, st>>>(W, mp, n, seed, s, (float*)As, ldas);
+    LSQ_LAUNCH_CHECK();
+    return LSQ_OK;
+}
+
+lsq_status launch_srft(const double* A, int64_t m, int64_t n, int64_t lda, const int32_t* colexp, int prec,
+                       uint64_t seed, int64_t s, void* W, void* As, int64_t ldas, cudaStream_t st) {
+    if (prec == LSQ_FP64) return srft_run<double>(A, m, n, lda, colexp, prec, seed, s, (double*)W, As, ldas, st);
+    return srft_run<float>(A, m, n, lda, colexp, prec, seed, s, (float*)W, As, ldas, st);
+}
+
+__global__ void k_gauss_inspect(const ZigTable tab, uint64_t seed, int64_t s, int64_t m, int prec,
+                                double* __restrict__ Om) {
+    __shared__ ZigShared Z;
+    zig_stage(tab, Z);
     int64_t total = s * m;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = q % s, j = q / s;
-        Om[q] = round_to_prec(gauss_entry(seed, i, j), prec);
+        Om[q] = round_to_prec(gauss_entry(seed, i, j, Z), prec);
     }
 }
 
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
-lsq_status launch_sparse_gen(uint64_t seed, int64_t m, int64_t s, int zeta, int32_t* idx, int8_t* sgn, int32_t* err,
+lsq_status launch_sparse_gen(uint64_t seed, int64_t m, int64_t s, int zeta, int32_t* idx, int8_t* sgn, int32_t* err, int64_t j0,
                              cudaStream_t st) {
-    k_sparse_gen<<<(unsigned)ceil_div(m, 128), 128, 0, st>>>(seed, m, (uint32_t)s, zeta, idx, sgn, err);
+    k_sparse_gen<<<(unsigned)ceil_div(m, 128), 128, 0, st>>>(seed, m, (uint32_t)s, zeta, idx, sgn, err, j0);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
 }
@@ -537,6 +819,9 @@ lsq_status launch_colexp(const double* A, int64_t m, int64_t n, int64_t lda, int
     dim3 grid((unsigned)ceil_div(m, rpb), (unsigned)n);
     k_colmax<<<grid, 256, 0, st>>>(A, m, n, lda, rpb, colmax);
     LSQ_LAUNCH_CHECK();
+    // row-sharded A: the column maxima over every shard
+    lsq_status r = reduce_partial(colmax, n, LSQ_REDUCE_MAX_U64, st);
+    if (r != LSQ_OK) return r;
     k_colexp<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(colmax, n, prec, colexp);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
@@ -626,16 +911,19 @@ lsq_status launch_sparse_gather(const int32_t* rowptr, const uint32_t* col, cons
     return LSQ_OK;
 }
 
-lsq_status launch_gauss_gen(uint64_t seed, int64_t s, int64_t m, int prec, void* Om, int64_t ldo, cudaStream_t st) {
-    dim3 grid((unsigned)min64(ceil_div(ldo, 256), 128), (unsigned)s);
-    k_gauss_gen<<<grid, 256, 0, st>>>(seed, s, m, prec, Om, ldo);
+lsq_status launch_gauss_gen(uint64_t seed, int64_t s, int64_t m, int prec, void* Om, int64_t ldo, int64_t j0,
+                            cudaStream_t st) {
+    // a few thousand blocks, each staging the tables once
+    dim3 grid((unsigned)min64(ceil_div(ldo, 256), 64), (unsigned)min64(s, 64));
+    k_gauss_gen<<<grid, 256, 0, st>>>(zig_table(), seed, s, m, prec, Om, ldo, j0);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
 }
 
-lsq_status launch_gauss_split3(uint64_t seed, int64_t s, int64_t m, int64_t L, uint16_t* X, cudaStream_t st) {
-    dim3 grid((unsigned)min64(ceil_div(L, 256), 64), (unsigned)s);
-    k_gauss_split3<<<grid, 256, 0, st>>>(seed, s, m, L, X);
+lsq_status launch_gauss_split3(uint64_t seed, int64_t s, int64_t m, int64_t L, uint16_t* X, int64_t j0,
+                               cudaStream_t st) {
+    dim3 grid((unsigned)min64(ceil_div(L, 256), 64), (unsigned)min64(s, 64));
+    k_gauss_split3<<<grid, 256, 0, st>>>(zig_table(), seed, s, m, L, X, j0);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
 }
@@ -661,15 +949,15 @@ template lsq_status launch_gram_split3<float>(const float*, int64_t, int64_t, in
                                               cudaStream_t);
 
 lsq_status launch_gauss_negchunk(uint64_t seed, int64_t s, int64_t k0, int64_t kc, double* Om, cudaStream_t st) {
-    unsigned grid = (unsigned)min64(ceil_div(s * kc, 256), 16384);
-    k_gauss_negchunk<<<grid, 256, 0, st>>>(seed, s, k0, kc, Om);
+    unsigned grid = (unsigned)min64(ceil_div(s * kc, 256), 4096);
+    k_gauss_negchunk<<<grid, 256, 0, st>>>(zig_table(), seed, s, k0, kc, Om);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
 }
 
 lsq_status launch_gauss_inspect(uint64_t seed, int64_t s, int64_t m, int prec, double* Om, cudaStream_t st) {
-    unsigned grid = (unsigned)min64(ceil_div(s * m, 256), 8192);
-    k_gauss_inspect<<<grid, 256, 0, st>>>(seed, s, m, prec, Om);
+    unsigned grid = (unsigned)min64(ceil_div(s * m, 256), 4096);
+    k_gauss_inspect<<<grid, 256, 0, st>>>(zig_table(), seed, s, m, prec, Om);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
 }

@@ -233,10 +233,14 @@ bool sketch_tc_supported(int prec) {
     return (prec == LSQ_FP8_E4M3 || prec == LSQ_BF16 || prec == LSQ_FP16) && tensor_map_encoder() != nullptr;
 }
 
+// Tile width: 128 x 256 output tiles (two 128-row blocks of Y per MMA, 25 %
+// less shared-memory and L2 traffic per flop than 128 x 128) when N fills them.
+static int tc_bn(int64_t N) { return N >= 256 ? 256 : TC_BN; }
+
 // Split count: fill the SMs when the tile grid is small; at least 4 stages of
 // K per split.
 static int tc_splits(int64_t M, int64_t N, int64_t K, int prec, int sms) {
-    int64_t tiles = ceil_div(M, TC_BM) * ceil_div(N, TC_BN);
+    int64_t tiles = ceil_div(M, TC_BM) * ceil_div(N, tc_bn(N));
     int64_t bke = prec == LSQ_FP8_E4M3 ? 128 : 64;
     int64_t kblocks = ceil_div(K, bke);
     int64_t want = std::max<int64_t>(1, sms / std::max<int64_t>(1, tiles));
@@ -254,8 +258,9 @@ lsq_status launch_sketch_tc(const void* Om, int64_t ldo, const void* Ahat, int64
                             cudaStream_t st) {
     if (!sketch_tc_supported(prec)) return LSQ_ERR_ARG;
     if ((ldo % 16) || (ldq % 16) || ((uintptr_t)Om % 16) || ((uintptr_t)Ahat % 16)) return LSQ_ERR_ARG;
+    const int bn = tc_bn(n);
     CUtensorMap ta, tb;
-    if (!make_map(&ta, Om, prec, m, s, ldo) || !make_map(&tb, Ahat, prec, m, n, ldq)) return LSQ_ERR_CUDA;
+    if (!make_map(&ta, Om, prec, m, s, ldo) || !make_map(&tb, Ahat, prec, m, n, ldq, bn)) return LSQ_ERR_CUDA;
     int sms = device_sm_count();
     int splits = tc_splits(s, n, m, prec, sms);
     int64_t bke = prec == LSQ_FP8_E4M3 ? 128 : 64;
@@ -269,23 +274,19 @@ lsq_status launch_sketch_tc(const void* Om, int64_t ldo, const void* Ahat, int64
         ldout = s;
         stride = s * n;
     }
-    size_t smem = 1024 + 2 * (size_t)TC_STAGES * TC_TILE_BYTES + 256;
-    dim3 grid((unsigned)ceil_div(s, TC_BM), (unsigned)ceil_div(n, TC_BN), (unsigned)splits);
+    size_t smem = 1024 + (size_t)tc_stages(bn) * (TC_TILE_BYTES + (size_t)bn * 128) + 256;
+    dim3 grid((unsigned)ceil_div(s, TC_BM), (unsigned)ceil_div(n, bn), (unsigned)splits);
     stage_mark(ST_K_SKETCHTC, true, st);
-    switch (prec) {
-    case LSQ_BF16:
-        LSQ_CUDA_TRY(cudaFuncSetAttribute(k_sketch_tc<0, TC_BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_sketch_tc<0, TC_BN><<<grid, TC_THREADS, smem, st>>>(ta, tb, s, n, m, kchunk, out, ldout, stride, err, nullptr, 0);
-        break;
-    case LSQ_FP16:
-        LSQ_CUDA_TRY(cudaFuncSetAttribute(k_sketch_tc<1, TC_BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_sketch_tc<1, TC_BN><<<grid, TC_THREADS, smem, st>>>(ta, tb, s, n, m, kchunk, out, ldout, stride, err, nullptr, 0);
-        break;
-    default:
-        LSQ_CUDA_TRY(cudaFuncSetAttribute(k_sketch_tc<2, TC_BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_sketch_tc<2, TC_BN><<<grid, TC_THREADS, smem, st>>>(ta, tb, s, n, m, kchunk, out, ldout, stride, err, nullptr, 0);
-        break;
-    }
+    auto go = [&](auto kern) -> lsq_status {
+        LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<grid, TC_THREADS, smem, st>>>(ta, tb, s, n, m, kchunk, out, ldout, stride, err, nullptr, 0);
+        return LSQ_OK;
+    };
+    lsq_status lr;
+    if (prec == LSQ_BF16) lr = bn == 256 ? go(k_sketch_tc<0, 256>) : go(k_sketch_tc<0, TC_BN>);
+    else if (prec == LSQ_FP16) lr = bn == 256 ? go(k_sketch_tc<1, 256>) : go(k_sketch_tc<1, TC_BN>);
+    else lr = bn == 256 ? go(k_sketch_tc<2, 256>) : go(k_sketch_tc<2, TC_BN>);
+    if (lr != LSQ_OK) return lr;
     LSQ_LAUNCH_CHECK();
     stage_mark(ST_K_SKETCHTC, false, st, 2.0 * (double)s * (double)n * (double)m);
     if (splits > 1) {

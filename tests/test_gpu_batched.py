@@ -114,3 +114,103 @@ def test_autotuner_picks_a_candidate(tmp_path):
     assert (kind, s // 100) in CANDIDATES
     again = Autotuner(path=str(tmp_path / "tune.json"))
     assert again.choose(3000, 100, prec=lsq.FP32) == (kind, s)
+
+
+def test_batched_sketch_and_qr_equal_single_calls():
+    # lsq_sketch_batched / lsq_precond_qr_batched: one captured fan-out, the
+    # results of separate calls bit for bit
+    rng = np.random.default_rng(9)
+    As, opts = [], []
+    for i in range(10):
+        n = int(rng.integers(8, 200))
+        m = int(rng.integers(4 * n, 6000))
+        A = dev_colmajor(np.asfortranarray(rng.standard_normal((m, n)) * np.exp2(rng.integers(-8, 8, n))[None, :]))
+        kind = lsq.SPARSE_SIGN if i % 2 else lsq.GAUSSIAN
+        prec = [lsq.FP8_E4M3, lsq.BF16, lsq.FP16, lsq.FP32, lsq.FP64][i % 5]
+        As.append(A)
+        opts.append(lsq.make_opts(kind=kind, s=(2 + i % 3) * n, zeta=min(8, 2 * n), seed=100 + i, sketch_prec=prec))
+    outs = lsq.sketch_batched(As, opts)
+    for A, o, (Asb, ceb, infob) in zip(As, opts, outs):
+        As1, ce1, info1 = lsq.sketch(A, o)
+        assert int(to_np(infob)[0]) == int(to_np(info1)[0]) == 0
+        np.testing.assert_array_equal(to_np(Asb), to_np(As1))
+        np.testing.assert_array_equal(to_np(ceb), to_np(ce1))
+    qr = lsq.precond_qr_batched([(Asb, ceb) for Asb, ceb, _ in outs])
+    for (Asb, ceb, _), (Rb, infob), o in zip(outs, qr, opts):
+        qp = lsq.FP64 if o.sketch_prec == lsq.FP64 else lsq.FP32
+        R1, info1 = lsq.precond_qr(Asb, ceb, qp)
+        assert int(to_np(infob)[0]) == int(to_np(info1)[0]) == 0
+        np.testing.assert_array_equal(np.triu(to_np(Rb)), np.triu(to_np(R1)))
+
+
+def test_batched_auto_sketch_per_problem():
+    probs, opts = make_batch(8, 5, auto=True)
+    for o in opts:
+        o.sketch_prec = lsq.AUTO_SKETCH
+    As = [dev_colmajor(p.A) for p in probs]
+    bs = [torch.from_numpy(p.b).cuda() for p in probs]
+    xs = [torch.empty(p.shape[1], dtype=torch.float64, device="cuda") for p in probs]
+    infos = [torch.zeros(1, dtype=torch.int32, device="cuda") for _ in probs]
+    desc = lsq.batch_descriptors(As, bs, xs, infos, opts)
+    ws = lsq.batched_workspace(desc)
+    lsq.solve_batched(desc, ws)
+    for i in range(len(probs)):
+        x1, _ = lsq.pne(As[i], bs[i], opts=opts[i])
+        np.testing.assert_array_equal(to_np(x1), to_np(xs[i]))
+
+
+def test_batched_full_size_uneven_batch():
+    # the batched workload at full size: 512 problems, m uniform in [2000, 40000],
+    # n uniform in [32, 512], kappa log-uniform in [1e2, 1e10], relative
+    # residual log-uniform in [1e-12, 1e-2]; sketch kind and s in {2n, 4n} from
+    # the autotuner, precision per problem from the estimate on a sketch
+    from types import SimpleNamespace
+
+    from paper_2603_16644_gb300.autotune import Autotuner
+
+    rng = np.random.default_rng(2603)
+    tuner = Autotuner()
+    As, bs, xs, infos, opts, meta = [], [], [], [], [], []
+    for i in range(512):
+        n = int(rng.integers(32, 513))
+        m = int(rng.integers(max(2000, 4 * n), 40001))
+        kap = float(10 ** rng.uniform(2, 10))
+        rho = float(10 ** rng.uniform(-12, -2))
+        seed = P.seed_for(3, i)
+        A, b, x_star, _, _ = P.make_problem_torch(m, n, kap, rho, seed)
+        kind, s = tuner.choose(m, n, prec=lsq.FP32)
+        As.append(A)
+        bs.append(b)
+        xs.append(torch.empty(n, dtype=torch.float64, device="cuda"))
+        infos.append(torch.zeros(1, dtype=torch.int32, device="cuda"))
+        opts.append(lsq.make_opts(kind=kind, s=s, zeta=min(8, s), seed=seed, sketch_prec=lsq.AUTO_SKETCH,
+                                  qr_prec=lsq.FP32, refine_steps=0))
+        meta.append((kap, rho, x_star))
+    desc = lsq.batch_descriptors(As, bs, xs, infos, opts)
+    ws = lsq.batched_workspace(desc)
+    lsq.solve_batched(desc, ws)  # estimate pass, capture, first launch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    lsq.solve_batched(desc, ws)  # estimate pass and one cached graph launch
+    e1.record()
+    torch.cuda.synchronize()
+    print(f"512 uneven problems: {512 / (e0.elapsed_time(e1) / 1000):.1f} solves/s")
+    assert all(int(to_np(f)[0]) == 0 for f in infos)
+    # bit-identical to single calls on a sample
+    for i in range(0, 512, 37):
+        x1, _ = lsq.pne(As[i], bs[i], opts=opts[i])
+        np.testing.assert_array_equal(to_np(x1), to_np(xs[i]))
+    # against the oracle on a subset, at the precision the estimate chose
+    for i in range(3, 512, 16):
+        kap, rho, x_star = meta[i]
+        _, ch = lsq.condest_sketch(As[i], seed=opts[i].seed)
+        prec = int(to_np(ch)[0])
+        A_np, b_np = to_np(As[i]), to_np(bs[i])
+        kw = dict(kind=opts[i].kind, s=opts[i].s, zeta=opts[i].zeta, seed=opts[i].seed, sketch_prec=prec,
+                  qr_prec=O.FP64 if prec == O.FP64 else O.FP32, refine_steps=0)
+        ref = O.solve(A_np, b_np, **kw)
+        assert ref["info"] == 0
+        more = oracle_realizations(SimpleNamespace(A=A_np, b=b_np), **kw)
+        assert_solution_parity(to_np(xs[i]), ref["x"], to_np(x_star), kap, rho, f"problem {i}", refined=False,
+                               u_p=prec, realizations=more)

@@ -26,7 +26,8 @@ def set_tc(on):
 
 
 @pytest.mark.parametrize("prec", [O.BF16, O.FP16, O.FP8_E4M3])
-@pytest.mark.parametrize("m,n,s", [(5000, 200, 300), (1037, 113, 250), (20000, 64, 128), (300, 129, 130)])
+@pytest.mark.parametrize("m,n,s", [(5000, 200, 300), (1037, 113, 250), (20000, 64, 128), (300, 129, 130),
+                                   (3001, 300, 400), (2000, 512, 520)])
 def test_tensor_core_sketch_matches_oracle_and_cuda_cores(prec, m, n, s):
     rng = np.random.default_rng(m + n + s)
     A = np.asfortranarray(rng.standard_normal((m, n)) * np.exp2(rng.integers(-6, 6, n))[None, :])
@@ -137,7 +138,8 @@ def _sketch_both_ways(A, prec, s, seed, fp64):
     return As_tc, to_np(As_cc).astype(np.float64), to_np(ce)
 
 
-@pytest.mark.parametrize("m,n,s", [(1037, 113, 250), (20011, 70, 200), (300, 129, 130), (5000, 200, 300)])
+@pytest.mark.parametrize("m,n,s", [(1037, 113, 250), (20011, 70, 200), (300, 129, 130), (5000, 200, 300),
+                                   (3001, 300, 600), (1500, 520, 600)])
 def test_fp32_gaussian_sketch_bf16_pieces(m, n, s):
     # FP32 sketch as six BF16 piece products on the tensor cores: against the
     # oracle's sequential FP32 sum (worst-case bound) and, in norm, no less

@@ -105,3 +105,21 @@ def test_auto_sketch_solve(kap, want):
     assert ref["prec"] == want
     assert int(to_np(info)[0]) == 0
     assert_solution_parity(to_np(x), ref["x"], pr.x_star, kap, 1e-6, refined=False, u_p=want)
+
+
+@pytest.mark.parametrize("hpne", [False, True])
+@pytest.mark.parametrize("m,n,kap,rho,prec", [(6000, 200, 1e6, 1e-8, O.FP32), (100000, 400, 1e7, 1e-6, O.FP32),
+                                              (3000, 100, 1e2, 0.0, O.FP16), (5000, 150, 1e10, 1e-6, O.FP64)])
+def test_srft_solve_matches_oracle(hpne, m, n, kap, rho, prec):
+    # the paper's own sketch (Eq. e_sketch) with d = 3n (Sec. 6.2); 100000 x 400
+    # at kappa = 1e7, residual 1e-6 is the shape of the paper's GPU timing
+    # experiment (Fig. 6) with its smallest n
+    pr = P.make_problem(m, n, kap, rho, P.seed_for(5, n + int(np.log10(kap))))
+    qr = O.FP64 if prec == O.FP64 else O.FP32
+    kw = dict(kind=O.SRFT, s=3 * n, zeta=0, seed=13, sketch_prec=prec, qr_prec=qr, refine_steps=0)
+    x, info = lsq.solve(dev_colmajor(pr.A), torch.from_numpy(pr.b).cuda(), hpne=hpne, opts=lsq.make_opts(**kw))
+    ref = O.solve(pr.A, pr.b, hpne=hpne, **kw)
+    assert int(to_np(info)[0]) == ref["info"] == 0
+    more = oracle_realizations(pr, hpne=hpne, **kw)
+    assert_solution_parity(to_np(x), ref["x"], pr.x_star, kap, rho, "srft", refined=False, u_p=prec,
+                           realizations=more)
