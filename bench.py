@@ -56,7 +56,7 @@ def parse():
     p.add_argument("--no-oracle-parity", action="store_true")
     p.add_argument("--c4-problems", type=int, default=1024,
                    help="uneven problems of the learned-proposal evaluation (0: skip)")
-    p.add_argument("--ncu-case", choices=["pne32", "pne64", "sketch32", "sketch64"], default=None,
+    p.add_argument("--ncu-case", choices=["pne32", "pne64", "sketch32", "sketch64", "estimate"], default=None,
                    help="run a bounded case for an ncu capture (2 calls on one problem of the workload shape) and exit")
     p.add_argument("--ncu-m", type=int, default=M, help="rows of the ncu case")
     return p.parse_args()
@@ -103,6 +103,11 @@ def ncu_case(args):
         ws = lsq.workspace(lsq.OP_PNE, m, N, opts)
         for _ in range(2):
             lsq.pne(A, b, opts=opts, ws=ws)
+    elif args.ncu_case == "estimate":
+        # the condition estimate on a sketch alone (the first step of the
+        # mixed-precision solve)
+        for _ in range(2):
+            lsq.condest_sketch(A, seed=7)
     else:
         for _ in range(2):
             lsq.sketch(A, opts)
@@ -287,6 +292,10 @@ def roofline(stages, recs, per_solve_stage_ms, step_mix):
     cand = {}
     for key in ("k_ot_update", "k_qr_panel", "k_sketch_tc"):
         ms, cnt, work = stages[key]
+        if key == "k_ot_update":
+            # both forms of the update kernel: method work = tensor work / pairs
+            ms3, cnt3, work3 = stages.get("k_ot_update3", (0.0, 0, 0.0))
+            ms, cnt, work = ms + ms3, cnt + cnt3, (work, work3)
         if cnt:
             cand[key] = (ms, cnt, work)
     if not cand:
@@ -294,8 +303,11 @@ def roofline(stages, recs, per_solve_stage_ms, step_mix):
     top = max(cand, key=lambda k: cand[k][0])
     ms, cnt, work = cand[top]
     if top == "k_ot_update":
-        # 36 BF16 digit-pair products per FP64 product
-        emul, bound, unit_peak = 36.0, "tensor", peak
+        # 36 BF16 digit-pair products per FP64 product (21 in the three-digit
+        # form of the FP64 sketch)
+        w36, w21 = work
+        work = w36 + w21
+        emul, bound, unit_peak = work / (w36 / 36.0 + w21 / 21.0), "tensor", peak
         kname = "k_ot_update (FP64 products by BF16 digit slicing: TRSM updates, Cholesky updates, FP64 sketch)"
     elif top == "k_sketch_tc":
         # FP32 sketches: six BF16 piece products per FP32 product

@@ -582,15 +582,16 @@ int64_t lsq_launch_count(void);
  * indices: 0 condition estimate, 1 sketch, 2 QR, 3 TRSM A R_s^{-1},
  * 4 Gram + right-hand side, 5 factorization, 6 solves, 7 refinement;
  * 8 single launches of the tensor-core FP64 update kernel (lsq_trsm_tc,
- * the Cholesky updates, the K chunks of an FP64 Gaussian sketch), 9 single
- * launches of the QR panel kernel, 10 single launches of the tensor-core
- * sketch GEMM);
+ * the Cholesky updates), 9 single launches of the QR panel kernel, 10 single
+ * launches of the tensor-core sketch GEMM, 11 single launches of the update
+ * kernel with three-digit X (the K chunks of an FP64 Gaussian sketch));
  * lsq_profile(0) stops.  lsq_profile_collect waits for the recorded events,
  * writes the summed milliseconds and the number of records per stage
  * (arrays of at least 8; indices >= nstages are skipped), and clears the
  * records; lsq_profile_collect_work also writes the summed algorithmic work
  * per stage (flops: 36 digit-pair products of 2 M N K each for the update
- * kernel, the Householder panel flops for the QR panel, 2 M N K of the
+ * kernel, 21 for its three-digit form, the Householder panel flops for the
+ * QR panel, 2 M N K of the
  * launch's K for the sketch GEMM, which is six times the product's for an
  * FP32 sketch of BF16 pieces; 0 for the steps).
  * Host-side state, not thread safe across concurrent solves on different

@@ -110,7 +110,7 @@ def lib():
 
 
 STAGES = ["condest", "sketch", "qr", "trsm", "gram", "factor", "solve", "refine", "k_ot_update", "k_qr_panel",
-          "k_sketch_tc"]
+          "k_sketch_tc", "k_ot_update3"]
 
 
 def launch_count() -> int:

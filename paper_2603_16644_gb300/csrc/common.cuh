@@ -37,7 +37,7 @@ void note_launch();
 // FP64 update and the QR panel) with their algorithmic work (flops).
 enum Stage {
     ST_CONDEST = 0, ST_SKETCH, ST_QR, ST_TRSM, ST_GRAM, ST_FACTOR, ST_SOLVE, ST_REFINE,
-    ST_K_UPDATE, ST_K_QRPANEL, ST_K_SKETCHTC, ST_COUNT
+    ST_K_UPDATE, ST_K_QRPANEL, ST_K_SKETCHTC, ST_K_UPDATE3, ST_COUNT
 };
 void stage_mark(int stage, bool begin, cudaStream_t st, double work = 0.0);
 

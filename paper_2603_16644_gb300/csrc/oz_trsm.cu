@@ -802,12 +802,13 @@ lsq_status ot_gemm_update(const double* X, int64_t ldx, const double* Y, int64_t
     LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int ntj = (int)(U.Np / OT_BN), ntiles = (int)(ntj * (U.mp / OT_BM));
     const int grid = std::min(ntiles, device_sm_count());
-    stage_mark(ST_K_UPDATE, true, st);
+    const int stage = x_digits == 3 ? ST_K_UPDATE3 : ST_K_UPDATE;
+    stage_mark(stage, true, st);
     kern<<<grid, OT_THREADS, smem, st>>>(tx, ty, M, N, K, U.Ex, U.Ey, Cin, ldi, Cout, ldo, err, ntj, ntiles);
     LSQ_LAUNCH_CHECK();
     // tensor-core work: the digit pairs actually issued
     const double pairs = x_digits == 3 ? 21.0 : 36.0;
-    stage_mark(ST_K_UPDATE, false, st, pairs * 2.0 * (double)M * (double)N * (double)K);
+    stage_mark(stage, false, st, pairs * 2.0 * (double)M * (double)N * (double)K);
     return LSQ_OK;
 }
 
