@@ -159,9 +159,8 @@ SketchLayout sketch_layout(int64_t m, int64_t n, int64_t s, int kind, int zeta, 
         // signed, zero-padded and transformed columns (m' x n)
         L.ahat = o.take(srft_ws_bytes(m, n, prec));
     } else if (gauss_fp64_tc(prec)) {
-        // FP64: K chunks of Omega generated one at a time, digit-sliced
-        // tensor-core products accumulated into A_s (A is read in place)
-        L.om = o.take(sizeof(double) * (size_t)s * kSketchChunk);
+        // FP64: K chunks of Omega generated one at a time as the digit planes
+        // of tensor-core products accumulated into A_s (A is read in place)
         L.gemm = o.take(ot_update_ws_bytes(s, n, kSketchChunk));
     } else if (gauss_fp32_tc(prec)) {
         // FP32: three BF16 pieces per value, six K segments of length ldq
@@ -369,16 +368,18 @@ lsq_status run_sketch(const double* A, int64_t m, int64_t n, int64_t lda, const 
     }
     if (gauss_fp64_tc(prec)) {
         // A_s = sum over K chunks of Omega[:, chunk] A[chunk, :], each chunk an
-        // FP64-accurate product (C - (-Omega) A), accumulated in FP64
+        // FP64-accurate product (C - (-Omega) A), accumulated in FP64.  The
+        // chunk of -Omega is generated straight into the product's X digit
+        // planes: its entries lie on the 2^-17 grid below 8, three digits.
         double* As64 = (double*)As;
-        double* om = (double*)(base + L.om);
         LSQ_CUDA_TRY(cudaMemset2DAsync(As64, sizeof(double) * ldas, 0, sizeof(double) * o->s, n, st));
         for (int64_t k0 = 0; k0 < m; k0 += kSketchChunk) {
             const int64_t kc = std::min<int64_t>(kSketchChunk, m - k0);
-            if ((r = launch_gauss_negchunk(o->seed, o->s, o->row_offset + k0, kc, om, st)) != LSQ_OK) return r;
-            // Omega's entries lie on the 2^-17 grid below 8: three digits
-            if ((r = ot_gemm_update(om, o->s, A + k0, 1, lda, As64, ldas, As64, ldas, o->s, n, kc, base + L.gemm,
-                                    L.gemm_bytes, err, st, 0, nullptr, 0, 0, 3)) != LSQ_OK)
+            if ((r = ot_gauss_digits(o->seed, o->s, o->row_offset + k0, kc, n, base + L.gemm, L.gemm_bytes, st)) !=
+                LSQ_OK)
+                return r;
+            if ((r = ot_gemm_update(nullptr, o->s, A + k0, 1, lda, As64, ldas, As64, ldas, o->s, n, kc,
+                                    base + L.gemm, L.gemm_bytes, err, st, 2, nullptr, 0, 0, 3)) != LSQ_OK)
                 return r;
         }
         return LSQ_OK;

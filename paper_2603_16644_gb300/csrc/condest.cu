@@ -11,7 +11,6 @@
 // = +inf and double precision.  The whole decision stays on the device.
 #include "common.cuh"
 #include "kernels.cuh"
-#include "trsv_block.cuh"
 
 #include <algorithm>
 
@@ -26,136 +25,20 @@ __device__ __forceinline__ int prec_from_kappa0(double k0) {
     return LSQ_FP64;
 }
 
-// ||G||_1 of the symmetric FP32 matrix: column sums in row order, max.
-__global__ void k_norm1(const float* __restrict__ G, int64_t n, int64_t ld, float* __restrict__ out) {
-    float mx = 0.0f;
-    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
-        float s = 0.0f;
-        for (int64_t i = 0; i < n; ++i) s += fabsf(G[i + c * ld]);
-        mx = fmaxf(mx, s);
+// kappa0 = 0.5 log10(n ||G||_1 gamma) in FP64 from the FP32 norm and estimate
+// gamma of ||G^{-1}||_1, and the precision; the overflow case (a failed
+// factorization, a timed-out wait, a non-finite value) gives +inf and FP64.
+__global__ void k_condest_final(int64_t n, const float* __restrict__ norm1, const float* __restrict__ gamma,
+                                const int32_t* __restrict__ fail, const int32_t* __restrict__ err,
+                                double* __restrict__ kappa0, int32_t* __restrict__ chosen) {
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    double k0 = inf;
+    if (*fail == 0 && (!err || *err == 0) && isfinite(*norm1) && isfinite(*gamma)) {
+        const double prod = (double)n * (double)(*norm1) * (double)(*gamma);
+        k0 = (isfinite(prod) && prod > 0.0) ? 0.5 * log10(prod) : inf;
     }
-    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    __shared__ float w[32];
-    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.0f;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t = fmaxf(t, w[q]);
-        *out = t;
-    }
-}
-
-__device__ float blk_sum(float v, float* red) {
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    float t = 0.0f;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
-    return t;
-}
-
-__device__ int blk_argmax_abs(const float* z, int64_t n, float* redv, int* redi, float* outmax) {
-    float best = -1.0f;
-    int bi = 0x7fffffff;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        float v = fabsf(z[i]);
-        if (v > best) { best = v; bi = (int)i; }
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-        float ov = __shfl_xor_sync(0xffffffffu, best, off);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) { redv[threadIdx.x >> 5] = best; redi[threadIdx.x >> 5] = bi; }
-    __syncthreads();
-    float b = -1.0f;
-    int ix = 0x7fffffff;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
-        if (redv[q] > b || (redv[q] == b && redi[q] < ix)) { b = redv[q]; ix = redi[q]; }
-    *outmax = b;
-    return ix;
-}
-
-// Hager / Higham loop, one block; vectors in dynamic shared memory.
-__global__ void __launch_bounds__(512) k_hager(const float* __restrict__ L, int64_t n, int64_t ld,
-                                               const float* __restrict__ norm1, const int32_t* __restrict__ chol_info,
-                                               double* __restrict__ kappa0, int32_t* __restrict__ chosen) {
-    extern __shared__ __align__(16) unsigned char hraw[];
-    float* x = reinterpret_cast<float*>(hraw);
-    float* y = x + n;
-    float* xi = y + n;
-    float* z = xi + n;
-    __shared__ float redv[32];
-    __shared__ int redi[32];
-    __shared__ int flag;
-    int tid = threadIdx.x;
-    if (*chol_info != 0 || !isfinite(*norm1)) {
-        if (tid == 0) {
-            *kappa0 = __longlong_as_double(0x7ff0000000000000ll);
-            *chosen = LSQ_FP64;
-        }
-        return;
-    }
-    float fn = (float)n;
-    for (int64_t i = tid; i < n; i += blockDim.x) { x[i] = 1.0f / fn; y[i] = 1.0f / fn; }
-    block_trsv<float>(TB_LOWER, L, n, ld, y);
-    block_trsv<float>(TB_LOWER_T, L, n, ld, y);
-    float ps = 0.0f;
-    for (int64_t i = tid; i < n; i += blockDim.x) ps += fabsf(y[i]);
-    float est = blk_sum(ps, redv);
-    for (int64_t i = tid; i < n; i += blockDim.x) { xi[i] = y[i] >= 0.0f ? 1.0f : -1.0f; z[i] = xi[i]; }
-    block_trsv<float>(TB_LOWER, L, n, ld, z);
-    block_trsv<float>(TB_LOWER_T, L, n, ld, z);
-    int jlast = -1;
-    for (int it = 1; it < 5; ++it) {
-        float zmax;
-        int j = blk_argmax_abs(z, n, redv, redi, &zmax);
-        float pz = 0.0f;
-        for (int64_t i = tid; i < n; i += blockDim.x) pz += z[i] * x[i];
-        float ztx = blk_sum(pz, redv);
-        if (zmax <= ztx || j == jlast) break;
-        jlast = j;
-        for (int64_t i = tid; i < n; i += blockDim.x) { x[i] = (i == j) ? 1.0f : 0.0f; y[i] = x[i]; }
-        block_trsv<float>(TB_LOWER, L, n, ld, y);
-        block_trsv<float>(TB_LOWER_T, L, n, ld, y);
-        float py = 0.0f;
-        int differ = 0;
-        for (int64_t i = tid; i < n; i += blockDim.x) {
-            py += fabsf(y[i]);
-            differ |= ((y[i] >= 0.0f ? 1.0f : -1.0f) != xi[i]);
-        }
-        float est_new = blk_sum(py, redv);
-        if (tid == 0) flag = 0;
-        __syncthreads();
-        if (differ) flag = 1;
-        __syncthreads();
-        if (!flag || est_new <= est) {
-            if (est_new > est) est = est_new;
-            break;
-        }
-        est = est_new;
-        for (int64_t i = tid; i < n; i += blockDim.x) { xi[i] = y[i] >= 0.0f ? 1.0f : -1.0f; z[i] = xi[i]; }
-        block_trsv<float>(TB_LOWER, L, n, ld, z);
-        block_trsv<float>(TB_LOWER_T, L, n, ld, z);
-    }
-    for (int64_t i = tid; i < n; i += blockDim.x) {
-        float mag = n > 1 ? 1.0f + (float)i / (float)(n - 1) : 1.0f;
-        y[i] = (i % 2 == 0) ? mag : -mag;
-    }
-    block_trsv<float>(TB_LOWER, L, n, ld, y);
-    block_trsv<float>(TB_LOWER_T, L, n, ld, y);
-    float pa = 0.0f;
-    for (int64_t i = tid; i < n; i += blockDim.x) pa += fabsf(y[i]);
-    float alt = 2.0f * blk_sum(pa, redv) / (3.0f * fn);
-    if (alt > est) est = alt;
-    if (tid == 0) {
-        double prod = (double)n * (double)(*norm1) * (double)est;
-        double k0 = (isfinite(prod) && prod > 0.0) ? 0.5 * log10(prod) : __longlong_as_double(0x7ff0000000000000ll);
-        *kappa0 = k0;
-        *chosen = prec_from_kappa0(k0);
-    }
+    *kappa0 = k0;
+    *chosen = prec_from_kappa0(k0);
 }
 
 __global__ void k_err_to_info(const int32_t* __restrict__ err, int32_t* __restrict__ info) {
@@ -163,7 +46,7 @@ __global__ void k_err_to_info(const int32_t* __restrict__ err, int32_t* __restri
 }
 
 struct CondLayout {
-    size_t g, norm, info, err, gemm, gemm_bytes, z, total;
+    size_t g, norm, info, err, gemm, gemm_bytes, z, gam, herr, hg, hg_bytes, total;
     bool tc;
     int64_t ldz;
 };
@@ -187,6 +70,10 @@ static CondLayout cond_layout(int64_t m, int64_t n, int num_sms) {
         L.gemm_bytes = gemm_kmajor_ws_bytes(plan_gemm_kmajor(n, n, m, true, LSQ_FP32, num_sms));
     }
     L.gemm = take(L.gemm_bytes);
+    L.gam = take(sizeof(float));
+    L.herr = take(sizeof(int32_t));
+    L.hg_bytes = hager_ws_bytes(n);
+    L.hg = take(L.hg_bytes);
     L.total = off + 256;
     return L;
 }
@@ -216,8 +103,7 @@ lsq_status launch_condest(const double* A, int64_t m, int64_t n, int64_t lda, do
     if (r != LSQ_OK) return r;
     // row-sharded A: A^T A summed over the shards
     if ((r = reduce_partial(G, n * n, LSQ_REDUCE_SUM_F32, st)) != LSQ_OK) return r;
-    k_norm1<<<1, 1024, 0, st>>>(G, n, n, nrm);
-    LSQ_LAUNCH_CHECK();
+    if ((r = launch_colnorm1_max(G, n, n, false, nrm, st)) != LSQ_OK) return r;
     LSQ_CUDA_TRY(cudaMemsetAsync(cinfo, 0, sizeof(int32_t), st));
     r = launch_cholesky<float>(G, n, n, cinfo, st);
     if (r != LSQ_OK) return r;
@@ -226,10 +112,12 @@ lsq_status launch_condest(const double* A, int64_t m, int64_t n, int64_t lda, do
         k_err_to_info<<<1, 1, 0, st>>>((const int32_t*)(base + L.err), cinfo);
         LSQ_LAUNCH_CHECK();
     }
-    size_t smem = sizeof(float) * 4 * (size_t)n;
-    if (smem > 200 * 1024) return LSQ_ERR_ARG;
-    if (smem > 48 * 1024) LSQ_CUDA_TRY(cudaFuncSetAttribute(k_hager, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_hager<<<1, 512, smem, st>>>(G, n, n, nrm, cinfo, kappa0, chosen);
+    // gamma ~ ||G^{-1}||_1 through the Cholesky factor (lower triangle of G)
+    float* gam = (float*)(base + L.gam);
+    int32_t* herr = (int32_t*)(base + L.herr);
+    LSQ_CUDA_TRY(cudaMemsetAsync(herr, 0, sizeof(int32_t), st));
+    if ((r = hager_inv_norm1(G, n, n, false, cinfo, gam, herr, base + L.hg, L.hg_bytes, st)) != LSQ_OK) return r;
+    k_condest_final<<<1, 1, 0, st>>>(n, nrm, gam, cinfo, herr, kappa0, chosen);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
 }
@@ -271,7 +159,7 @@ __global__ void k_sketch_guard(const int32_t* __restrict__ accept, double* __res
 }
 
 size_t condest_sketch_finish_ws_bytes(int64_t n) {
-    return align_up(sizeof(float) * (size_t)n * n, 256) + 512;
+    return align_up(sizeof(float) * (size_t)n * n, 256) + 256 + hager_ws_bytes(n) + 256;
 }
 
 lsq_status launch_condest_sketch_finish(float* G, const int32_t* colexp, const double* Re, int64_t n, int64_t ldr,
@@ -280,22 +168,24 @@ lsq_status launch_condest_sketch_finish(float* G, const int32_t* colexp, const d
     if (!ws || ws_bytes < condest_sketch_finish_ws_bytes(n)) return LSQ_ERR_NOMEM;
     char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
     float* L = (float*)base;
-    float* nrm = (float*)(base + align_up(sizeof(float) * (size_t)n * n, 256));
-    int32_t* cinfo = (int32_t*)(nrm + 1);
+    char* small = base + align_up(sizeof(float) * (size_t)n * n, 256);
+    float* nrm = (float*)small;
+    int32_t* cinfo = (int32_t*)(small + 4);
+    float* gam = (float*)(small + 8);
+    int32_t* herr = (int32_t*)(small + 12);
+    char* hg = small + 256;
     const unsigned g = (unsigned)std::min<int64_t>(ceil_div(n * n, 256), 8192);
     if (colexp) {
         k_unscale_gram<<<g, 256, 0, st>>>(G, n, colexp);
         LSQ_LAUNCH_CHECK();
     }
-    k_norm1<<<1, 1024, 0, st>>>(G, n, n, nrm);
-    LSQ_LAUNCH_CHECK();
+    lsq_status r;
+    if ((r = launch_colnorm1_max(G, n, n, false, nrm, st)) != LSQ_OK) return r;
     k_lower_from_upper<<<g, 256, 0, st>>>(Re, n, ldr, L);
     LSQ_LAUNCH_CHECK();
-    LSQ_CUDA_TRY(cudaMemsetAsync(cinfo, 0, sizeof(int32_t), st));
-    size_t smem = sizeof(float) * 4 * (size_t)n;
-    if (smem > 200 * 1024) return LSQ_ERR_ARG;
-    if (smem > 48 * 1024) LSQ_CUDA_TRY(cudaFuncSetAttribute(k_hager, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_hager<<<1, 512, smem, st>>>(L, n, n, nrm, cinfo, kappa0, chosen);
+    LSQ_CUDA_TRY(cudaMemsetAsync(small + 4, 0, 12, st));  // cinfo, gamma, herr
+    if ((r = hager_inv_norm1(L, n, n, false, cinfo, gam, herr, hg, hager_ws_bytes(n), st)) != LSQ_OK) return r;
+    k_condest_final<<<1, 1, 0, st>>>(n, nrm, gam, cinfo, herr, kappa0, chosen);
     LSQ_LAUNCH_CHECK();
     k_sketch_guard<<<1, 1, 0, st>>>(accept, kappa0, chosen);
     LSQ_LAUNCH_CHECK();

@@ -63,7 +63,6 @@ size_t srft_ws_bytes(int64_t m, int64_t n, int prec);
 lsq_status launch_srft(const double* A, int64_t m, int64_t n, int64_t lda, const int32_t* colexp, int prec,
                        uint64_t seed, int64_t s, void* W, void* As, int64_t ldas, cudaStream_t st);
 // Columns [k0, k0 + kc) of -Omega (FP64), s x kc column-major, ld s.
-lsq_status launch_gauss_negchunk(uint64_t seed, int64_t s, int64_t k0, int64_t kc, double* Om, cudaStream_t st);
 
 // ---- gemm.cu: dense contractions on CUDA cores ------------------------------
 // C (M x N, column-major, ldc) = sum_k X[i*ldx + k] * Y[j*ldy + k]  (both
@@ -141,6 +140,7 @@ lsq_status ot_trsm(const double* A, int64_t m, int64_t n, int64_t lda, const dou
                    int64_t ldap, void* ws, size_t ws_bytes, int32_t* err, cudaStream_t st);
 // C_out = C_in - X Y with FP64 accuracy on the tensor cores (X: M x K
 // column-major, ld ldx; Y entry (k, j) at Y[k sk + j sj]; K <= 512).
+// xmode 2: X's digit planes were written by ot_gauss_digits (X unused).
 // x_digits = 3 when every row of X has at most three nonzero balanced
 // base-128 digits below its maximum (X on a 2^-17 grid, |X| < 8: the
 // Gaussian sketch operator); the product is then the same with 21 digit
@@ -150,6 +150,23 @@ lsq_status ot_gemm_update(const double* X, int64_t ldx, const double* Y, int64_t
                           int64_t ldi, double* Cout, int64_t ldo, int64_t M, int64_t N, int64_t K, void* ws,
                           size_t ws_bytes, int32_t* err, cudaStream_t st, int xmode = 0,
                           const int32_t* Eblk = nullptr, int64_t b0 = 0, int nbk = 0, int x_digits = 8);
+// The negated Gaussian operator's columns j0 .. j0 + kc - 1 (rows 0 .. s - 1,
+// kc <= 512) written as the X digit planes of an update's scratch ws (the
+// scratch of ot_gemm_update with M = s, N, K = kc), for ot_gemm_update with
+// xmode = 2 and x_digits = 3.
+lsq_status ot_gauss_digits(uint64_t seed, int64_t s, int64_t j0, int64_t kc, int64_t N, void* ws, size_t ws_bytes,
+                           cudaStream_t st);
+
+// ---- hager.cu ----------------------------------------------------------------
+// Hager's estimate of ||M^{-1}||_1 in FP32 into *est (device), M n x n
+// (ld ld): (L L^T)^{-1} for L lower (upper = false) or R^{-1} for R upper.
+// fail (device, may be NULL): nonzero skips every solve (*est = +inf);
+// err: set to -2 when a wavefront solve's wait times out.
+size_t hager_ws_bytes(int64_t n);
+lsq_status hager_inv_norm1(const float* M, int64_t n, int64_t ld, bool upper, const int32_t* fail, float* est,
+                           int32_t* err, void* ws, size_t ws_bytes, cudaStream_t st);
+// ||M||_1 (upper: of the upper triangle) into *out (device float).
+lsq_status launch_colnorm1_max(const float* M, int64_t n, int64_t ld, bool upper, float* out, cudaStream_t st);
 
 // ---- qr.cu -------------------------------------------------------------------
 size_t qr_ws_bytes(int64_t s, int64_t n, int prec);

@@ -6,12 +6,12 @@
 //     forward, backward (per-sample deltas, then per-parameter sums over the
 //     batch in sample order: deterministic) and Adam;
 //   - the judge: Hager's 1-norm estimate (Sec. 6.1's estimator, single
-//     precision) of kappa_1(R_s) for a computed preconditioner; a precision
+//     precision, csrc/hager.cu) of kappa_1(R_s) for a computed
+//     preconditioner; a precision
 //     u_p is accepted when u_p * kappa_1(R_s) <= 1, the regime of Lemma
 //     rscond (eps * kappa(R_s) < 1).
 #include "common.cuh"
 #include "kernels.cuh"
-#include "trsv_block.cuh"
 
 #include <algorithm>
 
@@ -264,110 +264,17 @@ __global__ void k_to_f32_upper(const double* __restrict__ R, int64_t n, int64_t 
     }
 }
 
-__device__ float jsum(float v, float* red) {
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    float t = 0.0f;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
-    return t;
-}
-
-__global__ void __launch_bounds__(512) k_judge(const float* __restrict__ R, int64_t n, int prec,
-                                               int32_t* __restrict__ accept, double* __restrict__ kappa1) {
-    extern __shared__ __align__(16) unsigned char jraw[];
-    float* x = reinterpret_cast<float*>(jraw);
-    float* y = x + n;
-    float* xi = y + n;
-    float* z = xi + n;
-    __shared__ float red[32];
-    __shared__ float rv[32];
-    __shared__ int ri[32];
-    __shared__ int flag;
-    int tid = threadIdx.x;
-    // ||R||_1: largest column sum
-    float cm = 0.0f;
-    for (int64_t c = tid; c < n; c += blockDim.x) {
-        float s = 0.0f;
-        for (int64_t i = 0; i <= c; ++i) s += fabsf(R[i + c * n]);
-        cm = fmaxf(cm, s);
-    }
-    for (int off = 16; off > 0; off >>= 1) cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, off));
-    if ((tid & 31) == 0) red[tid >> 5] = cm;
-    __syncthreads();
-    float rnorm = 0.0f;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) rnorm = fmaxf(rnorm, red[q]);
-    __syncthreads();
-    float fn = (float)n;
-    for (int64_t i = tid; i < n; i += blockDim.x) { x[i] = 1.0f / fn; y[i] = 1.0f / fn; }
-    block_trsv<float>(TB_UPPER, R, n, n, y);
-    float ps = 0.0f;
-    for (int64_t i = tid; i < n; i += blockDim.x) ps += fabsf(y[i]);
-    float est = jsum(ps, red);
-    for (int64_t i = tid; i < n; i += blockDim.x) { xi[i] = y[i] >= 0.0f ? 1.0f : -1.0f; z[i] = xi[i]; }
-    block_trsv<float>(TB_UPPER_T, R, n, n, z);
-    int jlast = -1;
-    for (int it = 1; it < 5; ++it) {
-        float best = -1.0f;
-        int bi = 0x7fffffff;
-        for (int64_t i = tid; i < n; i += blockDim.x)
-            if (fabsf(z[i]) > best) { best = fabsf(z[i]); bi = (int)i; }
-        for (int off = 16; off > 0; off >>= 1) {
-            float ov = __shfl_xor_sync(0xffffffffu, best, off);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-        }
-        __syncthreads();
-        if ((tid & 31) == 0) { rv[tid >> 5] = best; ri[tid >> 5] = bi; }
-        __syncthreads();
-        float zmax = -1.0f;
-        int j = 0x7fffffff;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
-            if (rv[q] > zmax || (rv[q] == zmax && ri[q] < j)) { zmax = rv[q]; j = ri[q]; }
-        float pz = 0.0f;
-        for (int64_t i = tid; i < n; i += blockDim.x) pz += z[i] * x[i];
-        float ztx = jsum(pz, red);
-        if (zmax <= ztx || j == jlast) break;
-        jlast = j;
-        for (int64_t i = tid; i < n; i += blockDim.x) { x[i] = (i == j) ? 1.0f : 0.0f; y[i] = x[i]; }
-        block_trsv<float>(TB_UPPER, R, n, n, y);
-        float py = 0.0f;
-        int differ = 0;
-        for (int64_t i = tid; i < n; i += blockDim.x) {
-            py += fabsf(y[i]);
-            differ |= ((y[i] >= 0.0f ? 1.0f : -1.0f) != xi[i]);
-        }
-        float est_new = jsum(py, red);
-        if (tid == 0) flag = 0;
-        __syncthreads();
-        if (differ) flag = 1;
-        __syncthreads();
-        if (!flag || est_new <= est) {
-            if (est_new > est) est = est_new;
-            break;
-        }
-        est = est_new;
-        for (int64_t i = tid; i < n; i += blockDim.x) { xi[i] = y[i] >= 0.0f ? 1.0f : -1.0f; z[i] = xi[i]; }
-        block_trsv<float>(TB_UPPER_T, R, n, n, z);
-    }
-    for (int64_t i = tid; i < n; i += blockDim.x) {
-        float mag = n > 1 ? 1.0f + (float)i / (float)(n - 1) : 1.0f;
-        y[i] = (i % 2 == 0) ? mag : -mag;
-    }
-    block_trsv<float>(TB_UPPER, R, n, n, y);
-    float pa = 0.0f;
-    for (int64_t i = tid; i < n; i += blockDim.x) pa += fabsf(y[i]);
-    float alt = 2.0f * jsum(pa, red) / (3.0f * fn);
-    if (alt > est) est = alt;
-    if (tid == 0) {
-        double k1 = (double)rnorm * (double)est;
-        double u = prec == LSQ_FP8_E4M3 ? 0x1p-4 : prec == LSQ_BF16 ? 0x1p-8 : prec == LSQ_FP16 ? 0x1p-11
-                 : prec == LSQ_FP32 ? 0x1p-24 : 0x1p-53;
-        bool finite = isfinite(k1) && k1 > 0.0;
-        *kappa1 = finite ? k1 : __longlong_as_double(0x7ff0000000000000ll);
-        *accept = (finite && u * k1 <= 1.0) ? 1 : 0;
-    }
+// kappa_1(R) = ||R||_1 gamma (gamma ~ ||R^{-1}||_1) and the judgement
+// u_p kappa_1(R) <= 1; a non-finite value or a timed-out solve rejects.
+__global__ void k_judge_final(const float* __restrict__ rnorm, const float* __restrict__ gamma,
+                              const int32_t* __restrict__ err, int prec, int32_t* __restrict__ accept,
+                              double* __restrict__ kappa1) {
+    const double k1 = (double)(*rnorm) * (double)(*gamma);
+    const double u = prec == LSQ_FP8_E4M3 ? 0x1p-4 : prec == LSQ_BF16 ? 0x1p-8 : prec == LSQ_FP16 ? 0x1p-11
+                   : prec == LSQ_FP32 ? 0x1p-24 : 0x1p-53;
+    const bool finite = isfinite(k1) && k1 > 0.0 && *err == 0;
+    *kappa1 = finite ? k1 : __longlong_as_double(0x7ff0000000000000ll);
+    *accept = (finite && u * k1 <= 1.0) ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -432,18 +339,24 @@ lsq_status launch_propose(const float* logits, int32_t* prec, float* probs, cuda
     return LSQ_OK;
 }
 
-size_t judge_ws_bytes(int64_t n) { return align_up(sizeof(float) * (size_t)n * n, 256) + 256; }
+size_t judge_ws_bytes(int64_t n) { return align_up(sizeof(float) * (size_t)n * n, 256) + 256 + hager_ws_bytes(n) + 256; }
 
 lsq_status launch_judge(const double* Rs, int64_t n, int64_t ldr, int prec, int32_t* accept, double* kappa1, void* ws,
                         size_t ws_bytes, cudaStream_t st) {
     if (!ws || ws_bytes < judge_ws_bytes(n)) return LSQ_ERR_NOMEM;
     float* Rf = (float*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    char* small = (char*)Rf + align_up(sizeof(float) * (size_t)n * n, 256);
+    float* rnorm = (float*)small;
+    float* gam = (float*)(small + 4);
+    int32_t* herr = (int32_t*)(small + 8);
     k_to_f32_upper<<<(unsigned)std::min<int64_t>(ceil_div(n * n, 256), 4096), 256, 0, st>>>(Rs, n, ldr, Rf);
     LSQ_LAUNCH_CHECK();
-    size_t smem = sizeof(float) * 4 * (size_t)n;
-    if (smem > 200 * 1024) return LSQ_ERR_ARG;
-    if (smem > 48 * 1024) LSQ_CUDA_TRY(cudaFuncSetAttribute(k_judge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_judge<<<1, 512, smem, st>>>(Rf, n, prec, accept, kappa1);
+    lsq_status r;
+    if ((r = launch_colnorm1_max(Rf, n, n, true, rnorm, st)) != LSQ_OK) return r;
+    LSQ_CUDA_TRY(cudaMemsetAsync(herr, 0, sizeof(int32_t), st));
+    if ((r = hager_inv_norm1(Rf, n, n, true, nullptr, gam, herr, small + 256, hager_ws_bytes(n), st)) != LSQ_OK)
+        return r;
+    k_judge_final<<<1, 1, 0, st>>>(rnorm, gam, herr, prec, accept, kappa1);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
 }

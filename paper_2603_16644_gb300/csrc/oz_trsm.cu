@@ -26,6 +26,7 @@
 // Per product the dropped pairs and the truncations r contribute below
 // 2^-52.6 * 2^(Ex_i + Ey_j), the order of FP64 rounding.
 #include "common.cuh"
+#include "gauss.cuh"
 #include "kernels.cuh"
 #include "tcgen05.cuh"
 
@@ -58,6 +59,9 @@ __device__ __forceinline__ int32_t ot_exp_of_max(unsigned long long mx) {
     return (Eb > 1 ? Eb : 1) - 1022;  // every |x| < 2^E
 }
 
+constexpr unsigned long long OT_BIAS =
+    64ull * ((1ull << 42) + (1ull << 35) + (1ull << 28) + (1ull << 21) + (1ull << 14) + (1ull << 7) + 1ull);
+
 // Balanced base-128 digits of x with |x| < 2^E (see the file comment), as
 // the fields of W = V + BIAS, V = trunc(x 2^(55 - E)) in two's complement:
 // adding 64 to every lower 7-bit field makes each field t >= 1 equal to
@@ -77,9 +81,7 @@ __device__ __forceinline__ unsigned long long ot_fields(double x, int32_t E) {
         const int sh = (Eb != 0 ? Eb : 1) - (E + 1022) + 2;  // <= 2, so V < 2^55
         V = sh >= 0 ? (sig << sh) : (sh > -64 ? (sig >> (-sh)) : 0ull);
     }
-    constexpr unsigned long long BIAS = 64ull * ((1ull << 42) + (1ull << 35) + (1ull << 28) + (1ull << 21) +
-                                                 (1ull << 14) + (1ull << 7) + 1ull);
-    return (neg ? 0ull - V : V) + BIAS;
+    return (neg ? 0ull - V : V) + OT_BIAS;
 }
 
 // Digit t of W as an FP32 value: 2^23 1.5 + field, minus the same plus 64
@@ -728,6 +730,34 @@ size_t ot_update_ws_bytes(int64_t M, int64_t N, int64_t K) {
            align_up(sizeof(uint16_t) * OT_DIG * (size_t)Np * Kp, 256) + align_up(sizeof(int32_t) * Np, 256) + 256;
 }
 
+// The negated Gaussian sketch operator's K chunk as the update's X digit
+// planes: rows i < s of -Omega, columns j0 .. j0 + kc - 1 (global indices of
+// Omega's columns), entries -q 2^-17 (csrc/gauss.cuh) sliced with the fixed
+// row exponent E = 3 (|Omega| < 8): V = -q 2^35, so only digits 0..2 can be
+// nonzero and only those planes are written.  Rows s <= i < mp and columns
+// kc <= k < Kp are zero.  One warp per row and 64 columns (two per lane):
+// each plane's row segment is one 128-byte store.
+__global__ void __launch_bounds__(256) k_ot_gauss_digits(const ZigTable tab, uint64_t seed, int64_t s, int64_t j0,
+                                                         int64_t kc, int64_t mp, int64_t Kp,
+                                                         uint16_t* __restrict__ Z, int32_t* __restrict__ Ex) {
+    __shared__ ZigShared Zs;
+    zig_stage(tab, Zs);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t k = (int64_t)blockIdx.x * 64 + 2 * lane;
+    for (int64_t i = (int64_t)blockIdx.y * 8 + warp; i < mp; i += (int64_t)gridDim.y * 8) {
+        unsigned long long W[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int32_t q = (i < s && k + h < kc) ? gauss_q(seed, i, j0 + k + h, Zs) : 0;
+            W[h] = (unsigned long long)(-(long long)q * (1ll << 35)) + OT_BIAS;
+        }
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+            *(uint32_t*)(Z + ((int64_t)t * mp + i) * Kp + k) = ot_digit_pair(W[0], W[1], t);
+        if (blockIdx.x == 0 && lane == 0) Ex[i] = 3;
+    }
+}
+
 // Pieces of an update's scratch: X digit planes and row exponents, then the Y
 // digit planes and column exponents.
 struct OtUpd {
@@ -754,6 +784,16 @@ static OtUpd ot_upd_ptrs(void* ws, int64_t M, int64_t N, int64_t K) {
     return U;
 }
 
+lsq_status ot_gauss_digits(uint64_t seed, int64_t s, int64_t j0, int64_t kc, int64_t N, void* ws, size_t ws_bytes,
+                           cudaStream_t st) {
+    if (s <= 0 || kc <= 0 || kc > OT_KMAX || !ws || ws_bytes < ot_update_ws_bytes(s, N, kc)) return LSQ_ERR_ARG;
+    const OtUpd U = ot_upd_ptrs(ws, s, N, kc);
+    const dim3 grid((unsigned)(U.Kp / 64), (unsigned)std::min<int64_t>(ceil_div(U.mp, 8), 256));
+    k_ot_gauss_digits<<<grid, 256, 0, st>>>(zig_table(), seed, s, j0, kc, U.mp, U.Kp, U.Zx, U.Ex);
+    LSQ_LAUNCH_CHECK();
+    return LSQ_OK;
+}
+
 // C_out = C_in - X Y (M x N; X: M x K column-major, ld ldx; Y: entry (k, j)
 // at Y[k sk + j sj]) with FP64 accuracy on the tensor cores; K <= 512.
 // C_in may equal C_out (same ld).  xmode: 0 slice X here; 1 slice X with the
@@ -767,7 +807,11 @@ lsq_status ot_gemm_update(const double* X, int64_t ldx, const double* Y, int64_t
         return LSQ_ERR_ARG;
     const OtUpd U = ot_upd_ptrs(ws, M, N, K);
     CUtensorMap tzs, txs;
-    if (xmode == 1 && ot_map(&tzs, U.Zx, U.Kp, U.mp, OT_RS_ROWS)) {
+    if (xmode == 2) {
+        // X's digit planes and row exponents are already in the scratch
+        // (ot_gauss_digits), three digits per value
+        if (x_digits != 3) return LSQ_ERR_ARG;
+    } else if (xmode == 1 && ot_map(&tzs, U.Zx, U.Kp, U.mp, OT_RS_ROWS)) {
         const dim3 rg((unsigned)(U.mp / OT_RS_ROWS), (unsigned)(U.Kp / 64));
         if (ldx % 2 == 0 && ((uintptr_t)X % 16) == 0 && ot_map_f64(&txs, X, M, K, ldx)) {
             const size_t rsm = 1024 + (size_t)OT_DIG * OT_RS_ROWS * 128 + (size_t)OT_RS_ROWS * 64 * 8;

@@ -7,6 +7,7 @@
 //   - Gaussian operator generation (ziggurat in FP64, rounded to u_p).
 // The Gaussian product itself is a dense contraction (gemm.cu / sketch_tc.cu).
 #include "common.cuh"
+#include "gauss.cuh"
 #include "kernels.cuh"
 
 #include <algorithm>
@@ -360,45 +361,12 @@ __global__ void __launch_bounds__(256) k_sparse_gather_v(const int32_t* __restri
 }
 
 // ---------------------------------------------------------------------------
-// Gaussian entries by the ziggurat of Marsaglia & Tsang (J. Stat. Softw. 5(8),
-// 2000) with 256 layers of equal area v under f(x) = exp(-x^2 / 2), x >= 0:
-//   layer 0     the rectangle [0, r] x [0, f(r)] plus the tail x > r, drawn
-//               as a rectangle of width x_0 = v / f(r);
-//   layer i>=1  [0, x_i] x [f(x_i), f(x_{i+1})]: f(x_{i+1}) = f(x_i) + v / x_i,
-//               x_1 = r, x_256 = 0;
-// v = r f(r) + sqrt(pi/2) erfc(r / sqrt 2), r = 3.6541528853610088 (the root
-// of the closure f(x_255) + v / x_255 = 1).  The tables are built once on
-// the host in FP64 (no fused multiply-adds: the library's host code is built
-// with -ffp-contract=off) and passed to the kernels by value.
-//
-// Entry (i, j): round k takes the Philox block of counter (i, j_lo, j_hi,
-// 2 + 256 k).  A first-kind round: layer L = w0 & 255, sign = bit 8 of w0,
-// U = (2^30 (w0 >> 9) + (w1 >> 2)) 2^-53, V = (2^26 (w2 >> 5) + (w3 >> 6))
-// 2^-53; z = U x_L is kept if z < x_{L+1}, or (L >= 1) if
-// f(x_L) + V (f(x_{L+1}) - f(x_L)) < exp(-z^2 / 2); in layer 0 past r the
-// following rounds sample the tail (Marsaglia 1964): U1, U2 = V + 2^-53 from
-// (w0, w1) and (w2, w3), e1 = -ln(U1) / r, e2 = -ln(U2), kept when
-// 2 e2 > e1^2, giving r + e1.  At most 64 rounds (then 0; the chance of
-// getting there is below 1e-100).  Products and sums are explicitly rounded,
-// so the draw equals a plain sequential FP64 evaluation up to the accuracy
-// of exp and log, which only the rare slow paths call.
-//
-// The entry is the draw rounded to the nearest multiple of 2^-17 (ties to
-// even), clamped to |Omega| <= 8 - 2^-17: 20 significant bits, so every entry
-// is an FP32 value, and below any row maximum under 8 it has only three
-// nonzero balanced base-128 digits -- the FP64 sketch's digit-sliced product
-// then needs 21 digit pairs instead of 36.
+// Gaussian operator (the ziggurat and its grid: csrc/gauss.cuh).  The tables:
+// x_L and f(x_L) by the equal-area recurrence in FP64, and the first round's
+// integer acceptance bounds K_L = min{u : fl(u (x_L 2^-53)) >= x_{L+1}} by
+// bisection with the same FP64 product.
 // ---------------------------------------------------------------------------
-constexpr int kZigN = 256;
-constexpr double kZigR = 3.6541528853610088;
-constexpr uint32_t kZigRounds = 64;
-
-struct ZigTable {
-    double x[kZigN + 1];
-    double f[kZigN + 1];
-};
-
-static const ZigTable& zig_table() {
+const ZigTable& zig_table() {
     static const ZigTable t = [] {
         ZigTable z{};
         const double fr = std::exp(-0.5 * kZigR * kZigR);
@@ -415,82 +383,19 @@ static const ZigTable& zig_table() {
         }
         z.x[kZigN] = 0.0;
         z.f[kZigN] = 1.0;
+        for (int L = 0; L < kZigN; ++L) {
+            const double xs = z.x[L] * 0x1p-53;
+            unsigned long long lo = 0, hi = 1ull << 53;  // the answer lies in [lo, hi]
+            while (lo < hi) {
+                const unsigned long long mid = lo + (hi - lo) / 2;
+                if ((double)mid * xs >= z.x[L + 1]) hi = mid;
+                else lo = mid + 1;
+            }
+            z.kfast[L] = lo;
+        }
         return z;
     }();
     return t;
-}
-
-// The tables in shared memory: x_L 2^-53 (the proposal is one product with
-// the 53-bit integer), x_L, f(x_L).
-struct ZigShared {
-    double xs[kZigN + 1], x[kZigN + 1], f[kZigN + 1];
-};
-
-__device__ __forceinline__ void zig_stage(const ZigTable& t, ZigShared& z) {
-    for (int q = threadIdx.x; q <= kZigN; q += blockDim.x) {
-        z.xs[q] = t.x[q] * 0x1p-53;
-        z.x[q] = t.x[q];
-        z.f[q] = t.f[q];
-    }
-    __syncthreads();
-}
-
-__device__ __forceinline__ double zig_grid(double z) {
-    constexpr double lim = 8.0 - 0x1p-17;
-    const double q = __dmul_rn(rint(__dmul_rn(z, 131072.0)), 0x1p-17);
-    return q > lim ? lim : (q < -lim ? -lim : q);
-}
-
-__device__ __forceinline__ double zig_uniform53(uint32_t a, uint32_t b) {
-    return (double)(((uint64_t)(a >> 5) << 26) | (b >> 6)) * 0x1p-53;
-}
-
-__device__ __noinline__ double gauss_slow(uint64_t seed, int64_t i, int64_t j, const ZigShared& Z, U4 w, double z,
-                                          int L, bool neg) {
-    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    bool tail = L == 0;
-    for (uint32_t k = 0; k < kZigRounds; ++k) {
-        if (k > 0) {
-            w = philox(U4{(uint32_t)i, (uint32_t)j, (uint32_t)((uint64_t)j >> 32), 2u + 256u * k}, k0, k1);
-            if (!tail) {
-                L = (int)(w.x & 255u);
-                neg = (w.x >> 8) & 1u;
-                z = __dmul_rn((double)(((uint64_t)(w.x >> 9) << 30) | (w.y >> 2)), Z.xs[L]);
-                if (z < Z.x[L + 1]) return zig_grid(neg ? -z : z);
-                if (L == 0) {
-                    tail = true;
-                    continue;
-                }
-            } else {
-                const double u1 = __dadd_rn(zig_uniform53(w.x, w.y), 0x1p-53);
-                const double u2 = __dadd_rn(zig_uniform53(w.z, w.w), 0x1p-53);
-                const double e1 = __ddiv_rn(-log(u1), kZigR);
-                const double e2 = -log(u2);
-                if (__dadd_rn(e2, e2) > __dmul_rn(e1, e1)) {
-                    const double t = __dadd_rn(kZigR, e1);
-                    return zig_grid(neg ? -t : t);
-                }
-                continue;
-            }
-        } else if (tail) {
-            continue;  // the first round only sent the draw to the tail
-        }
-        // the wedge of layer L >= 1
-        const double V = zig_uniform53(w.z, w.w);
-        const double y = __dadd_rn(Z.f[L], __dmul_rn(V, __dsub_rn(Z.f[L + 1], Z.f[L])));
-        if (y < exp(__dmul_rn(__dmul_rn(-0.5, z), z))) return zig_grid(neg ? -z : z);
-    }
-    return 0.0;
-}
-
-__device__ __forceinline__ double gauss_entry(uint64_t seed, int64_t i, int64_t j, const ZigShared& Z) {
-    const U4 w = philox(U4{(uint32_t)i, (uint32_t)j, (uint32_t)((uint64_t)j >> 32), 2u}, (uint32_t)seed,
-                        (uint32_t)(seed >> 32));
-    const int L = (int)(w.x & 255u);
-    const bool neg = (w.x >> 8) & 1u;
-    const double z = __dmul_rn((double)(((uint64_t)(w.x >> 9) << 30) | (w.y >> 2)), Z.xs[L]);
-    if (z < Z.x[L + 1]) return zig_grid(neg ? -z : z);
-    return gauss_slow(seed, i, j, Z, w, z, L, neg);
 }
 
 __global__ void k_gauss_gen(const ZigTable tab, uint64_t seed, int64_t s, int64_t m, int prec,
@@ -546,7 +451,7 @@ __global__ void k_gauss_split3(const ZigTable tab, uint64_t seed, int64_t s, int
         uint16_t* row = X + (size_t)i * 6 * L;
         for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x) {
             uint16_t h = 0, mi = 0, l = 0;
-            if (j < m) split3_bf16(__double2float_rn(gauss_entry(seed, i, j0 + j, Z)), h, mi, l);
+            if (j < m) split3_bf16(gauss_f32(seed, i, j0 + j, Z), h, mi, l);
             row[j] = l;
             row[L + j] = mi;
             row[2 * L + j] = h;
@@ -596,20 +501,6 @@ __global__ void k_gram_split3(const TI* __restrict__ A, int64_t m, int64_t n, in
         col[4 * L + j] = mi;
         col[5 * L + j] = h;
         col[6 * L + j] = h;
-    }
-}
-
-// Negated FP64 Omega columns [k0, k0 + kc) as an s x kc column-major block
-// (ld s): the K chunk of the FP64 sketch, which the digit-sliced update
-// subtracts (C - (-Omega) Ahat).
-__global__ void k_gauss_negchunk(const ZigTable tab, uint64_t seed, int64_t s, int64_t k0, int64_t kc,
-                                 double* __restrict__ Om) {
-    __shared__ ZigShared Z;
-    zig_stage(tab, Z);
-    const int64_t total = s * kc;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = q % s, j = q / s;
-        Om[q] = -gauss_entry(seed, i, k0 + j, Z);
     }
 }
 
@@ -947,13 +838,6 @@ template lsq_status launch_gram_split3<double>(const double*, int64_t, int64_t, 
                                                cudaStream_t);
 template lsq_status launch_gram_split3<float>(const float*, int64_t, int64_t, int64_t, int64_t, uint16_t*,
                                               cudaStream_t);
-
-lsq_status launch_gauss_negchunk(uint64_t seed, int64_t s, int64_t k0, int64_t kc, double* Om, cudaStream_t st) {
-    unsigned grid = (unsigned)min64(ceil_div(s * kc, 256), 4096);
-    k_gauss_negchunk<<<grid, 256, 0, st>>>(zig_table(), seed, s, k0, kc, Om);
-    LSQ_LAUNCH_CHECK();
-    return LSQ_OK;
-}
 
 lsq_status launch_gauss_inspect(uint64_t seed, int64_t s, int64_t m, int prec, double* Om, cudaStream_t st) {
     unsigned grid = (unsigned)min64(ceil_div(s * m, 256), 4096);

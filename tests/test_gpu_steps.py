@@ -113,9 +113,10 @@ def test_gaussian_sketch_within_rounding(prec):
     tol = 2 * m * u * scale + 2 ** -7 * np.abs(Ah).max() * 4
     if prec == O.FP64:
         # the FP64 sketch is a sum of K chunks of 512 digit-sliced products,
-        # each accurate to 512 2^-50.6 max|Omega_i,chunk| max|A_chunk,c|
-        dig = sum(512 * 2.0 ** -50.6 * np.outer(np.abs(Om[:, k:k + 512]).max(axis=1),
-                                                  np.abs(Ah[k:k + 512, :]).max(axis=0)) for k in range(0, m, 512))
+        # each accurate to 512 2^-50.6 2^3 max|A_chunk,c| (Omega sliced with
+        # the fixed exponent 2^3 > |Omega|)
+        dig = sum(512 * 2.0 ** -50.6 * 8.0 * np.outer(np.ones(s), np.abs(Ah[k:k + 512, :]).max(axis=0))
+                  for k in range(0, m, 512))
         tol = tol + dig
     assert np.all(np.abs(to_np(As) - oAs) <= tol)
 

@@ -174,11 +174,11 @@ def test_fp64_gaussian_sketch_digit_sliced(m, n, s):
     As_tc, As_cc, ce = _sketch_both_ways(A, lsq.FP64, s, 29, True)
     oAs, _ = O.sketch(A, O.GAUSSIAN, s, 0, 29, O.FP64)
     Om = O.gaussian_operator(29, s, m, O.FP64)
-    # per chunk: digit error below 512 2^-50.6 max|Omega_i,chunk| max|A_chunk,c|
-    # and two FP64 roundings of the running sum; the oracle: gamma_m sum|terms|
+    # per chunk: digit error below 512 2^-50.6 2^3 max|A_chunk,c| (Omega is
+    # sliced with the fixed exponent 2^3 > |Omega|) and two FP64 roundings of
+    # the running sum; the oracle: gamma_m sum|terms|
     chunks = [slice(k, min(k + 512, m)) for k in range(0, m, 512)]
-    dig = sum(512 * 2.0 ** -50.6 * np.outer(np.abs(Om[:, c]).max(axis=1), np.abs(A[c, :]).max(axis=0))
-              for c in chunks)
+    dig = sum(512 * 2.0 ** -50.6 * 8.0 * np.outer(np.ones(s), np.abs(A[c, :]).max(axis=0)) for c in chunks)
     scale = np.abs(Om) @ np.abs(A)
     gamma = m * U64 / (1 - m * U64)
     tol = dig + 2 * gamma * scale
