@@ -88,6 +88,14 @@ bool g_fp64_emulation = true;
 
 inline cudaStream_t S(void* p) { return reinterpret_cast<cudaStream_t>(p); }
 
+}  // namespace
+
+namespace lsq {
+bool fp64_emulation_enabled() { return g_fp64_emulation; }
+}  // namespace lsq
+
+namespace {
+
 bool valid_sketch_prec(int p) { return p >= LSQ_FP8_E4M3 && p <= LSQ_FP64; }
 bool is_auto(int p) { return p == LSQ_AUTO || p == LSQ_AUTO_SKETCH; }
 
@@ -163,7 +171,9 @@ SketchLayout sketch_layout(int64_t m, int64_t n, int64_t s, int kind, int zeta, 
         // of tensor-core products accumulated into A_s (A is read in place)
         L.gemm = o.take(ot_update_ws_bytes(s, n, kSketchChunk));
     } else if (gauss_fp32_tc(prec)) {
-        // FP32: three BF16 pieces per value, six K segments of length ldq
+        // FP32: three BF16 pieces per value, six K segments of length ldq (a
+        // multiple of 64: the operands are K-blocked in slices of 64)
+        L.ldq = L.ldo = align_up((size_t)m, 64);
         L.ahat = o.take(sizeof(uint16_t) * 6 * (size_t)L.ldq * n);
         L.om = o.take(sizeof(uint16_t) * 6 * (size_t)L.ldo * s);
         L.gemm = o.take(sketch_tc_ws_bytes(s, n, 6 * L.ldq, LSQ_BF16, sms));
@@ -391,7 +401,7 @@ lsq_status run_sketch(const double* A, int64_t m, int64_t n, int64_t lda, const 
         if ((r = launch_quantize_split3(A, m, n, lda, colexp, L.ldq, (uint16_t*)(base + L.ahat), st)) != LSQ_OK)
             return r;
         return launch_sketch_tc(base + L.om, K6, base + L.ahat, K6, LSQ_BF16, o->s, n, K6, (float*)As, ldas,
-                                base + L.gemm, L.gemm_bytes, err, st);
+                                base + L.gemm, L.gemm_bytes, err, st, true);
     }
     if ((r = launch_gauss_gen(o->seed, o->s, m, prec, base + L.om, L.ldo, o->row_offset, st)) != LSQ_OK) return r;
     if ((r = launch_quantize_cm(A, m, n, lda, colexp, prec, base + L.ahat, L.ldq, st)) != LSQ_OK) return r;

@@ -122,7 +122,7 @@ bool sketch_tc_supported(int prec);
 size_t sketch_tc_ws_bytes(int64_t s, int64_t n, int64_t m, int prec, int sms);
 lsq_status launch_sketch_tc(const void* Om, int64_t ldo, const void* Ahat, int64_t ldq, int prec, int64_t s,
                             int64_t n, int64_t m, float* As, int64_t ldas, void* ws, size_t ws_bytes, int32_t* err,
-                            cudaStream_t st);
+                            cudaStream_t st, bool blocked = false);
 
 // ---- ozaki.cu: FP64 Gram on the FP8 tensor cores (digit slicing) ----------
 size_t oz_gram_ws_bytes(int64_t m, int64_t n);
@@ -135,6 +135,8 @@ lsq_status oz_gemm_tn(const double* X, int64_t ldx, const double* Y, int64_t ldy
 
 // ---- oz_trsm.cu: FP64 Ap = A R^{-1} with tensor-core updates -------------
 bool ot_trsm_supported();
+// FP64 products on the tensor cores (lsq_set_fp64_emulation; default on).
+bool fp64_emulation_enabled();
 size_t ot_trsm_ws_bytes(int64_t m, int64_t n);
 lsq_status ot_trsm(const double* A, int64_t m, int64_t n, int64_t lda, const double* R, int64_t ldr, double* Ap,
                    int64_t ldap, void* ws, size_t ws_bytes, int32_t* err, cudaStream_t st);

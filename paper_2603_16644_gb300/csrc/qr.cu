@@ -1108,9 +1108,196 @@ static QrStreams* qr_streams() {
     return &q;
 }
 
+// ---------------------------------------------------------------------------
+// FP64 QR with the trailing updates on the tensor cores.  The columns are
+// taken in blocks of QTB: inside a block, 32-column panels and their
+// rank-32 updates as above (restricted to the block); then the block's
+// reflectors H_1 ... H_b = I - V T V^T update every later column at once,
+//   W = V^T C,  X = T^T W,  C <- C - V X,
+// each an FP64-accurate digit-sliced product (csrc/oz_trsm.cu; K chunks of
+// at most 512).  T is formed from S = T^{-1} = striu(V^T V) + diag(1/beta)
+// (Puglisi 1992; Joffrain et al. 2006: the triangular factor of the compact
+// WY form is the inverse of that matrix), column by column with the betas
+// as factors (a zero beta, H = I, gives a zero row and column of T).
+// ---------------------------------------------------------------------------
+constexpr int QTB = 256;  // columns per block of the tensor-core form
+constexpr int QTK = 512;  // K chunk of one digit-sliced product
+
+static bool qr_tc_blocked(int es, int64_t n) { return es == 8 && n > QTB && fp64_emulation_enabled() && ot_trsm_supported(); }
+
+struct QrTcLayout {
+    size_t vx, vt, g, tt, wn, xp, err, ot, ot_bytes, total;
+};
+
+static QrTcLayout qr_tc_layout(int64_t s, int64_t n) {
+    QrTcLayout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    L.vx = take(sizeof(double) * (size_t)s * QTB);
+    L.vt = take(sizeof(double) * (size_t)s * QTB);
+    L.g = take(sizeof(double) * QTB * QTB);
+    L.tt = take(sizeof(double) * QTB * QTB);
+    L.wn = take(sizeof(double) * QTB * (size_t)n);
+    L.xp = take(sizeof(double) * QTB * (size_t)n);
+    L.err = take(sizeof(int32_t));
+    L.ot_bytes = ot_update_ws_bytes(std::max<int64_t>(s, QTB), std::max<int64_t>(n, QTB), QTK);
+    L.ot = take(L.ot_bytes);
+    L.total = off;
+    return L;
+}
+
+// The block's reflectors as explicit V (rows x nb, ld rows) and V^T (nb x
+// rows, ld nb): unit diagonal, zero above, Householder vectors below (the
+// lower part of W's columns j0 .. j0 + nb - 1 from row j0).
+__global__ void k_qr_vblock(const double* __restrict__ W, int64_t ld, int64_t j0, int64_t rows, int nb,
+                            double* __restrict__ Vx, double* __restrict__ Vt) {
+    const int64_t total = rows * nb;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = q % rows, c = q / rows;
+        const double v = r < c ? 0.0 : (r == c ? 1.0 : W[(j0 + r) + (j0 + c) * ld]);
+        Vx[q] = v;
+        Vt[c + r * nb] = v;
+    }
+}
+
+// T^T (ld nb) from Gn = -V^T V and the betas: column j of T by back
+// substitution, t_j = beta_j, t_i = -beta_i sum_{i < p <= j} S[i][p] t_p with
+// S[i][p] = (V^T V)[i][p]; one warp per column, the sums over lanes in a
+// fixed order.
+__global__ void __launch_bounds__(32) k_qr_tinv(const double* __restrict__ Gn, const double* __restrict__ beta,
+                                                 int nb, double* __restrict__ Tt) {
+    __shared__ double t[QTB];
+    const int j = blockIdx.x, lane = threadIdx.x;
+    for (int i = lane; i < nb; i += 32) t[i] = 0.0;
+    __syncwarp();
+    if (lane == 0) t[j] = beta[j];
+    __syncwarp();
+    for (int i = j - 1; i >= 0; --i) {
+        double acc = 0.0;
+        for (int p = i + 1 + lane; p <= j; p += 32) acc = fma(-Gn[i + (int64_t)p * nb], t[p], acc);
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) t[i] = -beta[i] * acc;
+        __syncwarp();
+    }
+    for (int i = lane; i < nb; i += 32) Tt[j + (int64_t)i * nb] = t[i];
+}
+
+__global__ void k_qr_err_to_info(const int32_t* __restrict__ err, int32_t* __restrict__ info) {
+    if (*err != 0 && *info == 0) *info = -2;
+}
+
+// C (rows x nt, ld s) <- (I - V T^T V^T) C for the block of nb reflectors
+// stored in W's columns j0 .. j0 + nb - 1 (C: W's rows j0.., columns j0 + nb..).
+static lsq_status qr_tc_trailing(double* W, int64_t s, int64_t j0, int nb, int64_t n, const double* beta, char* base,
+                                 const QrTcLayout& L, cudaStream_t st) {
+    const int64_t rows = s - j0, nt = n - j0 - nb;
+    if (nt <= 0) return LSQ_OK;
+    double* Vx = (double*)(base + L.vx);
+    double* Vt = (double*)(base + L.vt);
+    double* Gn = (double*)(base + L.g);
+    double* Tt = (double*)(base + L.tt);
+    double* Wn = (double*)(base + L.wn);
+    double* Xp = (double*)(base + L.xp);
+    int32_t* err = (int32_t*)(base + L.err);
+    char* ows = base + L.ot;
+    double* C = W + j0 + (j0 + nb) * s;
+    lsq_status r;
+    k_qr_vblock<<<(unsigned)std::min<int64_t>(ceil_div(rows * nb, 256), 8192), 256, 0, st>>>(W, s, j0, rows, nb, Vx,
+                                                                                              Vt);
+    LSQ_LAUNCH_CHECK();
+    // Gn = -V^T V and Wn = -V^T C, accumulated over K chunks of the rows
+    LSQ_CUDA_TRY(cudaMemsetAsync(Gn, 0, sizeof(double) * nb * nb, st));
+    LSQ_CUDA_TRY(cudaMemsetAsync(Wn, 0, sizeof(double) * nb * (size_t)nt, st));
+    for (int64_t k = 0; k < rows; k += QTK) {
+        const int64_t kc = std::min<int64_t>(QTK, rows - k);
+        if ((r = ot_gemm_update(Vt + k * nb, nb, Vx + k, 1, rows, Gn, nb, Gn, nb, nb, nb, kc, ows, L.ot_bytes, err,
+                                st)) != LSQ_OK)
+            return r;
+        if ((r = ot_gemm_update(Vt + k * nb, nb, C + k, 1, s, Wn, nb, Wn, nb, nb, nt, kc, ows, L.ot_bytes, err, st)) !=
+            LSQ_OK)
+            return r;
+    }
+    k_qr_tinv<<<(unsigned)nb, 32, 0, st>>>(Gn, beta + j0, nb, Tt);
+    LSQ_LAUNCH_CHECK();
+    // Xp = 0 - T^T Wn = T^T (V^T C)
+    LSQ_CUDA_TRY(cudaMemsetAsync(Xp, 0, sizeof(double) * nb * (size_t)nt, st));
+    if ((r = ot_gemm_update(Tt, nb, Wn, 1, nb, Xp, nb, Xp, nb, nb, nt, nb, ows, L.ot_bytes, err, st)) != LSQ_OK)
+        return r;
+    // C <- C - V Xp
+    return ot_gemm_update(Vx, rows, Xp, 1, nb, C, s, C, s, rows, nt, nb, ows, L.ot_bytes, err, st);
+}
+
 size_t qr_ws_bytes(int64_t s, int64_t n, int prec) {
     int es = prec == LSQ_FP64 ? 8 : 4;
-    return qr_layout(s, n, es).total + 256;
+    size_t b = qr_layout(s, n, es).total + 256;
+    if (qr_tc_blocked(es, n)) b += qr_tc_layout(s, n).total + 256;
+    return b;
+}
+
+// FP64 QR by blocks of QTB columns (see qr_tc_trailing): the panels and
+// rank-32 updates inside a block on the panel stream as in qr_run, the
+// block's update of every later column on the tensor cores.  W holds A_s.
+static lsq_status qr_blocked_f64(double* W, double* beta, int64_t s, int64_t n, const int32_t* colexp, double* Rs,
+                                 int64_t ldr, int32_t* info, char* base, const QrLayout& L, char* tcb,
+                                 cudaStream_t st) {
+    const QrTcLayout TL = qr_tc_layout(s, n);
+    int32_t* err = (int32_t*)(tcb + TL.err);
+    LSQ_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+    const QrCluster qc = qr_cluster_size<double>(s);
+    const int qcl = qc.qcl;
+    int k = 0;  // panel counter: the parity of the V and T buffers
+    lsq_status r = LSQ_OK;
+    for (int64_t j0 = 0; j0 < n && r == LSQ_OK; j0 += QTB) {
+        const int64_t j1 = std::min<int64_t>(n, j0 + QTB);
+        const double* Vprev = nullptr;
+        const double* Tprev = nullptr;
+        int64_t ldvprev = 0;
+        for (int64_t k0 = j0; k0 < j1; k0 += QNB, ++k) {
+            const int b = k & 1;
+            const int nb = (int)std::min<int64_t>(QNB, j1 - k0);
+            const int64_t rows = s - k0;
+            double* Tm = (double*)(base + L.tm[b]);
+            double* V = (double*)(base + L.v[b]);
+            if (qcl > 0) {
+                const size_t clsm = qr_cluster_smem<double>(rows, qcl, qc.fused);
+                if (qr_launch_cluster<double>(qcl, clsm, st, W, s, k0, nb, beta, Tm, V, rows, Vprev, ldvprev, Tprev) !=
+                    cudaSuccess)
+                    return LSQ_ERR_CUDA;
+            } else {
+                k_qr_panel<double><<<1, QPT, 0, st>>>(W, s, s, k0, nb, beta, Tm, V, rows);
+            }
+            note_launch();
+            if (cudaGetLastError() != cudaSuccess) return LSQ_ERR_CUDA;
+            // the rest of the block's columns
+            const int64_t nt = j1 - k0 - nb;
+            if (nt <= 0) {
+                ++k;
+                break;
+            }
+            const int64_t nn = std::min<int64_t>(QNB, nt), nw = nt - nn;
+            double* C = W + k0 + (k0 + nb) * s;
+            const bool fuse_next = qcl > 0 && qc.fused && nb == QNB;
+            r = fuse_next ? qr_apply<double>(V, Tm, nb, rows, C + nn * s, s, nw, st)
+                          : qr_apply<double>(V, Tm, nb, rows, C, s, nt, st);
+            if (r != LSQ_OK) return r;
+            Vprev = fuse_next ? V : nullptr;
+            Tprev = fuse_next ? Tm : nullptr;
+            ldvprev = rows;
+        }
+        // the block's reflectors on every later column
+        r = qr_tc_trailing(W, s, j0, (int)(j1 - j0), n, beta, tcb, TL, st);
+    }
+    if (r != LSQ_OK) return r;
+    k_qr_extract<double><<<(unsigned)std::min<int64_t>(ceil_div(n * n, 256), 4096), 256, 0, st>>>(W, s, n, colexp, Rs,
+                                                                                                ldr);
+    LSQ_LAUNCH_CHECK();
+    if (info) {
+        k_check_diag<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(Rs, n, ldr, info);
+        LSQ_LAUNCH_CHECK();
+        k_qr_err_to_info<<<1, 1, 0, st>>>(err, info);
+        LSQ_LAUNCH_CHECK();
+    }
+    return LSQ_OK;
 }
 
 template <typename T>
@@ -1128,6 +1315,13 @@ static lsq_status qr_run(const void* As, int64_t s, int64_t n, int64_t ldas, int
     else
         k_qr_load<float, T><<<g, 256, 0, st>>>((const float*)As, s, n, ldas, W);
     LSQ_LAUNCH_CHECK();
+    if constexpr (std::is_same<T, double>::value) {
+        if (qr_tc_blocked(es, n)) {
+            char* tcb = base + align_up(L.total, 256);
+            if (L.total + 256 + qr_tc_layout(s, n).total + ((char*)base - (char*)ws) > ws_bytes) return LSQ_ERR_NOMEM;
+            return qr_blocked_f64(W, beta, s, n, colexp, Rs, ldr, info, base, L, tcb, st);
+        }
+    }
     // look-ahead: while panel k + 1 is factored (high-priority stream), the
     // wide part of panel k's trailing update runs on the low-priority stream;
     // the narrow part (the next panel's columns) goes first on the panel

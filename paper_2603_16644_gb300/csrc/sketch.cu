@@ -441,43 +441,49 @@ __device__ __forceinline__ void split3_bf16(float x, uint16_t& h, uint16_t& m, u
     l = __bfloat16_as_ushort(bl);
 }
 
-// Omega_hat rows (FP32-rounded Gaussian entries) as BF16 pieces: row i at
-// X + i * 6L, segments l m h m h h.
+// The BF16 piece operands of the FP32 sketch are stored K-blocked: element
+// (row r, k) of an operand with `rows` rows at ((k / 64) rows + r) 64 + k % 64,
+// so that every 64-wide K slice of 128 rows the GEMM loads is one contiguous
+// 16 KB range (few DRAM pages and TLB entries per load, whatever m).
+__device__ __forceinline__ size_t kblk(int64_t k, int64_t r, int64_t rows) {
+    return ((size_t)(k >> 6) * (size_t)rows + (size_t)r) * 64 + (size_t)(k & 63);
+}
+
+// Omega_hat rows (FP32-rounded Gaussian entries) as BF16 pieces: K segments
+// of length L (a multiple of 64) l m h m h h, K-blocked over the s rows.
 __global__ void k_gauss_split3(const ZigTable tab, uint64_t seed, int64_t s, int64_t m, int64_t L,
                                uint16_t* __restrict__ X, int64_t j0) {
     __shared__ ZigShared Z;
     zig_stage(tab, Z);
     for (int64_t i = blockIdx.y; i < s; i += gridDim.y) {
-        uint16_t* row = X + (size_t)i * 6 * L;
         for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x) {
             uint16_t h = 0, mi = 0, l = 0;
             if (j < m) split3_bf16(gauss_f32(seed, i, j0 + j, Z), h, mi, l);
-            row[j] = l;
-            row[L + j] = mi;
-            row[2 * L + j] = h;
-            row[3 * L + j] = mi;
-            row[4 * L + j] = h;
-            row[5 * L + j] = h;
+            X[kblk(j, i, s)] = l;
+            X[kblk(L + j, i, s)] = mi;
+            X[kblk(2 * L + j, i, s)] = h;
+            X[kblk(3 * L + j, i, s)] = mi;
+            X[kblk(4 * L + j, i, s)] = h;
+            X[kblk(5 * L + j, i, s)] = h;
         }
     }
 }
 
-// Ahat = FP32(A 2^colexp) columns as BF16 pieces: column c at Y + c * 6L,
-// segments h m l h m h.
+// Ahat = FP32(A 2^colexp) columns as BF16 pieces: K segments h m l h m h,
+// K-blocked over the n columns.
 __global__ void k_quantize_split3(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda,
                                   const int32_t* __restrict__ colexp, int64_t L, uint16_t* __restrict__ Y) {
     const int64_t c = blockIdx.y;
     const int e = colexp[c];
-    uint16_t* col = Y + (size_t)c * 6 * L;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x) {
         uint16_t h = 0, mi = 0, l = 0;
         if (j < m) split3_bf16(__uint_as_float(quant_bits(A[j + c * lda], e, LSQ_FP32)), h, mi, l);
-        col[j] = h;
-        col[L + j] = mi;
-        col[2 * L + j] = l;
-        col[3 * L + j] = h;
-        col[4 * L + j] = mi;
-        col[5 * L + j] = h;
+        Y[kblk(j, c, n)] = h;
+        Y[kblk(L + j, c, n)] = mi;
+        Y[kblk(2 * L + j, c, n)] = l;
+        Y[kblk(3 * L + j, c, n)] = h;
+        Y[kblk(4 * L + j, c, n)] = mi;
+        Y[kblk(5 * L + j, c, n)] = h;
     }
 }
 
@@ -813,6 +819,7 @@ lsq_status launch_gauss_gen(uint64_t seed, int64_t s, int64_t m, int prec, void*
 
 lsq_status launch_gauss_split3(uint64_t seed, int64_t s, int64_t m, int64_t L, uint16_t* X, int64_t j0,
                                cudaStream_t st) {
+    if (L % 64) return LSQ_ERR_ARG;
     dim3 grid((unsigned)min64(ceil_div(L, 256), 64), (unsigned)min64(s, 64));
     k_gauss_split3<<<grid, 256, 0, st>>>(zig_table(), seed, s, m, L, X, j0);
     LSQ_LAUNCH_CHECK();
@@ -821,6 +828,7 @@ lsq_status launch_gauss_split3(uint64_t seed, int64_t s, int64_t m, int64_t L, u
 
 lsq_status launch_quantize_split3(const double* A, int64_t m, int64_t n, int64_t lda, const int32_t* colexp,
                                   int64_t L, uint16_t* Y, cudaStream_t st) {
+    if (L % 64) return LSQ_ERR_ARG;
     dim3 grid((unsigned)min64(ceil_div(L, 256), 64), (unsigned)n);
     k_quantize_split3<<<grid, 256, 0, st>>>(A, m, n, lda, colexp, L, Y);
     LSQ_LAUNCH_CHECK();

@@ -46,7 +46,7 @@ template <int KIND, int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_sketch_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t M, int64_t N,
                 int64_t K, int64_t kchunk, float* __restrict__ out, int64_t ldo, int64_t split_stride,
-                int32_t* __restrict__ err, const int2* __restrict__ tiles, int64_t ntiles) {
+                int32_t* __restrict__ err, const int2* __restrict__ tiles, int64_t ntiles, int blocked) {
     constexpr int ES = KIND == 2 ? 1 : 2;  // element bytes
     constexpr int BKE = 128 / ES;          // K elements per stage
     constexpr int ST = tc_stages(BN);
@@ -65,10 +65,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // tile list mode: blockIdx.x picks (m0, n0) and the tile is written to its
-    // own 128 x 128 slot (column-major, ld 128) of `out`
+    // own 128 x 128 slot (column-major, ld 128) of `out`; otherwise the
+    // column tiles run fastest, so that the CTAs of a wave share the row
+    // tiles of A (the larger operand) and read B once per wave
     const int2 tl = tiles ? tiles[blockIdx.x] : make_int2(0, 0);
-    const int64_t m0 = tiles ? (int64_t)tl.x : (int64_t)blockIdx.x * TC_BM;
-    const int64_t n0 = tiles ? (int64_t)tl.y : (int64_t)blockIdx.y * BN;
+    const int64_t m0 = tiles ? (int64_t)tl.x : (int64_t)blockIdx.y * TC_BM;
+    const int64_t n0 = tiles ? (int64_t)tl.y : (int64_t)blockIdx.x * BN;
     const int64_t kb0 = (int64_t)blockIdx.z * kchunk;
     const int64_t kb1 = min64(K, kb0 + kchunk);
     const int nk = (int)((kb1 - kb0 + BKE - 1) / BKE);
@@ -106,8 +108,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (*bad) break;
             mbar_expect_tx(&full[s], TC_TILE_BYTES + BBYTES);
             int x = (int)(kb0 + (int64_t)kb * BKE);
-            tma_load_2d(sA + s * TC_TILE_BYTES, &tmA, &full[s], x, (int)m0);
-            tma_load_2d(sB + s * BBYTES, &tmB, &full[s], x, (int)n0);
+            if (blocked) {
+                // K-blocked operands: block x / BKE holds every row's 128 bytes
+                tma_load_3d(sA + s * TC_TILE_BYTES, &tmA, &full[s], 0, (int)m0, x / BKE);
+                tma_load_3d(sB + s * BBYTES, &tmB, &full[s], 0, (int)n0, x / BKE);
+            } else {
+                tma_load_2d(sA + s * TC_TILE_BYTES, &tmA, &full[s], x, (int)m0);
+                tma_load_2d(sB + s * BBYTES, &tmB, &full[s], x, (int)n0);
+            }
             *issued = kb + 1;
         }
     } else if (warp == 1) {
@@ -229,6 +237,28 @@ static bool make_map(CUtensorMap* map, const void* base, int prec, int64_t K, in
     return r == CUDA_SUCCESS;
 }
 
+// A K-blocked operand: element (row r, k) at ((k / B) rows + r) B + k % B with
+// B = 128 bytes of K (64 BF16/FP16 or 128 FP8 values); every box of B x
+// box_rows is one contiguous range.  K a multiple of B.
+static bool make_map_blocked(CUtensorMap* map, const void* base, int prec, int64_t K, int64_t rows,
+                             int box_rows = 128) {
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) return false;
+    const int es = prec == LSQ_FP8_E4M3 ? 1 : 2;
+    const int64_t B = 128 / es;
+    if (K % B) return false;
+    CUtensorMapDataType dt = prec == LSQ_FP8_E4M3 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                             : prec == LSQ_BF16   ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                  : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    cuuint64_t dims[3] = {(cuuint64_t)B, (cuuint64_t)rows, (cuuint64_t)(K / B)};
+    cuuint64_t strides[2] = {(cuuint64_t)128, (cuuint64_t)(rows * 128)};
+    cuuint32_t box[3] = {(cuuint32_t)B, (cuuint32_t)box_rows, 1u};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult r = enc(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 bool sketch_tc_supported(int prec) {
     return (prec == LSQ_FP8_E4M3 || prec == LSQ_BF16 || prec == LSQ_FP16) && tensor_map_encoder() != nullptr;
 }
@@ -255,12 +285,16 @@ size_t sketch_tc_ws_bytes(int64_t s, int64_t n, int64_t m, int prec, int sms) {
 
 lsq_status launch_sketch_tc(const void* Om, int64_t ldo, const void* Ahat, int64_t ldq, int prec, int64_t s,
                             int64_t n, int64_t m, float* As, int64_t ldas, void* ws, size_t ws_bytes, int32_t* err,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool blocked) {
     if (!sketch_tc_supported(prec)) return LSQ_ERR_ARG;
     if ((ldo % 16) || (ldq % 16) || ((uintptr_t)Om % 16) || ((uintptr_t)Ahat % 16)) return LSQ_ERR_ARG;
     const int bn = tc_bn(n);
     CUtensorMap ta, tb;
-    if (!make_map(&ta, Om, prec, m, s, ldo) || !make_map(&tb, Ahat, prec, m, n, ldq, bn)) return LSQ_ERR_CUDA;
+    if (blocked) {
+        if (!make_map_blocked(&ta, Om, prec, m, s) || !make_map_blocked(&tb, Ahat, prec, m, n, bn)) return LSQ_ERR_ARG;
+    } else if (!make_map(&ta, Om, prec, m, s, ldo) || !make_map(&tb, Ahat, prec, m, n, ldq, bn)) {
+        return LSQ_ERR_CUDA;
+    }
     int sms = device_sm_count();
     int splits = tc_splits(s, n, m, prec, sms);
     int64_t bke = prec == LSQ_FP8_E4M3 ? 128 : 64;
@@ -275,11 +309,12 @@ lsq_status launch_sketch_tc(const void* Om, int64_t ldo, const void* Ahat, int64
         stride = s * n;
     }
     size_t smem = 1024 + (size_t)tc_stages(bn) * (TC_TILE_BYTES + (size_t)bn * 128) + 256;
-    dim3 grid((unsigned)ceil_div(s, TC_BM), (unsigned)ceil_div(n, bn), (unsigned)splits);
+    dim3 grid((unsigned)ceil_div(n, bn), (unsigned)ceil_div(s, TC_BM), (unsigned)splits);
     stage_mark(ST_K_SKETCHTC, true, st);
     auto go = [&](auto kern) -> lsq_status {
         LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<grid, TC_THREADS, smem, st>>>(ta, tb, s, n, m, kchunk, out, ldout, stride, err, nullptr, 0);
+        kern<<<grid, TC_THREADS, smem, st>>>(ta, tb, s, n, m, kchunk, out, ldout, stride, err, nullptr, 0,
+                                             blocked ? 1 : 0);
         return LSQ_OK;
     };
     lsq_status lr;
@@ -319,7 +354,7 @@ lsq_status launch_tc_tiles_fp8(const void* X, int64_t ldx, int64_t rowsX, const 
     LSQ_CUDA_TRY(cudaFuncSetAttribute(k_sketch_tc<2, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)ntiles, 1, (unsigned)chunks);
     k_sketch_tc<2, BN><<<grid, TC_THREADS, smem, st>>>(ta, tb, rowsX, rowsY, K, kchunk, out, TC_BM, 0, err, tiles,
-                                                      ntiles);
+                                                      ntiles, 0);
     LSQ_LAUNCH_CHECK();
     return LSQ_OK;
 }

@@ -122,8 +122,11 @@ def test_gaussian_sketch_within_rounding(prec):
 
 
 @pytest.mark.parametrize("qr_prec", [O.FP32, O.FP64])
-@pytest.mark.parametrize("s,n", [(300, 113), (256, 256), (4096, 200), (65, 1), (1000, 300)])
+@pytest.mark.parametrize("s,n", [(300, 113), (256, 256), (4096, 200), (65, 1), (1000, 300), (1500, 600),
+                                 (3000, 1030)])
 def test_precond_qr(qr_prec, s, n):
+    # FP64 with n > 256: blocks of 256 columns whose reflectors update the
+    # later columns by digit-sliced tensor-core products (ragged last block)
     rng = np.random.default_rng(s + n)
     As = np.asfortranarray(rng.standard_normal((s, n)) @ np.diag(np.logspace(0, -2, n)))
     if qr_prec == O.FP32:
