@@ -412,15 +412,34 @@ lsq_status run_sketch(const double* A, int64_t m, int64_t n, int64_t lda, const 
     return launch_gemm_kmajor(gp, base + L.om, prec, L.ldo, base + L.ahat, prec, L.ldq, As, ldas, base + L.gemm, st);
 }
 
-// HPNE through QR: M = [[H, v], [0, 1]] ((n+1) x (n+1), ld n+1); the
+// HPNE through QR: M = [[H, v], [0, g]] ((n+1) x (n+1), ld n+1); the
 // Householder R of M holds R_H and Q_H^T v, so H x = v gives x = R_H^{-1}
-// (Q_H^T v).
+// (Q_H^T v).  The corner g (the power of two at or above max |v|, 1 for a
+// zero or non-finite v) changes neither R_H nor Q_H^T v (the reflectors of
+// the first n columns have no component in the last row); a unit corner
+// would set the scale of the last column to 1 and with it the columnwise
+// error of the QR's products, whatever the size of v.
+__global__ void k_hq_gamma(const double* __restrict__ v, int64_t n, double* __restrict__ g) {
+    __shared__ double red[32];
+    double mx = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, fabs(v[i]));
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t = fmax(t, red[q]);
+        *g = (t > 0.0 && isfinite(t)) ? ldexp(1.0, ilogb(t) + 1) : 1.0;
+    }
+}
+
 __global__ void k_hq_augment(const double* __restrict__ H, int64_t n, int64_t ldh, const double* __restrict__ v,
-                             double* __restrict__ M) {
+                             const double* __restrict__ g, double* __restrict__ M) {
     const int64_t n1 = n + 1, total = n1 * n1;
+    const double corner = *g;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = q % n1, j = q / n1;
-        M[q] = (i < n && j < n) ? H[i + j * ldh] : (j == n ? (i < n ? v[i] : 1.0) : 0.0);
+        M[q] = (i < n && j < n) ? H[i + j * ldh] : (j == n ? (i < n ? v[i] : corner) : 0.0);
     }
 }
 
@@ -429,7 +448,10 @@ lsq_status hq_solve(const double* H, int64_t n, double* v, char* base, const Sol
     double* M = (double*)(base + L.hq_m);
     double* Ra = (double*)(base + L.hq_r);
     const int64_t n1 = n + 1;
-    k_hq_augment<<<(unsigned)std::min<int64_t>(ceil_div(n1 * n1, 256), 8192), 256, 0, st>>>(H, n, n, v, M);
+    double* g = Ra + n1 * n1 - 1;  // scratch until the QR writes R
+    k_hq_gamma<<<1, 1024, 0, st>>>(v, n, g);
+    LSQ_LAUNCH_CHECK();
+    k_hq_augment<<<(unsigned)std::min<int64_t>(ceil_div(n1 * n1, 256), 8192), 256, 0, st>>>(H, n, n, v, g, M);
     LSQ_LAUNCH_CHECK();
     lsq_status r = launch_precond_qr(M, n1, n1, n1, LSQ_FP64, LSQ_FP64, nullptr, Ra, n1, info, base + L.hq_qr,
                                      L.hq_qr_bytes, st);

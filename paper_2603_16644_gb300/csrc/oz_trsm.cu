@@ -100,55 +100,10 @@ __device__ __forceinline__ uint32_t ot_digit_pair(unsigned long long W0, unsigne
 
 // Rows of X (m x K, column-major): Ex[i] and digit planes Z[(t mp + i) Kp + k]
 // (K-contiguous; zero for rows m <= i < mp and for K <= k < Kp, so that every
-// TMA box lies inside the planes).  One thread per row.
-__global__ void __launch_bounds__(128) k_ot_rowslice(const double* __restrict__ X, int64_t m, int64_t mp, int64_t K,
-                                                     int64_t ld, int64_t Kp, int32_t* __restrict__ Ex,
-                                                     uint16_t* __restrict__ Z) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= mp) return;
-    const double* row = X + i;
-    const int64_t Kr = i < m ? K : 0;
-    unsigned long long mx = 0;
-    int64_t k = 0;
-    for (; k + 8 <= Kr; k += 8) {  // 8 loads in flight per thread
-        unsigned long long v[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = (unsigned long long)__double_as_longlong(row[(k + q) * ld]);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            unsigned long long a = v[q] & 0x7fffffffffffffffull;
-            mx = a > mx ? a : mx;
-        }
-    }
-    for (; k < Kr; ++k) {
-        unsigned long long v = (unsigned long long)__double_as_longlong(row[k * ld]) & 0x7fffffffffffffffull;
-        mx = v > mx ? v : mx;
-    }
-    const int32_t E = ot_exp_of_max(mx);
-    Ex[i] = E;
-    for (int64_t k0 = 0; k0 < Kp; k0 += 16) {
-        uint32_t pk[OT_DIG][8];
-#pragma unroll
-        for (int q2 = 0; q2 < 8; ++q2) {
-            const int64_t k = k0 + 2 * q2;
-            const unsigned long long W0 = ot_fields(k < Kr ? row[k * ld] : 0.0, E);
-            const unsigned long long W1 = ot_fields(k + 1 < Kr ? row[(k + 1) * ld] : 0.0, E);
-#pragma unroll
-            for (int t = 0; t < OT_DIG; ++t) pk[t][q2] = ot_digit_pair(W0, W1, t);
-        }
-#pragma unroll
-        for (int t = 0; t < OT_DIG; ++t) {
-            uint4* dst = (uint4*)(Z + ((int64_t)t * mp + i) * Kp + k0);
-            dst[0] = make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
-            dst[1] = make_uint4(pk[t][4], pk[t][5], pk[t][6], pk[t][7]);
-        }
-    }
-}
-
-// The same with the row exponents from the per-block exponents (Eblk[b m +
-// i] for blocks b0 .. b0+nbk-1, INT32_MIN for an all-zero block): a 2-D grid,
-// one thread per row and 64-wide range of K (blockIdx.y), so that many more
-// loads are in flight than with one thread per row.
+// TMA box lies inside the planes), with the row exponents from per-block
+// exponents (Eblk[b m + i] for blocks b0 .. b0+nbk-1, INT32_MIN for an
+// all-zero block): a 2-D grid, one thread per row and 64-wide range of K
+// (blockIdx.y), so that many loads are in flight.
 __global__ void __launch_bounds__(128) k_ot_rowslice_e(const double* __restrict__ X, int64_t m, int64_t mp,
                                                        int64_t K, int64_t ld, int64_t Kp, int32_t* __restrict__ Ex,
                                                        uint16_t* __restrict__ Z, const int32_t* __restrict__ Eblk,
@@ -183,6 +138,27 @@ __global__ void __launch_bounds__(128) k_ot_rowslice_e(const double* __restrict_
             dst[1] = make_uint4(pk[t][4], pk[t][5], pk[t][6], pk[t][7]);
         }
     }
+}
+
+// Row maxima of |X| (bit patterns, the sign cleared; atomicMax orders them
+// like the values) over 64-wide K ranges, one thread per row; Mx zeroed.
+__global__ void __launch_bounds__(128) k_ot_rowmax2d(const double* __restrict__ X, int64_t m, int64_t K, int64_t ld,
+                                                     unsigned long long* __restrict__ Mx) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int64_t k0 = (int64_t)blockIdx.y * 64, k1 = min64(K, k0 + 64);
+    unsigned long long mx = 0;
+    for (int64_t k = k0; k < k1; ++k) {
+        const unsigned long long a = (unsigned long long)__double_as_longlong(X[i + k * ld]) & 0x7fffffffffffffffull;
+        mx = a > mx ? a : mx;
+    }
+    if (mx) atomicMax(&Mx[i], mx);
+}
+
+// The rows' exponents in the per-block convention (INT32_MIN for a zero row).
+__global__ void k_ot_rowexp(const unsigned long long* __restrict__ Mx, int64_t m, int32_t* __restrict__ Eb) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) Eb[i] = Mx[i] == 0 ? INT32_MIN : ot_exp_of_max(Mx[i]);
 }
 
 // The same, with the digit planes written as whole 128-byte lines: a CTA
@@ -727,7 +703,8 @@ static size_t ot_update_smem() { return 1024 + 2 * OT_DIG * OT_YTILE + OT_XST * 
 size_t ot_update_ws_bytes(int64_t M, int64_t N, int64_t K) {
     const int64_t mp = ot_pad(M, OT_BM), Np = ot_pad(N, OT_BN), Kp = ot_kp(K);
     return align_up(sizeof(uint16_t) * OT_DIG * (size_t)mp * Kp, 256) + align_up(sizeof(int32_t) * mp, 256) +
-           align_up(sizeof(uint16_t) * OT_DIG * (size_t)Np * Kp, 256) + align_up(sizeof(int32_t) * Np, 256) + 256;
+           align_up(sizeof(uint16_t) * OT_DIG * (size_t)Np * Kp, 256) + align_up(sizeof(int32_t) * Np, 256) +
+           align_up(sizeof(unsigned long long) * mp, 256) + align_up(sizeof(int32_t) * mp, 256) + 256;
 }
 
 // The negated Gaussian sketch operator's K chunk as the update's X digit
@@ -765,6 +742,8 @@ struct OtUpd {
     int32_t* Ex;
     uint16_t* Zy;
     int32_t* Ey;
+    unsigned long long* Mx;  // row maxima of X (bit patterns), for the 2-D slicing
+    int32_t* Eb;             // their exponents
     int64_t mp, Np, Kp;
 };
 
@@ -781,6 +760,10 @@ static OtUpd ot_upd_ptrs(void* ws, int64_t M, int64_t N, int64_t K) {
     U.Zy = (uint16_t*)base;
     base += align_up(sizeof(uint16_t) * OT_DIG * (size_t)U.Np * U.Kp, 256);
     U.Ey = (int32_t*)base;
+    base += align_up(sizeof(int32_t) * U.Np, 256);
+    U.Mx = (unsigned long long*)base;
+    base += align_up(sizeof(unsigned long long) * U.mp, 256);
+    U.Eb = (int32_t*)base;
     return U;
 }
 
@@ -831,11 +814,20 @@ lsq_status ot_gemm_update(const double* X, int64_t ldx, const double* Y, int64_t
                                           (int)rsm));
         k_ot_rowslice_s<true, true><<<dim3((unsigned)(U.mp / OT_RS_ROWS), 1u), 128, rsm, st>>>(
             tzs, txs, X, M, U.mp, K, ldx, U.Ex, nullptr, 0, 0, err);
-    } else if (xmode == 1)
+    } else if (xmode == 1) {
         k_ot_rowslice_e<<<dim3((unsigned)(U.mp / 128), (unsigned)(U.Kp / 64)), 128, 0, st>>>(
             X, M, U.mp, K, ldx, U.Kp, U.Ex, U.Zx, Eblk, b0, nbk);
-    else
-        k_ot_rowslice<<<(unsigned)(U.mp / 128), 128, 0, st>>>(X, M, U.mp, K, ldx, U.Kp, U.Ex, U.Zx);
+    } else {
+        // row maxima over a 2-D grid (rows x 64-wide K ranges), then the
+        // slicing on the same grid: every SM has work even when M is small
+        LSQ_CUDA_TRY(cudaMemsetAsync(U.Mx, 0, sizeof(unsigned long long) * (size_t)U.mp, st));
+        const dim3 g2((unsigned)(U.mp / 128), (unsigned)(U.Kp / 64));
+        k_ot_rowmax2d<<<g2, 128, 0, st>>>(X, M, K, ldx, U.Mx);
+        LSQ_LAUNCH_CHECK();
+        k_ot_rowexp<<<(unsigned)ceil_div(M, 256), 256, 0, st>>>(U.Mx, M, U.Eb);
+        LSQ_LAUNCH_CHECK();
+        k_ot_rowslice_e<<<g2, 128, 0, st>>>(X, M, U.mp, K, ldx, U.Kp, U.Ex, U.Zx, U.Eb, 0, 1);
+    }
     LSQ_LAUNCH_CHECK();
     k_ot_colslice<<<(unsigned)U.Np, 128, 0, st>>>(Y, K, N, U.Np, sk, sj, U.Kp, U.Ey, U.Zy);
     LSQ_LAUNCH_CHECK();
