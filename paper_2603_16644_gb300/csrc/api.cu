@@ -138,7 +138,7 @@ struct SketchLayout {
 
 // Columns of Omega per digit-sliced product of the FP64 Gaussian sketch (the
 // largest K whose digit-pair sums stay exact in FP32).
-constexpr int64_t kSketchChunk = 512;
+constexpr int64_t kSketchChunk = 1024;  // K chunk of the FP64 sketch (three-digit Omega)
 
 // The Gaussian sketch on the tensor cores: FP64 by digit slicing (switch
 // lsq_set_fp64_emulation), FP32 as BF16 pieces (lsq_set_tensor_core_sketch).

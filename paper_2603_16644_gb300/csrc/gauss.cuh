@@ -55,16 +55,20 @@ struct ZigTable {
 // Built once per process (thread-safe), in csrc/sketch.cu.
 const ZigTable& zig_table();
 
-// The tables in shared memory.
+// The tables in shared memory (with FP32 copies of x and f for the wedge
+// test's first try).
 struct ZigShared {
     double x[kZigN + 1], f[kZigN + 1];
     unsigned long long kfast[kZigN];
+    float x32[kZigN + 1], f32[kZigN + 1];
 };
 
 __device__ __forceinline__ void zig_stage(const ZigTable& t, ZigShared& z) {
     for (int q = threadIdx.x; q <= kZigN; q += blockDim.x) {
         z.x[q] = t.x[q];
         z.f[q] = t.f[q];
+        z.x32[q] = __double2float_rn(t.x[q]);
+        z.f32[q] = __double2float_rn(t.f[q]);
         if (q < kZigN) z.kfast[q] = t.kfast[q];
     }
     __syncthreads();
@@ -137,12 +141,29 @@ __device__ __forceinline__ int32_t zig_fast_q(unsigned long long u, double x) {
     return q > (unsigned long long)kZigQMax ? kZigQMax : (int32_t)q;
 }
 
-// Rounds after a first round that did not settle the entry (FP64; rare).
+// The wedge test f(x_L) + V (f(x_{L+1}) - f(x_L)) < exp(-z^2 / 2), z =
+// fl(u x_L 2^-53), decided in FP32 where the two sides differ by more than
+// 2^-16 relative: the FP32 evaluation (z from the top 32 bits of u, the
+// tables and V rounded to FP32, expf within 2 ulp) is within 5e-6 relative
+// of the FP64 one, so the decision is the FP64 decision.  1 keep, 0 reject,
+// -1 undecided (the FP64 test decides; 0.25 % of the wedge tests).
+__device__ __forceinline__ int zig_wedge32(unsigned long long u, uint32_t w2, int L, const ZigShared& Z) {
+    const float z = __fmul_rn(__uint2float_rn((uint32_t)(u >> 21)), __fmul_rn(Z.x32[L], 0x1p-32f));
+    const float V = __fmul_rn(__uint2float_rn(w2 >> 8), 0x1p-24f);  // V truncated to 24 bits
+    const float y = __fadd_rn(Z.f32[L], __fmul_rn(V, __fsub_rn(Z.f32[L + 1], Z.f32[L])));
+    const float e = expf(__fmul_rn(__fmul_rn(-0.5f, z), z));
+    const float tol = __fmul_rn(e, 0x1p-16f);
+    if (y < __fsub_rn(e, tol)) return 1;
+    if (y > __fadd_rn(e, tol)) return 0;
+    return -1;
+}
+
+// Rounds after a first round that did not settle the entry (rare).
 // w, L, neg: the first round's words, layer and sign.  Returns q.
 static __device__ __noinline__ int32_t gauss_slow_q(uint64_t seed, int64_t i, int64_t j, const ZigShared& Z, U4 w, int L,
                                              bool neg) {
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    double z = __dmul_rn((double)zig_u53(w.x, w.y), __dmul_rn(Z.x[L], 0x1p-53));
+    unsigned long long u = zig_u53(w.x, w.y);
     bool tail = L == 0;
     for (uint32_t k = 0; k < kZigRounds; ++k) {
         if (k > 0) {
@@ -150,12 +171,11 @@ static __device__ __noinline__ int32_t gauss_slow_q(uint64_t seed, int64_t i, in
             if (!tail) {
                 L = (int)(w.x & 255u);
                 neg = (w.x >> 8) & 1u;
-                const unsigned long long u = zig_u53(w.x, w.y);
+                u = zig_u53(w.x, w.y);
                 if (u < Z.kfast[L]) {
                     const int32_t q = zig_fast_q(u, Z.x[L]);
                     return neg ? -q : q;
                 }
-                z = __dmul_rn((double)u, __dmul_rn(Z.x[L], 0x1p-53));
                 if (L == 0) {
                     tail = true;
                     continue;
@@ -174,10 +194,18 @@ static __device__ __noinline__ int32_t gauss_slow_q(uint64_t seed, int64_t i, in
         } else if (tail) {
             continue;  // the first round only sent the draw to the tail
         }
-        // the wedge of layer L >= 1
-        const double V = zig_uniform53(w.z, w.w);
-        const double y = __dadd_rn(Z.f[L], __dmul_rn(V, __dsub_rn(Z.f[L + 1], Z.f[L])));
-        if (y < exp(__dmul_rn(__dmul_rn(-0.5, z), z))) return zig_grid_q(neg ? -z : z);
+        // the wedge of layer L >= 1 (the kept value is z's grid integer,
+        // formed on the integer units as in the first round)
+        const int wd = zig_wedge32(u, w.z, L, Z);
+        if (wd == 0) continue;
+        if (wd < 0) {
+            const double z = __dmul_rn((double)u, __dmul_rn(Z.x[L], 0x1p-53));
+            const double V = zig_uniform53(w.z, w.w);
+            const double y = __dadd_rn(Z.f[L], __dmul_rn(V, __dsub_rn(Z.f[L + 1], Z.f[L])));
+            if (!(y < exp(__dmul_rn(__dmul_rn(-0.5, z), z)))) continue;
+        }
+        const int32_t q = zig_fast_q(u, Z.x[L]);
+        return neg ? -q : q;
     }
     return 0;
 }

@@ -141,7 +141,8 @@ size_t ot_trsm_ws_bytes(int64_t m, int64_t n);
 lsq_status ot_trsm(const double* A, int64_t m, int64_t n, int64_t lda, const double* R, int64_t ldr, double* Ap,
                    int64_t ldap, void* ws, size_t ws_bytes, int32_t* err, cudaStream_t st);
 // C_out = C_in - X Y with FP64 accuracy on the tensor cores (X: M x K
-// column-major, ld ldx; Y entry (k, j) at Y[k sk + j sj]; K <= 512).
+// column-major, ld ldx; Y entry (k, j) at Y[k sk + j sj]; K <= 512, or
+// K <= 1024 with x_digits = 3).
 // xmode 2: X's digit planes were written by ot_gauss_digits (X unused).
 // x_digits = 3 when every row of X has at most three nonzero balanced
 // base-128 digits below its maximum (X on a 2^-17 grid, |X| < 8: the
@@ -153,7 +154,7 @@ lsq_status ot_gemm_update(const double* X, int64_t ldx, const double* Y, int64_t
                           size_t ws_bytes, int32_t* err, cudaStream_t st, int xmode = 0,
                           const int32_t* Eblk = nullptr, int64_t b0 = 0, int nbk = 0, int x_digits = 8);
 // The negated Gaussian operator's columns j0 .. j0 + kc - 1 (rows 0 .. s - 1,
-// kc <= 512) written as the X digit planes of an update's scratch ws (the
+// kc <= 1024) written as the X digit planes of an update's scratch ws (the
 // scratch of ot_gemm_update with M = s, N, K = kc), for ot_gemm_update with
 // xmode = 2 and x_digits = 3.
 lsq_status ot_gauss_digits(uint64_t seed, int64_t s, int64_t j0, int64_t kc, int64_t N, void* ws, size_t ws_bytes,

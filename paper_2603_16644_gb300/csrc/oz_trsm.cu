@@ -40,6 +40,7 @@ constexpr int OT_BM = 128, OT_BN = 64;      // output tile (rows x columns)
 constexpr int OT_BK = 64;                   // K per stage: 64 BF16 = 128 bytes
 constexpr int OT_XST = 6;                   // stages of X digit tiles
 constexpr int OT_KMAX = 512;                // exact FP32 group sums up to this K
+constexpr int OT_KMAX3 = 1024;              // the same with three X digits (at most 3 pairs per group)
 constexpr int OT_NB = 32;                   // diagonal block solved by substitution
 constexpr int OT_THREADS = 608;             // warp 0 TMA, warps 1-2 MMA, warps 3-18 epilogue
 constexpr int OT_XTILE = OT_BM * 128;       // bytes of one X digit tile
@@ -769,7 +770,7 @@ static OtUpd ot_upd_ptrs(void* ws, int64_t M, int64_t N, int64_t K) {
 
 lsq_status ot_gauss_digits(uint64_t seed, int64_t s, int64_t j0, int64_t kc, int64_t N, void* ws, size_t ws_bytes,
                            cudaStream_t st) {
-    if (s <= 0 || kc <= 0 || kc > OT_KMAX || !ws || ws_bytes < ot_update_ws_bytes(s, N, kc)) return LSQ_ERR_ARG;
+    if (s <= 0 || kc <= 0 || kc > OT_KMAX3 || !ws || ws_bytes < ot_update_ws_bytes(s, N, kc)) return LSQ_ERR_ARG;
     const OtUpd U = ot_upd_ptrs(ws, s, N, kc);
     const dim3 grid((unsigned)(U.Kp / 64), (unsigned)std::min<int64_t>(ceil_div(U.mp, 8), 256));
     k_ot_gauss_digits<<<grid, 256, 0, st>>>(zig_table(), seed, s, j0, kc, U.mp, U.Kp, U.Zx, U.Ex);
@@ -786,7 +787,10 @@ lsq_status ot_gemm_update(const double* X, int64_t ldx, const double* Y, int64_t
                           size_t ws_bytes, int32_t* err, cudaStream_t st, int xmode, const int32_t* Eblk, int64_t b0,
                           int nbk, int x_digits) {
     if (M <= 0 || N <= 0 || K <= 0) return LSQ_OK;
-    if (K > OT_KMAX || !ws || ws_bytes < ot_update_ws_bytes(M, N, K) || (x_digits != 3 && x_digits != OT_DIG))
+    // exact group sums: at most 8 pairs of digits (|d_t d_u| <= 2^12) per
+    // group over K <= 512, or 3 pairs over K <= 1024 with three X digits
+    if (K > (x_digits == 3 ? OT_KMAX3 : OT_KMAX) || !ws || ws_bytes < ot_update_ws_bytes(M, N, K) ||
+        (x_digits != 3 && x_digits != OT_DIG))
         return LSQ_ERR_ARG;
     const OtUpd U = ot_upd_ptrs(ws, M, N, K);
     CUtensorMap tzs, txs;

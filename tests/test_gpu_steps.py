@@ -112,11 +112,11 @@ def test_gaussian_sketch_within_rounding(prec):
     # both sums carry at most (m-1) u sum|terms|; operator entries may differ next to ties
     tol = 2 * m * u * scale + 2 ** -7 * np.abs(Ah).max() * 4
     if prec == O.FP64:
-        # the FP64 sketch is a sum of K chunks of 512 digit-sliced products,
-        # each accurate to 512 2^-50.6 2^3 max|A_chunk,c| (Omega sliced with
+        # the FP64 sketch is a sum of K chunks of 1024 digit-sliced products,
+        # each accurate to 1024 2^-50.6 2^3 max|A_chunk,c| (Omega sliced with
         # the fixed exponent 2^3 > |Omega|)
-        dig = sum(512 * 2.0 ** -50.6 * 8.0 * np.outer(np.ones(s), np.abs(Ah[k:k + 512, :]).max(axis=0))
-                  for k in range(0, m, 512))
+        dig = sum(1024 * 2.0 ** -50.6 * 8.0 * np.outer(np.ones(s), np.abs(Ah[k:k + 1024, :]).max(axis=0))
+                  for k in range(0, m, 1024))
         tol = tol + dig
     assert np.all(np.abs(to_np(As) - oAs) <= tol)
 

@@ -164,7 +164,7 @@ def test_fp32_gaussian_sketch_bf16_pieces(m, n, s):
 
 @pytest.mark.parametrize("m,n,s", [(1037, 113, 250), (3001, 70, 200), (700, 129, 130)])
 def test_fp64_gaussian_sketch_digit_sliced(m, n, s):
-    # FP64 sketch as K chunks of 512 FP64-accurate digit-sliced products:
+    # FP64 sketch as K chunks of 1024 FP64-accurate digit-sliced products:
     # elementwise against the oracle's sequential FP64 sum within both error
     # bounds, and against the exact rational value on sampled entries
     from fractions import Fraction
@@ -174,11 +174,11 @@ def test_fp64_gaussian_sketch_digit_sliced(m, n, s):
     As_tc, As_cc, ce = _sketch_both_ways(A, lsq.FP64, s, 29, True)
     oAs, _ = O.sketch(A, O.GAUSSIAN, s, 0, 29, O.FP64)
     Om = O.gaussian_operator(29, s, m, O.FP64)
-    # per chunk: digit error below 512 2^-50.6 2^3 max|A_chunk,c| (Omega is
+    # per chunk: digit error below 1024 2^-50.6 2^3 max|A_chunk,c| (Omega is
     # sliced with the fixed exponent 2^3 > |Omega|) and two FP64 roundings of
     # the running sum; the oracle: gamma_m sum|terms|
-    chunks = [slice(k, min(k + 512, m)) for k in range(0, m, 512)]
-    dig = sum(512 * 2.0 ** -50.6 * 8.0 * np.outer(np.ones(s), np.abs(A[c, :]).max(axis=0)) for c in chunks)
+    chunks = [slice(k, min(k + 1024, m)) for k in range(0, m, 1024)]
+    dig = sum(1024 * 2.0 ** -50.6 * 8.0 * np.outer(np.ones(s), np.abs(A[c, :]).max(axis=0)) for c in chunks)
     scale = np.abs(Om) @ np.abs(A)
     gamma = m * U64 / (1 - m * U64)
     tol = dig + 2 * gamma * scale
