@@ -448,9 +448,9 @@ size_t lsq_batched_workspace_size(int32_t hpne, int32_t count, const lsq_batch_p
  * CUDA graph launched on `stream`; the executable graph is cached and
  * replayed while the descriptors (pointers, shapes, options, workspace) stay
  * the same.  Problems with sketch_prec = AUTO or AUTO_SKETCH first get one
- * batched condition-estimate pass (the estimates one after another on one
- * internal stream, in a cached graph of its own) and one readback of the
- * chosen precisions (a stream synchronisation).  Each problem's status goes to its own info.
+ * batched condition-estimate pass (the same fan-out, in a cached graph of
+ * its own) and one readback of the chosen precisions (a stream
+ * synchronisation).  Each problem's status goes to its own info.
  * Every problem still runs its own kernel sequence inside the graph (no
  * single persistent kernel walks the batch).  Not thread safe: one batched
  * call at a time per process. */

@@ -201,11 +201,7 @@ lsq_status batched(bool hpne, int32_t count, const lsq_batch_problem* probs, voi
     int sms = device_sm_count();
 
     // resolve AUTO precisions: one batched estimate pass (a cached graph of
-    // its own), one readback.  The estimates run one after another on one
-    // internal stream: spread over all internal streams, the estimates of the
-    // 512-problem uneven batch raised a GPU exception (the cause was not
-    // found; the same estimates one at a time, and the solves' fan-out over
-    // all streams, run clean).
+    // its own), one readback
     std::vector<lsq_batch_problem> q(probs, probs + count);
     bool any_auto = false;
     for (int i = 0; i < count; ++i) any_auto |= is_auto(q[i].opts.sketch_prec);
@@ -220,8 +216,7 @@ lsq_status batched(bool hpne, int32_t count, const lsq_batch_problem* probs, voi
         unsigned char* et = ekey.data() + sizeof(lsq_batch_problem) * count;
         std::memcpy(et, &ws, sizeof(ws));
         std::memcpy(et + 8, &ws_bytes, sizeof(ws_bytes));
-        const std::vector<int> est_stream(count, 0);
-        r = capture_fanout(g_est, est_order, est_stream, slots, P.slot_bytes, ekey, st,
+        r = capture_fanout(g_est, est_order, P.stream_of, slots, P.slot_bytes, ekey, st,
                            [&](int i, cudaStream_t sk, char* slot) {
                                if (q[i].opts.sketch_prec == LSQ_AUTO)
                                    return launch_condest(q[i].A, q[i].m, q[i].n, q[i].lda, k0 + i, ch + i, slot,

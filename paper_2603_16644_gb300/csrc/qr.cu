@@ -251,6 +251,10 @@ __global__ void __launch_bounds__(QCT)
         for (int c = 0; c < QNB; ++c) P[c * Rp + i] = x[c];
     }
     __syncthreads();
+    // A CTA may write into another CTA's shared memory only once that CTA is
+    // running: without a previous panel (below) the first column's exchange
+    // is the first such write, so the cluster meets here first.
+    if (Vp == nullptr) cluster.sync();
     if (Vp != nullptr) {
         // The previous panel's reflectors applied to this panel's columns,
         // C <- (I - V_p T_p^T V_p^T) C over rows k0 - QNB .. s - 1 (V_p: QNB
