@@ -428,7 +428,7 @@ def oracle_parity(lsq, torch, dev):
 
 
 # ----------------------------------------------------------------------------- learned proposal
-def learned_eval(lsq, torch, count):
+def learned_eval(lsq, torch, count, batch=True):
     """The learned proposal (judged by the estimator on a sketch) on `count`
     uneven problems drawn like the batched workload, next to the estimator on
     a sketch alone and the paper's estimate on A^T A: solves/s of each arm,
@@ -438,9 +438,10 @@ def learned_eval(lsq, torch, count):
 
     params = learned.load()
     if params is None:
-        return {"unavailable": "no shipped weights"}
+        return {"unavailable": "no shipped weights"}, None
     probs = learned.c3_like_problems(count, seed=2604)
     res = learned.evaluate(params, probs)
+    batched = batched_eval(lsq, torch, probs[:min(count, 512)]) if batch else None
     used = res["learned"]["used"]
     names = {0: "fp8_e4m3", 1: "bf16", 2: "fp16", 3: "fp32", 4: "fp64"}
     ratio = [a / max(b, 1e-300) for a, b in zip(res["learned"]["errors"], res["auto_sketch"]["errors"])]
@@ -453,7 +454,71 @@ def learned_eval(lsq, torch, count):
                1 for a in res.values() for i in a["infos"] if i != 0)}
     del probs
     torch.cuda.empty_cache()
-    return out
+    return out, batched
+
+
+# ----------------------------------------------------------------------------- batched solver
+def batched_eval(lsq, torch, probs):
+    """The batched solver on uneven problems drawn like the batched workload
+    (the first `len(probs)` problems of the learned-proposal batch): sketch
+    kind and s in {2n, 4n} per shape bucket from the autotuner, precision per
+    problem from the estimate on a sketch (one batched estimate pass and one
+    readback per call), PNE with one refinement step, every problem's kernel
+    sequence in one cached CUDA-graph launch.  Timed over two calls after the
+    call that captures the graphs; beside it the same batch with the chosen
+    precisions given (the cached solve graph alone)."""
+    from paper_2603_16644_gb300.autotune import Autotuner
+
+    tuner = Autotuner()
+    As, bs, xs, infos, opts, kinds = [], [], [], [], [], []
+    for p in probs:
+        m, n = p["A"].shape
+        kind, s = tuner.choose(m, n, prec=lsq.FP32)
+        kinds.append(kind)
+        As.append(p["A"])
+        bs.append(p["b"])
+        xs.append(torch.empty(n, dtype=torch.float64, device=p["A"].device))
+        infos.append(torch.zeros(1, dtype=torch.int32, device=p["A"].device))
+        opts.append(lsq.make_opts(kind=kind, s=s, zeta=min(8, s), seed=p["seed"], sketch_prec=lsq.AUTO_SKETCH,
+                                  qr_prec=lsq.FP32, refine_steps=1))
+
+    def run(desc, ws, calls):
+        lsq.solve_batched(desc, ws)  # capture and first launch
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(calls):
+            lsq.solve_batched(desc, ws)
+        e1.record()
+        torch.cuda.synchronize()
+        return calls * len(probs) / (e0.elapsed_time(e1) / 1000.0)
+
+    desc = lsq.batch_descriptors(As, bs, xs, infos, opts)
+    ws = lsq.batched_workspace(desc)
+    value = run(desc, ws, 2)
+    errs = [float(torch.linalg.norm(x - p["x_star"]) / torch.linalg.norm(x)) for x, p in zip(xs, probs)]
+    bad = sum(1 for f in infos if int(f.item()) != 0)
+    del ws
+    chosen = [int(lsq.condest_sketch(p["A"], seed=p["seed"])[1].item()) for p in probs]
+    opts2 = [lsq.make_opts(kind=o.kind, s=o.s, zeta=o.zeta, seed=o.seed, sketch_prec=c,
+                           qr_prec=lsq.FP64 if c == lsq.FP64 else lsq.FP32, refine_steps=1)
+             for o, c in zip(opts, chosen)]
+    desc2 = lsq.batch_descriptors(As, bs, xs, infos, opts2)
+    ws2 = lsq.batched_workspace(desc2)
+    value2 = run(desc2, ws2, 2)
+    del ws2
+    torch.cuda.empty_cache()
+    names = {0: "fp8_e4m3", 1: "bf16", 2: "fp16", 3: "fp32", 4: "fp64"}
+    return {"problems": len(probs), "solves_per_s": value, "unit": "solves/s",
+            "solves_per_s_precisions_given": value2,
+            "workload": "m in [2000, 40000], n in [32, 512], kappa log-uniform [1e2, 1e10], residual log-uniform "
+                        "[1e-12, 1e-2]; sketch kind and s in {2n, 4n} from the autotuner, precision from the estimate "
+                        "on a sketch, PNE, one refinement; one cached graph of per-problem kernel sequences over 16 "
+                        "internal streams",
+            "sketch_kinds": {"gaussian": kinds.count(lsq.GAUSSIAN), "sparse_sign": kinds.count(lsq.SPARSE_SIGN)},
+            "precisions_used": {names[k]: chosen.count(k) for k in sorted(set(chosen))},
+            "median_rel_err_vs_xstar": float(np.median(errs)), "max_rel_err_vs_xstar": max(errs),
+            "infos_nonzero": bad}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -593,9 +658,9 @@ def main():
 
     # ---- learned precision proposal (shipped weights) on a fresh batch of
     # uneven problems, against the estimate alone and the paper's estimate on A^T A
-    c4 = None
+    c4 = c3 = None
     if rank == 0 and args.c4_problems > 0:
-        c4 = learned_eval(lsq, torch, args.c4_problems)
+        c4, c3 = learned_eval(lsq, torch, args.c4_problems)
 
     result = None
     if rank == 0:
@@ -649,6 +714,7 @@ def main():
             "accuracy": err_mixed,
             "oracle_parity_downscale": parity,
             "learned_proposal": c4,
+            "batched_uneven": c3,
         }
         print(json.dumps(result), flush=True)
     if dist is not None:

@@ -117,8 +117,8 @@ def test_learned_solve_matches_oracle_and_gains_over_the_estimate_on_AtA():
         # solution tolerance of the method at the precision the judged proposal used
         pr = SimpleNamespace(A=A, b=b)
         assert_solution_parity(res["learned"]["x"][k], ref["x"], xs_, p["kappa"], p["rho"], f"problem {k}",
-                               refined=True, u_p=used, realizations=oracle_realizations(pr, k=4, **kw),
-                               gpu_realizations=gpu_realizations(pr, k=4, **kw))
+                               refined=True, u_p=used, realizations=oracle_realizations(pr, k=8, **kw),
+                               gpu_realizations=gpu_realizations(pr, k=8, **kw))
         ch = O.condest(A)[1]
         lower += used < ch
     # the gain: problems the estimate on A^T A sends to a higher precision
