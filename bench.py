@@ -56,7 +56,8 @@ def parse():
     p.add_argument("--no-oracle-parity", action="store_true")
     p.add_argument("--c4-problems", type=int, default=1024,
                    help="uneven problems of the learned-proposal evaluation (0: skip)")
-    p.add_argument("--ncu-case", choices=["pne32", "pne64", "sketch32", "sketch64", "estimate"], default=None,
+    p.add_argument("--ncu-case", choices=["pne32", "pne64", "sketch32", "sketch64", "estimate", "uneven"],
+                   default=None,
                    help="run a bounded case for an ncu capture (2 calls on one problem of the workload shape) and exit")
     p.add_argument("--ncu-m", type=int, default=M, help="rows of the ncu case")
     return p.parse_args()
@@ -93,6 +94,8 @@ def ncu_case(args):
     import paper_2603_16644_gb300 as lsq
 
     torch.cuda.set_device(0)
+    if args.ncu_case == "uneven":
+        return ncu_case_uneven(lsq, torch)
     m = args.ncu_m
     g = torch.Generator(device="cuda").manual_seed(7)
     A = torch.randn((N, m), generator=g, dtype=torch.float64, device="cuda").t()
@@ -113,6 +116,35 @@ def ncu_case(args):
             lsq.sketch(A, opts)
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case": args.ncu_case, "m": m, "ok": True}))
+    return 0
+
+
+def ncu_case_uneven(lsq, torch, count=32):
+    """The first `count` problems of the batched workload's draw (the batch
+    timed by the benchmark), each solved by a single call one after another
+    (PNE, sparse-sign sketch of s = 2n, precision from the estimate on a
+    sketch, one refinement), twice: the second pass is the one to capture.
+    The problems are generated on the host (no device linear algebra)."""
+    from paper_2603_16644_gb300 import learned
+
+    probs = learned.c3_like_problems(count, seed=2604, device="cpu")
+    items = []
+    for p in probs:
+        A = lsq.colmajor(p["A"].to("cuda"))
+        m, n = A.shape
+        c = int(lsq.condest_sketch(A, seed=p["seed"])[1].item())
+        o = lsq.make_opts(kind=lsq.SPARSE_SIGN, s=2 * n, zeta=8, seed=p["seed"], sketch_prec=c,
+                          qr_prec=lsq.FP64 if c == lsq.FP64 else lsq.FP32, refine_steps=1)
+        items.append((A, p["b"].cuda(), o))
+    wsz = max(lsq.workspace_size(lsq.OP_PNE, A.shape[0], A.shape[1], o) for A, _, o in items)
+    ws = torch.empty(wsz, dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        n0 = lsq.launch_count()
+        for A, b, o in items:
+            lsq.pne(A, b, opts=o, ws=ws)
+        launches = lsq.launch_count() - n0
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": "uneven", "problems": count, "launches_per_pass": launches, "ok": True}))
     return 0
 
 

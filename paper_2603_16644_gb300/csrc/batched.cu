@@ -15,6 +15,7 @@
 #include "kernels.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -30,15 +31,26 @@ namespace {
 
 using namespace lsq;
 
-constexpr int kStreams = 16;
+constexpr int kMaxStreams = 64;
+
+// Internal streams of the fan-out: 16, or $LSQ_BATCH_STREAMS (1 .. 64), read
+// once per process.
+int n_streams() {
+    static const int ns = [] {
+        const char* e = std::getenv("LSQ_BATCH_STREAMS");
+        const int v = e ? std::atoi(e) : 16;
+        return v < 1 ? 1 : (v > kMaxStreams ? kMaxStreams : v);
+    }();
+    return ns;
+}
 
 struct BatchState {
     std::mutex mu;
     int dev = -1;
-    cudaStream_t sub[kStreams] = {};
+    cudaStream_t sub[kMaxStreams] = {};
     cudaStream_t cap = nullptr;  // the graph is captured here, never on the caller stream
     cudaEvent_t fork = nullptr;
-    cudaEvent_t join[kStreams] = {};
+    cudaEvent_t join[kMaxStreams] = {};
 };
 BatchState g_batch;
 
@@ -58,7 +70,7 @@ lsq_status ensure_streams() {
     int dev = 0;
     LSQ_CUDA_TRY(cudaGetDevice(&dev));
     if (g_batch.dev == dev && g_batch.fork) return LSQ_OK;
-    for (int k = 0; k < kStreams; ++k) {
+    for (int k = 0; k < n_streams(); ++k) {
         LSQ_CUDA_TRY(cudaStreamCreateWithFlags(&g_batch.sub[k], cudaStreamNonBlocking));
         LSQ_CUDA_TRY(cudaEventCreateWithFlags(&g_batch.join[k], cudaEventDisableTiming));
     }
@@ -86,10 +98,10 @@ Plan make_plan(bool hpne, int32_t count, const lsq_batch_problem* probs) {
     for (int i = 0; i < count; ++i) P.order[i] = i;
     std::stable_sort(P.order.begin(), P.order.end(),
                      [&](int a, int b) { return work_of(probs[a]) > work_of(probs[b]); });
-    double load[kStreams] = {};
+    double load[kMaxStreams] = {};
     for (int i : P.order) {
         int best = 0;
-        for (int k = 1; k < kStreams; ++k)
+        for (int k = 1; k < n_streams(); ++k)
             if (load[k] < load[best]) best = k;
         P.stream_of[i] = best;
         load[best] += work_of(probs[i]);
@@ -139,14 +151,14 @@ lsq_status capture_fanout(GraphCache& cache, const std::vector<int>& order, cons
     LSQ_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
     lsq_status cap = LSQ_OK;
     if (cudaEventRecord(g_batch.fork, cs) != cudaSuccess) cap = LSQ_ERR_CUDA;
-    for (int k = 0; k < kStreams && cap == LSQ_OK; ++k)
+    for (int k = 0; k < n_streams() && cap == LSQ_OK; ++k)
         if (cudaStreamWaitEvent(g_batch.sub[k], g_batch.fork, 0) != cudaSuccess) cap = LSQ_ERR_CUDA;
     for (int i : order) {
         if (cap != LSQ_OK) break;
         int k = stream_of[i];
         cap = run(i, g_batch.sub[k], slots + (size_t)k * slot_bytes);
     }
-    for (int k = 0; k < kStreams && cap == LSQ_OK; ++k) {
+    for (int k = 0; k < n_streams() && cap == LSQ_OK; ++k) {
         if (cudaEventRecord(g_batch.join[k], g_batch.sub[k]) != cudaSuccess) cap = LSQ_ERR_CUDA;
         else if (cudaStreamWaitEvent(cs, g_batch.join[k], 0) != cudaSuccess) cap = LSQ_ERR_CUDA;
     }
@@ -173,10 +185,10 @@ void assign_streams(const std::vector<double>& work, std::vector<int>& order, st
     stream_of.assign(count, 0);
     for (int i = 0; i < count; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
-    double load[kStreams] = {};
+    double load[kMaxStreams] = {};
     for (int i : order) {
         int best = 0;
-        for (int k = 1; k < kStreams; ++k)
+        for (int k = 1; k < n_streams(); ++k)
             if (load[k] < load[best]) best = k;
         stream_of[i] = best;
         load[best] += work[i];
@@ -195,7 +207,7 @@ lsq_status batched(bool hpne, int32_t count, const lsq_batch_problem* probs, voi
     if (r != LSQ_OK) return r;
     Plan P = make_plan(hpne, count, probs);
     char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-    size_t need = P.head_bytes + P.slot_bytes * kStreams + 256;
+    size_t need = P.head_bytes + P.slot_bytes * n_streams() + 256;
     if (!ws || need > ws_bytes) return LSQ_ERR_NOMEM;
     char* slots = base + P.head_bytes;
     int sms = device_sm_count();
@@ -283,7 +295,7 @@ lsq_status batched_steps(int tag, int32_t count, const Prob* probs, void* ws, si
     }
     slot = align_up(slot, 256);
     char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-    if (!ws || slot * kStreams + 512 > ws_bytes) return LSQ_ERR_NOMEM;
+    if (!ws || slot * n_streams() + 512 > ws_bytes) return LSQ_ERR_NOMEM;
     std::lock_guard<std::mutex> lk(g_batch.mu);
     lsq_status r = ensure_streams();
     if (r != LSQ_OK) return r;
@@ -299,7 +311,7 @@ lsq_status batched_steps(int tag, int32_t count, const Prob* probs, void* ws, si
                           [&](int i, cudaStream_t sk, char* sl) { return run(probs[i], sl, slot, sk); });
 }
 
-size_t batched_steps_ws(size_t slot) { return align_up(slot, 256) * kStreams + 512; }
+size_t batched_steps_ws(size_t slot) { return align_up(slot, 256) * n_streams() + 512; }
 
 }  // namespace
 
@@ -310,7 +322,7 @@ size_t lsq_batched_workspace_size(int32_t hpne, int32_t count, const lsq_batch_p
     for (int i = 0; i < count; ++i)
         if (check_problem(probs[i]) != LSQ_OK) return 0;
     Plan P = make_plan(hpne != 0, count, probs);
-    return P.head_bytes + P.slot_bytes * kStreams + 512;
+    return P.head_bytes + P.slot_bytes * n_streams() + 512;
 }
 
 lsq_status lsq_pne_solve_batched(int32_t count, const lsq_batch_problem* probs, void* ws, size_t ws_bytes,

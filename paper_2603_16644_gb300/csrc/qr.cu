@@ -487,69 +487,79 @@ __global__ void __launch_bounds__(QCT)
         // divergent single-lane phases, no shared-memory round trips).
         // Measured: the FP64 path 6.2 -> 23.5 solves/s; for FP32 the
         // shared-memory form below is faster (3.07 against 4.55 ms per solve).
-        T a[QRC];
+        // The loops run over QR = 8, 16 or 32 rows per lane, the fewest that
+        // hold the warp's rows: FP64 instructions issue at a small fraction of
+        // the FP32 rate on this GPU, so masked rows are not free (a 32-column
+        // panel of ~1000 rows took 0.53 ms with 32 rows per lane).
+        auto f64_cols = [&](auto qr_tag) {
+            constexpr int QR = decltype(qr_tag)::value;
+            T a[QR];
 #pragma unroll
-        for (int q = 0; q < QRC; ++q) a[q] = g0 + q < g1 ? P[lane * Rp + g0 + q] : (T)0;
-        const int gr0 = r0 + g0;  // global row (from k0) of a[0]
-        const int nv = g1 - g0;   // valid rows of this warp (<= 0: none)
-        auto row_of = [&](int row) -> T {
-            T v = (T)0;
+            for (int q = 0; q < QR; ++q) a[q] = g0 + q < g1 ? P[lane * Rp + g0 + q] : (T)0;
+            const int gr0 = r0 + g0;  // global row (from k0) of a[0]
+            const int nv = g1 - g0;   // valid rows of this warp (<= 0: none)
+            auto row_of = [&](int row) -> T {
+                T v = (T)0;
 #pragma unroll
-            for (int q = 0; q < QRC; ++q)
-                if (gr0 + q == row && q < nv) v = a[q];
-            return v;
+                for (int q = 0; q < QR; ++q)
+                    if (gr0 + q == row && q < nv) v = a[q];
+                return v;
+            };
+            // column c below row `row` on this warp's rows, from lane c
+            T xn[QR];
+            auto column_below = [&](int c, int row) {
+#pragma unroll
+                for (int q = 0; q < QR; ++q) {
+                    const T x = __shfl_sync(0xffffffffu, a[q], c);
+                    xn[q] = (q < nv && gr0 + q > row) ? x : (T)0;
+                }
+            };
+            column_below(0, 0);
+            if (0 >= gr0 && 0 < gr0 + nv) rowbuf[lane] = row_of(0);
+            {
+                T s4[4] = {(T)0, (T)0, (T)0, (T)0};  // 4 chains of 8 FMAs
+#pragma unroll
+                for (int q = 0; q < QR; ++q) s4[q & 3] = fma(xn[q], a[q], s4[q & 3]);
+                acc = lane < nb ? (s4[0] + s4[1]) + (s4[2] + s4[3]) : (T)0;
+            }
+            for (int jj = 0; jj < nb; ++jj) {
+                const Scal sc = exchange(jj, acc, rowbuf, 1);
+                // v_jj on this warp's rows: 0 above row jj, 1 on it, x / v1 below
+                T v[QR];
+#pragma unroll
+                for (int q = 0; q < QR; ++q) {
+                    const T x = __shfl_sync(0xffffffffu, a[q], jj);
+                    const int gr = gr0 + q;
+                    v[q] = (gr < jj || q >= nv) ? (T)0 : (gr == jj ? (T)1 : (sc.scale ? x * sc.rv1 : x));
+                }
+                // lane jj: its column becomes v (R diagonal mu on row jj); later
+                // columns: a_c -= w_c v
+                const bool own = lane == jj, upd = lane > jj && lane < nb && sc.b != (T)0;
+#pragma unroll
+                for (int q = 0; q < QR; ++q) {
+                    const int gr = gr0 + q;
+                    const T ownv = (q < nv && gr > jj) ? v[q] : ((q < nv && gr == jj) ? sc.mu : a[q]);
+                    a[q] = own ? ownv : (upd ? fma(-sc.wc, v[q], a[q]) : a[q]);
+                }
+                const int jn = jj + 1;
+                if (jn < nb) {
+                    column_below(jn, jn);
+                    if (jn >= gr0 && jn < gr0 + nv) rowbuf[lane] = row_of(jn);
+                }
+                // lanes c > jj: dots of column jj + 1; lanes i < jj: Y[i][jj]
+                const bool ylane = lane < jj, dlane = lane >= jn && lane < nb && jn < nb;
+                T s4[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll
+                for (int q = 0; q < QR; ++q) s4[q & 3] = fma(ylane ? v[q] : xn[q], a[q], s4[q & 3]);
+                acc = (ylane || dlane) ? (s4[0] + s4[1]) + (s4[2] + s4[3]) : (T)0;
+            }
+#pragma unroll
+            for (int q = 0; q < QR; ++q)
+                if (q < nv) P[lane * Rp + g0 + q] = a[q];
         };
-        // column c below row `row` on this warp's rows, from lane c
-        T xn[QRC];
-        auto column_below = [&](int c, int row) {
-#pragma unroll
-            for (int q = 0; q < QRC; ++q) {
-                const T x = __shfl_sync(0xffffffffu, a[q], c);
-                xn[q] = (q < nv && gr0 + q > row) ? x : (T)0;
-            }
-        };
-        column_below(0, 0);
-        if (0 >= gr0 && 0 < gr0 + nv) rowbuf[lane] = row_of(0);
-        {
-            T s4[4] = {(T)0, (T)0, (T)0, (T)0};  // 4 chains of 8 FMAs
-#pragma unroll
-            for (int q = 0; q < QRC; ++q) s4[q & 3] = fma(xn[q], a[q], s4[q & 3]);
-            acc = lane < nb ? (s4[0] + s4[1]) + (s4[2] + s4[3]) : (T)0;
-        }
-        for (int jj = 0; jj < nb; ++jj) {
-            const Scal sc = exchange(jj, acc, rowbuf, 1);
-            // v_jj on this warp's rows: 0 above row jj, 1 on it, x / v1 below
-            T v[QRC];
-#pragma unroll
-            for (int q = 0; q < QRC; ++q) {
-                const T x = __shfl_sync(0xffffffffu, a[q], jj);
-                const int gr = gr0 + q;
-                v[q] = (gr < jj || q >= nv) ? (T)0 : (gr == jj ? (T)1 : (sc.scale ? x * sc.rv1 : x));
-            }
-            // lane jj: its column becomes v (R diagonal mu on row jj); later
-            // columns: a_c -= w_c v
-            const bool own = lane == jj, upd = lane > jj && lane < nb && sc.b != (T)0;
-#pragma unroll
-            for (int q = 0; q < QRC; ++q) {
-                const int gr = gr0 + q;
-                const T ownv = (q < nv && gr > jj) ? v[q] : ((q < nv && gr == jj) ? sc.mu : a[q]);
-                a[q] = own ? ownv : (upd ? fma(-sc.wc, v[q], a[q]) : a[q]);
-            }
-            const int jn = jj + 1;
-            if (jn < nb) {
-                column_below(jn, jn);
-                if (jn >= gr0 && jn < gr0 + nv) rowbuf[lane] = row_of(jn);
-            }
-            // lanes c > jj: dots of column jj + 1; lanes i < jj: Y[i][jj]
-            const bool ylane = lane < jj, dlane = lane >= jn && lane < nb && jn < nb;
-            T s4[4] = {(T)0, (T)0, (T)0, (T)0};
-#pragma unroll
-            for (int q = 0; q < QRC; ++q) s4[q & 3] = fma(ylane ? v[q] : xn[q], a[q], s4[q & 3]);
-            acc = (ylane || dlane) ? (s4[0] + s4[1]) + (s4[2] + s4[3]) : (T)0;
-        }
-#pragma unroll
-        for (int q = 0; q < QRC; ++q)
-            if (q < nv) P[lane * Rp + g0 + q] = a[q];
+        if (chunk <= 8) f64_cols(std::integral_constant<int, 8>{});
+        else if (chunk <= 16) f64_cols(std::integral_constant<int, 16>{});
+        else f64_cols(std::integral_constant<int, QRC>{});
     } else if (chunk <= QRC) {
         // Each thread keeps its column's QRC rows of this warp in registers
         // (rows g0 + q); per column a warp broadcasts v_jj and x_{jj+1} through
