@@ -232,6 +232,9 @@ __global__ void __launch_bounds__(QCT)
     __shared__ __align__(16) T bcv[QCT / 32][QRC];  // per warp: v_jj on its rows
     __shared__ __align__(16) T bcx[QCT / 32][QRC];  // per warp: x_{jj+1} below its diagonal
     __shared__ T rowbuf[QNB];                      // row jj of the panel (owning CTA)
+    __shared__ T scal_sh[4];                       // FP64: mu, b, v1, 1 / v1 of the column (warp 0)
+    __shared__ T wc_sh[QNB];                       // FP64: w_c of the column (warp 0)
+    __shared__ int scale_sh;
     const int rank = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rows = (int)(s - k0);
@@ -428,29 +431,19 @@ __global__ void __launch_bounds__(QCT)
     };
     // Every per-row step (scaling of v, the update, the next column's dots)
     // stays within the warp's own rows, so a column needs one CTA barrier
-    // (the partial dots) and one cluster barrier (their exchange).
+    // (the partial dots) and one cluster barrier (their exchange), and for
+    // FP64 a second CTA barrier (the scalars from warp 0).
     // Column jj's exchange: the partials of every warp summed (part), pushed
     // with the diagonal row (rowv, from the CTA that owns row jj) into every
-    // CTA; after the cluster barrier every thread forms the same Householder
-    // scalars, w_c for its column and (rank 0) column jj - 1 of Y.
+    // CTA; after the cluster barrier every CTA forms the same Householder
+    // scalars, w_c for each column and (rank 0) column jj - 1 of Y.
     struct Scal {
         T mu, b, v1, rv1, wc;
         bool scale;
     };
-    auto exchange = [&](int jj, T acc, const T* rowsrc, int rowstride) -> Scal {
-        const int buf = jj & 1;
-        const int owner = (int)(jj / R);
-        part[warp][lane] = acc;
-        __syncthreads();
-        if (warp == 0) {
-            const T t = tree_sum<T, QCT / 32>(&part[0][lane], QNB);
-            for (int q = 0; q < QCL; ++q) *cluster.map_shared_rank(&all_part[buf][rank][lane], q) = t;
-            if (rank == owner) {
-                const T rv = rowsrc[lane * rowstride];
-                for (int q = 0; q < QCL; ++q) *cluster.map_shared_rank(&all_row[buf][lane], q) = rv;
-            }
-        }
-        cluster.sync();
+    // The Householder scalars of column jj from the exchanged partials (the
+    // same in every CTA) and, per lane c > jj, w_c.
+    auto scalars = [&](int jj, int buf, int owner) -> Scal {
         Scal sc;
         const T sigma = tree_sum<T, QCL>(&all_part[buf][0][jj], QNB);
         const T x1 = all_row[buf][jj];
@@ -477,6 +470,48 @@ __global__ void __launch_bounds__(QCT)
         if (tid == 0) bsh[jj] = sc.b;  // identical in every CTA of the cluster
         if (rank == owner && tid == 0) beta_out[k0 + jj] = sc.b;
         return sc;
+    };
+    auto exchange = [&](int jj, T acc, const T* rowsrc, int rowstride) -> Scal {
+        const int buf = jj & 1;
+        const int owner = (int)(jj / R);
+        part[warp][lane] = acc;
+        __syncthreads();
+        if (warp == 0) {
+            const T t = tree_sum<T, QCT / 32>(&part[0][lane], QNB);
+            for (int q = 0; q < QCL; ++q) *cluster.map_shared_rank(&all_part[buf][rank][lane], q) = t;
+            if (rank == owner) {
+                const T rv = rowsrc[lane * rowstride];
+                for (int q = 0; q < QCL; ++q) *cluster.map_shared_rank(&all_row[buf][lane], q) = rv;
+            }
+        }
+        cluster.sync();
+        Scal sc;
+        if constexpr (std::is_same<T, double>::value) {
+            // FP64 instructions issue at a small fraction of the FP32 rate: the
+            // scalars and the columns' w_c are formed once per CTA, by warp 0
+            // (every warp forming them kept the FP64 pipe 73 % busy on a panel
+            // of few rows), and read by the other warps from shared memory.
+            if (warp == 0) {
+                sc = scalars(jj, buf, owner);
+                if (lane == 0) {
+                    scal_sh[0] = sc.mu;
+                    scal_sh[1] = sc.b;
+                    scal_sh[2] = sc.v1;
+                    scal_sh[3] = sc.rv1;
+                    scale_sh = sc.scale ? 1 : 0;
+                }
+                wc_sh[lane] = sc.wc;
+            }
+            __syncthreads();
+            sc.mu = scal_sh[0];
+            sc.b = scal_sh[1];
+            sc.v1 = scal_sh[2];
+            sc.rv1 = scal_sh[3];
+            sc.scale = scale_sh != 0;
+            sc.wc = wc_sh[lane];
+            return sc;
+        }
+        return scalars(jj, buf, owner);
     };
     T acc;
     if (std::is_same<T, double>::value && chunk <= QRC) {
