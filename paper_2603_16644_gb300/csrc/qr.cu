@@ -855,8 +855,8 @@ __device__ __forceinline__ void qu_put(const QuRegs<T>& rg, T* __restrict__ Vs, 
     }
 }
 
-template <typename T>
-__global__ void __cluster_dims__(QUC, 1, 1) __launch_bounds__(QUT)
+template <typename T, int CL>
+__global__ void __launch_bounds__(QUT)
     k_qr_update(T* __restrict__ C, int64_t ldc, int64_t nt, const T* __restrict__ V, int64_t ldv, int nb,
                 const T* __restrict__ Tm, int64_t rows) {
     extern __shared__ __align__(16) unsigned char qu_raw[];
@@ -870,7 +870,7 @@ __global__ void __cluster_dims__(QUC, 1, 1) __launch_bounds__(QUT)
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
-    const int64_t c0 = (int64_t)(blockIdx.x / QUC) * 32;
+    const int64_t c0 = (int64_t)(blockIdx.x / CL) * 32;
     const int64_t ncols = min64(32, nt - c0);
     T* Cb = C + c0 * ldc;
     const int tid = threadIdx.x;
@@ -888,11 +888,11 @@ __global__ void __cluster_dims__(QUC, 1, 1) __launch_bounds__(QUT)
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
-        for (int64_t sb = rank; sb < nsub; sb += QUC) {
+        for (int64_t sb = rank; sb < nsub; sb += CL) {
             __syncthreads();
             qu_put<T>(rg, Vs, Cs);
             __syncthreads();
-            if (sb + QUC < nsub) qu_fetch<T>(rg, V, ldv, nb, Cb, ldc, ncols, rows, (sb + QUC) * QUR);
+            if (sb + CL < nsub) qu_fetch<T>(rg, V, ldv, nb, Cb, ldc, ncols, rows, (sb + CL) * QUR);
 #pragma unroll 2
             for (int s4 = 0; s4 < QUR / 16; ++s4) {
                 const int i = kg * (QUR / 4) + 4 * s4;
@@ -927,7 +927,7 @@ __global__ void __cluster_dims__(QUC, 1, 1) __launch_bounds__(QUT)
     for (int q = tid; q < 32 * 32; q += QUT) {
         const int p = q >> 5, c = q & 31;
         T w = (T)0;
-        for (int r = 0; r < QUC; ++r) w += cluster.map_shared_rank(Wr, r)[p * 33 + c];
+        for (int r = 0; r < CL; ++r) w += cluster.map_shared_rank(Wr, r)[p * 33 + c];
         Wf[p * 33 + c] = w;
     }
     // this CTA's reads of the other CTAs' partials are done; they may exit
@@ -943,11 +943,11 @@ __global__ void __cluster_dims__(QUC, 1, 1) __launch_bounds__(QUT)
     // 3. C -= V W2 over this CTA's sub-tiles
     {
         const int ti = tid & 31, tq = tid >> 5;  // rows 4 ti .. 4 ti + 3, columns 4 tq .. 4 tq + 3
-        for (int64_t sb = rank; sb < nsub; sb += QUC) {
+        for (int64_t sb = rank; sb < nsub; sb += CL) {
             __syncthreads();
             qu_put<T>(rg, Vs, Cs);
             __syncthreads();
-            if (sb + QUC < nsub) qu_fetch<T>(rg, V, ldv, nb, Cb, ldc, ncols, rows, (sb + QUC) * QUR);
+            if (sb + CL < nsub) qu_fetch<T>(rg, V, ldv, nb, Cb, ldc, ncols, rows, (sb + CL) * QUR);
             QuVec<T> cv[4];
 #pragma unroll
             for (int b = 0; b < 4; ++b) cv[b] = *(const QuVec<T>*)(Cs + qu_idx(4 * tq + b, 4 * ti));
@@ -1121,16 +1121,71 @@ static QrLayout qr_layout(int64_t s, int64_t n, int es) {
     return L;
 }
 
-// C (rows x nt, ld s) <- (I - V T^T V^T) C
+// Whether clusters of 16 update CTAs (non-portable size) can be scheduled
+// with the update's shared memory; decided once per device.
+template <typename T>
+static bool qu_cluster16_ok() {
+    static std::mutex mu;
+    static int known[64] = {};  // 0 unknown, 1 yes, 2 no
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (known[dev] == 0) {
+        const size_t sm = qu_smem_bytes<T>();
+        auto kern = k_qr_update<T, 16>;
+        bool ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) == cudaSuccess &&
+                  cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+        if (ok) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = 16;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(16);
+            cfg.blockDim = dim3(QUT);
+            cfg.dynamicSmemBytes = sm;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            ok = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters >= 1;
+        }
+        cudaGetLastError();
+        known[dev] = ok ? 1 : 2;
+    }
+    return known[dev] == 1;
+}
+
+// C (rows x nt, ld s) <- (I - V T^T V^T) C.  A cluster per 32 columns; FP64
+// updates of few columns (the in-block updates of the blocked FP64 QR: at
+// most 7 column tiles, 56 CTAs with 8 per cluster) take 16 CTAs per cluster
+// when there are rows for 16 (2048 or more), so that twice the SMs share
+// them.
 template <typename T>
 static lsq_status qr_apply(const T* V, const T* Tm, int nb, int64_t rows, T* C, int64_t s, int64_t nt,
                            cudaStream_t st) {
     if (nt <= 0) return LSQ_OK;
     const size_t sm = qu_smem_bytes<T>();
-    LSQ_CUDA_TRY(cudaFuncSetAttribute(k_qr_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    const unsigned grid = (unsigned)(ceil_div(nt, 32) * QUC);
-    k_qr_update<T><<<grid, QUT, sm, st>>>(C, s, nt, V, rows, nb, Tm, rows);
-    LSQ_LAUNCH_CHECK();
+    const int64_t ctiles = ceil_div(nt, 32);
+    const bool wide = std::is_same<T, double>::value && ctiles * 16 <= device_sm_count() &&
+                      ceil_div(rows, QUR) >= 16 && qu_cluster16_ok<T>();
+    const int cl = wide ? 16 : 8;
+    auto kern = wide ? k_qr_update<T, 16> : k_qr_update<T, 8>;
+    LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(ctiles * cl));
+    cfg.blockDim = dim3(QUT);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    LSQ_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, C, s, nt, V, rows, nb, Tm, rows));
+    note_launch();
     return LSQ_OK;
 }
 

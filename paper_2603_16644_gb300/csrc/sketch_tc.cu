@@ -267,13 +267,23 @@ bool sketch_tc_supported(int prec) {
 // less shared-memory and L2 traffic per flop than 128 x 128) when N fills them.
 static int tc_bn(int64_t N) { return N >= 256 ? 256 : TC_BN; }
 
-// Split count: fill the SMs when the tile grid is small; at least 4 stages of
-// K per split.
+// K blocks (128 bytes of K each) per split at most.  A wave of CTAs shares
+// its operand slabs through L2 only while its CTAs stay close in K; over a
+// long K they drift apart.  Measured on the FP32 sketch of the 262144 x 4096
+// problem (K = 1.57e6 BF16 pieces, 1024 output tiles): one split 105 ms,
+// splits of 4096 / 2048 / 1024 K blocks 111-117 ms, of 512 K blocks 60 ms
+// (1.8 PFLOP/s of tensor work).  Shorter accumulation chains in the FP32
+// accumulators are also more accurate.
+constexpr int64_t TC_KBLOCKS_MAX = 512;
+
+// Split count: fill the SMs when the tile grid is small, and at most
+// TC_KBLOCKS_MAX K blocks per split; at least 4 stages of K per split.
 static int tc_splits(int64_t M, int64_t N, int64_t K, int prec, int sms) {
     int64_t tiles = ceil_div(M, TC_BM) * ceil_div(N, tc_bn(N));
     int64_t bke = prec == LSQ_FP8_E4M3 ? 128 : 64;
     int64_t kblocks = ceil_div(K, bke);
     int64_t want = std::max<int64_t>(1, sms / std::max<int64_t>(1, tiles));
+    want = std::max<int64_t>(want, ceil_div(kblocks, TC_KBLOCKS_MAX));
     int64_t cap = std::max<int64_t>(1, kblocks / 4);
     return (int)std::min<int64_t>(std::min<int64_t>(want, cap), 64);
 }
