@@ -443,8 +443,10 @@ typedef struct {
 size_t lsq_batched_workspace_size(int32_t hpne, int32_t count, const lsq_batch_problem* probs);
 
 /* Alg. 1 with PNE (Eq. e_pne) or HPNE (Eq. e_hpne) on `count` independent
- * problems.  The problems are spread over 16 internal streams (heaviest
- * first, least-loaded stream) and the whole fan-out is captured into one
+ * problems.  The problems are spread over 16 internal streams (or
+ * $LSQ_BATCH_STREAMS, 1 to 64, read once per process; the workspace size
+ * grows with it), heaviest first to the least-loaded stream, and the whole
+ * fan-out is captured into one
  * CUDA graph launched on `stream`; the executable graph is cached and
  * replayed while the descriptors (pointers, shapes, options, workspace) stay
  * the same.  Problems with sketch_prec = AUTO or AUTO_SKETCH first get one
