@@ -313,6 +313,30 @@ def method_flops(m, n, s, sk64):
             "gram": float(m) * n * n, "factor": n ** 3 / 3.0}
 
 
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_ot_update_traffic_262144x4096.md")
+TRAFFIC_SOURCES = ("oz_trsm.cu", "tcgen05.cuh", "common.cuh")
+
+
+def update_traffic():
+    """DRAM bytes per k_ot_update launch over the timed region's launch mix,
+    from the ncu capture summarised in profiles/ -- or None when the kernel's
+    sources have changed since that capture."""
+    import hashlib
+
+    try:
+        text = open(TRAFFIC_PROFILE).read()
+        fields = dict(l.split(": ", 1) for l in text.splitlines() if l.startswith(("traffic_bytes", "source_sha")))
+        h = hashlib.sha256()
+        for f in TRAFFIC_SOURCES:
+            with open(os.path.join(ROOT, "paper_2603_16644_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+    except (OSError, ValueError):
+        return None
+    if h.hexdigest()[:16] != fields.get("source_sha16", "").strip():
+        return None
+    return float(fields["traffic_bytes_per_launch"])
+
+
 def roofline(stages, recs, per_solve_stage_ms, step_mix):
     """The dominant instrumented kernel of the timed region (by total time),
     with `achieved` = the METHOD's flops per launch / its CUDA-event time
@@ -350,9 +374,12 @@ def roofline(stages, recs, per_solve_stage_ms, step_mix):
         kname = "k_qr_panel_cl (sketch QR panel)"
     hw_tflops = work / (ms / 1000.0) / 1e12
     achieved = hw_tflops / emul
+    traffic = update_traffic() if top == "k_ot_update" else None
     out = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": unit_peak, "unit": "TFLOP/s",
-           "frac": achieved / unit_peak, "traffic": None,
-           "traffic_source": "see profiles/ (kernel changed since the last dram capture)",
+           "frac": achieved / unit_peak, "traffic": traffic,
+           "traffic_unit": "bytes per launch (dram read + write, mean over the launch mix)",
+           "traffic_source": "profiles/k_ot_update_traffic_262144x4096.md" if traffic is not None
+           else "none (the kernel changed since the last dram capture)",
            "peak_source": src if bound == "tensor" else "nominal CUDA-core FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz)",
            "launches": cnt, "avg_launch_ms": ms / cnt, "emulation_factor": emul,
            "tensor_pipe_tflops": hw_tflops, "tensor_pipe_frac": hw_tflops / unit_peak if bound == "tensor" else None,
