@@ -370,6 +370,31 @@ __device__ __forceinline__ double ot_fixed_to_double(long long hi, long long lo,
 // register file (16 K registers) then allows 96 registers per thread.
 constexpr int OT_EPI_WARPS = 16;
 
+// Tile t -> (first row, first column).  GROUPED: bands of OT_GM row tiles
+// with the row tiles fastest inside a band, so that a wave of CTAs spans about
+// OT_GM row tiles and gridDim / OT_GM column tiles and shares the digit tiles
+// of both operands through L2.  The FP64 sketch's 64 x 64 tiles use it: with
+// the column tiles fastest over all rows a wave spanned 2.4 row tiles and read
+// the Y digit planes once per wave (2.3 -> 1.1 GB of DRAM traffic per launch,
+// 1.7 % less time).  The TRSM updates (many row tiles, few column tiles) keep
+// the column tiles fastest: a CTA then stays on one column tile, and the
+// banded order raised their traffic by 30 % at the same time.
+constexpr int OT_GM = 8;
+template <bool GROUPED>
+__device__ __forceinline__ void ot_tile_coords(int t, int ntj, int nti, int64_t& i0, int64_t& j0) {
+    if (!GROUPED) {
+        i0 = (int64_t)(t / ntj) * OT_BM;
+        j0 = (int64_t)(t % ntj) * OT_BN;
+        return;
+    }
+    const int per = OT_GM * ntj;
+    const int first = (t / per) * OT_GM;
+    const int gs = min(nti - first, OT_GM);
+    const int w = t % per;
+    i0 = (int64_t)(first + w % gs) * OT_BM;
+    j0 = (int64_t)(w / gs) * OT_BN;
+}
+
 // XD: digits of X taken (8, or 3 when X's lower digits are known to vanish);
 // pairs (t, u) with t < XD and t + u <= 7.
 template <int XD>
@@ -427,8 +452,7 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
         auto slab_tile = [&](int g, int64_t& i0, int64_t& j0, int& s) {
             const int tl = (int)blockIdx.x + (g / nslab) * (int)gridDim.x;
             s = g % nslab;
-            i0 = (int64_t)(tl / ntj) * OT_BM;
-            j0 = (int64_t)(tl % ntj) * OT_BN;
+            ot_tile_coords<XD == 3>(tl, ntj, ntiles / ntj, i0, j0);
         };
         auto load_y = [&](int g) -> bool {
             int64_t i0, j0;
@@ -597,7 +621,8 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
         };
         for (int i = 0; i < ntl; ++i) {
             const int tile = (int)blockIdx.x + i * (int)gridDim.x;
-            const int64_t i0 = (int64_t)(tile / ntj) * OT_BM, j0 = (int64_t)(tile % ntj) * OT_BN;
+            int64_t i0, j0;
+            ot_tile_coords<XD == 3>(tile, ntj, ntiles / ntj, i0, j0);
             const int64_t row = i0 + quad * 32 + lane;
             const bool narrow = N - j0 <= 32;
             const int64_t c0 = j0 + cq * (narrow ? 8 : 16);
