@@ -284,42 +284,54 @@ static OzPlan oz_plan(int64_t m, int64_t n, bool sym) {
 size_t oz_gram_ws_bytes(int64_t m, int64_t n) { return oz_plan(m, n, true).total; }
 size_t oz_gemm_tn_ws_bytes(int64_t m, int64_t n) { return oz_plan(m, n, false).total; }
 
-// Tile list (ordered so that neighbouring CTAs share the Y rows of a pair)
-// and the (t, u, P, Q) -> half-tile map (2 k + (Q & 1) for tile k, i.e. the
-// 128 x 128 block at (2 k + (Q & 1)) 16384 of the output), built on the
-// device in a fixed order (no host copies: the call stays capturable in a
-// CUDA graph).  One CTA: the tiles of each (u, Qp) are counted, prefix summed
-// in (u, Qp) order, and each (u, Qp) range is filled by its own thread, so the
-// list is the sequential enumeration u, Qp, t, P.
+// Tile list and the (t, u, P, Q) -> half-tile map (2 k + (Q & 1) for tile
+// k, i.e. the 128 x 128 block at (2 k + (Q & 1)) 16384 of the output), built
+// on the device in a fixed order (no host copies: the call stays capturable
+// in a CUDA graph).  A tile pairs X tile (t, P) (digit t, 128 rows) with Y
+// tile (u, Qp) (digit u, 256 rows).  The X tiles are taken in groups of
+// OZ_GX; inside a group the Y tiles run outer and the group's X tiles inner,
+// so that a wave of 152 CTAs spans about OZ_GX X tiles and 152 / OZ_GX Y
+// tiles and both are shared through L2 while the wave moves along K (with
+// the Y tiles outer over all X tiles a wave read ~152 distinct X tiles).  One
+// CTA: each group's tiles are counted by one thread, prefix summed in group
+// order, and each group's range is filled by its thread.
+constexpr int OZ_GX = 16;
+
+__device__ __forceinline__ bool oz_tile_valid(int t, int64_t P, int u, int64_t Qp, int sym) {
+    if (t + u > OZ_S - 1 || (sym && t > u)) return false;
+    return !(sym && t == u && P < 2 * Qp);  // P >= 2 Qp when t == u
+}
+
 __global__ void k_oz_tiles(int64_t nb, int64_t np, int sym, int2* __restrict__ tiles, int32_t* __restrict__ map) {
-    extern __shared__ int32_t oz_cnt[];  // OZ_S * nq + 1
+    extern __shared__ int32_t oz_cnt[];  // groups + 1
     const int64_t nq = (nb + 1) / 2;
-    const int64_t nuq = (int64_t)OZ_S * nq;
+    const int64_t nx = (int64_t)OZ_S * nb, ny = (int64_t)OZ_S * nq;
+    const int64_t groups = (nx + OZ_GX - 1) / OZ_GX;
     for (int64_t q = threadIdx.x; q < (int64_t)OZ_S * OZ_S * nb * nb; q += blockDim.x) map[q] = -1;
-    for (int64_t uq = threadIdx.x; uq < nuq; uq += blockDim.x) {
-        const int u = (int)(uq / nq);
-        const int64_t Qp = uq % nq;
+    for (int64_t g = threadIdx.x; g < groups; g += blockDim.x) {
         int32_t c = 0;
-        for (int t = 0; t < OZ_S; ++t) {
-            if (t + u > OZ_S - 1 || (sym && t > u)) continue;
-            c += (int32_t)((sym && t == u) ? nb - 2 * Qp : nb);  // P >= 2 Qp when t == u
-        }
-        oz_cnt[uq + 1] = c;
+        const int64_t x1 = min(nx, (g + 1) * OZ_GX);
+        for (int64_t yj = 0; yj < ny; ++yj)
+            for (int64_t xi = g * OZ_GX; xi < x1; ++xi)
+                c += oz_tile_valid((int)(xi / nb), xi % nb, (int)(yj / nq), yj % nq, sym) ? 1 : 0;
+        oz_cnt[g + 1] = c;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         oz_cnt[0] = 0;
-        for (int64_t uq = 0; uq < nuq; ++uq) oz_cnt[uq + 1] += oz_cnt[uq];
+        for (int64_t g = 0; g < groups; ++g) oz_cnt[g + 1] += oz_cnt[g];
     }
     __syncthreads();
-    for (int64_t uq = threadIdx.x; uq < nuq; uq += blockDim.x) {
-        const int u = (int)(uq / nq);
-        const int64_t Qp = uq % nq;
-        int32_t k = oz_cnt[uq];
-        for (int t = 0; t < OZ_S; ++t) {
-            if (t + u > OZ_S - 1 || (sym && t > u)) continue;
-            for (int64_t Pb = 0; Pb < nb; ++Pb) {
-                if (sym && t == u && Pb < 2 * Qp) continue;
+    for (int64_t g = threadIdx.x; g < groups; g += blockDim.x) {
+        int32_t k = oz_cnt[g];
+        const int64_t x1 = min(nx, (g + 1) * OZ_GX);
+        for (int64_t yj = 0; yj < ny; ++yj) {
+            const int u = (int)(yj / nq);
+            const int64_t Qp = yj % nq;
+            for (int64_t xi = g * OZ_GX; xi < x1; ++xi) {
+                const int t = (int)(xi / nb);
+                const int64_t Pb = xi % nb;
+                if (!oz_tile_valid(t, Pb, u, Qp, sym)) continue;
                 for (int h = 0; h < 2; ++h) {
                     const int64_t Q = 2 * Qp + h;
                     if (Q < nb && !(sym && t == u && Q > Pb))
@@ -348,7 +360,7 @@ static lsq_status oz_run(const double* X, int64_t ldx, const double* Y, int64_t 
     int32_t* map = (int32_t*)(base + P.z_bytes + P.t_bytes + P.tiles_bytes);
     int32_t* ex = (int32_t*)(base + P.z_bytes + P.t_bytes + P.tiles_bytes + P.map_bytes);
     int32_t* ey = sym ? ex : (int32_t*)((char*)ex + eb);
-    const size_t tsm = sizeof(int32_t) * (size_t)(OZ_S * ceil_div(P.nb, 2) + 1);
+    const size_t tsm = sizeof(int32_t) * (size_t)(ceil_div((int64_t)OZ_S * P.nb, OZ_GX) + 1);
     if (tsm > 48 * 1024) return LSQ_ERR_ARG;
     k_oz_tiles<<<1, 256, tsm, st>>>(P.nb, P.np, sym ? 1 : 0, tiles, map);
     LSQ_LAUNCH_CHECK();
