@@ -342,8 +342,8 @@ def roofline(stages, recs, per_solve_stage_ms, step_mix):
     with `achieved` = the METHOD's flops per launch / its CUDA-event time
     against the measured dense BF16 peak (GB300 has no FP64 tensor path; the
     FP64 products are emulated by BF16/FP8 digit slicing, reported as
-    `emulation_factor` and `tensor_pipe_frac`), and the whole-solve
-    sum(t_min) / t_measured of the survey's per-step rooflines."""
+    `emulation_factor` and `tensor_pipe_frac`).  The traffic figure comes
+    from the DRAM capture summarised in profiles/."""
     peak, src = bf16_peak()
     cand = {}
     for key in ("k_ot_update", "k_qr_panel", "k_sketch_tc"):
@@ -389,8 +389,8 @@ def roofline(stages, recs, per_solve_stage_ms, step_mix):
 
 def whole_solve_roofline(per_solve_stage_ms, flops):
     """sum over steps of t_min = work / peak of the step's unit, over the
-    measured time of the steps: (a) as the survey's table reads, with the FP64
-    steps at the FP64 CUDA-core rate (nominal; the emulated products beat it,
+    measured time of the steps: (a) with each step at the peak of the unit the
+    method's arithmetic names, the FP64 steps at the FP64 CUDA-core rate (nominal; the emulated products beat it,
     so this exceeds 1), (b) with every FP64 step at the BF16 tensor peak with
     no emulation credit."""
     peak, _ = bf16_peak()
