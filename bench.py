@@ -56,7 +56,7 @@ def parse():
     p.add_argument("--no-oracle-parity", action="store_true")
     p.add_argument("--c4-problems", type=int, default=1024,
                    help="uneven problems of the learned-proposal evaluation (0: skip)")
-    p.add_argument("--ncu-case", choices=["pne32", "pne64", "sketch32", "sketch64", "estimate", "uneven"],
+    p.add_argument("--ncu-case", choices=["pne32", "pne64", "sketch32", "sketch64", "estimate", "uneven", "tall"],
                    default=None,
                    help="run a bounded case for an ncu capture (2 calls on one problem of the workload shape) and exit")
     p.add_argument("--ncu-m", type=int, default=M, help="rows of the ncu case")
@@ -96,6 +96,21 @@ def ncu_case(args):
     torch.cuda.set_device(0)
     if args.ncu_case == "uneven":
         return ncu_case_uneven(lsq, torch)
+    if args.ncu_case == "tall":
+        # the 65536 x 1024 tall-skinny workload: sparse-sign sketch s = 4n,
+        # 8 nonzeros per column, BF16 sketch, FP32 QR, one refinement step
+        m, n = 65536, 1024
+        g = torch.Generator(device="cuda").manual_seed(7)
+        A = torch.randn((n, m), generator=g, dtype=torch.float64, device="cuda").t()
+        b = torch.randn(m, generator=g, dtype=torch.float64, device="cuda")
+        opts = lsq.make_opts(kind=lsq.SPARSE_SIGN, s=4 * n, zeta=8, seed=7, sketch_prec=lsq.BF16,
+                             qr_prec=lsq.FP32, refine_steps=1)
+        ws = lsq.workspace(lsq.OP_PNE, m, n, opts)
+        for _ in range(2):
+            lsq.pne(A, b, opts=opts, ws=ws)
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": "tall", "m": m, "n": n, "ok": True}))
+        return 0
     m = args.ncu_m
     g = torch.Generator(device="cuda").manual_seed(7)
     A = torch.randn((N, m), generator=g, dtype=torch.float64, device="cuda").t()
