@@ -56,7 +56,7 @@ def parse():
     p.add_argument("--no-oracle-parity", action="store_true")
     p.add_argument("--c4-problems", type=int, default=1024,
                    help="uneven problems of the learned-proposal evaluation (0: skip)")
-    p.add_argument("--ncu-case", choices=["pne32", "pne64", "sketch32", "sketch64", "estimate", "uneven", "tall"],
+    p.add_argument("--ncu-case", choices=["pne32", "pne64", "sketch32", "sketch64", "estimate", "uneven", "tall", "trsm64"],
                    default=None,
                    help="run a bounded case for an ncu capture (2 calls on one problem of the workload shape) and exit")
     p.add_argument("--ncu-m", type=int, default=M, help="rows of the ncu case")
@@ -96,6 +96,25 @@ def ncu_case(args):
     torch.cuda.set_device(0)
     if args.ncu_case == "uneven":
         return ncu_case_uneven(lsq, torch)
+    if args.ncu_case == "trsm64":
+        # A_p = A R^{-1} and its Gram with the tensor-core FP64 products
+        # switched off (the FP64 CUDA-core kernels), 65536 x 1024, R a
+        # well-conditioned upper triangle
+        m, n = 65536, 1024
+        g = torch.Generator(device="cuda").manual_seed(7)
+        A = torch.randn((n, m), generator=g, dtype=torch.float64, device="cuda").t()
+        b = torch.randn(m, generator=g, dtype=torch.float64, device="cuda")
+        R = torch.triu(torch.randn((n, n), generator=g, dtype=torch.float64, device="cuda")) * (0.1 / n ** 0.5)
+        R = lsq.colmajor(R + torch.eye(n, dtype=torch.float64, device="cuda"))
+        prev = lsq.set_fp64_emulation(False)
+        try:
+            for _ in range(2):
+                lsq.trsm_gram(A, R, b)
+            torch.cuda.synchronize()
+        finally:
+            lsq.set_fp64_emulation(prev)
+        print(json.dumps({"ncu_case": "trsm64", "m": m, "n": n, "ok": True}))
+        return 0
     if args.ncu_case == "tall":
         # the 65536 x 1024 tall-skinny workload: sparse-sign sketch s = 4n,
         # 8 nonzeros per column, BF16 sketch, FP32 QR, one refinement step
